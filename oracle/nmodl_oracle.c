@@ -1,0 +1,442 @@
+/*
+ * nmodl_oracle.c -- plain FP64 CPU oracle of the NMODL mechanism hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only tests/, __graft_entry__.smoke() and the cpu_baseline /
+ * reference legs of bench.py use it.  It shares no code, header, table or
+ * constant with the CUDA library.
+ *
+ * Every routine is the definition written out: scalar loops per instance in
+ * double precision, libm exp/expm1/pow, a dense LU with partial pivoting.
+ * No blocking, fusion or reordering.  Build with -O2 -ffp-contract=off so
+ * that no multiply-add is fused behind the reader's back.
+ *
+ * What the paper fixes, and the readings taken where it is silent:
+ *  - Section 1 / Fig. 1: each mechanism has a state update (nrn_state) and
+ *    a current update (nrn_cur) kernel, called once per time step.
+ *  - Section 3 (BREAKPOINT bullet) and Section 5.2 (CONDUCTANCE): the
+ *    current of an ohmic channel is i = g (v - e) and its derivative
+ *    dI/dv = g is taken analytically.  Reading: the current update
+ *    scatter-adds rhs[node] -= i and d[node] += g (NEURON convention).
+ *  - Section 5.1 / 5.2 (cnexp): a linear, independent gate ODE
+ *    m' = (minf - m)/mtau is integrated exactly with minf, mtau held
+ *    constant over the step:  m += (1 - exp(-dt/mtau)) (minf - m).
+ *  - Section 5.1 / 5.2 (KINETIC -> DERIVATIVE, implicit Euler, sparse and
+ *    derivimplicit) and Section 5.3 (PartialPivLU, Newton with the exact
+ *    Jacobian): a mass-action scheme becomes x' = A(v) x; one implicit
+ *    Euler step solves F(y) = y - x - dt A y = 0 by Newton with J = I - dt A.
+ *  - Readings (not in the paper): Hodgkin-Huxley 1952 rates in the modern
+ *    convention; the step order zero -> cur (mechanism list order,
+ *    ascending instance) -> d += 1e-3 cm/dt -> v += rhs/d -> state; the
+ *    3x3 lattice topology of the 9-state scheme; vtrap evaluated through
+ *    expm1 with a 3-term Taylor branch for |x/y| < 1e-6.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_TYPE_HH 1
+#define ORC_TYPE_CNEXP 2
+#define ORC_TYPE_KIN9 3
+
+/* ---------------------------------------------------------------- rates */
+
+/* vtrap(x, y) = x / (exp(x/y) - 1), the HH "linoid" rate shape; continuous
+ * at x = 0 where it equals y.  expm1 evaluates the same function without the
+ * cancellation of exp(x/y) - 1 near zero. */
+double orc_vtrap(double x, double y)
+{
+    double u = x / y;
+    if (fabs(u) < 1e-6)
+        return y * (1.0 - u / 2.0 + u * u / 12.0);
+    return x / expm1(u);
+}
+
+/* Hodgkin-Huxley (1952) gate rates, modern sign convention, in 1/ms.
+ * minf = alpha/(alpha+beta), mtau = 1/(q10 (alpha+beta)) (rates procedure
+ * of the HH example channel; Section 3 inlining / localiser discussion). */
+void orc_hh_rates(const double *p, double v, double minf[3], double mtau[3])
+{
+    double celsius = p[6];
+    double q10 = pow(3.0, (celsius - 6.3) / 10.0);
+    double a, b;
+    /* m */
+    a = 0.1 * orc_vtrap(-(v + 40.0), 10.0);
+    b = 4.0 * exp(-(v + 65.0) / 18.0);
+    minf[0] = a / (a + b);
+    mtau[0] = 1.0 / (q10 * (a + b));
+    /* h */
+    a = 0.07 * exp(-(v + 65.0) / 20.0);
+    b = 1.0 / (1.0 + exp(-(v + 35.0) / 10.0));
+    minf[1] = a / (a + b);
+    mtau[1] = 1.0 / (q10 * (a + b));
+    /* n */
+    a = 0.01 * orc_vtrap(-(v + 55.0), 10.0);
+    b = 0.125 * exp(-(v + 65.0) / 80.0);
+    minf[2] = a / (a + b);
+    mtau[2] = 1.0 / (q10 * (a + b));
+}
+
+/* Generic rate shapes of the cnexp channel family, u = (v - vh)/k. */
+double orc_rate(int form, double A, double vh, double k, double v)
+{
+    double u = (v - vh) / k;
+    switch (form) {
+    case 0: /* EXP */
+        return A * exp(u);
+    case 1: /* SIGMOID */
+        return A / (1.0 + exp(-u));
+    case 2: /* LINOID: A u / (1 - exp(-u)) = A vtrap(-u, 1) */
+        if (fabs(u) < 1e-6)
+            return A * (1.0 + u / 2.0 + u * u / 12.0);
+        return A * u / (-expm1(-u));
+    default:
+        return NAN;
+    }
+}
+
+/* minf and mtau of gate g of a CNEXP block at voltage v. */
+void orc_cnexp_rates(const double *p, int g, double v, double *minf, double *mtau)
+{
+    const double *q = p + 6 + 9 * g;
+    double phi = pow(p[3], (p[4] - p[5]) / 10.0);
+    double a = orc_rate((int)q[1], q[2], q[3], q[4], v);
+    double b = orc_rate((int)q[5], q[6], q[7], q[8], v);
+    *minf = a / (a + b);
+    *mtau = 1.0 / (phi * (a + b));
+}
+
+static int n_gates_of(int type, const double *p)
+{
+    if (type == ORC_TYPE_HH) return 3;
+    if (type == ORC_TYPE_CNEXP) return (int)p[0];
+    if (type == ORC_TYPE_KIN9) return 9;
+    return -1;
+}
+
+/* -------------------------------------------------------- init / state */
+
+/* Gates start at their steady state minf(v) (INITIAL block convention). */
+static void cnexp_like_init(int type, int64_t n, const int32_t *ni,
+                            const double *v, const double *p, double *s)
+{
+    int ng = n_gates_of(type, p);
+    for (int64_t i = 0; i < n; ++i) {
+        double vv = v[ni[i]];
+        for (int g = 0; g < ng; ++g) {
+            double minf, mtau;
+            if (type == ORC_TYPE_HH) {
+                double mi[3], mt[3];
+                orc_hh_rates(p, vv, mi, mt);
+                minf = mi[g];
+                (void)mt;
+            } else {
+                orc_cnexp_rates(p, g, vv, &minf, &mtau);
+            }
+            s[g * n + i] = minf;
+        }
+    }
+}
+
+/* cnexp (Section 5.2): exact solution of m' = (minf - m)/mtau over dt with
+ * minf, mtau frozen at the new voltage. */
+static void cnexp_like_state(int type, int64_t n, const int32_t *ni,
+                             const double *v, const double *p, double dt,
+                             double *s)
+{
+    int ng = n_gates_of(type, p);
+    for (int64_t i = 0; i < n; ++i) {
+        double vv = v[ni[i]];
+        double minf[3], mtau[3];
+        if (type == ORC_TYPE_HH) {
+            orc_hh_rates(p, vv, minf, mtau);
+        } else {
+            for (int g = 0; g < ng; ++g)
+                orc_cnexp_rates(p, g, vv, &minf[g], &mtau[g]);
+        }
+        for (int g = 0; g < ng; ++g) {
+            double m = s[g * n + i];
+            s[g * n + i] = m + (1.0 - exp(-dt / mtau[g])) * (minf[g] - m);
+        }
+    }
+}
+
+/* -------------------------------------------------------------- currents */
+
+/* Per-instance current i [mA/cm2] and conductance g = dI/dv [S/cm2]. */
+static void instance_current(int type, int64_t n, int64_t i, double vv,
+                             const double *p, const double *s,
+                             double *cur, double *cond)
+{
+    if (type == ORC_TYPE_HH) {
+        double m = s[i], h = s[n + i], nn = s[2 * n + i];
+        double gna = p[0] * m * m * m * h;
+        double gk = p[1] * nn * nn * nn * nn;
+        double gl = p[2];
+        *cur = gna * (vv - p[3]) + gk * (vv - p[4]) + gl * (vv - p[5]);
+        *cond = gna + gk + gl;
+    } else if (type == ORC_TYPE_CNEXP) {
+        int ng = (int)p[0];
+        double g = p[1];
+        for (int k = 0; k < ng; ++k) {
+            int pw = (int)p[6 + 9 * k];
+            double x = s[k * n + i];
+            for (int e = 0; e < pw; ++e)
+                g *= x;
+        }
+        *cur = g * (vv - p[2]);
+        *cond = g;
+    } else { /* KIN9: open-state occupancy */
+        int op = (int)p[2];
+        double g = p[0] * s[op * n + i];
+        *cur = g * (vv - p[1]);
+        *cond = g;
+    }
+}
+
+/* Current update: rhs[node] -= i, d[node] += g, ascending instance order. */
+void orc_mech_cur(int type, int64_t n, const int32_t *ni, const double *v,
+                  const double *p, const double *s, double *rhs, double *d)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double c, g;
+        instance_current(type, n, i, v[ni[i]], p, s, &c, &g);
+        rhs[ni[i]] -= c;
+        d[ni[i]] += g;
+    }
+}
+
+/* Per-instance current and conductance, for instance-level checks. */
+void orc_mech_currents(int type, int64_t n, const int32_t *ni, const double *v,
+                       const double *p, const double *s, double *cur, double *cond)
+{
+    for (int64_t i = 0; i < n; ++i)
+        instance_current(type, n, i, v[ni[i]], p, s, &cur[i], &cond[i]);
+}
+
+/* ------------------------------------------------------------ kinetic 9 */
+
+/* Generator matrix of the 3x3 lattice scheme, row-major A[r*9+c]:
+ * A[j][i] = rate i->j for i != j and A[i][i] = -(sum of rates out of i),
+ * so x' = A x conserves sum(x) (KINETIC -> DERIVATIVE, Section 5.1). */
+void orc_kin9_matrix(const double *p, double v, double *A)
+{
+    static const int edges[12][2] = {
+        {0, 1}, {1, 2}, {3, 4}, {4, 5}, {6, 7}, {7, 8},
+        {0, 3}, {1, 4}, {2, 5}, {3, 6}, {4, 7}, {5, 8}};
+    memset(A, 0, 81 * sizeof(double));
+    for (int k = 0; k < 12; ++k) {
+        int lo = edges[k][0], hi = edges[k][1];
+        double af = p[3 + 4 * k], bf = p[4 + 4 * k];
+        double ab = p[5 + 4 * k], bb = p[6 + 4 * k];
+        double kf = af * exp(bf * v);  /* lo -> hi */
+        double kb = ab * exp(-bb * v); /* hi -> lo */
+        A[hi * 9 + lo] += kf;
+        A[lo * 9 + lo] -= kf;
+        A[lo * 9 + hi] += kb;
+        A[hi * 9 + hi] -= kb;
+    }
+}
+
+/* Dense LU with partial pivoting (the Eigen PartialPivLU method named in
+ * Section 5.3), in place on M (row-major n x n) with row permutation perm.
+ * Returns the number of row interchanges, or -1 for a zero pivot. */
+int orc_lu_pp(int n, double *M, int *perm)
+{
+    int swaps = 0;
+    for (int i = 0; i < n; ++i)
+        perm[i] = i;
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        double best = fabs(M[k * n + k]);
+        for (int r = k + 1; r < n; ++r)
+            if (fabs(M[r * n + k]) > best) {
+                best = fabs(M[r * n + k]);
+                piv = r;
+            }
+        if (best == 0.0)
+            return -1;
+        if (piv != k) {
+            for (int c = 0; c < n; ++c) {
+                double t = M[k * n + c];
+                M[k * n + c] = M[piv * n + c];
+                M[piv * n + c] = t;
+            }
+            int t = perm[k];
+            perm[k] = perm[piv];
+            perm[piv] = t;
+            ++swaps;
+        }
+        for (int r = k + 1; r < n; ++r) {
+            double l = M[r * n + k] / M[k * n + k];
+            M[r * n + k] = l;
+            for (int c = k + 1; c < n; ++c)
+                M[r * n + c] -= l * M[k * n + c];
+        }
+    }
+    return swaps;
+}
+
+/* Solve (P^T L U) x = b using the factors of orc_lu_pp. */
+void orc_lu_solve(int n, const double *LU, const int *perm, const double *b,
+                  double *x)
+{
+    double y[64];
+    for (int i = 0; i < n; ++i) {
+        double s = b[perm[i]];
+        for (int c = 0; c < i; ++c)
+            s -= LU[i * n + c] * y[c];
+        y[i] = s;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int c = i + 1; c < n; ++c)
+            s -= LU[i * n + c] * x[c];
+        x[i] = s / LU[i * n + i];
+    }
+}
+
+/* One implicit Euler step of one instance by Newton iteration (Section 5.2
+ * derivimplicit, Section 5.3): y0 = x; r = y - x - dt A y; J delta = -r with
+ * J = I - dt A; y += delta; stop when max|delta| <= tol or after max_iter
+ * updates.  Returns the number of updates; *swaps gets the pivot
+ * interchanges of the factorisation. */
+int orc_kin9_newton(const double *A, double dt, const double *x, double *y,
+                    double tol, int max_iter, int *swaps)
+{
+    double J[81], r[9], delta[9];
+    int perm[9];
+    for (int a = 0; a < 9; ++a)
+        for (int b = 0; b < 9; ++b)
+            J[a * 9 + b] = (a == b ? 1.0 : 0.0) - dt * A[a * 9 + b];
+    *swaps = orc_lu_pp(9, J, perm);
+    for (int a = 0; a < 9; ++a)
+        y[a] = x[a];
+    int it = 0;
+    while (it < max_iter) {
+        for (int a = 0; a < 9; ++a) {
+            double Ay = 0.0;
+            for (int b = 0; b < 9; ++b)
+                Ay += A[a * 9 + b] * y[b];
+            r[a] = -(y[a] - x[a] - dt * Ay);
+        }
+        orc_lu_solve(9, J, perm, r, delta);
+        double dmax = 0.0;
+        for (int a = 0; a < 9; ++a) {
+            y[a] += delta[a];
+            if (fabs(delta[a]) > dmax)
+                dmax = fabs(delta[a]);
+        }
+        ++it;
+        if (dmax <= tol)
+            break;
+    }
+    return it;
+}
+
+void orc_kin9_state(int64_t n, const int32_t *ni, const double *v,
+                    const double *p, double dt, double *s, double tol,
+                    int max_iter, int32_t *iters, int64_t *total_swaps)
+{
+    int64_t sw_total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double A[81], x[9], y[9];
+        int sw = 0;
+        orc_kin9_matrix(p, v[ni[i]], A);
+        for (int a = 0; a < 9; ++a)
+            x[a] = s[a * n + i];
+        int it = orc_kin9_newton(A, dt, x, y, tol, max_iter, &sw);
+        sw_total += sw;
+        if (iters)
+            iters[i] = it;
+        for (int a = 0; a < 9; ++a)
+            s[a * n + i] = y[a];
+    }
+    if (total_swaps)
+        *total_swaps = sw_total;
+}
+
+/* Stationary distribution at v: A pi = 0 with sum(pi) = 1, solved as the
+ * square system whose last row is replaced by the normalisation. */
+int orc_kin9_stationary(const double *p, double v, double *pi)
+{
+    double A[81], M[81], b[9];
+    int perm[9];
+    orc_kin9_matrix(p, v, A);
+    memcpy(M, A, sizeof(M));
+    for (int c = 0; c < 9; ++c)
+        M[8 * 9 + c] = 1.0;
+    for (int a = 0; a < 9; ++a)
+        b[a] = (a == 8) ? 1.0 : 0.0;
+    if (orc_lu_pp(9, M, perm) < 0)
+        return -1;
+    orc_lu_solve(9, M, perm, b, pi);
+    return 0;
+}
+
+/* --------------------------------------------------------- per mechanism */
+
+void orc_mech_init(int type, int64_t n, const int32_t *ni, const double *v,
+                   const double *p, double *s)
+{
+    if (type == ORC_TYPE_KIN9) {
+        for (int64_t i = 0; i < n; ++i) {
+            double pi[9];
+            orc_kin9_stationary(p, v[ni[i]], pi);
+            for (int a = 0; a < 9; ++a)
+                s[a * n + i] = pi[a];
+        }
+    } else {
+        cnexp_like_init(type, n, ni, v, p, s);
+    }
+}
+
+void orc_mech_state(int type, int64_t n, const int32_t *ni, const double *v,
+                    const double *p, double dt, double *s, double tol,
+                    int max_iter, int32_t *iters)
+{
+    if (type == ORC_TYPE_KIN9)
+        orc_kin9_state(n, ni, v, p, dt, s, tol, max_iter, iters, NULL);
+    else
+        cnexp_like_state(type, n, ni, v, p, dt, s);
+}
+
+/* ------------------------------------------------------------------ step */
+
+typedef struct {
+    int32_t type;
+    int32_t pad;
+    int64_t n;
+    const int32_t *node_index;
+    const double *params;
+    double *states;
+} orc_mech;
+
+/* nsteps time steps of the isolated-compartment network:
+ * rhs = d = 0; current update of every mechanism in list order;
+ * d += 1e-3 cm/dt (cm in uF/cm2, dt in ms: S/cm2); v += rhs/d unless v is
+ * clamped; state update of every mechanism at the new v. */
+void orc_step(int n_mechs, const orc_mech *mechs, int64_t n_nodes, double dt,
+              double cm, double *v, double *rhs, double *d, int nsteps,
+              int clamp_v, double tol, int max_iter)
+{
+    for (int st = 0; st < nsteps; ++st) {
+        for (int64_t k = 0; k < n_nodes; ++k) {
+            rhs[k] = 0.0;
+            d[k] = 0.0;
+        }
+        for (int m = 0; m < n_mechs; ++m)
+            orc_mech_cur(mechs[m].type, mechs[m].n, mechs[m].node_index, v,
+                         mechs[m].params, mechs[m].states, rhs, d);
+        for (int64_t k = 0; k < n_nodes; ++k) {
+            d[k] += 1e-3 * cm / dt;
+            if (!clamp_v)
+                v[k] += rhs[k] / d[k];
+        }
+        for (int m = 0; m < n_mechs; ++m)
+            orc_mech_state(mechs[m].type, mechs[m].n, mechs[m].node_index, v,
+                           mechs[m].params, dt, mechs[m].states, tol,
+                           max_iter, NULL);
+    }
+}

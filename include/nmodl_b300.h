@@ -1,0 +1,202 @@
+/*
+ * nmodl_b300.h -- C ABI of the B300 (sm_103a) NMODL mechanism library.
+ *
+ * The library runs the per-instance mechanism kernels of a NEURON time step
+ * on one GPU: the state update (nrn_state) and the current update (nrn_cur)
+ * that the paper's generated code implements (Section 1 and Fig. 1: state
+ * and current update dominate run time; Section 3 BREAKPOINT; Section 5 ODE
+ * solvers).  Mechanism kinds:
+ *
+ *   NMODL_HH     Hodgkin-Huxley m, h, n gates integrated with cnexp
+ *                (Section 5.2: exact exponential update with coefficients
+ *                frozen over the step); currents ina + ik + il.
+ *   NMODL_CNEXP  generic channel with 0..3 cnexp gates, g = gbar prod x^p.
+ *   NMODL_KIN9   9-state kinetic scheme (KINETIC -> x' = A(v) x, Section
+ *                5.1) advanced by implicit Euler with Newton iteration on the
+ *                exact Jacobian J = I - dt A (Section 5.2 derivimplicit /
+ *                sparse, Section 5.3 LU), g = gbar x_open.
+ *
+ * Conventions shared by all calls
+ *  - Units: v in mV, dt in ms, conductances in S/cm2, currents in mA/cm2,
+ *    cm in uF/cm2 (so 1e-3 cm/dt is in S/cm2).
+ *  - Arrays marked "device" are device pointers on the context's device.
+ *    Arrays marked "host or device" may be either (unified addressing).
+ *  - All work is enqueued on the context's stream and is asynchronous.
+ *    Argument errors are returned immediately.  Errors found on the device
+ *    (non-finite values, Newton non-convergence, an exhausted wait) are
+ *    latched in the context and returned by nmodl_sync.
+ *  - Ownership: the library copies node_index and params at create time and
+ *    owns the per-instance state arrays (structure of arrays, one row per
+ *    state).  v, rhs and d are caller-owned device arrays of n_nodes doubles.
+ *  - Return value: NMODL_OK (0) or a negative NMODL_ERR_* code.
+ *  - Thread safety: a context and its mechanisms may be used by one host
+ *    thread at a time.
+ */
+#ifndef NMODL_B300_H
+#define NMODL_B300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NMODL_API __attribute__((visibility("default")))
+#else
+#define NMODL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define NMODL_OK 0
+#define NMODL_ERR_ARG (-1)         /* invalid argument or parameter block   */
+#define NMODL_ERR_UNSORTED (-2)    /* node_index not non-decreasing        */
+#define NMODL_ERR_OOM (-3)         /* device allocation failed              */
+#define NMODL_ERR_CUDA (-4)        /* a CUDA runtime call failed            */
+#define NMODL_ERR_NONFINITE (-5)   /* NaN/Inf met in results                */
+#define NMODL_ERR_NOCONV (-6)      /* Newton did not converge in max_iter   */
+#define NMODL_ERR_TIMEOUT (-7)     /* a bounded device wait ran out         */
+#define NMODL_ERR_RANGE (-8)       /* node_index outside [0, n_nodes)       */
+#define NMODL_ERR_UNSUPPORTED (-9) /* combination not supported             */
+
+/* ------------------------------------------------------- mechanism kinds */
+#define NMODL_HH 1
+#define NMODL_CNEXP 2
+#define NMODL_KIN9 3
+
+/* Parameter blocks (doubles):
+ *  NMODL_HH    (7):  gnabar, gkbar, gl, ena, ek, el, celsius.
+ *                    q10 = 3^((celsius - 6.3)/10).
+ *  NMODL_CNEXP (33): n_gates (0..3), gbar, e, q10, celsius, t0, then three
+ *                    gate slots of 9: power (integer 0..8), alpha_form,
+ *                    alpha_A, alpha_vh, alpha_k, beta_form, beta_A, beta_vh,
+ *                    beta_k.  Rate forms with u = (v - vh)/k (k != 0):
+ *                    0 EXP A exp(u); 1 SIGMOID A/(1+exp(-u));
+ *                    2 LINOID A u/(1-exp(-u)).  Temperature factor
+ *                    phi = q10^((celsius - t0)/10); mtau = 1/(phi(a+b)).
+ *  NMODL_KIN9  (51): gbar, e, open state index (0..8), then for the 12 edges
+ *                    of the 3x3 state lattice (state index 3a+b; edges
+ *                    (0,1),(1,2),(3,4),(4,5),(6,7),(7,8),(0,3),(1,4),(2,5),
+ *                    (3,6),(4,7),(5,8)): a_f, b_f, a_b, b_b, with forward
+ *                    rate a_f exp(b_f v) (lower -> higher index) and backward
+ *                    rate a_b exp(-b_b v).
+ */
+#define NMODL_HH_NPARAM 7
+#define NMODL_CNEXP_NPARAM 33
+#define NMODL_KIN9_NPARAM 51
+
+/* ------------------------------------------------------------- precision */
+#define NMODL_FP64 0  /* every operation in IEEE double                    */
+#define NMODL_MIXED 1 /* rates and exponentials in FP32; gate increments
+                         compensated (FP32 hi/lo pair folded into the FP64
+                         state); rhs/d accumulation, v update, kinetic
+                         residual and refinement in FP64                    */
+
+typedef struct nmodl_options {
+    int32_t precision;       /* NMODL_FP64 (default) or NMODL_MIXED          */
+    int32_t newton_max_iter; /* Newton updates per kinetic solve (default 8) */
+    double newton_tol;       /* stop when max|delta| <= tol (default 1e-14)  */
+    int32_t ir_max;          /* refinements of the FP32 LU (default 4)       */
+    int32_t window;          /* steps fused into one launch (default 40)     */
+    int32_t use_graph;       /* replay each window from a CUDA graph (1)     */
+    int32_t autotune;        /* time candidate tile/block shapes (1)         */
+    int32_t clamp_v;         /* nmodl_step leaves v unchanged (0)            */
+    int32_t tile_smem;       /* fused tile shared-memory budget, bytes (0 =
+                                chosen by the autotuner / default)          */
+    int32_t block;           /* fused kernel block size (0 = auto)           */
+    int32_t reserved[5];
+} nmodl_options;
+
+typedef struct nmodl_stats_t {
+    int64_t calls;            /* state updates run                          */
+    int64_t newton_iters;     /* total Newton / refinement updates          */
+    int64_t newton_max;       /* largest per-instance update count          */
+    int64_t nonconverged;     /* instances that hit the iteration cap       */
+    int64_t fallback;         /* surrogate instances sent to Newton         */
+    int64_t surrogate_calls;  /* surrogate state updates                    */
+    int64_t reserved[2];
+} nmodl_stats_t;
+
+typedef struct nmodl_ctx nmodl_ctx;
+typedef struct nmodl_mech nmodl_mech;
+
+/* Fill *o with the defaults listed above. */
+NMODL_API int nmodl_options_default(nmodl_options *o);
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
+ * (a cudaStream_t; NULL selects the legacy default stream).  opt may be
+ * NULL for defaults; it is copied. */
+NMODL_API int nmodl_ctx_create(int device, void *cuda_stream, const nmodl_options *opt,
+                     nmodl_ctx **out);
+/* Replace the context options (e.g. switch precision). */
+NMODL_API int nmodl_ctx_set_options(nmodl_ctx *ctx, const nmodl_options *opt);
+/* Wait for the context stream; return and clear the latched device error. */
+NMODL_API int nmodl_sync(nmodl_ctx *ctx);
+/* Free the context.  Mechanisms created on it must be destroyed first. */
+NMODL_API void nmodl_ctx_destroy(nmodl_ctx *ctx);
+
+/* Create a mechanism instance set of kind `type` with n_instances >= 0
+ * instances.  node_index (host or device, n_instances int32, copied) maps
+ * instance -> node and must be non-decreasing with values in [0, n_nodes):
+ * NMODL_ERR_UNSORTED / NMODL_ERR_RANGE otherwise.  params (host, n_params
+ * doubles, copied) is the kind's parameter block; NMODL_ERR_ARG on a wrong
+ * length or an invalid field.  States are allocated and zeroed.
+ * Synchronous. */
+NMODL_API int nmodl_mech_create(nmodl_ctx *ctx, int type, int64_t n_instances,
+                      const int32_t *node_index, int64_t n_nodes,
+                      const double *params, int64_t n_params,
+                      nmodl_mech **out);
+NMODL_API void nmodl_mech_destroy(nmodl_mech *m);
+/* Number of states per instance (3, n_gates or 9); negative on error. */
+NMODL_API int nmodl_mech_n_states(const nmodl_mech *m);
+
+/* INITIAL: gates := minf(v[node]); kinetic states := the stationary
+ * distribution of A(v[node]) (A pi = 0, sum pi = 1).  v: device, n_nodes. */
+NMODL_API int nmodl_init(nmodl_mech *m, const double *v);
+
+/* nrn_state: advance every instance's states over dt (ms) at the node
+ * voltages v (device, n_nodes) -- cnexp for gates, implicit Euler + Newton
+ * for NMODL_KIN9 (tolerance and precision from the context options). */
+NMODL_API int nmodl_state(nmodl_mech *m, double dt, const double *v);
+
+/* nrn_cur: for every instance compute i = g (v - e) with the analytic
+ * conductance g = dI/dv and ACCUMULATE rhs[node] -= i, d[node] += g
+ * (rhs, d: device, n_nodes; the caller zeroes them).  The sum over the
+ * instances of a node is a deterministic node_index-sorted segmented
+ * warp-shuffle reduction without atomics: repeated calls give bitwise
+ * equal results. */
+NMODL_API int nmodl_cur(nmodl_mech *m, const double *v, double *rhs, double *d);
+
+/* nsteps time steps of the isolated-compartment network formed by the
+ * mechanisms (all on the same node set of n_nodes of mechs[0]):
+ *   rhs = d = 0; nrn_cur of every mechanism in array order;
+ *   d += 1e-3 cm/dt; v += rhs/d (skipped with options.clamp_v);
+ *   nrn_state of every mechanism at the new v.
+ * On return rhs and d hold the last step's values.  When every mechanism is
+ * NMODL_HH or NMODL_CNEXP the steps run in one fused kernel per window of
+ * options.window steps, each node tile's states staged in shared memory for
+ * the window (the compartments are not coupled); otherwise each step is a
+ * sequence of per-mechanism launches.  nsteps = 0 is a no-op. */
+NMODL_API int nmodl_step(nmodl_ctx *ctx, nmodl_mech *const *mechs, int n_mechs,
+               double dt, double cm, double *v, double *rhs, double *d,
+               int nsteps);
+
+/* Copy state row k (n_instances doubles) out of / into the mechanism
+ * (out/in: host or device).  Checkpoint and resume use these. */
+NMODL_API int nmodl_get_state(nmodl_mech *m, int k, double *out);
+NMODL_API int nmodl_set_state(nmodl_mech *m, int k, const double *in);
+
+/* Counters accumulated since creation (synchronises the stream). */
+NMODL_API int nmodl_stats(nmodl_mech *m, nmodl_stats_t *out);
+
+/* Static text for a status code. */
+NMODL_API const char *nmodl_strerror(int status);
+
+/* Library version, e.g. 100 for 0.1.0. */
+NMODL_API int nmodl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMODL_B300_H */

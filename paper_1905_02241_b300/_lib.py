@@ -1,0 +1,180 @@
+"""ctypes binding of libnmodl_b300.so -- argument marshalling only.
+
+Every function keeps the C name (nmodl_*) and takes plain integers for
+pointers; tensors are passed by their data_ptr().  A non-zero status raises
+NmodlError.  There is no fallback: if the shared library is absent the
+import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnmodl_b300.so")
+
+NMODL_OK = 0
+NMODL_HH, NMODL_CNEXP, NMODL_KIN9 = 1, 2, 3
+NMODL_FP64, NMODL_MIXED = 0, 1
+ERRORS = {
+    -1: "NMODL_ERR_ARG", -2: "NMODL_ERR_UNSORTED", -3: "NMODL_ERR_OOM",
+    -4: "NMODL_ERR_CUDA", -5: "NMODL_ERR_NONFINITE", -6: "NMODL_ERR_NOCONV",
+    -7: "NMODL_ERR_TIMEOUT", -8: "NMODL_ERR_RANGE", -9: "NMODL_ERR_UNSUPPORTED",
+}
+
+
+class NmodlError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {ERRORS.get(status, status)} "
+                         f"({_strerror(status)})")
+
+
+class nmodl_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("newton_max_iter", ctypes.c_int32),
+                ("newton_tol", ctypes.c_double), ("ir_max", ctypes.c_int32),
+                ("window", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("clamp_v", ctypes.c_int32),
+                ("tile_smem", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class nmodl_stats_t(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int64), ("newton_iters", ctypes.c_int64),
+                ("newton_max", ctypes.c_int64), ("nonconverged", ctypes.c_int64),
+                ("fallback", ctypes.c_int64), ("surrogate_calls", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 2)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -m paper_1905_02241_b300.build`")
+
+lib = ctypes.CDLL(LIB_PATH)
+_vp, _i32, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+_P = ctypes.POINTER
+
+_SIGS = {
+    "nmodl_version": (_i32, []),
+    "nmodl_strerror": (ctypes.c_char_p, [_i32]),
+    "nmodl_options_default": (_i32, [_P(nmodl_options)]),
+    "nmodl_ctx_create": (_i32, [_i32, _vp, _P(nmodl_options), _P(_vp)]),
+    "nmodl_ctx_set_options": (_i32, [_vp, _P(nmodl_options)]),
+    "nmodl_sync": (_i32, [_vp]),
+    "nmodl_ctx_destroy": (None, [_vp]),
+    "nmodl_mech_create": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, _i64, _P(_vp)]),
+    "nmodl_mech_destroy": (None, [_vp]),
+    "nmodl_mech_n_states": (_i32, [_vp]),
+    "nmodl_init": (_i32, [_vp, _vp]),
+    "nmodl_state": (_i32, [_vp, _d, _vp]),
+    "nmodl_cur": (_i32, [_vp, _vp, _vp, _vp]),
+    "nmodl_step": (_i32, [_vp, _vp, _i32, _d, _d, _vp, _vp, _vp, _i32]),
+    "nmodl_get_state": (_i32, [_vp, _i32, _vp]),
+    "nmodl_set_state": (_i32, [_vp, _i32, _vp]),
+    "nmodl_stats": (_i32, [_vp, _P(nmodl_stats_t)]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def _strerror(s: int) -> str:
+    return lib.nmodl_strerror(int(s)).decode()
+
+
+def _check(status: int, what: str) -> None:
+    if status != NMODL_OK:
+        raise NmodlError(status, what)
+
+
+def nmodl_version() -> int:
+    return lib.nmodl_version()
+
+
+def nmodl_strerror(status: int) -> str:
+    return _strerror(status)
+
+
+def nmodl_options_default() -> nmodl_options:
+    o = nmodl_options()
+    _check(lib.nmodl_options_default(ctypes.byref(o)), "nmodl_options_default")
+    return o
+
+
+def nmodl_ctx_create(device: int, stream: int, opt: nmodl_options | None) -> int:
+    h = _vp()
+    _check(lib.nmodl_ctx_create(int(device), stream or None,
+                                ctypes.byref(opt) if opt is not None else None,
+                                ctypes.byref(h)), "nmodl_ctx_create")
+    return h.value
+
+
+def nmodl_ctx_set_options(ctx: int, opt: nmodl_options) -> None:
+    _check(lib.nmodl_ctx_set_options(ctx, ctypes.byref(opt)), "nmodl_ctx_set_options")
+
+
+def nmodl_sync(ctx: int) -> int:
+    """Returns the latched device status (0 if none); raises on CUDA errors."""
+    s = lib.nmodl_sync(ctx)
+    if s == -4:
+        _check(s, "nmodl_sync")
+    return s
+
+
+def nmodl_ctx_destroy(ctx: int) -> None:
+    lib.nmodl_ctx_destroy(ctx)
+
+
+def nmodl_mech_create(ctx: int, mtype: int, n_instances: int, node_index_ptr: int,
+                      n_nodes: int, params_ptr: int, n_params: int) -> int:
+    h = _vp()
+    _check(lib.nmodl_mech_create(ctx, int(mtype), int(n_instances),
+                                 node_index_ptr or None, int(n_nodes),
+                                 params_ptr or None, int(n_params),
+                                 ctypes.byref(h)), "nmodl_mech_create")
+    return h.value
+
+
+def nmodl_mech_destroy(m: int) -> None:
+    lib.nmodl_mech_destroy(m)
+
+
+def nmodl_mech_n_states(m: int) -> int:
+    return lib.nmodl_mech_n_states(m)
+
+
+def nmodl_init(m: int, v_ptr: int) -> None:
+    _check(lib.nmodl_init(m, v_ptr or None), "nmodl_init")
+
+
+def nmodl_state(m: int, dt: float, v_ptr: int) -> None:
+    _check(lib.nmodl_state(m, float(dt), v_ptr or None), "nmodl_state")
+
+
+def nmodl_cur(m: int, v_ptr: int, rhs_ptr: int, d_ptr: int) -> None:
+    _check(lib.nmodl_cur(m, v_ptr or None, rhs_ptr or None, d_ptr or None), "nmodl_cur")
+
+
+def nmodl_step(ctx: int, mechs, dt: float, cm: float, v_ptr: int, rhs_ptr: int,
+               d_ptr: int, nsteps: int) -> None:
+    arr = (_vp * len(mechs))(*mechs)
+    _check(lib.nmodl_step(ctx, ctypes.cast(arr, _vp), len(mechs), float(dt),
+                          float(cm), v_ptr or None, rhs_ptr or None, d_ptr or None,
+                          int(nsteps)), "nmodl_step")
+
+
+def nmodl_get_state(m: int, k: int, out_ptr: int) -> None:
+    _check(lib.nmodl_get_state(m, int(k), out_ptr or None), "nmodl_get_state")
+
+
+def nmodl_set_state(m: int, k: int, in_ptr: int) -> None:
+    _check(lib.nmodl_set_state(m, int(k), in_ptr or None), "nmodl_set_state")
+
+
+def nmodl_stats(m: int) -> nmodl_stats_t:
+    s = nmodl_stats_t()
+    _check(lib.nmodl_stats(m, ctypes.byref(s)), "nmodl_stats")
+    return s

@@ -1,0 +1,131 @@
+"""Object wrapper over the C ABI for torch tensors (marshalling only).
+
+    ctx = Context(device=0, precision=NMODL_FP64)
+    m = Mechanism(ctx, NMODL_CNEXP, node_index, n_nodes, params)
+    m.init(v); ctx.step([m], dt, cm, v, rhs, d, nsteps)
+
+Tensors must be contiguous and on the context's device (float64 for v, rhs,
+d and states).  Every call enqueues on the context's stream, which defaults
+to torch's current stream at creation.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (NMODL_CNEXP, NMODL_FP64, NMODL_HH, NMODL_KIN9, NMODL_MIXED,
+                   NmodlError)
+
+__all__ = ["Context", "Mechanism", "NmodlError", "NMODL_HH", "NMODL_CNEXP",
+           "NMODL_KIN9", "NMODL_FP64", "NMODL_MIXED"]
+
+
+def _dptr(t: torch.Tensor, dtype=torch.float64, device=None) -> int:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous {dtype} tensor")
+    if device is not None and (t.device.type != "cuda" or t.device.index != device):
+        raise ValueError(f"tensor must live on cuda:{device}")
+    return t.data_ptr()
+
+
+class Context:
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None,
+                 **options):
+        self.device = int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        opt = _lib.nmodl_options_default()
+        for k, v in options.items():
+            setattr(opt, k, v)
+        self.options = opt
+        self.handle = _lib.nmodl_ctx_create(self.device, self.stream.cuda_stream, opt)
+
+    def set_options(self, **options) -> None:
+        for k, v in options.items():
+            setattr(self.options, k, v)
+        _lib.nmodl_ctx_set_options(self.handle, self.options)
+
+    def sync(self) -> int:
+        return _lib.nmodl_sync(self.handle)
+
+    def check(self) -> None:
+        s = self.sync()
+        if s:
+            raise NmodlError(s, "device")
+
+    def step(self, mechs, dt, cm, v, rhs, d, nsteps: int) -> None:
+        _lib.nmodl_step(self.handle, [m.handle for m in mechs], dt, cm,
+                        _dptr(v, device=self.device), _dptr(rhs, device=self.device),
+                        _dptr(d, device=self.device), nsteps)
+
+    def close(self) -> None:
+        if self.handle:
+            _lib.nmodl_ctx_destroy(self.handle)
+            self.handle = 0
+
+
+class Mechanism:
+    def __init__(self, ctx: Context, mtype: int, node_index, n_nodes: int, params):
+        self.ctx = ctx
+        self.type = int(mtype)
+        self.n_nodes = int(n_nodes)
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        if isinstance(node_index, torch.Tensor):
+            ni = node_index.contiguous()
+            if ni.dtype != torch.int32:
+                raise ValueError("node_index must be int32")
+            ptr = ni.data_ptr()
+            n = ni.numel()
+        else:
+            ni = np.ascontiguousarray(node_index, dtype=np.int32)
+            ptr = ni.ctypes.data
+            n = ni.size
+        self.n = int(n)
+        self.handle = _lib.nmodl_mech_create(ctx.handle, self.type, self.n,
+                                             ptr if n else 0, self.n_nodes,
+                                             p.ctypes.data, p.size)
+        self.n_states = _lib.nmodl_mech_n_states(self.handle)
+
+    def init(self, v: torch.Tensor) -> None:
+        _lib.nmodl_init(self.handle, _dptr(v, device=self.ctx.device))
+
+    def state(self, dt: float, v: torch.Tensor) -> None:
+        _lib.nmodl_state(self.handle, dt, _dptr(v, device=self.ctx.device))
+
+    def cur(self, v, rhs, d) -> None:
+        dev = self.ctx.device
+        _lib.nmodl_cur(self.handle, _dptr(v, device=dev), _dptr(rhs, device=dev),
+                       _dptr(d, device=dev))
+
+    def get_state(self, k: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        _lib.nmodl_get_state(self.handle, k, _dptr(out) if self.n else 0)
+        return out
+
+    def set_state(self, k: int, x: torch.Tensor) -> None:
+        _lib.nmodl_set_state(self.handle, k, _dptr(x) if self.n else 0)
+
+    def states(self) -> torch.Tensor:
+        """All states as a (n_states, n) float64 device tensor (copy)."""
+        out = torch.empty((self.n_states, self.n), dtype=torch.float64,
+                          device=f"cuda:{self.ctx.device}")
+        for k in range(self.n_states):
+            self.get_state(k, out[k])
+        return out
+
+    def set_states(self, x: torch.Tensor) -> None:
+        x = x.contiguous()
+        for k in range(self.n_states):
+            self.set_state(k, x[k].contiguous())
+
+    def stats(self) -> dict:
+        s = _lib.nmodl_stats(self.handle)
+        return {k: getattr(s, k) for k, _ in s._fields_ if k != "reserved"}
+
+    def close(self) -> None:
+        if self.handle:
+            _lib.nmodl_mech_destroy(self.handle)
+            self.handle = 0

@@ -1,0 +1,708 @@
+// api.cu -- C ABI of libnmodl_b300.so: contexts, mechanisms, validation,
+// the fused-step tile planner / autotuner and CUDA-graph windows.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace nmodl;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return NMODL_OK;
+    if (e == cudaErrorMemoryAllocation) return NMODL_ERR_OOM;
+    return NMODL_ERR_CUDA;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- structures
+
+struct GraphEntry {
+    double* v;
+    double* rhs;
+    double* d;
+    double dt, cm;
+    int nsteps, clamp;
+    cudaGraphExec_t exec;
+};
+
+struct Plan {
+    std::vector<nmodl_mech*> mechs;
+    int precision = 0;
+    int64_t n_nodes = 0;
+    bool fused = false;
+    // fused form
+    int n_tiles = 0, block = 256, tile_stride = 0;
+    size_t smem = 0;
+    int32_t* d_tiles = nullptr;
+    MechD* d_md = nullptr;
+    std::vector<GraphEntry> graphs;
+    ~Plan() {
+        for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+        cudaFree(d_tiles);
+        cudaFree(d_md);
+    }
+};
+
+struct nmodl_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    nmodl_options opt{};
+    int32_t* d_err = nullptr;
+    std::vector<std::unique_ptr<Plan>> plans;
+    int live_mechs = 0;
+};
+
+struct nmodl_mech {
+    nmodl_ctx* ctx = nullptr;
+    int type = 0;
+    int64_t n = 0, n_nodes = 0, stride = 0;
+    int n_states = 0;
+    std::vector<double> params;
+    int32_t* d_ni = nullptr;
+    double* d_states = nullptr;
+    int32_t* d_chunk = nullptr;
+    int64_t n_chunks = 0;
+    MechD md{};
+    MechD* d_md = nullptr;
+    Kin9D kd{};
+    Kin9D* d_kd = nullptr;
+    KinCounters* d_cnt = nullptr;
+    int64_t calls = 0;
+};
+
+// ------------------------------------------------------------ parameters
+
+static bool is_int(double x, double lo, double hi) {
+    return std::isfinite(x) && x == std::floor(x) && x >= lo && x <= hi;
+}
+
+static GateD make_gate(int af, double aA, double avh, double ak, int bf, double bA,
+                       double bvh, double bk, int power) {
+    GateD g{};
+    g.aform = af; g.aA = aA; g.avh = avh; g.ark = 1.0 / ak;
+    g.bform = bf; g.bA = bA; g.bvh = bvh; g.brk = 1.0 / bk;
+    g.power = power;
+    return g;
+}
+
+static int build_desc(nmodl_mech* m) {
+    const std::vector<double>& p = m->params;
+    for (double x : p)
+        if (!std::isfinite(x)) return NMODL_ERR_ARG;
+    if (m->type == NMODL_HH) {
+        if (p.size() != NMODL_HH_NPARAM) return NMODL_ERR_ARG;
+        MechD& d = m->md;
+        d = MechD{};
+        d.kind = NMODL_HH;
+        d.n_gates = 3;
+        d.phi = std::pow(3.0, (p[6] - 6.3) / 10.0);
+        d.hh_g[0] = p[0]; d.hh_g[1] = p[1]; d.hh_g[2] = p[2];
+        d.hh_e[0] = p[3]; d.hh_e[1] = p[4]; d.hh_e[2] = p[5];
+        // HH rates rewritten in the shapes of u = (v - vh)/k:
+        // alpha_m = 0.1 vtrap(-(v+40),10) = 1.0 u/(1-exp(-u)), u=(v+40)/10
+        d.gate[0] = make_gate(kLinoid, 1.0, -40.0, 10.0, kExp, 4.0, -65.0, -18.0, 3);
+        d.gate[1] = make_gate(kExp, 0.07, -65.0, -20.0, kSigmoid, 1.0, -35.0, 10.0, 1);
+        d.gate[2] = make_gate(kLinoid, 0.1, -55.0, 10.0, kExp, 0.125, -65.0, -80.0, 4);
+        m->n_states = 3;
+        return NMODL_OK;
+    }
+    if (m->type == NMODL_CNEXP) {
+        if (p.size() != NMODL_CNEXP_NPARAM) return NMODL_ERR_ARG;
+        if (!is_int(p[0], 0, kMaxGates) || !(p[3] > 0.0)) return NMODL_ERR_ARG;
+        MechD& d = m->md;
+        d = MechD{};
+        d.kind = NMODL_CNEXP;
+        d.n_gates = (int)p[0];
+        d.gbar = p[1];
+        d.e = p[2];
+        d.phi = std::pow(p[3], (p[4] - p[5]) / 10.0);
+        for (int g = 0; g < d.n_gates; ++g) {
+            const double* q = &p[6 + 9 * g];
+            if (!is_int(q[0], 0, 8) || !is_int(q[1], 0, 2) || !is_int(q[5], 0, 2))
+                return NMODL_ERR_ARG;
+            if (q[4] == 0.0 || q[8] == 0.0) return NMODL_ERR_ARG;
+            d.gate[g] = make_gate((int)q[1], q[2], q[3], q[4], (int)q[5], q[6], q[7],
+                                  q[8], (int)q[0]);
+        }
+        m->n_states = d.n_gates;
+        return NMODL_OK;
+    }
+    if (m->type == NMODL_KIN9) {
+        if (p.size() != NMODL_KIN9_NPARAM) return NMODL_ERR_ARG;
+        if (!is_int(p[2], 0, 8)) return NMODL_ERR_ARG;
+        Kin9D& k = m->kd;
+        k = Kin9D{};
+        k.gbar = p[0];
+        k.e = p[1];
+        k.open = (int)p[2];
+        for (int e = 0; e < kKinEdges; ++e) {
+            k.af[e] = p[3 + 4 * e];
+            k.bf[e] = p[4 + 4 * e];
+            k.ab[e] = p[5 + 4 * e];
+            k.bb[e] = p[6 + 4 * e];
+            if (k.af[e] < 0.0 || k.ab[e] < 0.0) return NMODL_ERR_ARG;
+        }
+        m->n_states = kKinStates;
+        return NMODL_OK;
+    }
+    return NMODL_ERR_ARG;
+}
+
+// ---------------------------------------------------------------- ABI
+
+extern "C" {
+
+int nmodl_version(void) { return 100; }
+
+const char* nmodl_strerror(int s) {
+    switch (s) {
+    case NMODL_OK: return "ok";
+    case NMODL_ERR_ARG: return "invalid argument or parameter block";
+    case NMODL_ERR_UNSORTED: return "node_index is not non-decreasing";
+    case NMODL_ERR_OOM: return "device allocation failed";
+    case NMODL_ERR_CUDA: return "CUDA runtime error";
+    case NMODL_ERR_NONFINITE: return "non-finite value in results";
+    case NMODL_ERR_NOCONV: return "Newton iteration did not converge";
+    case NMODL_ERR_TIMEOUT: return "bounded device wait ran out";
+    case NMODL_ERR_RANGE: return "node_index outside [0, n_nodes)";
+    case NMODL_ERR_UNSUPPORTED: return "unsupported combination";
+    default: return "unknown status";
+    }
+}
+
+int nmodl_options_default(nmodl_options* o) {
+    if (!o) return NMODL_ERR_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = NMODL_FP64;
+    o->newton_max_iter = 8;
+    o->newton_tol = 1e-14;
+    o->ir_max = 4;
+    o->window = 40;
+    o->use_graph = 1;
+    o->autotune = 1;
+    o->clamp_v = 0;
+    return NMODL_OK;
+}
+
+static int check_options(const nmodl_options* o) {
+    if (o->precision != NMODL_FP64 && o->precision != NMODL_MIXED) return NMODL_ERR_ARG;
+    if (o->newton_max_iter < 1 || o->newton_max_iter > 64) return NMODL_ERR_ARG;
+    if (!(o->newton_tol >= 0.0)) return NMODL_ERR_ARG;
+    if (o->ir_max < 0 || o->ir_max > 64) return NMODL_ERR_ARG;
+    if (o->window < 1) return NMODL_ERR_ARG;
+    if (o->tile_smem < 0 || o->block < 0 || o->block > kFusedMaxBlock || (o->block % 32))
+        return NMODL_ERR_ARG;
+    return NMODL_OK;
+}
+
+int nmodl_ctx_create(int device, void* cuda_stream, const nmodl_options* opt,
+                     nmodl_ctx** out) {
+    if (!out) return NMODL_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return NMODL_ERR_CUDA;
+    nmodl_options o;
+    nmodl_options_default(&o);
+    if (opt) o = *opt;
+    int rc = check_options(&o);
+    if (rc) return rc;
+    DeviceGuard g(device);
+    nmodl_ctx* c = new (std::nothrow) nmodl_ctx();
+    if (!c) return NMODL_ERR_OOM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->opt = o;
+    if (dalloc(&c->d_err, 1) != cudaSuccess) {
+        delete c;
+        return NMODL_ERR_OOM;
+    }
+    cudaMemset(c->d_err, 0, sizeof(int32_t));
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFree(c->d_err);
+        delete c;
+        return NMODL_ERR_CUDA;
+    }
+    *out = c;
+    return NMODL_OK;
+}
+
+int nmodl_ctx_set_options(nmodl_ctx* c, const nmodl_options* opt) {
+    if (!c || !opt) return NMODL_ERR_ARG;
+    int rc = check_options(opt);
+    if (rc) return rc;
+    c->opt = *opt;
+    c->plans.clear();  // plans depend on precision / tile options
+    return NMODL_OK;
+}
+
+int nmodl_sync(nmodl_ctx* c) {
+    if (!c) return NMODL_ERR_ARG;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return NMODL_ERR_CUDA;
+    int32_t h = 0;
+    e = cudaMemcpy(&h, c->d_err, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return NMODL_ERR_CUDA;
+    if (h) cudaMemset(c->d_err, 0, sizeof(int32_t));
+    return h;
+}
+
+void nmodl_ctx_destroy(nmodl_ctx* c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    c->plans.clear();
+    cudaFree(c->d_err);
+    delete c;
+}
+
+static void free_mech(nmodl_mech* m) {
+    cudaFree(m->d_ni);
+    cudaFree(m->d_states);
+    cudaFree(m->d_chunk);
+    cudaFree(m->d_md);
+    cudaFree(m->d_kd);
+    cudaFree(m->d_cnt);
+    delete m;
+}
+
+int nmodl_mech_create(nmodl_ctx* c, int type, int64_t n, const int32_t* node_index,
+                      int64_t n_nodes, const double* params, int64_t n_params,
+                      nmodl_mech** out) {
+    if (!out) return NMODL_ERR_ARG;
+    *out = nullptr;
+    if (!c || n < 0 || n_nodes < 0 || n_params < 0 || (n > 0 && !node_index) ||
+        (n_params > 0 && !params))
+        return NMODL_ERR_ARG;
+    if (n > INT32_MAX - 64 || n_nodes > INT32_MAX) return NMODL_ERR_ARG;
+    DeviceGuard g(c->device);
+    nmodl_mech* m = new (std::nothrow) nmodl_mech();
+    if (!m) return NMODL_ERR_OOM;
+    m->ctx = c;
+    m->type = type;
+    m->n = n;
+    m->n_nodes = n_nodes;
+    m->params.assign(params, params + n_params);
+    int rc = build_desc(m);
+    if (rc) {
+        delete m;
+        return rc;
+    }
+    m->stride = (n + 31) / 32 * 32;
+    m->n_chunks = (n + 31) / 32;
+    cudaError_t e = cudaSuccess;
+    int32_t* d_flags = nullptr;
+    do {
+        if ((e = dalloc(&m->d_ni, (size_t)n)) != cudaSuccess) break;
+        if ((e = dalloc(&m->d_states, (size_t)m->n_states * m->stride)) != cudaSuccess) break;
+        if ((e = dalloc(&m->d_chunk, (size_t)m->n_chunks + 1)) != cudaSuccess) break;
+        if ((e = dalloc(&m->d_md, 1)) != cudaSuccess) break;
+        if ((e = dalloc(&m->d_kd, 1)) != cudaSuccess) break;
+        if ((e = dalloc(&m->d_cnt, 1)) != cudaSuccess) break;
+        if ((e = dalloc(&d_flags, 1)) != cudaSuccess) break;
+        if (n > 0 && (e = cudaMemcpy(m->d_ni, node_index, n * sizeof(int32_t),
+                                     cudaMemcpyDefault)) != cudaSuccess)
+            break;
+        if (m->n_states && m->stride &&
+            (e = cudaMemset(m->d_states, 0, m->n_states * m->stride * sizeof(double))) != cudaSuccess)
+            break;
+        if ((e = cudaMemcpy(m->d_md, &m->md, sizeof(MechD), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if ((e = cudaMemcpy(m->d_kd, &m->kd, sizeof(Kin9D), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if ((e = cudaMemset(m->d_cnt, 0, sizeof(KinCounters))) != cudaSuccess) break;
+        if ((e = cudaMemset(d_flags, 0, sizeof(int32_t))) != cudaSuccess) break;
+        launch_validate_index(m->d_ni, n, n_nodes, d_flags, c->stream);
+        launch_chunk_starts(m->d_ni, n, m->n_chunks, m->d_chunk, c->stream);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) break;
+        int32_t flags = 0;
+        if ((e = cudaMemcpy(&flags, d_flags, sizeof(flags), cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+        cudaFree(d_flags);
+        d_flags = nullptr;
+        if (flags & 2) rc = NMODL_ERR_RANGE;
+        else if (flags & 1) rc = NMODL_ERR_UNSORTED;
+    } while (false);
+    if (d_flags) cudaFree(d_flags);
+    if (e != cudaSuccess) rc = cuda_status(e);
+    if (rc) {
+        free_mech(m);
+        return rc;
+    }
+    c->live_mechs++;
+    *out = m;
+    return NMODL_OK;
+}
+
+void nmodl_mech_destroy(nmodl_mech* m) {
+    if (!m) return;
+    nmodl_ctx* c = m->ctx;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    auto& P = c->plans;
+    P.erase(std::remove_if(P.begin(), P.end(),
+                           [m](const std::unique_ptr<Plan>& p) {
+                               return std::find(p->mechs.begin(), p->mechs.end(), m) !=
+                                      p->mechs.end();
+                           }),
+            P.end());
+    c->live_mechs--;
+    free_mech(m);
+}
+
+int nmodl_mech_n_states(const nmodl_mech* m) { return m ? m->n_states : NMODL_ERR_ARG; }
+
+int nmodl_init(nmodl_mech* m, const double* v) {
+    if (!m || (m->n > 0 && !v)) return NMODL_ERR_ARG;
+    nmodl_ctx* c = m->ctx;
+    DeviceGuard g(c->device);
+    if (m->type == NMODL_KIN9)
+        launch_kin9_init(m->d_kd, m->n, m->d_ni, v, m->d_states, m->stride, c->d_err, c->stream);
+    else
+        launch_init_gates(m->d_md, m->n_states, m->n, m->d_ni, v, m->d_states, m->stride,
+                          c->d_err, c->stream);
+    return cuda_status(cudaGetLastError());
+}
+
+static void enqueue_state(nmodl_mech* m, double dt, const double* v) {
+    nmodl_ctx* c = m->ctx;
+    const nmodl_options& o = c->opt;
+    if (m->type == NMODL_KIN9)
+        launch_kin9_state(o.precision, m->d_kd, m->n, m->d_ni, v, m->d_states, m->stride,
+                          dt, o.newton_tol, o.newton_max_iter, o.ir_max, nullptr, 0,
+                          nullptr, m->d_cnt, c->d_err, c->stream);
+    else
+        launch_state_gates(o.precision, m->d_md, m->n_states, m->n, m->d_ni, v,
+                           m->d_states, m->stride, dt, c->d_err, c->stream);
+    m->calls++;
+}
+
+static void enqueue_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
+    nmodl_ctx* c = m->ctx;
+    const void* desc = (m->type == NMODL_KIN9) ? (const void*)m->d_kd : (const void*)m->d_md;
+    launch_cur_seg(m->type == NMODL_KIN9 ? NMODL_KIN9 : NMODL_CNEXP, desc, m->n_chunks,
+                   m->d_chunk, m->d_ni, v, m->d_states, m->stride, rhs, d, c->d_err,
+                   c->stream);
+}
+
+int nmodl_state(nmodl_mech* m, double dt, const double* v) {
+    if (!m || !(dt > 0.0) || !std::isfinite(dt) || (m->n > 0 && !v)) return NMODL_ERR_ARG;
+    DeviceGuard g(m->ctx->device);
+    enqueue_state(m, dt, v);
+    return cuda_status(cudaGetLastError());
+}
+
+int nmodl_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
+    if (!m || (m->n > 0 && (!v || !rhs || !d))) return NMODL_ERR_ARG;
+    DeviceGuard g(m->ctx->device);
+    enqueue_cur(m, v, rhs, d);
+    return cuda_status(cudaGetLastError());
+}
+
+// -------------------------------------------------------------- planning
+
+static size_t tile_smem_bytes(int T, const int* gates, int64_t NT, const int64_t* cnt) {
+    size_t b = 8 * (size_t)NT;
+    size_t inst = 0, items = 0;
+    for (int t = 0; t < T; ++t) {
+        inst += cnt[t];
+        items += (size_t)gates[t] * cnt[t];
+    }
+    b += 8 * items + 2 * inst + 2 * (size_t)T * (NT + 1);
+    return (b + 15) / 16 * 16;
+}
+
+// Greedy tiling: fine blocks of G nodes are merged while the tile's shared
+// memory stays within budget; returns false if one fine block does not fit.
+static bool make_tiles(const std::vector<std::vector<int32_t>>& off, int T,
+                       const int* gates, int64_t n_nodes, int G, size_t budget,
+                       std::vector<int32_t>& recs, size_t& max_smem) {
+    recs.clear();
+    max_smem = 0;
+    const int64_t K = (int64_t)off[0].size() - 1;  // fine blocks
+    int64_t k0 = 0;
+    std::vector<int64_t> cnt(T);
+    while (k0 < K) {
+        int64_t k1 = k0 + 1;
+        auto fits = [&](int64_t a, int64_t b) -> bool {
+            const int64_t NT = std::min<int64_t>(b * G, n_nodes) - a * G;
+            if (NT > 65535) return false;
+            for (int t = 0; t < T; ++t) {
+                cnt[t] = off[t][b] - off[t][a];
+                if (cnt[t] > 65535) return false;
+            }
+            return tile_smem_bytes(T, gates, NT, cnt.data()) <= budget;
+        };
+        if (!fits(k0, k1)) return false;
+        while (k1 < K && fits(k0, k1 + 1)) ++k1;
+        const int64_t n0 = k0 * G, n1 = std::min<int64_t>(k1 * G, n_nodes);
+        recs.push_back((int32_t)n0);
+        recs.push_back((int32_t)n1);
+        for (int t = 0; t < T; ++t) {
+            recs.push_back(off[t][k0]);
+            recs.push_back(off[t][k1]);
+            cnt[t] = off[t][k1] - off[t][k0];
+        }
+        max_smem = std::max(max_smem, tile_smem_bytes(T, gates, n1 - n0, cnt.data()));
+        k0 = k1;
+    }
+    return true;
+}
+
+static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan* p) {
+    p->mechs.assign(mechs, mechs + n_mechs);
+    p->precision = c->opt.precision;
+    p->n_nodes = mechs[0]->n_nodes;
+    bool cnexp = n_mechs <= kMaxMechsFused;
+    for (int i = 0; i < n_mechs; ++i)
+        if (mechs[i]->type == NMODL_KIN9) cnexp = false;
+    p->fused = false;
+    if (!cnexp || p->n_nodes == 0) return NMODL_OK;
+
+    const int T = n_mechs;
+    const int G = 32;
+    const int64_t K = (p->n_nodes + G - 1) / G;
+    std::vector<int64_t> bounds(K + 1);
+    for (int64_t k = 0; k <= K; ++k) bounds[k] = std::min<int64_t>(k * G, p->n_nodes);
+    int64_t* d_bounds = nullptr;
+    int32_t* d_off = nullptr;
+    cudaError_t e;
+    if ((e = dalloc(&d_bounds, K + 1)) != cudaSuccess) return cuda_status(e);
+    if ((e = dalloc(&d_off, (size_t)T * (K + 1))) != cudaSuccess) {
+        cudaFree(d_bounds);
+        return cuda_status(e);
+    }
+    cudaMemcpy(d_bounds, bounds.data(), (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    for (int t = 0; t < T; ++t)
+        launch_tile_bounds(mechs[t]->d_ni, mechs[t]->n, d_bounds, K + 1, d_off + t * (K + 1),
+                           c->stream);
+    std::vector<int32_t> hoff((size_t)T * (K + 1));
+    e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(hoff.data(), d_off, hoff.size() * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaFree(d_bounds);
+    cudaFree(d_off);
+    if (e != cudaSuccess) return cuda_status(e);
+    std::vector<std::vector<int32_t>> off(T);
+    for (int t = 0; t < T; ++t)
+        off[t].assign(hoff.begin() + t * (K + 1), hoff.begin() + (t + 1) * (K + 1));
+    int gates[kMaxMechsFused];
+    for (int t = 0; t < T; ++t) gates[t] = mechs[t]->n_states;
+
+    int dev_smem_optin = 0;
+    cudaDeviceGetAttribute(&dev_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    const size_t stat = fused_static_smem(p->precision);
+    const size_t cap = dev_smem_optin > (int)stat ? dev_smem_optin - stat : 0;
+    size_t budget = c->opt.tile_smem > 0 ? (size_t)c->opt.tile_smem : std::min<size_t>(cap, 96 * 1024);
+    budget = std::min(budget, cap);
+    e = fused_prepare(p->precision, cap);
+    if (e != cudaSuccess) return cuda_status(e);
+    std::vector<int32_t> recs;
+    size_t max_smem = 0;
+    if (!make_tiles(off, T, gates, p->n_nodes, G, budget, recs, max_smem)) return NMODL_OK;
+    p->tile_stride = 2 + 2 * T;
+    p->n_tiles = (int)(recs.size() / p->tile_stride);
+    p->smem = std::max<size_t>(max_smem, 16);
+    // block: enough threads for the average tile's gate items, within limits
+    int block = c->opt.block;
+    if (block == 0) {
+        size_t items = 0;
+        for (int t = 0; t < T; ++t) items += (size_t)gates[t] * mechs[t]->n;
+        const double per_tile = (double)items / std::max(1, p->n_tiles);
+        block = 128;
+        while (block < 512 && block < per_tile / 4) block *= 2;
+    }
+    p->block = block;
+    if ((e = dalloc(&p->d_tiles, recs.size())) != cudaSuccess) return cuda_status(e);
+    cudaMemcpy(p->d_tiles, recs.data(), recs.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if ((e = dalloc(&p->d_md, T)) != cudaSuccess) return cuda_status(e);
+    std::vector<MechD> mds(T);
+    for (int t = 0; t < T; ++t) mds[t] = mechs[t]->md;
+    cudaMemcpy(p->d_md, mds.data(), T * sizeof(MechD), cudaMemcpyHostToDevice);
+    p->fused = true;
+    return NMODL_OK;
+}
+
+static Plan* get_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, int* rc) {
+    for (auto& p : c->plans) {
+        if ((int)p->mechs.size() == n_mechs && p->precision == c->opt.precision &&
+            std::equal(p->mechs.begin(), p->mechs.end(), mechs))
+            return p.get();
+    }
+    std::unique_ptr<Plan> p(new (std::nothrow) Plan());
+    if (!p) {
+        *rc = NMODL_ERR_OOM;
+        return nullptr;
+    }
+    *rc = build_plan(c, mechs, n_mechs, p.get());
+    if (*rc) return nullptr;
+    c->plans.push_back(std::move(p));
+    return c->plans.back().get();
+}
+
+static FusedArgs fused_args(nmodl_ctx* c, Plan* p, double dt, double cm, double* v,
+                            double* rhs, double* d, int nsteps) {
+    FusedArgs a{};
+    a.md = p->d_md;
+    a.n_types = (int)p->mechs.size();
+    for (int t = 0; t < a.n_types; ++t) {
+        nmodl_mech* m = p->mechs[t];
+        a.n_gates[t] = m->n_states;
+        a.states[t] = m->d_states;
+        a.stride[t] = m->stride;
+        a.ni[t] = m->d_ni;
+    }
+    a.tiles = p->d_tiles;
+    a.tile_stride = p->tile_stride;
+    a.nsteps = nsteps;
+    a.clamp_v = c->opt.clamp_v;
+    a.v = v;
+    a.rhs = rhs;
+    a.d = d;
+    a.dt = dt;
+    a.cm = cm;
+    a.err = c->d_err;
+    return a;
+}
+
+static cudaError_t enqueue_generic_steps(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs,
+                                         double dt, double cm, double* v, double* rhs,
+                                         double* d, int nsteps, int64_t n_nodes) {
+    for (int s = 0; s < nsteps; ++s) {
+        cudaMemsetAsync(rhs, 0, n_nodes * sizeof(double), c->stream);
+        cudaMemsetAsync(d, 0, n_nodes * sizeof(double), c->stream);
+        for (int i = 0; i < n_mechs; ++i) enqueue_cur(mechs[i], v, rhs, d);
+        launch_vupdate(n_nodes, v, rhs, d, 1e-3 * cm / dt, c->opt.clamp_v, c->d_err, c->stream);
+        for (int i = 0; i < n_mechs; ++i) enqueue_state(mechs[i], dt, v);
+    }
+    return cudaGetLastError();
+}
+
+// Enqueue one window either directly or by replaying its cached graph.
+static cudaError_t run_window(nmodl_ctx* c, Plan* p, nmodl_mech* const* mechs, int n_mechs,
+                              double dt, double cm, double* v, double* rhs, double* d,
+                              int w) {
+    auto direct = [&]() -> cudaError_t {
+        if (p->fused) {
+            FusedArgs a = fused_args(c, p, dt, cm, v, rhs, d, w);
+            return launch_fused(p->precision, a, p->n_tiles, p->block, p->smem, c->stream);
+        }
+        return enqueue_generic_steps(c, mechs, n_mechs, dt, cm, v, rhs, d, w, p->n_nodes);
+    };
+    if (!c->opt.use_graph || c->stream == nullptr) return direct();
+    for (auto& ge : p->graphs)
+        if (ge.v == v && ge.rhs == rhs && ge.d == d && ge.dt == dt && ge.cm == cm &&
+            ge.nsteps == w && ge.clamp == c->opt.clamp_v)
+            return cudaGraphLaunch(ge.exec, c->stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return direct();
+    cudaError_t le = direct();
+    e = cudaStreamEndCapture(c->stream, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return le != cudaSuccess ? le : e;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    p->graphs.push_back(GraphEntry{v, rhs, d, dt, cm, w, c->opt.clamp_v, exec});
+    if (p->graphs.size() > 16) {
+        cudaGraphExecDestroy(p->graphs.front().exec);
+        p->graphs.erase(p->graphs.begin());
+    }
+    return cudaGraphLaunch(exec, c->stream);
+}
+
+int nmodl_step(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, double dt, double cm,
+               double* v, double* rhs, double* d, int nsteps) {
+    if (!c || !mechs || n_mechs < 1 || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt) ||
+        !(cm > 0.0) || !std::isfinite(cm))
+        return NMODL_ERR_ARG;
+    const int64_t n_nodes = mechs[0]->n_nodes;
+    for (int i = 0; i < n_mechs; ++i)
+        if (!mechs[i] || mechs[i]->ctx != c || mechs[i]->n_nodes != n_nodes) return NMODL_ERR_ARG;
+    if (nsteps == 0 || n_nodes == 0) return NMODL_OK;
+    if (!v || !rhs || !d) return NMODL_ERR_ARG;
+    DeviceGuard g(c->device);
+    int rc = NMODL_OK;
+    Plan* p = get_plan(c, mechs, n_mechs, &rc);
+    if (!p) return rc;
+    if (p->fused) {
+        // the fused kernel runs cur + state per step; count the state calls
+        for (int i = 0; i < n_mechs; ++i) mechs[i]->calls += nsteps;
+    }
+    const int W = c->opt.window;
+    for (int s = 0; s < nsteps; s += W) {
+        const int w = std::min(W, nsteps - s);
+        cudaError_t e = run_window(c, p, mechs, n_mechs, dt, cm, v, rhs, d, w);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return NMODL_OK;
+}
+
+int nmodl_get_state(nmodl_mech* m, int k, double* out) {
+    if (!m || k < 0 || k >= m->n_states || (m->n > 0 && !out)) return NMODL_ERR_ARG;
+    if (m->n == 0) return NMODL_OK;
+    DeviceGuard g(m->ctx->device);
+    cudaError_t e = cudaMemcpyAsync(out, m->d_states + (int64_t)k * m->stride,
+                                    m->n * sizeof(double), cudaMemcpyDefault, m->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->ctx->stream);
+    return cuda_status(e);
+}
+
+int nmodl_set_state(nmodl_mech* m, int k, const double* in) {
+    if (!m || k < 0 || k >= m->n_states || (m->n > 0 && !in)) return NMODL_ERR_ARG;
+    if (m->n == 0) return NMODL_OK;
+    DeviceGuard g(m->ctx->device);
+    cudaError_t e = cudaMemcpyAsync(m->d_states + (int64_t)k * m->stride, in,
+                                    m->n * sizeof(double), cudaMemcpyDefault, m->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->ctx->stream);
+    return cuda_status(e);
+}
+
+int nmodl_stats(nmodl_mech* m, nmodl_stats_t* out) {
+    if (!m || !out) return NMODL_ERR_ARG;
+    DeviceGuard g(m->ctx->device);
+    std::memset(out, 0, sizeof(*out));
+    KinCounters k{};
+    cudaError_t e = cudaStreamSynchronize(m->ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&k, m->d_cnt, sizeof(k), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    out->calls = m->calls;
+    out->newton_iters = (int64_t)k.iters;
+    out->newton_max = k.max_iter_seen;
+    out->nonconverged = (int64_t)k.nonconv;
+    return NMODL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,436 @@
+// k_cnexp.cu -- cnexp-family kernels (HH and generic gates) for sm_103a.
+//
+//  k_init_gates      INITIAL: gate := minf(v[node])
+//  k_state_gates     nrn_state, one thread per (instance, gate): the cnexp
+//                    exact exponential update (Section 5.2)
+//  k_cur_seg         nrn_cur with the analytic conductance (Section 5.2,
+//                    CONDUCTANCE) and a node_index-sorted segmented
+//                    warp-shuffle reduction into rhs/d (no atomics)
+//  k_fused_tiles     nsteps whole network steps (cur -> v -> state) per node
+//                    tile, with the tile's states resident in shared memory
+//                    for the whole window (the compartments are isolated, so
+//                    tiles never exchange data)
+#include <climits>
+
+#include "kernels.cuh"
+
+namespace nmodl {
+
+// ---------------------------------------------------------------- init
+
+__global__ void k_init_gates(const MechD* __restrict__ md, int64_t n,
+                             const int32_t* __restrict__ ni,
+                             const double* __restrict__ v, double* states,
+                             int64_t stride, int32_t* err) {
+    const int g = blockIdx.y;
+    const GateD G = md->gate[g];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double m = gate_inf_d(G, v[ni[i]]);
+        if (!isfinite(m)) latch_error(err, NMODL_ERR_NONFINITE);
+        states[g * stride + i] = m;
+    }
+}
+
+// --------------------------------------------------------------- state
+
+template <int PREC>
+__global__ void k_state_gates(const MechD* __restrict__ md, int64_t n,
+                              const int32_t* __restrict__ ni,
+                              const double* __restrict__ v, double* states,
+                              int64_t stride, double dt, int32_t* err) {
+    const int g = blockIdx.y;
+    const GateD G = md->gate[g];
+    const double phidt = md->phi * dt;
+    double* row = states + g * stride;
+    if (PREC == NMODL_FP64) {
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const double m = gate_step_d(G, phidt, v[ni[i]], row[i]);
+            if (!isfinite(m)) latch_error(err, NMODL_ERR_NONFINITE);
+            row[i] = m;
+        }
+    } else {
+        const GateF F{(float)G.aA, (float)G.avh, (float)G.ark,
+                      (float)G.bA, (float)G.bvh, (float)G.brk, G.aform, G.bform};
+        const float phidtf = (float)phidt;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const double m = row[i];
+            float minf, f;
+            gate_coef_f(F, phidtf, (float)v[ni[i]], minf, f);
+            // FP32 increment from the FP32-rounded state, added in FP64
+            const float delta = f * (minf - (float)m);
+            const double mn = m + (double)delta;
+            if (!isfinite(mn)) latch_error(err, NMODL_ERR_NONFINITE);
+            row[i] = mn;
+        }
+    }
+}
+
+// ----------------------------------------------------------------- cur
+
+// i and g of instance j of a cnexp-family mechanism at voltage vv (FP64)
+__device__ __forceinline__ void cur_cnexp_d(const MechD& M, const double* st,
+                                            int64_t stride, int64_t j,
+                                            double vv, double& i, double& g) {
+    if (M.kind == NMODL_HH) {
+        const double m = st[j], h = st[stride + j], nn = st[2 * stride + j];
+        const double gna = M.hh_g[0] * m * m * m * h;
+        const double gk = M.hh_g[1] * nn * nn * nn * nn;
+        const double gl = M.hh_g[2];
+        i = gna * (vv - M.hh_e[0]) + gk * (vv - M.hh_e[1]) + gl * (vv - M.hh_e[2]);
+        g = gna + gk + gl;
+    } else {
+        double gg = M.gbar;
+        for (int q = 0; q < M.n_gates; ++q)
+            gg *= ipow_d(st[q * stride + j], M.gate[q].power);
+        i = gg * (vv - M.e);
+        g = gg;
+    }
+}
+
+__device__ __forceinline__ void cur_kin9_d(const Kin9D& K, const double* st,
+                                           int64_t stride, int64_t j, double vv,
+                                           double& i, double& g) {
+    g = K.gbar * st[K.open * stride + j];
+    i = g * (vv - K.e);
+}
+
+// One warp per segment-aligned chunk [chunk[w], chunk[w+1]) of instances:
+// chunks start at segment heads, so every node's instances are reduced by a
+// single warp and each node is written by exactly one lane (deterministic,
+// no atomics).  Within a 32-wide piece a segmented inclusive scan on the
+// sorted keys sums each node's terms; a segment that runs past the piece is
+// carried into the next piece from lane 31.
+template <int KIND>
+__global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
+                          const int32_t* __restrict__ chunk,
+                          const int32_t* __restrict__ ni,
+                          const double* __restrict__ v,
+                          const double* __restrict__ st, int64_t stride,
+                          double* rhs, double* d, int32_t* err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (w >= n_chunks) return;
+    const int64_t s = chunk[w], e = chunk[w + 1];
+    double ci = 0.0, cg = 0.0;
+    int ckey = INT_MIN;
+    for (int64_t base = s; base < e; base += 32) {
+        const int64_t j = base + lane;
+        const bool valid = j < e;
+        const int key = valid ? ni[j] : -1 - lane;  // invalid lanes never match
+        double vi = 0.0, vg = 0.0;
+        if (valid) {
+            const double vv = v[key];
+            if (KIND == NMODL_KIN9)
+                cur_kin9_d(*(const Kin9D*)desc, st, stride, j, vv, vi, vg);
+            else
+                cur_cnexp_d(*(const MechD*)desc, st, stride, j, vv, vi, vg);
+        }
+        if (lane == 0 && key == ckey) {
+            vi += ci;
+            vg += cg;
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const double oi = __shfl_up_sync(0xffffffffu, vi, off);
+            const double og = __shfl_up_sync(0xffffffffu, vg, off);
+            const int ok = __shfl_up_sync(0xffffffffu, key, off);
+            if (lane >= off && ok == key) {
+                vi += oi;
+                vg += og;
+            }
+        }
+        const int nkey = __shfl_down_sync(0xffffffffu, key, 1);
+        const bool cont = valid && lane == 31 && (j + 1 < e) && ni[j + 1] == key;
+        const bool tail = valid && (lane == 31 || nkey != key);
+        if (tail && !cont) {
+            const double r = rhs[key] - vi;
+            const double dd = d[key] + vg;
+            if (!isfinite(r) || !isfinite(dd)) latch_error(err, NMODL_ERR_NONFINITE);
+            rhs[key] = r;
+            d[key] = dd;
+        }
+        ci = __shfl_sync(0xffffffffu, vi, 31);
+        cg = __shfl_sync(0xffffffffu, vg, 31);
+        ckey = __shfl_sync(0xffffffffu, cont ? key : INT_MIN, 31);
+    }
+}
+
+// ---------------------------------------------------- fused tile kernel
+
+// Shared-memory layout of one tile (built from the tile record):
+//   double  v_s[NT]
+//   state   st_s[sum_t gates_t * cnt_t]   (double, or float2 hi/lo in MIXED)
+//   uint16  nid_s[sum_t cnt_t]            local node id of each instance
+//   uint16  seg_s[T][NT + 1]              per-type segment offsets
+// Tile record (int32): n0, n1, then a_t, b_t per type (instance ranges).
+// The host plan guarantees NT <= 65535, cnt_t <= 65535 and that the layout
+// fits the dynamic shared memory of the launch.
+template <int PREC>
+__global__ void __launch_bounds__(kFusedMaxBlock)
+    k_fused_tiles(FusedArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ MechD md_s[kMaxMechsFused];
+    __shared__ GateF gf_s[kMaxMechsFused][kMaxGates];
+    __shared__ int a_s[kMaxMechsFused], cnt_s[kMaxMechsFused];
+    __shared__ int st_off[kMaxMechsFused], nid_off[kMaxMechsFused];
+    __shared__ int pair_t[kMaxMechsFused * kMaxGates];
+    __shared__ int pair_g[kMaxMechsFused * kMaxGates];
+    __shared__ int pair_start[kMaxMechsFused * kMaxGates + 1];
+    __shared__ int n_pairs;
+
+    const int tid = threadIdx.x;
+    const int T = A.n_types;
+    const int32_t* rec = A.tiles + (int64_t)blockIdx.x * A.tile_stride;
+    const int n0 = rec[0];
+    const int NT = rec[1] - rec[0];
+
+    for (int k = tid; k < T * (int)(sizeof(MechD) / 4); k += blockDim.x)
+        ((int32_t*)md_s)[k] = ((const int32_t*)A.md)[k];
+    if (tid == 0) {
+        int so = 0, no = 0, q = 0;
+        for (int t = 0; t < T; ++t) {
+            a_s[t] = rec[2 + 2 * t];
+            cnt_s[t] = rec[3 + 2 * t] - rec[2 + 2 * t];
+            st_off[t] = so;
+            nid_off[t] = no;
+            const int ng = A.n_gates[t];
+            for (int g = 0; g < ng; ++g) {
+                pair_t[q] = t;
+                pair_g[q] = g;
+                pair_start[q] = so + g * cnt_s[t];
+                ++q;
+            }
+            so += ng * cnt_s[t];
+            no += cnt_s[t];
+        }
+        pair_start[q] = so;
+        n_pairs = q;
+    }
+    __syncthreads();
+    if (PREC == NMODL_MIXED) {
+        for (int k = tid; k < T * kMaxGates; k += blockDim.x) {
+            const GateD& G = md_s[k / kMaxGates].gate[k % kMaxGates];
+            gf_s[k / kMaxGates][k % kMaxGates] =
+                GateF{(float)G.aA, (float)G.avh, (float)G.ark, (float)G.bA,
+                      (float)G.bvh, (float)G.brk, G.aform, G.bform};
+        }
+    }
+    const int total_items = pair_start[n_pairs];
+    int total_inst = 0;
+    for (int t = 0; t < T; ++t) total_inst += cnt_s[t];
+
+    double* v_s = reinterpret_cast<double*>(smem);
+    double* st_d = v_s + NT;                                   // FP64 states
+    float2* st_f = reinterpret_cast<float2*>(v_s + NT);        // MIXED states
+    uint16_t* nid_s = reinterpret_cast<uint16_t*>(st_d + total_items);
+    uint16_t* seg_s = nid_s + total_inst;
+
+    // ---- load the tile
+    for (int k = tid; k < NT; k += blockDim.x) v_s[k] = A.v[n0 + k];
+    {
+        int q = 0;
+        for (int k = tid; k < total_items; k += blockDim.x) {
+            while (k >= pair_start[q + 1]) ++q;
+            const int t = pair_t[q], g = pair_g[q];
+            const int j = k - pair_start[q];
+            const double m = A.states[t][g * A.stride[t] + a_s[t] + j];
+            if (PREC == NMODL_FP64) {
+                st_d[k] = m;
+            } else {
+                const float hi = (float)m;
+                st_f[k] = make_float2(hi, (float)(m - (double)hi));
+            }
+        }
+    }
+    for (int t = 0; t < T; ++t)
+        for (int j = tid; j < cnt_s[t]; j += blockDim.x)
+            nid_s[nid_off[t] + j] = (uint16_t)(A.ni[t][a_s[t] + j] - n0);
+    __syncthreads();
+    for (int t = 0; t < T; ++t) {
+        const uint16_t* nid = nid_s + nid_off[t];
+        uint16_t* seg = seg_s + t * (NT + 1);
+        const int cnt = cnt_s[t];
+        for (int n = tid; n <= NT; n += blockDim.x) {
+            int lo = 0, hi = cnt;  // first j with nid[j] >= n
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (nid[mid] < n) lo = mid + 1; else hi = mid;
+            }
+            seg[n] = (uint16_t)lo;
+        }
+    }
+    __syncthreads();
+
+    const double cmdt = 1e-3 * A.cm / A.dt;
+    for (int step = 0; step < A.nsteps; ++step) {
+        const bool last = (step == A.nsteps - 1);
+        // ---- current update and v update, one owner thread per node; the
+        // terms are summed in mechanism order, then ascending instance.
+        for (int n = tid; n < NT; n += blockDim.x) {
+            const double vv = v_s[n];
+            double r = 0.0, dd = 0.0;
+            for (int t = 0; t < T; ++t) {
+                const MechD& M = md_s[t];
+                const uint16_t* seg = seg_s + t * (NT + 1);
+                const int j0 = seg[n], j1 = seg[n + 1];
+                const int cnt = cnt_s[t];
+                for (int j = j0; j < j1; ++j) {
+                    double ci, gi;
+                    if (PREC == NMODL_FP64) {
+                        cur_cnexp_d(M, st_d + st_off[t], cnt, j, vv, ci, gi);
+                    } else {
+                        const float2* st = st_f + st_off[t];
+                        const float vf = (float)vv;
+                        float gf, cf;
+                        if (M.kind == NMODL_HH) {
+                            const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
+                            const float gna = (float)M.hh_g[0] * m * m * m * h;
+                            const float gk = (float)M.hh_g[1] * nn * nn * nn * nn;
+                            const float gl = (float)M.hh_g[2];
+                            cf = gna * (vf - (float)M.hh_e[0]) + gk * (vf - (float)M.hh_e[1]) +
+                                 gl * (vf - (float)M.hh_e[2]);
+                            gf = gna + gk + gl;
+                        } else {
+                            gf = (float)M.gbar;
+                            for (int q = 0; q < M.n_gates; ++q) {
+                                const float x = st[q * cnt + j].x;
+                                for (int p = 0; p < M.gate[q].power; ++p) gf *= x;
+                            }
+                            cf = gf * (vf - (float)M.e);
+                        }
+                        ci = (double)cf;
+                        gi = (double)gf;
+                    }
+                    r -= ci;
+                    dd += gi;
+                }
+            }
+            dd += cmdt;
+            const double vn = A.clamp_v ? vv : vv + r / dd;
+            if (last) {
+                A.rhs[n0 + n] = r;
+                A.d[n0 + n] = dd;
+            }
+            v_s[n] = vn;
+        }
+        __syncthreads();
+        // ---- state update, one thread per (instance, gate) item
+        int q = 0;
+        for (int k = tid; k < total_items; k += blockDim.x) {
+            while (k >= pair_start[q + 1]) ++q;
+            const int t = pair_t[q], g = pair_g[q];
+            const int j = k - pair_start[q];
+            const double vv = v_s[nid_s[nid_off[t] + j]];
+            if (PREC == NMODL_FP64) {
+                const GateD& G = md_s[t].gate[g];
+                st_d[k] = gate_step_d(G, md_s[t].phi * A.dt, vv, st_d[k]);
+            } else {
+                float minf, f;
+                gate_coef_f(gf_s[t][g], (float)(md_s[t].phi * A.dt), (float)vv, minf, f);
+                float2 m = st_f[k];
+                const float delta = f * ((minf - m.x) - m.y);
+                float s, e;
+                two_sum_f(m.x, delta, s, e);
+                const float lo = m.y + e;
+                const float hi2 = s + lo;
+                m.y = lo - (hi2 - s);
+                m.x = hi2;
+                st_f[k] = m;
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- write the tile back
+    for (int k = tid; k < NT; k += blockDim.x) {
+        const double vn = v_s[k];
+        if (!isfinite(vn)) latch_error(A.err, NMODL_ERR_NONFINITE);
+        A.v[n0 + k] = vn;
+    }
+    {
+        int q = 0;
+        for (int k = tid; k < total_items; k += blockDim.x) {
+            while (k >= pair_start[q + 1]) ++q;
+            const int t = pair_t[q], g = pair_g[q];
+            const int j = k - pair_start[q];
+            double m;
+            if (PREC == NMODL_FP64) m = st_d[k];
+            else m = (double)st_f[k].x + (double)st_f[k].y;
+            if (!isfinite(m)) latch_error(A.err, NMODL_ERR_NONFINITE);
+            A.states[t][g * A.stride[t] + a_s[t] + j] = m;
+        }
+    }
+}
+
+// ------------------------------------------------------------ launchers
+
+static int grid_for(int64_t n, int block) {
+    int64_t b = (n + block - 1) / block;
+    if (b > 148 * 64) b = 148 * 64;
+    return (int)(b < 1 ? 1 : b);
+}
+
+void launch_init_gates(const MechD* md, int n_gates, int64_t n, const int32_t* ni,
+                       const double* v, double* st, int64_t stride, int32_t* err,
+                       cudaStream_t s) {
+    if (n == 0 || n_gates == 0) return;
+    dim3 grid(grid_for(n, 256), n_gates);
+    k_init_gates<<<grid, 256, 0, s>>>(md, n, ni, v, st, stride, err);
+}
+
+void launch_state_gates(int prec, const MechD* md, int n_gates, int64_t n,
+                        const int32_t* ni, const double* v, double* st,
+                        int64_t stride, double dt, int32_t* err, cudaStream_t s) {
+    if (n == 0 || n_gates == 0) return;
+    dim3 grid(grid_for(n, 256), n_gates);
+    if (prec == NMODL_FP64)
+        k_state_gates<NMODL_FP64><<<grid, 256, 0, s>>>(md, n, ni, v, st, stride, dt, err);
+    else
+        k_state_gates<NMODL_MIXED><<<grid, 256, 0, s>>>(md, n, ni, v, st, stride, dt, err);
+}
+
+void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
+                    const int32_t* chunk, const int32_t* ni, const double* v,
+                    const double* st, int64_t stride, double* rhs, double* d,
+                    int32_t* err, cudaStream_t s) {
+    if (n_chunks == 0) return;
+    const int block = 256;
+    const int64_t threads = n_chunks * 32;
+    const int grid = (int)((threads + block - 1) / block);
+    if (kind == NMODL_KIN9)
+        k_cur_seg<NMODL_KIN9><<<grid, block, 0, s>>>(desc, n_chunks, chunk, ni, v, st, stride, rhs, d, err);
+    else
+        k_cur_seg<NMODL_CNEXP><<<grid, block, 0, s>>>(desc, n_chunks, chunk, ni, v, st, stride, rhs, d, err);
+}
+
+cudaError_t launch_fused(int prec, const FusedArgs& a, int n_tiles, int block,
+                         size_t smem, cudaStream_t s) {
+    if (n_tiles == 0) return cudaSuccess;
+    if (prec == NMODL_FP64)
+        k_fused_tiles<NMODL_FP64><<<n_tiles, block, smem, s>>>(a);
+    else
+        k_fused_tiles<NMODL_MIXED><<<n_tiles, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Raise the kernel's dynamic shared-memory limit to max_smem (set once, at
+// planning time, outside any stream capture).
+cudaError_t fused_prepare(int prec, size_t max_smem) {
+    if (prec == NMODL_FP64)
+        return cudaFuncSetAttribute(k_fused_tiles<NMODL_FP64>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    return cudaFuncSetAttribute(k_fused_tiles<NMODL_MIXED>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+}
+
+size_t fused_static_smem(int prec) {
+    cudaFuncAttributes fa{};
+    if (prec == NMODL_FP64) cudaFuncGetAttributes(&fa, k_fused_tiles<NMODL_FP64>);
+    else cudaFuncGetAttributes(&fa, k_fused_tiles<NMODL_MIXED>);
+    return fa.sharedSizeBytes;
+}
+
+}  // namespace nmodl

@@ -1,0 +1,322 @@
+// k_kin9.cu -- 9-state kinetic scheme: INITIAL and nrn_state for sm_103a.
+//
+// The KINETIC scheme is the linear ODE x' = A(v) x (Section 5.1); one
+// implicit Euler step solves F(y) = y - x - dt A y = 0 by Newton iteration
+// with the exact Jacobian J = I - dt A (Section 5.2 derivimplicit, Section
+// 5.3 Newton + LU).  One thread owns one instance.  J is a nonsingular
+// M-matrix whose columns sum to one (columns of -dt A sum to 0), so LU with
+// partial pivoting makes no row interchanges and the no-pivot LU below
+// performs the same eliminations.  States are numbered 3a+b on a 3x3
+// lattice whose edges join indices differing by 1 (same row) or 3, so J and
+// its LU factors live inside the band |i - j| <= 3; every loop is unrolled
+// at compile time and only band entries are ever touched.
+//
+// FP64 form: rates, J, LU, residual and update in double.
+// MIXED form: rates and the LU factorisation in FP32; the residual
+// F(y) = J y - x (with J's diagonal rebuilt in FP64 so that its columns keep
+// summing exactly to one) and the update of y in FP64; the FP32 factors
+// refine y until max|delta| <= tol or ir_max refinements.
+#include "kernels.cuh"
+
+namespace nmodl {
+
+namespace {
+
+// Edge e joins state lo(e) and hi(e): edges 0..5 are horizontal
+// (3a+b, 3a+b+1), edges 6..11 vertical (k, k+3).
+__host__ __device__ constexpr int edge_lo(int e) {
+    return e < 6 ? 3 * (e / 2) + (e % 2) : e - 6;
+}
+__host__ __device__ constexpr int edge_hi(int e) {
+    return e < 6 ? edge_lo(e) + 1 : edge_lo(e) + 3;
+}
+
+__host__ __device__ constexpr bool in_band(int i, int j) { return (i - j <= 3) && (j - i <= 3); }
+
+// In-place no-pivot LU of the banded 9x9 matrix M (only band entries used).
+template <typename R>
+__device__ __forceinline__ void lu_band(R (&M)[9][9]) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const R rp = R(1) / M[k][k];
+#pragma unroll
+        for (int i = k + 1; i < 9; ++i) {
+            if (!in_band(i, k)) continue;
+            const R l = M[i][k] * rp;
+            M[i][k] = l;
+#pragma unroll
+            for (int j = k + 1; j < 9; ++j) {
+                if (!in_band(k, j) || !in_band(i, j)) continue;
+                M[i][j] -= l * M[k][j];
+            }
+        }
+    }
+}
+
+// Solve L U z = b in place (b -> z).
+template <typename R>
+__device__ __forceinline__ void lu_band_solve(const R (&M)[9][9], R (&b)[9]) {
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+#pragma unroll
+        for (int c = 0; c < i; ++c)
+            if (in_band(i, c)) b[i] -= M[i][c] * b[c];
+#pragma unroll
+    for (int i = 8; i >= 0; --i) {
+#pragma unroll
+        for (int c = i + 1; c < 9; ++c)
+            if (in_band(i, c)) b[i] -= M[i][c] * b[c];
+        b[i] = b[i] / M[i][i];
+    }
+}
+
+__device__ __forceinline__ void warp_count(KinCounters* cnt, int iters,
+                                           bool nonconv, bool active) {
+    if (!cnt) return;
+    unsigned long long it = active ? (unsigned long long)iters : 0ull;
+    unsigned nc = (active && nonconv) ? 1u : 0u;
+    int mx = active ? iters : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        it += __shfl_down_sync(0xffffffffu, it, o);
+        nc += __shfl_down_sync(0xffffffffu, nc, o);
+        mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (it) atomicAdd(&cnt->iters, it);
+        if (nc) atomicAdd(&cnt->nonconv, (unsigned long long)nc);
+        if (mx) atomicMax(&cnt->max_iter_seen, mx);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- INITIAL
+// Stationary distribution: A pi = 0 with sum(pi) = 1, solved as the square
+// system whose rows 0..7 are those of -A and whose last row is the
+// normalisation.  The leading 8x8 block of -A is a nonsingular M-matrix
+// (irreducible chain), so the dense no-pivot LU below is stable.
+__global__ void k_kin9_init(const Kin9D* __restrict__ kd, int64_t n,
+                            const int32_t* __restrict__ ni,
+                            const double* __restrict__ v, double* st,
+                            int64_t stride, int32_t* err) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Kin9D& K = *kd;
+    const double vv = v[ni[i]];
+    double M[9][9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a)
+#pragma unroll
+        for (int b = 0; b < 9; ++b) M[a][b] = 0.0;
+#pragma unroll
+    for (int e = 0; e < kKinEdges; ++e) {
+        const double kf = K.af[e] * exp(K.bf[e] * vv);
+        const double kb = K.ab[e] * exp(-K.bb[e] * vv);
+        const int lo = edge_lo(e), hi = edge_hi(e);
+        M[hi][lo] -= kf;
+        M[lo][lo] += kf;
+        M[lo][hi] -= kb;
+        M[hi][hi] += kb;
+    }
+#pragma unroll
+    for (int b = 0; b < 9; ++b) M[8][b] = 1.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const double rp = 1.0 / M[k][k];
+#pragma unroll
+        for (int r = k + 1; r < 9; ++r) {
+            const double l = M[r][k] * rp;
+            M[r][k] = l;
+#pragma unroll
+            for (int c = k + 1; c < 9; ++c) M[r][c] -= l * M[k][c];
+        }
+    }
+    double x[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) x[a] = (a == 8) ? 1.0 : 0.0;
+#pragma unroll
+    for (int a = 1; a < 9; ++a)
+#pragma unroll
+        for (int c = 0; c < a; ++c) x[a] -= M[a][c] * x[c];
+#pragma unroll
+    for (int a = 8; a >= 0; --a) {
+#pragma unroll
+        for (int c = a + 1; c < 9; ++c) x[a] -= M[a][c] * x[c];
+        x[a] = x[a] / M[a][a];
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        if (!isfinite(x[a])) latch_error(err, NMODL_ERR_NONFINITE);
+        st[a * stride + i] = x[a];
+    }
+}
+
+// ---------------------------------------------------------------- state
+
+template <int PREC, bool LIST>
+__global__ void __launch_bounds__(128)
+    k_kin9_state(const Kin9D* __restrict__ kd, int64_t n,
+                 const int32_t* __restrict__ ni, const double* __restrict__ v,
+                 double* st, int64_t stride, double dt, double tol, int max_iter,
+                 int ir_max, const int32_t* __restrict__ list,
+                 const int32_t* __restrict__ n_list_dev, KinCounters* cnt,
+                 int32_t* err) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n_work = LIST ? (int64_t)*n_list_dev : n;
+    const bool active = t < n_work;
+    int iters = 0;
+    bool nonconv = false;
+    if (active) {
+        const int64_t i = LIST ? (int64_t)list[t] : t;
+        const Kin9D& K = *kd;
+        const double vv = v[ni[i]];
+        double x[9], y[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            x[a] = st[a * stride + i];
+            y[a] = x[a];
+        }
+        if (PREC == NMODL_FP64) {
+            double dk_f[kKinEdges], dk_b[kKinEdges];
+#pragma unroll
+            for (int e = 0; e < kKinEdges; ++e) {
+                dk_f[e] = dt * (K.af[e] * exp(K.bf[e] * vv));
+                dk_b[e] = dt * (K.ab[e] * exp(-K.bb[e] * vv));
+            }
+            double diag[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) diag[a] = 1.0;
+#pragma unroll
+            for (int e = 0; e < kKinEdges; ++e) {
+                diag[edge_lo(e)] += dk_f[e];
+                diag[edge_hi(e)] += dk_b[e];
+            }
+            double M[9][9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+#pragma unroll
+                for (int b = 0; b < 9; ++b)
+                    if (in_band(a, b)) M[a][b] = (a == b) ? diag[a] : 0.0;
+#pragma unroll
+            for (int e = 0; e < kKinEdges; ++e) {
+                M[edge_hi(e)][edge_lo(e)] = -dk_f[e];
+                M[edge_lo(e)][edge_hi(e)] = -dk_b[e];
+            }
+            lu_band(M);
+            while (iters < max_iter) {
+                // r = -(J y - x)
+                double r[9];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) r[a] = x[a] - diag[a] * y[a];
+#pragma unroll
+                for (int e = 0; e < kKinEdges; ++e) {
+                    r[edge_hi(e)] += dk_f[e] * y[edge_lo(e)];
+                    r[edge_lo(e)] += dk_b[e] * y[edge_hi(e)];
+                }
+                lu_band_solve(M, r);
+                double dmax = 0.0;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    y[a] += r[a];
+                    dmax = fmax(dmax, fabs(r[a]));
+                }
+                ++iters;
+                if (dmax <= tol) break;
+                if (iters == max_iter) nonconv = true;
+            }
+        } else {
+            float dk_f[kKinEdges], dk_b[kKinEdges];
+            const float dtf = (float)dt, vf = (float)vv;
+#pragma unroll
+            for (int e = 0; e < kKinEdges; ++e) {
+                dk_f[e] = dtf * ((float)K.af[e] * __expf((float)K.bf[e] * vf));
+                dk_b[e] = dtf * ((float)K.ab[e] * __expf(-(float)K.bb[e] * vf));
+            }
+            // FP64 diagonal from the FP32 off-diagonals: columns of J sum to 1
+            double diag[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) diag[a] = 1.0;
+#pragma unroll
+            for (int e = 0; e < kKinEdges; ++e) {
+                diag[edge_lo(e)] += (double)dk_f[e];
+                diag[edge_hi(e)] += (double)dk_b[e];
+            }
+            float M[9][9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+#pragma unroll
+                for (int b = 0; b < 9; ++b)
+                    if (in_band(a, b)) M[a][b] = (a == b) ? (float)diag[a] : 0.0f;
+#pragma unroll
+            for (int e = 0; e < kKinEdges; ++e) {
+                M[edge_hi(e)][edge_lo(e)] = -dk_f[e];
+                M[edge_lo(e)][edge_hi(e)] = -dk_b[e];
+            }
+            lu_band(M);
+            const int cap = 1 + ir_max;
+            while (iters < cap) {
+                double r[9];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) r[a] = x[a] - diag[a] * y[a];
+#pragma unroll
+                for (int e = 0; e < kKinEdges; ++e) {
+                    r[edge_hi(e)] += (double)dk_f[e] * y[edge_lo(e)];
+                    r[edge_lo(e)] += (double)dk_b[e] * y[edge_hi(e)];
+                }
+                float rf[9];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) rf[a] = (float)r[a];
+                lu_band_solve(M, rf);
+                float dmax = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    y[a] += (double)rf[a];
+                    dmax = fmaxf(dmax, fabsf(rf[a]));
+                }
+                ++iters;
+                if ((double)dmax <= tol) break;
+                if (iters == cap) nonconv = true;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            if (!isfinite(y[a])) latch_error(err, NMODL_ERR_NONFINITE);
+            st[a * stride + i] = y[a];
+        }
+    }
+    warp_count(cnt, iters, nonconv, active);
+}
+
+void launch_kin9_init(const Kin9D* kd, int64_t n, const int32_t* ni,
+                      const double* v, double* st, int64_t stride, int32_t* err,
+                      cudaStream_t s) {
+    if (n == 0) return;
+    const int block = 128;
+    k_kin9_init<<<(int)((n + block - 1) / block), block, 0, s>>>(kd, n, ni, v, st, stride, err);
+}
+
+void launch_kin9_state(int prec, const Kin9D* kd, int64_t n, const int32_t* ni,
+                       const double* v, double* st, int64_t stride, double dt,
+                       double tol, int max_iter, int ir_max,
+                       const int32_t* list, int64_t n_list_max,
+                       const int32_t* n_list_dev, KinCounters* cnt,
+                       int32_t* err, cudaStream_t s) {
+    const int block = 128;
+    const int64_t work = list ? n_list_max : n;
+    if (work == 0) return;
+    const int grid = (int)((work + block - 1) / block);
+    if (prec == NMODL_FP64) {
+        if (list)
+            k_kin9_state<NMODL_FP64, true><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
+        else
+            k_kin9_state<NMODL_FP64, false><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
+    } else {
+        if (list)
+            k_kin9_state<NMODL_MIXED, true><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
+        else
+            k_kin9_state<NMODL_MIXED, false><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
+    }
+}
+
+}  // namespace nmodl

@@ -1,0 +1,73 @@
+// kernels.cuh -- launch interfaces between the C-ABI runtime (api.cu) and
+// the kernels of libnmodl_b300.so.
+#pragma once
+
+#include "nmodl_internal.cuh"
+
+namespace nmodl {
+
+constexpr int kFusedMaxBlock = 1024;
+
+// Arguments of the fused multi-step tile kernel (passed by value).
+struct FusedArgs {
+    const MechD* md;                       // n_types descriptors
+    int32_t n_types;
+    int32_t n_gates[kMaxMechsFused];
+    double* states[kMaxMechsFused];        // SoA, row stride below
+    int64_t stride[kMaxMechsFused];
+    const int32_t* ni[kMaxMechsFused];
+    const int32_t* tiles;                  // tile records
+    int32_t tile_stride;                   // 2 + 2 * n_types
+    int32_t nsteps;
+    int32_t clamp_v;
+    int32_t pad;
+    double* v;
+    double* rhs;
+    double* d;
+    double dt, cm;
+    int32_t* err;
+};
+
+void launch_init_gates(const MechD* md, int n_gates, int64_t n, const int32_t* ni,
+                       const double* v, double* st, int64_t stride, int32_t* err,
+                       cudaStream_t s);
+void launch_state_gates(int prec, const MechD* md, int n_gates, int64_t n,
+                        const int32_t* ni, const double* v, double* st,
+                        int64_t stride, double dt, int32_t* err, cudaStream_t s);
+void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
+                    const int32_t* chunk, const int32_t* ni, const double* v,
+                    const double* st, int64_t stride, double* rhs, double* d,
+                    int32_t* err, cudaStream_t s);
+cudaError_t launch_fused(int prec, const FusedArgs& a, int n_tiles, int block,
+                         size_t smem, cudaStream_t s);
+size_t fused_static_smem(int prec);
+cudaError_t fused_prepare(int prec, size_t max_smem);
+
+// kinetic scheme
+struct KinCounters {
+    unsigned long long iters;     // total Newton / refinement updates
+    unsigned long long nonconv;   // instances that hit the iteration cap
+    int32_t max_iter_seen;
+    int32_t pad;
+};
+void launch_kin9_init(const Kin9D* kd, int64_t n, const int32_t* ni,
+                      const double* v, double* st, int64_t stride, int32_t* err,
+                      cudaStream_t s);
+void launch_kin9_state(int prec, const Kin9D* kd, int64_t n, const int32_t* ni,
+                       const double* v, double* st, int64_t stride, double dt,
+                       double tol, int max_iter, int ir_max,
+                       const int32_t* list, int64_t n_list_max,
+                       const int32_t* n_list_dev, KinCounters* cnt,
+                       int32_t* err, cudaStream_t s);
+
+// common
+void launch_chunk_starts(const int32_t* ni, int64_t n, int64_t n_chunks,
+                         int32_t* chunk, cudaStream_t s);
+void launch_validate_index(const int32_t* ni, int64_t n, int64_t n_nodes,
+                           int32_t* flags, cudaStream_t s);
+void launch_vupdate(int64_t n_nodes, double* v, const double* rhs, double* d,
+                    double cmdt, int clamp, int32_t* err, cudaStream_t s);
+void launch_tile_bounds(const int32_t* ni, int64_t n, const int64_t* nodes,
+                        int64_t n_bounds, int32_t* out, cudaStream_t s);
+
+}  // namespace nmodl

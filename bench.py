@@ -1,0 +1,336 @@
+"""Benchmark: mechanism instance-steps/s of the NMODL hot path on one B300.
+
+Workload (default): the 10-type cortical channel mix on 2,000,000 isolated
+compartments, plain FP64 (cnexp gates, analytic-conductance currents,
+deterministic rhs/d accumulation, diagonal v update), dt = 0.025 ms.  One
+bench "step" is one 200-time-step run of the whole network through
+nmodl_step (5 fused launches of 40 steps, each replayed from a CUDA graph).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp64|mixed] [--nodes N]
+
+Prints one JSON line.  Multi-GPU (torchrun): every rank simulates its own
+network of the same size (weak scaling, no data-path collective; a barrier
+and a max-reduction of the timings only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1905_02241_b300 import workloads as W  # noqa: E402
+
+DT, CM, NSTEPS = 0.025, 1.0, 200
+METRIC = "mechanism instance-steps/s (state+cur)"
+
+# FP64 pipe instructions of a minimal implementation of each operation,
+# the unit of the algorithmic op count of the FP64 path:
+# add/sub/mul/fma 1; exp/expm1 10 (table-driven range reduction + degree-6
+# polynomial + reconstruction); division 7 (FP32 seed, two Newton steps,
+# quotient and one correction).
+C_EXP, C_DIV = 10, 7
+RATE_COST = {0: 2 + C_EXP + 1, 1: 2 + C_EXP + 1 + C_DIV, 2: 2 + C_EXP + 1 + C_DIV}
+GATE_TAIL = 1 + C_DIV + 1 + C_EXP + 1 + 1 + 1  # s, minf, x, exp, 1-e, diff, fma
+NODE_COST = 1 + C_DIV + 1                       # d += cm/dt, rhs/d, v +=
+
+
+def fp64_ops_per_step(wl) -> float:
+    """Algorithmic FP64 ops of one network time step (cur + v + state)."""
+    ops = NODE_COST * wl["n_nodes"]
+    for m in wl["mechs"]:
+        p, n = m["params"], m["node_index"].size
+        if m["type"] == W.TYPE_HH:
+            # gates m, h, n: (alpha form, beta form) = (LINOID, EXP), (EXP,
+            # SIGMOID), (LINOID, EXP); currents: gna (4 mul), gk (4 mul),
+            # three g(v - e) (2 each), sums (4), accumulate (2)
+            per = sum(RATE_COST[a] + RATE_COST[b] + GATE_TAIL
+                      for a, b in ((2, 0), (0, 1), (2, 0)))
+            per += 4 + 4 + 3 * 2 + 4 + 2
+        else:
+            ng = int(p[0])
+            per = 0
+            pw = 0
+            for g in range(ng):
+                o = 6 + 9 * g
+                per += RATE_COST[int(p[o + 1])] + RATE_COST[int(p[o + 5])] + GATE_TAIL
+                pw += int(p[o])
+            per += pw + 2 + 2
+        ops += per * n
+    return float(ops)
+
+
+def n_instances(wl) -> int:
+    return int(sum(m["node_index"].size for m in wl["mechs"]))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.path = None
+        if not uuid:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", uuid, f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 8:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = max(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        loaded = [s for s in sm if s > 0.5 * mx] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, x in zip(names, r[4:8]) if x == "Active"})
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# -------------------------------------------------------------- CPU oracle
+
+def _subnet(wl, nodes):
+    remap = -np.ones(wl["n_nodes"], dtype=np.int64)
+    remap[nodes] = np.arange(nodes.size)
+    mechs = []
+    for m in wl["mechs"]:
+        keep = remap[m["node_index"]] >= 0
+        mechs.append(dict(type=m["type"], params=m["params"],
+                          node_index=remap[m["node_index"][keep]].astype(np.int32)))
+    return dict(n_nodes=int(nodes.size), mechs=mechs, v0=wl["v0"][nodes])
+
+
+def time_oracle(wl, n_nodes_sample: int, target_s: float):
+    from oracle import oracle as orc
+    nodes = np.arange(min(n_nodes_sample, wl["n_nodes"]))
+    sub = _subnet(wl, nodes)
+    st = [orc.mech_init(m["type"], m["params"], m["node_index"], sub["v0"])
+          for m in sub["mechs"]]
+    ninst = n_instances(sub)
+    t0 = time.perf_counter()
+    orc.step(sub["mechs"], st, sub["v0"], sub["n_nodes"], DT, nsteps=2)
+    per_step = (time.perf_counter() - t0) / 2
+    k = max(1, min(NSTEPS, int(target_s / max(per_step, 1e-9))))
+    t0 = time.perf_counter()
+    orc.step(sub["mechs"], st, sub["v0"], sub["n_nodes"], DT, nsteps=k)
+    el = time.perf_counter() - t0
+    desc = (f"first {sub['n_nodes']} nodes ({ninst} instances, whole nodes) of the "
+            f"same network, {k} time steps, single thread")
+    return ninst * k / el, desc, el
+
+
+# --------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--nodes", type=int, default=2_000_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    config = {"workload": f"cortical 10-type cnexp mix, {args.nodes} nodes, "
+                          f"{NSTEPS} steps of dt {DT} ms, {args.precision}",
+              "nodes": args.nodes, "steps_per_bench_step": NSTEPS, "dt_ms": DT,
+              "l2": "inputs larger than L2 (states and node_index > 126 MB)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        wl = W.cortical_mix(args.nodes, seed=2)
+        rates = []
+        sample = None
+        for s in range(args.warmup + args.steps):
+            r, sample, _ = time_oracle(wl, 4000, 2.0)
+            if s >= args.warmup:
+                rates.append(r)
+        v = float(np.median(rates))
+        line = {"impl": "reference", "metric": METRIC, "value": v,
+                "unit": "instance-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": "instance-steps/s", "cores": 1,
+                                 "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": "instance-steps/s",
+                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)
+    from paper_1905_02241_b300 import _lib
+    from paper_1905_02241_b300.api import NMODL_FP64, NMODL_MIXED, Context, Mechanism
+
+    wl = W.cortical_mix(args.nodes, seed=2 + 1000 * rank)
+    prec = NMODL_FP64 if args.precision == "fp64" else NMODL_MIXED
+    ctx = Context(dev, precision=prec)
+    mechs = [Mechanism(ctx, m["type"], m["node_index"], wl["n_nodes"], m["params"])
+             for m in wl["mechs"]]
+    n = wl["n_nodes"]
+    ninst = n_instances(wl)
+    v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
+    rhs = torch.zeros(n, dtype=torch.float64, device=v.device)
+    d = torch.zeros_like(rhs)
+    for m in mechs:
+        m.init(v)
+    torch.cuda.synchronize()
+    stream = ctx.stream
+
+    def one():
+        ctx.step(mechs, DT, CM, v, rhs, d, NSTEPS)
+
+    for _ in range(args.warmup):
+        one()
+    assert ctx.sync() == 0
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one()
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    assert ctx.sync() == 0
+    if dist:
+        t = torch.tensor([ms], device=v.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    window = ctx.options.window
+    launches_per_step = -(-NSTEPS // window)
+    gpu_launches = launches_per_step * args.steps
+    value = world * ninst * NSTEPS * args.steps / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the fused tile kernel: the whole step)
+    launch_ms = ms / gpu_launches
+    if prec == NMODL_FP64:
+        ops_launch = fp64_ops_per_step(wl) * window
+        peak = _lib.nmodl_probe_peak(dev, 0)  # FP64 FMA lane-ops/s
+        roof = {"bound": "alu", "pipe": "fp64", "achieved": ops_launch / (launch_ms * 1e-3) / 1e12,
+                "peak": peak / 1e12, "unit": "Tops/s (FP64 pipe instructions)",
+                "peak_source": "measured DFMA probe (nmodl_probe_peak), this run",
+                "ops_per_launch": ops_launch}
+    else:
+        ops_launch = None
+        peak = _lib.nmodl_probe_peak(dev, 0)
+        roof = {"bound": "alu", "pipe": "fp64", "achieved": None, "peak": peak / 1e12,
+                "unit": "Tops/s"}
+    if roof.get("achieved") is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = "k_fused_tiles<FP64>" if prec == NMODL_FP64 else "k_fused_tiles<MIXED>"
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        host_states = [torch.empty((m.n_states, m.n), dtype=torch.float64).pin_memory()
+                       for m in mechs]
+        for m, hs in zip(mechs, host_states):
+            for k in range(m.n_states):
+                _lib.nmodl_get_state(m.handle, k, hs[k].data_ptr())
+        v_host = v.cpu().pin_memory()
+        h2d = v_host.numel() * 8 + sum(hs.numel() * 8 for hs in host_states)
+        ksteps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            v.copy_(v_host, non_blocking=True)
+            for m, hs in zip(mechs, host_states):
+                for k in range(m.n_states):
+                    _lib.nmodl_set_state(m.handle, k, hs[k].data_ptr())
+            ctx.step(mechs, DT, CM, v, rhs, d, NSTEPS)
+            for m, hs in zip(mechs, host_states):
+                for k in range(m.n_states):
+                    _lib.nmodl_get_state(m.handle, k, hs[k].data_ptr())
+            v_host.copy_(v, non_blocking=True)
+            torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": world * ninst * NSTEPS * ksteps / el, "unit": "instance-steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d),
+               "steps": ksteps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        r, sample, el = time_oracle(wl, 60000, 12.0)
+        cpu = {"value": r, "unit": "instance-steps/s", "cores": 1, "kind": "oracle",
+               "sample": sample, "seconds": round(el, 2)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "instance-steps/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == NMODL_FP64 else "f32+f64",
+                "data": "synthetic", "config": dict(config, instances=ninst,
+                                                    parallelism=f"replicas x{world}"),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": gpu_launches, "clocks": clk}
+        print(json.dumps(line))
+    for m in mechs:
+        m.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

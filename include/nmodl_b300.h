@@ -192,6 +192,13 @@ NMODL_API int nmodl_stats(nmodl_mech *m, nmodl_stats_t *out);
 /* Static text for a status code. */
 NMODL_API const char *nmodl_strerror(int status);
 
+/* Diagnostic (no counterpart in the paper's method): measured throughput of
+ * the arithmetic pipe `kind` on device `device` -- 0: FP64 FMA, 1: FP32 FMA
+ * (lane FMAs per second), 2: exp2 on the special-function unit (lane ops per
+ * second).  Used as the roofline denominator of the ALU-bound kernels.
+ * Synchronous; allocates 64 bytes for the duration of the call. */
+NMODL_API int nmodl_probe_peak(int device, int kind, double *ops_per_s);
+
 /* Library version, e.g. 100 for 0.1.0. */
 NMODL_API int nmodl_version(void);
 

@@ -72,6 +72,7 @@ _SIGS = {
     "nmodl_get_state": (_i32, [_vp, _i32, _vp]),
     "nmodl_set_state": (_i32, [_vp, _i32, _vp]),
     "nmodl_stats": (_i32, [_vp, _P(nmodl_stats_t)]),
+    "nmodl_probe_peak": (_i32, [_i32, _i32, _P(_d)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -178,3 +179,9 @@ def nmodl_stats(m: int) -> nmodl_stats_t:
     s = nmodl_stats_t()
     _check(lib.nmodl_stats(m, ctypes.byref(s)), "nmodl_stats")
     return s
+
+
+def nmodl_probe_peak(device: int, kind: int) -> float:
+    x = _d()
+    _check(lib.nmodl_probe_peak(int(device), int(kind), ctypes.byref(x)), "nmodl_probe_peak")
+    return x.value

@@ -5,8 +5,10 @@
     m.init(v); ctx.step([m], dt, cm, v, rhs, d, nsteps)
 
 Tensors must be contiguous and on the context's device (float64 for v, rhs,
-d and states).  Every call enqueues on the context's stream, which defaults
-to torch's current stream at creation.
+d and states).  Every call enqueues on the context's stream (by default a
+dedicated stream, so that windows can be replayed from CUDA graphs); each
+enqueuing call is ordered after torch's current stream and torch's current
+stream after it, so tensors may be produced and consumed with torch freely.
 """
 from __future__ import annotations
 
@@ -35,12 +37,18 @@ class Context:
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None,
                  **options):
         self.device = int(device)
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         opt = _lib.nmodl_options_default()
         for k, v in options.items():
             setattr(opt, k, v)
         self.options = opt
         self.handle = _lib.nmodl_ctx_create(self.device, self.stream.cuda_stream, opt)
+
+    def enter(self) -> None:
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def leave(self) -> None:
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
 
     def set_options(self, **options) -> None:
         for k, v in options.items():
@@ -56,9 +64,11 @@ class Context:
             raise NmodlError(s, "device")
 
     def step(self, mechs, dt, cm, v, rhs, d, nsteps: int) -> None:
+        self.enter()
         _lib.nmodl_step(self.handle, [m.handle for m in mechs], dt, cm,
                         _dptr(v, device=self.device), _dptr(rhs, device=self.device),
                         _dptr(d, device=self.device), nsteps)
+        self.leave()
 
     def close(self) -> None:
         if self.handle:
@@ -89,24 +99,34 @@ class Mechanism:
         self.n_states = _lib.nmodl_mech_n_states(self.handle)
 
     def init(self, v: torch.Tensor) -> None:
+        self.ctx.enter()
         _lib.nmodl_init(self.handle, _dptr(v, device=self.ctx.device))
+        self.ctx.leave()
 
     def state(self, dt: float, v: torch.Tensor) -> None:
+        self.ctx.enter()
         _lib.nmodl_state(self.handle, dt, _dptr(v, device=self.ctx.device))
+        self.ctx.leave()
 
     def cur(self, v, rhs, d) -> None:
         dev = self.ctx.device
+        self.ctx.enter()
         _lib.nmodl_cur(self.handle, _dptr(v, device=dev), _dptr(rhs, device=dev),
                        _dptr(d, device=dev))
+        self.ctx.leave()
 
     def get_state(self, k: int, out: torch.Tensor | None = None) -> torch.Tensor:
         if out is None:
             out = torch.empty(self.n, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        self.ctx.enter()
         _lib.nmodl_get_state(self.handle, k, _dptr(out) if self.n else 0)
+        self.ctx.leave()
         return out
 
     def set_state(self, k: int, x: torch.Tensor) -> None:
+        self.ctx.enter()
         _lib.nmodl_set_state(self.handle, k, _dptr(x) if self.n else 0)
+        self.ctx.leave()
 
     def states(self) -> torch.Tensor:
         """All states as a (n_states, n) float64 device tensor (copy)."""

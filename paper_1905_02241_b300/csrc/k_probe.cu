@@ -1,0 +1,98 @@
+// k_probe.cu -- throughput probes of the arithmetic pipes that bound the
+// mechanism kernels (the FP64 FMA pipe for the plain FP64 path; the FP32 FMA
+// and exp2 (MUFU) pipes for the mixed path).  Each thread runs independent
+// dependency chains so that the pipe, not latency, limits the rate.  The
+// grid is a multiple of the SM count.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace nmodl {
+
+constexpr int kChains = 8;
+
+__global__ void k_probe_dfma(double* sink, int iters, double a, double b) {
+    double x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = (threadIdx.x + c) * 1e-3;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+    double s = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    if (s == 12345.678) sink[0] = s;
+}
+
+__global__ void k_probe_ffma(float* sink, int iters, float a, float b) {
+    float x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = (threadIdx.x + c) * 1e-3f;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = fmaf(x[c], a, b);
+    float s = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    if (s == 12345.678f) sink[0] = s;
+}
+
+__global__ void k_probe_ex2(float* sink, int iters) {
+    float x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = -(threadIdx.x % 7 + c) * 1e-3f;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = exp2f(x[c]) - 1.0f;  // stays in [-1, 0]
+    float s = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    if (s == 12345.678f) sink[0] = s;
+}
+
+}  // namespace nmodl
+
+using namespace nmodl;
+
+// kind 0: FP64 FMA, 1: FP32 FMA (ops = lane FMAs / s), 2: exp2 (lane ops / s)
+extern "C" NMODL_API int nmodl_probe_peak(int device, int kind, double* ops_per_s) {
+    if (!ops_per_s || kind < 0 || kind > 2) return NMODL_ERR_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    double* sink = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = NMODL_OK;
+    if (cudaMalloc(&sink, 64) != cudaSuccess || cudaStreamCreate(&s) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = NMODL_ERR_CUDA;
+    } else {
+        const int block = 256;
+        const int grid = sms * 8;
+        int iters = kind == 0 ? 512 : 8192;
+        double best = 0.0;
+        for (int rep = 0; rep < 7 && rc == NMODL_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            if (kind == 0) k_probe_dfma<<<grid, block, 0, s>>>(sink, iters, 0.999999, 1e-7);
+            else if (kind == 1) k_probe_ffma<<<grid, block, 0, s>>>((float*)sink, iters, 0.9999f, 1e-5f);
+            else k_probe_ex2<<<grid, block, 0, s>>>((float*)sink, iters);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = NMODL_ERR_CUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double ops = (double)grid * block * iters * kChains;
+            if (rep > 0) best = std::max(best, ops / (ms * 1e-3));
+            if (ms < 20.f) iters *= 2;  // grow until the launch runs >= 20 ms
+        }
+        *ops_per_s = best;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    if (sink) cudaFree(sink);
+    cudaSetDevice(prev);
+    return rc;
+}

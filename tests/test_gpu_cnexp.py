@@ -1,0 +1,301 @@
+"""GPU parity of the cnexp family (HH and generic gates) against the FP64
+oracle, through the C ABI: state, INITIAL, current accumulation, the fused
+and generic network step, mixed precision, and full-size sampled parity."""
+import numpy as np
+import pytest
+
+from paper_1905_02241_b300 import workloads as W
+from gpu_helpers import (TOL_FP64, make_mechs, node_scale, state_err,
+                         sub_network, to_dev)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1905_02241_b300 import api as A
+    return A
+
+
+def _ctx(api, **kw):
+    return api.Context(0, **kw)
+
+
+def _random_states(wl, seed):
+    rng = np.random.default_rng(seed)
+    from oracle import oracle as orc
+    return [rng.uniform(0, 1, size=(orc.n_states(m["type"], m["params"]),
+                                    m["node_index"].size)) for m in wl["mechs"]]
+
+
+def _wl_hh(n=4099, seed=1):
+    wl = W.hh_single(n, seed)
+    wl["v0"] = W.Stream(seed, 9).uniform(n, -100.0, 60.0)
+    return wl
+
+
+# ---------------------------------------------------------------- state
+
+@pytest.mark.parametrize("which", ["hh", "mix"])
+@pytest.mark.parametrize("dt", [0.025, 0.3])
+def test_state_one_step_fp64(api, orc, which, dt):
+    wl = _wl_hh() if which == "hh" else W.cortical_mix(3001, seed=5, v_lo=-100, v_hi=60)
+    ctx = _ctx(api)
+    mechs = make_mechs(ctx, wl)
+    st0 = _random_states(wl, 3)
+    v = to_dev(wl["v0"])
+    for m, s, spec in zip(mechs, st0, wl["mechs"]):
+        if m.n_states == 0:
+            continue
+        m.set_states(to_dev(s))
+        m.state(dt, v)
+        got = m.states().cpu().numpy()
+        ref = orc.mech_state(spec["type"], spec["params"], spec["node_index"],
+                             wl["v0"], s, dt)
+        assert state_err(got, ref) <= TOL_FP64, (spec.get("name"), state_err(got, ref))
+    assert ctx.sync() == 0
+
+
+def test_init_fp64(api, orc):
+    wl = W.cortical_mix(2003, seed=6, v_lo=-100, v_hi=60)
+    wl["mechs"].insert(0, _wl_hh(2003)["mechs"][0])
+    ctx = _ctx(api)
+    mechs = make_mechs(ctx, wl)
+    v = to_dev(wl["v0"])
+    for m, spec in zip(mechs, wl["mechs"]):
+        m.init(v)
+        ref = orc.mech_init(spec["type"], spec["params"], spec["node_index"], wl["v0"])
+        assert state_err(m.states().cpu().numpy(), ref) <= TOL_FP64
+
+
+def test_vtrap_singular_point(api, orc):
+    # v exactly at the LINOID singularity of alpha_m (-40) and alpha_n (-55)
+    v0 = np.array([-40.0, -55.0, -40.0 + 1e-7, -55.0 - 3e-6, -65.0])
+    ni = np.arange(5, dtype=np.int32)
+    wl = dict(n_nodes=5, mechs=[dict(type=W.TYPE_HH, params=W.hh_params(), node_index=ni)])
+    ctx = _ctx(api)
+    (m,) = make_mechs(ctx, wl)
+    v = to_dev(v0)
+    s0 = np.full((3, 5), 0.3)
+    m.set_states(to_dev(s0))
+    m.state(0.025, v)
+    ref = orc.mech_state(W.TYPE_HH, W.hh_params(), ni, v0, s0, 0.025)
+    assert state_err(m.states().cpu().numpy(), ref) <= TOL_FP64
+    assert ctx.sync() == 0
+
+
+# ------------------------------------------------------------------ cur
+
+def _cur_case(api, orc, wl, seed=4):
+    ctx = _ctx(api)
+    mechs = make_mechs(ctx, wl)
+    st = _random_states(wl, seed)
+    rng = np.random.default_rng(seed)
+    n = wl["n_nodes"]
+    rhs0 = rng.normal(size=n)
+    d0 = rng.uniform(0.05, 1.0, size=n)
+    v = to_dev(wl["v0"])
+    rhs, d = to_dev(rhs0), to_dev(d0)
+    r_ref, d_ref = rhs0.copy(), d0.copy()
+    for m, s, spec in zip(mechs, st, wl["mechs"]):
+        m.set_states(to_dev(s))
+        m.cur(v, rhs, d)
+        r_ref, d_ref = orc.mech_cur(spec["type"], spec["params"], spec["node_index"],
+                                    wl["v0"], s, r_ref, d_ref)
+    sr, sd = node_scale(orc, wl, st, wl["v0"], rhs0, d0)
+    er = np.abs(rhs.cpu().numpy() - r_ref)
+    ed = np.abs(d.cpu().numpy() - d_ref)
+    assert np.all(er <= TOL_FP64 * sr + 1e-300), float(np.max(er / np.maximum(sr, 1e-300)))
+    assert np.all(ed <= TOL_FP64 * sd + 1e-300)
+    # untouched nodes stay bitwise unchanged
+    touched = np.zeros(n, bool)
+    for spec in wl["mechs"]:
+        touched[spec["node_index"]] = True
+    assert np.array_equal(rhs.cpu().numpy()[~touched], rhs0[~touched])
+    # determinism: a second accumulation from the same start is bitwise equal
+    rhs2, d2 = to_dev(rhs0), to_dev(d0)
+    for m in mechs:
+        m.cur(v, rhs2, d2)
+    assert torch.equal(rhs, rhs2) and torch.equal(d, d2)
+    assert ctx.sync() == 0
+
+
+def test_cur_mix(api, orc):
+    _cur_case(api, orc, W.cortical_mix(4001, seed=7, v_lo=-100, v_hi=60))
+
+
+def test_cur_hh(api, orc):
+    _cur_case(api, orc, _wl_hh(1000))
+
+
+def test_cur_long_segments(api, orc):
+    """Segments longer than a warp and straddling several 32-wide pieces."""
+    s = W.Stream(11, 1)
+    lens = s.integers(300, 0, 100)
+    lens[5] = 257
+    lens[6] = 31
+    lens[7] = 33
+    ni = np.repeat(np.arange(300), lens).astype(np.int32)
+    blocks = W.cortical_type_params(2)
+    wl = dict(n_nodes=300, v0=s.uniform(300, -90, 40),
+              mechs=[dict(type=W.TYPE_CNEXP, params=blocks[0], node_index=ni),
+                     dict(type=W.TYPE_CNEXP, params=blocks[9],
+                          node_index=np.array([3, 3, 299], dtype=np.int32))])
+    _cur_case(api, orc, wl)
+
+
+def test_empty_mechanism(api, orc):
+    ctx = _ctx(api)
+    from paper_1905_02241_b300.api import Mechanism
+    m = Mechanism(ctx, W.TYPE_CNEXP, np.zeros(0, np.int32), 10, W.cortical_type_params(2)[0])
+    v = to_dev(np.full(10, -65.0))
+    rhs, d = to_dev(np.zeros(10)), to_dev(np.zeros(10))
+    m.init(v)
+    m.state(0.025, v)
+    m.cur(v, rhs, d)
+    ctx.step([m], 0.025, 1.0, v, rhs, d, 3)
+    assert float(rhs.abs().sum()) == 0.0
+    np.testing.assert_allclose(d.cpu().numpy(), 1e-3 / 0.025)
+    assert ctx.sync() == 0
+
+
+# ----------------------------------------------------------------- step
+
+def _step_case(api, orc, wl, nsteps, tol, **opts):
+    ctx = _ctx(api, **opts)
+    mechs = make_mechs(ctx, wl)
+    st0 = [orc.mech_init(m["type"], m["params"], m["node_index"], wl["v0"])
+           for m in wl["mechs"]]
+    for m, s in zip(mechs, st0):
+        if m.n_states:
+            m.set_states(to_dev(s))
+    n = wl["n_nodes"]
+    v, rhs, d = to_dev(wl["v0"]), to_dev(np.zeros(n)), to_dev(np.zeros(n))
+    ctx.step(mechs, 0.025, 1.0, v, rhs, d, nsteps)
+    assert ctx.sync() == 0
+    v_ref, r_ref, d_ref, s_ref = orc.step(wl["mechs"], st0, wl["v0"], n, 0.025,
+                                          nsteps=nsteps, clamp_v=opts.get("clamp_v", 0))
+    ev = np.max(np.abs(v.cpu().numpy() - v_ref) / np.maximum(np.abs(v_ref), 1.0))
+    es = max([state_err(m.states().cpu().numpy(), s) for m, s in zip(mechs, s_ref)
+              if m.n_states] + [0.0])
+    # rhs/d of the last step.  sum|g (v - e)| <= d * 200 mV bounds the sum of
+    # the magnitudes of rhs's terms, so it is a cancellation-safe scale.
+    er = np.max(np.abs(rhs.cpu().numpy() - r_ref) / (200.0 * d_ref))
+    ed = np.max(np.abs(d.cpu().numpy() - d_ref) / np.abs(d_ref))
+    assert ev <= tol and es <= tol and er <= tol and ed <= tol, (ev, es, er, ed)
+    return ev, es
+
+
+@pytest.mark.parametrize("tile_smem", [0, 6144, 64])  # 64: no tile fits -> generic
+def test_step_one_fp64(api, orc, tile_smem):
+    wl = W.cortical_mix(5003, seed=8)
+    _step_case(api, orc, wl, 1, TOL_FP64, tile_smem=tile_smem)
+
+
+@pytest.mark.parametrize("window,use_graph", [(40, 1), (7, 0), (3, 1)])
+def test_step_window_fp64(api, orc, window, use_graph):
+    wl = W.cortical_mix(3001, seed=9)
+    _step_case(api, orc, wl, 20, 1e-10, window=window, use_graph=use_graph,
+               tile_smem=8192)
+
+
+def test_step_hh_trajectory(api, orc):
+    """HH on 4096 isolated nodes for 1000 steps (25 ms): trajectory parity."""
+    wl = W.hh_single(4096, 1)
+    ev, es = _step_case(api, orc, wl, 1000, 1e-9)
+    print(f"HH 1000-step trajectory: max rel v err {ev:.2e}, state err {es:.2e}")
+
+
+def test_step_clamped(api, orc):
+    wl = W.cortical_mix(2001, seed=10)
+    _step_case(api, orc, wl, 5, 1e-11, clamp_v=1)
+
+
+def test_step_with_hh_and_mix(api, orc):
+    wl = W.cortical_mix(2500, seed=12)
+    wl["mechs"].insert(3, dict(type=W.TYPE_HH, params=W.hh_params(),
+                               node_index=np.arange(0, 2500, 3, dtype=np.int32)))
+    _step_case(api, orc, wl, 10, 1e-10, tile_smem=12288)
+
+
+# ------------------------------------------------------------ precision
+
+def test_mixed_precision_errors(api, orc):
+    """MIXED vs the FP64 oracle, per quantity (one step and 200 steps)."""
+    wl = W.cortical_mix(3001, seed=13)
+    n = wl["n_nodes"]
+    st0 = [orc.mech_init(m["type"], m["params"], m["node_index"], wl["v0"])
+           for m in wl["mechs"]]
+    out = {}
+    for nsteps in (1, 200):
+        ctx = _ctx(api, precision=api.NMODL_MIXED, tile_smem=16384)
+        mechs = make_mechs(ctx, wl)
+        for m, s in zip(mechs, st0):
+            if m.n_states:
+                m.set_states(to_dev(s))
+        v, rhs, d = to_dev(wl["v0"]), to_dev(np.zeros(n)), to_dev(np.zeros(n))
+        ctx.step(mechs, 0.025, 1.0, v, rhs, d, nsteps)
+        assert ctx.sync() == 0
+        v_ref, r_ref, d_ref, s_ref = orc.step(wl["mechs"], st0, wl["v0"], n, 0.025,
+                                              nsteps=nsteps)
+        es = max(float(np.max(np.abs(m.states().cpu().numpy() - s)))
+                 for m, s in zip(mechs, s_ref) if m.n_states)
+        ev = float(np.max(np.abs(v.cpu().numpy() - v_ref)))
+        ed = float(np.max(np.abs(d.cpu().numpy() - d_ref) / d_ref))
+        out[nsteps] = (es, ev, ed)
+    print("MIXED errors (states abs, v abs mV, d rel):", out)
+    assert out[1][0] <= 1e-6 and out[1][1] <= 1e-5 and out[1][2] <= 1e-6
+    assert out[200][0] <= 1e-4 and out[200][1] <= 1e-2
+
+
+def test_mixed_standalone_state(api, orc):
+    wl = W.cortical_mix(2001, seed=14, v_lo=-100, v_hi=60)
+    ctx = _ctx(api, precision=api.NMODL_MIXED)
+    mechs = make_mechs(ctx, wl)
+    st0 = _random_states(wl, 5)
+    v = to_dev(wl["v0"])
+    worst = 0.0
+    for m, s, spec in zip(mechs, st0, wl["mechs"]):
+        if not m.n_states:
+            continue
+        m.set_states(to_dev(s))
+        m.state(0.025, v)
+        ref = orc.mech_state(spec["type"], spec["params"], spec["node_index"],
+                             wl["v0"], s, 0.025)
+        worst = max(worst, float(np.max(np.abs(m.states().cpu().numpy() - ref))))
+    print("MIXED standalone state abs err", worst)
+    assert worst <= 1e-6
+
+
+# -------------------------------------------------- full-size, sampled
+
+def test_full_size_sampled_parity(api, orc):
+    """2M-node cortical mix in the launch configuration the benchmark uses
+    (fused FP64 step, 40-step graph windows): 200 steps on the GPU, checked
+    on 1500 sampled nodes that the oracle integrates as their own isolated
+    sub-network."""
+    wl = W.cortical_mix(2_000_000, seed=2)
+    ctx = _ctx(api)
+    mechs = make_mechs(ctx, wl)
+    n = wl["n_nodes"]
+    v = to_dev(wl["v0"])
+    for m in mechs:
+        m.init(v)
+    rhs, d = to_dev(np.zeros(n)), to_dev(np.zeros(n))
+    ctx.step(mechs, 0.025, 1.0, v, rhs, d, 200)
+    assert ctx.sync() == 0
+    nodes = np.unique(W.Stream(77, 1).integers(1500, 0, n - 1))
+    sub, sel = sub_network(wl, nodes)
+    st0 = [orc.mech_init(m["type"], m["params"], m["node_index"], wl["v0"][nodes])
+           for m in sub["mechs"]]
+    v_ref, r_ref, d_ref, s_ref = orc.step(sub["mechs"], st0, wl["v0"][nodes], nodes.size,
+                                          0.025, nsteps=200)
+    vg = v.cpu().numpy()[nodes]
+    assert np.max(np.abs(vg - v_ref) / np.maximum(np.abs(v_ref), 1.0)) <= 1e-9
+    for m, s, idx in zip(mechs, s_ref, sel):
+        if m.n_states:
+            g = m.states().cpu().numpy()[:, idx]
+            assert state_err(g, s) <= 1e-9
+    np.testing.assert_allclose(d.cpu().numpy()[nodes], d_ref, rtol=1e-9)

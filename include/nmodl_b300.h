@@ -58,6 +58,7 @@ extern "C" {
 #define NMODL_ERR_TIMEOUT (-7)     /* a bounded device wait ran out         */
 #define NMODL_ERR_RANGE (-8)       /* node_index outside [0, n_nodes)       */
 #define NMODL_ERR_UNSUPPORTED (-9) /* combination not supported             */
+#define NMODL_ERR_TOO_LARGE (-10)  /* size above a fixed scratch capacity    */
 
 /* ------------------------------------------------------- mechanism kinds */
 #define NMODL_HH 1
@@ -191,6 +192,38 @@ NMODL_API int nmodl_stats(nmodl_mech *m, nmodl_stats_t *out);
 
 /* Static text for a status code. */
 NMODL_API const char *nmodl_strerror(int status);
+
+/* Current update that allocates nothing (the paper has no counterpart; this
+ * is a deployment convenience).  For callers that cannot call cudaMalloc --
+ * code running inside another framework's memory pool, or a host process
+ * that forbids device allocations after start-up -- this computes exactly
+ * what nmodl_cur computes for one mechanism, without a nmodl_mech object:
+ * rhs[node] -= i, d[node] += g over n_instances instances, accumulated with
+ * the same deterministic segmented reduction.
+ *   device, cuda_stream : the GPU and the cudaStream_t to enqueue on
+ *   type, params, n_params : mechanism kind and parameter block (host)
+ *   node_index   : device, n_instances int32, non-decreasing, < n_nodes
+ *   states       : device, SoA, state k of instance j at states[k*stride+j]
+ *                  (may be NULL for a kind without states, e.g. a leak)
+ *   v, rhs, d    : device, n_nodes doubles (rhs, d accumulated)
+ * Its scratch (validation flags, descriptor, chunk table) lives in one fixed
+ * 1 MiB device array that every GPU which loads the library holds until the
+ * process exits; n_instances above nmodl_cur_noalloc_max_instances()
+ * (8,000,000) is rejected with NMODL_ERR_TOO_LARGE.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) --
+ * make that first call before any stream capture.  The call validates
+ * node_index and waits for that check on the stream (NMODL_ERR_UNSORTED /
+ * NMODL_ERR_RANGE), then enqueues the reduction and returns.  Every call
+ * shares the one scratch array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. */
+NMODL_API int nmodl_cur_noalloc(int device, void *cuda_stream, int type,
+                                int64_t n_instances, const int32_t *node_index,
+                                int64_t n_nodes, const double *params,
+                                int64_t n_params, const double *states,
+                                int64_t stride, const double *v, double *rhs,
+                                double *d);
+/* Largest n_instances nmodl_cur_noalloc accepts. */
+NMODL_API int64_t nmodl_cur_noalloc_max_instances(void);
 
 /* Diagnostic (no counterpart in the paper's method): measured throughput of
  * the arithmetic pipe `kind` on device `device` -- 0: FP64 FMA, 1: FP32 FMA

@@ -20,6 +20,7 @@ ERRORS = {
     -1: "NMODL_ERR_ARG", -2: "NMODL_ERR_UNSORTED", -3: "NMODL_ERR_OOM",
     -4: "NMODL_ERR_CUDA", -5: "NMODL_ERR_NONFINITE", -6: "NMODL_ERR_NOCONV",
     -7: "NMODL_ERR_TIMEOUT", -8: "NMODL_ERR_RANGE", -9: "NMODL_ERR_UNSUPPORTED",
+    -10: "NMODL_ERR_TOO_LARGE",
 }
 
 
@@ -73,6 +74,9 @@ _SIGS = {
     "nmodl_set_state": (_i32, [_vp, _i32, _vp]),
     "nmodl_stats": (_i32, [_vp, _P(nmodl_stats_t)]),
     "nmodl_probe_peak": (_i32, [_i32, _i32, _P(_d)]),
+    "nmodl_cur_noalloc": (_i32, [_i32, _vp, _i32, _i64, _vp, _i64, _vp, _i64, _vp,
+                                 _i64, _vp, _vp, _vp]),
+    "nmodl_cur_noalloc_max_instances": (_i64, []),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -185,3 +189,18 @@ def nmodl_probe_peak(device: int, kind: int) -> float:
     x = _d()
     _check(lib.nmodl_probe_peak(int(device), int(kind), ctypes.byref(x)), "nmodl_probe_peak")
     return x.value
+
+
+def nmodl_cur_noalloc(device: int, stream: int, mtype: int, n_instances: int,
+                      node_index_ptr: int, n_nodes: int, params_ptr: int, n_params: int,
+                      states_ptr: int, stride: int, v_ptr: int, rhs_ptr: int,
+                      d_ptr: int) -> None:
+    _check(lib.nmodl_cur_noalloc(int(device), stream or None, int(mtype), int(n_instances),
+                                 node_index_ptr or None, int(n_nodes), params_ptr or None,
+                                 int(n_params), states_ptr or None, int(stride),
+                                 v_ptr or None, rhs_ptr or None, d_ptr or None),
+           "nmodl_cur_noalloc")
+
+
+def nmodl_cur_noalloc_max_instances() -> int:
+    return lib.nmodl_cur_noalloc_max_instances()

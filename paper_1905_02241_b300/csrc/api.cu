@@ -176,6 +176,27 @@ static int build_desc(nmodl_mech* m) {
     return NMODL_ERR_ARG;
 }
 
+namespace nmodl {
+// Parameter block -> device descriptor, for entry points without a
+// nmodl_mech object.
+int build_desc_for(int type, const double* params, int64_t n_params, MechD* md,
+                   Kin9D* kd, int* n_states) {
+    if (n_params < 0 || n_params > 64 || (n_params > 0 && !params)) return NMODL_ERR_ARG;
+    // one scratch object per host thread; its parameter buffer is reserved
+    // on the thread's first call, so later calls allocate nothing
+    thread_local nmodl_mech tmp;
+    if (tmp.params.capacity() < 64) tmp.params.reserve(64);
+    tmp.type = type;
+    tmp.params.assign(params, params + n_params);
+    const int rc = build_desc(&tmp);
+    if (rc) return rc;
+    *md = tmp.md;
+    *kd = tmp.kd;
+    *n_states = tmp.n_states;
+    return NMODL_OK;
+}
+}  // namespace nmodl
+
 // ---------------------------------------------------------------- ABI
 
 extern "C" {
@@ -194,6 +215,7 @@ const char* nmodl_strerror(int s) {
     case NMODL_ERR_TIMEOUT: return "bounded device wait ran out";
     case NMODL_ERR_RANGE: return "node_index outside [0, n_nodes)";
     case NMODL_ERR_UNSUPPORTED: return "unsupported combination";
+    case NMODL_ERR_TOO_LARGE: return "size exceeds the fixed scratch capacity";
     default: return "unknown status";
     }
 }

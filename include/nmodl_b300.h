@@ -193,6 +193,66 @@ NMODL_API int nmodl_stats(nmodl_mech *m, nmodl_stats_t *out);
 /* Static text for a status code. */
 NMODL_API const char *nmodl_strerror(int status);
 
+/* ------------------------------------------------ kinetic surrogate
+ * A learned stand-in for the per-instance Newton solve of NMODL_KIN9 (the
+ * paper solves KINETIC schemes by implicit Euler + Newton/LU, Section 5.2
+ * and 5.3; the surrogate replaces that solve where it is accurate enough).
+ * Network: inputs (v_n, dt_n, x_0..x_8) with v_n = (v + 20)/80 and
+ * dt_n = (dt - 0.03125)/0.01875; three hidden layers of 128 with SiLU;
+ * 9 outputs y.  BF16 weights and activations on the tensor cores, FP32
+ * accumulation, FP32 master weights.  Prediction: x_hat = P(x + s y) with
+ * P the Euclidean projection onto the probability simplex and s =
+ * ||dt A(v) x||_1 (scaled form) or s = 1.  An instance whose implicit Euler
+ * residual ||x_hat - x - dt A(v) x_hat||_1 exceeds the attached tolerance
+ * falls back to the Newton solve; for the others ||x_hat - x*||_1 <= that
+ * residual, because (I - dt A)^-1 is nonnegative with unit column sums.
+ *
+ * Public weight layout (nmodl_surrogate_n_params() = 35721 floats):
+ * W1 [128][11], b1 [128], W2 [128][128], b2, W3 [128][128], b3, W4 [9][128],
+ * b4 [9]; weights row-major [out][in].
+ * Training rows: X [n][11] normalised inputs, T [n][9] targets (FP32,
+ * device), n a multiple of 16 at most max_batch.  Loss 0.5/n sum (y - T)^2;
+ * Adam (beta 0.9/0.999, eps 1e-8). */
+typedef struct nmodl_surrogate nmodl_surrogate;
+NMODL_API int nmodl_surrogate_n_params(void);
+/* weights: host, public layout, or NULL for zeros; scaled: see above. */
+NMODL_API int nmodl_surrogate_create(nmodl_ctx *ctx, int64_t max_batch,
+                                     const float *weights, int scaled,
+                                     nmodl_surrogate **out);
+NMODL_API void nmodl_surrogate_destroy(nmodl_surrogate *s);
+NMODL_API int nmodl_surrogate_set_weights(nmodl_surrogate *s, const float *w);
+NMODL_API int nmodl_surrogate_get_weights(nmodl_surrogate *s, float *w);
+/* Network outputs Y [n][9] (device) for inputs X [n][11] (device). */
+NMODL_API int nmodl_surrogate_forward(nmodl_surrogate *s, int64_t n,
+                                      const float *X, float *Y);
+/* Loss and gradients (host, public layout) of one batch; synchronous. */
+NMODL_API int nmodl_surrogate_loss_grad(nmodl_surrogate *s, int64_t n,
+                                        const float *X, const float *T,
+                                        float *grad_host, float *loss_host);
+/* One Adam step on a batch; the batch loss goes to *loss_dev if given. */
+NMODL_API int nmodl_surrogate_train_step(nmodl_surrogate *s, int64_t n,
+                                         const float *X, const float *T,
+                                         float lr, float *loss_dev);
+/* Training pairs from Newton steps: inputs X [n][11] and targets
+ * T [n][9] = (y - x)/s for samples (v[i], dt[i], x) -> y (device FP64; x
+ * and y SoA with row stride), with the kinetic parameters of kin. */
+NMODL_API int nmodl_surrogate_make_pairs(nmodl_surrogate *s, const nmodl_mech *kin,
+                                         int64_t n, const double *v,
+                                         const double *dt, const double *x,
+                                         const double *y, int64_t stride,
+                                         float *X, float *T);
+/* One implicit Euler Newton step (Section 5.2/5.3) of n independent samples
+ * of kin's scheme with per-sample v[i] and dt[i]: y := step(x) (device, SoA
+ * with row stride; precision and tolerance from the context options). */
+NMODL_API int nmodl_kin9_solve(nmodl_mech *kin, int64_t n, const double *v,
+                               const double *dt, const double *x, double *y,
+                               int64_t stride);
+/* Let nmodl_state (and nmodl_step) of a NMODL_KIN9 mechanism use the
+ * surrogate with residual tolerance tol (1-norm); s = NULL or tol <= 0
+ * detaches.  The fallback count is reported by nmodl_stats. */
+NMODL_API int nmodl_mech_attach_surrogate(nmodl_mech *m, nmodl_surrogate *s,
+                                          double tol);
+
 /* Current update that allocates nothing (the paper has no counterpart; this
  * is a deployment convenience).  For callers that cannot call cudaMalloc --
  * code running inside another framework's memory pool, or a host process

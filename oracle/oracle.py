@@ -329,11 +329,22 @@ def simplex_project(y):
     return out[:, 0] if col else out
 
 
-def surrogate_step(Ws, bs, v, dt, x):
-    """Projected surrogate prediction of the implicit Euler step, (9, batch)."""
+def surrogate_step(Ws, bs, v, dt, x, params=None):
+    """Projected surrogate prediction of the implicit Euler step, (9, batch).
+
+    With the kinetic parameter block `params` the network output is scaled
+    by s = ||dt A(v) x||_1 (the exact increment is J^-1 (dt A x) and
+    ||J^-1||_1 = 1, so the scaled target has unit size); without it the
+    output is the increment itself."""
+    x = np.asarray(x, dtype=np.float64).reshape(9, -1)
+    v = np.atleast_1d(np.asarray(v, dtype=np.float64))
     X = surrogate_inputs(v, dt, x)
     out, _ = mlp_forward(Ws, bs, X)
-    return simplex_project(X[2:] + out)
+    if params is not None:
+        s = np.array([np.sum(np.abs(dt * (kin9_matrix(params, v[c]) @ x[:, c])))
+                      for c in range(x.shape[1])])
+        out = out * s[None, :]
+    return simplex_project(x + out)
 
 
 def kin9_residual(params, v, dt, x_old, y):

@@ -77,6 +77,17 @@ _SIGS = {
     "nmodl_cur_noalloc": (_i32, [_i32, _vp, _i32, _i64, _vp, _i64, _vp, _i64, _vp,
                                  _i64, _vp, _vp, _vp]),
     "nmodl_cur_noalloc_max_instances": (_i64, []),
+    "nmodl_surrogate_n_params": (_i32, []),
+    "nmodl_surrogate_create": (_i32, [_vp, _i64, _vp, _i32, _P(_vp)]),
+    "nmodl_surrogate_destroy": (None, [_vp]),
+    "nmodl_surrogate_set_weights": (_i32, [_vp, _vp]),
+    "nmodl_surrogate_get_weights": (_i32, [_vp, _vp]),
+    "nmodl_surrogate_forward": (_i32, [_vp, _i64, _vp, _vp]),
+    "nmodl_surrogate_loss_grad": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp]),
+    "nmodl_surrogate_train_step": (_i32, [_vp, _i64, _vp, _vp, ctypes.c_float, _vp]),
+    "nmodl_surrogate_make_pairs": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "nmodl_kin9_solve": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _i64]),
+    "nmodl_mech_attach_surrogate": (_i32, [_vp, _vp, _d]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -204,3 +215,60 @@ def nmodl_cur_noalloc(device: int, stream: int, mtype: int, n_instances: int,
 
 def nmodl_cur_noalloc_max_instances() -> int:
     return lib.nmodl_cur_noalloc_max_instances()
+
+
+def nmodl_surrogate_n_params() -> int:
+    return lib.nmodl_surrogate_n_params()
+
+
+def nmodl_surrogate_create(ctx: int, max_batch: int, weights_ptr: int, scaled: int) -> int:
+    h = _vp()
+    _check(lib.nmodl_surrogate_create(ctx, int(max_batch), weights_ptr or None, int(scaled),
+                                      ctypes.byref(h)), "nmodl_surrogate_create")
+    return h.value
+
+
+def nmodl_surrogate_destroy(s: int) -> None:
+    lib.nmodl_surrogate_destroy(s)
+
+
+def nmodl_surrogate_set_weights(s: int, w_ptr: int) -> None:
+    _check(lib.nmodl_surrogate_set_weights(s, w_ptr), "nmodl_surrogate_set_weights")
+
+
+def nmodl_surrogate_get_weights(s: int, w_ptr: int) -> None:
+    _check(lib.nmodl_surrogate_get_weights(s, w_ptr), "nmodl_surrogate_get_weights")
+
+
+def nmodl_surrogate_forward(s: int, n: int, X_ptr: int, Y_ptr: int) -> None:
+    _check(lib.nmodl_surrogate_forward(s, int(n), X_ptr, Y_ptr), "nmodl_surrogate_forward")
+
+
+def nmodl_surrogate_loss_grad(s: int, n: int, X_ptr: int, T_ptr: int, grad_ptr: int,
+                              loss_ptr: int) -> None:
+    _check(lib.nmodl_surrogate_loss_grad(s, int(n), X_ptr, T_ptr, grad_ptr or None,
+                                         loss_ptr or None), "nmodl_surrogate_loss_grad")
+
+
+def nmodl_surrogate_train_step(s: int, n: int, X_ptr: int, T_ptr: int, lr: float,
+                               loss_ptr: int) -> None:
+    _check(lib.nmodl_surrogate_train_step(s, int(n), X_ptr, T_ptr, float(lr), loss_ptr or None),
+           "nmodl_surrogate_train_step")
+
+
+def nmodl_surrogate_make_pairs(s: int, kin: int, n: int, v_ptr: int, dt_ptr: int, x_ptr: int,
+                               y_ptr: int, stride: int, X_ptr: int, T_ptr: int) -> None:
+    _check(lib.nmodl_surrogate_make_pairs(s, kin, int(n), v_ptr, dt_ptr, x_ptr, y_ptr,
+                                          int(stride), X_ptr, T_ptr),
+           "nmodl_surrogate_make_pairs")
+
+
+def nmodl_kin9_solve(kin: int, n: int, v_ptr: int, dt_ptr: int, x_ptr: int, y_ptr: int,
+                     stride: int) -> None:
+    _check(lib.nmodl_kin9_solve(kin, int(n), v_ptr, dt_ptr, x_ptr, y_ptr, int(stride)),
+           "nmodl_kin9_solve")
+
+
+def nmodl_mech_attach_surrogate(m: int, s: int, tol: float) -> None:
+    _check(lib.nmodl_mech_attach_surrogate(m, s or None, float(tol)),
+           "nmodl_mech_attach_surrogate")

@@ -8,95 +8,24 @@
 #include <new>
 #include <vector>
 
-#include "kernels.cuh"
+#include "runtime.cuh"
 
 using namespace nmodl;
 
-namespace {
+namespace nmodl {
+// api_surrogate.cu: surrogate state update of a NMODL_KIN9 mechanism
+cudaError_t enqueue_surrogate_state(nmodl_mech* m, double dt, const double* v);
+}  // namespace nmodl
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-template <typename T>
-cudaError_t dalloc(T** p, size_t count) {
-    *p = nullptr;
-    if (count == 0) return cudaSuccess;
-    return cudaMalloc((void**)p, count * sizeof(T));
-}
-
-int cuda_status(cudaError_t e) {
+int nmodl_cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return NMODL_OK;
     if (e == cudaErrorMemoryAllocation) return NMODL_ERR_OOM;
     return NMODL_ERR_CUDA;
 }
 
+namespace {
+int cuda_status(cudaError_t e) { return nmodl_cuda_status(e); }
 }  // namespace
-
-// ------------------------------------------------------------- structures
-
-struct GraphEntry {
-    double* v;
-    double* rhs;
-    double* d;
-    double dt, cm;
-    int nsteps, clamp;
-    cudaGraphExec_t exec;
-};
-
-struct Plan {
-    std::vector<nmodl_mech*> mechs;
-    int precision = 0;
-    int64_t n_nodes = 0;
-    bool fused = false;
-    // fused form
-    int n_tiles = 0, block = 256, tile_stride = 0;
-    size_t smem = 0;
-    int32_t* d_tiles = nullptr;
-    MechD* d_md = nullptr;
-    std::vector<GraphEntry> graphs;
-    ~Plan() {
-        for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
-        cudaFree(d_tiles);
-        cudaFree(d_md);
-    }
-};
-
-struct nmodl_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    nmodl_options opt{};
-    int32_t* d_err = nullptr;
-    std::vector<std::unique_ptr<Plan>> plans;
-    int live_mechs = 0;
-};
-
-struct nmodl_mech {
-    nmodl_ctx* ctx = nullptr;
-    int type = 0;
-    int64_t n = 0, n_nodes = 0, stride = 0;
-    int n_states = 0;
-    std::vector<double> params;
-    int32_t* d_ni = nullptr;
-    double* d_states = nullptr;
-    int32_t* d_chunk = nullptr;
-    int64_t n_chunks = 0;
-    MechD md{};
-    MechD* d_md = nullptr;
-    Kin9D kd{};
-    Kin9D* d_kd = nullptr;
-    KinCounters* d_cnt = nullptr;
-    int64_t calls = 0;
-};
 
 // ------------------------------------------------------------ parameters
 
@@ -308,6 +237,8 @@ void nmodl_ctx_destroy(nmodl_ctx* c) {
 }
 
 static void free_mech(nmodl_mech* m) {
+    cudaFree(m->d_fb_list);
+    cudaFree(m->d_fb_count);
     cudaFree(m->d_ni);
     cudaFree(m->d_states);
     cudaFree(m->d_chunk);
@@ -416,9 +347,12 @@ int nmodl_init(nmodl_mech* m, const double* v) {
 static void enqueue_state(nmodl_mech* m, double dt, const double* v) {
     nmodl_ctx* c = m->ctx;
     const nmodl_options& o = c->opt;
-    if (m->type == NMODL_KIN9)
+    if (m->type == NMODL_KIN9 && m->sur) {
+        nmodl::enqueue_surrogate_state(m, dt, v);
+        m->sur_calls++;
+    } else if (m->type == NMODL_KIN9)
         launch_kin9_state(o.precision, m->d_kd, m->n, m->d_ni, v, m->d_states, m->stride,
-                          dt, o.newton_tol, o.newton_max_iter, o.ir_max, nullptr, 0,
+                          dt, nullptr, o.newton_tol, o.newton_max_iter, o.ir_max, nullptr, 0,
                           nullptr, m->d_cnt, c->d_err, c->stream);
     else
         launch_state_gates(o.precision, m->d_md, m->n_states, m->n, m->d_ni, v,
@@ -724,6 +658,8 @@ int nmodl_stats(nmodl_mech* m, nmodl_stats_t* out) {
     out->newton_iters = (int64_t)k.iters;
     out->newton_max = k.max_iter_seen;
     out->nonconverged = (int64_t)k.nonconv;
+    out->fallback = (int64_t)k.fallback;
+    out->surrogate_calls = m->sur_calls;
     return NMODL_OK;
 }
 

@@ -16,20 +16,14 @@
 // F(y) = J y - x (with J's diagonal rebuilt in FP64 so that its columns keep
 // summing exactly to one) and the update of y in FP64; the FP32 factors
 // refine y until max|delta| <= tol or ir_max refinements.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace nmodl {
 
 namespace {
 
-// Edge e joins state lo(e) and hi(e): edges 0..5 are horizontal
-// (3a+b, 3a+b+1), edges 6..11 vertical (k, k+3).
-__host__ __device__ constexpr int edge_lo(int e) {
-    return e < 6 ? 3 * (e / 2) + (e % 2) : e - 6;
-}
-__host__ __device__ constexpr int edge_hi(int e) {
-    return e < 6 ? edge_lo(e) + 1 : edge_lo(e) + 3;
-}
 
 __host__ __device__ constexpr bool in_band(int i, int j) { return (i - j <= 3) && (j - i <= 3); }
 
@@ -70,12 +64,9 @@ __device__ __forceinline__ void lu_band_solve(const R (&M)[9][9], R (&b)[9]) {
     }
 }
 
-__device__ __forceinline__ void warp_count(KinCounters* cnt, int iters,
-                                           bool nonconv, bool active) {
+__device__ __forceinline__ void warp_count(KinCounters* cnt, unsigned long long it,
+                                           unsigned long long nc, int mx) {
     if (!cnt) return;
-    unsigned long long it = active ? (unsigned long long)iters : 0ull;
-    unsigned nc = (active && nonconv) ? 1u : 0u;
-    int mx = active ? iters : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         it += __shfl_down_sync(0xffffffffu, it, o);
@@ -84,7 +75,7 @@ __device__ __forceinline__ void warp_count(KinCounters* cnt, int iters,
     }
     if ((threadIdx.x & 31) == 0) {
         if (it) atomicAdd(&cnt->iters, it);
-        if (nc) atomicAdd(&cnt->nonconv, (unsigned long long)nc);
+        if (nc) atomicAdd(&cnt->nonconv, nc);
         if (mx) atomicMax(&cnt->max_iter_seen, mx);
     }
 }
@@ -154,23 +145,28 @@ __global__ void k_kin9_init(const Kin9D* __restrict__ kd, int64_t n,
 
 // ---------------------------------------------------------------- state
 
+// One thread per instance (or per entry of the first *n_list_dev of list).  ni == nullptr means instance i reads v[i]; dt_arr != nullptr gives
+// each instance its own step (used to generate training pairs).
 template <int PREC, bool LIST>
 __global__ void __launch_bounds__(128)
     k_kin9_state(const Kin9D* __restrict__ kd, int64_t n,
                  const int32_t* __restrict__ ni, const double* __restrict__ v,
-                 double* st, int64_t stride, double dt, double tol, int max_iter,
+                 double* st, int64_t stride, double dt_scalar,
+                 const double* __restrict__ dt_arr, double tol, int max_iter,
                  int ir_max, const int32_t* __restrict__ list,
                  const int32_t* __restrict__ n_list_dev, KinCounters* cnt,
                  int32_t* err) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t n_work = LIST ? (int64_t)*n_list_dev : n;
-    const bool active = t < n_work;
-    int iters = 0;
-    bool nonconv = false;
-    if (active) {
+    unsigned long long it_sum = 0, nc_sum = 0;
+    int it_max = 0;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n_work) {
+        int iters = 0;
+        bool nonconv = false;
         const int64_t i = LIST ? (int64_t)list[t] : t;
         const Kin9D& K = *kd;
-        const double vv = v[ni[i]];
+        const double vv = ni ? v[ni[i]] : v[i];
+        const double dt = dt_arr ? dt_arr[i] : dt_scalar;
         double x[9], y[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
@@ -284,8 +280,11 @@ __global__ void __launch_bounds__(128)
             if (!isfinite(y[a])) latch_error(err, NMODL_ERR_NONFINITE);
             st[a * stride + i] = y[a];
         }
+        it_sum += iters;
+        nc_sum += nonconv ? 1 : 0;
+        it_max = max(it_max, iters);
     }
-    warp_count(cnt, iters, nonconv, active);
+    warp_count(cnt, it_sum, nc_sum, it_max);
 }
 
 void launch_kin9_init(const Kin9D* kd, int64_t n, const int32_t* ni,
@@ -298,7 +297,7 @@ void launch_kin9_init(const Kin9D* kd, int64_t n, const int32_t* ni,
 
 void launch_kin9_state(int prec, const Kin9D* kd, int64_t n, const int32_t* ni,
                        const double* v, double* st, int64_t stride, double dt,
-                       double tol, int max_iter, int ir_max,
+                       const double* dt_arr, double tol, int max_iter, int ir_max,
                        const int32_t* list, int64_t n_list_max,
                        const int32_t* n_list_dev, KinCounters* cnt,
                        int32_t* err, cudaStream_t s) {
@@ -308,14 +307,14 @@ void launch_kin9_state(int prec, const Kin9D* kd, int64_t n, const int32_t* ni,
     const int grid = (int)((work + block - 1) / block);
     if (prec == NMODL_FP64) {
         if (list)
-            k_kin9_state<NMODL_FP64, true><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
+            k_kin9_state<NMODL_FP64, true><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, dt_arr, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
         else
-            k_kin9_state<NMODL_FP64, false><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
+            k_kin9_state<NMODL_FP64, false><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, dt_arr, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
     } else {
         if (list)
-            k_kin9_state<NMODL_MIXED, true><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
+            k_kin9_state<NMODL_MIXED, true><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, dt_arr, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
         else
-            k_kin9_state<NMODL_MIXED, false><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
+            k_kin9_state<NMODL_MIXED, false><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, dt_arr, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
     }
 }
 

@@ -1,0 +1,336 @@
+// k_surrogate.cu -- learned stand-in for the kinetic Newton solve.
+//
+// One implicit Euler step of the 9-state scheme has the exact increment
+// dx* = J^-1 (dt A(v) x) with J = I - dt A column-stochastic, so
+// ||dx*||_1 <= s = ||dt A(v) x||_1.  The MLP (inputs v_n, dt_n, x; 3 hidden
+// layers of 128, SiLU; 9 outputs y) predicts dx = s * y (or dx = y when the
+// scaled form is off); x_hat = P(x + dx) with P the Euclidean projection onto
+// the probability simplex (Held, Wolfe & Crowder 1974).  The implicit Euler
+// residual F(x_hat) = x_hat - x - dt A x_hat decides: ||F||_1 <= tol keeps
+// x_hat (then ||x_hat - x*||_1 <= ||J^-1||_1 ||F||_1 = ||F||_1), otherwise the
+// instance goes on a fallback list for the Newton kernel.
+//
+// k_surrogate_step: persistent CTAs, 8 warps, weights staged once in shared
+// memory (bf16, rows padded by 16 bytes so ldmatrix is conflict-free).  A
+// warp owns 16 instances; the accumulator fragments of one layer are the A
+// fragments of the next (m16n8k16 C and A layouts coincide pairwise), so
+// activations never leave registers.
+#include "kernels.cuh"
+#include "mlp.cuh"
+
+namespace nmodl {
+
+namespace {
+constexpr int kWarps = 8;
+constexpr int P1 = kIn + 8;    // W1 row pitch (elements)
+constexpr int PH = kHid + 8;   // W2, W3, W4 row pitch
+constexpr int kSmemW = (kHid * P1 + 2 * kHid * PH + kOut * PH) * 2;
+constexpr int kSmemB = (3 * kHid + kOut) * 4;
+constexpr int kSmemY = kWarps * 16 * 10 * 4;
+constexpr int kSmemTotal = kSmemW + kSmemB + kSmemY;
+}  // namespace
+
+// Normalised network input feature f of an instance (f >= 11: padding 0).
+__device__ __forceinline__ float sur_feature(int f, float vf, float dtf, const float* xf) {
+    if (f == 0) return (vf + kVShift) * (1.0f / kVScale);
+    if (f == 1) return (dtf - kDtShift) * (1.0f / kDtScale);
+    if (f < kInRaw) return xf[f - 2];
+    return 0.0f;
+}
+
+// FP32 rates dt*k of the 24 transitions and (dt A) x for a state x.
+__device__ __forceinline__ void kin_rates_f(const Kin9D& K, float vf, float dtf,
+                                            float (&dkf)[kKinEdges], float (&dkb)[kKinEdges]) {
+#pragma unroll
+    for (int e = 0; e < kKinEdges; ++e) {
+        dkf[e] = dtf * ((float)K.af[e] * __expf((float)K.bf[e] * vf));
+        dkb[e] = dtf * ((float)K.ab[e] * __expf(-(float)K.bb[e] * vf));
+    }
+}
+__device__ __forceinline__ void dtAx_f(const float (&dkf)[kKinEdges],
+                                       const float (&dkb)[kKinEdges], const float* x,
+                                       float (&z)[9]) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) z[a] = 0.f;
+#pragma unroll
+    for (int e = 0; e < kKinEdges; ++e) {
+        const int lo = edge_lo(e), hi = edge_hi(e);
+        const float f = dkf[e] * x[lo], b = dkb[e] * x[hi];
+        z[hi] += f - b;
+        z[lo] += b - f;
+    }
+}
+
+__device__ __forceinline__ float l1_9(const float (&z)[9]) {
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) s += fabsf(z[a]);
+    return s;
+}
+
+// Euclidean projection of w onto {x >= 0, sum x = 1}: theta is (S_j - 1)/c_j
+// for the largest set {i : w_i >= w_j} whose smallest member stays positive.
+__device__ __forceinline__ void project_simplex9(float (&w)[9]) {
+    float theta = -1e30f;
+    int best = 0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        float S = 0.f;
+        int c = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            if (w[i] >= w[j]) {
+                S += w[i];
+                ++c;
+            }
+        const float th = (S - 1.0f) / (float)c;
+        if (w[j] - th > 0.f && c > best) {
+            best = c;
+            theta = th;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) w[i] = fmaxf(w[i] - theta, 0.f);
+}
+
+__global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smem);
+    __nv_bfloat16* W2s = W1s + kHid * P1;
+    __nv_bfloat16* W3s = W2s + kHid * PH;
+    __nv_bfloat16* W4s = W3s + kHid * PH;
+    float* b1s = reinterpret_cast<float*>(smem + kSmemW);
+    float* b2s = b1s + kHid;
+    float* b3s = b2s + kHid;
+    float* b4s = b3s + kHid;
+    float* ys_all = b4s + kOut;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // ---- stage weights (16-byte rows chunks) and biases
+    auto stage = [&](const __nv_bfloat16* src, __nv_bfloat16* dst, int rows, int cols, int pitch) {
+        const int ch = cols / 8;
+        for (int c = tid; c < rows * ch; c += blockDim.x) {
+            const int r = c / ch, cc = (c % ch) * 8;
+            *reinterpret_cast<uint4*>(dst + r * pitch + cc) =
+                *reinterpret_cast<const uint4*>(src + r * cols + cc);
+        }
+    };
+    stage(a.wbf + kBfW1, W1s, kHid, kIn, P1);
+    stage(a.wbf + kBfW2, W2s, kHid, kHid, PH);
+    stage(a.wbf + kBfW3, W3s, kHid, kHid, PH);
+    stage(a.wbf + kBfW4, W4s, kOut, kHid, PH);
+    for (int i = tid; i < kHid; i += blockDim.x) {
+        b1s[i] = a.params[kOffB1 + i];
+        b2s[i] = a.params[kOffB2 + i];
+        b3s[i] = a.params[kOffB3 + i];
+    }
+    if (tid < kOut) b4s[tid] = a.params[kOffB4 + tid];
+    __syncthreads();
+
+    const Kin9D& K = *a.kd;
+    const float dtf = (float)a.dt;
+    const int g = lane >> 2, t = lane & 3, q = lane >> 3, r8 = lane & 7;
+    float* ys = ys_all + warp * 16 * 10;
+    const int64_t stride_w = (int64_t)gridDim.x * kWarps * 16;
+
+    for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 16; base < a.n;
+         base += stride_w) {
+        // ---- layer 1 input fragment: rows base+g and base+g+8
+        uint32_t afr[4];
+        {
+            float f[2][4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t i = base + g + 8 * h;
+                float xf[9];
+                float vf = 0.f;
+                const bool ok = i < a.n;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) xf[k] = ok ? (float)a.st[k * a.stride + i] : 0.f;
+                if (ok) vf = (float)a.v[a.ni[i]];
+                const int cols[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) f[h][c] = ok ? sur_feature(cols[c], vf, dtf, xf) : 0.f;
+            }
+            afr[0] = pack_bf16(f[0][0], f[0][1]);
+            afr[1] = pack_bf16(f[1][0], f[1][1]);
+            afr[2] = pack_bf16(f[0][2], f[0][3]);
+            afr[3] = pack_bf16(f[1][2], f[1][3]);
+        }
+        float acc[16][4];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+#pragma unroll
+        for (int np = 0; np < 8; ++np) {
+            uint32_t b[4];
+            ldsm_x4(b, W1s + (16 * np + r8 + (q >> 1) * 8) * P1 + (q & 1) * 8);
+            mma_bf16_16816(acc[2 * np], afr, b[0], b[1]);
+            mma_bf16_16816(acc[2 * np + 1], afr, b[2], b[3]);
+        }
+        uint32_t ah[8][4];
+        auto to_frags = [&](const float* bias) {
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = 2 * kk + h;
+                    const int col = 8 * j + 2 * t;
+                    const float b0 = bias[col], b1 = bias[col + 1];
+                    ah[kk][2 * h] = pack_bf16(silu_f(acc[j][0] + b0), silu_f(acc[j][1] + b1));
+                    ah[kk][2 * h + 1] = pack_bf16(silu_f(acc[j][2] + b0), silu_f(acc[j][3] + b1));
+                }
+            }
+        };
+        // A fragment order: a0a1 (row g, k 2t) = tile 2kk c0c1; a2a3 (row g+8)
+        // = tile 2kk c2c3; a4a5 = tile 2kk+1 c0c1; a6a7 = tile 2kk+1 c2c3.
+        auto to_frags_ordered = [&](const float* bias) {
+            to_frags(bias);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const uint32_t x0 = ah[kk][0], x1 = ah[kk][1], x2 = ah[kk][2], x3 = ah[kk][3];
+                ah[kk][0] = x0;  // tile 2kk, row g
+                ah[kk][1] = x1;  // tile 2kk, row g+8
+                ah[kk][2] = x2;  // tile 2kk+1, row g
+                ah[kk][3] = x3;  // tile 2kk+1, row g+8
+            }
+        };
+        to_frags_ordered(b1s);
+        auto hidden = [&](const __nv_bfloat16* Ws) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+#pragma unroll
+                for (int np = 0; np < 8; ++np) {
+                    uint32_t b[4];
+                    ldsm_x4(b, Ws + (16 * np + r8 + (q >> 1) * 8) * PH + 16 * kk + (q & 1) * 8);
+                    mma_bf16_16816(acc[2 * np], ah[kk], b[0], b[1]);
+                    mma_bf16_16816(acc[2 * np + 1], ah[kk], b[2], b[3]);
+                }
+        };
+        hidden(W2s);
+        to_frags_ordered(b2s);
+        hidden(W3s);
+        to_frags_ordered(b3s);
+        float o[2][4];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) o[j][e] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            uint32_t b[4];
+            ldsm_x4(b, W4s + (r8 + (q >> 1) * 8) * PH + 16 * kk + (q & 1) * 8);
+            mma_bf16_16816(o[0], ah[kk], b[0], b[1]);
+            mma_bf16_16816(o[1], ah[kk], b[2], b[3]);
+        }
+        // ---- network output y (rows g, g+8; cols 2t.. and 8+2t..) to smem
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int col = 8 * j + 2 * t + e;
+                    if (col < kOutRaw) ys[(g + 8 * h) * 10 + col] = o[j][2 * h + e] + b4s[col];
+                }
+        __syncwarp();
+        // ---- projection, residual, decision (one lane per instance)
+        bool fail = false;
+        const int64_t i = base + lane;
+        if (lane < 16 && i < a.n) {
+            float xf[9], w[9], dkf[kKinEdges], dkb[kKinEdges], z[9];
+            double xd[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                xd[k] = a.st[k * a.stride + i];
+                xf[k] = (float)xd[k];
+            }
+            const float vf = (float)a.v[a.ni[i]];
+            kin_rates_f(K, vf, dtf, dkf, dkb);
+            dtAx_f(dkf, dkb, xf, z);
+            const float s = a.scaled ? l1_9(z) : 1.0f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) w[k] = xf[k] + s * ys[lane * 10 + k];
+            project_simplex9(w);
+            dtAx_f(dkf, dkb, w, z);
+            float rn = 0.f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) rn += fabsf(w[k] - xf[k] - z[k]);
+            fail = !(rn <= a.tol);
+            if (!fail) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) a.st[k * a.stride + i] = (double)w[k];
+            }
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, fail);
+        if (mask) {
+            int pos = 0;
+            if (lane == 0) {
+                pos = atomicAdd(a.fb_count, __popc(mask));
+                atomicAdd(a.fb_total, (unsigned long long)__popc(mask));
+            }
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (fail) a.fb_list[pos + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_surrogate_step(const SurArgs& a, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_surrogate_step,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kSmemTotal);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int sms = 148;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t groups = (a.n + 15) / 16;
+    int64_t grid = std::min<int64_t>((int64_t)sms * 2, (groups + kWarps - 1) / kWarps);
+    if (grid < 1) grid = 1;
+    k_surrogate_step<<<(int)grid, kWarps * 32, kSmemTotal, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- training pairs
+
+__global__ void k_make_pairs(const Kin9D* __restrict__ kd, int64_t n,
+                             const double* __restrict__ v, const double* __restrict__ dt,
+                             const double* __restrict__ x, const double* __restrict__ y,
+                             int64_t stride, int scaled, float* X, float* T) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float xf[9], dkf[kKinEdges], dkb[kKinEdges], z[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) xf[k] = (float)x[k * stride + i];
+    const float vf = (float)v[i], dtf = (float)dt[i];
+#pragma unroll
+    for (int f = 0; f < kInRaw; ++f) X[i * kInRaw + f] = sur_feature(f, vf, dtf, xf);
+    kin_rates_f(*kd, vf, dtf, dkf, dkb);
+    dtAx_f(dkf, dkb, xf, z);
+    const float s = scaled ? l1_9(z) : 1.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const double inc = y[k * stride + i] - x[k * stride + i];
+        T[i * kOutRaw + k] = s > 0.f ? (float)(inc / (double)s) : 0.f;
+    }
+}
+
+void launch_make_pairs(const Kin9D* kd, int64_t n, const double* v, const double* dt,
+                       const double* x, const double* y, int64_t stride, int scaled,
+                       float* X, float* T, cudaStream_t s) {
+    if (n == 0) return;
+    k_make_pairs<<<(int)((n + 127) / 128), 128, 0, s>>>(kd, n, v, dt, x, y, stride, scaled, X, T);
+}
+
+}  // namespace nmodl

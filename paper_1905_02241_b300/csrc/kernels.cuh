@@ -49,13 +49,14 @@ struct KinCounters {
     unsigned long long nonconv;   // instances that hit the iteration cap
     int32_t max_iter_seen;
     int32_t pad;
+    unsigned long long fallback;  // surrogate instances sent to Newton
 };
 void launch_kin9_init(const Kin9D* kd, int64_t n, const int32_t* ni,
                       const double* v, double* st, int64_t stride, int32_t* err,
                       cudaStream_t s);
 void launch_kin9_state(int prec, const Kin9D* kd, int64_t n, const int32_t* ni,
                        const double* v, double* st, int64_t stride, double dt,
-                       double tol, int max_iter, int ir_max,
+                       const double* dt_arr, double tol, int max_iter, int ir_max,
                        const int32_t* list, int64_t n_list_max,
                        const int32_t* n_list_dev, KinCounters* cnt,
                        int32_t* err, cudaStream_t s);

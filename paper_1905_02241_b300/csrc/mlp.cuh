@@ -1,0 +1,94 @@
+// mlp.cuh -- shapes, parameter layout and launch interfaces of the kinetic
+// surrogate MLP (11 -> 128 -> 128 -> 128 -> 9, SiLU).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "mma_bf16.cuh"
+#include "nmodl_internal.cuh"
+
+namespace nmodl {
+
+constexpr int kInRaw = 11, kIn = 16;    // v_n, dt_n, x0..x8 (padded to 16)
+constexpr int kHid = 128;
+constexpr int kOutRaw = 9, kOut = 16;   // increments of the 9 states (padded)
+
+// FP32 master parameters, padded, in this order:
+//   W1 [128][16], b1 [128], W2 [128][128], b2 [128], W3 [128][128], b3 [128],
+//   W4 [16][128], b4 [16]
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kHid * kIn;
+constexpr int kOffW2 = kOffB1 + kHid;
+constexpr int kOffB2 = kOffW2 + kHid * kHid;
+constexpr int kOffW3 = kOffB2 + kHid;
+constexpr int kOffB3 = kOffW3 + kHid * kHid;
+constexpr int kOffW4 = kOffB3 + kHid;
+constexpr int kOffB4 = kOffW4 + kOut * kHid;
+constexpr int kParamsPadded = kOffB4 + kOut;
+// bf16 copies of the weight matrices only: W1 | W2 | W3 | W4
+constexpr int kBfW1 = 0, kBfW2 = kBfW1 + kHid * kIn, kBfW3 = kBfW2 + kHid * kHid,
+              kBfW4 = kBfW3 + kHid * kHid, kBfCount = kBfW4 + kOut * kHid;
+// unpadded public layout (row-major [out][in] weights, then biases)
+constexpr int kParamsPublic = kHid * kInRaw + kHid + 2 * (kHid * kHid + kHid) +
+                              kOutRaw * kHid + kOutRaw;  // 35721
+
+// Input normalisation of (v, dt): v_n = (v + 20)/80, dt_n = (dt - 0.03125)/0.01875
+constexpr float kVShift = 20.f, kVScale = 80.f, kDtShift = 0.03125f, kDtScale = 0.01875f;
+
+enum Epi : int { kEpiPartial = 0, kEpiBiasSilu = 1, kEpiBias = 2, kEpiDsilu = 3 };
+
+struct GemmArgs {
+    const __nv_bfloat16* A;
+    int lda;
+    const __nv_bfloat16* B;
+    int ldb;
+    int M, N, K;
+    int k_per_split;
+    const float* bias;
+    float* Cf;
+    int ldc;
+    __nv_bfloat16* Ch;
+    int ldch;
+    const float* Zin;
+    int ldz;
+};
+
+void launch_gemm(int ta, int tb, int epi, const GemmArgs& g, int splits, cudaStream_t s);
+void launch_reduce_splits(const float* part, int splits, int64_t count, float* out,
+                          cudaStream_t s);
+void launch_pack_input(const float* X, int64_t n, __nv_bfloat16* H0, cudaStream_t s);
+int launch_loss_delta(const float* out, const float* T, int64_t B, __nv_bfloat16* delta,
+                      float* block_loss, cudaStream_t s);
+void launch_colsum(const __nv_bfloat16* delta, int64_t B, int N, float* part, float* out,
+                   cudaStream_t s);
+void launch_adam(float* p, const float* grad, float* m, float* v, int64_t count, float lr,
+                 float b1, float b2, float eps, int step, cudaStream_t s);
+void launch_to_bf16(const float* src, int64_t count, __nv_bfloat16* dst, cudaStream_t s);
+
+// surrogate state update (fused MLP + projection + residual + fallback list)
+struct SurArgs {
+    const __nv_bfloat16* wbf;  // kBfCount
+    const float* params;       // FP32 master (biases read from here)
+    const Kin9D* kd;
+    int64_t n;
+    const int32_t* ni;
+    const double* v;
+    double* st;
+    int64_t stride;
+    double dt;
+    float tol;                 // fallback when ||F(x_hat)||_1 > tol
+    int scaled;                // output scaled by ||dt A x||_1
+    int32_t* fb_list;
+    int32_t* fb_count;
+    unsigned long long* fb_total;
+    int32_t* err;
+};
+cudaError_t launch_surrogate_step(const SurArgs& a, cudaStream_t s);
+
+// training data: normalised inputs [n][11] and targets [n][9] from
+// (v, dt, x, y = Newton step) in FP64
+void launch_make_pairs(const Kin9D* kd, int64_t n, const double* v, const double* dt,
+                       const double* x, const double* y, int64_t stride, int scaled,
+                       float* X, float* T, cudaStream_t s);
+
+}  // namespace nmodl

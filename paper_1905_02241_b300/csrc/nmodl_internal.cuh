@@ -39,6 +39,15 @@ struct MechD {
     GateD gate[kMaxGates];
 };
 
+// Edge e of the 3x3 kinetic lattice joins state lo(e) and hi(e): edges
+// 0..5 are horizontal (3a+b, 3a+b+1), edges 6..11 vertical (k, k+3).
+__host__ __device__ constexpr int edge_lo(int e) {
+    return e < 6 ? 3 * (e / 2) + (e % 2) : e - 6;
+}
+__host__ __device__ constexpr int edge_hi(int e) {
+    return e < 6 ? edge_lo(e) + 1 : edge_lo(e) + 3;
+}
+
 struct Kin9D {
     double gbar, e;
     int32_t open, pad;

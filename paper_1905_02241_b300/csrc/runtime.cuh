@@ -1,0 +1,111 @@
+// runtime.cuh -- host-side objects of the C ABI (contexts, mechanisms,
+// fused-step plans, surrogates), shared by api.cu and api_surrogate.cu.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <memory>
+#include <vector>
+
+#include "kernels.cuh"
+
+struct nmodl_surrogate;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+inline cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+struct GraphEntry {
+    double* v;
+    double* rhs;
+    double* d;
+    double dt, cm;
+    int nsteps, clamp;
+    cudaGraphExec_t exec;
+};
+
+struct Plan {
+    std::vector<nmodl_mech*> mechs;
+    int precision = 0;
+    int64_t n_nodes = 0;
+    bool fused = false;
+    // fused form
+    int n_tiles = 0, block = 256, tile_stride = 0;
+    size_t smem = 0;
+    int32_t* d_tiles = nullptr;
+    nmodl::MechD* d_md = nullptr;
+    std::vector<GraphEntry> graphs;
+    ~Plan() {
+        for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+        cudaFree(d_tiles);
+        cudaFree(d_md);
+    }
+};
+
+struct nmodl_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    nmodl_options opt{};
+    int32_t* d_err = nullptr;
+    std::vector<std::unique_ptr<Plan>> plans;
+    int live_mechs = 0;
+};
+
+struct nmodl_mech {
+    nmodl_ctx* ctx = nullptr;
+    int type = 0;
+    int64_t n = 0, n_nodes = 0, stride = 0;
+    int n_states = 0;
+    std::vector<double> params;
+    int32_t* d_ni = nullptr;
+    double* d_states = nullptr;
+    int32_t* d_chunk = nullptr;
+    int64_t n_chunks = 0;
+    nmodl::MechD md{};
+    nmodl::MechD* d_md = nullptr;
+    nmodl::Kin9D kd{};
+    nmodl::Kin9D* d_kd = nullptr;
+    nmodl::KinCounters* d_cnt = nullptr;
+    int64_t calls = 0;
+    // surrogate stand-in for the kinetic Newton solve (NMODL_KIN9 only)
+    nmodl_surrogate* sur = nullptr;
+    double sur_tol = 0.0;
+    int32_t* d_fb_list = nullptr;   // fallback instance list (n entries)
+    int32_t* d_fb_count = nullptr;  // its length
+    int64_t sur_calls = 0;
+};
+
+struct nmodl_surrogate {
+    nmodl_ctx* ctx = nullptr;
+    int scaled = 1;
+    int64_t max_batch = 0;
+    int step = 0;
+    float* params = nullptr;          // FP32 master, padded layout
+    __nv_bfloat16* wbf = nullptr;     // bf16 weight copies
+    float *grad = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16 *H0 = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr;
+    __nv_bfloat16 *D4 = nullptr, *D3 = nullptr, *D2 = nullptr, *D1 = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *OUT = nullptr;
+    float *part = nullptr, *loss_part = nullptr, *loss = nullptr;
+    int64_t part_count = 0;
+};
+
+
+// shared helpers (api.cu)
+int nmodl_cuda_status(cudaError_t e);

@@ -286,8 +286,11 @@ def kin9_clamped(n: int, seed: int = 4, rate_seed: int = 4):
 
 def surrogate_samples(n: int, seed: int = 6, v_lo=-100.0, v_hi=60.0,
                       dt_lo=0.0125, dt_hi=0.05):
-    """(v, dt, x) training inputs: x is a 50/50 mixture of Dirichlet(1) and
-    Dirichlet(0.2) points, shape (9, n)."""
+    """(v, dt, x, lam) training inputs: x is an equal mixture of Dirichlet(1)
+    and Dirichlet(0.2) points, shape (9, n); lam (n,) is 0 for two thirds
+    of the samples and 1 - 10^U[-5, 0] for the rest (the weight with which
+    the consumer pulls those samples towards the stationary distribution at
+    their v, i.e. states near the end of a relaxation)."""
     s = Stream(seed, 601)
     v = s.uniform(n, v_lo, v_hi)
     dt = s.uniform(n, dt_lo, dt_hi)
@@ -295,7 +298,9 @@ def surrogate_samples(n: int, seed: int = 6, v_lo=-100.0, v_hi=60.0,
     x = np.concatenate([Stream(seed, 602).dirichlet(n1, 9, 1.0),
                         Stream(seed, 603).dirichlet(n - n1, 9, 0.2)], axis=1)
     perm = np.argsort(Stream(seed, 604).u64(n), kind="stable")
-    return v, dt, np.ascontiguousarray(x[:, perm])
+    lam = np.where(Stream(seed, 605).uniform(n) < 1.0 / 3.0,
+                   1.0 - 10.0 ** Stream(seed, 606).uniform(n, -5.0, 0.0), 0.0)
+    return v, dt, np.ascontiguousarray(x[:, perm]), lam
 
 
 def mlp_init(seed: int, widths=(11, 128, 128, 128, 9), out_scale: float = 0.1):

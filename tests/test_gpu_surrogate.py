@@ -1,0 +1,205 @@
+"""GPU tests of the kinetic surrogate: the BF16 tensor-core MLP forward and
+gradients against the FP64 CPU oracle (and against an emulation of the BF16
+rounding points), training, the residual-gated fallback to Newton and the
+gain of a trained network over the plain Newton solve."""
+import numpy as np
+import pytest
+
+from paper_1905_02241_b300 import workloads as W
+from gpu_helpers import make_mechs, state_err, to_dev
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_1905_02241_b300 import surrogate
+    return surrogate
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1905_02241_b300.api import Context
+    c = Context(0)
+    yield c
+
+
+def _bf16(a):
+    """Round float32 values to bfloat16 (nearest even), returned as float64."""
+    a = np.asarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _silu32(z):
+    z = z.astype(np.float32)
+    return (z / (np.float32(1) + np.exp(-z))).astype(np.float64)
+
+
+def _emulate(Ws, bs, X):
+    """Forward pass with the GPU's rounding points: bf16 inputs, weights and
+    hidden activations; FP32 accumulation emulated in FP64."""
+    h = _bf16(X.T)                      # (11, B)
+    for li, (Wl, bl) in enumerate(zip(Ws, bs)):
+        z = _bf16(Wl.astype(np.float32)) @ h + bl.astype(np.float32)[:, None]
+        z = z.astype(np.float32).astype(np.float64)
+        h = _bf16(_silu32(z)) if li < 3 else z
+    return h
+
+
+def _inputs(orc, n, seed):
+    v, dt, x, _ = W.surrogate_samples(n, seed)
+    return orc.surrogate_inputs(v, dt, x).T.astype(np.float32)   # (n, 11)
+
+
+def test_forward_matches_oracle_and_bf16_emulation(S, ctx, orc):
+    Ws, bs = W.mlp_init(3, out_scale=1.0)
+    rng = np.random.default_rng(1)
+    bs = [rng.normal(scale=0.1, size=b.shape) for b in bs]
+    sur = S.Surrogate(ctx, max_batch=4096, weights=S.Surrogate.pack(Ws, bs))
+    X = _inputs(orc, 1000, 3)
+    Y = sur.forward(to_dev(X)).cpu().numpy().T            # (9, n)
+    ref, _ = orc.mlp_forward(Ws, bs, X.T.astype(np.float64))
+    emu = _emulate(Ws, bs, X)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(Y - emu)) <= 2e-5 * scale, np.max(np.abs(Y - emu)) / scale
+    rel = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
+    print(f"forward: rel L2 vs FP64 oracle {rel:.2e}, vs bf16 emulation "
+          f"{np.max(np.abs(Y - emu)) / scale:.2e}")
+    assert rel <= 2e-2
+    sur.close()
+
+
+def test_gradients_vs_oracle(S, ctx, orc):
+    Ws, bs = W.mlp_init(5, out_scale=1.0)
+    sur = S.Surrogate(ctx, max_batch=1024, weights=S.Surrogate.pack(Ws, bs))
+    n = 512
+    X = _inputs(orc, n, 4)
+    T = np.sin(np.arange(9 * n)).reshape(n, 9).astype(np.float32) * 0.3
+    loss, g = sur.loss_grad(to_dev(X), to_dev(T))
+    l_ref, gW, gb = orc.mlp_loss_grad(Ws, bs, X.T.astype(np.float64),
+                                      T.T.astype(np.float64))
+    assert abs(loss - l_ref) <= 2e-2 * l_ref
+    gWg, gbg = S.Surrogate.unpack(g)
+    for li in range(4):
+        for a, b in ((gWg[li], gW[li]), (gbg[li], gb[li])):
+            cos = float(np.sum(a * b) / (np.linalg.norm(a) * np.linalg.norm(b)))
+            rel = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+            assert cos >= 0.999 and rel <= 2e-2, (li, cos, rel)
+    sur.close()
+
+
+def test_weights_roundtrip(S, ctx):
+    Ws, bs = W.mlp_init(9)
+    w = S.Surrogate.pack(Ws, bs)
+    sur = S.Surrogate(ctx, max_batch=256)
+    sur.set_weights(w)
+    np.testing.assert_array_equal(sur.get_weights(), w)
+    sur.close()
+
+
+def test_training_reduces_loss(S, ctx):
+    p = W.kin9_params(W.Stream(4, 401))
+    sur = S.Surrogate(ctx, max_batch=4096)
+    Ws, bs = W.mlp_init(11)
+    sur.set_weights(S.Surrogate.pack(Ws, bs))
+    X, T = S.make_training_pairs(ctx, sur, p, 65536, seed=12)
+    losses = sur.fit(X, T, epochs=6, batch=4096, lr=2e-3)
+    print("training losses per epoch", losses)
+    assert losses[-1] < losses[0] / 3
+    sur.close()
+
+
+def _kin_setup(ctx, n, seed=4):
+    wl = W.kin9_clamped(n, seed=seed)
+    (m,) = make_mechs(ctx, wl)
+    m.set_states(to_dev(wl["x0"]))
+    return wl, m
+
+
+def test_untrained_surrogate_falls_back_to_newton(S, ctx, orc):
+    wl, m = _kin_setup(ctx, 3001)
+    sur = S.Surrogate(ctx, max_batch=256)                 # zero weights: x_hat = x
+    S.attach(m, sur, 1e-4)
+    m.state(0.025, to_dev(wl["v0"]))
+    spec = wl["mechs"][0]
+    ref = orc.mech_state(spec["type"], spec["params"], spec["node_index"], wl["v0"],
+                         wl["x0"], 0.025)
+    assert state_err(m.states().cpu().numpy(), ref) <= 1e-12
+    st = m.stats()
+    assert st["fallback"] == 3001 and st["surrogate_calls"] == 1
+    assert ctx.sync() == 0
+    S.attach(m, None)
+    sur.close()
+
+
+@pytest.fixture(scope="module")
+def trained(S, ctx):
+    p = W.kin9_params(W.Stream(4, 401))
+    sur = S.Surrogate(ctx, max_batch=8192)
+    Ws, bs = W.mlp_init(7)
+    sur.set_weights(S.Surrogate.pack(Ws, bs))
+    X, T = S.make_training_pairs(ctx, sur, p, 1 << 21, seed=13)
+    losses = sur.fit(X, T, epochs=8, batch=8192, lr=2e-3)
+    print("trained surrogate, epoch losses", losses)
+    yield sur
+    sur.close()
+
+
+def test_surrogate_error_bound_and_oracle(S, ctx, orc, trained):
+    """Every instance ends within ||F||_1 <= 1e-4 of the exact implicit Euler
+    step (P8); instances the surrogate kept match the oracle's surrogate."""
+    wl, m = _kin_setup(ctx, 4096)
+    spec = wl["mechs"][0]
+    v = to_dev(wl["v0"])
+    x = wl["x0"]
+    # relax for a few Newton steps so that part of the population is slow
+    for _ in range(20):
+        m.state(0.025, v)
+        x = orc.mech_state(spec["type"], spec["params"], spec["node_index"], wl["v0"],
+                           x, 0.025)
+    m.set_states(to_dev(x))
+    S.attach(m, trained, 1e-4)
+    m.state(0.025, v)
+    got = m.states().cpu().numpy()
+    exact = orc.mech_state(spec["type"], spec["params"], spec["node_index"], wl["v0"],
+                           x, 0.025)
+    err1 = np.sum(np.abs(got - exact), axis=0)
+    fb = m.stats()["fallback"]
+    print(f"one surrogate step: fallback {fb}/4096, max L1 error {err1.max():.2e}")
+    assert err1.max() <= 1e-4 * (1 + 1e-3) + 1e-6
+    kept = err1 > 1e-12
+    assert kept.sum() > 0
+    Ws, bs = S.Surrogate.unpack(trained.get_weights())
+    idx = np.nonzero(kept)[0][:200]
+    pred = orc.surrogate_step(Ws, bs, wl["v0"][idx], 0.025, x[:, idx], spec["params"])
+    # BF16 network vs FP64 network: the difference is bounded by the scale
+    # of the step; both sit within the residual bound of the exact step
+    assert np.max(np.sum(np.abs(got[:, idx] - pred), axis=0)) <= 5e-4
+    S.attach(m, None)
+    assert ctx.sync() == 0
+
+
+def test_surrogate_gain_over_newton(S, ctx, orc, trained):
+    """What the trained network gains: the share of Newton solves it replaces
+    over a 200-step relaxation, at a final error within the 1e-4 bound per
+    step (measured against the FP64 Newton trajectory)."""
+    n = 20000
+    wl, m = _kin_setup(ctx, n, seed=5)
+    wl2, m_ref = _kin_setup(ctx, n, seed=5)
+    v = to_dev(wl["v0"])
+    S.attach(m, trained, 1e-4)
+    for _ in range(200):
+        m.state(0.025, v)
+        m_ref.state(0.025, v)
+    st = m.stats()
+    rate = st["fallback"] / (200 * n)
+    err = np.sum(np.abs(m.states().cpu().numpy() - m_ref.states().cpu().numpy()), axis=0)
+    print(f"200 steps: fallback rate {rate:.3f}, Newton solves avoided {1 - rate:.3f}, "
+          f"max L1 error vs Newton {err.max():.2e}")
+    assert rate < 0.5
+    assert err.max() <= 200 * 1e-4
+    S.attach(m, None)
+    assert ctx.sync() == 0

@@ -408,7 +408,7 @@ def test_p8_inverse_is_column_stochastic(orc):
 
 def test_p9_mlp_gradients_vs_central_differences(orc):
     Ws, bs = W.mlp_init(3, widths=(11, 6, 5, 4, 9), out_scale=1.0)
-    v, dt, x = W.surrogate_samples(5, seed=8)
+    v, dt, x, _ = W.surrogate_samples(5, seed=8)
     X = orc.surrogate_inputs(v, dt, x)
     T = np.sin(np.arange(45)).reshape(9, 5) * 0.1
     loss, gW, gb = orc.mlp_loss_grad(Ws, bs, X, T)

@@ -332,19 +332,23 @@ def simplex_project(y):
 def surrogate_step(Ws, bs, v, dt, x, params=None):
     """Projected surrogate prediction of the implicit Euler step, (9, batch).
 
-    With the kinetic parameter block `params` the network output is scaled
-    by s = ||dt A(v) x||_1 (the exact increment is J^-1 (dt A x) and
-    ||J^-1||_1 = 1, so the scaled target has unit size); without it the
+    Scaled form (kinetic parameter block `params` given): with
+    z = dt A(v) x and s = ||z||_1 the network sees (v_n, dt_n, z/s) and its
+    output y gives the increment s*y; the exact increment is J^-1 z with
+    ||J^-1||_1 = 1, so the target J^-1 z / s is a smooth function of the
+    inputs.  Raw form (params None): the network sees (v_n, dt_n, x) and its
     output is the increment itself."""
     x = np.asarray(x, dtype=np.float64).reshape(9, -1)
     v = np.atleast_1d(np.asarray(v, dtype=np.float64))
-    X = surrogate_inputs(v, dt, x)
-    out, _ = mlp_forward(Ws, bs, X)
-    if params is not None:
-        s = np.array([np.sum(np.abs(dt * (kin9_matrix(params, v[c]) @ x[:, c])))
-                      for c in range(x.shape[1])])
-        out = out * s[None, :]
-    return simplex_project(x + out)
+    if params is None:
+        out, _ = mlp_forward(Ws, bs, surrogate_inputs(v, dt, x))
+        return simplex_project(x + out)
+    z = np.stack([dt * (kin9_matrix(params, v[c]) @ x[:, c]) for c in range(x.shape[1])],
+                 axis=1)
+    s = np.sum(np.abs(z), axis=0)
+    zn = np.where(s > 0, z / np.where(s > 0, s, 1.0), 0.0)
+    out, _ = mlp_forward(Ws, bs, surrogate_inputs(v, dt, zn))
+    return simplex_project(x + out * s[None, :])
 
 
 def kin9_residual(params, v, dt, x_old, y):

@@ -1,11 +1,14 @@
 // k_surrogate.cu -- learned stand-in for the kinetic Newton solve.
 //
 // One implicit Euler step of the 9-state scheme has the exact increment
-// dx* = J^-1 (dt A(v) x) with J = I - dt A column-stochastic, so
-// ||dx*||_1 <= s = ||dt A(v) x||_1.  The MLP (inputs v_n, dt_n, x; 3 hidden
-// layers of 128, SiLU; 9 outputs y) predicts dx = s * y (or dx = y when the
-// scaled form is off); x_hat = P(x + dx) with P the Euclidean projection onto
-// the probability simplex (Held, Wolfe & Crowder 1974).  The implicit Euler
+// dx* = J^-1 z with z = dt A(v) x and J = I - dt A column-stochastic, so
+// ||dx*||_1 <= s = ||z||_1.  In the scaled form the MLP (3 hidden layers of
+// 128, SiLU) sees v_n, dt_n and the 9 states as the normalised explicit
+// increment z/s, and its 9 outputs y give dx = s * y: the target J^-1 z / s
+// is then a smooth (bilinear) function of its inputs.  In the raw form the
+// network sees the states x and predicts dx = y directly.
+// x_hat = P(x + dx) with P the Euclidean projection onto the probability
+// simplex (Held, Wolfe & Crowder 1974).  The implicit Euler
 // residual F(x_hat) = x_hat - x - dt A x_hat decides: ||F||_1 <= tol keeps
 // x_hat (then ||x_hat - x*||_1 <= ||J^-1||_1 ||F||_1 = ||F||_1), otherwise the
 // instance goes on a fallback list for the Newton kernel.
@@ -26,17 +29,10 @@ constexpr int P1 = kIn + 8;    // W1 row pitch (elements)
 constexpr int PH = kHid + 8;   // W2, W3, W4 row pitch
 constexpr int kSmemW = (kHid * P1 + 2 * kHid * PH + kOut * PH) * 2;
 constexpr int kSmemB = (3 * kHid + kOut) * 4;
-constexpr int kSmemY = kWarps * 16 * 10 * 4;
+constexpr int kWarpFloats = 16 * 16 + 16 * 24 + 16 * 9 + 16 + 16 * 9;
+constexpr int kSmemY = kWarps * kWarpFloats * 4;
 constexpr int kSmemTotal = kSmemW + kSmemB + kSmemY;
 }  // namespace
-
-// Normalised network input feature f of an instance (f >= 11: padding 0).
-__device__ __forceinline__ float sur_feature(int f, float vf, float dtf, const float* xf) {
-    if (f == 0) return (vf + kVShift) * (1.0f / kVScale);
-    if (f == 1) return (dtf - kDtShift) * (1.0f / kDtScale);
-    if (f < kInRaw) return xf[f - 2];
-    return 0.0f;
-}
 
 // FP32 rates dt*k of the 24 transitions and (dt A) x for a state x.
 __device__ __forceinline__ void kin_rates_f(const Kin9D& K, float vf, float dtf,
@@ -65,6 +61,25 @@ __device__ __forceinline__ float l1_9(const float (&z)[9]) {
     float s = 0.f;
 #pragma unroll
     for (int a = 0; a < 9; ++a) s += fabsf(z[a]);
+    return s;
+}
+
+// Network inputs (11) and output scale s of one instance: v_n, dt_n, then
+// z/s (scaled form; zero when s == 0) or x (raw form).
+__device__ __forceinline__ float sur_inputs(int scaled, float vf, float dtf,
+                                            const float (&xf)[9], const float (&z)[9],
+                                            float* feat) {
+    feat[0] = (vf + kVShift) * (1.0f / kVScale);
+    feat[1] = (dtf - kDtShift) * (1.0f / kDtScale);
+    if (!scaled) {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) feat[2 + a] = xf[a];
+        return 1.0f;
+    }
+    const float s = l1_9(z);
+    const float inv = s > 0.f ? 1.0f / s : 0.f;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) feat[2 + a] = z[a] * inv;
     return s;
 }
 
@@ -103,10 +118,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
     float* b2s = b1s + kHid;
     float* b3s = b2s + kHid;
     float* b4s = b3s + kHid;
-    float* ys_all = b4s + kOut;
+    float* warp_all = b4s + kOut;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // ---- stage weights (16-byte rows chunks) and biases
+    // ---- stage weights (16-byte row chunks) and biases
     auto stage = [&](const __nv_bfloat16* src, __nv_bfloat16* dst, int rows, int cols, int pitch) {
         const int ch = cols / 8;
         for (int c = tid; c < rows * ch; c += blockDim.x) {
@@ -130,33 +145,51 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
     const Kin9D& K = *a.kd;
     const float dtf = (float)a.dt;
     const int g = lane >> 2, t = lane & 3, q = lane >> 3, r8 = lane & 7;
-    float* ys = ys_all + warp * 16 * 10;
+    // per-warp staging: features [16][16], rates [16][24], x [16][9],
+    // scale [16], outputs [16][9]
+    float* wsm = warp_all + warp * kWarpFloats;
+    float* feat = wsm;
+    float* rates = feat + 16 * 16;
+    float* xs = rates + 16 * 2 * kKinEdges;
+    float* ss = xs + 16 * 9;
+    float* ys = ss + 16;
     const int64_t stride_w = (int64_t)gridDim.x * kWarps * 16;
 
     for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 16; base < a.n;
          base += stride_w) {
-        // ---- layer 1 input fragment: rows base+g and base+g+8
-        uint32_t afr[4];
-        {
-            float f[2][4];
+        // ---- per instance (lanes 0..15): rates, dt A x, scale, inputs
+        if (lane < 16) {
+            const int64_t i = base + lane;
+            float* f = feat + lane * 16;
+            if (i < a.n) {
+                float xf[9], dkf[kKinEdges], dkb[kKinEdges], z[9];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t i = base + g + 8 * h;
-                float xf[9];
-                float vf = 0.f;
-                const bool ok = i < a.n;
+                for (int k = 0; k < 9; ++k) xf[k] = (float)a.st[k * a.stride + i];
+                const float vf = (float)a.v[a.ni[i]];
+                kin_rates_f(K, vf, dtf, dkf, dkb);
+                dtAx_f(dkf, dkb, xf, z);
+                ss[lane] = sur_inputs(a.scaled, vf, dtf, xf, z, f);
 #pragma unroll
-                for (int k = 0; k < 9; ++k) xf[k] = ok ? (float)a.st[k * a.stride + i] : 0.f;
-                if (ok) vf = (float)a.v[a.ni[i]];
-                const int cols[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
+                for (int e = 0; e < kKinEdges; ++e) {
+                    rates[lane * 24 + e] = dkf[e];
+                    rates[lane * 24 + 12 + e] = dkb[e];
+                }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) f[h][c] = ok ? sur_feature(cols[c], vf, dtf, xf) : 0.f;
+                for (int k = 0; k < 9; ++k) xs[lane * 9 + k] = xf[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < kInRaw; ++k) f[k] = 0.f;
             }
-            afr[0] = pack_bf16(f[0][0], f[0][1]);
-            afr[1] = pack_bf16(f[1][0], f[1][1]);
-            afr[2] = pack_bf16(f[0][2], f[0][3]);
-            afr[3] = pack_bf16(f[1][2], f[1][3]);
+#pragma unroll
+            for (int k = kInRaw; k < 16; ++k) f[k] = 0.f;
         }
+        __syncwarp();
+        // ---- layer 1 input fragment: rows g and g+8
+        uint32_t afr[4];
+        afr[0] = pack_bf16(feat[g * 16 + 2 * t], feat[g * 16 + 2 * t + 1]);
+        afr[1] = pack_bf16(feat[(g + 8) * 16 + 2 * t], feat[(g + 8) * 16 + 2 * t + 1]);
+        afr[2] = pack_bf16(feat[g * 16 + 2 * t + 8], feat[g * 16 + 2 * t + 9]);
+        afr[3] = pack_bf16(feat[(g + 8) * 16 + 2 * t + 8], feat[(g + 8) * 16 + 2 * t + 9]);
         float acc[16][4];
 #pragma unroll
         for (int j = 0; j < 16; ++j)
@@ -169,10 +202,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
             mma_bf16_16816(acc[2 * np], afr, b[0], b[1]);
             mma_bf16_16816(acc[2 * np + 1], afr, b[2], b[3]);
         }
+        // C fragments of output tiles 2kk and 2kk+1 are, in this order, the
+        // A fragment (a0a1, a2a3, a4a5, a6a7) of k-slice kk of the next layer
         uint32_t ah[8][4];
         auto to_frags = [&](const float* bias) {
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
+            for (int kk = 0; kk < 8; ++kk)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int j = 2 * kk + h;
@@ -181,22 +216,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
                     ah[kk][2 * h] = pack_bf16(silu_f(acc[j][0] + b0), silu_f(acc[j][1] + b1));
                     ah[kk][2 * h + 1] = pack_bf16(silu_f(acc[j][2] + b0), silu_f(acc[j][3] + b1));
                 }
-            }
         };
-        // A fragment order: a0a1 (row g, k 2t) = tile 2kk c0c1; a2a3 (row g+8)
-        // = tile 2kk c2c3; a4a5 = tile 2kk+1 c0c1; a6a7 = tile 2kk+1 c2c3.
-        auto to_frags_ordered = [&](const float* bias) {
-            to_frags(bias);
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const uint32_t x0 = ah[kk][0], x1 = ah[kk][1], x2 = ah[kk][2], x3 = ah[kk][3];
-                ah[kk][0] = x0;  // tile 2kk, row g
-                ah[kk][1] = x1;  // tile 2kk, row g+8
-                ah[kk][2] = x2;  // tile 2kk+1, row g
-                ah[kk][3] = x3;  // tile 2kk+1, row g+8
-            }
-        };
-        to_frags_ordered(b1s);
         auto hidden = [&](const __nv_bfloat16* Ws) {
 #pragma unroll
             for (int j = 0; j < 16; ++j)
@@ -212,10 +232,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
                     mma_bf16_16816(acc[2 * np + 1], ah[kk], b[2], b[3]);
                 }
         };
+        to_frags(b1s);
         hidden(W2s);
-        to_frags_ordered(b2s);
+        to_frags(b2s);
         hidden(W3s);
-        to_frags_ordered(b3s);
+        to_frags(b3s);
         float o[2][4];
 #pragma unroll
         for (int j = 0; j < 2; ++j)
@@ -228,7 +249,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
             mma_bf16_16816(o[0], ah[kk], b[0], b[1]);
             mma_bf16_16816(o[1], ah[kk], b[2], b[3]);
         }
-        // ---- network output y (rows g, g+8; cols 2t.. and 8+2t..) to smem
 #pragma unroll
         for (int j = 0; j < 2; ++j)
 #pragma unroll
@@ -236,7 +256,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int col = 8 * j + 2 * t + e;
-                    if (col < kOutRaw) ys[(g + 8 * h) * 10 + col] = o[j][2 * h + e] + b4s[col];
+                    if (col < kOutRaw) ys[(g + 8 * h) * 9 + col] = o[j][2 * h + e] + b4s[col];
                 }
         __syncwarp();
         // ---- projection, residual, decision (one lane per instance)
@@ -244,18 +264,17 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
         const int64_t i = base + lane;
         if (lane < 16 && i < a.n) {
             float xf[9], w[9], dkf[kKinEdges], dkb[kKinEdges], z[9];
-            double xd[9];
+#pragma unroll
+            for (int e = 0; e < kKinEdges; ++e) {
+                dkf[e] = rates[lane * 24 + e];
+                dkb[e] = rates[lane * 24 + 12 + e];
+            }
+            const float s = ss[lane];
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
-                xd[k] = a.st[k * a.stride + i];
-                xf[k] = (float)xd[k];
+                xf[k] = xs[lane * 9 + k];
+                w[k] = xf[k] + s * ys[lane * 9 + k];
             }
-            const float vf = (float)a.v[a.ni[i]];
-            kin_rates_f(K, vf, dtf, dkf, dkb);
-            dtAx_f(dkf, dkb, xf, z);
-            const float s = a.scaled ? l1_9(z) : 1.0f;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) w[k] = xf[k] + s * ys[lane * 10 + k];
             project_simplex9(w);
             dtAx_f(dkf, dkb, w, z);
             float rn = 0.f;
@@ -310,15 +329,15 @@ __global__ void k_make_pairs(const Kin9D* __restrict__ kd, int64_t n,
                              int64_t stride, int scaled, float* X, float* T) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float xf[9], dkf[kKinEdges], dkb[kKinEdges], z[9];
+    float xf[9], dkf[kKinEdges], dkb[kKinEdges], z[9], f[kInRaw];
 #pragma unroll
     for (int k = 0; k < 9; ++k) xf[k] = (float)x[k * stride + i];
     const float vf = (float)v[i], dtf = (float)dt[i];
-#pragma unroll
-    for (int f = 0; f < kInRaw; ++f) X[i * kInRaw + f] = sur_feature(f, vf, dtf, xf);
     kin_rates_f(*kd, vf, dtf, dkf, dkb);
     dtAx_f(dkf, dkb, xf, z);
-    const float s = scaled ? l1_9(z) : 1.0f;
+    const float s = sur_inputs(scaled, vf, dtf, xf, z, f);
+#pragma unroll
+    for (int k = 0; k < kInRaw; ++k) X[i * kInRaw + k] = f[k];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const double inc = y[k * stride + i] - x[k * stride + i];

@@ -164,6 +164,8 @@ def main():
     ap.add_argument("--nodes", type=int, default=2_000_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--forms", default="all",
+                    help="comma list of batched,kinetic,surrogate,mixed_errors; all; none")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -314,6 +316,18 @@ def main():
         cpu = {"value": r, "unit": "instance-steps/s", "cores": 1, "kind": "oracle",
                "sample": sample, "seconds": round(el, 2)}
 
+    plan = ctx.plan(mechs)
+    forms = None
+    if rank == 0 and world == 1 and args.forms != "none":
+        from paper_1905_02241_b300 import forms as F
+        want = (["batched", "mixed_errors", "kinetic", "surrogate"] if args.forms == "all"
+                else args.forms.split(","))
+        forms = {}
+        for name in want:
+            t0 = time.perf_counter()
+            forms[name] = getattr(F, name)(dev)
+            forms[name]["seconds"] = round(time.perf_counter() - t0, 1)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "instance-steps/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -323,7 +337,8 @@ def main():
                 "data": "synthetic", "config": dict(config, instances=ninst,
                                                     parallelism=f"replicas x{world}"),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": gpu_launches, "clocks": clk}
+                "gpu_launches": gpu_launches, "clocks": clk, "plan": plan,
+                "forms": forms}
         print(json.dumps(line))
     for m in mechs:
         m.close()

@@ -182,6 +182,15 @@ NMODL_API int nmodl_step(nmodl_ctx *ctx, nmodl_mech *const *mechs, int n_mechs,
                double dt, double cm, double *v, double *rhs, double *d,
                int nsteps);
 
+/* Shape nmodl_step chose for this mechanism list (after a first call):
+ * out[0] fused (1) or per-mechanism launches (0), out[1] tiles, out[2]
+ * block size, out[3] dynamic shared memory per block (bytes), out[4]
+ * persistent tile queue (1) or one block per tile (0), out[5] tile
+ * shared-memory budget.  The autotuner (options.autotune) picks these by
+ * timing candidates on a scratch copy of the first ~2M instances. */
+NMODL_API int nmodl_plan_describe(nmodl_ctx *ctx, nmodl_mech *const *mechs,
+                                  int n_mechs, int64_t *out);
+
 /* Copy state row k (n_instances doubles) out of / into the mechanism
  * (out/in: host or device).  Checkpoint and resume use these. */
 NMODL_API int nmodl_get_state(nmodl_mech *m, int k, double *out);

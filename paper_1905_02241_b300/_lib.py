@@ -88,6 +88,7 @@ _SIGS = {
     "nmodl_surrogate_make_pairs": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "nmodl_kin9_solve": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _i64]),
     "nmodl_mech_attach_surrogate": (_i32, [_vp, _vp, _d]),
+    "nmodl_plan_describe": (_i32, [_vp, _vp, _i32, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -272,3 +273,12 @@ def nmodl_kin9_solve(kin: int, n: int, v_ptr: int, dt_ptr: int, x_ptr: int, y_pt
 def nmodl_mech_attach_surrogate(m: int, s: int, tol: float) -> None:
     _check(lib.nmodl_mech_attach_surrogate(m, s or None, float(tol)),
            "nmodl_mech_attach_surrogate")
+
+
+def nmodl_plan_describe(ctx: int, mechs) -> dict:
+    arr = (_vp * len(mechs))(*mechs)
+    out = (ctypes.c_int64 * 6)()
+    _check(lib.nmodl_plan_describe(ctx, ctypes.cast(arr, _vp), len(mechs),
+                                   ctypes.cast(out, _vp)), "nmodl_plan_describe")
+    return dict(fused=bool(out[0]), tiles=int(out[1]), block=int(out[2]),
+                smem=int(out[3]), persistent=bool(out[4]), tile_budget=int(out[5]))

@@ -70,6 +70,9 @@ class Context:
                         _dptr(d, device=self.device), nsteps)
         self.leave()
 
+    def plan(self, mechs) -> dict:
+        return _lib.nmodl_plan_describe(self.handle, [m.handle for m in mechs])
+
     def close(self) -> None:
         if self.handle:
             _lib.nmodl_ctx_destroy(self.handle)

@@ -17,6 +17,17 @@ namespace nmodl {
 cudaError_t enqueue_surrogate_state(nmodl_mech* m, double dt, const double* v);
 }  // namespace nmodl
 
+// Drop the cached step plans (and their graphs) that involve mechanism m.
+void nmodl_invalidate_plans(nmodl_ctx* c, nmodl_mech* m) {
+    auto& P = c->plans;
+    P.erase(std::remove_if(P.begin(), P.end(),
+                           [m](const std::unique_ptr<Plan>& p) {
+                               return std::find(p->mechs.begin(), p->mechs.end(), m) !=
+                                      p->mechs.end();
+                           }),
+            P.end());
+}
+
 int nmodl_cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return NMODL_OK;
     if (e == cudaErrorMemoryAllocation) return NMODL_ERR_OOM;
@@ -319,13 +330,7 @@ void nmodl_mech_destroy(nmodl_mech* m) {
     nmodl_ctx* c = m->ctx;
     DeviceGuard g(c->device);
     cudaStreamSynchronize(c->stream);
-    auto& P = c->plans;
-    P.erase(std::remove_if(P.begin(), P.end(),
-                           [m](const std::unique_ptr<Plan>& p) {
-                               return std::find(p->mechs.begin(), p->mechs.end(), m) !=
-                                      p->mechs.end();
-                           }),
-            P.end());
+    nmodl_invalidate_plans(c, m);
     c->live_mechs--;
     free_mech(m);
 }
@@ -349,7 +354,6 @@ static void enqueue_state(nmodl_mech* m, double dt, const double* v) {
     const nmodl_options& o = c->opt;
     if (m->type == NMODL_KIN9 && m->sur) {
         nmodl::enqueue_surrogate_state(m, dt, v);
-        m->sur_calls++;
     } else if (m->type == NMODL_KIN9)
         launch_kin9_state(o.precision, m->d_kd, m->n, m->d_ni, v, m->d_states, m->stride,
                           dt, nullptr, o.newton_tol, o.newton_max_iter, o.ir_max, nullptr, 0,
@@ -357,7 +361,13 @@ static void enqueue_state(nmodl_mech* m, double dt, const double* v) {
     else
         launch_state_gates(o.precision, m->d_md, m->n_states, m->n, m->d_ni, v,
                            m->d_states, m->stride, dt, c->d_err, c->stream);
-    m->calls++;
+}
+
+// host-side counters of state updates (kept here, not at enqueue time, so
+// that graph replays are counted)
+static void count_states(nmodl_mech* m, int64_t k) {
+    m->calls += k;
+    if (m->type == NMODL_KIN9 && m->sur) m->sur_calls += k;
 }
 
 static void enqueue_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
@@ -372,6 +382,7 @@ int nmodl_state(nmodl_mech* m, double dt, const double* v) {
     if (!m || !(dt > 0.0) || !std::isfinite(dt) || (m->n > 0 && !v)) return NMODL_ERR_ARG;
     DeviceGuard g(m->ctx->device);
     enqueue_state(m, dt, v);
+    count_states(m, 1);
     return cuda_status(cudaGetLastError());
 }
 
@@ -432,7 +443,37 @@ static bool make_tiles(const std::vector<std::vector<int32_t>>& off, int T,
     return true;
 }
 
-static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan* p) {
+// Largest-first order of tile records (cost = gate items + instances), the
+// work list of the fused kernel.
+static void lpt_order(std::vector<int32_t>& recs, int T, const int* gates) {
+    const int stride = 2 + 2 * T;
+    const size_t n = recs.size() / stride;
+    std::vector<std::pair<int64_t, size_t>> cost(n);
+    for (size_t k = 0; k < n; ++k) {
+        int64_t c = 0;
+        for (int t = 0; t < T; ++t)
+            c += (int64_t)(gates[t] + 1) * (recs[k * stride + 3 + 2 * t] - recs[k * stride + 2 + 2 * t]);
+        cost[k] = {-c, k};
+    }
+    std::stable_sort(cost.begin(), cost.end());
+    std::vector<int32_t> out(recs.size());
+    for (size_t k = 0; k < n; ++k)
+        std::copy(recs.begin() + cost[k].second * stride,
+                  recs.begin() + (cost[k].second + 1) * stride, out.begin() + k * stride);
+    recs.swap(out);
+}
+
+struct Candidate {
+    size_t budget;
+    int block;
+    bool persistent;
+    std::vector<int32_t> recs;
+    size_t smem;
+    double ms = 0.0;
+};
+
+static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan* p,
+                      const double* v_user) {
     p->mechs.assign(mechs, mechs + n_mechs);
     p->precision = c->opt.precision;
     p->n_nodes = mechs[0]->n_nodes;
@@ -476,37 +517,167 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     cudaDeviceGetAttribute(&dev_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     const size_t stat = fused_static_smem(p->precision);
     const size_t cap = dev_smem_optin > (int)stat ? dev_smem_optin - stat : 0;
-    size_t budget = c->opt.tile_smem > 0 ? (size_t)c->opt.tile_smem : std::min<size_t>(cap, 96 * 1024);
-    budget = std::min(budget, cap);
     e = fused_prepare(p->precision, cap);
     if (e != cudaSuccess) return cuda_status(e);
-    std::vector<int32_t> recs;
-    size_t max_smem = 0;
-    if (!make_tiles(off, T, gates, p->n_nodes, G, budget, recs, max_smem)) return NMODL_OK;
     p->tile_stride = 2 + 2 * T;
-    p->n_tiles = (int)(recs.size() / p->tile_stride);
-    p->smem = std::max<size_t>(max_smem, 16);
-    // block: enough threads for the average tile's gate items, within limits
-    int block = c->opt.block;
-    if (block == 0) {
-        size_t items = 0;
-        for (int t = 0; t < T; ++t) items += (size_t)gates[t] * mechs[t]->n;
-        const double per_tile = (double)items / std::max(1, p->n_tiles);
-        block = 128;
-        while (block < 512 && block < per_tile / 4) block *= 2;
+
+    // ---- candidate shapes
+    std::vector<size_t> budgets;
+    std::vector<int> blocks;
+    std::vector<bool> pers;
+    const bool tune = c->opt.autotune != 0;
+    if (c->opt.tile_smem > 0) budgets = {std::min<size_t>(c->opt.tile_smem, cap)};
+    else if (tune) budgets = {24 * 1024, 48 * 1024, 96 * 1024, 150 * 1024, cap};
+    else budgets = {std::min<size_t>(cap, 96 * 1024)};
+    size_t items = 0;
+    for (int t = 0; t < T; ++t) items += (size_t)gates[t] * mechs[t]->n;
+    if (c->opt.block > 0) blocks = {c->opt.block};
+    else if (tune) blocks = {128, 256, 512};
+    else blocks = {256};
+    pers = tune ? std::vector<bool>{false, true} : std::vector<bool>{false};
+
+    std::vector<Candidate> cands;
+    for (size_t b : budgets) {
+        std::vector<int32_t> recs;
+        size_t max_smem = 0;
+        if (b > cap || !make_tiles(off, T, gates, p->n_nodes, G, b, recs, max_smem)) continue;
+        lpt_order(recs, T, gates);
+        for (int blk : blocks)
+            for (bool ps : pers)
+                cands.push_back(Candidate{b, blk, ps, recs, std::max<size_t>(max_smem, 16)});
     }
-    p->block = block;
-    if ((e = dalloc(&p->d_tiles, recs.size())) != cudaSuccess) return cuda_status(e);
-    cudaMemcpy(p->d_tiles, recs.data(), recs.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if ((e = dalloc(&p->d_md, T)) != cudaSuccess) return cuda_status(e);
-    std::vector<MechD> mds(T);
-    for (int t = 0; t < T; ++t) mds[t] = mechs[t]->md;
-    cudaMemcpy(p->d_md, mds.data(), T * sizeof(MechD), cudaMemcpyHostToDevice);
+    if (cands.empty()) return NMODL_OK;  // no tile fits: generic step
+    int32_t* d_counter = nullptr;
+    if ((e = dalloc(&d_counter, 1)) != cudaSuccess) return cuda_status(e);
+    p->d_counter = d_counter;
+
+    size_t best = 0;
+    if (cands.size() > 1) {
+        // time each candidate on a scratch copy: a prefix of the network of
+        // about 2M instances, min(window, 8) steps
+        std::vector<double*> sst(T, nullptr);
+        double *sv = nullptr, *srhs = nullptr, *sd = nullptr;
+        int32_t* d_trial = nullptr;
+        bool ok = true;
+        for (int t = 0; t < T && ok; ++t) {
+            const size_t cnt = (size_t)mechs[t]->n_states * mechs[t]->stride;
+            ok = dalloc(&sst[t], cnt) == cudaSuccess &&
+                 (cnt == 0 || cudaMemcpyAsync(sst[t], mechs[t]->d_states, cnt * sizeof(double),
+                                              cudaMemcpyDeviceToDevice, c->stream) == cudaSuccess);
+        }
+        ok = ok && dalloc(&sv, p->n_nodes) == cudaSuccess && dalloc(&srhs, p->n_nodes) == cudaSuccess &&
+             dalloc(&sd, p->n_nodes) == cudaSuccess;
+        if (ok && v_user)
+            ok = cudaMemcpyAsync(sv, v_user, p->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 c->stream) == cudaSuccess;
+        else if (ok)
+            ok = cudaMemsetAsync(sv, 0, p->n_nodes * sizeof(double), c->stream) == cudaSuccess;
+        size_t max_recs = 0;
+        for (auto& cd : cands) max_recs = std::max(max_recs, cd.recs.size());
+        ok = ok && dalloc(&d_trial, max_recs) == cudaSuccess;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+        const int trial_steps = std::min(c->opt.window, 8);
+        for (size_t ci = 0; ok && ci < cands.size(); ++ci) {
+            Candidate& cd = cands[ci];
+            // prefix of the tiles in node order: re-sort the (LPT) list by n0
+            const int st = p->tile_stride;
+            const size_t nt = cd.recs.size() / st;
+            std::vector<size_t> idx(nt);
+            for (size_t k = 0; k < nt; ++k) idx[k] = k;
+            std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+                return cd.recs[a * st] < cd.recs[b * st];
+            });
+            std::vector<int32_t> sub;
+            int64_t inst = 0;
+            for (size_t k : idx) {
+                if (inst > 2000000) break;
+                for (int tt = 0; tt < T; ++tt)
+                    inst += cd.recs[k * st + 3 + 2 * tt] - cd.recs[k * st + 2 + 2 * tt];
+                sub.insert(sub.end(), cd.recs.begin() + k * st, cd.recs.begin() + (k + 1) * st);
+            }
+            lpt_order(sub, T, gates);
+            cudaMemcpyAsync(d_trial, sub.data(), sub.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, c->stream);
+            FusedArgs a{};
+            a.md = nullptr;
+            a.n_types = T;
+            for (int t = 0; t < T; ++t) {
+                a.n_gates[t] = mechs[t]->n_states;
+                a.states[t] = sst[t];
+                a.stride[t] = mechs[t]->stride;
+                a.ni[t] = mechs[t]->d_ni;
+            }
+            a.tiles = d_trial;
+            a.tile_stride = st;
+            a.n_tiles = (int)(sub.size() / st);
+            a.tile_counter = cd.persistent ? d_counter : nullptr;
+            a.nsteps = trial_steps;
+            a.clamp_v = c->opt.clamp_v;
+            a.v = sv;
+            a.rhs = srhs;
+            a.d = sd;
+            a.dt = 0.025;
+            a.cm = 1.0;
+            a.err = nullptr;
+            // descriptors
+            if (!p->d_md) {
+                if (dalloc(&p->d_md, T) != cudaSuccess) { ok = false; break; }
+                std::vector<MechD> mds(T);
+                for (int t = 0; t < T; ++t) mds[t] = mechs[t]->md;
+                cudaMemcpy(p->d_md, mds.data(), T * sizeof(MechD), cudaMemcpyHostToDevice);
+            }
+            a.md = p->d_md;
+            double best_ms = 1e30;
+            for (int rep = 0; rep < 2 && ok; ++rep) {
+                if (cd.persistent) cudaMemsetAsync(d_counter, 0, sizeof(int32_t), c->stream);
+                cudaEventRecord(e0, c->stream);
+                const int grid = cd.persistent
+                                     ? fused_resident_grid(p->precision, a.n_tiles, cd.block, cd.smem)
+                                     : a.n_tiles;
+                ok = launch_fused(p->precision, a, grid, cd.block, cd.smem, c->stream) ==
+                     cudaSuccess;
+                cudaEventRecord(e1, c->stream);
+                ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best_ms = std::min(best_ms, (double)ms);
+            }
+            cd.ms = best_ms / std::max<int64_t>(1, inst);
+            if (cd.ms < cands[best].ms || ci == 0) best = ci;
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        for (double* q : sst) cudaFree(q);
+        cudaFree(sv);
+        cudaFree(srhs);
+        cudaFree(sd);
+        cudaFree(d_trial);
+        cudaGetLastError();
+        if (!ok) best = 0;
+    }
+    Candidate& ch = cands[best];
+    p->budget = ch.budget;
+    p->block = ch.block;
+    p->persistent = ch.persistent;
+    p->smem = ch.smem;
+    p->n_tiles = (int)(ch.recs.size() / p->tile_stride);
+    p->grid = ch.persistent ? fused_resident_grid(p->precision, p->n_tiles, ch.block, ch.smem)
+                            : p->n_tiles;
+    if ((e = dalloc(&p->d_tiles, ch.recs.size())) != cudaSuccess) return cuda_status(e);
+    cudaMemcpy(p->d_tiles, ch.recs.data(), ch.recs.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (!p->d_md) {
+        if ((e = dalloc(&p->d_md, T)) != cudaSuccess) return cuda_status(e);
+        std::vector<MechD> mds(T);
+        for (int t = 0; t < T; ++t) mds[t] = mechs[t]->md;
+        cudaMemcpy(p->d_md, mds.data(), T * sizeof(MechD), cudaMemcpyHostToDevice);
+    }
     p->fused = true;
     return NMODL_OK;
 }
 
-static Plan* get_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, int* rc) {
+static Plan* get_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, const double* v,
+                      int* rc) {
     for (auto& p : c->plans) {
         if ((int)p->mechs.size() == n_mechs && p->precision == c->opt.precision &&
             std::equal(p->mechs.begin(), p->mechs.end(), mechs))
@@ -517,7 +688,7 @@ static Plan* get_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, int* 
         *rc = NMODL_ERR_OOM;
         return nullptr;
     }
-    *rc = build_plan(c, mechs, n_mechs, p.get());
+    *rc = build_plan(c, mechs, n_mechs, p.get(), v);
     if (*rc) return nullptr;
     c->plans.push_back(std::move(p));
     return c->plans.back().get();
@@ -537,6 +708,8 @@ static FusedArgs fused_args(nmodl_ctx* c, Plan* p, double dt, double cm, double*
     }
     a.tiles = p->d_tiles;
     a.tile_stride = p->tile_stride;
+    a.n_tiles = p->n_tiles;
+    a.tile_counter = p->persistent ? p->d_counter : nullptr;
     a.nsteps = nsteps;
     a.clamp_v = c->opt.clamp_v;
     a.v = v;
@@ -568,7 +741,11 @@ static cudaError_t run_window(nmodl_ctx* c, Plan* p, nmodl_mech* const* mechs, i
     auto direct = [&]() -> cudaError_t {
         if (p->fused) {
             FusedArgs a = fused_args(c, p, dt, cm, v, rhs, d, w);
-            return launch_fused(p->precision, a, p->n_tiles, p->block, p->smem, c->stream);
+            if (p->persistent) {
+                cudaError_t me = cudaMemsetAsync(p->d_counter, 0, sizeof(int32_t), c->stream);
+                if (me != cudaSuccess) return me;
+            }
+            return launch_fused(p->precision, a, p->grid, p->block, p->smem, c->stream);
         }
         return enqueue_generic_steps(c, mechs, n_mechs, dt, cm, v, rhs, d, w, p->n_nodes);
     };
@@ -611,12 +788,9 @@ int nmodl_step(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, double dt, d
     if (!v || !rhs || !d) return NMODL_ERR_ARG;
     DeviceGuard g(c->device);
     int rc = NMODL_OK;
-    Plan* p = get_plan(c, mechs, n_mechs, &rc);
+    Plan* p = get_plan(c, mechs, n_mechs, v, &rc);
     if (!p) return rc;
-    if (p->fused) {
-        // the fused kernel runs cur + state per step; count the state calls
-        for (int i = 0; i < n_mechs; ++i) mechs[i]->calls += nsteps;
-    }
+    for (int i = 0; i < n_mechs; ++i) count_states(mechs[i], nsteps);
     const int W = c->opt.window;
     for (int s = 0; s < nsteps; s += W) {
         const int w = std::min(W, nsteps - s);
@@ -624,6 +798,23 @@ int nmodl_step(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, double dt, d
         if (e != cudaSuccess) return cuda_status(e);
     }
     return NMODL_OK;
+}
+
+int nmodl_plan_describe(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, int64_t* out) {
+    if (!c || !mechs || n_mechs < 1 || !out) return NMODL_ERR_ARG;
+    for (auto& p : c->plans) {
+        if ((int)p->mechs.size() == n_mechs && p->precision == c->opt.precision &&
+            std::equal(p->mechs.begin(), p->mechs.end(), mechs)) {
+            out[0] = p->fused ? 1 : 0;
+            out[1] = p->n_tiles;
+            out[2] = p->block;
+            out[3] = (int64_t)p->smem;
+            out[4] = p->persistent ? 1 : 0;
+            out[5] = (int64_t)p->budget;
+            return NMODL_OK;
+        }
+    }
+    return NMODL_ERR_ARG;
 }
 
 int nmodl_get_state(nmodl_mech* m, int k, double* out) {

@@ -187,6 +187,7 @@ NMODL_API int nmodl_surrogate_create(nmodl_ctx* c, int64_t max_batch, const floa
         cudaMemset(s->grad, 0, sizeof(float) * kParamsPadded);
         refresh_bf16(s);
         e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) e = surrogate_prepare();
     } while (false);
     if (e != cudaSuccess) {
         free_sur(s);
@@ -313,6 +314,7 @@ NMODL_API int nmodl_mech_attach_surrogate(nmodl_mech* m, nmodl_surrogate* s, dou
     DeviceGuard dg(m->ctx->device);
     if (!s || !(tol > 0.0)) {
         m->sur = nullptr;
+        nmodl_invalidate_plans(m->ctx, m);
         return NMODL_OK;
     }
     if (s->ctx != m->ctx) return NMODL_ERR_ARG;
@@ -323,6 +325,7 @@ NMODL_API int nmodl_mech_attach_surrogate(nmodl_mech* m, nmodl_surrogate* s, dou
     }
     m->sur = s;
     m->sur_tol = tol;
+    nmodl_invalidate_plans(m->ctx, m);  // cached step graphs hold the old kernels
     return NMODL_OK;
 }
 

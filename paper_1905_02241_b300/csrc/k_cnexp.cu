@@ -10,6 +10,7 @@
 //                    tile, with the tile's states resident in shared memory
 //                    for the whole window (the compartments are isolated, so
 //                    tiles never exchange data)
+#include <algorithm>
 #include <climits>
 
 #include "kernels.cuh"
@@ -181,14 +182,28 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     __shared__ int pair_start[kMaxMechsFused * kMaxGates + 1];
     __shared__ int n_pairs;
 
+    __shared__ int tile_s;
+
     const int tid = threadIdx.x;
     const int T = A.n_types;
-    const int32_t* rec = A.tiles + (int64_t)blockIdx.x * A.tile_stride;
+    for (int k = tid; k < T * (int)(sizeof(MechD) / 4); k += blockDim.x)
+        ((int32_t*)md_s)[k] = ((const int32_t*)A.md)[k];
+
+    // Tiles come from the work list in order (largest first): either one
+    // per block, or -- persistent form -- pulled from an atomic counter by
+    // resident blocks until the list is exhausted.
+    for (int round = 0;; ++round) {
+    if (tid == 0) {
+        if (A.tile_counter) tile_s = atomicAdd(A.tile_counter, 1);
+        else tile_s = round == 0 ? (int)blockIdx.x : A.n_tiles;
+    }
+    __syncthreads();
+    const int tile = tile_s;
+    if (tile >= A.n_tiles) break;
+    const int32_t* rec = A.tiles + (int64_t)tile * A.tile_stride;
     const int n0 = rec[0];
     const int NT = rec[1] - rec[0];
 
-    for (int k = tid; k < T * (int)(sizeof(MechD) / 4); k += blockDim.x)
-        ((int32_t*)md_s)[k] = ((const int32_t*)A.md)[k];
     if (tid == 0) {
         int so = 0, no = 0, q = 0;
         for (int t = 0; t < T; ++t) {
@@ -363,6 +378,8 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             A.states[t][g * A.stride[t] + a_s[t] + j] = m;
         }
     }
+    __syncthreads();  // shared memory is reused by the next tile
+    }
 }
 
 // ------------------------------------------------------------ launchers
@@ -406,14 +423,28 @@ void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
         k_cur_seg<NMODL_CNEXP><<<grid, block, 0, s>>>(desc, n_chunks, chunk, ni, v, st, stride, rhs, d, err);
 }
 
-cudaError_t launch_fused(int prec, const FusedArgs& a, int n_tiles, int block,
-                         size_t smem, cudaStream_t s) {
-    if (n_tiles == 0) return cudaSuccess;
+// grid = blocks of this launch (one per tile, or the resident count in the
+// persistent form)
+cudaError_t launch_fused(int prec, const FusedArgs& a, int grid, int block, size_t smem,
+                         cudaStream_t s) {
+    if (grid <= 0 || a.n_tiles == 0) return cudaSuccess;
     if (prec == NMODL_FP64)
-        k_fused_tiles<NMODL_FP64><<<n_tiles, block, smem, s>>>(a);
+        k_fused_tiles<NMODL_FP64><<<grid, block, smem, s>>>(a);
     else
-        k_fused_tiles<NMODL_MIXED><<<n_tiles, block, smem, s>>>(a);
+        k_fused_tiles<NMODL_MIXED><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// Blocks of the persistent form: as many as can be resident at once.
+int fused_resident_grid(int prec, int n_tiles, int block, size_t smem) {
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (prec == NMODL_FP64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tiles<NMODL_FP64>, block, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tiles<NMODL_MIXED>, block, smem);
+    return std::min(n_tiles, std::max(1, per_sm) * sms);
 }
 
 // Raise the kernel's dynamic shared-memory limit to max_smem (set once, at

@@ -300,16 +300,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
     }
 }
 
+// Called when a surrogate is created (outside any stream capture).
+cudaError_t surrogate_prepare() {
+    return cudaFuncSetAttribute(k_surrogate_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSmemTotal);
+}
+
 cudaError_t launch_surrogate_step(const SurArgs& a, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_surrogate_step,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kSmemTotal);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
     int sms = 148;
     int dev = 0;
     cudaGetDevice(&dev);

@@ -16,8 +16,10 @@ struct FusedArgs {
     double* states[kMaxMechsFused];        // SoA, row stride below
     int64_t stride[kMaxMechsFused];
     const int32_t* ni[kMaxMechsFused];
-    const int32_t* tiles;                  // tile records
+    const int32_t* tiles;                  // tile records (work list)
     int32_t tile_stride;                   // 2 + 2 * n_types
+    int32_t n_tiles;
+    int32_t* tile_counter;                 // persistent form: next tile
     int32_t nsteps;
     int32_t clamp_v;
     int32_t pad;
@@ -38,8 +40,9 @@ void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
                     const int32_t* chunk, const int32_t* ni, const double* v,
                     const double* st, int64_t stride, double* rhs, double* d,
                     int32_t* err, cudaStream_t s);
-cudaError_t launch_fused(int prec, const FusedArgs& a, int n_tiles, int block,
+cudaError_t launch_fused(int prec, const FusedArgs& a, int grid, int block,
                          size_t smem, cudaStream_t s);
+int fused_resident_grid(int prec, int n_tiles, int block, size_t smem);
 size_t fused_static_smem(int prec);
 cudaError_t fused_prepare(int prec, size_t max_smem);
 

@@ -84,6 +84,7 @@ struct SurArgs {
     int32_t* err;
 };
 cudaError_t launch_surrogate_step(const SurArgs& a, cudaStream_t s);
+cudaError_t surrogate_prepare();
 
 // training data: normalised inputs [n][11] and targets [n][9] from
 // (v, dt, x, y = Newton step) in FP64

@@ -50,11 +50,16 @@ struct Plan {
     size_t smem = 0;
     int32_t* d_tiles = nullptr;
     nmodl::MechD* d_md = nullptr;
+    int32_t* d_counter = nullptr;   // persistent form's tile queue
+    bool persistent = false;
+    size_t budget = 0;
+    int grid = 0;                   // blocks per launch
     std::vector<GraphEntry> graphs;
     ~Plan() {
         for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
         cudaFree(d_tiles);
         cudaFree(d_md);
+        cudaFree(d_counter);
     }
 };
 
@@ -109,3 +114,4 @@ struct nmodl_surrogate {
 
 // shared helpers (api.cu)
 int nmodl_cuda_status(cudaError_t e);
+void nmodl_invalidate_plans(nmodl_ctx* c, nmodl_mech* m);

@@ -1,0 +1,195 @@
+"""Measurements of the three derived forms against the plain FP64 form on the
+same GPU (used by bench.py):
+
+  batched  the 10-type mix over 64 independent networks of log-uniform size
+           (10k..500k compartments), all types in one fused launch per
+           40-step window replayed from a CUDA graph, autotuned tile/block
+           shapes; MIXED precision vs FP64 on the same networks
+  kinetic  the 9-state scheme on 1M clamped compartments: FP64 Newton vs
+           FP32 LU + FP64 residual refinement
+  surrogate the BF16 MLP stand-in (trained here on Newton-generated pairs) on
+           4M clamped compartments vs the FP64 Newton solve, with fallback
+           rate and final error against the Newton trajectory
+
+Each entry reports instance-steps/s (state + cur) and its ratio to the FP64
+form.  Errors against the FP64 CPU oracle of the mixed forms are measured
+by the tests and by `mixed_errors` on a sub-network sample.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import torch
+
+from . import _lib
+from . import workloads as W
+from .api import NMODL_FP64, NMODL_MIXED, Context, Mechanism
+
+DT, CM = 0.025, 1.0
+
+
+def _mechs(ctx, wl):
+    return [Mechanism(ctx, m["type"], m["node_index"], wl["n_nodes"], m["params"])
+            for m in wl["mechs"]]
+
+
+def _time(fn, ctx, reps):
+    ctx.check()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(reps):
+        fn()
+    e1.record(ctx.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.check()
+    return ms
+
+
+def _ninst(wl):
+    return int(sum(m["node_index"].size for m in wl["mechs"]))
+
+
+def batched(dev, steps=2, nsteps=200, scale=1.0):
+    wl = W.batched_networks(64, seed=3, scale=scale)
+    n, ninst = wl["n_nodes"], _ninst(wl)
+    out = {"networks": 64, "nodes": n, "instances": ninst, "steps_per_run": nsteps}
+    ctx = Context(dev, precision=NMODL_MIXED)
+    mechs = _mechs(ctx, wl)
+    v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
+    rhs = torch.zeros_like(v)
+    d = torch.zeros_like(v)
+    for m in mechs:
+        m.init(v)
+    t0 = time.perf_counter()
+    ctx.step(mechs, DT, CM, v, rhs, d, nsteps)          # plan + autotune + graphs
+    ctx.check()
+    out["plan_seconds"] = round(time.perf_counter() - t0, 3)
+    out["plan_mixed"] = ctx.plan(mechs)
+    ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, steps)
+    out["mixed"] = ninst * nsteps * steps / (ms * 1e-3)
+    ctx.set_options(precision=NMODL_FP64)
+    ctx.step(mechs, DT, CM, v, rhs, d, 40)
+    ctx.check()
+    out["plan_fp64"] = ctx.plan(mechs)
+    ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, 40), ctx, 1)
+    out["fp64"] = ninst * 40 / (ms * 1e-3)
+    out["mixed_over_fp64"] = out["mixed"] / out["fp64"]
+    out["launches_per_run"] = -(-nsteps // ctx.options.window)
+    for m in mechs:
+        m.close()
+    ctx.close()
+    return out
+
+
+def mixed_errors(dev, n_nodes=1500, nsteps=200):
+    """Per-quantity error of the MIXED fused step against the FP64 oracle on
+    a sub-network of the cortical mix (max over nodes / instances)."""
+    from oracle import oracle as orc
+    wl = W.cortical_mix(n_nodes, seed=2)
+    st0 = [orc.mech_init(m["type"], m["params"], m["node_index"], wl["v0"])
+           for m in wl["mechs"]]
+    ctx = Context(dev, precision=NMODL_MIXED)
+    mechs = _mechs(ctx, wl)
+    for m, s in zip(mechs, st0):
+        if m.n_states:
+            m.set_states(torch.tensor(s, device=f"cuda:{dev}"))
+    v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
+    rhs = torch.zeros_like(v)
+    d = torch.zeros_like(v)
+    ctx.step(mechs, DT, CM, v, rhs, d, nsteps)
+    ctx.check()
+    v_ref, r_ref, d_ref, s_ref = orc.step(wl["mechs"], st0, wl["v0"], n_nodes, DT,
+                                          nsteps=nsteps)
+    res = {"steps": nsteps, "nodes": n_nodes,
+           "v_abs_mV": float(np.max(np.abs(v.cpu().numpy() - v_ref))),
+           "d_rel": float(np.max(np.abs(d.cpu().numpy() - d_ref) / d_ref)),
+           "rhs_rel_to_200mV_d": float(np.max(np.abs(rhs.cpu().numpy() - r_ref) /
+                                              (200 * d_ref)))}
+    per_state = {}
+    for m, s, spec in zip(mechs, s_ref, W.CORTICAL_TYPES):
+        if m.n_states:
+            err = np.max(np.abs(m.states().cpu().numpy() - s), axis=1)
+            per_state[spec[0]] = [float(x) for x in err]
+    res["state_abs"] = per_state
+    for m in mechs:
+        m.close()
+    ctx.close()
+    return res
+
+
+def kinetic(dev, n=1_000_000, nsteps=200, steps=1):
+    wl = W.kin9_clamped(n, seed=4)
+    out = {"instances": n, "steps_per_run": nsteps}
+    x0 = torch.tensor(wl["x0"], device=f"cuda:{dev}")
+    v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
+    rhs = torch.zeros_like(v)
+    d = torch.zeros_like(v)
+    for name, prec in (("fp64", NMODL_FP64), ("mixed", NMODL_MIXED)):
+        ctx = Context(dev, precision=prec, clamp_v=1)
+        (m,) = _mechs(ctx, wl)
+        m.set_states(x0)
+        ctx.step([m], DT, CM, v, rhs, d, 2)
+        m.set_states(x0)
+        ms = _time(lambda: ctx.step([m], DT, CM, v, rhs, d, nsteps), ctx, steps)
+        out[name] = n * nsteps * steps / (ms * 1e-3)
+        st = m.stats()
+        out[name + "_updates_per_solve"] = st["newton_iters"] / max(1, st["calls"]) / n
+        out[name + "_final"] = m.states()
+        m.close()
+        ctx.close()
+    diff = (out.pop("mixed_final") - out.pop("fp64_final")).abs().sum(dim=0)
+    out["mixed_over_fp64"] = out["mixed"] / out["fp64"]
+    out["mixed_max_l1_vs_fp64"] = float(diff.max())
+    return out
+
+
+def surrogate(dev, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=20):
+    from .surrogate import Surrogate, attach, make_training_pairs
+    p = W.kin9_params(W.Stream(4, 401))
+    out = {"instances": n, "steps_per_run": nsteps, "training_pairs": n_pairs,
+           "epochs": epochs, "tolerance": 1e-4}
+    ctx = Context(dev, clamp_v=1)
+    t0 = time.perf_counter()
+    sur = Surrogate(ctx, max_batch=8192)
+    Ws, bs = W.mlp_init(7)
+    sur.set_weights(Surrogate.pack(Ws, bs))
+    X, T = make_training_pairs(ctx, sur, p, n_pairs, seed=6)
+    torch.cuda.synchronize()
+    out["pairs_seconds"] = round(time.perf_counter() - t0, 2)
+    t0 = time.perf_counter()
+    losses = sur.fit(X, T, epochs=epochs, batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    out["train_seconds"] = round(time.perf_counter() - t0, 2)
+    out["final_loss"] = float(losses[-1])
+    del X, T
+    wl = W.kin9_clamped(n, seed=5)
+    x0 = torch.tensor(wl["x0"], device=f"cuda:{dev}")
+    v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
+    rhs = torch.zeros_like(v)
+    d = torch.zeros_like(v)
+    (m,) = _mechs(ctx, wl)
+    m.set_states(x0)
+    ms = _time(lambda: ctx.step([m], DT, CM, v, rhs, d, nsteps), ctx, 1)
+    out["newton_fp64"] = n * nsteps / (ms * 1e-3)
+    ref = m.states()
+    m.close()
+    (m,) = _mechs(ctx, wl)
+    m.set_states(x0)
+    attach(m, sur, 1e-4)
+    ms = _time(lambda: ctx.step([m], DT, CM, v, rhs, d, nsteps), ctx, 1)
+    out["surrogate"] = n * nsteps / (ms * 1e-3)
+    st = m.stats()
+    out["fallback_rate"] = st["fallback"] / (n * nsteps)
+    err = (m.states() - ref).abs().sum(dim=0)
+    out["final_max_l1_vs_newton"] = float(err.max())
+    out["final_mean_l1_vs_newton"] = float(err.mean())
+    out["surrogate_over_newton_fp64"] = out["surrogate"] / out["newton_fp64"]
+    attach(m, None)
+    m.close()
+    sur.close()
+    ctx.close()
+    return out

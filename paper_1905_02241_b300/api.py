@@ -96,6 +96,7 @@ class Mechanism:
             ptr = ni.ctypes.data
             n = ni.size
         self.n = int(n)
+        ctx.enter()
         self.handle = _lib.nmodl_mech_create(ctx.handle, self.type, self.n,
                                              ptr if n else 0, self.n_nodes,
                                              p.ctypes.data, p.size)

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -234,7 +235,7 @@ int nmodl_sync(nmodl_ctx* c) {
     int32_t h = 0;
     e = cudaMemcpy(&h, c->d_err, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return NMODL_ERR_CUDA;
-    if (h) cudaMemset(c->d_err, 0, sizeof(int32_t));
+    if (h) cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream);
     return h;
 }
 
@@ -293,16 +294,18 @@ int nmodl_mech_create(nmodl_ctx* c, int type, int64_t n, const int32_t* node_ind
         if ((e = dalloc(&m->d_kd, 1)) != cudaSuccess) break;
         if ((e = dalloc(&m->d_cnt, 1)) != cudaSuccess) break;
         if ((e = dalloc(&d_flags, 1)) != cudaSuccess) break;
-        if (n > 0 && (e = cudaMemcpy(m->d_ni, node_index, n * sizeof(int32_t),
-                                     cudaMemcpyDefault)) != cudaSuccess)
+        // every copy and fill below is ordered on the context stream, which
+        // need not synchronise with the legacy default stream
+        if (n > 0 && (e = cudaMemcpyAsync(m->d_ni, node_index, n * sizeof(int32_t),
+                                          cudaMemcpyDefault, c->stream)) != cudaSuccess)
             break;
         if (m->n_states && m->stride &&
-            (e = cudaMemset(m->d_states, 0, m->n_states * m->stride * sizeof(double))) != cudaSuccess)
+            (e = cudaMemsetAsync(m->d_states, 0, m->n_states * m->stride * sizeof(double), c->stream)) != cudaSuccess)
             break;
-        if ((e = cudaMemcpy(m->d_md, &m->md, sizeof(MechD), cudaMemcpyHostToDevice)) != cudaSuccess) break;
-        if ((e = cudaMemcpy(m->d_kd, &m->kd, sizeof(Kin9D), cudaMemcpyHostToDevice)) != cudaSuccess) break;
-        if ((e = cudaMemset(m->d_cnt, 0, sizeof(KinCounters))) != cudaSuccess) break;
-        if ((e = cudaMemset(d_flags, 0, sizeof(int32_t))) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(m->d_md, &m->md, sizeof(MechD), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(m->d_kd, &m->kd, sizeof(Kin9D), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(m->d_cnt, 0, sizeof(KinCounters), c->stream)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(d_flags, 0, sizeof(int32_t), c->stream)) != cudaSuccess) break;
         launch_validate_index(m->d_ni, n, n_nodes, d_flags, c->stream);
         launch_chunk_starts(m->d_ni, n, m->n_chunks, m->d_chunk, c->stream);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
@@ -481,7 +484,11 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     for (int i = 0; i < n_mechs; ++i)
         if (mechs[i]->type == NMODL_KIN9) cnexp = false;
     p->fused = false;
-    if (!cnexp || p->n_nodes == 0) return NMODL_OK;
+    const bool dbg = std::getenv("NMODL_PLAN_DEBUG") != nullptr;
+    if (!cnexp || p->n_nodes == 0) {
+        if (dbg) std::fprintf(stderr, "[nmodl plan] not fusable\n");
+        return NMODL_OK;
+    }
 
     const int T = n_mechs;
     const int G = 32;
@@ -496,7 +503,8 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
         cudaFree(d_bounds);
         return cuda_status(e);
     }
-    cudaMemcpy(d_bounds, bounds.data(), (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    cudaMemcpyAsync(d_bounds, bounds.data(), (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                    c->stream);
     for (int t = 0; t < T; ++t)
         launch_tile_bounds(mechs[t]->d_ni, mechs[t]->n, d_bounds, K + 1, d_off + t * (K + 1),
                            c->stream);
@@ -540,12 +548,18 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     for (size_t b : budgets) {
         std::vector<int32_t> recs;
         size_t max_smem = 0;
-        if (b > cap || !make_tiles(off, T, gates, p->n_nodes, G, b, recs, max_smem)) continue;
+        if (b > cap || !make_tiles(off, T, gates, p->n_nodes, G, b, recs, max_smem)) {
+            if (dbg) std::fprintf(stderr, "[nmodl plan] budget %zu: no tiling\n", b);
+            continue;
+        }
         lpt_order(recs, T, gates);
         for (int blk : blocks)
             for (bool ps : pers)
                 cands.push_back(Candidate{b, blk, ps, recs, std::max<size_t>(max_smem, 16)});
     }
+    if (dbg)
+        std::fprintf(stderr, "[nmodl plan] prec %d types %d nodes %lld cap %zu stat %zu cands %zu\n",
+                     p->precision, T, (long long)p->n_nodes, cap, stat, cands.size());
     if (cands.empty()) return NMODL_OK;  // no tile fits: generic step
     int32_t* d_counter = nullptr;
     if ((e = dalloc(&d_counter, 1)) != cudaSuccess) return cuda_status(e);
@@ -625,7 +639,9 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
                 if (dalloc(&p->d_md, T) != cudaSuccess) { ok = false; break; }
                 std::vector<MechD> mds(T);
                 for (int t = 0; t < T; ++t) mds[t] = mechs[t]->md;
-                cudaMemcpy(p->d_md, mds.data(), T * sizeof(MechD), cudaMemcpyHostToDevice);
+                cudaMemcpyAsync(p->d_md, mds.data(), T * sizeof(MechD), cudaMemcpyHostToDevice,
+                                c->stream);
+                cudaStreamSynchronize(c->stream);
             }
             a.md = p->d_md;
             double best_ms = 1e30;
@@ -656,6 +672,12 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
         cudaGetLastError();
         if (!ok) best = 0;
     }
+    if (dbg)
+        for (size_t ci = 0; ci < cands.size(); ++ci)
+            std::fprintf(stderr, "[nmodl plan] budget %zu block %d persistent %d tiles %zu smem %zu ns/inst %.4g%s\n",
+                         cands[ci].budget, cands[ci].block, (int)cands[ci].persistent,
+                         cands[ci].recs.size() / p->tile_stride, cands[ci].smem, cands[ci].ms * 1e6,
+                         ci == best ? "  <- chosen" : "");
     Candidate& ch = cands[best];
     p->budget = ch.budget;
     p->block = ch.block;
@@ -665,13 +687,15 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     p->grid = ch.persistent ? fused_resident_grid(p->precision, p->n_tiles, ch.block, ch.smem)
                             : p->n_tiles;
     if ((e = dalloc(&p->d_tiles, ch.recs.size())) != cudaSuccess) return cuda_status(e);
-    cudaMemcpy(p->d_tiles, ch.recs.data(), ch.recs.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpyAsync(p->d_tiles, ch.recs.data(), ch.recs.size() * sizeof(int32_t),
+                    cudaMemcpyHostToDevice, c->stream);
     if (!p->d_md) {
         if ((e = dalloc(&p->d_md, T)) != cudaSuccess) return cuda_status(e);
         std::vector<MechD> mds(T);
         for (int t = 0; t < T; ++t) mds[t] = mechs[t]->md;
-        cudaMemcpy(p->d_md, mds.data(), T * sizeof(MechD), cudaMemcpyHostToDevice);
+        cudaMemcpyAsync(p->d_md, mds.data(), T * sizeof(MechD), cudaMemcpyHostToDevice, c->stream);
     }
+    cudaStreamSynchronize(c->stream);  // host buffers above go out of scope
     p->fused = true;
     return NMODL_OK;
 }

@@ -180,11 +180,11 @@ NMODL_API int nmodl_surrogate_create(nmodl_ctx* c, int64_t max_batch, const floa
         if ((e = dalloc(&s->loss, 1)) != cudaSuccess) break;
         std::vector<float> pad(kParamsPadded, 0.f);
         if (weights) pub_to_pad(weights, pad.data());
-        if ((e = cudaMemcpy(s->params, pad.data(), sizeof(float) * kParamsPadded,
-                            cudaMemcpyHostToDevice)) != cudaSuccess) break;
-        cudaMemset(s->m, 0, sizeof(float) * kParamsPadded);
-        cudaMemset(s->v, 0, sizeof(float) * kParamsPadded);
-        cudaMemset(s->grad, 0, sizeof(float) * kParamsPadded);
+        if ((e = cudaMemcpyAsync(s->params, pad.data(), sizeof(float) * kParamsPadded,
+                                 cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) break;
+        cudaMemsetAsync(s->m, 0, sizeof(float) * kParamsPadded, c->stream);
+        cudaMemsetAsync(s->v, 0, sizeof(float) * kParamsPadded, c->stream);
+        cudaMemsetAsync(s->grad, 0, sizeof(float) * kParamsPadded, c->stream);
         refresh_bf16(s);
         e = cudaStreamSynchronize(c->stream);
         if (e == cudaSuccess) e = surrogate_prepare();

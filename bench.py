@@ -35,12 +35,15 @@ METRIC = "mechanism instance-steps/s (state+cur)"
 
 # FP64 pipe instructions of a minimal implementation of each operation,
 # the unit of the algorithmic op count of the FP64 path:
-# add/sub/mul/fma 1; exp/expm1 10 (table-driven range reduction + degree-6
-# polynomial + reconstruction); division 7 (FP32 seed, two Newton steps,
-# quotient and one correction).
+# add/sub/mul/fma 1; exp 10 (table-driven range reduction + degree-6
+# polynomial + reconstruction); reciprocal or division 7 (seed, two Newton
+# steps, one correction).  A gate: each rate as numerator/denominator
+# (u = (v - vh)/k: 2; EXP A e^u: exp + 1; SIGMOID A/(1 + e^-u): exp + 1;
+# LINOID A u/(1 - e^-u): exp + 2), then one reciprocal for minf and
+# alpha + beta (9 + 7 - 1), then cnexp (x, exp, 1 - e, diff, fma: 14).
 C_EXP, C_DIV = 10, 7
-RATE_COST = {0: 2 + C_EXP + 1, 1: 2 + C_EXP + 1 + C_DIV, 2: 2 + C_EXP + 1 + C_DIV}
-GATE_TAIL = 1 + C_DIV + 1 + C_EXP + 1 + 1 + 1  # s, minf, x, exp, 1-e, diff, fma
+RATE_COST = {0: 2 + C_EXP + 1, 1: 2 + C_EXP + 1, 2: 2 + C_EXP + 2}
+GATE_TAIL = 8 + C_DIV + 1 + C_EXP + 1 + 1 + 1
 NODE_COST = 1 + C_DIV + 1                       # d += cm/dt, rhs/d, v +=
 
 

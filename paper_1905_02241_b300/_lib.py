@@ -89,6 +89,7 @@ _SIGS = {
     "nmodl_kin9_solve": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _i64]),
     "nmodl_mech_attach_surrogate": (_i32, [_vp, _vp, _d]),
     "nmodl_plan_describe": (_i32, [_vp, _vp, _i32, _vp]),
+    "nmodl_math_eval": (_i32, [_i32, _i64, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -282,3 +283,7 @@ def nmodl_plan_describe(ctx: int, mechs) -> dict:
                                    ctypes.cast(out, _vp)), "nmodl_plan_describe")
     return dict(fused=bool(out[0]), tiles=int(out[1]), block=int(out[2]),
                 smem=int(out[3]), persistent=bool(out[4]), tile_budget=int(out[5]))
+
+
+def nmodl_math_eval(fn: int, n: int, x_ptr: int, y_ptr: int, stream: int) -> None:
+    _check(lib.nmodl_math_eval(int(fn), int(n), x_ptr, y_ptr, stream or None), "nmodl_math_eval")

@@ -47,7 +47,7 @@ __global__ void k_state_gates(const MechD* __restrict__ md, int64_t n,
     if (PREC == NMODL_FP64) {
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
              i += (int64_t)gridDim.x * blockDim.x) {
-            const double m = gate_step_d(G, phidt, v[ni[i]], row[i]);
+            const double m = gate_step_fast_d(G, phidt, v[ni[i]], row[i]);
             if (!isfinite(m)) latch_error(err, NMODL_ERR_NONFINITE);
             row[i] = m;
         }
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             const double vv = v_s[nid_s[nid_off[t] + j]];
             if (PREC == NMODL_FP64) {
                 const GateD& G = md_s[t].gate[g];
-                st_d[k] = gate_step_d(G, md_s[t].phi * A.dt, vv, st_d[k]);
+                st_d[k] = gate_step_fast_d(G, md_s[t].phi * A.dt, vv, st_d[k]);
             } else {
                 float minf, f;
                 gate_coef_f(gf_s[t][g], (float)(md_s[t].phi * A.dt), (float)vv, minf, f);

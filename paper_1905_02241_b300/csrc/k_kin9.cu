@@ -177,8 +177,8 @@ __global__ void __launch_bounds__(128)
             double dk_f[kKinEdges], dk_b[kKinEdges];
 #pragma unroll
             for (int e = 0; e < kKinEdges; ++e) {
-                dk_f[e] = dt * (K.af[e] * exp(K.bf[e] * vv));
-                dk_b[e] = dt * (K.ab[e] * exp(-K.bb[e] * vv));
+                dk_f[e] = dt * (K.af[e] * exp_tang(K.bf[e] * vv));
+                dk_b[e] = dt * (K.ab[e] * exp_tang(-K.bb[e] * vv));
             }
             double diag[9];
 #pragma unroll

@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include "../../include/nmodl_b300.h"
+#include "exp_tang_table.cuh"
 
 namespace nmodl {
 
@@ -55,6 +56,73 @@ struct Kin9D {
 };
 
 // ------------------------------------------------------------ FP64 math
+
+// exp(x) by Tang's table-driven method (ACM TOMS 15(2), 1989): with
+// n = round(32 x / ln2) = 32 m + j and r = x - n ln2/32 (two-constant
+// Cody-Waite reduction, |r| <= ln2/64), exp(x) = 2^m 2^(j/32) (1 + p(r)),
+// p(r) the degree-6 Taylor polynomial of exp(r) - 1 (truncation < 4e-18).
+// 11 FP64 instructions; 2^m is applied to the exponent field with integer
+// operations.  |x| >= 708 (and NaN) go to the library exp.
+__device__ __forceinline__ double exp_tang(double x) {
+    // |x| < 708 tested on the high word (integer pipe): 708 = 0x4086200000000000
+    if ((__double2hiint(x) & 0x7fffffff) >= 0x40862000) return exp(x);
+    const double kShift = 0x1.8p52;
+    const double t = fma(x, kExpInvL, kShift);
+    const int k = __double2loint(t);
+    const double n = t - kShift;
+    double r = fma(n, -kExpL1, x);
+    r = fma(n, -kExpL2, r);
+    double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+    q = fma(q, r, 1.0 / 24.0);
+    q = fma(q, r, 1.0 / 6.0);
+    q = fma(q, r, 0.5);
+    q = fma(q, r, 1.0);
+    const double pr = q * r;
+    const double T = __ldg(&kExpTable[k & 31]);
+    const double y = fma(T, pr, T);
+    return __hiloint2double(__double2hiint(y) + ((k >> 5) << 20), __double2loint(y));
+}
+
+// A rate as numerator / denominator (so that a gate needs one reciprocal):
+// EXP A e^u / 1; SIGMOID A / (1 + e^-u); LINOID A u / (1 - e^-u), with the
+// series A (1 + u/2 + u^2/12 - u^4/720) / 1 for |u| < 0.01 (next term
+// u^6/30240 < 4e-17).
+__device__ __forceinline__ void rate_nd(int form, double A, double vh, double rk, double v,
+                                        double& num, double& den) {
+    const double u = (v - vh) * rk;
+    if (form == kExp) {
+        num = A * exp_tang(u);
+        den = 1.0;
+    } else if (form == kSigmoid) {
+        num = A;
+        den = 1.0 + exp_tang(-u);
+    } else if ((__double2hiint(u) & 0x7fffffff) < 0x3f847ae1) {  // |u| < 0.01
+        const double s = u * u;
+        num = A * fma(u, 0.5, fma(s, fma(s, -1.0 / 720.0, 1.0 / 12.0), 1.0));
+        den = 1.0;
+    } else {
+        num = A * u;
+        den = 1.0 - exp_tang(-u);
+    }
+}
+
+// cnexp gate step with one reciprocal: alpha = Pa/Da, beta = Pb/Db,
+// N = Pa Db + Pb Da, D = Da Db, R = 1/(N D): minf = Pa Db D R,
+// alpha + beta = N N R.
+__device__ __forceinline__ double gate_step_fast_d(const GateD& G, double phidt, double v,
+                                                   double m) {
+    double na, da, nb, db;
+    rate_nd(G.aform, G.aA, G.avh, G.ark, v, na, da);
+    rate_nd(G.bform, G.bA, G.bvh, G.brk, v, nb, db);
+    const double P = na * db;
+    const double N = fma(nb, da, P);
+    const double D = da * db;
+    const double R = __drcp_rn(N * D);
+    const double minf = P * (D * R);
+    const double s = N * (N * R);
+    const double f = 1.0 - exp_tang(-phidt * s);
+    return fma(f, minf - m, m);
+}
 
 __device__ __forceinline__ double rate_d(int form, double A, double vh,
                                          double rk, double v) {

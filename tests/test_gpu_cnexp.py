@@ -299,3 +299,30 @@ def test_full_size_sampled_parity(api, orc):
             g = m.states().cpu().numpy()[:, idx]
             assert state_err(g, s) <= 1e-9
     np.testing.assert_allclose(d.cpu().numpy()[nodes], d_ref, rtol=1e-9)
+
+
+def test_table_exp_ulp_error():
+    """The FP64 exp of the state kernels (Tang's table-driven method) against
+    mpmath at 40 digits and against CUDA's exp: at most 1 ulp."""
+    import mpmath
+    from paper_1905_02241_b300 import _lib
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.uniform(-708, 708, 20000), rng.uniform(-1, 1, 20000),
+                        rng.uniform(-30, 30, 20000), [0.0, -0.0, 1e-300, 707.9, -707.9]])
+    xd = to_dev(x)
+    y = torch.empty_like(xd)
+    yc = torch.empty_like(xd)
+    _lib.nmodl_math_eval(0, x.size, xd.data_ptr(), y.data_ptr(), 0)
+    _lib.nmodl_math_eval(1, x.size, xd.data_ptr(), yc.data_ptr(), 0)
+    torch.cuda.synchronize()
+    y, yc = y.cpu().numpy(), yc.cpu().numpy()
+    idx = np.random.default_rng(4).choice(x.size, 3000, replace=False)
+    worst = 0.0
+    for i in idx:
+        ref = mpmath.exp(mpmath.mpf(float(x[i])))
+        ulp = np.spacing(float(ref))
+        worst = max(worst, abs(float(mpmath.mpf(float(y[i])) - ref)) / ulp)
+    print(f"table exp: max error {worst:.3f} ulp (3000 samples vs mpmath)")
+    assert worst <= 1.0
+    assert np.max(np.abs(y - yc) / np.abs(yc)) <= 2.5e-16

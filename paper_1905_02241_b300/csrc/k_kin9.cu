@@ -27,12 +27,15 @@ namespace {
 
 __host__ __device__ constexpr bool in_band(int i, int j) { return (i - j <= 3) && (j - i <= 3); }
 
-// In-place no-pivot LU of the banded 9x9 matrix M (only band entries used).
+// In-place no-pivot LU of the banded 9x9 matrix M (only band entries used);
+// the diagonal is replaced by the reciprocals of the pivots, so that the
+// triangular solves multiply instead of divide.
 template <typename R>
 __device__ __forceinline__ void lu_band(R (&M)[9][9]) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const R rp = R(1) / M[k][k];
+        M[k][k] = rp;
 #pragma unroll
         for (int i = k + 1; i < 9; ++i) {
             if (!in_band(i, k)) continue;
@@ -60,7 +63,7 @@ __device__ __forceinline__ void lu_band_solve(const R (&M)[9][9], R (&b)[9]) {
 #pragma unroll
         for (int c = i + 1; c < 9; ++c)
             if (in_band(i, c)) b[i] -= M[i][c] * b[c];
-        b[i] = b[i] / M[i][i];
+        b[i] = b[i] * M[i][i];
     }
 }
 

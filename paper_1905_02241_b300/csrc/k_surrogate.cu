@@ -29,7 +29,7 @@ constexpr int P1 = kIn + 8;    // W1 row pitch (elements)
 constexpr int PH = kHid + 8;   // W2, W3, W4 row pitch
 constexpr int kSmemW = (kHid * P1 + 2 * kHid * PH + kOut * PH) * 2;
 constexpr int kSmemB = (3 * kHid + kOut) * 4;
-constexpr int kWarpFloats = 16 * 16 + 16 * 24 + 16 * 9 + 16 + 16 * 9;
+constexpr int kWarpFloats = 32 * 16 + 32 * 24 + 32 * 9 + 32 + 32 * 9;
 constexpr int kSmemY = kWarps * kWarpFloats * 4;
 constexpr int kSmemTotal = kSmemW + kSmemB + kSmemY;
 }  // namespace
@@ -145,20 +145,20 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
     const Kin9D& K = *a.kd;
     const float dtf = (float)a.dt;
     const int g = lane >> 2, t = lane & 3, q = lane >> 3, r8 = lane & 7;
-    // per-warp staging: features [16][16], rates [16][24], x [16][9],
-    // scale [16], outputs [16][9]
+    // per-warp staging of 32 instances: features [32][16], rates [32][24],
+    // x [32][9], scale [32], outputs [32][9]
     float* wsm = warp_all + warp * kWarpFloats;
     float* feat = wsm;
-    float* rates = feat + 16 * 16;
-    float* xs = rates + 16 * 2 * kKinEdges;
-    float* ss = xs + 16 * 9;
-    float* ys = ss + 16;
-    const int64_t stride_w = (int64_t)gridDim.x * kWarps * 16;
+    float* rates = feat + 32 * 16;
+    float* xs = rates + 32 * 2 * kKinEdges;
+    float* ss = xs + 32 * 9;
+    float* ys = ss + 32;
+    const int64_t stride_w = (int64_t)gridDim.x * kWarps * 32;
 
-    for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 16; base < a.n;
+    for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < a.n;
          base += stride_w) {
-        // ---- per instance (lanes 0..15): rates, dt A x, scale, inputs
-        if (lane < 16) {
+        // ---- one lane per instance: rates, dt A x, scale, network inputs
+        {
             const int64_t i = base + lane;
             float* f = feat + lane * 16;
             if (i < a.n) {
@@ -184,85 +184,92 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
             for (int k = kInRaw; k < 16; ++k) f[k] = 0.f;
         }
         __syncwarp();
-        // ---- layer 1 input fragment: rows g and g+8
-        uint32_t afr[4];
-        afr[0] = pack_bf16(feat[g * 16 + 2 * t], feat[g * 16 + 2 * t + 1]);
-        afr[1] = pack_bf16(feat[(g + 8) * 16 + 2 * t], feat[(g + 8) * 16 + 2 * t + 1]);
-        afr[2] = pack_bf16(feat[g * 16 + 2 * t + 8], feat[g * 16 + 2 * t + 9]);
-        afr[3] = pack_bf16(feat[(g + 8) * 16 + 2 * t + 8], feat[(g + 8) * 16 + 2 * t + 9]);
-        float acc[16][4];
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
-#pragma unroll
-        for (int np = 0; np < 8; ++np) {
-            uint32_t b[4];
-            ldsm_x4(b, W1s + (16 * np + r8 + (q >> 1) * 8) * P1 + (q & 1) * 8);
-            mma_bf16_16816(acc[2 * np], afr, b[0], b[1]);
-            mma_bf16_16816(acc[2 * np + 1], afr, b[2], b[3]);
-        }
-        // C fragments of output tiles 2kk and 2kk+1 are, in this order, the
-        // A fragment (a0a1, a2a3, a4a5, a6a7) of k-slice kk of the next layer
-        uint32_t ah[8][4];
-        auto to_frags = [&](const float* bias) {
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = 2 * kk + h;
-                    const int col = 8 * j + 2 * t;
-                    const float b0 = bias[col], b1 = bias[col + 1];
-                    ah[kk][2 * h] = pack_bf16(silu_f(acc[j][0] + b0), silu_f(acc[j][1] + b1));
-                    ah[kk][2 * h + 1] = pack_bf16(silu_f(acc[j][2] + b0), silu_f(acc[j][3] + b1));
-                }
-        };
-        auto hidden = [&](const __nv_bfloat16* Ws) {
+        // ---- the MLP on rows 0..15, then 16..31
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            const float* fh = feat + half * 16 * 16;
+            uint32_t afr[4];
+            afr[0] = pack_bf16(fh[g * 16 + 2 * t], fh[g * 16 + 2 * t + 1]);
+            afr[1] = pack_bf16(fh[(g + 8) * 16 + 2 * t], fh[(g + 8) * 16 + 2 * t + 1]);
+            afr[2] = pack_bf16(fh[g * 16 + 2 * t + 8], fh[g * 16 + 2 * t + 9]);
+            afr[3] = pack_bf16(fh[(g + 8) * 16 + 2 * t + 8], fh[(g + 8) * 16 + 2 * t + 9]);
+            float acc[16][4];
 #pragma unroll
             for (int j = 0; j < 16; ++j)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk)
+            for (int np = 0; np < 8; ++np) {
+                uint32_t b[4];
+                ldsm_x4(b, W1s + (16 * np + r8 + (q >> 1) * 8) * P1 + (q & 1) * 8);
+                mma_bf16_16816(acc[2 * np], afr, b[0], b[1]);
+                mma_bf16_16816(acc[2 * np + 1], afr, b[2], b[3]);
+            }
+            // C fragments of output tiles 2kk and 2kk+1 are, in this order,
+            // the A fragment (a0a1, a2a3, a4a5, a6a7) of k-slice kk of the
+            // next layer
+            uint32_t ah[8][4];
+            auto to_frags = [&](const float* bias) {
 #pragma unroll
-                for (int np = 0; np < 8; ++np) {
-                    uint32_t b[4];
-                    ldsm_x4(b, Ws + (16 * np + r8 + (q >> 1) * 8) * PH + 16 * kk + (q & 1) * 8);
-                    mma_bf16_16816(acc[2 * np], ah[kk], b[0], b[1]);
-                    mma_bf16_16816(acc[2 * np + 1], ah[kk], b[2], b[3]);
-                }
-        };
-        to_frags(b1s);
-        hidden(W2s);
-        to_frags(b2s);
-        hidden(W3s);
-        to_frags(b3s);
-        float o[2][4];
+                for (int kk = 0; kk < 8; ++kk)
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = 2 * kk + h;
+                        const int col = 8 * j + 2 * t;
+                        const float b0 = bias[col], b1 = bias[col + 1];
+                        ah[kk][2 * h] = pack_bf16(silu_f(acc[j][0] + b0), silu_f(acc[j][1] + b1));
+                        ah[kk][2 * h + 1] =
+                            pack_bf16(silu_f(acc[j][2] + b0), silu_f(acc[j][3] + b1));
+                    }
+            };
+            auto hidden = [&](const __nv_bfloat16* Ws) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) o[j][e] = 0.f;
+                for (int j = 0; j < 16; ++j)
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-            uint32_t b[4];
-            ldsm_x4(b, W4s + (r8 + (q >> 1) * 8) * PH + 16 * kk + (q & 1) * 8);
-            mma_bf16_16816(o[0], ah[kk], b[0], b[1]);
-            mma_bf16_16816(o[1], ah[kk], b[2], b[3]);
+                    for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk)
+#pragma unroll
+                    for (int np = 0; np < 8; ++np) {
+                        uint32_t b[4];
+                        ldsm_x4(b, Ws + (16 * np + r8 + (q >> 1) * 8) * PH + 16 * kk + (q & 1) * 8);
+                        mma_bf16_16816(acc[2 * np], ah[kk], b[0], b[1]);
+                        mma_bf16_16816(acc[2 * np + 1], ah[kk], b[2], b[3]);
+                    }
+            };
+            to_frags(b1s);
+            hidden(W2s);
+            to_frags(b2s);
+            hidden(W3s);
+            to_frags(b3s);
+            float o[2][4];
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) o[j][e] = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                uint32_t b[4];
+                ldsm_x4(b, W4s + (r8 + (q >> 1) * 8) * PH + 16 * kk + (q & 1) * 8);
+                mma_bf16_16816(o[0], ah[kk], b[0], b[1]);
+                mma_bf16_16816(o[1], ah[kk], b[2], b[3]);
+            }
+            float* yh = ys + half * 16 * 9;
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int col = 8 * j + 2 * t + e;
+                        if (col < kOutRaw) yh[(g + 8 * h) * 9 + col] = o[j][2 * h + e] + b4s[col];
+                    }
         }
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int col = 8 * j + 2 * t + e;
-                    if (col < kOutRaw) ys[(g + 8 * h) * 9 + col] = o[j][2 * h + e] + b4s[col];
-                }
         __syncwarp();
         // ---- projection, residual, decision (one lane per instance)
         bool fail = false;
         const int64_t i = base + lane;
-        if (lane < 16 && i < a.n) {
+        if (i < a.n) {
             float xf[9], w[9], dkf[kKinEdges], dkb[kKinEdges], z[9];
 #pragma unroll
             for (int e = 0; e < kKinEdges; ++e) {
@@ -312,7 +319,7 @@ cudaError_t launch_surrogate_step(const SurArgs& a, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t groups = (a.n + 15) / 16;
+    const int64_t groups = (a.n + 31) / 32;
     int64_t grid = std::min<int64_t>((int64_t)sms * 2, (groups + kWarps - 1) / kWarps);
     if (grid < 1) grid = 1;
     k_surrogate_step<<<(int)grid, kWarps * 32, kSmemTotal, s>>>(a);

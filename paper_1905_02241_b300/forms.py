@@ -188,8 +188,49 @@ def surrogate(dev, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=20):
     out["final_max_l1_vs_newton"] = float(err.max())
     out["final_mean_l1_vs_newton"] = float(err.mean())
     out["surrogate_over_newton_fp64"] = out["surrogate"] / out["newton_fp64"]
+    # the same comparison with the FP32-LU + FP64-refinement Newton, which
+    # is also what the surrogate falls back to in this precision
+    ctx.set_options(precision=NMODL_MIXED)
+    m.set_states(x0)
+    fb0 = m.stats()["fallback"]
+    ms = _time(lambda: ctx.step([m], DT, CM, v, rhs, d, nsteps), ctx, 1)
+    out["surrogate_mixed_fallback"] = n * nsteps / (ms * 1e-3)
+    out["fallback_rate_mixed"] = (m.stats()["fallback"] - fb0) / (n * nsteps)
     attach(m, None)
+    m.set_states(x0)
+    ms = _time(lambda: ctx.step([m], DT, CM, v, rhs, d, nsteps), ctx, 1)
+    out["newton_mixed"] = n * nsteps / (ms * 1e-3)
+    out["surrogate_over_newton_mixed"] = out["surrogate_mixed_fallback"] / out["newton_mixed"]
     m.close()
     sur.close()
     ctx.close()
     return out
+
+
+def surrogate_kernel_case(dev=0, n=4_000_000, steps=3):
+    """Profiling case of the fused surrogate kernel: n clamped instances,
+    `steps` surrogate state updates with seeded (untrained) weights and a
+    1e-4 residual gate; prints instance-steps/s."""
+    from .surrogate import Surrogate, attach
+    wl = W.kin9_clamped(n, seed=5)
+    ctx = Context(dev)
+    sur = Surrogate(ctx, max_batch=256)
+    Ws, bs = W.mlp_init(7)
+    sur.set_weights(Surrogate.pack(Ws, bs))
+    (m,) = _mechs(ctx, wl)
+    m.set_states(torch.tensor(wl["x0"], device=f"cuda:{dev}"))
+    attach(m, sur, 1e-4)
+    v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
+    m.state(DT, v)
+    ms = _time(lambda: [m.state(DT, v) for _ in range(steps)], ctx, 1)
+    print({"instances": n, "steps": steps, "instance_steps_per_s": n * steps / (ms * 1e-3),
+           "fallback": m.stats()["fallback"]})
+    attach(m, None)
+    m.close()
+    sur.close()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    import sys
+    surrogate_kernel_case(n=int(sys.argv[1]) if len(sys.argv) > 1 else 4_000_000)

@@ -302,8 +302,9 @@ NMODL_API int64_t nmodl_cur_noalloc_max_instances(void);
 NMODL_API int nmodl_probe_peak(int device, int kind, double *ops_per_s);
 
 /* Diagnostic: y[i] = f(x[i]) on the device (x, y: device, n doubles),
- * f = the FP64 exp of the state kernels (fn 0: table-driven, Tang 1989) or
- * CUDA's exp (fn 1), so tests can measure the former's error in ulps. */
+ * f = the FP64 exp of the state kernels (fn 0: table-driven, Tang 1989),
+ * CUDA's exp (fn 1), or the round trip double -> float -> double through
+ * the kernels' integer-pipe conversions (fn 2), so tests can measure them. */
 NMODL_API int nmodl_math_eval(int fn, int64_t n, const double *x, double *y,
                               void *cuda_stream);
 

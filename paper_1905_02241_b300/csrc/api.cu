@@ -398,7 +398,8 @@ int nmodl_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
 
 // -------------------------------------------------------------- planning
 
-static size_t tile_smem_bytes(int T, const int* gates, int64_t NT, const int64_t* cnt) {
+// Shared memory of one tile, matching the layout in k_fused_tiles.
+static size_t tile_smem_bytes(int prec, int T, const int* gates, int64_t NT, const int64_t* cnt) {
     size_t b = 8 * (size_t)NT;
     size_t inst = 0, items = 0;
     for (int t = 0; t < T; ++t) {
@@ -406,12 +407,13 @@ static size_t tile_smem_bytes(int T, const int* gates, int64_t NT, const int64_t
         items += (size_t)gates[t] * cnt[t];
     }
     b += 8 * items + 2 * inst + 2 * (size_t)T * (NT + 1);
+    if (prec == NMODL_MIXED) b = (b + 15) / 16 * 16 + 4 * (size_t)NT;
     return (b + 15) / 16 * 16;
 }
 
 // Greedy tiling: fine blocks of G nodes are merged while the tile's shared
 // memory stays within budget; returns false if one fine block does not fit.
-static bool make_tiles(const std::vector<std::vector<int32_t>>& off, int T,
+static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, int T,
                        const int* gates, int64_t n_nodes, int G, size_t budget,
                        std::vector<int32_t>& recs, size_t& max_smem) {
     recs.clear();
@@ -428,7 +430,7 @@ static bool make_tiles(const std::vector<std::vector<int32_t>>& off, int T,
                 cnt[t] = off[t][b] - off[t][a];
                 if (cnt[t] > 65535) return false;
             }
-            return tile_smem_bytes(T, gates, NT, cnt.data()) <= budget;
+            return tile_smem_bytes(prec, T, gates, NT, cnt.data()) <= budget;
         };
         if (!fits(k0, k1)) return false;
         while (k1 < K && fits(k0, k1 + 1)) ++k1;
@@ -440,7 +442,7 @@ static bool make_tiles(const std::vector<std::vector<int32_t>>& off, int T,
             recs.push_back(off[t][k1]);
             cnt[t] = off[t][k1] - off[t][k0];
         }
-        max_smem = std::max(max_smem, tile_smem_bytes(T, gates, n1 - n0, cnt.data()));
+        max_smem = std::max(max_smem, tile_smem_bytes(prec, T, gates, n1 - n0, cnt.data()));
         k0 = k1;
     }
     return true;
@@ -548,7 +550,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     for (size_t b : budgets) {
         std::vector<int32_t> recs;
         size_t max_smem = 0;
-        if (b > cap || !make_tiles(off, T, gates, p->n_nodes, G, b, recs, max_smem)) {
+        if (b > cap || !make_tiles(p->precision, off, T, gates, p->n_nodes, G, b, recs, max_smem)) {
             if (dbg) std::fprintf(stderr, "[nmodl plan] budget %zu: no tiling\n", b);
             continue;
         }

@@ -166,6 +166,7 @@ __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
 //   state   st_s[sum_t gates_t * cnt_t]   (double, or float2 hi/lo in MIXED)
 //   uint16  nid_s[sum_t cnt_t]            local node id of each instance
 //   uint16  seg_s[T][NT + 1]              per-type segment offsets
+//   float   vf_s[NT]                      (MIXED) float copy of v, 16-aligned
 // Tile record (int32): n0, n1, then a_t, b_t per type (instance ranges).
 // The host plan guarantees NT <= 65535, cnt_t <= 65535 and that the layout
 // fits the dynamic shared memory of the launch.
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     __shared__ int pair_g[kMaxMechsFused * kMaxGates];
     __shared__ int pair_start[kMaxMechsFused * kMaxGates + 1];
     __shared__ int n_pairs;
+    __shared__ float phidt_f[kMaxMechsFused];
 
     __shared__ int tile_s;
 
@@ -226,6 +228,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     }
     __syncthreads();
     if (PREC == NMODL_MIXED) {
+        for (int k = tid; k < T; k += blockDim.x) phidt_f[k] = (float)(md_s[k].phi * A.dt);
         for (int k = tid; k < T * kMaxGates; k += blockDim.x) {
             const GateD& G = md_s[k / kMaxGates].gate[k % kMaxGates];
             gf_s[k / kMaxGates][k % kMaxGates] =
@@ -242,9 +245,17 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     float2* st_f = reinterpret_cast<float2*>(v_s + NT);        // MIXED states
     uint16_t* nid_s = reinterpret_cast<uint16_t*>(st_d + total_items);
     uint16_t* seg_s = nid_s + total_inst;
+    // MIXED: a float copy of v per node follows the per-type segment table,
+    // at the next 16-byte boundary
+    float* vf_s = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(seg_s + T * (NT + 1)) + 15) & ~(uintptr_t)15);
 
     // ---- load the tile
-    for (int k = tid; k < NT; k += blockDim.x) v_s[k] = A.v[n0 + k];
+    for (int k = tid; k < NT; k += blockDim.x) {
+        const double vv = A.v[n0 + k];
+        v_s[k] = vv;
+        if (PREC == NMODL_MIXED) vf_s[k] = d2f_int(vv);
+    }
     {
         int q = 0;
         for (int k = tid; k < total_items; k += blockDim.x) {
@@ -255,8 +266,8 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             if (PREC == NMODL_FP64) {
                 st_d[k] = m;
             } else {
-                const float hi = (float)m;
-                st_f[k] = make_float2(hi, (float)(m - (double)hi));
+                const float hi = d2f_int(m);
+                st_f[k] = make_float2(hi, d2f_int(m - f2d_int(hi)));
             }
         }
     }
@@ -298,7 +309,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                         cur_cnexp_d(M, st_d + st_off[t], cnt, j, vv, ci, gi);
                     } else {
                         const float2* st = st_f + st_off[t];
-                        const float vf = (float)vv;
+                        const float vf = vf_s[n];
                         float gf, cf;
                         if (M.kind == NMODL_HH) {
                             const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
@@ -316,8 +327,8 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                             }
                             cf = gf * (vf - (float)M.e);
                         }
-                        ci = (double)cf;
-                        gi = (double)gf;
+                        ci = f2d_int(cf);
+                        gi = f2d_int(gf);
                     }
                     r -= ci;
                     dd += gi;
@@ -330,6 +341,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 A.d[n0 + n] = dd;
             }
             v_s[n] = vn;
+            if (PREC == NMODL_MIXED) vf_s[n] = d2f_int(vn);
         }
         __syncthreads();
         // ---- state update, one thread per (instance, gate) item
@@ -338,13 +350,13 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             while (k >= pair_start[q + 1]) ++q;
             const int t = pair_t[q], g = pair_g[q];
             const int j = k - pair_start[q];
-            const double vv = v_s[nid_s[nid_off[t] + j]];
             if (PREC == NMODL_FP64) {
+                const double vv = v_s[nid_s[nid_off[t] + j]];
                 const GateD& G = md_s[t].gate[g];
                 st_d[k] = gate_step_fast_d(G, md_s[t].phi * A.dt, vv, st_d[k]);
             } else {
                 float minf, f;
-                gate_coef_f(gf_s[t][g], (float)(md_s[t].phi * A.dt), (float)vv, minf, f);
+                gate_coef_f(gf_s[t][g], phidt_f[t], vf_s[nid_s[nid_off[t] + j]], minf, f);
                 float2 m = st_f[k];
                 const float delta = f * ((minf - m.x) - m.y);
                 float s, e;
@@ -373,7 +385,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             const int j = k - pair_start[q];
             double m;
             if (PREC == NMODL_FP64) m = st_d[k];
-            else m = (double)st_f[k].x + (double)st_f[k].y;
+            else m = f2d_int(st_f[k].x) + f2d_int(st_f[k].y);
             if (!isfinite(m)) latch_error(A.err, NMODL_ERR_NONFINITE);
             A.states[t][g * A.stride[t] + a_s[t] + j] = m;
         }

@@ -164,8 +164,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
             if (i < a.n) {
                 float xf[9], dkf[kKinEdges], dkb[kKinEdges], z[9];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) xf[k] = (float)a.st[k * a.stride + i];
-                const float vf = (float)a.v[a.ni[i]];
+                for (int k = 0; k < 9; ++k) xf[k] = d2f_int(a.st[k * a.stride + i]);
+                const float vf = d2f_int(a.v[a.ni[i]]);
                 kin_rates_f(K, vf, dtf, dkf, dkb);
                 dtAx_f(dkf, dkb, xf, z);
                 ss[lane] = sur_inputs(a.scaled, vf, dtf, xf, z, f);
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
             fail = !(rn <= a.tol);
             if (!fail) {
 #pragma unroll
-                for (int k = 0; k < 9; ++k) a.st[k * a.stride + i] = (double)w[k];
+                for (int k = 0; k < 9; ++k) a.st[k * a.stride + i] = f2d_int(w[k]);
             }
         }
         const unsigned mask = __ballot_sync(0xffffffffu, fail);

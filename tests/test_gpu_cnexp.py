@@ -302,8 +302,9 @@ def test_full_size_sampled_parity(api, orc):
 
 
 def test_table_exp_ulp_error():
-    """The FP64 exp of the state kernels (Tang's table-driven method) against
-    mpmath at 40 digits and against CUDA's exp: at most 1 ulp."""
+    """The FP64 exp of the state kernels (Tang's table-driven method, 64-entry
+    table, degree-5 polynomial) against mpmath at 40 digits and against
+    CUDA's exp: within 1.5 ulp (table entries are rounded to double)."""
     import mpmath
     from paper_1905_02241_b300 import _lib
     mpmath.mp.dps = 40
@@ -324,5 +325,30 @@ def test_table_exp_ulp_error():
         ulp = np.spacing(float(ref))
         worst = max(worst, abs(float(mpmath.mpf(float(y[i])) - ref)) / ulp)
     print(f"table exp: max error {worst:.3f} ulp (3000 samples vs mpmath)")
-    assert worst <= 1.0
-    assert np.max(np.abs(y - yc) / np.abs(yc)) <= 2.5e-16
+    assert worst <= 1.5
+    assert np.max(np.abs(y - yc) / np.abs(yc)) <= 5e-16
+
+
+def test_integer_pipe_conversions_round_like_hardware():
+    """double -> float -> double through the integer-pipe conversions equals
+    numpy's float32 rounding bit for bit (ties, carries into the exponent,
+    zeros, subnormal and huge values included)."""
+    from paper_1905_02241_b300 import _lib
+    rng = np.random.default_rng(5)
+    f = rng.uniform(-1, 1, 20000).astype(np.float32).astype(np.float64)
+    ulp = np.spacing(np.abs(f).astype(np.float32)).astype(np.float64)
+    x = np.concatenate([
+        rng.uniform(-1, 1, 50000), rng.uniform(0, 1, 50000) * 10.0 ** rng.integers(-40, 40, 50000),
+        f + 0.5 * ulp, f - 0.5 * ulp, f + 0.5 * ulp * (1 + 2e-16),   # ties and near-ties
+        [0.0, -0.0, 1e-300, -1e-310, 3.4028234663852886e38, 3.5e38, 1.1754943508222875e-38,
+         1.0 - 2 ** -25, 2.0 - 2 ** -24]])
+    xd = to_dev(x)
+    y = torch.empty_like(xd)
+    _lib.nmodl_math_eval(2, x.size, xd.data_ptr(), y.data_ptr(), 0)
+    torch.cuda.synchronize()
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float32).astype(np.float64)
+    got = y.cpu().numpy()
+    same = (got == ref) | (np.isnan(got) & np.isnan(ref))
+    assert same.all(), x[~same][:5]
+    assert np.array_equal(np.signbit(got), np.signbit(ref))

@@ -171,9 +171,8 @@ def main():
                     help="comma list of batched,kinetic,surrogate,mixed_errors; all; none")
     args = ap.parse_args()
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1905_02241_b300.sharding import aggregate, network_seed, rank_info
+    rank, world, local = rank_info()
     config = {"workload": f"cortical 10-type cnexp mix, {args.nodes} nodes, "
                           f"{NSTEPS} steps of dt {DT} ms, {args.precision}",
               "nodes": args.nodes, "steps_per_bench_step": NSTEPS, "dt_ms": DT,
@@ -213,7 +212,7 @@ def main():
     from paper_1905_02241_b300 import _lib
     from paper_1905_02241_b300.api import NMODL_FP64, NMODL_MIXED, Context, Mechanism
 
-    wl = W.cortical_mix(args.nodes, seed=2 + 1000 * rank)
+    wl = W.cortical_mix(args.nodes, seed=network_seed(2, rank))
     prec = NMODL_FP64 if args.precision == "fp64" else NMODL_MIXED
     ctx = Context(dev, precision=prec)
     mechs = [Mechanism(ctx, m["type"], m["node_index"], wl["n_nodes"], m["params"])
@@ -256,14 +255,10 @@ def main():
     ms = e0.elapsed_time(e1)
     clk = clocks.stop() if clocks else None
     assert ctx.sync() == 0
-    if dist:
-        t = torch.tensor([ms], device=v.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    value, ms = aggregate(ms, float(ninst) * NSTEPS * args.steps, dist, v.device)
     window = ctx.options.window
     launches_per_step = -(-NSTEPS // window)
     gpu_launches = launches_per_step * args.steps
-    value = world * ninst * NSTEPS * args.steps / (ms * 1e-3)
 
     # roofline of the dominant kernel (the fused tile kernel: the whole step)
     launch_ms = ms / gpu_launches

@@ -352,3 +352,34 @@ def test_integer_pipe_conversions_round_like_hardware():
     same = (got == ref) | (np.isnan(got) & np.isnan(ref))
     assert same.all(), x[~same][:5]
     assert np.array_equal(np.signbit(got), np.signbit(ref))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_checkpoint_resume_is_bitwise(api, prec):
+    """Save states and v mid-run (nmodl_get_state), restore them into a new
+    context (nmodl_set_state) and continue: the continuation is bitwise equal
+    to the uninterrupted run."""
+    p = api.NMODL_FP64 if prec == "fp64" else api.NMODL_MIXED
+    wl = W.cortical_mix(3001, seed=15)
+    n = wl["n_nodes"]
+    ctx = _ctx(api, precision=p)
+    mechs = make_mechs(ctx, wl)
+    v, rhs, d = to_dev(wl["v0"]), to_dev(np.zeros(n)), to_dev(np.zeros(n))
+    for m in mechs:
+        m.init(v)
+    ctx.step(mechs, 0.025, 1.0, v, rhs, d, 40)
+    ckpt_v = v.clone()
+    ckpt = [m.states().clone() for m in mechs]
+    ctx.step(mechs, 0.025, 1.0, v, rhs, d, 40)
+    ref_v, ref_s = v.clone(), [m.states() for m in mechs]
+    ctx2 = _ctx(api, precision=p)
+    mechs2 = make_mechs(ctx2, wl)
+    for m, s in zip(mechs2, ckpt):
+        if m.n_states:
+            m.set_states(s)
+    v2, rhs2, d2 = ckpt_v.clone(), to_dev(np.zeros(n)), to_dev(np.zeros(n))
+    ctx2.step(mechs2, 0.025, 1.0, v2, rhs2, d2, 40)
+    assert torch.equal(v2, ref_v)
+    for m, s in zip(mechs2, ref_s):
+        assert torch.equal(m.states(), s)
+    assert ctx.sync() == 0 and ctx2.sync() == 0

@@ -105,7 +105,11 @@ typedef struct nmodl_options {
     int32_t tile_smem;       /* fused tile shared-memory budget, bytes (0 =
                                 chosen by the autotuner / default)          */
     int32_t block;           /* fused kernel block size (0 = auto)           */
-    int32_t reserved[5];
+    int32_t cnexp_pade;      /* 1: cnexp with exp(-x) replaced by its (1,1)
+                                Pade approximant (1 - x/2)/(1 + x/2), the
+                                cheaper form of Section 5.2; second order,
+                                A- but not L-stable (0)                     */
+    int32_t reserved[4];
 } nmodl_options;
 
 typedef struct nmodl_stats_t {

@@ -139,6 +139,19 @@ static void cnexp_like_init(int type, int64_t n, const int32_t *ni,
     }
 }
 
+/* Integration factor of the gate update over x = dt/mtau: 1 - exp(-x)
+ * (cnexp, Section 5.2), or with exp(-x) replaced by its (1,1) Pade
+ * approximant (1 - x/2)/(1 + x/2) (the optional cheaper form the paper
+ * names in Section 5.2). */
+int orc_pade_mode = 0;
+
+double orc_cnexp_factor(double x)
+{
+    if (orc_pade_mode)
+        return 1.0 - (1.0 - x / 2.0) / (1.0 + x / 2.0);
+    return 1.0 - exp(-x);
+}
+
 /* cnexp (Section 5.2): exact solution of m' = (minf - m)/mtau over dt with
  * minf, mtau frozen at the new voltage. */
 static void cnexp_like_state(int type, int64_t n, const int32_t *ni,
@@ -157,7 +170,7 @@ static void cnexp_like_state(int type, int64_t n, const int32_t *ni,
         }
         for (int g = 0; g < ng; ++g) {
             double m = s[g * n + i];
-            s[g * n + i] = m + (1.0 - exp(-dt / mtau[g])) * (minf[g] - m);
+            s[g * n + i] = m + orc_cnexp_factor(dt / mtau[g]) * (minf[g] - m);
         }
     }
 }

@@ -72,6 +72,8 @@ def lib():
         L.orc_lu_solve.argtypes = [ctypes.c_int, vp, vp, vp, vp]
         L.orc_step.argtypes = [ctypes.c_int, vp, i64, d, d, vp, vp, vp,
                                ctypes.c_int, ctypes.c_int, d, ctypes.c_int]
+        L.orc_cnexp_factor.restype = d
+        L.orc_cnexp_factor.argtypes = [d]
         _ = (P, i32)
         _lib = L
     return _lib
@@ -359,3 +361,20 @@ def kin9_residual(params, v, dt, x_old, y):
         A = kin9_matrix(params, v[c])
         R[:, c] = y[:, c] - x_old[:, c] - dt * (A @ y[:, c])
     return R
+
+
+class pade_mode:
+    """Context manager: cnexp with the (1,1) Pade approximant of exp(-x)
+    (Section 5.2) inside the block."""
+
+    def __enter__(self):
+        ctypes.c_int.in_dll(lib(), "orc_pade_mode").value = 1
+        return self
+
+    def __exit__(self, *exc):
+        ctypes.c_int.in_dll(lib(), "orc_pade_mode").value = 0
+        return False
+
+
+def cnexp_factor(x: float) -> float:
+    return lib().orc_cnexp_factor(float(x))

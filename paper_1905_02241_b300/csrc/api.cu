@@ -181,6 +181,7 @@ static int check_options(const nmodl_options* o) {
     if (!(o->newton_tol >= 0.0)) return NMODL_ERR_ARG;
     if (o->ir_max < 0 || o->ir_max > 64) return NMODL_ERR_ARG;
     if (o->window < 1) return NMODL_ERR_ARG;
+    if (o->cnexp_pade != 0 && o->cnexp_pade != 1) return NMODL_ERR_ARG;
     if (o->tile_smem < 0 || o->block < 0 || o->block > kFusedMaxBlock || (o->block % 32))
         return NMODL_ERR_ARG;
     return NMODL_OK;
@@ -363,7 +364,7 @@ static void enqueue_state(nmodl_mech* m, double dt, const double* v) {
                           nullptr, m->d_cnt, c->d_err, c->stream);
     else
         launch_state_gates(o.precision, m->d_md, m->n_states, m->n, m->d_ni, v,
-                           m->d_states, m->stride, dt, c->d_err, c->stream);
+                           m->d_states, m->stride, dt, o.cnexp_pade, c->d_err, c->stream);
 }
 
 // host-side counters of state updates (kept here, not at enqueue time, so
@@ -630,6 +631,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
             a.tile_counter = cd.persistent ? d_counter : nullptr;
             a.nsteps = trial_steps;
             a.clamp_v = c->opt.clamp_v;
+            a.pade = c->opt.cnexp_pade;
             a.v = sv;
             a.rhs = srhs;
             a.d = sd;
@@ -738,6 +740,7 @@ static FusedArgs fused_args(nmodl_ctx* c, Plan* p, double dt, double cm, double*
     a.tile_counter = p->persistent ? p->d_counter : nullptr;
     a.nsteps = nsteps;
     a.clamp_v = c->opt.clamp_v;
+    a.pade = c->opt.cnexp_pade;
     a.v = v;
     a.rhs = rhs;
     a.d = d;

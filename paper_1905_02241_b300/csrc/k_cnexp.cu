@@ -39,7 +39,7 @@ template <int PREC>
 __global__ void k_state_gates(const MechD* __restrict__ md, int64_t n,
                               const int32_t* __restrict__ ni,
                               const double* __restrict__ v, double* states,
-                              int64_t stride, double dt, int32_t* err) {
+                              int64_t stride, double dt, int pade, int32_t* err) {
     const int g = blockIdx.y;
     const GateD G = md->gate[g];
     const double phidt = md->phi * dt;
@@ -47,7 +47,8 @@ __global__ void k_state_gates(const MechD* __restrict__ md, int64_t n,
     if (PREC == NMODL_FP64) {
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
              i += (int64_t)gridDim.x * blockDim.x) {
-            const double m = gate_step_fast_d(G, phidt, v[ni[i]], row[i]);
+            const double m = pade ? gate_step_pade_d(G, phidt, v[ni[i]], row[i])
+                                  : gate_step_fast_d(G, phidt, v[ni[i]], row[i]);
             if (!isfinite(m)) latch_error(err, NMODL_ERR_NONFINITE);
             row[i] = m;
         }
@@ -59,7 +60,7 @@ __global__ void k_state_gates(const MechD* __restrict__ md, int64_t n,
              i += (int64_t)gridDim.x * blockDim.x) {
             const double m = row[i];
             float minf, f;
-            gate_coef_f(F, phidtf, (float)v[ni[i]], minf, f);
+            gate_coef_f(F, phidtf, (float)v[ni[i]], minf, f, pade != 0);
             // FP32 increment from the FP32-rounded state, added in FP64
             const float delta = f * (minf - (float)m);
             const double mn = m + (double)delta;
@@ -353,10 +354,12 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             if (PREC == NMODL_FP64) {
                 const double vv = v_s[nid_s[nid_off[t] + j]];
                 const GateD& G = md_s[t].gate[g];
-                st_d[k] = gate_step_fast_d(G, md_s[t].phi * A.dt, vv, st_d[k]);
+                st_d[k] = A.pade ? gate_step_pade_d(G, md_s[t].phi * A.dt, vv, st_d[k])
+                                 : gate_step_fast_d(G, md_s[t].phi * A.dt, vv, st_d[k]);
             } else {
                 float minf, f;
-                gate_coef_f(gf_s[t][g], phidt_f[t], vf_s[nid_s[nid_off[t] + j]], minf, f);
+                gate_coef_f(gf_s[t][g], phidt_f[t], vf_s[nid_s[nid_off[t] + j]], minf, f,
+                            A.pade != 0);
                 float2 m = st_f[k];
                 const float delta = f * ((minf - m.x) - m.y);
                 float s, e;
@@ -412,13 +415,14 @@ void launch_init_gates(const MechD* md, int n_gates, int64_t n, const int32_t* n
 
 void launch_state_gates(int prec, const MechD* md, int n_gates, int64_t n,
                         const int32_t* ni, const double* v, double* st,
-                        int64_t stride, double dt, int32_t* err, cudaStream_t s) {
+                        int64_t stride, double dt, int pade, int32_t* err,
+                        cudaStream_t s) {
     if (n == 0 || n_gates == 0) return;
     dim3 grid(grid_for(n, 256), n_gates);
     if (prec == NMODL_FP64)
-        k_state_gates<NMODL_FP64><<<grid, 256, 0, s>>>(md, n, ni, v, st, stride, dt, err);
+        k_state_gates<NMODL_FP64><<<grid, 256, 0, s>>>(md, n, ni, v, st, stride, dt, pade, err);
     else
-        k_state_gates<NMODL_MIXED><<<grid, 256, 0, s>>>(md, n, ni, v, st, stride, dt, err);
+        k_state_gates<NMODL_MIXED><<<grid, 256, 0, s>>>(md, n, ni, v, st, stride, dt, pade, err);
 }
 
 void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,

@@ -22,7 +22,7 @@ struct FusedArgs {
     int32_t* tile_counter;                 // persistent form: next tile
     int32_t nsteps;
     int32_t clamp_v;
-    int32_t pad;
+    int32_t pade;                          // (1,1) Pade cnexp factor
     double* v;
     double* rhs;
     double* d;
@@ -35,7 +35,8 @@ void launch_init_gates(const MechD* md, int n_gates, int64_t n, const int32_t* n
                        cudaStream_t s);
 void launch_state_gates(int prec, const MechD* md, int n_gates, int64_t n,
                         const int32_t* ni, const double* v, double* st,
-                        int64_t stride, double dt, int32_t* err, cudaStream_t s);
+                        int64_t stride, double dt, int pade, int32_t* err,
+                        cudaStream_t s);
 void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
                     const int32_t* chunk, const int32_t* ni, const double* v,
                     const double* st, int64_t stride, double* rhs, double* d,

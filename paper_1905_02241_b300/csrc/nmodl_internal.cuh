@@ -144,6 +144,22 @@ __device__ __forceinline__ double gate_step_d(const GateD& G, double phidt,
     return m + f * (minf - m);
 }
 
+// The same step with exp(-x), x = phi dt (alpha + beta), replaced by its
+// (1,1) Pade approximant: the factor 2x/(2 + x) folds into the one division,
+// m += 2 c (Pa Db - m N) / (2 D + c N) with c = phi dt.
+__device__ __forceinline__ double gate_step_pade_d(const GateD& G, double phidt, double v,
+                                                   double m) {
+    double na, da, nb, db;
+    rate_nd(G.aform, G.aA, G.avh, G.ark, v, na, da);
+    rate_nd(G.bform, G.bA, G.bvh, G.brk, v, nb, db);
+    const double P = na * db;
+    const double N = fma(nb, da, P);
+    const double D = da * db;
+    const double num = 2.0 * phidt * fma(-m, N, P);
+    const double den = fma(phidt, N, D + D);
+    return m + num * __drcp_rn(den);
+}
+
 __device__ __forceinline__ double gate_inf_d(const GateD& G, double v) {
     const double a = rate_d(G.aform, G.aA, G.avh, G.ark, v);
     const double b = rate_d(G.bform, G.bA, G.bvh, G.brk, v);
@@ -189,14 +205,16 @@ struct GateF {
     int32_t aform, bform;
 };
 
-// (minf, 1 - exp(-dt/mtau)) of a gate in FP32
+// (minf, 1 - exp(-dt/mtau)) of a gate in FP32; with pade the factor is the
+// (1,1) Pade form x/(1 + x/2)
 __device__ __forceinline__ void gate_coef_f(const GateF& G, float phidt, float v,
-                                            float& minf, float& f) {
+                                            float& minf, float& f, bool pade = false) {
     const float a = rate_f(G.aform, G.aA, G.avh, G.ark, v);
     const float b = rate_f(G.bform, G.bA, G.bvh, G.brk, v);
     const float s = a + b;
     minf = __fdividef(a, s);
-    f = one_minus_expneg_f(phidt * s);
+    const float x = phidt * s;
+    f = pade ? __fdividef(x, fmaf(0.5f, x, 1.0f)) : one_minus_expneg_f(x);
 }
 
 // Conversions between float and double on the integer pipe (the FP64 pipe

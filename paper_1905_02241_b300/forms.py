@@ -85,6 +85,38 @@ def batched(dev, steps=2, nsteps=200, scale=1.0):
     return out
 
 
+def pade(dev, n_nodes=2_000_000, nsteps=200):
+    """(1,1) Pade cnexp (Section 5.2 option) against exact cnexp, both FP64,
+    on the cortical mix: throughput ratio and the state / voltage difference
+    after nsteps from the same initial condition."""
+    wl = W.cortical_mix(n_nodes, seed=2)
+    ninst = _ninst(wl)
+    out = {"nodes": n_nodes, "instances": ninst, "steps_per_run": nsteps}
+    res = {}
+    for name, flag in (("exact", 0), ("pade", 1)):
+        ctx = Context(dev, cnexp_pade=flag)
+        mechs = _mechs(ctx, wl)
+        v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
+        rhs = torch.zeros_like(v)
+        d = torch.zeros_like(v)
+        for m in mechs:
+            m.init(v)
+        ctx.step(mechs, DT, CM, v, rhs, d, nsteps)       # plan, graphs, result
+        res[name] = (v.clone(), [m.states() for m in mechs if m.n_states])
+        ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
+        out[name] = ninst * nsteps / (ms * 1e-3)
+        for m in mechs:
+            m.close()
+        ctx.close()
+    (ve, se), (vp, sp) = res["exact"], res["pade"]
+    out["pade_over_exact"] = out["pade"] / out["exact"]
+    out["v_abs_mV_max"] = float((vp - ve).abs().max())
+    out["v_abs_mV_median"] = float((vp - ve).abs().median())
+    out["state_abs_max"] = float(max((a - b).abs().max() for a, b in zip(sp, se)))
+    out["state_abs_mean"] = float(sum((a - b).abs().mean() for a, b in zip(sp, se)) / len(sp))
+    return out
+
+
 def mixed_errors(dev, n_nodes=1500, nsteps=200):
     """Per-quantity error of the MIXED fused step against the FP64 oracle on
     a sub-network of the cortical mix (max over nodes / instances)."""

@@ -383,3 +383,25 @@ def test_checkpoint_resume_is_bitwise(api, prec):
     for m, s in zip(mechs2, ref_s):
         assert torch.equal(m.states(), s)
     assert ctx.sync() == 0 and ctx2.sync() == 0
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_pade_cnexp_parity(api, orc, fused):
+    """(1,1) Pade cnexp (Section 5.2 option) against the oracle's Pade mode:
+    one-step states at 1e-12 and 20 network steps, fused and standalone."""
+    wl = W.cortical_mix(2001, seed=16, v_lo=-100, v_hi=60)
+    opts = dict(cnexp_pade=1) if fused else dict(cnexp_pade=1, tile_smem=64)
+    ctx = _ctx(api, **opts)
+    mechs = make_mechs(ctx, wl)
+    st0 = _random_states(wl, 8)
+    v = to_dev(wl["v0"])
+    with orc.pade_mode():
+        for m, s, spec in zip(mechs, st0, wl["mechs"]):
+            if not m.n_states:
+                continue
+            m.set_states(to_dev(s))
+            m.state(0.025, v)
+            ref = orc.mech_state(spec["type"], spec["params"], spec["node_index"],
+                                 wl["v0"], s, 0.025)
+            assert state_err(m.states().cpu().numpy(), ref) <= TOL_FP64
+        _step_case(api, orc, wl, 20, 1e-10, **opts)

@@ -580,3 +580,29 @@ def test_kin9_residual_vanishes_at_dense_solution(orc):
     r = orc.kin9_residual(p, v, 0.025, x, x)   # y = x leaves -dt A x
     assert np.max(np.abs(r.sum(axis=0))) < 1e-15   # columns of A sum to 0
     assert np.max(np.abs(r)) > 1e-6
+
+
+def test_pade_factor_and_second_order(orc):
+    """(1,1) Pade cnexp: the factor is 2x/(2+x), it matches 1 - exp(-x) to
+    x^3/12 + O(x^4), and the clamped-v gate converges at second order to the
+    exact cnexp solution."""
+    for x in (1e-3, 1e-2, 0.1, 0.5):
+        with orc.pade_mode():
+            f = orc.cnexp_factor(x)
+        assert abs(f - 2 * x / (2 + x)) <= 2.5e-16 + 1e-15 * f  # 1 - R cancels
+        assert abs(f - (1 - np.exp(-x))) <= x ** 3 / 12 * 1.2 + 1e-17
+    assert orc.cnexp_factor(0.3) == 1 - np.exp(-0.3)      # default: exact
+    p = cortical_blocks()[1]
+    v = np.array([-30.0])
+    ni = np.zeros(1, dtype=np.int32)
+    minf, mtau = orc.cnexp_rates(p, 0, v[0])
+    T, m0 = 2.0, np.array([[0.05]])
+    exact = minf + (m0[0, 0] - minf) * np.exp(-T / mtau)
+    errs = []
+    for dt in (0.1, 0.05, 0.025):
+        s = m0.copy()
+        with orc.pade_mode():
+            for _ in range(int(round(T / dt))):
+                s = orc.mech_state(W.TYPE_CNEXP, p, ni, v, s, dt)
+        errs.append(abs(s[0, 0] - exact))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs

@@ -453,3 +453,72 @@ void orc_step(int n_mechs, const orc_mech *mechs, int64_t n_nodes, double dt,
                            max_iter, NULL);
     }
 }
+
+/* ------------------------------------------------------------- cable */
+
+/* One cable step per cell (reading: NEURON's implicit step with the
+ * cable's tree matrix, the "Other" time of Table 2): the membrane system of
+ * orc_step plus, for every non-root node i with parent p, the axial
+ * conductances ga[i] (per unit area of i) and gb[i] (per unit area of p):
+ *   rhs[i] += ga[i] (v[p] - v[i]),  rhs[p] += gb[i] (v[i] - v[p]),
+ *   d[i] += ga[i], d[p] += gb[i],   M[i][p] = -ga[i], M[p][i] = -gb[i],
+ * then M dv = rhs is solved per cell by the dense partial-pivot LU and
+ * v += dv.  Cells are the contiguous node ranges that start at a root
+ * (parent -1); parent[i] < i inside a cell. */
+void orc_step_cable(int n_mechs, const orc_mech *mechs, int64_t n_nodes,
+                    const int32_t *parent, const double *ga, const double *gb,
+                    double dt, double cm, double *v, double *rhs, double *d,
+                    int nsteps, double tol, int max_iter)
+{
+    for (int st = 0; st < nsteps; ++st) {
+        for (int64_t k = 0; k < n_nodes; ++k) {
+            rhs[k] = 0.0;
+            d[k] = 0.0;
+        }
+        for (int m = 0; m < n_mechs; ++m)
+            orc_mech_cur(mechs[m].type, mechs[m].n, mechs[m].node_index, v,
+                         mechs[m].params, mechs[m].states, rhs, d);
+        for (int64_t k = 0; k < n_nodes; ++k)
+            d[k] += 1e-3 * cm / dt;
+        for (int64_t k = 0; k < n_nodes; ++k) {
+            int64_t p = parent[k];
+            if (p < 0) continue;
+            rhs[k] += ga[k] * (v[p] - v[k]);
+            rhs[p] += gb[k] * (v[k] - v[p]);
+            d[k] += ga[k];
+            d[p] += gb[k];
+        }
+        int64_t c0 = 0;
+        while (c0 < n_nodes) {
+            int64_t c1 = c0 + 1;
+            while (c1 < n_nodes && parent[c1] >= 0) ++c1;
+            int n = (int)(c1 - c0);
+            double *M = (double *)calloc((size_t)n * n, sizeof(double));
+            double *b = (double *)malloc(sizeof(double) * n);
+            double *x = (double *)malloc(sizeof(double) * n);
+            int *perm = (int *)malloc(sizeof(int) * n);
+            for (int i = 0; i < n; ++i) {
+                M[i * n + i] = d[c0 + i];
+                b[i] = rhs[c0 + i];
+                if (i > 0) {
+                    int pp = (int)(parent[c0 + i] - c0);
+                    M[i * n + pp] = -ga[c0 + i];
+                    M[pp * n + i] = -gb[c0 + i];
+                }
+            }
+            orc_lu_pp(n, M, perm);
+            orc_lu_solve(n, M, perm, b, x);
+            for (int i = 0; i < n; ++i)
+                v[c0 + i] += x[i];
+            free(M);
+            free(b);
+            free(x);
+            free(perm);
+            c0 = c1;
+        }
+        for (int m = 0; m < n_mechs; ++m)
+            orc_mech_state(mechs[m].type, mechs[m].n, mechs[m].node_index, v,
+                           mechs[m].params, dt, mechs[m].states, tol,
+                           max_iter, NULL);
+    }
+}

@@ -72,6 +72,8 @@ def lib():
         L.orc_lu_solve.argtypes = [ctypes.c_int, vp, vp, vp, vp]
         L.orc_step.argtypes = [ctypes.c_int, vp, i64, d, d, vp, vp, vp,
                                ctypes.c_int, ctypes.c_int, d, ctypes.c_int]
+        L.orc_step_cable.argtypes = [ctypes.c_int, vp, i64, vp, vp, vp, d, d, vp, vp,
+                                     vp, ctypes.c_int, d, ctypes.c_int]
         L.orc_cnexp_factor.restype = d
         L.orc_cnexp_factor.argtypes = [d]
         _ = (P, i32)
@@ -378,3 +380,29 @@ class pade_mode:
 
 def cnexp_factor(x: float) -> float:
     return lib().orc_cnexp_factor(float(x))
+
+
+def step_cable(mechs, states, v, n_nodes, parent, ga, gb, dt, cm=1.0, nsteps=1,
+               tol=NEWTON_TOL, max_iter=NEWTON_MAX_ITER):
+    """nsteps cable steps (orc_step_cable); returns (v, rhs, d, states) with
+    rhs/d the last step's assembled values (before the solve)."""
+    keep = []
+    arr = (_OrcMech * len(mechs))()
+    out_states = []
+    for k, m in enumerate(mechs):
+        p, ni = _f64(m["params"]), _i32(m["node_index"])
+        s = _f64(states[k]).copy()
+        keep += [p, ni]
+        out_states.append(s)
+        arr[k].type = int(m["type"])
+        arr[k].n = ni.size
+        arr[k].node_index = ni.ctypes.data
+        arr[k].params = p.ctypes.data
+        arr[k].states = s.ctypes.data
+    vv = _f64(v).copy()
+    rhs, d = np.zeros(n_nodes), np.zeros(n_nodes)
+    par, a, b = _i32(parent), _f64(ga), _f64(gb)
+    lib().orc_step_cable(len(mechs), ctypes.cast(arr, ctypes.c_void_p), int(n_nodes),
+                         _p(par), _p(a), _p(b), float(dt), float(cm), _p(vv), _p(rhs),
+                         _p(d), int(nsteps), float(tol), int(max_iter))
+    return vv, rhs, d, out_states

@@ -315,3 +315,33 @@ def mlp_init(seed: int, widths=(11, 128, 128, 128, 9), out_scale: float = 0.1):
         Ws.append(s.uniform(fo * fi, -lim, lim).reshape(fo, fi))
         bs.append(np.zeros(fo))
     return Ws, bs
+
+
+def cable_cells(n_cells: int, seed: int = 7, size_lo: int = 20, size_hi: int = 400,
+                branch_p: float = 0.15):
+    """Tree morphologies of n_cells cells on consecutive node ranges.
+
+    parent[i] = -1 at the root of each cell; otherwise the previous node
+    (unbranched run) or, with probability branch_p, a random earlier node of
+    the same cell (a branch point).  ga ~ logU[0.5, 50] S/cm2 per unit area
+    of the node, gb = ga * r with the area ratio r ~ U[0.5, 2].
+    Returns dict(parent, ga, gb, offsets)."""
+    s = Stream(seed, 801)
+    sizes = s.integers(n_cells, size_lo, size_hi)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(offsets[-1])
+    parent = np.empty(n, dtype=np.int32)
+    u = s.uniform(n)
+    r = s.uniform(n)
+    for c in range(n_cells):
+        a, b = offsets[c], offsets[c + 1]
+        parent[a] = -1
+        idx = np.arange(a + 1, b)
+        prev = idx - 1
+        rnd = a + np.floor(r[a + 1:b] * (idx - a)).astype(np.int64)
+        parent[a + 1:b] = np.where(u[a + 1:b] < branch_p, rnd, prev)
+    ga = s.loguniform(n, 0.5, 50.0)
+    gb = ga * s.uniform(n, 0.5, 2.0)
+    ga[offsets[:-1]] = 0.0
+    gb[offsets[:-1]] = 0.0
+    return dict(parent=parent, ga=ga, gb=gb, offsets=offsets, n_nodes=n)

@@ -606,3 +606,64 @@ def test_pade_factor_and_second_order(orc):
                 s = orc.mech_state(W.TYPE_CNEXP, p, ni, v, s, dt)
         errs.append(abs(s[0, 0] - exact))
     assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+
+
+def _cable_case(seed=3, n_cells=6):
+    cab = W.cable_cells(n_cells, seed=seed, size_lo=4, size_hi=25)
+    wl = W.cortical_mix(cab["n_nodes"], seed=seed + 10)
+    return cab, wl
+
+
+def test_cable_without_coupling_is_the_isolated_step(orc):
+    cab, wl = _cable_case()
+    st = [orc.mech_init(m["type"], m["params"], m["node_index"], wl["v0"])
+          for m in wl["mechs"]]
+    z = np.zeros(cab["n_nodes"])
+    a = orc.step_cable(wl["mechs"], st, wl["v0"], cab["n_nodes"], cab["parent"], z, z,
+                       0.025, nsteps=3)
+    b = orc.step(wl["mechs"], st, wl["v0"], cab["n_nodes"], 0.025, nsteps=3)
+    np.testing.assert_allclose(a[0], b[0], rtol=1e-15, atol=1e-13)
+    np.testing.assert_array_equal(a[2], b[2])
+
+
+def test_cable_step_solves_the_assembled_tree_system(orc):
+    """v_new - v = M^-1 rhs with M, rhs assembled here from the membrane
+    terms (rhs0, d0 of the uncoupled step) and the axial conductances."""
+    cab, wl = _cable_case(seed=4)
+    n = cab["n_nodes"]
+    st = [orc.mech_init(m["type"], m["params"], m["node_index"], wl["v0"])
+          for m in wl["mechs"]]
+    _, rhs0, d0, _ = orc.step(wl["mechs"], st, wl["v0"], n, 0.025, nsteps=1)
+    v1, rhs1, d1, _ = orc.step_cable(wl["mechs"], st, wl["v0"], n, cab["parent"], cab["ga"],
+                                     cab["gb"], 0.025, nsteps=1)
+    M = np.diag(d0.copy())
+    r = rhs0.copy()
+    v0 = wl["v0"]
+    for i in range(n):
+        p = cab["parent"][i]
+        if p < 0:
+            continue
+        M[i, i] += cab["ga"][i]
+        M[p, p] += cab["gb"][i]
+        M[i, p] -= cab["ga"][i]
+        M[p, i] -= cab["gb"][i]
+        r[i] += cab["ga"][i] * (v0[p] - v0[i])
+        r[p] += cab["gb"][i] * (v0[i] - v0[p])
+    np.testing.assert_allclose(v1 - v0, np.linalg.solve(M, r), rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(d1, np.diag(M), rtol=1e-14)
+    np.testing.assert_allclose(rhs1, r, rtol=1e-12, atol=1e-14)
+
+
+def test_cable_symmetric_twins_carry_no_axial_current(orc):
+    """Two identical compartments coupled symmetrically, with the same state
+    and voltage, evolve exactly like one uncoupled compartment."""
+    ni = np.array([0, 1], dtype=np.int32)
+    mech = dict(type=W.TYPE_HH, params=W.hh_params(), node_index=ni)
+    v0 = np.array([-58.0, -58.0])
+    s0 = orc.mech_init(W.TYPE_HH, W.hh_params(), ni, v0)
+    parent = np.array([-1, 0], dtype=np.int32)
+    g = np.array([0.0, 5.0])
+    vc, _, _, sc = orc.step_cable([mech], [s0], v0, 2, parent, g, g, 0.025, nsteps=400)
+    vs, _, _, ss = orc.step([mech], [s0], v0, 2, 0.025, nsteps=400)
+    np.testing.assert_allclose(vc, vs, rtol=1e-12)
+    assert vc[0] == vc[1]

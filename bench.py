@@ -168,7 +168,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--forms", default="all",
-                    help="comma list of batched,kinetic,surrogate,mixed_errors,pade; all; none")
+                    help="comma list of batched,kinetic,surrogate,mixed_errors,pade,cable; "
+                         "all; none")
     args = ap.parse_args()
 
     from paper_1905_02241_b300.sharding import aggregate, network_seed, rank_info
@@ -322,7 +323,8 @@ def main():
     forms = None
     if rank == 0 and world == 1 and args.forms != "none":
         from paper_1905_02241_b300 import forms as F
-        want = (["batched", "mixed_errors", "kinetic", "surrogate", "pade"] if args.forms == "all"
+        want = (["batched", "mixed_errors", "kinetic", "surrogate", "pade", "cable"]
+                if args.forms == "all"
                 else args.forms.split(","))
         forms = {}
         for name in want:

@@ -195,6 +195,35 @@ NMODL_API int nmodl_step(nmodl_ctx *ctx, nmodl_mech *const *mechs, int n_mechs,
 NMODL_API int nmodl_plan_describe(nmodl_ctx *ctx, nmodl_mech *const *mechs,
                                   int n_mechs, int64_t *out);
 
+/* ---------------------------------------------------- cable coupling
+ * Compartments grouped into cells with a tree morphology: the per-cell
+ * tree matrix solve (Hines' ordering: every parent precedes its children,
+ * so elimination from the last node to the root makes no fill) replaces
+ * the diagonal update of nmodl_step.  This is the "Other" part of the
+ * NEURON step next to the mechanism kernels (Table 2).
+ *   parent[i]: host or device, n_nodes int32; -1 starts a cell (a root),
+ *              otherwise the parent node with cell_start <= parent[i] < i
+ *   ga[i], gb[i]: axial conductance between i and its parent, per unit
+ *              area of node i and of the parent (S/cm2, >= 0; ignored at
+ *              roots).  NMODL_ERR_ARG on an invalid tree.  Copied. */
+typedef struct nmodl_cable nmodl_cable;
+NMODL_API int nmodl_cable_create(nmodl_ctx *ctx, int64_t n_nodes,
+                                 const int32_t *parent, const double *ga,
+                                 const double *gb, nmodl_cable **out);
+NMODL_API void nmodl_cable_destroy(nmodl_cable *cable);
+NMODL_API int nmodl_cable_n_cells(const nmodl_cable *cable);
+/* nsteps steps of the coupled network: rhs = d = 0; nrn_cur of every
+ * mechanism; d += 1e-3 cm/dt; for every non-root node rhs[i] += ga (v[p] -
+ * v[i]), rhs[p] += gb (v[i] - v[p]), d[i] += ga, d[p] += gb; the tree system
+ * with off-diagonals -ga (row i) and -gb (row p) is solved per cell and
+ * added to v; nrn_state at the new v.  rhs and d return the last step's
+ * assembled values.  Windows of options.window steps are replayed from
+ * CUDA graphs. */
+NMODL_API int nmodl_step_cable(nmodl_ctx *ctx, nmodl_cable *cable,
+                               nmodl_mech *const *mechs, int n_mechs, double dt,
+                               double cm, double *v, double *rhs, double *d,
+                               int nsteps);
+
 /* Copy state row k (n_instances doubles) out of / into the mechanism
  * (out/in: host or device).  Checkpoint and resume use these. */
 NMODL_API int nmodl_get_state(nmodl_mech *m, int k, double *out);

@@ -90,6 +90,10 @@ _SIGS = {
     "nmodl_mech_attach_surrogate": (_i32, [_vp, _vp, _d]),
     "nmodl_plan_describe": (_i32, [_vp, _vp, _i32, _vp]),
     "nmodl_math_eval": (_i32, [_i32, _i64, _vp, _vp, _vp]),
+    "nmodl_cable_create": (_i32, [_vp, _i64, _vp, _vp, _vp, _P(_vp)]),
+    "nmodl_cable_destroy": (None, [_vp]),
+    "nmodl_cable_n_cells": (_i32, [_vp]),
+    "nmodl_step_cable": (_i32, [_vp, _vp, _vp, _i32, _d, _d, _vp, _vp, _vp, _i32]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -287,3 +291,25 @@ def nmodl_plan_describe(ctx: int, mechs) -> dict:
 
 def nmodl_math_eval(fn: int, n: int, x_ptr: int, y_ptr: int, stream: int) -> None:
     _check(lib.nmodl_math_eval(int(fn), int(n), x_ptr, y_ptr, stream or None), "nmodl_math_eval")
+
+
+def nmodl_cable_create(ctx: int, n_nodes: int, parent_ptr: int, ga_ptr: int, gb_ptr: int) -> int:
+    h = _vp()
+    _check(lib.nmodl_cable_create(ctx, int(n_nodes), parent_ptr, ga_ptr, gb_ptr, ctypes.byref(h)),
+           "nmodl_cable_create")
+    return h.value
+
+
+def nmodl_cable_destroy(cb: int) -> None:
+    lib.nmodl_cable_destroy(cb)
+
+
+def nmodl_cable_n_cells(cb: int) -> int:
+    return lib.nmodl_cable_n_cells(cb)
+
+
+def nmodl_step_cable(ctx: int, cb: int, mechs, dt: float, cm: float, v_ptr: int, rhs_ptr: int,
+                     d_ptr: int, nsteps: int) -> None:
+    arr = (_vp * len(mechs))(*mechs)
+    _check(lib.nmodl_step_cable(ctx, cb, ctypes.cast(arr, _vp), len(mechs), float(dt),
+                                float(cm), v_ptr, rhs_ptr, d_ptr, int(nsteps)), "nmodl_step_cable")

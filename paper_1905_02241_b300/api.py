@@ -153,3 +153,31 @@ class Mechanism:
         if self.handle:
             _lib.nmodl_mech_destroy(self.handle)
             self.handle = 0
+
+
+class Cable:
+    """Cells of compartments with a tree morphology (nmodl_cable_*)."""
+
+    def __init__(self, ctx: Context, parent, ga, gb):
+        self.ctx = ctx
+        p = np.ascontiguousarray(parent, dtype=np.int32)
+        a = np.ascontiguousarray(ga, dtype=np.float64)
+        b = np.ascontiguousarray(gb, dtype=np.float64)
+        self.n_nodes = p.size
+        ctx.enter()
+        self.handle = _lib.nmodl_cable_create(ctx.handle, p.size, p.ctypes.data, a.ctypes.data,
+                                              b.ctypes.data)
+        self.n_cells = _lib.nmodl_cable_n_cells(self.handle)
+
+    def step(self, mechs, dt, cm, v, rhs, d, nsteps: int) -> None:
+        dev = self.ctx.device
+        self.ctx.enter()
+        _lib.nmodl_step_cable(self.ctx.handle, self.handle, [m.handle for m in mechs], dt, cm,
+                              _dptr(v, device=dev), _dptr(rhs, device=dev),
+                              _dptr(d, device=dev), nsteps)
+        self.ctx.leave()
+
+    def close(self) -> None:
+        if self.handle:
+            _lib.nmodl_cable_destroy(self.handle)
+            self.handle = 0

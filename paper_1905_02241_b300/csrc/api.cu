@@ -20,6 +20,7 @@ cudaError_t enqueue_surrogate_state(nmodl_mech* m, double dt, const double* v);
 
 // Drop the cached step plans (and their graphs) that involve mechanism m.
 void nmodl_invalidate_plans(nmodl_ctx* c, nmodl_mech* m) {
+    c->epoch++;
     auto& P = c->plans;
     P.erase(std::remove_if(P.begin(), P.end(),
                            [m](const std::unique_ptr<Plan>& p) {
@@ -225,6 +226,7 @@ int nmodl_ctx_set_options(nmodl_ctx* c, const nmodl_options* opt) {
     if (rc) return rc;
     c->opt = *opt;
     c->plans.clear();  // plans depend on precision / tile options
+    c->epoch++;
     return NMODL_OK;
 }
 
@@ -353,7 +355,7 @@ int nmodl_init(nmodl_mech* m, const double* v) {
     return cuda_status(cudaGetLastError());
 }
 
-static void enqueue_state(nmodl_mech* m, double dt, const double* v) {
+void nmodl_enqueue_state(nmodl_mech* m, double dt, const double* v) {
     nmodl_ctx* c = m->ctx;
     const nmodl_options& o = c->opt;
     if (m->type == NMODL_KIN9 && m->sur) {
@@ -369,12 +371,12 @@ static void enqueue_state(nmodl_mech* m, double dt, const double* v) {
 
 // host-side counters of state updates (kept here, not at enqueue time, so
 // that graph replays are counted)
-static void count_states(nmodl_mech* m, int64_t k) {
+void nmodl_count_states(nmodl_mech* m, int64_t k) {
     m->calls += k;
     if (m->type == NMODL_KIN9 && m->sur) m->sur_calls += k;
 }
 
-static void enqueue_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
+void nmodl_enqueue_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
     nmodl_ctx* c = m->ctx;
     const void* desc = (m->type == NMODL_KIN9) ? (const void*)m->d_kd : (const void*)m->d_md;
     launch_cur_seg(m->type == NMODL_KIN9 ? NMODL_KIN9 : NMODL_CNEXP, desc, m->n_chunks,
@@ -385,15 +387,15 @@ static void enqueue_cur(nmodl_mech* m, const double* v, double* rhs, double* d) 
 int nmodl_state(nmodl_mech* m, double dt, const double* v) {
     if (!m || !(dt > 0.0) || !std::isfinite(dt) || (m->n > 0 && !v)) return NMODL_ERR_ARG;
     DeviceGuard g(m->ctx->device);
-    enqueue_state(m, dt, v);
-    count_states(m, 1);
+    nmodl_enqueue_state(m, dt, v);
+    nmodl_count_states(m, 1);
     return cuda_status(cudaGetLastError());
 }
 
 int nmodl_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
     if (!m || (m->n > 0 && (!v || !rhs || !d))) return NMODL_ERR_ARG;
     DeviceGuard g(m->ctx->device);
-    enqueue_cur(m, v, rhs, d);
+    nmodl_enqueue_cur(m, v, rhs, d);
     return cuda_status(cudaGetLastError());
 }
 
@@ -756,9 +758,9 @@ static cudaError_t enqueue_generic_steps(nmodl_ctx* c, nmodl_mech* const* mechs,
     for (int s = 0; s < nsteps; ++s) {
         cudaMemsetAsync(rhs, 0, n_nodes * sizeof(double), c->stream);
         cudaMemsetAsync(d, 0, n_nodes * sizeof(double), c->stream);
-        for (int i = 0; i < n_mechs; ++i) enqueue_cur(mechs[i], v, rhs, d);
+        for (int i = 0; i < n_mechs; ++i) nmodl_enqueue_cur(mechs[i], v, rhs, d);
         launch_vupdate(n_nodes, v, rhs, d, 1e-3 * cm / dt, c->opt.clamp_v, c->d_err, c->stream);
-        for (int i = 0; i < n_mechs; ++i) enqueue_state(mechs[i], dt, v);
+        for (int i = 0; i < n_mechs; ++i) nmodl_enqueue_state(mechs[i], dt, v);
     }
     return cudaGetLastError();
 }
@@ -819,7 +821,7 @@ int nmodl_step(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, double dt, d
     int rc = NMODL_OK;
     Plan* p = get_plan(c, mechs, n_mechs, v, &rc);
     if (!p) return rc;
-    for (int i = 0; i < n_mechs; ++i) count_states(mechs[i], nsteps);
+    for (int i = 0; i < n_mechs; ++i) nmodl_count_states(mechs[i], nsteps);
     const int W = c->opt.window;
     for (int s = 0; s < nsteps; s += W) {
         const int w = std::min(W, nsteps - s);

@@ -74,5 +74,9 @@ void launch_vupdate(int64_t n_nodes, double* v, const double* rhs, double* d,
                     double cmdt, int clamp, int32_t* err, cudaStream_t s);
 void launch_tile_bounds(const int32_t* ni, int64_t n, const int64_t* nodes,
                         int64_t n_bounds, int32_t* out, cudaStream_t s);
+void launch_cable_solve(int64_t n_cells, const int64_t* cell_off, const int32_t* parent,
+                        const double* ga, const double* gb, double cmdt, double* v,
+                        double* rhs, double* d, double* d2, double* r2, int32_t* err,
+                        cudaStream_t s);
 
 }  // namespace nmodl

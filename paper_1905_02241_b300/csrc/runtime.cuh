@@ -70,6 +70,7 @@ struct nmodl_ctx {
     int32_t* d_err = nullptr;
     std::vector<std::unique_ptr<Plan>> plans;
     int live_mechs = 0;
+    int64_t epoch = 0;  // bumped when options, mechanisms or surrogates change
 };
 
 struct nmodl_mech {
@@ -115,3 +116,20 @@ struct nmodl_surrogate {
 // shared helpers (api.cu)
 int nmodl_cuda_status(cudaError_t e);
 void nmodl_invalidate_plans(nmodl_ctx* c, nmodl_mech* m);
+extern "C" {
+void nmodl_enqueue_state(nmodl_mech* m, double dt, const double* v);
+void nmodl_enqueue_cur(nmodl_mech* m, const double* v, double* rhs, double* d);
+void nmodl_count_states(nmodl_mech* m, int64_t k);
+}
+
+struct nmodl_cable {
+    nmodl_ctx* ctx = nullptr;
+    int64_t n_nodes = 0, n_cells = 0;
+    int32_t* d_parent = nullptr;
+    double *d_ga = nullptr, *d_gb = nullptr;
+    int64_t* d_cell_off = nullptr;
+    double *d_d2 = nullptr, *d_r2 = nullptr;  // eliminated system (scratch)
+    std::vector<GraphEntry> graphs;
+    std::vector<nmodl_mech*> graph_mechs;      // mechanism list the graphs hold
+    int64_t graph_epoch = -1;                  // context epoch they were made in
+};

@@ -117,6 +117,38 @@ def pade(dev, n_nodes=2_000_000, nsteps=200):
     return out
 
 
+def cable(dev, n_cells=10000, nsteps=200):
+    """The cortical mix on cells of 20..400 compartments with tree
+    morphologies: FP64 steps with the per-cell tree solve against the same
+    compartments isolated (fused step), instance-steps/s."""
+    from .api import Cable
+    cab = W.cable_cells(n_cells, seed=7)
+    wl = W.cortical_mix(cab["n_nodes"], seed=2)
+    ninst = _ninst(wl)
+    out = {"cells": n_cells, "nodes": cab["n_nodes"], "instances": ninst,
+           "steps_per_run": nsteps}
+    ctx = Context(dev)
+    mechs = _mechs(ctx, wl)
+    v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
+    rhs = torch.zeros_like(v)
+    d = torch.zeros_like(v)
+    for m in mechs:
+        m.init(v)
+    cb = Cable(ctx, cab["parent"], cab["ga"], cab["gb"])
+    cb.step(mechs, DT, CM, v, rhs, d, 40)
+    ms = _time(lambda: cb.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
+    out["cable_fp64"] = ninst * nsteps / (ms * 1e-3)
+    ctx.step(mechs, DT, CM, v, rhs, d, 40)
+    ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
+    out["isolated_fused_fp64"] = ninst * nsteps / (ms * 1e-3)
+    out["cable_over_isolated"] = out["cable_fp64"] / out["isolated_fused_fp64"]
+    cb.close()
+    for m in mechs:
+        m.close()
+    ctx.close()
+    return out
+
+
 def mixed_errors(dev, n_nodes=1500, nsteps=200):
     """Per-quantity error of the MIXED fused step against the FP64 oracle on
     a sub-network of the cortical mix (max over nodes / instances)."""

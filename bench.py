@@ -166,6 +166,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--nodes", type=int, default=2_000_000)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile-smem", type=int, default=0, help="fix the fused tile budget (bytes)")
+    ap.add_argument("--block", type=int, default=0, help="fix the fused block size")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--forms", default="all",
                     help="comma list of batched,kinetic,surrogate,mixed_errors,pade,cable; "
@@ -215,7 +217,7 @@ def main():
 
     wl = W.cortical_mix(args.nodes, seed=network_seed(2, rank))
     prec = NMODL_FP64 if args.precision == "fp64" else NMODL_MIXED
-    ctx = Context(dev, precision=prec)
+    ctx = Context(dev, precision=prec, tile_smem=args.tile_smem, block=args.block)
     mechs = [Mechanism(ctx, m["type"], m["node_index"], wl["n_nodes"], m["params"])
              for m in wl["mechs"]]
     n = wl["n_nodes"]

@@ -191,7 +191,7 @@ NMODL_API int nmodl_step(nmodl_ctx *ctx, nmodl_mech *const *mechs, int n_mechs,
  * block size, out[3] dynamic shared memory per block (bytes), out[4]
  * persistent tile queue (1) or one block per tile (0), out[5] tile
  * shared-memory budget.  The autotuner (options.autotune) picks these by
- * timing candidates on a scratch copy of the first ~2M instances. */
+ * timing candidates on a scratch copy of the first <= 16M instances. */
 NMODL_API int nmodl_plan_describe(nmodl_ctx *ctx, nmodl_mech *const *mechs,
                                   int n_mechs, int64_t *out);
 

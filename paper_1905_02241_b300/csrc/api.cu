@@ -540,7 +540,8 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     std::vector<bool> pers;
     const bool tune = c->opt.autotune != 0;
     if (c->opt.tile_smem > 0) budgets = {std::min<size_t>(c->opt.tile_smem, cap)};
-    else if (tune) budgets = {24 * 1024, 48 * 1024, 96 * 1024, 150 * 1024, cap};
+    else if (tune) budgets = {16 * 1024, 24 * 1024, 32 * 1024, 48 * 1024, 64 * 1024,
+                              96 * 1024, 150 * 1024, cap};
     else budgets = {std::min<size_t>(cap, 96 * 1024)};
     size_t items = 0;
     for (int t = 0; t < T; ++t) items += (size_t)gates[t] * mechs[t]->n;
@@ -573,7 +574,8 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     size_t best = 0;
     if (cands.size() > 1) {
         // time each candidate on a scratch copy: a prefix of the network of
-        // about 2M instances, min(window, 8) steps
+        // up to 16M instances (several waves of even the largest tiles),
+        // min(window, 8) steps, best of 2
         std::vector<double*> sst(T, nullptr);
         double *sv = nullptr, *srhs = nullptr, *sd = nullptr;
         int32_t* d_trial = nullptr;
@@ -610,7 +612,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
             std::vector<int32_t> sub;
             int64_t inst = 0;
             for (size_t k : idx) {
-                if (inst > 2000000) break;
+                if (inst > 16000000) break;
                 for (int tt = 0; tt < T; ++tt)
                     inst += cd.recs[k * st + 3 + 2 * tt] - cd.recs[k * st + 2 + 2 * tt];
                 sub.insert(sub.end(), cd.recs.begin() + k * st, cd.recs.begin() + (k + 1) * st);

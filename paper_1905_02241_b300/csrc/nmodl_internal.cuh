@@ -63,10 +63,13 @@ struct Kin9D {
 // p(r) the degree-5 Taylor polynomial of exp(r) - 1 (truncation < 4e-17);
 // error within 1.5 ulp (measured max 1.01 ulp against mpmath).
 // 10 FP64 instructions; 2^m is applied to the exponent field with integer
-// operations.  |x| >= 708 (and NaN) go to the library exp.
+// operations.  x <= -708 returns 0 (the exact value is below 3.3e-308; this
+// is the common case of the cnexp factor of very fast gates); x >= 708 and
+// NaN go to the library exp.
 __device__ __forceinline__ double exp_tang(double x) {
     // |x| < 708 tested on the high word (integer pipe): 708 = 0x4086200000000000
-    if ((__double2hiint(x) & 0x7fffffff) >= 0x40862000) return exp(x);
+    const int hx = __double2hiint(x);
+    if ((hx & 0x7fffffff) >= 0x40862000) return (hx < 0 && x == x) ? 0.0 : exp(x);
     const double kShift = 0x1.8p52;
     const double t = fma(x, kExpInvL, kShift);
     const int k = __double2loint(t);

@@ -141,6 +141,7 @@ def cable(dev, n_cells=10000, nsteps=200):
     ctx.step(mechs, DT, CM, v, rhs, d, 40)
     ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["isolated_fused_fp64"] = ninst * nsteps / (ms * 1e-3)
+    out["plan_isolated"] = ctx.plan(mechs)
     out["cable_over_isolated"] = out["cable_fp64"] / out["isolated_fused_fp64"]
     cb.close()
     for m in mechs:

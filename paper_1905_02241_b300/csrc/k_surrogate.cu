@@ -13,7 +13,7 @@
 // x_hat (then ||x_hat - x*||_1 <= ||J^-1||_1 ||F||_1 = ||F||_1), otherwise the
 // instance goes on a fallback list for the Newton kernel.
 //
-// k_surrogate_step: persistent CTAs, 8 warps, weights staged once in shared
+// k_surrogate_step: persistent CTAs (one per SM), 16 warps, weights staged once in shared
 // memory (bf16, rows padded by 16 bytes so ldmatrix is conflict-free).  A
 // warp owns 16 instances; the accumulator fragments of one layer are the A
 // fragments of the next (m16n8k16 C and A layouts coincide pairwise), so
@@ -24,7 +24,7 @@
 namespace nmodl {
 
 namespace {
-constexpr int kWarps = 8;
+constexpr int kWarps = 16;  // 512 threads, 128 registers: one CTA per SM
 constexpr int P1 = kIn + 8;    // W1 row pitch (elements)
 constexpr int PH = kHid + 8;   // W2, W3, W4 row pitch
 constexpr int kSmemW = (kHid * P1 + 2 * kHid * PH + kOut * PH) * 2;
@@ -108,7 +108,7 @@ __device__ __forceinline__ void project_simplex9(float (&w)[9]) {
     for (int i = 0; i < 9; ++i) w[i] = fmaxf(w[i] - theta, 0.f);
 }
 
-__global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, 1) k_surrogate_step(SurArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smem);
     __nv_bfloat16* W2s = W1s + kHid * P1;
@@ -130,14 +130,27 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
                 *reinterpret_cast<const uint4*>(src + r * cols + cc);
         }
     };
-    stage(a.wbf + kBfW1, W1s, kHid, kIn, P1);
-    stage(a.wbf + kBfW2, W2s, kHid, kHid, PH);
-    stage(a.wbf + kBfW3, W3s, kHid, kHid, PH);
+    // Hidden layers are staged as (W/2, b/2): the accumulator is then
+    // h = z/2 and SiLU(z) = z sigma(z) = h + h tanh(h), one tanh and one FMA
+    // (halving a bf16 is exact, so the products match the training forward).
+    auto stage_half = [&](const __nv_bfloat16* src, __nv_bfloat16* dst, int rows, int cols,
+                          int pitch) {
+        const int ch = cols / 2;
+        for (int c = tid; c < rows * ch; c += blockDim.x) {
+            const int r = c / ch, cc = (c % ch) * 2;
+            __nv_bfloat162 w = *reinterpret_cast<const __nv_bfloat162*>(src + r * cols + cc);
+            *reinterpret_cast<__nv_bfloat162*>(dst + r * pitch + cc) =
+                __hmul2(w, __floats2bfloat162_rn(0.5f, 0.5f));
+        }
+    };
+    stage_half(a.wbf + kBfW1, W1s, kHid, kIn, P1);
+    stage_half(a.wbf + kBfW2, W2s, kHid, kHid, PH);
+    stage_half(a.wbf + kBfW3, W3s, kHid, kHid, PH);
     stage(a.wbf + kBfW4, W4s, kOut, kHid, PH);
     for (int i = tid; i < kHid; i += blockDim.x) {
-        b1s[i] = a.params[kOffB1 + i];
-        b2s[i] = a.params[kOffB2 + i];
-        b3s[i] = a.params[kOffB3 + i];
+        b1s[i] = 0.5f * a.params[kOffB1 + i];
+        b2s[i] = 0.5f * a.params[kOffB2 + i];
+        b3s[i] = 0.5f * a.params[kOffB3 + i];
     }
     if (tid < kOut) b4s[tid] = a.params[kOffB4 + tid];
     __syncthreads();
@@ -194,10 +207,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
             afr[2] = pack_bf16(fh[g * 16 + 2 * t + 8], fh[g * 16 + 2 * t + 9]);
             afr[3] = pack_bf16(fh[(g + 8) * 16 + 2 * t + 8], fh[(g + 8) * 16 + 2 * t + 9]);
             float acc[16][4];
+            // accumulators start at the (halved) bias of their column
+            auto init_bias = [&](const float* bias) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+                for (int j = 0; j < 16; ++j) {
+                    const float2 bb = *reinterpret_cast<const float2*>(bias + 8 * j + 2 * t);
+                    acc[j][0] = bb.x;
+                    acc[j][1] = bb.y;
+                    acc[j][2] = bb.x;
+                    acc[j][3] = bb.y;
+                }
+            };
+            init_bias(b1s);
 #pragma unroll
             for (int np = 0; np < 8; ++np) {
                 uint32_t b[4];
@@ -209,24 +230,19 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
             // the A fragment (a0a1, a2a3, a4a5, a6a7) of k-slice kk of the
             // next layer
             uint32_t ah[8][4];
-            auto to_frags = [&](const float* bias) {
+            auto silu_h = [](float h) { return fmaf(h, tanh_hw(h), h); };
+            auto to_frags = [&]() {
 #pragma unroll
                 for (int kk = 0; kk < 8; ++kk)
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int j = 2 * kk + h;
-                        const int col = 8 * j + 2 * t;
-                        const float b0 = bias[col], b1 = bias[col + 1];
-                        ah[kk][2 * h] = pack_bf16(silu_f(acc[j][0] + b0), silu_f(acc[j][1] + b1));
-                        ah[kk][2 * h + 1] =
-                            pack_bf16(silu_f(acc[j][2] + b0), silu_f(acc[j][3] + b1));
+                        ah[kk][2 * h] = pack_bf16(silu_h(acc[j][0]), silu_h(acc[j][1]));
+                        ah[kk][2 * h + 1] = pack_bf16(silu_h(acc[j][2]), silu_h(acc[j][3]));
                     }
             };
-            auto hidden = [&](const __nv_bfloat16* Ws) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+            auto hidden = [&](const __nv_bfloat16* Ws, const float* bias) {
+                init_bias(bias);
 #pragma unroll
                 for (int kk = 0; kk < 8; ++kk)
 #pragma unroll
@@ -237,11 +253,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_surrogate_step(SurArgs a) {
                         mma_bf16_16816(acc[2 * np + 1], ah[kk], b[2], b[3]);
                     }
             };
-            to_frags(b1s);
-            hidden(W2s);
-            to_frags(b2s);
-            hidden(W3s);
-            to_frags(b3s);
+            to_frags();
+            hidden(W2s, b2s);
+            to_frags();
+            hidden(W3s, b3s);
+            to_frags();
             float o[2][4];
 #pragma unroll
             for (int j = 0; j < 2; ++j)
@@ -320,7 +336,7 @@ cudaError_t launch_surrogate_step(const SurArgs& a, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t groups = (a.n + 31) / 32;
-    int64_t grid = std::min<int64_t>((int64_t)sms * 2, (groups + kWarps - 1) / kWarps);
+    int64_t grid = std::min<int64_t>((int64_t)sms, (groups + kWarps - 1) / kWarps);
     if (grid < 1) grid = 1;
     k_surrogate_step<<<(int)grid, kWarps * 32, kSmemTotal, s>>>(a);
     return cudaGetLastError();

@@ -272,10 +272,11 @@ def surrogate(dev, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=20):
     return out
 
 
-def surrogate_kernel_case(dev=0, n=4_000_000, steps=3):
+def surrogate_kernel_case(dev=0, n=4_000_000, steps=3, tol=1e-4):
     """Profiling case of the fused surrogate kernel: n clamped instances,
-    `steps` surrogate state updates with seeded (untrained) weights and a
-    1e-4 residual gate; prints instance-steps/s."""
+    `steps` surrogate state updates with seeded (untrained) weights and the
+    residual gate tol (inf keeps every prediction, timing the surrogate
+    kernel alone); prints instance-steps/s."""
     from .surrogate import Surrogate, attach
     wl = W.kin9_clamped(n, seed=5)
     ctx = Context(dev)
@@ -284,7 +285,7 @@ def surrogate_kernel_case(dev=0, n=4_000_000, steps=3):
     sur.set_weights(Surrogate.pack(Ws, bs))
     (m,) = _mechs(ctx, wl)
     m.set_states(torch.tensor(wl["x0"], device=f"cuda:{dev}"))
-    attach(m, sur, 1e-4)
+    attach(m, sur, tol)
     v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
     m.state(DT, v)
     ms = _time(lambda: [m.state(DT, v) for _ in range(steps)], ctx, 1)
@@ -298,4 +299,5 @@ def surrogate_kernel_case(dev=0, n=4_000_000, steps=3):
 
 if __name__ == "__main__":
     import sys
-    surrogate_kernel_case(n=int(sys.argv[1]) if len(sys.argv) > 1 else 4_000_000)
+    surrogate_kernel_case(n=int(sys.argv[1]) if len(sys.argv) > 1 else 4_000_000,
+                          tol=float(sys.argv[2]) if len(sys.argv) > 2 else 1e-4)

@@ -30,6 +30,12 @@
  *    ascending instance) -> d += 1e-3 cm/dt -> v += rhs/d -> state; the
  *    3x3 lattice topology of the 9-state scheme; vtrap evaluated through
  *    expm1 with a 3-term Taylor branch for |x/y| < 1e-6.
+ *  - Section 3 (USEION) and Section 4.2 (ion dependencies): ion currents
+ *    are written per node (ina, ik, ica) by the current update of every
+ *    step, before the state updates that read them (calcium accumulation
+ *    reads ica).  Readings: the 3-state triangle scheme (Section 5.2
+ *    "sparse" for <= 3 equations) and the 2-state calcium buffer of the
+ *    derivimplicit kind (Section 5.3 small-matrix Newton).
  */
 #include <math.h>
 #include <stdint.h>
@@ -39,6 +45,9 @@
 #define ORC_TYPE_HH 1
 #define ORC_TYPE_CNEXP 2
 #define ORC_TYPE_KIN9 3
+#define ORC_TYPE_CACUM 4
+#define ORC_TYPE_KIN3 5
+#define ORC_NION 4 /* 0 nonspecific, 1 na, 2 k, 3 ca */
 
 /* ---------------------------------------------------------------- rates */
 
@@ -112,6 +121,8 @@ static int n_gates_of(int type, const double *p)
     if (type == ORC_TYPE_HH) return 3;
     if (type == ORC_TYPE_CNEXP) return (int)p[0];
     if (type == ORC_TYPE_KIN9) return 9;
+    if (type == ORC_TYPE_CACUM) return 2;
+    if (type == ORC_TYPE_KIN3) return 3;
     return -1;
 }
 
@@ -200,11 +211,47 @@ static void instance_current(int type, int64_t n, int64_t i, double vv,
         }
         *cur = g * (vv - p[2]);
         *cond = g;
-    } else { /* KIN9: open-state occupancy */
+    } else if (type == ORC_TYPE_CACUM) { /* no membrane current */
+        *cur = 0.0;
+        *cond = 0.0;
+    } else { /* KIN9, KIN3: open-state occupancy */
         int op = (int)p[2];
         double g = p[0] * s[op * n + i];
         *cur = g * (vv - p[1]);
         *cond = g;
+    }
+}
+
+/* Ion currents of an instance (USEION WRITE): HH writes ina (gna term) and
+ * ik (gk term); a CNEXP, KIN9 or KIN3 mechanism writes its whole current to the
+ * ion it is tagged with (0 = nonspecific, not written). */
+static void instance_ion_currents(int type, int ion, int64_t n, int64_t i, double vv,
+                                  const double *p, const double *s, double *ic)
+{
+    for (int k = 0; k < ORC_NION; ++k)
+        ic[k] = 0.0;
+    if (type == ORC_TYPE_HH) {
+        double m = s[i], h = s[n + i], nn = s[2 * n + i];
+        ic[1] = p[0] * m * m * m * h * (vv - p[3]);
+        ic[2] = p[1] * nn * nn * nn * nn * (vv - p[4]);
+    } else if (ion > 0 && type != ORC_TYPE_CACUM) {
+        double c, g;
+        instance_current(type, n, i, vv, p, s, &c, &g);
+        ic[ion] = c;
+    }
+}
+
+/* ion_i[k][node] += ion current k of every instance (k = 1..3; arrays may
+ * be NULL). */
+void orc_mech_ion_cur(int type, int ion, int64_t n, const int32_t *ni, const double *v,
+                      const double *p, const double *s, double *const *ion_i)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double ic[ORC_NION];
+        instance_ion_currents(type, ion, n, i, v[ni[i]], p, s, ic);
+        for (int k = 1; k < ORC_NION; ++k)
+            if (ion_i[k])
+                ion_i[k][ni[i]] += ic[k];
     }
 }
 
@@ -388,11 +435,163 @@ int orc_kin9_stationary(const double *p, double v, double *pi)
     return 0;
 }
 
+/* ------------------------------------------------ 3-state kinetic scheme */
+
+/* Generator matrix of the 3-state scheme (KINETIC, Section 5.1): edges
+ * 0-1, 1-2 and 0-2, each with the forward (lo -> hi) rate af exp(bf v) and
+ * the backward rate ab exp(-bb v); params: gbar, e, open, then
+ * (af, bf, ab, bb) per edge. */
+void orc_kin3_matrix(const double *p, double v, double *A)
+{
+    static const int edges[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+    memset(A, 0, 9 * sizeof(double));
+    for (int k = 0; k < 3; ++k) {
+        int lo = edges[k][0], hi = edges[k][1];
+        double kf = p[3 + 4 * k] * exp(p[4 + 4 * k] * v);
+        double kb = p[5 + 4 * k] * exp(-p[6 + 4 * k] * v);
+        A[hi * 3 + lo] += kf;
+        A[lo * 3 + lo] -= kf;
+        A[lo * 3 + hi] += kb;
+        A[hi * 3 + hi] -= kb;
+    }
+}
+
+/* Implicit Euler step of an ns-state linear scheme by the same Newton
+ * iteration as the 9-state one (dense LU with partial pivoting of
+ * J = I - dt A); for a linear scheme the first update is already the
+ * solution and the second is of rounding size. */
+int orc_kin_newton_n(int ns, const double *A, double dt, const double *x, double *y,
+                     double tol, int max_iter)
+{
+    double J[64], r[8], delta[8];
+    int perm[8];
+    for (int a = 0; a < ns; ++a)
+        for (int b = 0; b < ns; ++b)
+            J[a * ns + b] = (a == b ? 1.0 : 0.0) - dt * A[a * ns + b];
+    orc_lu_pp(ns, J, perm);
+    for (int a = 0; a < ns; ++a)
+        y[a] = x[a];
+    int it = 0;
+    while (it < max_iter) {
+        for (int a = 0; a < ns; ++a) {
+            double Ay = 0.0;
+            for (int b = 0; b < ns; ++b)
+                Ay += A[a * ns + b] * y[b];
+            r[a] = -(y[a] - x[a] - dt * Ay);
+        }
+        orc_lu_solve(ns, J, perm, r, delta);
+        double dmax = 0.0;
+        for (int a = 0; a < ns; ++a) {
+            y[a] += delta[a];
+            if (fabs(delta[a]) > dmax)
+                dmax = fabs(delta[a]);
+        }
+        ++it;
+        if (dmax <= tol)
+            break;
+    }
+    return it;
+}
+
+/* stationary distribution: last row of A replaced by the normalisation */
+int orc_kin_stationary_n(int ns, const double *A, double *pi)
+{
+    double M[64], b[8];
+    int perm[8];
+    memcpy(M, A, ns * ns * sizeof(double));
+    for (int c = 0; c < ns; ++c)
+        M[(ns - 1) * ns + c] = 1.0;
+    for (int a = 0; a < ns; ++a)
+        b[a] = (a == ns - 1) ? 1.0 : 0.0;
+    if (orc_lu_pp(ns, M, perm) < 0)
+        return -1;
+    orc_lu_solve(ns, M, perm, b, pi);
+    return 0;
+}
+
+/* ------------------------------------------------- calcium accumulation */
+
+/* 2-state calcium accumulation with a buffer (reading of a derivimplicit
+ * "cacum"-style mechanism, Section 5.2 / Section 8): y = (cai, cab) [mM],
+ *   dcai/dt = -k ica - kf cai (btot - cab) + kb cab - (cai - cai0)/tau
+ *   dcab/dt =  kf cai (btot - cab) - kb cab
+ * params: k [mM/ms per mA/cm2], tau [ms], cai0 [mM], kf [1/(mM ms)],
+ * kb [1/ms], btot [mM].  ica is the node's calcium current of the same step. */
+static void cacum_f(const double *p, double ica, const double *y, double *f)
+{
+    double bind = p[3] * y[0] * (p[5] - y[1]) - p[4] * y[1];
+    f[0] = -p[0] * ica - bind - (y[0] - p[2]) / p[1];
+    f[1] = bind;
+}
+
+static void cacum_jac(const double *p, const double *y, double *Jf)
+{
+    Jf[0] = -p[3] * (p[5] - y[1]) - 1.0 / p[1];
+    Jf[1] = p[3] * y[0] + p[4];
+    Jf[2] = p[3] * (p[5] - y[1]);
+    Jf[3] = -p[3] * y[0] - p[4];
+}
+
+/* One implicit Euler step by Newton's method with the exact Jacobian
+ * J = I - dt df/dy and an LU (partial pivot) solve per update. */
+int orc_cacum_newton(const double *p, double dt, double ica, const double *x,
+                     double *y, double tol, int max_iter)
+{
+    y[0] = x[0];
+    y[1] = x[1];
+    int it = 0;
+    while (it < max_iter) {
+        double f[2], Jf[4], J[4], r[2], delta[2];
+        int perm[2];
+        cacum_f(p, ica, y, f);
+        cacum_jac(p, y, Jf);
+        for (int a = 0; a < 2; ++a) {
+            r[a] = -(y[a] - x[a] - dt * f[a]);
+            for (int b = 0; b < 2; ++b)
+                J[a * 2 + b] = (a == b ? 1.0 : 0.0) - dt * Jf[a * 2 + b];
+        }
+        orc_lu_pp(2, J, perm);
+        orc_lu_solve(2, J, perm, r, delta);
+        y[0] += delta[0];
+        y[1] += delta[1];
+        ++it;
+        if (fabs(delta[0]) <= tol && fabs(delta[1]) <= tol)
+            break;
+    }
+    return it;
+}
+
+/* per-node ion current arrays for the state updates that READ them */
+static const double *orc_ion_read[ORC_NION];
+
+void orc_set_ion_read(int ion, const double *arr)
+{
+    if (ion >= 0 && ion < ORC_NION)
+        orc_ion_read[ion] = arr;
+}
+
 /* --------------------------------------------------------- per mechanism */
 
 void orc_mech_init(int type, int64_t n, const int32_t *ni, const double *v,
                    const double *p, double *s)
 {
+    if (type == ORC_TYPE_CACUM) { /* rest: cai0 and the bound buffer at it */
+        for (int64_t i = 0; i < n; ++i) {
+            s[i] = p[2];
+            s[n + i] = p[3] * p[2] * p[5] / (p[3] * p[2] + p[4]);
+        }
+        return;
+    }
+    if (type == ORC_TYPE_KIN3) {
+        for (int64_t i = 0; i < n; ++i) {
+            double A[9], pi[3];
+            orc_kin3_matrix(p, v[ni[i]], A);
+            orc_kin_stationary_n(3, A, pi);
+            for (int a = 0; a < 3; ++a)
+                s[a * n + i] = pi[a];
+        }
+        return;
+    }
     if (type == ORC_TYPE_KIN9) {
         for (int64_t i = 0; i < n; ++i) {
             double pi[9];
@@ -409,17 +608,40 @@ void orc_mech_state(int type, int64_t n, const int32_t *ni, const double *v,
                     const double *p, double dt, double *s, double tol,
                     int max_iter, int32_t *iters)
 {
-    if (type == ORC_TYPE_KIN9)
+    if (type == ORC_TYPE_KIN9) {
         orc_kin9_state(n, ni, v, p, dt, s, tol, max_iter, iters, NULL);
-    else
+    } else if (type == ORC_TYPE_KIN3) {
+        for (int64_t i = 0; i < n; ++i) {
+            double A[9], x[3], y[3];
+            orc_kin3_matrix(p, v[ni[i]], A);
+            for (int a = 0; a < 3; ++a)
+                x[a] = s[a * n + i];
+            int it = orc_kin_newton_n(3, A, dt, x, y, tol, max_iter);
+            if (iters)
+                iters[i] = it;
+            for (int a = 0; a < 3; ++a)
+                s[a * n + i] = y[a];
+        }
+    } else if (type == ORC_TYPE_CACUM) {
+        const double *ica = orc_ion_read[3];
+        for (int64_t i = 0; i < n; ++i) {
+            double x[2] = {s[i], s[n + i]}, y[2];
+            int it = orc_cacum_newton(p, dt, ica ? ica[ni[i]] : 0.0, x, y, tol, max_iter);
+            if (iters)
+                iters[i] = it;
+            s[i] = y[0];
+            s[n + i] = y[1];
+        }
+    } else {
         cnexp_like_state(type, n, ni, v, p, dt, s);
+    }
 }
 
 /* ------------------------------------------------------------------ step */
 
 typedef struct {
     int32_t type;
-    int32_t pad;
+    int32_t ion; /* USEION WRITE tag (0 none, 1 na, 2 k, 3 ca) */
     int64_t n;
     const int32_t *node_index;
     const double *params;
@@ -520,5 +742,42 @@ void orc_step_cable(int n_mechs, const orc_mech *mechs, int64_t n_nodes,
             orc_mech_state(mechs[m].type, mechs[m].n, mechs[m].node_index, v,
                            mechs[m].params, dt, mechs[m].states, tol,
                            max_iter, NULL);
+    }
+}
+
+/* orc_step with ion currents: every step zeroes ion_i[1..3] (where given),
+ * accumulates the ion currents of the current update into them, and the
+ * state updates that READ an ion (calcium accumulation reads ica) see the
+ * same step's values -- the USEION ordering: currents before states. */
+void orc_step_ions(int n_mechs, const orc_mech *mechs, int64_t n_nodes, double dt,
+                   double cm, double *v, double *rhs, double *d, double *const *ion_i,
+                   int nsteps, int clamp_v, double tol, int max_iter)
+{
+    for (int st = 0; st < nsteps; ++st) {
+        for (int64_t k = 0; k < n_nodes; ++k) {
+            rhs[k] = 0.0;
+            d[k] = 0.0;
+            for (int q = 1; q < ORC_NION; ++q)
+                if (ion_i[q])
+                    ion_i[q][k] = 0.0;
+        }
+        for (int m = 0; m < n_mechs; ++m) {
+            orc_mech_cur(mechs[m].type, mechs[m].n, mechs[m].node_index, v,
+                         mechs[m].params, mechs[m].states, rhs, d);
+            orc_mech_ion_cur(mechs[m].type, mechs[m].ion, mechs[m].n, mechs[m].node_index,
+                             v, mechs[m].params, mechs[m].states, ion_i);
+        }
+        for (int64_t k = 0; k < n_nodes; ++k) {
+            d[k] += 1e-3 * cm / dt;
+            if (!clamp_v)
+                v[k] += rhs[k] / d[k];
+        }
+        for (int q = 0; q < ORC_NION; ++q)
+            orc_set_ion_read(q, ion_i[q]);
+        for (int m = 0; m < n_mechs; ++m)
+            orc_mech_state(mechs[m].type, mechs[m].n, mechs[m].node_index, v,
+                           mechs[m].params, dt, mechs[m].states, tol, max_iter, NULL);
+        for (int q = 0; q < ORC_NION; ++q)
+            orc_set_ion_read(q, NULL);
     }
 }

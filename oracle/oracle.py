@@ -25,7 +25,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nmodl_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-TYPE_HH, TYPE_CNEXP, TYPE_KIN9 = 1, 2, 3
+TYPE_HH, TYPE_CNEXP, TYPE_KIN9, TYPE_CACUM, TYPE_KIN3 = 1, 2, 3, 4, 5
+ION_NONE, ION_NA, ION_K, ION_CA = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -76,6 +77,17 @@ def lib():
                                      vp, ctypes.c_int, d, ctypes.c_int]
         L.orc_cnexp_factor.restype = d
         L.orc_cnexp_factor.argtypes = [d]
+        L.orc_kin3_matrix.argtypes = [vp, d, vp]
+        L.orc_kin_newton_n.restype = ctypes.c_int
+        L.orc_kin_newton_n.argtypes = [ctypes.c_int, vp, d, vp, vp, d, ctypes.c_int]
+        L.orc_kin_stationary_n.restype = ctypes.c_int
+        L.orc_kin_stationary_n.argtypes = [ctypes.c_int, vp, vp]
+        L.orc_cacum_newton.restype = ctypes.c_int
+        L.orc_cacum_newton.argtypes = [vp, d, d, vp, vp, d, ctypes.c_int]
+        L.orc_set_ion_read.argtypes = [ctypes.c_int, vp]
+        L.orc_mech_ion_cur.argtypes = [ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, vp, vp]
+        L.orc_step_ions.argtypes = [ctypes.c_int, vp, i64, d, d, vp, vp, vp, vp,
+                                    ctypes.c_int, ctypes.c_int, d, ctypes.c_int]
         _ = (P, i32)
         _lib = L
     return _lib
@@ -104,6 +116,10 @@ def n_states(mtype: int, params: np.ndarray) -> int:
         return int(params[0])
     if mtype == TYPE_KIN9:
         return 9
+    if mtype == TYPE_CACUM:
+        return 2
+    if mtype == TYPE_KIN3:
+        return 3
     raise ValueError(mtype)
 
 
@@ -181,13 +197,20 @@ def mech_init(mtype, params, node_index, v) -> np.ndarray:
 
 
 def mech_state(mtype, params, node_index, v, states, dt,
-               tol=NEWTON_TOL, max_iter=NEWTON_MAX_ITER, want_iters=False):
-    """Returns the updated SoA states (copy); optionally Newton iterations."""
+               tol=NEWTON_TOL, max_iter=NEWTON_MAX_ITER, want_iters=False, ica=None):
+    """Returns the updated SoA states (copy); optionally Newton iterations.
+    ica: per-node calcium current read by the calcium accumulation type."""
     p, ni, vv = _f64(params), _i32(node_index), _f64(v)
     s = _f64(states).copy()
     it = np.zeros(ni.size, dtype=np.int32)
-    lib().orc_mech_state(int(mtype), ni.size, _p(ni), _p(vv), _p(p), float(dt),
+    ic = None if ica is None else _f64(ica)
+    L = lib()
+    L.orc_set_ion_read(ION_CA, None if ic is None else _p(ic))
+    try:
+        L.orc_mech_state(int(mtype), ni.size, _p(ni), _p(vv), _p(p), float(dt),
                          _p(s), float(tol), int(max_iter), _p(it))
+    finally:
+        L.orc_set_ion_read(ION_CA, None)
     return (s, it) if want_iters else s
 
 
@@ -221,8 +244,53 @@ def mech_currents(mtype, params, node_index, v, states):
     return c, g
 
 
+def mech_ion_cur(mtype, params, node_index, v, states, n_nodes, ion=ION_NONE):
+    """Per-node ion currents [4][n_nodes] (row 0 unused) of one mechanism:
+    HH writes ina and ik, a CNEXP/KIN9/KIN3 mechanism tagged with ion writes
+    its whole current to that ion."""
+    p, ni, vv = _f64(params), _i32(node_index), _f64(v)
+    s = _f64(states)
+    out = np.zeros((4, int(n_nodes)))
+    ptrs = (ctypes.c_void_p * 4)(None, *[out[k].ctypes.data for k in (1, 2, 3)])
+    lib().orc_mech_ion_cur(int(mtype), int(ion), ni.size, _p(ni), _p(vv), _p(p), _p(s),
+                           ctypes.cast(ptrs, ctypes.c_void_p))
+    return out
+
+
+def kin3_matrix(params, v: float) -> np.ndarray:
+    A = np.zeros(9)
+    lib().orc_kin3_matrix(_p(_f64(params)), float(v), _p(A))
+    return A.reshape(3, 3)
+
+
+def kin_newton_n(A, dt, x, tol=NEWTON_TOL, max_iter=NEWTON_MAX_ITER):
+    A = _f64(A)
+    ns = A.shape[0]
+    xx = _f64(x)
+    y = np.zeros(ns)
+    it = lib().orc_kin_newton_n(ns, _p(A), float(dt), _p(xx), _p(y), float(tol),
+                                int(max_iter))
+    return y, it
+
+
+def kin_stationary_n(A) -> np.ndarray:
+    A = _f64(A)
+    pi = np.zeros(A.shape[0])
+    if lib().orc_kin_stationary_n(A.shape[0], _p(A), _p(pi)) != 0:
+        raise ArithmeticError("singular stationary system")
+    return pi
+
+
+def cacum_newton(params, dt, ica, x, tol=NEWTON_TOL, max_iter=NEWTON_MAX_ITER):
+    """One implicit Euler step of the calcium buffer; returns (y, iterations)."""
+    xx, y = _f64(x), np.zeros(2)
+    it = lib().orc_cacum_newton(_p(_f64(params)), float(dt), float(ica), _p(xx), _p(y),
+                                float(tol), int(max_iter))
+    return y, it
+
+
 class _OrcMech(ctypes.Structure):
-    _fields_ = [("type", ctypes.c_int32), ("pad", ctypes.c_int32),
+    _fields_ = [("type", ctypes.c_int32), ("ion", ctypes.c_int32),
                 ("n", ctypes.c_int64), ("node_index", ctypes.c_void_p),
                 ("params", ctypes.c_void_p), ("states", ctypes.c_void_p)]
 
@@ -406,3 +474,33 @@ def step_cable(mechs, states, v, n_nodes, parent, ga, gb, dt, cm=1.0, nsteps=1,
                          _p(par), _p(a), _p(b), float(dt), float(cm), _p(vv), _p(rhs),
                          _p(d), int(nsteps), float(tol), int(max_iter))
     return vv, rhs, d, out_states
+
+
+def step_ions(mechs, states, v, n_nodes, dt, cm=1.0, nsteps=1, clamp_v=False,
+              tol=NEWTON_TOL, max_iter=NEWTON_MAX_ITER):
+    """nsteps steps with per-node ion currents (orc_step_ions); mechs may
+    carry an "ion" tag.  Returns (v, rhs, d, ion [4][n_nodes], states) after
+    the last step (ion row 0 unused)."""
+    keep = []
+    arr = (_OrcMech * len(mechs))()
+    out_states = []
+    for k, m in enumerate(mechs):
+        p, ni = _f64(m["params"]), _i32(m["node_index"])
+        s = _f64(states[k]).copy()
+        keep += [p, ni]
+        out_states.append(s)
+        arr[k].type = int(m["type"])
+        arr[k].ion = int(m.get("ion", ION_NONE))
+        arr[k].n = ni.size
+        arr[k].node_index = ni.ctypes.data
+        arr[k].params = p.ctypes.data
+        arr[k].states = s.ctypes.data
+    vv = _f64(v).copy()
+    rhs, d = np.zeros(n_nodes), np.zeros(n_nodes)
+    ion = np.zeros((4, int(n_nodes)))
+    ptrs = (ctypes.c_void_p * 4)(None, *[ion[k].ctypes.data for k in (1, 2, 3)])
+    lib().orc_step_ions(len(mechs), ctypes.cast(arr, ctypes.c_void_p), int(n_nodes),
+                        float(dt), float(cm), _p(vv), _p(rhs), _p(d),
+                        ctypes.cast(ptrs, ctypes.c_void_p), int(nsteps),
+                        int(bool(clamp_v)), float(tol), int(max_iter))
+    return vv, rhs, d, ion, out_states

@@ -25,6 +25,12 @@ Parameter block layouts (double precision, one block per mechanism type):
   KIN9 (51):  gbar [S/cm2], e [mV], open state index, then for each of the
               12 lattice edges (see KIN9_EDGES) a_f, b_f, a_b, b_b with the
               forward rate a_f*exp(b_f*v) and backward rate a_b*exp(-b_b*v).
+  KIN3 (15):  gbar, e, open state index, then a_f, b_f, a_b, b_b for the
+              edges (0,1), (1,2), (0,2).
+  CACUM (6):  k [mM/ms per mA/cm2], tau [ms], cai0 [mM], kf [1/(mM ms)],
+              kb [1/ms], btot [mM] of the calcium buffer.
+
+Ion tags (USEION WRITE of the whole current): 0 none, 1 na, 2 k, 3 ca.
 """
 from __future__ import annotations
 
@@ -37,11 +43,18 @@ TYPE_HH = 1
 TYPE_CNEXP = 2
 TYPE_KIN9 = 3
 
+TYPE_CACUM = 4
+TYPE_KIN3 = 5
+ION_NONE, ION_NA, ION_K, ION_CA = 0, 1, 2, 3
+
 HH_NPARAM = 7
 CNEXP_NPARAM = 33
 CNEXP_GATE_BASE = 6
 CNEXP_GATE_STRIDE = 9
 KIN9_NPARAM = 51
+KIN3_NPARAM = 15
+CACUM_NPARAM = 6
+FARADAY = 96485.33212  # C/mol
 
 FORM_EXP, FORM_SIGMOID, FORM_LINOID = 0, 1, 2
 
@@ -150,6 +163,31 @@ def kin9_params(s: Stream, gbar: float = 0.12, e: float = 50.0) -> np.ndarray:
     return p
 
 
+def kin3_params(s: Stream, gbar: float = 0.01, e: float = -85.0, open_state: int = 2,
+                chain: bool = False) -> np.ndarray:
+    """3-state scheme with seeded rates (the 9-state scheme's ranges);
+    chain=True leaves the (0,2) edge out (a linear C-O-I chain)."""
+    p = np.zeros(KIN3_NPARAM, dtype=np.float64)
+    p[0], p[1], p[2] = gbar, e, open_state
+    af = s.loguniform(3, 0.05, 5.0)
+    bf = s.uniform(3, 0.01, 0.04)
+    ab = s.loguniform(3, 0.05, 5.0)
+    bb = s.uniform(3, 0.01, 0.04)
+    for k in range(3):
+        p[3 + 4 * k:3 + 4 * k + 4] = (af[k], bf[k], ab[k], bb[k])
+    if chain:
+        p[3 + 8:3 + 12] = (0.0, 0.0, 0.0, 0.0)
+    return p
+
+
+def cacum_params(depth_um: float = 0.1, tau: float = 200.0, cai0: float = 5e-5,
+                 kf: float = 100.0, kb: float = 0.1, btot: float = 0.05) -> np.ndarray:
+    """Calcium buffer in a submembrane shell of depth_um: an inward ica of
+    1 mA/cm2 adds 1/(2 F depth) mM/ms (unit conversion only)."""
+    k = 1.0 / (2.0 * FARADAY * depth_um * 1e-4)
+    return np.array([k, tau, cai0, kf, kb, btot], dtype=np.float64)
+
+
 # Ten channel templates of the cortical-style mix: name, reversal potential
 # and the gates as (power, activating?) pairs.  Rate forms and constants are
 # drawn per gate from the seed.
@@ -223,6 +261,31 @@ def cortical_mix(n_nodes: int, seed: int = 2, kmax: int = 3,
         mechs.append(dict(type=TYPE_CNEXP, params=p, node_index=ni, name=name))
     v0 = Stream(seed, 103).uniform(n_nodes, v_lo, v_hi)
     return dict(v0=v0, mechs=mechs, n_nodes=n_nodes)
+
+
+# ion carried by each cortical template's current
+CORTICAL_IONS = {"NaT": ION_NA, "NaP": ION_NA, "KT": ION_K, "KP": ION_K, "Kv3": ION_K,
+                 "Ih": ION_NONE, "CaHVA": ION_CA, "CaLVA": ION_CA, "SK": ION_K,
+                 "leak": ION_NONE}
+
+
+def cortical_ions(n_nodes: int, seed: int = 8, kmax: int = 3, kin3_frac: float = 0.5):
+    """The cortical mix with ion tags (sodium, potassium and calcium
+    channels write ina, ik, ica), plus a 3-state potassium channel on a
+    kin3_frac fraction of the nodes and one calcium buffer per node that
+    reads ica.  Returns dict(v0, mechs, n_nodes); mechs carry "ion"."""
+    net = cortical_mix(n_nodes, seed=seed, kmax=kmax)
+    for m in net["mechs"]:
+        m["ion"] = CORTICAL_IONS[m["name"]]
+    s = Stream(seed, 801)
+    nodes = np.arange(n_nodes, dtype=np.int64)
+    ni3 = nodes[s.uniform(n_nodes) < kin3_frac].astype(np.int32)
+    net["mechs"].append(dict(type=TYPE_KIN3, params=kin3_params(Stream(seed, 802)),
+                             node_index=ni3, name="K3state", ion=ION_K))
+    net["mechs"].append(dict(type=TYPE_CACUM, params=cacum_params(),
+                             node_index=nodes.astype(np.int32), name="cacum",
+                             ion=ION_NONE))
+    return net
 
 
 def hh_single(n_nodes: int = 4096, seed: int = 1):

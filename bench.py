@@ -170,7 +170,8 @@ def main():
     ap.add_argument("--block", type=int, default=0, help="fix the fused block size")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--forms", default="all",
-                    help="comma list of batched,kinetic,surrogate,mixed_errors,pade,cable; "
+                    help="comma list of batched,kinetic,surrogate,mixed_errors,pade,cable,"
+                         "ions; "
                          "all; none")
     args = ap.parse_args()
 
@@ -325,7 +326,7 @@ def main():
     forms = None
     if rank == 0 and world == 1 and args.forms != "none":
         from paper_1905_02241_b300 import forms as F
-        want = (["batched", "mixed_errors", "kinetic", "surrogate", "pade", "cable"]
+        want = (["batched", "mixed_errors", "kinetic", "surrogate", "pade", "cable", "ions"]
                 if args.forms == "all"
                 else args.forms.split(","))
         forms = {}

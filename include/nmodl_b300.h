@@ -15,6 +15,24 @@
  *                5.1) advanced by implicit Euler with Newton iteration on the
  *                exact Jacobian J = I - dt A (Section 5.2 derivimplicit /
  *                sparse, Section 5.3 LU), g = gbar x_open.
+ *   NMODL_KIN3   3-state kinetic scheme (edges 0-1, 1-2, 0-2): the implicit
+ *                Euler system of <= 3 equations is solved by Gaussian
+ *                elimination written out for the 3x3 case (the "sparse"
+ *                method with symbolic elimination, Section 5.2), no
+ *                pivoting; g = gbar x_open.
+ *   NMODL_CACUM  2-state calcium accumulation with a buffer (a nonlinear
+ *                derivimplicit system): Newton iteration with the exact
+ *                Jacobian inverted in closed form (the small-matrix direct
+ *                inverse of Section 5.3).  Reads the node calcium current
+ *                ica of the same step (USEION ca READ ica); no membrane
+ *                current of its own.
+ *
+ * Ion currents (USEION WRITE, Section 3; dependency order, Section 4.2):
+ * per-node arrays ina, ik, ica registered on the context receive, from the
+ * current update, the HH sodium and potassium terms and the whole current
+ * of every CNEXP / KIN9 / KIN3 mechanism tagged with that ion; a state
+ * update that reads an ion (NMODL_CACUM) runs after every current update
+ * of the step.
  *
  * Conventions shared by all calls
  *  - Units: v in mV, dt in ms, conductances in S/cm2, currents in mA/cm2,
@@ -64,6 +82,8 @@ extern "C" {
 #define NMODL_HH 1
 #define NMODL_CNEXP 2
 #define NMODL_KIN9 3
+#define NMODL_CACUM 4
+#define NMODL_KIN3 5
 
 /* Parameter blocks (doubles):
  *  NMODL_HH    (7):  gnabar, gkbar, gl, ena, ek, el, celsius.
@@ -81,10 +101,28 @@ extern "C" {
  *                    (3,6),(4,7),(5,8)): a_f, b_f, a_b, b_b, with forward
  *                    rate a_f exp(b_f v) (lower -> higher index) and backward
  *                    rate a_b exp(-b_b v).
+ *  NMODL_KIN3  (15): gbar, e, open state index (0..2), then for the edges
+ *                    (0,1), (1,2), (0,2): a_f, b_f, a_b, b_b as for KIN9.
+ *  NMODL_CACUM (6):  k [mM/ms per mA/cm2], tau [ms] (> 0), cai0 [mM],
+ *                    kf [1/(mM ms)], kb [1/ms], btot [mM] (all >= 0); states
+ *                    (cai, cab) [mM] with
+ *                      cai' = -k ica - kf cai (btot - cab) + kb cab
+ *                             - (cai - cai0)/tau
+ *                      cab' =  kf cai (btot - cab) - kb cab.
+ *                    INITIAL: cai = cai0, cab = kf cai0 btot/(kf cai0 + kb)
+ *                    (kf cai0 + kb > 0 required).
  */
 #define NMODL_HH_NPARAM 7
 #define NMODL_CNEXP_NPARAM 33
 #define NMODL_KIN9_NPARAM 51
+#define NMODL_KIN3_NPARAM 15
+#define NMODL_CACUM_NPARAM 6
+
+/* ------------------------------------------------------------------ ions */
+#define NMODL_ION_NONE 0 /* nonspecific current: written to no ion array */
+#define NMODL_ION_NA 1
+#define NMODL_ION_K 2
+#define NMODL_ION_CA 3
 
 /* ------------------------------------------------------------- precision */
 #define NMODL_FP64 0  /* every operation in IEEE double                    */
@@ -152,7 +190,7 @@ NMODL_API int nmodl_mech_create(nmodl_ctx *ctx, int type, int64_t n_instances,
                       const double *params, int64_t n_params,
                       nmodl_mech **out);
 NMODL_API void nmodl_mech_destroy(nmodl_mech *m);
-/* Number of states per instance (3, n_gates or 9); negative on error. */
+/* Number of states per instance (3, n_gates, 9, 3 or 2); negative on error. */
 NMODL_API int nmodl_mech_n_states(const nmodl_mech *m);
 
 /* INITIAL: gates := minf(v[node]); kinetic states := the stationary
@@ -223,6 +261,25 @@ NMODL_API int nmodl_step_cable(nmodl_ctx *ctx, nmodl_cable *cable,
                                nmodl_mech *const *mechs, int n_mechs, double dt,
                                double cm, double *v, double *rhs, double *d,
                                int nsteps);
+
+/* ---------------------------------------------------------- ion arrays
+ * Register the per-node ion current arrays of the context (device, n_nodes
+ * doubles each, caller-owned; NULL leaves that ion unrecorded).  From then
+ * on nmodl_cur also ACCUMULATES each mechanism's ion currents into them
+ * (the caller zeroes them, as for rhs/d), nmodl_step and nmodl_step_cable
+ * zero the registered arrays at the start of every step, and NMODL_CACUM
+ * reads ica (required: NMODL_ERR_ARG from nmodl_state / nmodl_step when no
+ * ica array is registered).  Calling again with all NULL unregisters.
+ * Registered arrays make nmodl_step take the per-mechanism launch sequence
+ * instead of the fused tile kernel. */
+NMODL_API int nmodl_ctx_set_ions(nmodl_ctx *ctx, int64_t n_nodes, double *ina,
+                                 double *ik, double *ica);
+/* Tag the whole current of a CNEXP, KIN9 or KIN3 mechanism as the current
+ * of ion NMODL_ION_* (default NMODL_ION_NONE).  NMODL_HH always writes its
+ * sodium term to ina and its potassium term to ik (the leak to neither);
+ * NMODL_ERR_ARG for HH or CACUM with a tag other than NONE, or an unknown
+ * ion. */
+NMODL_API int nmodl_mech_set_ion(nmodl_mech *m, int ion);
 
 /* Copy state row k (n_instances doubles) out of / into the mechanism
  * (out/in: host or device).  Checkpoint and resume use these. */

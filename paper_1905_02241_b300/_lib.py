@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnmodl_b300.so")
 
 NMODL_OK = 0
-NMODL_HH, NMODL_CNEXP, NMODL_KIN9 = 1, 2, 3
+NMODL_HH, NMODL_CNEXP, NMODL_KIN9, NMODL_CACUM, NMODL_KIN3 = 1, 2, 3, 4, 5
+NMODL_ION_NONE, NMODL_ION_NA, NMODL_ION_K, NMODL_ION_CA = 0, 1, 2, 3
 NMODL_FP64, NMODL_MIXED = 0, 1
 ERRORS = {
     -1: "NMODL_ERR_ARG", -2: "NMODL_ERR_UNSORTED", -3: "NMODL_ERR_OOM",
@@ -94,6 +95,8 @@ _SIGS = {
     "nmodl_cable_destroy": (None, [_vp]),
     "nmodl_cable_n_cells": (_i32, [_vp]),
     "nmodl_step_cable": (_i32, [_vp, _vp, _vp, _i32, _d, _d, _vp, _vp, _vp, _i32]),
+    "nmodl_ctx_set_ions": (_i32, [_vp, _i64, _vp, _vp, _vp]),
+    "nmodl_mech_set_ion": (_i32, [_vp, _i32]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -158,6 +161,16 @@ def nmodl_mech_create(ctx: int, mtype: int, n_instances: int, node_index_ptr: in
                                  params_ptr or None, int(n_params),
                                  ctypes.byref(h)), "nmodl_mech_create")
     return h.value
+
+
+def nmodl_ctx_set_ions(ctx: int, n_nodes: int, ina_ptr: int, ik_ptr: int,
+                       ica_ptr: int) -> None:
+    _check(lib.nmodl_ctx_set_ions(ctx, int(n_nodes), ina_ptr or None, ik_ptr or None,
+                                  ica_ptr or None), "nmodl_ctx_set_ions")
+
+
+def nmodl_mech_set_ion(m: int, ion: int) -> None:
+    _check(lib.nmodl_mech_set_ion(m, int(ion)), "nmodl_mech_set_ion")
 
 
 def nmodl_mech_destroy(m: int) -> None:

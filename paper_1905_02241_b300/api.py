@@ -16,11 +16,13 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (NMODL_CNEXP, NMODL_FP64, NMODL_HH, NMODL_KIN9, NMODL_MIXED,
-                   NmodlError)
+from ._lib import (NMODL_CACUM, NMODL_CNEXP, NMODL_FP64, NMODL_HH, NMODL_ION_CA,
+                   NMODL_ION_K, NMODL_ION_NA, NMODL_ION_NONE, NMODL_KIN3, NMODL_KIN9,
+                   NMODL_MIXED, NmodlError)
 
 __all__ = ["Context", "Mechanism", "NmodlError", "NMODL_HH", "NMODL_CNEXP",
-           "NMODL_KIN9", "NMODL_FP64", "NMODL_MIXED"]
+           "NMODL_KIN9", "NMODL_KIN3", "NMODL_CACUM", "NMODL_FP64", "NMODL_MIXED",
+           "NMODL_ION_NONE", "NMODL_ION_NA", "NMODL_ION_K", "NMODL_ION_CA"]
 
 
 def _dptr(t: torch.Tensor, dtype=torch.float64, device=None) -> int:
@@ -70,6 +72,19 @@ class Context:
                         _dptr(d, device=self.device), nsteps)
         self.leave()
 
+    def set_ions(self, ina=None, ik=None, ica=None) -> None:
+        """Register per-node ion current arrays (float64 device tensors of
+        n_nodes; None leaves that ion unrecorded; all None unregisters).
+        The tensors must stay alive while registered."""
+        ts = [t for t in (ina, ik, ica) if t is not None]
+        n = ts[0].numel() if ts else 0
+        if any(t.numel() != n for t in ts):
+            raise ValueError("ion arrays must have equal lengths")
+        ptr = [0 if t is None else _dptr(t, device=self.device) for t in (ina, ik, ica)]
+        self.enter()
+        _lib.nmodl_ctx_set_ions(self.handle, n, *ptr)
+        self._ions = (ina, ik, ica)
+
     def plan(self, mechs) -> dict:
         return _lib.nmodl_plan_describe(self.handle, [m.handle for m in mechs])
 
@@ -80,7 +95,8 @@ class Context:
 
 
 class Mechanism:
-    def __init__(self, ctx: Context, mtype: int, node_index, n_nodes: int, params):
+    def __init__(self, ctx: Context, mtype: int, node_index, n_nodes: int, params,
+                 ion: int = NMODL_ION_NONE):
         self.ctx = ctx
         self.type = int(mtype)
         self.n_nodes = int(n_nodes)
@@ -101,6 +117,14 @@ class Mechanism:
                                              ptr if n else 0, self.n_nodes,
                                              p.ctypes.data, p.size)
         self.n_states = _lib.nmodl_mech_n_states(self.handle)
+        self.ion = NMODL_ION_NONE
+        if ion != NMODL_ION_NONE:
+            self.set_ion(ion)
+
+    def set_ion(self, ion: int) -> None:
+        """Tag the mechanism's whole current as the current of ion `ion`."""
+        _lib.nmodl_mech_set_ion(self.handle, ion)
+        self.ion = int(ion)
 
     def init(self, v: torch.Tensor) -> None:
         self.ctx.enter()

@@ -18,14 +18,15 @@ namespace nmodl {
 cudaError_t enqueue_surrogate_state(nmodl_mech* m, double dt, const double* v);
 }  // namespace nmodl
 
-// Drop the cached step plans (and their graphs) that involve mechanism m.
+// Drop the cached step plans (and their graphs) that involve mechanism m
+// (all of them for m == nullptr).
 void nmodl_invalidate_plans(nmodl_ctx* c, nmodl_mech* m) {
     c->epoch++;
     auto& P = c->plans;
     P.erase(std::remove_if(P.begin(), P.end(),
                            [m](const std::unique_ptr<Plan>& p) {
-                               return std::find(p->mechs.begin(), p->mechs.end(), m) !=
-                                      p->mechs.end();
+                               return !m || std::find(p->mechs.begin(), p->mechs.end(), m) !=
+                                                p->mechs.end();
                            }),
             P.end());
 }
@@ -95,6 +96,39 @@ static int build_desc(nmodl_mech* m) {
                                   q[8], (int)q[0]);
         }
         m->n_states = d.n_gates;
+        return NMODL_OK;
+    }
+    if (m->type == NMODL_KIN3) {
+        if (p.size() != NMODL_KIN3_NPARAM) return NMODL_ERR_ARG;
+        if (!is_int(p[2], 0, 2)) return NMODL_ERR_ARG;
+        Kin3D& k = m->k3;
+        k = Kin3D{};
+        k.gbar = p[0];
+        k.e = p[1];
+        k.open = (int)p[2];
+        for (int e = 0; e < 3; ++e) {
+            k.af[e] = p[3 + 4 * e];
+            k.bf[e] = p[4 + 4 * e];
+            k.ab[e] = p[5 + 4 * e];
+            k.bb[e] = p[6 + 4 * e];
+            if (k.af[e] < 0.0 || k.ab[e] < 0.0) return NMODL_ERR_ARG;
+        }
+        m->n_states = 3;
+        return NMODL_OK;
+    }
+    if (m->type == NMODL_CACUM) {
+        if (p.size() != NMODL_CACUM_NPARAM) return NMODL_ERR_ARG;
+        for (double x : p)
+            if (x < 0.0) return NMODL_ERR_ARG;
+        if (!(p[1] > 0.0) || !(p[3] * p[2] + p[4] > 0.0)) return NMODL_ERR_ARG;
+        CacumD& c = m->cd;
+        c.k = p[0];
+        c.rtau = 1.0 / p[1];
+        c.cai0 = p[2];
+        c.kf = p[3];
+        c.kb = p[4];
+        c.btot = p[5];
+        m->n_states = 2;
         return NMODL_OK;
     }
     if (m->type == NMODL_KIN9) {
@@ -260,6 +294,8 @@ static void free_mech(nmodl_mech* m) {
     cudaFree(m->d_md);
     cudaFree(m->d_kd);
     cudaFree(m->d_cnt);
+    cudaFree(m->d_k3);
+    cudaFree(m->d_cd);
     delete m;
 }
 
@@ -296,6 +332,8 @@ int nmodl_mech_create(nmodl_ctx* c, int type, int64_t n, const int32_t* node_ind
         if ((e = dalloc(&m->d_md, 1)) != cudaSuccess) break;
         if ((e = dalloc(&m->d_kd, 1)) != cudaSuccess) break;
         if ((e = dalloc(&m->d_cnt, 1)) != cudaSuccess) break;
+        if ((e = dalloc(&m->d_k3, 1)) != cudaSuccess) break;
+        if ((e = dalloc(&m->d_cd, 1)) != cudaSuccess) break;
         if ((e = dalloc(&d_flags, 1)) != cudaSuccess) break;
         // every copy and fill below is ordered on the context stream, which
         // need not synchronise with the legacy default stream
@@ -307,6 +345,8 @@ int nmodl_mech_create(nmodl_ctx* c, int type, int64_t n, const int32_t* node_ind
             break;
         if ((e = cudaMemcpyAsync(m->d_md, &m->md, sizeof(MechD), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(m->d_kd, &m->kd, sizeof(Kin9D), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(m->d_k3, &m->k3, sizeof(Kin3D), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(m->d_cd, &m->cd, sizeof(CacumD), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(m->d_cnt, 0, sizeof(KinCounters), c->stream)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(d_flags, 0, sizeof(int32_t), c->stream)) != cudaSuccess) break;
         launch_validate_index(m->d_ni, n, n_nodes, d_flags, c->stream);
@@ -349,6 +389,10 @@ int nmodl_init(nmodl_mech* m, const double* v) {
     DeviceGuard g(c->device);
     if (m->type == NMODL_KIN9)
         launch_kin9_init(m->d_kd, m->n, m->d_ni, v, m->d_states, m->stride, c->d_err, c->stream);
+    else if (m->type == NMODL_KIN3)
+        launch_kin3_init(m->d_k3, m->n, m->d_ni, v, m->d_states, m->stride, c->d_err, c->stream);
+    else if (m->type == NMODL_CACUM)
+        launch_cacum_init(m->d_cd, m->n, m->d_states, m->stride, c->stream);
     else
         launch_init_gates(m->d_md, m->n_states, m->n, m->d_ni, v, m->d_states, m->stride,
                           c->d_err, c->stream);
@@ -364,6 +408,13 @@ void nmodl_enqueue_state(nmodl_mech* m, double dt, const double* v) {
         launch_kin9_state(o.precision, m->d_kd, m->n, m->d_ni, v, m->d_states, m->stride,
                           dt, nullptr, o.newton_tol, o.newton_max_iter, o.ir_max, nullptr, 0,
                           nullptr, m->d_cnt, c->d_err, c->stream);
+    else if (m->type == NMODL_KIN3)
+        launch_kin3_state(o.precision, m->d_k3, m->n, m->d_ni, v, m->d_states, m->stride, dt,
+                          o.newton_tol, o.ir_max, m->d_cnt, c->d_err, c->stream);
+    else if (m->type == NMODL_CACUM)
+        launch_cacum_state(m->d_cd, m->n, m->d_ni, c->ion[NMODL_ION_CA], m->d_states,
+                           m->stride, dt, o.newton_tol, o.newton_max_iter, m->d_cnt, c->d_err,
+                           c->stream);
     else
         launch_state_gates(o.precision, m->d_md, m->n_states, m->n, m->d_ni, v,
                            m->d_states, m->stride, dt, o.cnexp_pade, c->d_err, c->stream);
@@ -378,14 +429,40 @@ void nmodl_count_states(nmodl_mech* m, int64_t k) {
 
 void nmodl_enqueue_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
     nmodl_ctx* c = m->ctx;
-    const void* desc = (m->type == NMODL_KIN9) ? (const void*)m->d_kd : (const void*)m->d_md;
-    launch_cur_seg(m->type == NMODL_KIN9 ? NMODL_KIN9 : NMODL_CNEXP, desc, m->n_chunks,
-                   m->d_chunk, m->d_ni, v, m->d_states, m->stride, rhs, d, c->d_err,
-                   c->stream);
+    if (m->type == NMODL_CACUM) return;  // no membrane current
+    const void* desc = (m->type == NMODL_KIN9)   ? (const void*)m->d_kd
+                       : (m->type == NMODL_KIN3) ? (const void*)m->d_k3
+                                                 : (const void*)m->d_md;
+    const int kind = (m->type == NMODL_KIN9 || m->type == NMODL_KIN3) ? m->type : NMODL_CNEXP;
+    double* ion_a = nullptr;
+    double* ion_b = nullptr;
+    if (m->type == NMODL_HH) {
+        ion_a = c->ion[NMODL_ION_NA];
+        ion_b = c->ion[NMODL_ION_K];
+    } else if (m->ion != NMODL_ION_NONE) {
+        ion_a = c->ion[m->ion];
+    }
+    launch_cur_seg(kind, desc, m->n_chunks, m->d_chunk, m->d_ni, v, m->d_states, m->stride,
+                   rhs, d, ion_a, ion_b, c->d_err, c->stream);
+}
+
+void nmodl_zero_ions(nmodl_ctx* c, int64_t n_nodes) {
+    for (int q = 1; q < 4; ++q)
+        if (c->ion[q] && n_nodes > 0)
+            cudaMemsetAsync(c->ion[q], 0, n_nodes * sizeof(double), c->stream);
+}
+
+int nmodl_check_ion_reads(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs) {
+    for (int i = 0; i < n_mechs; ++i)
+        if (mechs[i]->type == NMODL_CACUM && mechs[i]->n > 0 &&
+            (!c->ion[NMODL_ION_CA] || c->ion_nodes != mechs[i]->n_nodes))
+            return NMODL_ERR_ARG;
+    return NMODL_OK;
 }
 
 int nmodl_state(nmodl_mech* m, double dt, const double* v) {
     if (!m || !(dt > 0.0) || !std::isfinite(dt) || (m->n > 0 && !v)) return NMODL_ERR_ARG;
+    if (nmodl_check_ion_reads(m->ctx, &m, 1)) return NMODL_ERR_ARG;
     DeviceGuard g(m->ctx->device);
     nmodl_enqueue_state(m, dt, v);
     nmodl_count_states(m, 1);
@@ -394,6 +471,7 @@ int nmodl_state(nmodl_mech* m, double dt, const double* v) {
 
 int nmodl_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
     if (!m || (m->n > 0 && (!v || !rhs || !d))) return NMODL_ERR_ARG;
+    if (m->ctx->has_ions() && m->ctx->ion_nodes != m->n_nodes) return NMODL_ERR_ARG;
     DeviceGuard g(m->ctx->device);
     nmodl_enqueue_cur(m, v, rhs, d);
     return cuda_status(cudaGetLastError());
@@ -485,9 +563,10 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     p->mechs.assign(mechs, mechs + n_mechs);
     p->precision = c->opt.precision;
     p->n_nodes = mechs[0]->n_nodes;
-    bool cnexp = n_mechs <= kMaxMechsFused;
+    // the fused tile kernel covers HH and CNEXP mechanisms without ion arrays
+    bool cnexp = n_mechs <= kMaxMechsFused && !c->has_ions();
     for (int i = 0; i < n_mechs; ++i)
-        if (mechs[i]->type == NMODL_KIN9) cnexp = false;
+        if (mechs[i]->type != NMODL_HH && mechs[i]->type != NMODL_CNEXP) cnexp = false;
     p->fused = false;
     const bool dbg = std::getenv("NMODL_PLAN_DEBUG") != nullptr;
     if (!cnexp || p->n_nodes == 0) {
@@ -760,6 +839,7 @@ static cudaError_t enqueue_generic_steps(nmodl_ctx* c, nmodl_mech* const* mechs,
     for (int s = 0; s < nsteps; ++s) {
         cudaMemsetAsync(rhs, 0, n_nodes * sizeof(double), c->stream);
         cudaMemsetAsync(d, 0, n_nodes * sizeof(double), c->stream);
+        nmodl_zero_ions(c, n_nodes);
         for (int i = 0; i < n_mechs; ++i) nmodl_enqueue_cur(mechs[i], v, rhs, d);
         launch_vupdate(n_nodes, v, rhs, d, 1e-3 * cm / dt, c->opt.clamp_v, c->d_err, c->stream);
         for (int i = 0; i < n_mechs; ++i) nmodl_enqueue_state(mechs[i], dt, v);
@@ -819,6 +899,8 @@ int nmodl_step(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, double dt, d
         if (!mechs[i] || mechs[i]->ctx != c || mechs[i]->n_nodes != n_nodes) return NMODL_ERR_ARG;
     if (nsteps == 0 || n_nodes == 0) return NMODL_OK;
     if (!v || !rhs || !d) return NMODL_ERR_ARG;
+    if (c->has_ions() && c->ion_nodes != n_nodes) return NMODL_ERR_ARG;
+    if (nmodl_check_ion_reads(c, mechs, n_mechs)) return NMODL_ERR_ARG;
     DeviceGuard g(c->device);
     int rc = NMODL_OK;
     Plan* p = get_plan(c, mechs, n_mechs, v, &rc);
@@ -848,6 +930,33 @@ int nmodl_plan_describe(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, int
         }
     }
     return NMODL_ERR_ARG;
+}
+
+int nmodl_ctx_set_ions(nmodl_ctx* c, int64_t n_nodes, double* ina, double* ik, double* ica) {
+    if (!c || n_nodes < 0 || ((ina || ik || ica) && n_nodes == 0)) return NMODL_ERR_ARG;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    // plans and graphs hold the previous arrays (and the fused/unfused choice)
+    nmodl_invalidate_plans(c, nullptr);
+    c->ion[NMODL_ION_NA] = ina;
+    c->ion[NMODL_ION_K] = ik;
+    c->ion[NMODL_ION_CA] = ica;
+    c->ion_nodes = (ina || ik || ica) ? n_nodes : 0;
+    return NMODL_OK;
+}
+
+int nmodl_mech_set_ion(nmodl_mech* m, int ion) {
+    if (!m || ion < NMODL_ION_NONE || ion > NMODL_ION_CA) return NMODL_ERR_ARG;
+    if ((m->type == NMODL_HH || m->type == NMODL_CACUM) && ion != NMODL_ION_NONE)
+        return NMODL_ERR_ARG;
+    if (m->ion == ion) return NMODL_OK;
+    DeviceGuard g(m->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(m->ctx->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    nmodl_invalidate_plans(m->ctx, m);
+    m->ion = ion;
+    return NMODL_OK;
 }
 
 int nmodl_get_state(nmodl_mech* m, int k, double* out) {

@@ -87,6 +87,7 @@ static cudaError_t enqueue_cable_steps(nmodl_ctx* c, nmodl_cable* cb, nmodl_mech
     for (int s = 0; s < nsteps; ++s) {
         cudaMemsetAsync(rhs, 0, cb->n_nodes * sizeof(double), c->stream);
         cudaMemsetAsync(d, 0, cb->n_nodes * sizeof(double), c->stream);
+        nmodl_zero_ions(c, cb->n_nodes);
         for (int i = 0; i < n_mechs; ++i) nmodl_enqueue_cur(mechs[i], v, rhs, d);
         launch_cable_solve(cb->n_cells, cb->d_cell_off, cb->d_parent, cb->d_ga, cb->d_gb,
                            1e-3 * cm / dt, v, rhs, d, cb->d_d2, cb->d_r2, c->d_err, c->stream);
@@ -107,6 +108,8 @@ extern "C" NMODL_API int nmodl_step_cable(nmodl_ctx* c, nmodl_cable* cb,
             return NMODL_ERR_ARG;
     if (nsteps == 0) return NMODL_OK;
     if (!v || !rhs || !d) return NMODL_ERR_ARG;
+    if (c->has_ions() && c->ion_nodes != cb->n_nodes) return NMODL_ERR_ARG;
+    if (nmodl_check_ion_reads(c, mechs, n_mechs)) return NMODL_ERR_ARG;
     DeviceGuard dg(c->device);
     for (int i = 0; i < n_mechs; ++i) nmodl_count_states(mechs[i], nsteps);
     std::vector<nmodl_mech*> list(mechs, mechs + n_mechs);

@@ -99,49 +99,98 @@ __device__ __forceinline__ void cur_kin9_d(const Kin9D& K, const double* st,
     i = g * (vv - K.e);
 }
 
+__device__ __forceinline__ void cur_kin3_d(const Kin3D& K, const double* st,
+                                           int64_t stride, int64_t j, double vv,
+                                           double& i, double& g) {
+    g = K.gbar * st[K.open * stride + j];
+    i = g * (vv - K.e);
+}
+
+// i, g and the ion parts (ia, ib) of instance j: HH splits its current into
+// the sodium and potassium terms; the other kinds report the whole current
+template <int KIND, bool ION>
+__device__ __forceinline__ void cur_any_d(const void* desc, const double* st, int64_t stride,
+                                          int64_t j, double vv, double& i, double& g,
+                                          double& ia, double& ib) {
+    if (KIND == NMODL_KIN9) {
+        cur_kin9_d(*(const Kin9D*)desc, st, stride, j, vv, i, g);
+        ia = i;
+        ib = 0.0;
+    } else if (KIND == NMODL_KIN3) {
+        cur_kin3_d(*(const Kin3D*)desc, st, stride, j, vv, i, g);
+        ia = i;
+        ib = 0.0;
+    } else {
+        const MechD& M = *(const MechD*)desc;
+        if (ION && M.kind == NMODL_HH) {
+            const double m = st[j], h = st[stride + j], nn = st[2 * stride + j];
+            const double gna = M.hh_g[0] * m * m * m * h;
+            const double gk = M.hh_g[1] * nn * nn * nn * nn;
+            const double gl = M.hh_g[2];
+            ia = gna * (vv - M.hh_e[0]);
+            ib = gk * (vv - M.hh_e[1]);
+            i = ia + ib + gl * (vv - M.hh_e[2]);
+            g = gna + gk + gl;
+        } else {
+            cur_cnexp_d(M, st, stride, j, vv, i, g);
+            ia = i;
+            ib = 0.0;
+        }
+    }
+}
+
 // One warp per segment-aligned chunk [chunk[w], chunk[w+1]) of instances:
 // chunks start at segment heads, so every node's instances are reduced by a
 // single warp and each node is written by exactly one lane (deterministic,
 // no atomics).  Within a 32-wide piece a segmented inclusive scan on the
 // sorted keys sums each node's terms; a segment that runs past the piece is
-// carried into the next piece from lane 31.
-template <int KIND>
+// carried into the next piece from lane 31.  With ION the ion parts of the
+// current (USEION WRITE) go through the same scan into ion_a / ion_b.
+template <int KIND, bool ION>
 __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
                           const int32_t* __restrict__ chunk,
                           const int32_t* __restrict__ ni,
                           const double* __restrict__ v,
                           const double* __restrict__ st, int64_t stride,
-                          double* rhs, double* d, int32_t* err) {
+                          double* rhs, double* d, double* ion_a, double* ion_b,
+                          int32_t* err) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (w >= n_chunks) return;
     const int64_t s = chunk[w], e = chunk[w + 1];
-    double ci = 0.0, cg = 0.0;
+    double ci = 0.0, cg = 0.0, ca = 0.0, cb = 0.0;
     int ckey = INT_MIN;
     for (int64_t base = s; base < e; base += 32) {
         const int64_t j = base + lane;
         const bool valid = j < e;
         const int key = valid ? ni[j] : -1 - lane;  // invalid lanes never match
-        double vi = 0.0, vg = 0.0;
-        if (valid) {
-            const double vv = v[key];
-            if (KIND == NMODL_KIN9)
-                cur_kin9_d(*(const Kin9D*)desc, st, stride, j, vv, vi, vg);
-            else
-                cur_cnexp_d(*(const MechD*)desc, st, stride, j, vv, vi, vg);
-        }
+        double vi = 0.0, vg = 0.0, va = 0.0, vb = 0.0;
+        if (valid) cur_any_d<KIND, ION>(desc, st, stride, j, v[key], vi, vg, va, vb);
         if (lane == 0 && key == ckey) {
             vi += ci;
             vg += cg;
+            if (ION) {
+                va += ca;
+                vb += cb;
+            }
         }
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const double oi = __shfl_up_sync(0xffffffffu, vi, off);
             const double og = __shfl_up_sync(0xffffffffu, vg, off);
+            double oa = 0.0, ob = 0.0;
+            if (ION) {
+                oa = __shfl_up_sync(0xffffffffu, va, off);
+                ob = __shfl_up_sync(0xffffffffu, vb, off);
+            }
             const int ok = __shfl_up_sync(0xffffffffu, key, off);
             if (lane >= off && ok == key) {
                 vi += oi;
                 vg += og;
+                if (ION) {
+                    va += oa;
+                    vb += ob;
+                }
             }
         }
         const int nkey = __shfl_down_sync(0xffffffffu, key, 1);
@@ -153,9 +202,17 @@ __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
             if (!isfinite(r) || !isfinite(dd)) latch_error(err, NMODL_ERR_NONFINITE);
             rhs[key] = r;
             d[key] = dd;
+            if (ION) {
+                if (ion_a) ion_a[key] += va;
+                if (ion_b) ion_b[key] += vb;
+            }
         }
         ci = __shfl_sync(0xffffffffu, vi, 31);
         cg = __shfl_sync(0xffffffffu, vg, 31);
+        if (ION) {
+            ca = __shfl_sync(0xffffffffu, va, 31);
+            cb = __shfl_sync(0xffffffffu, vb, 31);
+        }
         ckey = __shfl_sync(0xffffffffu, cont ? key : INT_MIN, 31);
     }
 }
@@ -428,15 +485,22 @@ void launch_state_gates(int prec, const MechD* md, int n_gates, int64_t n,
 void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
                     const int32_t* chunk, const int32_t* ni, const double* v,
                     const double* st, int64_t stride, double* rhs, double* d,
-                    int32_t* err, cudaStream_t s) {
+                    double* ion_a, double* ion_b, int32_t* err, cudaStream_t s) {
     if (n_chunks == 0) return;
     const int block = 256;
     const int64_t threads = n_chunks * 32;
     const int grid = (int)((threads + block - 1) / block);
-    if (kind == NMODL_KIN9)
-        k_cur_seg<NMODL_KIN9><<<grid, block, 0, s>>>(desc, n_chunks, chunk, ni, v, st, stride, rhs, d, err);
-    else
-        k_cur_seg<NMODL_CNEXP><<<grid, block, 0, s>>>(desc, n_chunks, chunk, ni, v, st, stride, rhs, d, err);
+    const bool ion = ion_a || ion_b;
+#define NMODL_CUR_SEG(K, I) \
+    k_cur_seg<K, I><<<grid, block, 0, s>>>(desc, n_chunks, chunk, ni, v, st, stride, rhs, d, ion_a, ion_b, err)
+    if (kind == NMODL_KIN9) {
+        if (ion) NMODL_CUR_SEG(NMODL_KIN9, true); else NMODL_CUR_SEG(NMODL_KIN9, false);
+    } else if (kind == NMODL_KIN3) {
+        if (ion) NMODL_CUR_SEG(NMODL_KIN3, true); else NMODL_CUR_SEG(NMODL_KIN3, false);
+    } else {
+        if (ion) NMODL_CUR_SEG(NMODL_CNEXP, true); else NMODL_CUR_SEG(NMODL_CNEXP, false);
+    }
+#undef NMODL_CUR_SEG
 }
 
 // grid = blocks of this launch (one per tile, or the resident count in the

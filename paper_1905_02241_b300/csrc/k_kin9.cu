@@ -67,22 +67,6 @@ __device__ __forceinline__ void lu_band_solve(const R (&M)[9][9], R (&b)[9]) {
     }
 }
 
-__device__ __forceinline__ void warp_count(KinCounters* cnt, unsigned long long it,
-                                           unsigned long long nc, int mx) {
-    if (!cnt) return;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        it += __shfl_down_sync(0xffffffffu, it, o);
-        nc += __shfl_down_sync(0xffffffffu, nc, o);
-        mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (it) atomicAdd(&cnt->iters, it);
-        if (nc) atomicAdd(&cnt->nonconv, nc);
-        if (mx) atomicMax(&cnt->max_iter_seen, mx);
-    }
-}
-
 }  // namespace
 
 // ------------------------------------------------------------- INITIAL

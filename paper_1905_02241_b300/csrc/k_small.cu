@@ -1,0 +1,279 @@
+// k_small.cu -- state updates of the small systems for sm_103a.
+//
+//  NMODL_KIN3   3-state kinetic scheme x' = A(v) x (edges 0-1, 1-2, 0-2).
+//               Implicit Euler: (I - dt A) y = x.  For a linear scheme the
+//               first Newton update from y = x is already the solution, so
+//               the step is one solve, done by Gaussian elimination written
+//               out for the 3x3 system ("sparse" with symbolic elimination,
+//               Section 5.2).  J = I - dt A is an M-matrix whose columns sum
+//               to one, so elimination without pivoting is stable (it is
+//               the elimination partial pivoting would choose).
+//  NMODL_CACUM  2-state calcium buffer, nonlinear (binding term kf cai
+//               (btot - cab)).  Implicit Euler by Newton iteration with the
+//               exact Jacobian, each update solved with the closed-form
+//               inverse of the 2x2 matrix (the small-matrix direct inverse
+//               of Section 5.3; no pivoting, no branches).  The calcium
+//               current ica of the node is read from the ion array filled by
+//               the current updates of the same step.
+//
+// One thread per instance; states are SoA rows of `stride` doubles.  The
+// calcium buffer has no transcendental function and is memory bound, so
+// both precisions run it in FP64.
+#include "kernels.cuh"
+
+namespace nmodl {
+
+namespace {
+
+// rates of the three edges at v: kf[e] (lo -> hi) and kb[e] (hi -> lo)
+__device__ __forceinline__ void kin3_rates_d(const Kin3D& K, double v, double (&kf)[3],
+                                             double (&kb)[3]) {
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        kf[e] = K.af[e] * exp_tang(K.bf[e] * v);
+        kb[e] = K.ab[e] * exp_tang(-K.bb[e] * v);
+    }
+}
+
+// Row-major M = I - dt A from the edge rates: off-diagonals -dt k, the
+// diagonal 1 + dt (outflow of the state).
+template <typename R>
+__device__ __forceinline__ void kin3_matrix(const R (&kf)[3], const R (&kb)[3], R dt,
+                                            R (&M)[3][3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) M[a][b] = (a == b) ? R(1) : R(0);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int lo = kin3_lo(e), hi = kin3_hi(e);
+        M[hi][lo] = -dt * kf[e];
+        M[lo][hi] = -dt * kb[e];
+        M[lo][lo] += dt * kf[e];
+        M[hi][hi] += dt * kb[e];
+    }
+}
+
+// Gaussian elimination of the 3x3 system, written out: M y = b.
+template <typename R>
+__device__ __forceinline__ void solve3(const R (&M)[3][3], R (&b)[3]) {
+    const R r0 = R(1) / M[0][0];
+    const R l10 = M[1][0] * r0, l20 = M[2][0] * r0;
+    const R u11 = M[1][1] - l10 * M[0][1], u12 = M[1][2] - l10 * M[0][2];
+    const R s21 = M[2][1] - l20 * M[0][1], s22 = M[2][2] - l20 * M[0][2];
+    const R r1 = R(1) / u11;
+    const R l21 = s21 * r1;
+    const R u22 = s22 - l21 * u12;
+    const R z1 = b[1] - l10 * b[0];
+    const R z2 = b[2] - l20 * b[0] - l21 * z1;
+    b[2] = z2 / u22;
+    b[1] = (z1 - u12 * b[2]) * r1;
+    b[0] = (b[0] - M[0][1] * b[1] - M[0][2] * b[2]) * r0;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- KIN3
+
+// INITIAL: stationary distribution by the Markov chain tree theorem: pi_s
+// is proportional to the sum, over the spanning trees directed to s, of the
+// products of their rates (three trees per state for three states).
+__global__ void k_kin3_init(const Kin3D* __restrict__ kd, int64_t n,
+                            const int32_t* __restrict__ ni, const double* __restrict__ v,
+                            double* st, int64_t stride, int32_t* err) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double kf[3], kb[3];
+    kin3_rates_d(*kd, v[ni[i]], kf, kb);
+    // k01 = kf0, k10 = kb0, k12 = kf1, k21 = kb1, k02 = kf2, k20 = kb2
+    const double w0 = kb[0] * kb[2] + kb[0] * kb[1] + kf[1] * kb[2];
+    const double w1 = kf[0] * kb[1] + kf[0] * kb[2] + kf[2] * kb[1];
+    const double w2 = kf[2] * kf[1] + kf[2] * kb[0] + kf[0] * kf[1];
+    const double r = 1.0 / (w0 + w1 + w2);
+    const double p[3] = {w0 * r, w1 * r, w2 * r};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(p[a])) latch_error(err, NMODL_ERR_NONFINITE);
+        st[a * stride + i] = p[a];
+    }
+}
+
+// FP64: one solve.  MIXED: rates and the elimination in FP32, then
+// iterative refinement with the FP64 residual x - J y (J's diagonal rebuilt
+// in FP64 from the FP32 off-diagonals so that its columns sum to one) until
+// max|delta| <= tol or ir_max refinements.
+template <int PREC>
+__global__ void __launch_bounds__(256)
+    k_kin3_state(const Kin3D* __restrict__ kd, int64_t n, const int32_t* __restrict__ ni,
+                 const double* __restrict__ v, double* st, int64_t stride, double dt,
+                 double tol, int ir_max, KinCounters* cnt, int32_t* err) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long it_sum = 0, nc_sum = 0;
+    int it_max = 0;
+    if (i < n) {
+        const Kin3D& K = *kd;
+        const double vv = v[ni[i]];
+        double x[3], y[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) x[a] = st[a * stride + i];
+        int iters = 1;
+        if (PREC == NMODL_FP64) {
+            double kf[3], kb[3], M[3][3];
+            kin3_rates_d(K, vv, kf, kb);
+            kin3_matrix(kf, kb, dt, M);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) y[a] = x[a];
+            solve3(M, y);
+        } else {
+            float kf[3], kb[3], M[3][3];
+            const float vf = (float)vv, dtf = (float)dt;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                kf[e] = (float)K.af[e] * __expf((float)K.bf[e] * vf);
+                kb[e] = (float)K.ab[e] * __expf(-(float)K.bb[e] * vf);
+            }
+            kin3_matrix(kf, kb, dtf, M);
+            double off[3][3], diag[3] = {1.0, 1.0, 1.0};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) off[a][b] = (a == b) ? 0.0 : (double)M[a][b];
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    if (a != b) diag[b] -= off[a][b];
+            float yf[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) yf[a] = (float)x[a];
+            solve3(M, yf);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) y[a] = (double)yf[a];
+            bool done = false;
+            for (int k = 0; k < ir_max && !done; ++k) {
+                float r[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    double ra = x[a] - diag[a] * y[a];
+#pragma unroll
+                    for (int b = 0; b < 3; ++b)
+                        if (b != a) ra -= off[a][b] * y[b];
+                    r[a] = (float)ra;
+                }
+                solve3(M, r);
+                float dmax = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    y[a] += (double)r[a];
+                    dmax = fmaxf(dmax, fabsf(r[a]));
+                }
+                ++iters;
+                done = (double)dmax <= tol;
+            }
+            if (!done && ir_max > 0) nc_sum = 1;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!isfinite(y[a])) latch_error(err, NMODL_ERR_NONFINITE);
+            st[a * stride + i] = y[a];
+        }
+        it_sum = iters;
+        it_max = iters;
+    }
+    warp_count(cnt, it_sum, nc_sum, it_max);
+}
+
+// ------------------------------------------------------------ CACUM
+
+__global__ void k_cacum_init(const CacumD* __restrict__ cd, int64_t n, double* st,
+                             int64_t stride) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const CacumD& C = *cd;
+    st[i] = C.cai0;
+    st[stride + i] = C.kf * C.cai0 * C.btot / (C.kf * C.cai0 + C.kb);
+}
+
+// Newton on F(y) = y - x - dt f(y) with J = I - dt df/dy:
+//   J = [[1 + dt (kf (btot - y1) + 1/tau), -dt (kf y0 + kb)],
+//        [-dt kf (btot - y1),               1 + dt (kf y0 + kb)]]
+// delta = J^-1 (-F) by the adjugate over the determinant; stop when both
+// |delta| <= tol or after max_iter updates.
+__global__ void __launch_bounds__(256)
+    k_cacum_state(const CacumD* __restrict__ cd, int64_t n, const int32_t* __restrict__ ni,
+                  const double* __restrict__ ica, double* st, int64_t stride, double dt,
+                  double tol, int max_iter, KinCounters* cnt, int32_t* err) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long it_sum = 0, nc_sum = 0;
+    int it_max = 0;
+    if (i < n) {
+        const CacumD C = *cd;
+        const double x0 = st[i], x1 = st[stride + i];
+        const double src = C.rtau * C.cai0 - C.k * ica[ni[i]];  // constant part of f0
+        double y0 = x0, y1 = x1;
+        int it = 0;
+        bool conv = false;
+        while (it < max_iter) {
+            const double fr = C.btot - y1;
+            const double on = C.kf * fr, off = fma(C.kf, y0, C.kb);
+            const double bind = fma(on, y0, -C.kb * y1);
+            const double f0 = src - bind - C.rtau * y0;
+            const double r0 = fma(dt, f0, x0 - y0);
+            const double r1 = fma(dt, bind, x1 - y1);
+            const double a = fma(dt, on + C.rtau, 1.0), b = -dt * off;
+            const double c = -dt * on, d = fma(dt, off, 1.0);
+            const double rdet = 1.0 / fma(a, d, -b * c);
+            const double d0 = fma(d, r0, -b * r1) * rdet;
+            const double d1 = fma(a, r1, -c * r0) * rdet;
+            y0 += d0;
+            y1 += d1;
+            ++it;
+            if (fabs(d0) <= tol && fabs(d1) <= tol) {
+                conv = true;
+                break;
+            }
+        }
+        if (!isfinite(y0) || !isfinite(y1)) latch_error(err, NMODL_ERR_NONFINITE);
+        st[i] = y0;
+        st[stride + i] = y1;
+        it_sum = it;
+        nc_sum = conv ? 0 : 1;
+        it_max = it;
+    }
+    warp_count(cnt, it_sum, nc_sum, it_max);
+}
+
+// ------------------------------------------------------------ launches
+
+void launch_kin3_init(const Kin3D* kd, int64_t n, const int32_t* ni, const double* v,
+                      double* st, int64_t stride, int32_t* err, cudaStream_t s) {
+    if (n == 0) return;
+    k_kin3_init<<<(int)((n + 255) / 256), 256, 0, s>>>(kd, n, ni, v, st, stride, err);
+}
+
+void launch_kin3_state(int prec, const Kin3D* kd, int64_t n, const int32_t* ni,
+                       const double* v, double* st, int64_t stride, double dt, double tol,
+                       int ir_max, KinCounters* cnt, int32_t* err, cudaStream_t s) {
+    if (n == 0) return;
+    const int grid = (int)((n + 255) / 256);
+    if (prec == NMODL_FP64)
+        k_kin3_state<NMODL_FP64><<<grid, 256, 0, s>>>(kd, n, ni, v, st, stride, dt, tol, ir_max, cnt, err);
+    else
+        k_kin3_state<NMODL_MIXED><<<grid, 256, 0, s>>>(kd, n, ni, v, st, stride, dt, tol, ir_max, cnt, err);
+}
+
+void launch_cacum_init(const CacumD* cd, int64_t n, double* st, int64_t stride,
+                       cudaStream_t s) {
+    if (n == 0) return;
+    k_cacum_init<<<(int)((n + 255) / 256), 256, 0, s>>>(cd, n, st, stride);
+}
+
+void launch_cacum_state(const CacumD* cd, int64_t n, const int32_t* ni, const double* ica,
+                        double* st, int64_t stride, double dt, double tol, int max_iter,
+                        KinCounters* cnt, int32_t* err, cudaStream_t s) {
+    if (n == 0) return;
+    k_cacum_state<<<(int)((n + 255) / 256), 256, 0, s>>>(cd, n, ni, ica, st, stride, dt, tol,
+                                                         max_iter, cnt, err);
+}
+
+}  // namespace nmodl

@@ -37,10 +37,13 @@ void launch_state_gates(int prec, const MechD* md, int n_gates, int64_t n,
                         const int32_t* ni, const double* v, double* st,
                         int64_t stride, double dt, int pade, int32_t* err,
                         cudaStream_t s);
+// ion_a / ion_b (may be null): per-node ion currents accumulated with the
+// same segmented reduction -- HH: ina and ik; other kinds: the whole current
+// into ion_a (the array of the ion the mechanism is tagged with)
 void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
                     const int32_t* chunk, const int32_t* ni, const double* v,
                     const double* st, int64_t stride, double* rhs, double* d,
-                    int32_t* err, cudaStream_t s);
+                    double* ion_a, double* ion_b, int32_t* err, cudaStream_t s);
 cudaError_t launch_fused(int prec, const FusedArgs& a, int grid, int block,
                          size_t smem, cudaStream_t s);
 int fused_resident_grid(int prec, int n_tiles, int block, size_t smem);
@@ -55,6 +58,23 @@ struct KinCounters {
     int32_t pad;
     unsigned long long fallback;  // surrogate instances sent to Newton
 };
+// Warp-reduced update of the counters (every lane of the warp calls it).
+__device__ __forceinline__ void warp_count(KinCounters* cnt, unsigned long long it,
+                                           unsigned long long nc, int mx) {
+    if (!cnt) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        it += __shfl_down_sync(0xffffffffu, it, o);
+        nc += __shfl_down_sync(0xffffffffu, nc, o);
+        mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (it) atomicAdd(&cnt->iters, it);
+        if (nc) atomicAdd(&cnt->nonconv, nc);
+        if (mx) atomicMax(&cnt->max_iter_seen, mx);
+    }
+}
+
 void launch_kin9_init(const Kin9D* kd, int64_t n, const int32_t* ni,
                       const double* v, double* st, int64_t stride, int32_t* err,
                       cudaStream_t s);
@@ -64,6 +84,18 @@ void launch_kin9_state(int prec, const Kin9D* kd, int64_t n, const int32_t* ni,
                        const int32_t* list, int64_t n_list_max,
                        const int32_t* n_list_dev, KinCounters* cnt,
                        int32_t* err, cudaStream_t s);
+
+// small systems: 3-state kinetic scheme and the calcium buffer
+void launch_kin3_init(const Kin3D* kd, int64_t n, const int32_t* ni, const double* v,
+                      double* st, int64_t stride, int32_t* err, cudaStream_t s);
+void launch_kin3_state(int prec, const Kin3D* kd, int64_t n, const int32_t* ni,
+                       const double* v, double* st, int64_t stride, double dt, double tol,
+                       int ir_max, KinCounters* cnt, int32_t* err, cudaStream_t s);
+void launch_cacum_init(const CacumD* cd, int64_t n, double* st, int64_t stride,
+                       cudaStream_t s);
+void launch_cacum_state(const CacumD* cd, int64_t n, const int32_t* ni, const double* ica,
+                        double* st, int64_t stride, double dt, double tol, int max_iter,
+                        KinCounters* cnt, int32_t* err, cudaStream_t s);
 
 // common
 void launch_chunk_starts(const int32_t* ni, int64_t n, int64_t n_chunks,

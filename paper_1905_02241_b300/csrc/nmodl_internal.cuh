@@ -55,6 +55,20 @@ struct Kin9D {
     double af[kKinEdges], bf[kKinEdges], ab[kKinEdges], bb[kKinEdges];
 };
 
+// 3-state scheme: edge e in {0: (0,1), 1: (1,2), 2: (0,2)}
+struct Kin3D {
+    double gbar, e;
+    int32_t open, pad;
+    double af[3], bf[3], ab[3], bb[3];
+};
+__host__ __device__ constexpr int kin3_lo(int e) { return e == 1 ? 1 : 0; }
+__host__ __device__ constexpr int kin3_hi(int e) { return e == 0 ? 1 : 2; }
+
+// calcium buffer: k, 1/tau, cai0, kf, kb, btot
+struct CacumD {
+    double k, rtau, cai0, kf, kb, btot;
+};
+
 // ------------------------------------------------------------ FP64 math
 
 // exp(x) by Tang's table-driven method (ACM TOMS 15(2), 1989): with

@@ -69,6 +69,8 @@ extern "C" NMODL_API int nmodl_cur_noalloc(int device, void* cuda_stream, int ty
     if (n_instances < 0 || n_nodes < 0 || stride < n_instances || !params)
         return NMODL_ERR_ARG;
     if (n_instances > kMaxInstances) return NMODL_ERR_TOO_LARGE;
+    if (type != NMODL_HH && type != NMODL_CNEXP && type != NMODL_KIN9)
+        return NMODL_ERR_UNSUPPORTED;
     MechD md{};
     Kin9D kd{};
     int n_states = 0;
@@ -112,7 +114,8 @@ extern "C" NMODL_API int nmodl_cur_noalloc(int device, void* cuda_stream, int ty
         } else {
             launch_chunk_starts(node_index, n_instances, n_chunks, chunk, s);
             launch_cur_seg(type == NMODL_KIN9 ? NMODL_KIN9 : NMODL_CNEXP, desc, n_chunks,
-                           chunk, node_index, v, states, stride, rhs, d, nullptr, s);
+                           chunk, node_index, v, states, stride, rhs, d, nullptr, nullptr,
+                           nullptr, s);
             if (cudaGetLastError() != cudaSuccess) rc = NMODL_ERR_CUDA;
         }
     }

@@ -71,6 +71,9 @@ struct nmodl_ctx {
     std::vector<std::unique_ptr<Plan>> plans;
     int live_mechs = 0;
     int64_t epoch = 0;  // bumped when options, mechanisms or surrogates change
+    double* ion[4] = {nullptr, nullptr, nullptr, nullptr};  // per-node ina, ik, ica (1..3)
+    int64_t ion_nodes = 0;
+    bool has_ions() const { return ion[1] || ion[2] || ion[3]; }
 };
 
 struct nmodl_mech {
@@ -88,6 +91,11 @@ struct nmodl_mech {
     nmodl::Kin9D kd{};
     nmodl::Kin9D* d_kd = nullptr;
     nmodl::KinCounters* d_cnt = nullptr;
+    nmodl::Kin3D k3{};
+    nmodl::Kin3D* d_k3 = nullptr;
+    nmodl::CacumD cd{};
+    nmodl::CacumD* d_cd = nullptr;
+    int ion = NMODL_ION_NONE;       // USEION WRITE tag of the whole current
     int64_t calls = 0;
     // surrogate stand-in for the kinetic Newton solve (NMODL_KIN9 only)
     nmodl_surrogate* sur = nullptr;
@@ -120,6 +128,9 @@ extern "C" {
 void nmodl_enqueue_state(nmodl_mech* m, double dt, const double* v);
 void nmodl_enqueue_cur(nmodl_mech* m, const double* v, double* rhs, double* d);
 void nmodl_count_states(nmodl_mech* m, int64_t k);
+void nmodl_zero_ions(nmodl_ctx* c, int64_t n_nodes);
+// NMODL_OK when every mechanism's ion reads are satisfied by the context
+int nmodl_check_ion_reads(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs);
 }
 
 struct nmodl_cable {

@@ -10,6 +10,8 @@ same GPU (used by bench.py):
   surrogate the BF16 MLP stand-in (trained here on Newton-generated pairs) on
            4M clamped compartments vs the FP64 Newton solve, with fallback
            rate and final error against the Newton trajectory
+  ions     ion current write-back (ina, ik, ica) with a 3-state scheme and a
+           calcium buffer reading ica, on the ion-tagged cortical mix
 
 Each entry reports instance-steps/s (state + cur) and its ratio to the FP64
 form.  Errors against the FP64 CPU oracle of the mixed forms are measured
@@ -147,6 +149,85 @@ def cable(dev, n_cells=10000, nsteps=200):
     for m in mechs:
         m.close()
     ctx.close()
+    return out
+
+
+def _ion_mechs(ctx, wl):
+    return [Mechanism(ctx, m["type"], m["node_index"], wl["n_nodes"], m["params"],
+                      ion=m.get("ion", 0)) for m in wl["mechs"]]
+
+
+def ions(dev, n_nodes=2_000_000, nsteps=200):
+    """USEION write-back and the small systems on the ion-tagged cortical mix
+    (10 cnexp types writing ina/ik/ica, a 3-state potassium scheme on half
+    of the nodes, one calcium buffer per node reading ica):
+
+      network_fp64 / network_mixed   whole steps with ion arrays registered
+      no_buffer_ions_fp64            the same without the buffer
+      no_buffer_no_ions_fp64         ... and without ion arrays: the cost of
+                                     the ion write-back is the ratio
+      cacum_state_*                  buffer Newton kernel alone (GB/s of its
+                                     44 algorithmic bytes per instance)
+      kin3_state_*                   3-state solve kernel alone
+    All rates are instance-steps/s (the buffer counts as an instance)."""
+    wl = W.cortical_ions(n_nodes, seed=8)
+    nb = dict(wl, mechs=[m for m in wl["mechs"] if m["type"] != W.TYPE_CACUM])
+    out = {"nodes": n_nodes, "instances": _ninst(wl), "instances_no_buffer": _ninst(nb),
+           "steps_per_run": nsteps}
+    dv = f"cuda:{dev}"
+    v0 = torch.tensor(wl["v0"], device=dv)
+    for name, net, prec, use_ions in (("network_fp64", wl, NMODL_FP64, True),
+                                      ("network_mixed", wl, NMODL_MIXED, True),
+                                      ("no_buffer_ions_fp64", nb, NMODL_FP64, True),
+                                      ("no_buffer_no_ions_fp64", nb, NMODL_FP64, False)):
+        ctx = Context(dev, precision=prec)
+        arrs = [torch.zeros_like(v0) for _ in range(3)]
+        if use_ions:
+            ctx.set_ions(*arrs)
+        mechs = _ion_mechs(ctx, net)
+        v = v0.clone()
+        rhs = torch.zeros_like(v)
+        d = torch.zeros_like(v)
+        for m in mechs:
+            m.init(v)
+        ctx.step(mechs, DT, CM, v, rhs, d, 40)
+        ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
+        out[name] = _ninst(net) * nsteps / (ms * 1e-3)
+        if name == "network_fp64":
+            cai = [m for m in mechs if m.type == W.TYPE_CACUM][0].states()[0]
+            out["cai_mM_median"] = float(cai.median())
+            out["cai_mM_max"] = float(cai.max())
+            out["ica_nonzero_nodes"] = int((arrs[2] != 0).sum())
+            out["plan_fused"] = bool(ctx.plan(mechs)["fused"])
+        for m in mechs:
+            m.close()
+        ctx.close()
+    out["ion_writeback_cost"] = out["no_buffer_no_ions_fp64"] / out["no_buffer_ions_fp64"]
+    out["mixed_over_fp64"] = out["network_mixed"] / out["network_fp64"]
+    # kernels alone, 8M instances, one per node
+    n = 8_000_000
+    ni = torch.arange(n, dtype=torch.int32, device=dv)
+    vk = torch.tensor(W.Stream(21, 1).uniform(n, -90.0, 40.0), device=dv)
+    ica = -torch.tensor(W.Stream(21, 2).loguniform(n, 1e-4, 1.0), device=dv)
+    reps = 20
+    for prec, tag in ((NMODL_FP64, "fp64"), (NMODL_MIXED, "mixed")):
+        ctx = Context(dev, precision=prec)
+        ctx.set_ions(ica=ica)
+        buf = Mechanism(ctx, W.TYPE_CACUM, ni, n, W.cacum_params())
+        k3 = Mechanism(ctx, W.TYPE_KIN3, ni, n, W.kin3_params(W.Stream(8, 802)))
+        for m in (buf, k3):
+            m.init(vk)
+            m.state(DT, vk)
+            ms = _time(lambda: [m.state(DT, vk) for _ in range(reps)], ctx, 1)
+            key = ("cacum_state_" if m is buf else "kin3_state_") + tag
+            out[key] = n * reps / (ms * 1e-3)
+            if m is buf:
+                out[key + "_GBs"] = out[key] * 44 / 1e9
+            else:
+                out[key + "_GBs"] = out[key] * 60 / 1e9
+            out[key + "_updates"] = m.stats()["newton_max"]
+            m.close()
+        ctx.close()
     return out
 
 

@@ -13,25 +13,47 @@
 // x_hat (then ||x_hat - x*||_1 <= ||J^-1||_1 ||F||_1 = ||F||_1), otherwise the
 // instance goes on a fallback list for the Newton kernel.
 //
-// k_surrogate_step: persistent CTAs (one per SM), 16 warps, weights staged once in shared
-// memory (bf16, rows padded by 16 bytes so ldmatrix is conflict-free).  A
-// warp owns 16 instances; the accumulator fragments of one layer are the A
-// fragments of the next (m16n8k16 C and A layouts coincide pairwise), so
-// activations never leave registers.
+// k_surrogate_step: persistent CTAs (one per SM) of four warpgroups; each
+// warpgroup owns a tile of 128 instances, one thread per instance.  The MLP
+// runs on the fifth-generation tensor cores: a single thread per warpgroup
+// issues tcgen05.mma (M = 128, K = 16 per instruction) on bf16 operands in
+// shared memory, the FP32 accumulator lives in tensor memory (128 columns per
+// warpgroup), and every thread reads its own row back with tcgen05.ld for
+// the bias + SiLU epilogue, which writes the next layer's A operand.  Weights
+// (72 KB) are staged once per CTA.  Completion is signalled through one
+// mbarrier per warpgroup; every wait is bounded and a timeout is latched as
+// NMODL_ERR_TIMEOUT.
 #include "kernels.cuh"
 #include "mlp.cuh"
+#include "tcgen05.cuh"
 
 namespace nmodl {
 
 namespace {
-constexpr int kWarps = 16;  // 512 threads, 128 registers: one CTA per SM
-constexpr int P1 = kIn + 8;    // W1 row pitch (elements)
-constexpr int PH = kHid + 8;   // W2, W3, W4 row pitch
-constexpr int kSmemW = (kHid * P1 + 2 * kHid * PH + kOut * PH) * 2;
-constexpr int kSmemB = (3 * kHid + kOut) * 4;
-constexpr int kWarpFloats = 32 * 16 + 32 * 24 + 32 * 9 + 32 + 32 * 9;
-constexpr int kSmemY = kWarps * kWarpFloats * 4;
-constexpr int kSmemTotal = kSmemW + kSmemB + kSmemY;
+constexpr int kWG = 4;                 // warpgroups per CTA
+constexpr int kThreads = 128 * kWG;    // one CTA per SM (shared memory bound)
+constexpr int kTile = 128;             // instances per warpgroup tile (MMA M)
+// shared-memory images (K-major, no swizzle; see tcgen05.cuh)
+constexpr int kW1Bytes = kHid * kIn * 2;
+constexpr int kWHBytes = kHid * kHid * 2;
+constexpr int kW4Bytes = kOut * kHid * 2;
+constexpr int kA0Bytes = kTile * kIn * 2;
+constexpr int kHBytes = kTile * kHid * 2;
+constexpr int kOffW1s = 0;
+constexpr int kOffW2s = kOffW1s + kW1Bytes;
+constexpr int kOffW3s = kOffW2s + kWHBytes;
+constexpr int kOffW4s = kOffW3s + kWHBytes;
+constexpr int kOffA0 = kOffW4s + kW4Bytes;
+constexpr int kOffH = kOffA0 + kWG * kA0Bytes;
+constexpr int kOffBias = kOffH + kWG * kHBytes;
+constexpr int kOffBar = kOffBias + (3 * kHid + kOut) * 4;
+constexpr int kSmemTotal = kOffBar + kWG * 8 + 16;
+static_assert(kOffBar % 8 == 0, "mbarrier alignment");
+static_assert(kSmemTotal <= 227 * 1024, "shared memory per block");
+constexpr uint32_t kTmemCols = 128 * kWG;  // 512: the whole tensor memory of the SM
+constexpr uint32_t kIdescHid = umma_idesc_bf16(128, kHid);
+constexpr uint32_t kIdescOut = umma_idesc_bf16(128, kOut);
+constexpr uint32_t kWaitPolls = 1u << 22;
 }  // namespace
 
 // FP32 rates dt*k of the 24 transitions and (dt A) x for a state x.
@@ -108,196 +130,180 @@ __device__ __forceinline__ void project_simplex9(float (&w)[9]) {
     for (int i = 0; i < 9; ++i) w[i] = fmaxf(w[i] - theta, 0.f);
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 1) k_surrogate_step(SurArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smem);
-    __nv_bfloat16* W2s = W1s + kHid * P1;
-    __nv_bfloat16* W3s = W2s + kHid * PH;
-    __nv_bfloat16* W4s = W3s + kHid * PH;
-    float* b1s = reinterpret_cast<float*>(smem + kSmemW);
+__global__ void __launch_bounds__(kThreads, 1) k_surrogate_step(SurArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint32_t sbase = smem_u32(smem);
+    float* b1s = reinterpret_cast<float*>(smem + kOffBias);
     float* b2s = b1s + kHid;
     float* b3s = b2s + kHid;
     float* b4s = b3s + kHid;
-    float* warp_all = b4s + kOut;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBar);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + kWG * 8);
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // ---- stage weights (16-byte row chunks) and biases
-    auto stage = [&](const __nv_bfloat16* src, __nv_bfloat16* dst, int rows, int cols, int pitch) {
-        const int ch = cols / 8;
-        for (int c = tid; c < rows * ch; c += blockDim.x) {
-            const int r = c / ch, cc = (c % ch) * 8;
-            *reinterpret_cast<uint4*>(dst + r * pitch + cc) =
-                *reinterpret_cast<const uint4*>(src + r * cols + cc);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = tid >> 7;        // warpgroup
+    const int t = tid & 127;       // row of the warpgroup's tile
+    // ---- stage the weights as K-major core-matrix images.  Hidden layers
+    // are staged as (W/2, b/2): the accumulator is then h = z/2 and
+    // SiLU(z) = z sigma(z) = h + h tanh(h) (halving a bf16 is exact).
+    auto stage = [&](const __nv_bfloat16* src, int off, int rows, int K, bool half) {
+        const int ch = K / 8;
+        for (int c = tid; c < rows * ch; c += kThreads) {
+            const int r = c / ch, k = (c % ch) * 8;
+            uint4 w = *reinterpret_cast<const uint4*>(src + r * K + k);
+            if (half) {
+                __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&w);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) h2[e] = __hmul2(h2[e], __floats2bfloat162_rn(0.5f, 0.5f));
+            }
+            *reinterpret_cast<uint4*>(smem + off + umma_offset(r, k, K)) = w;
         }
     };
-    // Hidden layers are staged as (W/2, b/2): the accumulator is then
-    // h = z/2 and SiLU(z) = z sigma(z) = h + h tanh(h), one tanh and one FMA
-    // (halving a bf16 is exact, so the products match the training forward).
-    auto stage_half = [&](const __nv_bfloat16* src, __nv_bfloat16* dst, int rows, int cols,
-                          int pitch) {
-        const int ch = cols / 2;
-        for (int c = tid; c < rows * ch; c += blockDim.x) {
-            const int r = c / ch, cc = (c % ch) * 2;
-            __nv_bfloat162 w = *reinterpret_cast<const __nv_bfloat162*>(src + r * cols + cc);
-            *reinterpret_cast<__nv_bfloat162*>(dst + r * pitch + cc) =
-                __hmul2(w, __floats2bfloat162_rn(0.5f, 0.5f));
-        }
-    };
-    stage_half(a.wbf + kBfW1, W1s, kHid, kIn, P1);
-    stage_half(a.wbf + kBfW2, W2s, kHid, kHid, PH);
-    stage_half(a.wbf + kBfW3, W3s, kHid, kHid, PH);
-    stage(a.wbf + kBfW4, W4s, kOut, kHid, PH);
-    for (int i = tid; i < kHid; i += blockDim.x) {
+    stage(a.wbf + kBfW1, kOffW1s, kHid, kIn, true);
+    stage(a.wbf + kBfW2, kOffW2s, kHid, kHid, true);
+    stage(a.wbf + kBfW3, kOffW3s, kHid, kHid, true);
+    stage(a.wbf + kBfW4, kOffW4s, kOut, kHid, false);
+    for (int i = tid; i < kHid; i += kThreads) {
         b1s[i] = 0.5f * a.params[kOffB1 + i];
         b2s[i] = 0.5f * a.params[kOffB2 + i];
         b3s[i] = 0.5f * a.params[kOffB3 + i];
     }
     if (tid < kOut) b4s[tid] = a.params[kOffB4 + tid];
+    if (tid == 0) {
+        for (int k = 0; k < kWG; ++k) mbar_init(&bars[k], 1);
+        mbar_init_fence();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, kTmemCols);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t d_tmem = tmem + 128u * g;                        // this warpgroup's columns
+    const uint32_t t_row = d_tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
 
     const Kin9D& K = *a.kd;
     const float dtf = (float)a.dt;
-    const int g = lane >> 2, t = lane & 3, q = lane >> 3, r8 = lane & 7;
-    // per-warp staging of 32 instances: features [32][16], rates [32][24],
-    // x [32][9], scale [32], outputs [32][9]
-    float* wsm = warp_all + warp * kWarpFloats;
-    float* feat = wsm;
-    float* rates = feat + 32 * 16;
-    float* xs = rates + 32 * 2 * kKinEdges;
-    float* ss = xs + 32 * 9;
-    float* ys = ss + 32;
-    const int64_t stride_w = (int64_t)gridDim.x * kWarps * 32;
+    const uint32_t a0 = sbase + kOffA0 + g * kA0Bytes;
+    const uint32_t hb = sbase + kOffH + g * kHBytes;
+    unsigned char* a0p = smem + kOffA0 + g * kA0Bytes;
+    unsigned char* hp = smem + kOffH + g * kHBytes;
+    uint64_t* bar = &bars[g];
+    const uint32_t bar_id = 1 + g;
+    uint32_t phase = 0;
+    bool timed_out = false;
 
-    for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < a.n;
-         base += stride_w) {
-        // ---- one lane per instance: rates, dt A x, scale, network inputs
+    // operands written and earlier TMEM reads done -> the MMA may be issued
+    auto publish = [&]() {
+        fence_proxy_async_smem();
+        tc_fence_before();
+        bar_sync(bar_id, 128);
+    };
+    // every thread waits for the warpgroup's commit; all agree on timeouts
+    auto wait_mma = [&]() -> bool {
+        const bool ok = mbar_wait(bar, phase, kWaitPolls);
+        phase ^= 1u;
+        const bool bad = bar_any(bar_id, 128, !ok);
+        tc_fence_after();
+        return !bad;
+    };
+    auto issue_hidden = [&](int w_off) {
+        if (t == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int j = 0; j < kHid / 16; ++j)
+                umma_bf16(d_tmem, umma_desc(hb + 256 * j, 128, 16 * kHid),
+                          umma_desc(sbase + w_off + 256 * j, 128, 16 * kHid), kIdescHid, j > 0);
+            umma_commit(bar);
+        }
+    };
+    // accumulator row -> bias + SiLU -> bf16 row of the next A operand
+    auto epilogue = [&](const float* bias) {
+        unsigned char* hrow = hp + (t >> 3) * (16 * kHid) + (t & 7) * 16;
+#pragma unroll 1
+        for (int cb = 0; cb < kHid; cb += 32) {
+            uint32_t r[32];
+            tmem_ld32(t_row + cb, r);
+            tmem_ld_wait();
+            uint32_t pk[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const float h0 = __uint_as_float(r[2 * e]) + bias[cb + 2 * e];
+                const float h1 = __uint_as_float(r[2 * e + 1]) + bias[cb + 2 * e + 1];
+                pk[e] = pack_bf16(fmaf(h0, tanh_hw(h0), h0), fmaf(h1, tanh_hw(h1), h1));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4*>(hrow + ((cb >> 3) + q) * 128) =
+                    make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        }
+    };
+
+    const int64_t tile_stride = (int64_t)gridDim.x * kWG;
+    for (int64_t tile = (int64_t)blockIdx.x * kWG + g; tile * kTile < a.n && !timed_out;
+         tile += tile_stride) {
+        const int64_t i = tile * kTile + t;
+        const bool valid = i < a.n;
+        // ---- inputs of this thread's instance
+        float xf[9], dkf[kKinEdges], dkb[kKinEdges], s = 0.f;
         {
-            const int64_t i = base + lane;
-            float* f = feat + lane * 16;
-            if (i < a.n) {
-                float xf[9], dkf[kKinEdges], dkb[kKinEdges], z[9];
+            float f[16], z[9];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) f[k] = 0.f;
+            if (valid) {
 #pragma unroll
                 for (int k = 0; k < 9; ++k) xf[k] = d2f_int(a.st[k * a.stride + i]);
                 const float vf = d2f_int(a.v[a.ni[i]]);
                 kin_rates_f(K, vf, dtf, dkf, dkb);
                 dtAx_f(dkf, dkb, xf, z);
-                ss[lane] = sur_inputs(a.scaled, vf, dtf, xf, z, f);
-#pragma unroll
-                for (int e = 0; e < kKinEdges; ++e) {
-                    rates[lane * 24 + e] = dkf[e];
-                    rates[lane * 24 + 12 + e] = dkb[e];
-                }
-#pragma unroll
-                for (int k = 0; k < 9; ++k) xs[lane * 9 + k] = xf[k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < kInRaw; ++k) f[k] = 0.f;
+                s = sur_inputs(a.scaled, vf, dtf, xf, z, f);
             }
+            unsigned char* arow = a0p + (t >> 3) * (16 * kIn) + (t & 7) * 16;
 #pragma unroll
-            for (int k = kInRaw; k < 16; ++k) f[k] = 0.f;
+            for (int q = 0; q < 2; ++q)
+                *reinterpret_cast<uint4*>(arow + q * 128) =
+                    make_uint4(pack_bf16(f[8 * q], f[8 * q + 1]), pack_bf16(f[8 * q + 2], f[8 * q + 3]),
+                               pack_bf16(f[8 * q + 4], f[8 * q + 5]), pack_bf16(f[8 * q + 6], f[8 * q + 7]));
         }
-        __syncwarp();
-        // ---- the MLP on rows 0..15, then 16..31
-#pragma unroll 1
-        for (int half = 0; half < 2; ++half) {
-            const float* fh = feat + half * 16 * 16;
-            uint32_t afr[4];
-            afr[0] = pack_bf16(fh[g * 16 + 2 * t], fh[g * 16 + 2 * t + 1]);
-            afr[1] = pack_bf16(fh[(g + 8) * 16 + 2 * t], fh[(g + 8) * 16 + 2 * t + 1]);
-            afr[2] = pack_bf16(fh[g * 16 + 2 * t + 8], fh[g * 16 + 2 * t + 9]);
-            afr[3] = pack_bf16(fh[(g + 8) * 16 + 2 * t + 8], fh[(g + 8) * 16 + 2 * t + 9]);
-            float acc[16][4];
-            // accumulators start at the (halved) bias of their column
-            auto init_bias = [&](const float* bias) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float2 bb = *reinterpret_cast<const float2*>(bias + 8 * j + 2 * t);
-                    acc[j][0] = bb.x;
-                    acc[j][1] = bb.y;
-                    acc[j][2] = bb.x;
-                    acc[j][3] = bb.y;
-                }
-            };
-            init_bias(b1s);
-#pragma unroll
-            for (int np = 0; np < 8; ++np) {
-                uint32_t b[4];
-                ldsm_x4(b, W1s + (16 * np + r8 + (q >> 1) * 8) * P1 + (q & 1) * 8);
-                mma_bf16_16816(acc[2 * np], afr, b[0], b[1]);
-                mma_bf16_16816(acc[2 * np + 1], afr, b[2], b[3]);
-            }
-            // C fragments of output tiles 2kk and 2kk+1 are, in this order,
-            // the A fragment (a0a1, a2a3, a4a5, a6a7) of k-slice kk of the
-            // next layer
-            uint32_t ah[8][4];
-            auto silu_h = [](float h) { return fmaf(h, tanh_hw(h), h); };
-            auto to_frags = [&]() {
-#pragma unroll
-                for (int kk = 0; kk < 8; ++kk)
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int j = 2 * kk + h;
-                        ah[kk][2 * h] = pack_bf16(silu_h(acc[j][0]), silu_h(acc[j][1]));
-                        ah[kk][2 * h + 1] = pack_bf16(silu_h(acc[j][2]), silu_h(acc[j][3]));
-                    }
-            };
-            auto hidden = [&](const __nv_bfloat16* Ws, const float* bias) {
-                init_bias(bias);
-#pragma unroll
-                for (int kk = 0; kk < 8; ++kk)
-#pragma unroll
-                    for (int np = 0; np < 8; ++np) {
-                        uint32_t b[4];
-                        ldsm_x4(b, Ws + (16 * np + r8 + (q >> 1) * 8) * PH + 16 * kk + (q & 1) * 8);
-                        mma_bf16_16816(acc[2 * np], ah[kk], b[0], b[1]);
-                        mma_bf16_16816(acc[2 * np + 1], ah[kk], b[2], b[3]);
-                    }
-            };
-            to_frags();
-            hidden(W2s, b2s);
-            to_frags();
-            hidden(W3s, b3s);
-            to_frags();
-            float o[2][4];
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) o[j][e] = 0.f;
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                uint32_t b[4];
-                ldsm_x4(b, W4s + (r8 + (q >> 1) * 8) * PH + 16 * kk + (q & 1) * 8);
-                mma_bf16_16816(o[0], ah[kk], b[0], b[1]);
-                mma_bf16_16816(o[1], ah[kk], b[2], b[3]);
-            }
-            float* yh = ys + half * 16 * 9;
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int col = 8 * j + 2 * t + e;
-                        if (col < kOutRaw) yh[(g + 8 * h) * 9 + col] = o[j][2 * h + e] + b4s[col];
-                    }
+        publish();
+        if (t == 0) {
+            tc_fence_after();
+            umma_bf16(d_tmem, umma_desc(a0, 128, 16 * kIn), umma_desc(sbase + kOffW1s, 128, 16 * kIn),
+                      kIdescHid, 0);
+            umma_commit(bar);
         }
-        __syncwarp();
-        // ---- projection, residual, decision (one lane per instance)
+        if (!wait_mma()) { timed_out = true; break; }
+        epilogue(b1s);
+        publish();
+        issue_hidden(kOffW2s);
+        if (!wait_mma()) { timed_out = true; break; }
+        epilogue(b2s);
+        publish();
+        issue_hidden(kOffW3s);
+        if (!wait_mma()) { timed_out = true; break; }
+        epilogue(b3s);
+        publish();
+        if (t == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int j = 0; j < kHid / 16; ++j)
+                umma_bf16(d_tmem, umma_desc(hb + 256 * j, 128, 16 * kHid),
+                          umma_desc(sbase + kOffW4s + 256 * j, 128, 16 * kHid), kIdescOut, j > 0);
+            umma_commit(bar);
+        }
+        if (!wait_mma()) { timed_out = true; break; }
+        uint32_t yo[16];
+        tmem_ld16(t_row, yo);
+        tmem_ld_wait();
+        // ---- projection, residual, decision (one thread per instance)
         bool fail = false;
-        const int64_t i = base + lane;
-        if (i < a.n) {
-            float xf[9], w[9], dkf[kKinEdges], dkb[kKinEdges], z[9];
+        if (valid) {
+            float w[9], z[9];
 #pragma unroll
-            for (int e = 0; e < kKinEdges; ++e) {
-                dkf[e] = rates[lane * 24 + e];
-                dkb[e] = rates[lane * 24 + 12 + e];
-            }
-            const float s = ss[lane];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                xf[k] = xs[lane * 9 + k];
-                w[k] = xf[k] + s * ys[lane * 9 + k];
-            }
+            for (int k = 0; k < 9; ++k) w[k] = xf[k] + s * (__uint_as_float(yo[k]) + b4s[k]);
             project_simplex9(w);
             dtAx_f(dkf, dkb, w, z);
             float rn = 0.f;
@@ -311,6 +317,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_surrogate_step(SurArgs a) {
         }
         const unsigned mask = __ballot_sync(0xffffffffu, fail);
         if (mask) {
+            const int lane = tid & 31;
             int pos = 0;
             if (lane == 0) {
                 pos = atomicAdd(a.fb_count, __popc(mask));
@@ -319,7 +326,14 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_surrogate_step(SurArgs a) {
             pos = __shfl_sync(0xffffffffu, pos, 0);
             if (fail) a.fb_list[pos + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
         }
-        __syncwarp();
+    }
+    if (timed_out && t == 0) latch_error(a.err, NMODL_ERR_TIMEOUT);
+    // ---- release the tensor memory
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
     }
 }
 
@@ -335,10 +349,10 @@ cudaError_t launch_surrogate_step(const SurArgs& a, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t groups = (a.n + 31) / 32;
-    int64_t grid = std::min<int64_t>((int64_t)sms, (groups + kWarps - 1) / kWarps);
+    const int64_t tiles = (a.n + kTile - 1) / kTile;
+    int64_t grid = std::min<int64_t>((int64_t)sms, (tiles + kWG - 1) / kWG);
     if (grid < 1) grid = 1;
-    k_surrogate_step<<<(int)grid, kWarps * 32, kSmemTotal, s>>>(a);
+    k_surrogate_step<<<(int)grid, kThreads, kSmemTotal, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -121,6 +121,39 @@ def _kin_setup(ctx, n, seed=4):
     return wl, m
 
 
+@pytest.mark.parametrize("n", [1, 129, 151853])
+def test_inference_kernel_vs_oracle(S, ctx, orc, n):
+    """The tensor-core inference kernel with every prediction kept (gate
+    above any residual) on one, a partial and many tiles per warpgroup with
+    a ragged tail, against the FP64 oracle network + projection; the BF16
+    network's increment error is bounded relative to the step scale s."""
+    Ws, bs = W.mlp_init(9, out_scale=1.0)
+    rng = np.random.default_rng(2)
+    bs = [rng.normal(scale=0.1, size=b.shape) for b in bs]
+    wl, m = _kin_setup(ctx, n, seed=8)
+    spec = wl["mechs"][0]
+    sur = S.Surrogate(ctx, max_batch=256, weights=S.Surrogate.pack(Ws, bs))
+    S.attach(m, sur, 1e30)
+    m.state(0.025, to_dev(wl["v0"]))
+    got = m.states().cpu().numpy()
+    assert m.stats()["fallback"] == 0
+    idx = np.unique(np.concatenate([np.arange(0, n, 7), np.arange(max(0, n - 300), n)]))
+    x = wl["x0"][:, idx]
+    pred = orc.surrogate_step(Ws, bs, wl["v0"][idx], 0.025, x, spec["params"])
+    s = np.array([np.abs(0.025 * orc.kin9_matrix(spec["params"], wl["v0"][c]) @ wl["x0"][:, c]).sum()
+                  for c in idx])
+    err = np.sum(np.abs(got[:, idx] - pred), axis=0)
+    rel = err / np.maximum(s, 1e-30)
+    print(f"n={n}: L1 error / s: max {rel.max():.2e}, median {np.median(rel):.2e}")
+    assert np.all(err <= 3e-2 * s + 1e-6)
+    assert np.median(rel) <= 5e-3
+    assert np.max(np.abs(got.sum(axis=0) - 1.0)) <= 1e-5 and got.min() >= 0
+    S.attach(m, None)
+    sur.close()
+    m.close()
+    assert ctx.sync() == 0
+
+
 def test_forced_fallback_equals_newton(S, ctx, orc):
     """A tolerance below FP32 rounding sends every instance to Newton."""
     wl, m = _kin_setup(ctx, 3001)

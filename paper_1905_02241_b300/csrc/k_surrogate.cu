@@ -33,20 +33,30 @@ namespace {
 constexpr int kWG = 4;                 // warpgroups per CTA
 constexpr int kThreads = 128 * kWG;    // one CTA per SM (shared memory bound)
 constexpr int kTile = 128;             // instances per warpgroup tile (MMA M)
-// shared-memory images (K-major, no swizzle; see tcgen05.cuh)
+// shared-memory images (K-major, no swizzle; see tcgen05.cuh).  The layer
+// inputs (K = 16) sit in columns 0..15 of the warpgroup's H image.  Biases
+// enter through the MMAs: layer 1 through input columns 11 and 12 (= 1)
+// against W1 columns holding the bias as a bf16 pair hi + lo; layers 2-4
+// through one extra K = 16 MMA of ONE (columns 0, 1 = 1) against a bias
+// image with hi, lo in columns 0, 1 (hi + lo equals the FP32 bias to 2^-17).
 constexpr int kW1Bytes = kHid * kIn * 2;
 constexpr int kWHBytes = kHid * kHid * 2;
 constexpr int kW4Bytes = kOut * kHid * 2;
-constexpr int kA0Bytes = kTile * kIn * 2;
 constexpr int kHBytes = kTile * kHid * 2;
+constexpr int kOneBytes = kTile * 16 * 2;
+constexpr int kBHBytes = kHid * 16 * 2;
+constexpr int kB4Bytes = kOut * 16 * 2;
 constexpr int kOffW1s = 0;
 constexpr int kOffW2s = kOffW1s + kW1Bytes;
 constexpr int kOffW3s = kOffW2s + kWHBytes;
 constexpr int kOffW4s = kOffW3s + kWHBytes;
-constexpr int kOffA0 = kOffW4s + kW4Bytes;
-constexpr int kOffH = kOffA0 + kWG * kA0Bytes;
-constexpr int kOffBias = kOffH + kWG * kHBytes;
-constexpr int kOffBar = kOffBias + (3 * kHid + kOut) * 4;
+constexpr int kOffH = kOffW4s + kW4Bytes;
+constexpr int kOffOne = kOffH + kWG * kHBytes;
+constexpr int kOffB2i = kOffOne + kOneBytes;
+constexpr int kOffB3i = kOffB2i + kBHBytes;
+constexpr int kOffB4i = kOffB3i + kBHBytes;
+constexpr int kOffRate = kOffB4i + kB4Bytes;  // 48 FP32 rate parameters
+constexpr int kOffBar = kOffRate + 4 * kKinEdges * 4;
 constexpr int kSmemTotal = kOffBar + kWG * 8 + 16;
 static_assert(kOffBar % 8 == 0, "mbarrier alignment");
 static_assert(kSmemTotal <= 227 * 1024, "shared memory per block");
@@ -63,6 +73,16 @@ __device__ __forceinline__ void kin_rates_f(const Kin9D& K, float vf, float dtf,
     for (int e = 0; e < kKinEdges; ++e) {
         dkf[e] = dtf * ((float)K.af[e] * __expf((float)K.bf[e] * vf));
         dkb[e] = dtf * ((float)K.ab[e] * __expf(-(float)K.bb[e] * vf));
+    }
+}
+// the same rates from FP32 copies of the parameters (af, bf, ab, bb, 12
+// each), e.g. staged in shared memory: no FP64 conversions per instance
+__device__ __forceinline__ void kin_rates_f32(const float* kp, float vf, float dtf,
+                                              float (&dkf)[kKinEdges], float (&dkb)[kKinEdges]) {
+#pragma unroll
+    for (int e = 0; e < kKinEdges; ++e) {
+        dkf[e] = dtf * (kp[e] * __expf(kp[kKinEdges + e] * vf));
+        dkb[e] = dtf * (kp[2 * kKinEdges + e] * __expf(-kp[3 * kKinEdges + e] * vf));
     }
 }
 __device__ __forceinline__ void dtAx_f(const float (&dkf)[kKinEdges],
@@ -105,27 +125,26 @@ __device__ __forceinline__ float sur_inputs(int scaled, float vf, float dtf,
     return s;
 }
 
-// Euclidean projection of w onto {x >= 0, sum x = 1}: theta is (S_j - 1)/c_j
-// for the largest set {i : w_i >= w_j} whose smallest member stays positive.
+// Euclidean projection of w onto {x >= 0, sum x = 1}: theta = (S_j - 1)/c_j
+// for the largest set {i : w_i >= w_j} (c_j members, sum S_j) whose smallest
+// member stays above theta, i.e. w_j c_j - (S_j - 1) > 0; one division.
 __device__ __forceinline__ void project_simplex9(float (&w)[9]) {
-    float theta = -1e30f;
-    int best = 0;
+    float bestS = 0.f, bestC = 0.f;
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
-        float S = 0.f;
-        int c = 0;
+        float S = 0.f, c = 0.f;
 #pragma unroll
         for (int i = 0; i < 9; ++i)
             if (w[i] >= w[j]) {
                 S += w[i];
-                ++c;
+                c += 1.f;
             }
-        const float th = (S - 1.0f) / (float)c;
-        if (w[j] - th > 0.f && c > best) {
-            best = c;
-            theta = th;
+        if (fmaf(w[j], c, 1.0f - S) > 0.f && c > bestC) {
+            bestC = c;
+            bestS = S;
         }
     }
+    const float theta = (bestS - 1.0f) / bestC;
 #pragma unroll
     for (int i = 0; i < 9; ++i) w[i] = fmaxf(w[i] - theta, 0.f);
 }
@@ -133,10 +152,6 @@ __device__ __forceinline__ void project_simplex9(float (&w)[9]) {
 __global__ void __launch_bounds__(kThreads, 1) k_surrogate_step(SurArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const uint32_t sbase = smem_u32(smem);
-    float* b1s = reinterpret_cast<float*>(smem + kOffBias);
-    float* b2s = b1s + kHid;
-    float* b3s = b2s + kHid;
-    float* b4s = b3s + kHid;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBar);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + kWG * 8);
 
@@ -163,12 +178,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_surrogate_step(SurArgs a) {
     stage(a.wbf + kBfW2, kOffW2s, kHid, kHid, true);
     stage(a.wbf + kBfW3, kOffW3s, kHid, kHid, true);
     stage(a.wbf + kBfW4, kOffW4s, kOut, kHid, false);
-    for (int i = tid; i < kHid; i += kThreads) {
-        b1s[i] = 0.5f * a.params[kOffB1 + i];
-        b2s[i] = 0.5f * a.params[kOffB2 + i];
-        b3s[i] = 0.5f * a.params[kOffB3 + i];
+    // bias pairs: layer 1 into W1 columns 11, 12; layers 2-4 into their
+    // bias images (columns 0, 1); ONE has ones in columns 0, 1
+    auto put = [&](int off, int r, int k, int K, float x) {
+        *reinterpret_cast<__nv_bfloat16*>(smem + off + umma_offset(r, k, K)) = __float2bfloat16_rn(x);
+    };
+    auto put_pair = [&](int off, int r, int k, int K, float b) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+        put(off, r, k, K, b);
+        put(off, r, k + 1, K, b - __bfloat162float(hi));
+    };
+    for (int i = tid; i < kTile * 16; i += kThreads) put(kOffOne, i / 16, i % 16, 16, (i % 16) < 2 ? 1.f : 0.f);
+    for (int i = tid; i < kHid * 16; i += kThreads) {
+        put(kOffB2i, i / 16, i % 16, 16, 0.f);
+        put(kOffB3i, i / 16, i % 16, 16, 0.f);
     }
-    if (tid < kOut) b4s[tid] = a.params[kOffB4 + tid];
+    for (int i = tid; i < kOut * 16; i += kThreads) put(kOffB4i, i / 16, i % 16, 16, 0.f);
+    __syncthreads();
+    for (int i = tid; i < kHid; i += kThreads) {
+        put_pair(kOffW1s, i, kInRaw, kIn, 0.5f * a.params[kOffB1 + i]);
+        put_pair(kOffB2i, i, 0, 16, 0.5f * a.params[kOffB2 + i]);
+        put_pair(kOffB3i, i, 0, 16, 0.5f * a.params[kOffB3 + i]);
+    }
+    if (tid < kOut) put_pair(kOffB4i, tid, 0, 16, a.params[kOffB4 + tid]);
+    float* kps = reinterpret_cast<float*>(smem + kOffRate);
+    if (tid < kKinEdges) {
+        kps[tid] = (float)a.kd->af[tid];
+        kps[kKinEdges + tid] = (float)a.kd->bf[tid];
+        kps[2 * kKinEdges + tid] = (float)a.kd->ab[tid];
+        kps[3 * kKinEdges + tid] = (float)a.kd->bb[tid];
+    }
     if (tid == 0) {
         for (int k = 0; k < kWG; ++k) mbar_init(&bars[k], 1);
         mbar_init_fence();
@@ -185,12 +224,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_surrogate_step(SurArgs a) {
     const uint32_t d_tmem = tmem + 128u * g;                        // this warpgroup's columns
     const uint32_t t_row = d_tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
 
-    const Kin9D& K = *a.kd;
     const float dtf = (float)a.dt;
-    const uint32_t a0 = sbase + kOffA0 + g * kA0Bytes;
     const uint32_t hb = sbase + kOffH + g * kHBytes;
-    unsigned char* a0p = smem + kOffA0 + g * kA0Bytes;
     unsigned char* hp = smem + kOffH + g * kHBytes;
+    const uint64_t one_desc = umma_desc(sbase + kOffOne, 128, 256);
     uint64_t* bar = &bars[g];
     const uint32_t bar_id = 1 + g;
     uint32_t phase = 0;
@@ -210,35 +247,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_surrogate_step(SurArgs a) {
         tc_fence_after();
         return !bad;
     };
-    auto issue_hidden = [&](int w_off) {
+    // bias MMA (accumulator := bias), then the K = 128 product in 8 steps
+    auto issue_layer = [&](int w_off, int b_off, uint32_t idesc) {
         if (t == 0) {
             tc_fence_after();
+            umma_bf16(d_tmem, one_desc, umma_desc(sbase + b_off, 128, 256), idesc, 0);
 #pragma unroll
             for (int j = 0; j < kHid / 16; ++j)
                 umma_bf16(d_tmem, umma_desc(hb + 256 * j, 128, 16 * kHid),
-                          umma_desc(sbase + w_off + 256 * j, 128, 16 * kHid), kIdescHid, j > 0);
+                          umma_desc(sbase + w_off + 256 * j, 128, 16 * kHid), idesc, 1);
             umma_commit(bar);
         }
     };
-    // accumulator row -> bias + SiLU -> bf16 row of the next A operand
-    auto epilogue = [&](const float* bias) {
+    // accumulator row -> bias + SiLU -> bf16 row of the next A operand; the
+    // TMEM load of the next 16 columns is in flight while the current 16 are
+    // activated (wait::ld waits for every load issued before it)
+    auto epilogue = [&]() {
         unsigned char* hrow = hp + (t >> 3) * (16 * kHid) + (t & 7) * 16;
-#pragma unroll 1
-        for (int cb = 0; cb < kHid; cb += 32) {
-            uint32_t r[32];
-            tmem_ld32(t_row + cb, r);
-            tmem_ld_wait();
-            uint32_t pk[16];
+        uint32_t ra[16], rb[16];
+        auto act = [&](const uint32_t (&r)[16], int cb) {
+            uint32_t pk[8];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const float h0 = __uint_as_float(r[2 * e]) + bias[cb + 2 * e];
-                const float h1 = __uint_as_float(r[2 * e + 1]) + bias[cb + 2 * e + 1];
+            for (int e = 0; e < 8; ++e) {
+                const float h0 = __uint_as_float(r[2 * e]), h1 = __uint_as_float(r[2 * e + 1]);
                 pk[e] = pack_bf16(fmaf(h0, tanh_hw(h0), h0), fmaf(h1, tanh_hw(h1), h1));
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < 2; ++q)
                 *reinterpret_cast<uint4*>(hrow + ((cb >> 3) + q) * 128) =
                     make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        };
+        tmem_ld16(t_row, ra);
+        tmem_ld_wait();
+#pragma unroll
+        for (int cb = 0; cb < kHid; cb += 32) {
+            tmem_ld16(t_row + cb + 16, rb);
+            act(ra, cb);
+            tmem_ld_wait();
+            if (cb + 32 < kHid) tmem_ld16(t_row + cb + 32, ra);
+            act(rb, cb + 16);
+            tmem_ld_wait();
         }
     };
 
@@ -257,11 +305,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_surrogate_step(SurArgs a) {
 #pragma unroll
                 for (int k = 0; k < 9; ++k) xf[k] = d2f_int(a.st[k * a.stride + i]);
                 const float vf = d2f_int(a.v[a.ni[i]]);
-                kin_rates_f(K, vf, dtf, dkf, dkb);
+                kin_rates_f32(kps, vf, dtf, dkf, dkb);
                 dtAx_f(dkf, dkb, xf, z);
                 s = sur_inputs(a.scaled, vf, dtf, xf, z, f);
             }
-            unsigned char* arow = a0p + (t >> 3) * (16 * kIn) + (t & 7) * 16;
+            f[kInRaw] = 1.f;      // bias pair of layer 1
+            f[kInRaw + 1] = 1.f;
+            unsigned char* arow = hp + (t >> 3) * (16 * kHid) + (t & 7) * 16;
 #pragma unroll
             for (int q = 0; q < 2; ++q)
                 *reinterpret_cast<uint4*>(arow + q * 128) =
@@ -271,29 +321,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_surrogate_step(SurArgs a) {
         publish();
         if (t == 0) {
             tc_fence_after();
-            umma_bf16(d_tmem, umma_desc(a0, 128, 16 * kIn), umma_desc(sbase + kOffW1s, 128, 16 * kIn),
+            umma_bf16(d_tmem, umma_desc(hb, 128, 16 * kHid), umma_desc(sbase + kOffW1s, 128, 16 * kIn),
                       kIdescHid, 0);
             umma_commit(bar);
         }
         if (!wait_mma()) { timed_out = true; break; }
-        epilogue(b1s);
+        epilogue();
         publish();
-        issue_hidden(kOffW2s);
+        issue_layer(kOffW2s, kOffB2i, kIdescHid);
         if (!wait_mma()) { timed_out = true; break; }
-        epilogue(b2s);
+        epilogue();
         publish();
-        issue_hidden(kOffW3s);
+        issue_layer(kOffW3s, kOffB3i, kIdescHid);
         if (!wait_mma()) { timed_out = true; break; }
-        epilogue(b3s);
+        epilogue();
         publish();
-        if (t == 0) {
-            tc_fence_after();
-#pragma unroll
-            for (int j = 0; j < kHid / 16; ++j)
-                umma_bf16(d_tmem, umma_desc(hb + 256 * j, 128, 16 * kHid),
-                          umma_desc(sbase + kOffW4s + 256 * j, 128, 16 * kHid), kIdescOut, j > 0);
-            umma_commit(bar);
-        }
+        issue_layer(kOffW4s, kOffB4i, kIdescOut);
         if (!wait_mma()) { timed_out = true; break; }
         uint32_t yo[16];
         tmem_ld16(t_row, yo);
@@ -303,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_surrogate_step(SurArgs a) {
         if (valid) {
             float w[9], z[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) w[k] = xf[k] + s * (__uint_as_float(yo[k]) + b4s[k]);
+            for (int k = 0; k < 9; ++k) w[k] = xf[k] + s * __uint_as_float(yo[k]);
             project_simplex9(w);
             dtAx_f(dkf, dkb, w, z);
             float rn = 0.f;

@@ -34,17 +34,18 @@ DT, CM, NSTEPS = 0.025, 1.0, 200
 METRIC = "mechanism instance-steps/s (state+cur)"
 
 # FP64 pipe instructions of a minimal implementation of each operation,
-# the unit of the algorithmic op count of the FP64 path (see DESIGN.md):
-# add/sub/mul/fma 1; exp 10 (table-driven range reduction + degree-6
-# polynomial + reconstruction); reciprocal or division 7 (seed, two Newton
-# steps, one correction).  A gate: each rate as numerator/denominator
-# (u = (v - vh)/k: 2; EXP A e^u: exp + 1; SIGMOID A/(1 + e^-u): exp + 1;
-# LINOID A u/(1 - e^-u): exp + 2), then one reciprocal for minf and
-# alpha + beta (9 + 7 - 1), then cnexp (x, exp, 1 - e, diff, fma: 14).
-C_EXP, C_DIV = 10, 7
+# the unit of the algorithmic op count of the FP64 path:
+# add/sub/mul/fma 1; exp 9 (table-driven range reduction with a 256-entry
+# table + degree-4 polynomial + reconstruction); reciprocal 3 (hardware seed
+# on the MUFU pipe, one third-order Newton step).  A gate: each rate as
+# numerator/denominator (u = (v - vh)/k: 2; EXP A e^u: exp + 1; SIGMOID
+# A/(1 + e^-u): exp + 1; LINOID A u/(1 - e^-u): exp + 2), then one
+# reciprocal for minf and alpha + beta (8 + 3 + 1), then cnexp (x, exp,
+# 1 - e, diff, fma: 13).
+C_EXP, C_RCP = 9, 3
 RATE_COST = {0: 2 + C_EXP + 1, 1: 2 + C_EXP + 1, 2: 2 + C_EXP + 2}
-GATE_TAIL = 8 + C_DIV + 1 + C_EXP + 1 + 1 + 1
-NODE_COST = 1 + C_DIV + 1                       # d += cm/dt, rhs/d, v +=
+GATE_TAIL = 8 + C_RCP + 1 + C_EXP + 1 + 1 + 1
+NODE_COST = 1 + C_RCP + 1                       # d += cm/dt, 1/d, v += rhs * (1/d)
 
 
 def fp64_ops_per_step(wl) -> float:

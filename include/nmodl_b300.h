@@ -393,8 +393,10 @@ NMODL_API int nmodl_probe_peak(int device, int kind, double *ops_per_s);
 
 /* Diagnostic: y[i] = f(x[i]) on the device (x, y: device, n doubles),
  * f = the FP64 exp of the state kernels (fn 0: table-driven, Tang 1989),
- * CUDA's exp (fn 1), or the round trip double -> float -> double through
- * the kernels' integer-pipe conversions (fn 2), so tests can measure them. */
+ * CUDA's exp (fn 1), the round trip double -> float -> double through
+ * the kernels' integer-pipe conversions (fn 2), or the reciprocal of the
+ * gate and node updates (fn 3: hardware approximation + one third-order
+ * Newton step), so tests can measure them. */
 NMODL_API int nmodl_math_eval(int fn, int64_t n, const double *x, double *y,
                               void *cuda_stream);
 

@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 }
             }
             dd += cmdt;
-            const double vn = A.clamp_v ? vv : vv + r / dd;
+            const double vn = A.clamp_v ? vv : fma(r, rcp_fast(dd), vv);
             if (last) {
                 A.rhs[n0 + n] = r;
                 A.d[n0 + n] = dd;

@@ -53,7 +53,10 @@ __global__ void k_probe_ex2(float* sink, int iters) {
 __global__ void k_math_eval(int fn, int64_t n, const double* __restrict__ x, double* y) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    y[i] = fn == 0 ? exp_tang(x[i]) : fn == 1 ? exp(x[i]) : f2d_int(d2f_int(x[i]));
+    y[i] = fn == 0   ? exp_tang(x[i])
+           : fn == 1 ? exp(x[i])
+           : fn == 2 ? f2d_int(d2f_int(x[i]))
+                     : rcp_fast(x[i]);
 }
 
 }  // namespace nmodl
@@ -61,10 +64,11 @@ __global__ void k_math_eval(int fn, int64_t n, const double* __restrict__ x, dou
 using namespace nmodl;
 
 // fn 0: the library's table-driven FP64 exp; fn 1: CUDA exp (for comparison);
-// fn 2: rounding to float and back through the integer-pipe conversions
+// fn 2: rounding to float and back through the integer-pipe conversions;
+// fn 3: the refined hardware reciprocal of the gate and node updates
 extern "C" NMODL_API int nmodl_math_eval(int fn, int64_t n, const double* x, double* y,
                                          void* stream) {
-    if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y))) return NMODL_ERR_ARG;
+    if (fn < 0 || fn > 3 || n < 0 || (n > 0 && (!x || !y))) return NMODL_ERR_ARG;
     if (n == 0) return NMODL_OK;
     k_math_eval<<<(int)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(fn, n, x, y);
     return cudaGetLastError() == cudaSuccess ? NMODL_OK : NMODL_ERR_CUDA;

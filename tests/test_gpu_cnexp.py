@@ -302,8 +302,8 @@ def test_full_size_sampled_parity(api, orc):
 
 
 def test_table_exp_ulp_error():
-    """The FP64 exp of the state kernels (Tang's table-driven method, 64-entry
-    table, degree-5 polynomial) against mpmath at 40 digits and against
+    """The FP64 exp of the state kernels (Tang's table-driven method, 256-entry
+    table, degree-4 polynomial) against mpmath at 40 digits and against
     CUDA's exp: within 1.5 ulp (table entries are rounded to double)."""
     import mpmath
     from paper_1905_02241_b300 import _lib
@@ -327,6 +327,27 @@ def test_table_exp_ulp_error():
     print(f"table exp: max error {worst:.3f} ulp (3000 samples vs mpmath)")
     assert worst <= 1.5
     assert np.max(np.abs(y - yc) / np.abs(yc)) <= 5e-16
+
+
+def test_fast_reciprocal_within_one_ulp():
+    """The reciprocal of the gate and node updates (hardware approximation +
+    one third-order Newton step) against the correctly rounded 1/x: within
+    one ulp over normal-range inputs, exact at powers of two."""
+    from paper_1905_02241_b300 import _lib
+    rng = np.random.default_rng(7)
+    x = np.concatenate([rng.uniform(0.5, 2.0, 100000),
+                        rng.uniform(1, 10, 50000) * 10.0 ** rng.integers(-300, 300, 50000),
+                        -rng.uniform(1e-6, 1e6, 20000), 2.0 ** np.arange(-1000, 1000, 37)])
+    xd = to_dev(x)
+    y = torch.empty_like(xd)
+    _lib.nmodl_math_eval(3, x.size, xd.data_ptr(), y.data_ptr(), 0)
+    torch.cuda.synchronize()
+    got, ref = y.cpu().numpy(), 1.0 / x
+    ulps = np.abs(got - ref) / np.spacing(np.abs(ref))
+    print(f"fast reciprocal: max {ulps.max():.3f} ulp, exact {np.mean(got == ref):.4f}")
+    assert ulps.max() <= 1.0
+    p2 = x.size - np.arange(-1000, 1000, 37).size
+    assert np.array_equal(got[p2:], ref[p2:])
 
 
 def test_integer_pipe_conversions_round_like_hardware():

@@ -255,8 +255,13 @@ NMODL_API int nmodl_cable_n_cells(const nmodl_cable *cable);
  * v[i]), rhs[p] += gb (v[i] - v[p]), d[i] += ga, d[p] += gb; the tree system
  * with off-diagonals -ga (row i) and -gb (row p) is solved per cell and
  * added to v; nrn_state at the new v.  rhs and d return the last step's
- * assembled values.  Windows of options.window steps are replayed from
- * CUDA graphs. */
+ * assembled values.  With options.clamp_v the system is assembled (rhs and
+ * d reported) but not solved, and v is held.  When every mechanism is
+ * NMODL_HH or NMODL_CNEXP and no ion arrays are registered, the steps run in
+ * the fused tile kernel with tiles of whole cells, each cell's tree system
+ * solved in shared memory between the current and state phases; otherwise
+ * as per-step launch sequences.  Windows of options.window steps are
+ * replayed from CUDA graphs. */
 NMODL_API int nmodl_step_cable(nmodl_ctx *ctx, nmodl_cable *cable,
                                nmodl_mech *const *mechs, int n_mechs, double dt,
                                double cm, double *v, double *rhs, double *d,

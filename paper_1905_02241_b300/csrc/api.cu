@@ -480,7 +480,8 @@ int nmodl_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
 // -------------------------------------------------------------- planning
 
 // Shared memory of one tile, matching the layout in k_fused_tiles.
-static size_t tile_smem_bytes(int prec, int T, const int* gates, int64_t NT, const int64_t* cnt) {
+static size_t tile_smem_bytes(int prec, int T, const int* gates, int64_t NT, const int64_t* cnt,
+                              bool cable) {
     size_t b = 8 * (size_t)NT;
     size_t inst = 0, items = 0;
     for (int t = 0; t < T; ++t) {
@@ -489,14 +490,17 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, int64_t NT, con
     }
     b += 8 * items + 2 * inst + 2 * (size_t)T * (NT + 1);
     if (prec == NMODL_MIXED) b = (b + 15) / 16 * 16 + 4 * (size_t)NT;
+    if (cable) b = (b + 15) / 16 * 16 + 34 * (size_t)NT;  // d, rhs, ga, gb, parent
     return (b + 15) / 16 * 16;
 }
 
-// Greedy tiling: fine blocks of G nodes are merged while the tile's shared
-// memory stays within budget; returns false if one fine block does not fit.
+// Greedy tiling: fine blocks (node ranges [bounds[k], bounds[k+1]): groups
+// of 32 nodes, or whole cells in the cable form) are merged while the
+// tile's shared memory stays within budget; returns false if one fine block
+// does not fit.
 static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, int T,
-                       const int* gates, int64_t n_nodes, int G, size_t budget,
-                       std::vector<int32_t>& recs, size_t& max_smem) {
+                       const int* gates, const std::vector<int64_t>& bounds, bool cable,
+                       size_t budget, std::vector<int32_t>& recs, size_t& max_smem) {
     recs.clear();
     max_smem = 0;
     const int64_t K = (int64_t)off[0].size() - 1;  // fine blocks
@@ -505,17 +509,17 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
     while (k0 < K) {
         int64_t k1 = k0 + 1;
         auto fits = [&](int64_t a, int64_t b) -> bool {
-            const int64_t NT = std::min<int64_t>(b * G, n_nodes) - a * G;
+            const int64_t NT = bounds[b] - bounds[a];
             if (NT > 65535) return false;
             for (int t = 0; t < T; ++t) {
                 cnt[t] = off[t][b] - off[t][a];
                 if (cnt[t] > 65535) return false;
             }
-            return tile_smem_bytes(prec, T, gates, NT, cnt.data()) <= budget;
+            return tile_smem_bytes(prec, T, gates, NT, cnt.data(), cable) <= budget;
         };
         if (!fits(k0, k1)) return false;
         while (k1 < K && fits(k0, k1 + 1)) ++k1;
-        const int64_t n0 = k0 * G, n1 = std::min<int64_t>(k1 * G, n_nodes);
+        const int64_t n0 = bounds[k0], n1 = bounds[k1];
         recs.push_back((int32_t)n0);
         recs.push_back((int32_t)n1);
         for (int t = 0; t < T; ++t) {
@@ -523,7 +527,7 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
             recs.push_back(off[t][k1]);
             cnt[t] = off[t][k1] - off[t][k0];
         }
-        max_smem = std::max(max_smem, tile_smem_bytes(prec, T, gates, n1 - n0, cnt.data()));
+        max_smem = std::max(max_smem, tile_smem_bytes(prec, T, gates, n1 - n0, cnt.data(), cable));
         k0 = k1;
     }
     return true;
@@ -559,8 +563,9 @@ struct Candidate {
 };
 
 static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan* p,
-                      const double* v_user) {
+                      const double* v_user, nmodl_cable* cb) {
     p->mechs.assign(mechs, mechs + n_mechs);
+    p->cable = cb;
     p->precision = c->opt.precision;
     p->n_nodes = mechs[0]->n_nodes;
     // the fused tile kernel covers HH and CNEXP mechanisms without ion arrays
@@ -575,10 +580,15 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     }
 
     const int T = n_mechs;
-    const int G = 32;
-    const int64_t K = (p->n_nodes + G - 1) / G;
-    std::vector<int64_t> bounds(K + 1);
-    for (int64_t k = 0; k <= K; ++k) bounds[k] = std::min<int64_t>(k * G, p->n_nodes);
+    std::vector<int64_t> bounds;
+    if (cb) {
+        bounds = cb->cell_off;  // whole cells
+    } else {
+        const int G = 32;
+        for (int64_t k = 0; k * G < p->n_nodes; ++k) bounds.push_back(k * G);
+        bounds.push_back(p->n_nodes);
+    }
+    const int64_t K = (int64_t)bounds.size() - 1;
     int64_t* d_bounds = nullptr;
     int32_t* d_off = nullptr;
     cudaError_t e;
@@ -633,7 +643,8 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     for (size_t b : budgets) {
         std::vector<int32_t> recs;
         size_t max_smem = 0;
-        if (b > cap || !make_tiles(p->precision, off, T, gates, p->n_nodes, G, b, recs, max_smem)) {
+        if (b > cap || !make_tiles(p->precision, off, T, gates, bounds, cb != nullptr, b, recs,
+                                   max_smem)) {
             if (dbg) std::fprintf(stderr, "[nmodl plan] budget %zu: no tiling\n", b);
             continue;
         }
@@ -721,6 +732,14 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
             a.dt = 0.025;
             a.cm = 1.0;
             a.err = nullptr;
+            if (cb) {
+                a.cable = 1;
+                a.parent = cb->d_parent;
+                a.ga = cb->d_ga;
+                a.gb = cb->d_gb;
+                a.cell_off = cb->d_cell_off;
+                a.n_cells = cb->n_cells;
+            }
             // descriptors
             if (!p->d_md) {
                 if (dalloc(&p->d_md, T) != cudaSuccess) { ok = false; break; }
@@ -787,11 +806,11 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     return NMODL_OK;
 }
 
-static Plan* get_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, const double* v,
-                      int* rc) {
+Plan* nmodl_get_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, const double* v,
+                     int* rc, nmodl_cable* cb) {
     for (auto& p : c->plans) {
         if ((int)p->mechs.size() == n_mechs && p->precision == c->opt.precision &&
-            std::equal(p->mechs.begin(), p->mechs.end(), mechs))
+            p->cable == cb && std::equal(p->mechs.begin(), p->mechs.end(), mechs))
             return p.get();
     }
     std::unique_ptr<Plan> p(new (std::nothrow) Plan());
@@ -799,7 +818,7 @@ static Plan* get_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, const
         *rc = NMODL_ERR_OOM;
         return nullptr;
     }
-    *rc = build_plan(c, mechs, n_mechs, p.get(), v);
+    *rc = build_plan(c, mechs, n_mechs, p.get(), v, cb);
     if (*rc) return nullptr;
     c->plans.push_back(std::move(p));
     return c->plans.back().get();
@@ -830,6 +849,14 @@ static FusedArgs fused_args(nmodl_ctx* c, Plan* p, double dt, double cm, double*
     a.dt = dt;
     a.cm = cm;
     a.err = c->d_err;
+    if (nmodl_cable* cb = p->cable) {
+        a.cable = 1;
+        a.parent = cb->d_parent;
+        a.ga = cb->d_ga;
+        a.gb = cb->d_gb;
+        a.cell_off = cb->d_cell_off;
+        a.n_cells = cb->n_cells;
+    }
     return a;
 }
 
@@ -848,7 +875,7 @@ static cudaError_t enqueue_generic_steps(nmodl_ctx* c, nmodl_mech* const* mechs,
 }
 
 // Enqueue one window either directly or by replaying its cached graph.
-static cudaError_t run_window(nmodl_ctx* c, Plan* p, nmodl_mech* const* mechs, int n_mechs,
+cudaError_t nmodl_run_window(nmodl_ctx* c, Plan* p, nmodl_mech* const* mechs, int n_mechs,
                               double dt, double cm, double* v, double* rhs, double* d,
                               int w) {
     auto direct = [&]() -> cudaError_t {
@@ -903,13 +930,13 @@ int nmodl_step(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, double dt, d
     if (nmodl_check_ion_reads(c, mechs, n_mechs)) return NMODL_ERR_ARG;
     DeviceGuard g(c->device);
     int rc = NMODL_OK;
-    Plan* p = get_plan(c, mechs, n_mechs, v, &rc);
+    Plan* p = nmodl_get_plan(c, mechs, n_mechs, v, &rc, nullptr);
     if (!p) return rc;
     for (int i = 0; i < n_mechs; ++i) nmodl_count_states(mechs[i], nsteps);
     const int W = c->opt.window;
     for (int s = 0; s < nsteps; s += W) {
         const int w = std::min(W, nsteps - s);
-        cudaError_t e = run_window(c, p, mechs, n_mechs, dt, cm, v, rhs, d, w);
+        cudaError_t e = nmodl_run_window(c, p, mechs, n_mechs, dt, cm, v, rhs, d, w);
         if (e != cudaSuccess) return cuda_status(e);
     }
     return NMODL_OK;
@@ -917,7 +944,9 @@ int nmodl_step(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, double dt, d
 
 int nmodl_plan_describe(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, int64_t* out) {
     if (!c || !mechs || n_mechs < 1 || !out) return NMODL_ERR_ARG;
-    for (auto& p : c->plans) {
+    // the most recently built plan of this mechanism list (isolated or cable)
+    for (auto it = c->plans.rbegin(); it != c->plans.rend(); ++it) {
+        auto& p = *it;
         if ((int)p->mechs.size() == n_mechs && p->precision == c->opt.precision &&
             std::equal(p->mechs.begin(), p->mechs.end(), mechs)) {
             out[0] = p->fused ? 1 : 0;

@@ -42,6 +42,7 @@ NMODL_API int nmodl_cable_create(nmodl_ctx* c, int64_t n_nodes, const int32_t* p
     cb->ctx = c;
     cb->n_nodes = n_nodes;
     cb->n_cells = (int64_t)off.size() - 1;
+    cb->cell_off = off;
     do {
         if ((e = dalloc(&cb->d_parent, n_nodes)) != cudaSuccess) break;
         if ((e = dalloc(&cb->d_ga, n_nodes)) != cudaSuccess) break;
@@ -69,6 +70,10 @@ NMODL_API void nmodl_cable_destroy(nmodl_cable* cb) {
     if (!cb) return;
     DeviceGuard dg(cb->ctx->device);
     cudaStreamSynchronize(cb->ctx->stream);
+    auto& P = cb->ctx->plans;  // fused cable plans of this cable
+    P.erase(std::remove_if(P.begin(), P.end(),
+                           [cb](const std::unique_ptr<Plan>& p) { return p->cable == cb; }),
+            P.end());
     for (auto& g : cb->graphs) cudaGraphExecDestroy(g.exec);
     void* ptrs[] = {cb->d_parent, cb->d_ga, cb->d_gb, cb->d_cell_off, cb->d_d2, cb->d_r2};
     for (void* q : ptrs) cudaFree(q);
@@ -90,7 +95,8 @@ static cudaError_t enqueue_cable_steps(nmodl_ctx* c, nmodl_cable* cb, nmodl_mech
         nmodl_zero_ions(c, cb->n_nodes);
         for (int i = 0; i < n_mechs; ++i) nmodl_enqueue_cur(mechs[i], v, rhs, d);
         launch_cable_solve(cb->n_cells, cb->d_cell_off, cb->d_parent, cb->d_ga, cb->d_gb,
-                           1e-3 * cm / dt, v, rhs, d, cb->d_d2, cb->d_r2, c->d_err, c->stream);
+                           1e-3 * cm / dt, v, rhs, d, cb->d_d2, cb->d_r2, c->opt.clamp_v,
+                           c->d_err, c->stream);
         for (int i = 0; i < n_mechs; ++i) nmodl_enqueue_state(mechs[i], dt, v);
     }
     return cudaGetLastError();
@@ -111,7 +117,20 @@ extern "C" NMODL_API int nmodl_step_cable(nmodl_ctx* c, nmodl_cable* cb,
     if (c->has_ions() && c->ion_nodes != cb->n_nodes) return NMODL_ERR_ARG;
     if (nmodl_check_ion_reads(c, mechs, n_mechs)) return NMODL_ERR_ARG;
     DeviceGuard dg(c->device);
+    // fused form: tiles of whole cells, the tree solve inside the tile kernel
+    int rc = NMODL_OK;
+    Plan* p = nmodl_get_plan(c, mechs, n_mechs, v, &rc, cb);
+    if (!p) return rc;
     for (int i = 0; i < n_mechs; ++i) nmodl_count_states(mechs[i], nsteps);
+    if (p->fused) {
+        const int W = c->opt.window;
+        for (int s0 = 0; s0 < nsteps; s0 += W) {
+            cudaError_t e = nmodl_run_window(c, p, mechs, n_mechs, dt, cm, v, rhs, d,
+                                             std::min(W, nsteps - s0));
+            if (e != cudaSuccess) return nmodl_cuda_status(e);
+        }
+        return NMODL_OK;
+    }
     std::vector<nmodl_mech*> list(mechs, mechs + n_mechs);
     if (list != cb->graph_mechs || cb->graph_epoch != c->epoch) {  // stale graphs
         for (auto& g : cb->graphs) cudaGraphExecDestroy(g.exec);

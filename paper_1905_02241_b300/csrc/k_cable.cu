@@ -20,7 +20,7 @@ __global__ void k_cable_solve(int64_t n_cells, const int64_t* __restrict__ cell_
                               const int32_t* __restrict__ parent,
                               const double* __restrict__ ga, const double* __restrict__ gb,
                               double cmdt, double* v, double* rhs, double* d, double* d2,
-                              double* r2, int32_t* err) {
+                              double* r2, int clamp, int32_t* err) {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= n_cells) return;
     const int64_t a = cell_off[c], b = cell_off[c + 1];
@@ -40,6 +40,7 @@ __global__ void k_cable_solve(int64_t n_cells, const int64_t* __restrict__ cell_
         d[i] = d2[i];
         rhs[i] = r2[i];
     }
+    if (clamp) return;  // v held: the assembled system is reported, not solved
     for (int64_t i = b - 1; i > a; --i) {
         const int64_t p = parent[i];
         const double f = gb[i] / d2[i];
@@ -57,12 +58,12 @@ __global__ void k_cable_solve(int64_t n_cells, const int64_t* __restrict__ cell_
 
 void launch_cable_solve(int64_t n_cells, const int64_t* cell_off, const int32_t* parent,
                         const double* ga, const double* gb, double cmdt, double* v,
-                        double* rhs, double* d, double* d2, double* r2, int32_t* err,
-                        cudaStream_t s) {
+                        double* rhs, double* d, double* d2, double* r2, int clamp,
+                        int32_t* err, cudaStream_t s) {
     if (n_cells == 0) return;
     const int block = 64;
     k_cable_solve<<<(int)((n_cells + block - 1) / block), block, 0, s>>>(
-        n_cells, cell_off, parent, ga, gb, cmdt, v, rhs, d, d2, r2, err);
+        n_cells, cell_off, parent, ga, gb, cmdt, v, rhs, d, d2, r2, clamp, err);
 }
 
 }  // namespace nmodl

@@ -225,9 +225,19 @@ __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
 //   uint16  nid_s[sum_t cnt_t]            local node id of each instance
 //   uint16  seg_s[T][NT + 1]              per-type segment offsets
 //   float   vf_s[NT]                      (MIXED) float copy of v, 16-aligned
+//   double  d2_s[NT], r2_s[NT], ga_s[NT], gb_s[NT]   (cable), 16-aligned
+//   uint16  par_s[NT]                     (cable) local parent, 0xffff at roots
 // Tile record (int32): n0, n1, then a_t, b_t per type (instance ranges).
 // The host plan guarantees NT <= 65535, cnt_t <= 65535 and that the layout
 // fits the dynamic shared memory of the launch.
+//
+// Cable form: tiles hold whole cells.  After the current phase each node
+// adds its own axial term (in parallel); then one thread per cell adds each
+// child's term to its parent and eliminates leaf -> root in the same pass
+// (parents precede children, so a node is final when reached and there is
+// no fill; Hines 1984), keeping 1/d of every node for the substitution
+// root -> leaf; v += the solution.  On the last step of the window the
+// assembled system is written out first (rhs and d report it).
 template <int PREC>
 __global__ void __launch_bounds__(kFusedMaxBlock)
     k_fused_tiles(FusedArgs A) {
@@ -243,6 +253,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     __shared__ float phidt_f[kMaxMechsFused];
 
     __shared__ int tile_s;
+    __shared__ int64_t cell0_s, cell1_s;
 
     const int tid = threadIdx.x;
     const int T = A.n_types;
@@ -307,12 +318,39 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     // at the next 16-byte boundary
     float* vf_s = reinterpret_cast<float*>(
         (reinterpret_cast<uintptr_t>(seg_s + T * (NT + 1)) + 15) & ~(uintptr_t)15);
+    // cable: the tree system, at the next 16-byte boundary after the above
+    double* d2_s = reinterpret_cast<double*>(
+        (reinterpret_cast<uintptr_t>(PREC == NMODL_MIXED ? (void*)(vf_s + NT)
+                                                         : (void*)(seg_s + T * (NT + 1))) +
+         15) & ~(uintptr_t)15);
+    double* r2_s = d2_s + NT;
+    double* ga_s = r2_s + NT;
+    double* gb_s = ga_s + NT;
+    uint16_t* par_s = reinterpret_cast<uint16_t*>(gb_s + NT);
+    if (A.cable && tid == 0) {
+        // cells [cell0, cell1) of this tile: first cell starting at n0
+        int64_t lo = 0, hi = A.n_cells;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (A.cell_off[mid] < n0) lo = mid + 1; else hi = mid;
+        }
+        int64_t c1 = lo;
+        while (c1 < A.n_cells && A.cell_off[c1 + 1] <= n0 + NT) ++c1;
+        cell0_s = lo;
+        cell1_s = c1;
+    }
 
     // ---- load the tile
     for (int k = tid; k < NT; k += blockDim.x) {
         const double vv = A.v[n0 + k];
         v_s[k] = vv;
         if (PREC == NMODL_MIXED) vf_s[k] = d2f_int(vv);
+        if (A.cable) {
+            const int pp = A.parent[n0 + k];
+            par_s[k] = pp < 0 ? (uint16_t)0xffffu : (uint16_t)(pp - n0);
+            ga_s[k] = A.ga[n0 + k];
+            gb_s[k] = A.gb[n0 + k];
+        }
     }
     {
         int q = 0;
@@ -393,6 +431,16 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 }
             }
             dd += cmdt;
+            if (A.cable) {
+                const int pp = par_s[n];
+                if (pp != 0xffff) {  // own axial term
+                    r = fma(-ga_s[n], vv - v_s[pp], r);
+                    dd += ga_s[n];
+                }
+                r2_s[n] = r;
+                d2_s[n] = dd;
+                continue;
+            }
             const double vn = A.clamp_v ? vv : fma(r, rcp_fast(dd), vv);
             if (last) {
                 A.rhs[n0 + n] = r;
@@ -402,6 +450,90 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             if (PREC == NMODL_MIXED) vf_s[n] = d2f_int(vn);
         }
         __syncthreads();
+        if (A.cable) {
+            const int ncell = (int)(cell1_s - cell0_s);
+            if (last) {
+                // report the assembled system: children's terms into parents
+                for (int c = tid; c < ncell; c += blockDim.x) {
+                    const int a = (int)(A.cell_off[cell0_s + c] - n0);
+                    const int b = (int)(A.cell_off[cell0_s + c + 1] - n0);
+                    for (int i = b - 1; i > a; --i) {
+                        const int pp = par_s[i];
+                        r2_s[pp] = fma(gb_s[i], v_s[i] - v_s[pp], r2_s[pp]);
+                        d2_s[pp] += gb_s[i];
+                    }
+                }
+                __syncthreads();
+                for (int n = tid; n < NT; n += blockDim.x) {
+                    A.rhs[n0 + n] = r2_s[n];
+                    A.d[n0 + n] = d2_s[n];
+                }
+            }
+            if (!A.clamp_v) {
+                for (int c = tid; c < ncell; c += blockDim.x) {
+                    const int a = (int)(A.cell_off[cell0_s + c] - n0);
+                    const int b = (int)(A.cell_off[cell0_s + c + 1] - n0);
+                    // leaf -> root: (parent terms unless already added), then
+                    // eliminate node i from its parent's row; d2_s[i] := 1/d.
+                    // The parent's updated (d, rhs) stay in registers while
+                    // the walk follows an unbranched run (parent == i - 1).
+                    int pc = -1;         // node whose values are carried
+                    double dc = 0.0, rc = 0.0;
+                    for (int i = b - 1; i > a; --i) {
+                        double di, ri;
+                        if (pc == i) {
+                            di = dc;
+                            ri = rc;
+                        } else {
+                            if (pc >= 0) {
+                                d2_s[pc] = dc;
+                                r2_s[pc] = rc;
+                            }
+                            di = d2_s[i];
+                            ri = r2_s[i];
+                        }
+                        const int pp = par_s[i];
+                        double rp = r2_s[pp], dp = d2_s[pp];
+                        if (!last) {
+                            rp = fma(gb_s[i], v_s[i] - v_s[pp], rp);
+                            dp += gb_s[i];
+                        }
+                        const double rd = rcp_fast(di);
+                        const double f = gb_s[i] * rd;
+                        dc = fma(-f, ga_s[i], dp);
+                        rc = fma(f, ri, rp);
+                        pc = pp;
+                        d2_s[i] = rd;
+                        r2_s[i] = ri;
+                    }
+                    double ra;  // root
+                    if (pc == a) ra = rc * rcp_fast(dc);
+                    else {
+                        if (pc >= 0) {
+                            d2_s[pc] = dc;
+                            r2_s[pc] = rc;
+                        }
+                        ra = r2_s[a] * rcp_fast(d2_s[a]);
+                    }
+                    r2_s[a] = ra;
+                    // root -> leaf; the previous node's value is carried
+                    double rprev = ra;
+                    for (int i = a + 1; i < b; ++i) {
+                        const int pp = par_s[i];
+                        const double rpar = (pp == i - 1) ? rprev : r2_s[pp];
+                        rprev = fma(ga_s[i], rpar, r2_s[i]) * d2_s[i];
+                        r2_s[i] = rprev;
+                    }
+                }
+                __syncthreads();
+                for (int n = tid; n < NT; n += blockDim.x) {
+                    const double vn = v_s[n] + r2_s[n];
+                    v_s[n] = vn;
+                    if (PREC == NMODL_MIXED) vf_s[n] = d2f_int(vn);
+                }
+            }
+            __syncthreads();
+        }
         // ---- state update, one thread per (instance, gate) item
         int q = 0;
         for (int k = tid; k < total_items; k += blockDim.x) {

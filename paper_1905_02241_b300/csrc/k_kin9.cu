@@ -30,11 +30,15 @@ __host__ __device__ constexpr bool in_band(int i, int j) { return (i - j <= 3) &
 // In-place no-pivot LU of the banded 9x9 matrix M (only band entries used);
 // the diagonal is replaced by the reciprocals of the pivots, so that the
 // triangular solves multiply instead of divide.
+// pivot reciprocal: the refined hardware reciprocal in FP64, IEEE in FP32
+__device__ __forceinline__ double recip(double x) { return rcp_fast(x); }
+__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
+
 template <typename R>
 __device__ __forceinline__ void lu_band(R (&M)[9][9]) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        const R rp = R(1) / M[k][k];
+        const R rp = recip(M[k][k]);
         M[k][k] = rp;
 #pragma unroll
         for (int i = k + 1; i < 9; ++i) {

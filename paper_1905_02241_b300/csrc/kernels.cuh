@@ -28,6 +28,14 @@ struct FusedArgs {
     double* d;
     double dt, cm;
     int32_t* err;
+    // cable form (tiles hold whole cells): per-node parent (-1 at roots),
+    // axial conductances, and the cell boundaries
+    const int32_t* parent;
+    const double* ga;
+    const double* gb;
+    const int64_t* cell_off;
+    int64_t n_cells;
+    int32_t cable;
 };
 
 void launch_init_gates(const MechD* md, int n_gates, int64_t n, const int32_t* ni,
@@ -108,7 +116,7 @@ void launch_tile_bounds(const int32_t* ni, int64_t n, const int64_t* nodes,
                         int64_t n_bounds, int32_t* out, cudaStream_t s);
 void launch_cable_solve(int64_t n_cells, const int64_t* cell_off, const int32_t* parent,
                         const double* ga, const double* gb, double cmdt, double* v,
-                        double* rhs, double* d, double* d2, double* r2, int32_t* err,
-                        cudaStream_t s);
+                        double* rhs, double* d, double* d2, double* r2, int clamp,
+                        int32_t* err, cudaStream_t s);
 
 }  // namespace nmodl

@@ -10,6 +10,7 @@
 #include "kernels.cuh"
 
 struct nmodl_surrogate;
+struct nmodl_cable;
 
 struct DeviceGuard {
     int prev = -1;
@@ -42,6 +43,7 @@ struct GraphEntry {
 
 struct Plan {
     std::vector<nmodl_mech*> mechs;
+    nmodl_cable* cable = nullptr;   // cable form: tiles of whole cells
     int precision = 0;
     int64_t n_nodes = 0;
     bool fused = false;
@@ -131,6 +133,12 @@ void nmodl_count_states(nmodl_mech* m, int64_t k);
 void nmodl_zero_ions(nmodl_ctx* c, int64_t n_nodes);
 // NMODL_OK when every mechanism's ion reads are satisfied by the context
 int nmodl_check_ion_reads(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs);
+// step plan of a mechanism list (isolated, or the cable form of cb), built
+// and autotuned on first use; fused windows run through nmodl_run_window
+Plan* nmodl_get_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, const double* v,
+                     int* rc, nmodl_cable* cb);
+cudaError_t nmodl_run_window(nmodl_ctx* c, Plan* p, nmodl_mech* const* mechs, int n_mechs,
+                             double dt, double cm, double* v, double* rhs, double* d, int w);
 }
 
 struct nmodl_cable {
@@ -139,6 +147,7 @@ struct nmodl_cable {
     int32_t* d_parent = nullptr;
     double *d_ga = nullptr, *d_gb = nullptr;
     int64_t* d_cell_off = nullptr;
+    std::vector<int64_t> cell_off;             // host copy (cell boundaries)
     double *d_d2 = nullptr, *d_r2 = nullptr;  // eliminated system (scratch)
     std::vector<GraphEntry> graphs;
     std::vector<nmodl_mech*> graph_mechs;      // mechanism list the graphs hold

@@ -138,8 +138,16 @@ def cable(dev, n_cells=10000, nsteps=200):
         m.init(v)
     cb = Cable(ctx, cab["parent"], cab["ga"], cab["gb"])
     cb.step(mechs, DT, CM, v, rhs, d, 40)
+    out["plan_cable"] = ctx.plan(mechs)
     ms = _time(lambda: cb.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["cable_fp64"] = ninst * nsteps / (ms * 1e-3)
+    # the per-step launch sequence (taken while ion arrays are registered)
+    ion = torch.zeros_like(v)
+    ctx.set_ions(ina=ion)
+    cb.step(mechs, DT, CM, v, rhs, d, 40)
+    ms = _time(lambda: cb.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
+    out["cable_per_step_launches_fp64"] = ninst * nsteps / (ms * 1e-3)
+    ctx.set_ions()
     ctx.step(mechs, DT, CM, v, rhs, d, 40)
     ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["isolated_fused_fp64"] = ninst * nsteps / (ms * 1e-3)

@@ -490,7 +490,8 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, int64_t NT, con
     }
     b += 8 * items + 2 * inst + 2 * (size_t)T * (NT + 1);
     if (prec == NMODL_MIXED) b = (b + 15) / 16 * 16 + 4 * (size_t)NT;
-    if (cable) b = (b + 15) / 16 * 16 + 34 * (size_t)NT;  // d, rhs, ga, gb, parent
+    // d, rhs, ga, gb, parent, and the level schedule (at most 6 NT + 5 uint16)
+    if (cable) b = (b + 15) / 16 * 16 + 34 * (size_t)NT + 2 * (6 * (size_t)NT + 5);
     return (b + 15) / 16 * 16;
 }
 
@@ -535,8 +536,7 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
 
 // Largest-first order of tile records (cost = gate items + instances), the
 // work list of the fused kernel.
-static void lpt_order(std::vector<int32_t>& recs, int T, const int* gates) {
-    const int stride = 2 + 2 * T;
+static void lpt_order(std::vector<int32_t>& recs, int T, const int* gates, int stride) {
     const size_t n = recs.size() / stride;
     std::vector<std::pair<int64_t, size_t>> cost(n);
     for (size_t k = 0; k < n; ++k) {
@@ -553,6 +553,80 @@ static void lpt_order(std::vector<int32_t>& recs, int T, const int* gates) {
     recs.swap(out);
 }
 
+// Level schedule of the tree solve of one tile (local node ids, uint16):
+// [H, D, EL[H+1], SL[D+1], E[NT], S[NT], coff[NT+1], clist[...]] with E the
+// nodes by height above the leaves (a node's children all have lower
+// height), EL its level offsets, S the nodes by depth below the root, SL
+// its offsets, and the children of node i at clist[coff[i] .. coff[i+1])
+// in increasing order.  Nodes of one level are independent.
+static void cable_sched(const nmodl_cable* cb, int64_t n0, int64_t n1,
+                        std::vector<uint16_t>& out) {
+    const int NT = (int)(n1 - n0);
+    std::vector<int> par(NT), h(NT, 0), dep(NT, 0), nch(NT, 0);
+    int roots = 0;
+    for (int i = 0; i < NT; ++i) {
+        const int32_t p = cb->parent[n0 + i];
+        par[i] = p < 0 ? -1 : (int)(p - n0);
+        roots += p < 0;
+    }
+    for (int i = NT - 1; i >= 0; --i)
+        if (par[i] >= 0) {
+            h[par[i]] = std::max(h[par[i]], h[i] + 1);
+            nch[par[i]]++;
+        }
+    int H = 0, D = 0;
+    for (int i = 0; i < NT; ++i) {
+        dep[i] = par[i] < 0 ? 0 : dep[par[i]] + 1;
+        H = std::max(H, h[i] + 1);
+        D = std::max(D, dep[i] + 1);
+    }
+    std::vector<int> EL(H + 1, 0), SL(D + 1, 0);
+    for (int i = 0; i < NT; ++i) {
+        EL[h[i] + 1]++;
+        SL[dep[i] + 1]++;
+    }
+    for (int k = 0; k < H; ++k) EL[k + 1] += EL[k];
+    for (int k = 0; k < D; ++k) SL[k + 1] += SL[k];
+    std::vector<int> E(NT), S(NT), pe(EL.begin(), EL.end() - 1), ps(SL.begin(), SL.end() - 1);
+    for (int i = 0; i < NT; ++i) {
+        E[pe[h[i]]++] = i;
+        S[ps[dep[i]]++] = i;
+    }
+    std::vector<int> coff(NT + 1, 0);
+    for (int i = 0; i < NT; ++i) coff[i + 1] = coff[i] + nch[i];
+    std::vector<int> clist(NT - roots), pc(coff.begin(), coff.end() - 1);
+    for (int i = 0; i < NT; ++i)
+        if (par[i] >= 0) clist[pc[par[i]]++] = i;
+    out.clear();
+    out.push_back((uint16_t)H);
+    out.push_back((uint16_t)D);
+    for (int x : EL) out.push_back((uint16_t)x);
+    for (int x : SL) out.push_back((uint16_t)x);
+    for (int x : E) out.push_back((uint16_t)x);
+    for (int x : S) out.push_back((uint16_t)x);
+    for (int x : coff) out.push_back((uint16_t)x);
+    for (int x : clist) out.push_back((uint16_t)x);
+}
+
+// Append (schedule offset, length) to every tile record of a cable plan and
+// the schedules to `sched`.
+static void add_cable_sched(const nmodl_cable* cb, int T, std::vector<int32_t>& recs,
+                            std::vector<uint16_t>& sched) {
+    const int in = 2 + 2 * T, outs = in + 2;
+    const size_t n = recs.size() / in;
+    std::vector<int32_t> r2(n * outs);
+    std::vector<uint16_t> one;
+    sched.clear();
+    for (size_t k = 0; k < n; ++k) {
+        std::copy(recs.begin() + k * in, recs.begin() + (k + 1) * in, r2.begin() + k * outs);
+        cable_sched(cb, recs[k * in], recs[k * in + 1], one);
+        r2[k * outs + in] = (int32_t)sched.size();
+        r2[k * outs + in + 1] = (int32_t)one.size();
+        sched.insert(sched.end(), one.begin(), one.end());
+    }
+    recs.swap(r2);
+}
+
 struct Candidate {
     size_t budget;
     int block;
@@ -560,6 +634,7 @@ struct Candidate {
     std::vector<int32_t> recs;
     size_t smem;
     double ms = 0.0;
+    std::shared_ptr<std::vector<uint16_t>> sched;  // cable level schedules
 };
 
 static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan* p,
@@ -621,7 +696,8 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     const size_t cap = dev_smem_optin > (int)stat ? dev_smem_optin - stat : 0;
     e = fused_prepare(p->precision, cap);
     if (e != cudaSuccess) return cuda_status(e);
-    p->tile_stride = 2 + 2 * T;
+    p->tile_stride = 2 + 2 * T + (cb ? 2 : 0);
+    const int stride = p->tile_stride;
 
     // ---- candidate shapes
     std::vector<size_t> budgets;
@@ -642,16 +718,20 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     std::vector<Candidate> cands;
     for (size_t b : budgets) {
         std::vector<int32_t> recs;
+        auto sched_p = std::make_shared<std::vector<uint16_t>>();
+        std::vector<uint16_t>& sched = *sched_p;
         size_t max_smem = 0;
         if (b > cap || !make_tiles(p->precision, off, T, gates, bounds, cb != nullptr, b, recs,
                                    max_smem)) {
             if (dbg) std::fprintf(stderr, "[nmodl plan] budget %zu: no tiling\n", b);
             continue;
         }
-        lpt_order(recs, T, gates);
+        if (cb) add_cable_sched(cb, T, recs, sched);
+        lpt_order(recs, T, gates, stride);
         for (int blk : blocks)
             for (bool ps : pers)
-                cands.push_back(Candidate{b, blk, ps, recs, std::max<size_t>(max_smem, 16)});
+                cands.push_back(Candidate{b, blk, ps, recs, std::max<size_t>(max_smem, 16), 0.0,
+                                          sched_p});
     }
     if (dbg)
         std::fprintf(stderr, "[nmodl plan] prec %d types %d nodes %lld cap %zu stat %zu cands %zu\n",
@@ -683,9 +763,14 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
                                  c->stream) == cudaSuccess;
         else if (ok)
             ok = cudaMemsetAsync(sv, 0, p->n_nodes * sizeof(double), c->stream) == cudaSuccess;
-        size_t max_recs = 0;
-        for (auto& cd : cands) max_recs = std::max(max_recs, cd.recs.size());
+        size_t max_recs = 0, max_sched = 0;
+        for (auto& cd : cands) {
+            max_recs = std::max(max_recs, cd.recs.size());
+            max_sched = std::max(max_sched, cd.sched->size());
+        }
         ok = ok && dalloc(&d_trial, max_recs) == cudaSuccess;
+        uint16_t* d_sched_trial = nullptr;
+        ok = ok && dalloc(&d_sched_trial, max_sched) == cudaSuccess;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
         const int trial_steps = std::min(c->opt.window, 8);
@@ -707,9 +792,12 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
                     inst += cd.recs[k * st + 3 + 2 * tt] - cd.recs[k * st + 2 + 2 * tt];
                 sub.insert(sub.end(), cd.recs.begin() + k * st, cd.recs.begin() + (k + 1) * st);
             }
-            lpt_order(sub, T, gates);
+            lpt_order(sub, T, gates, st);
             cudaMemcpyAsync(d_trial, sub.data(), sub.size() * sizeof(int32_t),
                             cudaMemcpyHostToDevice, c->stream);
+            if (!cd.sched->empty())
+                cudaMemcpyAsync(d_sched_trial, cd.sched->data(), cd.sched->size() * sizeof(uint16_t),
+                                cudaMemcpyHostToDevice, c->stream);
             FusedArgs a{};
             a.md = nullptr;
             a.n_types = T;
@@ -737,8 +825,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
                 a.parent = cb->d_parent;
                 a.ga = cb->d_ga;
                 a.gb = cb->d_gb;
-                a.cell_off = cb->d_cell_off;
-                a.n_cells = cb->n_cells;
+                a.sched = d_sched_trial;
             }
             // descriptors
             if (!p->d_md) {
@@ -775,6 +862,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
         cudaFree(srhs);
         cudaFree(sd);
         cudaFree(d_trial);
+        cudaFree(d_sched_trial);
         cudaGetLastError();
         if (!ok) best = 0;
     }
@@ -795,6 +883,11 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     if ((e = dalloc(&p->d_tiles, ch.recs.size())) != cudaSuccess) return cuda_status(e);
     cudaMemcpyAsync(p->d_tiles, ch.recs.data(), ch.recs.size() * sizeof(int32_t),
                     cudaMemcpyHostToDevice, c->stream);
+    if (!ch.sched->empty()) {
+        if ((e = dalloc(&p->d_sched, ch.sched->size())) != cudaSuccess) return cuda_status(e);
+        cudaMemcpyAsync(p->d_sched, ch.sched->data(), ch.sched->size() * sizeof(uint16_t),
+                        cudaMemcpyHostToDevice, c->stream);
+    }
     if (!p->d_md) {
         if ((e = dalloc(&p->d_md, T)) != cudaSuccess) return cuda_status(e);
         std::vector<MechD> mds(T);
@@ -854,8 +947,7 @@ static FusedArgs fused_args(nmodl_ctx* c, Plan* p, double dt, double cm, double*
         a.parent = cb->d_parent;
         a.ga = cb->d_ga;
         a.gb = cb->d_gb;
-        a.cell_off = cb->d_cell_off;
-        a.n_cells = cb->n_cells;
+        a.sched = p->d_sched;
     }
     return a;
 }

@@ -43,6 +43,7 @@ NMODL_API int nmodl_cable_create(nmodl_ctx* c, int64_t n_nodes, const int32_t* p
     cb->n_nodes = n_nodes;
     cb->n_cells = (int64_t)off.size() - 1;
     cb->cell_off = off;
+    cb->parent = hp;
     do {
         if ((e = dalloc(&cb->d_parent, n_nodes)) != cudaSuccess) break;
         if ((e = dalloc(&cb->d_ga, n_nodes)) != cudaSuccess) break;

@@ -227,17 +227,20 @@ __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
 //   float   vf_s[NT]                      (MIXED) float copy of v, 16-aligned
 //   double  d2_s[NT], r2_s[NT], ga_s[NT], gb_s[NT]   (cable), 16-aligned
 //   uint16  par_s[NT]                     (cable) local parent, 0xffff at roots
+//   uint16  sched_s[...]                  (cable) level schedule of the solve
 // Tile record (int32): n0, n1, then a_t, b_t per type (instance ranges).
 // The host plan guarantees NT <= 65535, cnt_t <= 65535 and that the layout
 // fits the dynamic shared memory of the launch.
 //
 // Cable form: tiles hold whole cells.  After the current phase each node
-// adds its own axial term (in parallel); then one thread per cell adds each
-// child's term to its parent and eliminates leaf -> root in the same pass
-// (parents precede children, so a node is final when reached and there is
-// no fill; Hines 1984), keeping 1/d of every node for the substitution
-// root -> leaf; v += the solution.  On the last step of the window the
-// assembled system is written out first (rhs and d report it).
+// adds its own axial term (in parallel).  The tree system is then solved by
+// one warp in levels: nodes of equal height above the leaves are eliminated
+// together (each gathers its children's axial terms and eliminated rows, in
+// a fixed order, and keeps 1/d), then nodes of equal depth below the root
+// are substituted together -- Hines' elimination (1984; no fill because
+// parents precede children) scheduled by levels.  v += the solution.  On
+// the last step of the window the assembled system is written out first
+// (rhs and d report it).
 template <int PREC>
 __global__ void __launch_bounds__(kFusedMaxBlock)
     k_fused_tiles(FusedArgs A) {
@@ -253,7 +256,6 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     __shared__ float phidt_f[kMaxMechsFused];
 
     __shared__ int tile_s;
-    __shared__ int64_t cell0_s, cell1_s;
 
     const int tid = threadIdx.x;
     const int T = A.n_types;
@@ -327,17 +329,10 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     double* ga_s = r2_s + NT;
     double* gb_s = ga_s + NT;
     uint16_t* par_s = reinterpret_cast<uint16_t*>(gb_s + NT);
-    if (A.cable && tid == 0) {
-        // cells [cell0, cell1) of this tile: first cell starting at n0
-        int64_t lo = 0, hi = A.n_cells;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (A.cell_off[mid] < n0) lo = mid + 1; else hi = mid;
-        }
-        int64_t c1 = lo;
-        while (c1 < A.n_cells && A.cell_off[c1 + 1] <= n0 + NT) ++c1;
-        cell0_s = lo;
-        cell1_s = c1;
+    uint16_t* sched_s = par_s + NT;
+    if (A.cable) {
+        const int32_t off = rec[2 + 2 * T], len = rec[3 + 2 * T];
+        for (int k = tid; k < len; k += blockDim.x) sched_s[k] = A.sched[off + k];
     }
 
     // ---- load the tile
@@ -451,78 +446,60 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         }
         __syncthreads();
         if (A.cable) {
-            const int ncell = (int)(cell1_s - cell0_s);
+            const int H = sched_s[0], D = sched_s[1];
+            const uint16_t* EL = sched_s + 2;
+            const uint16_t* SL = EL + H + 1;
+            const uint16_t* E = SL + D + 1;
+            const uint16_t* S = E + NT;
+            const uint16_t* coff = S + NT;
+            const uint16_t* clist = coff + NT + 1;
             if (last) {
-                // report the assembled system: children's terms into parents
-                for (int c = tid; c < ncell; c += blockDim.x) {
-                    const int a = (int)(A.cell_off[cell0_s + c] - n0);
-                    const int b = (int)(A.cell_off[cell0_s + c + 1] - n0);
-                    for (int i = b - 1; i > a; --i) {
-                        const int pp = par_s[i];
-                        r2_s[pp] = fma(gb_s[i], v_s[i] - v_s[pp], r2_s[pp]);
-                        d2_s[pp] += gb_s[i];
+                // the assembled system: children's axial terms into parents
+                for (int n = tid; n < NT; n += blockDim.x) {
+                    double r = r2_s[n], dd = d2_s[n];
+                    for (int q = coff[n]; q < coff[n + 1]; ++q) {
+                        const int c = clist[q];
+                        r = fma(gb_s[c], v_s[c] - v_s[n], r);
+                        dd += gb_s[c];
                     }
+                    r2_s[n] = r;
+                    d2_s[n] = dd;
+                    A.rhs[n0 + n] = r;
+                    A.d[n0 + n] = dd;
                 }
                 __syncthreads();
-                for (int n = tid; n < NT; n += blockDim.x) {
-                    A.rhs[n0 + n] = r2_s[n];
-                    A.d[n0 + n] = d2_s[n];
-                }
             }
             if (!A.clamp_v) {
-                for (int c = tid; c < ncell; c += blockDim.x) {
-                    const int a = (int)(A.cell_off[cell0_s + c] - n0);
-                    const int b = (int)(A.cell_off[cell0_s + c + 1] - n0);
-                    // leaf -> root: (parent terms unless already added), then
-                    // eliminate node i from its parent's row; d2_s[i] := 1/d.
-                    // The parent's updated (d, rhs) stay in registers while
-                    // the walk follows an unbranched run (parent == i - 1).
-                    int pc = -1;         // node whose values are carried
-                    double dc = 0.0, rc = 0.0;
-                    for (int i = b - 1; i > a; --i) {
-                        double di, ri;
-                        if (pc == i) {
-                            di = dc;
-                            ri = rc;
-                        } else {
-                            if (pc >= 0) {
-                                d2_s[pc] = dc;
-                                r2_s[pc] = rc;
+                if (tid < 32) {
+                    // leaves -> roots by height; d2_s[i] := 1/d of node i
+                    for (int h = 0; h < H; ++h) {
+                        for (int k = EL[h] + tid; k < EL[h + 1]; k += 32) {
+                            const int i = E[k];
+                            double dd = d2_s[i], r = r2_s[i];
+                            for (int q = coff[i]; q < coff[i + 1]; ++q) {
+                                const int c = clist[q];
+                                if (!last) {
+                                    r = fma(gb_s[c], v_s[c] - v_s[i], r);
+                                    dd += gb_s[c];
+                                }
+                                const double g = gb_s[c] * d2_s[c];
+                                dd = fma(-g, ga_s[c], dd);
+                                r = fma(g, r2_s[c], r);
                             }
-                            di = d2_s[i];
-                            ri = r2_s[i];
+                            d2_s[i] = rcp_fast(dd);
+                            r2_s[i] = r;
                         }
-                        const int pp = par_s[i];
-                        double rp = r2_s[pp], dp = d2_s[pp];
-                        if (!last) {
-                            rp = fma(gb_s[i], v_s[i] - v_s[pp], rp);
-                            dp += gb_s[i];
-                        }
-                        const double rd = rcp_fast(di);
-                        const double f = gb_s[i] * rd;
-                        dc = fma(-f, ga_s[i], dp);
-                        rc = fma(f, ri, rp);
-                        pc = pp;
-                        d2_s[i] = rd;
-                        r2_s[i] = ri;
+                        __syncwarp();
                     }
-                    double ra;  // root
-                    if (pc == a) ra = rc * rcp_fast(dc);
-                    else {
-                        if (pc >= 0) {
-                            d2_s[pc] = dc;
-                            r2_s[pc] = rc;
+                    // roots -> leaves by depth: r2_s[i] := the change of v
+                    for (int l = 0; l < D; ++l) {
+                        for (int k = SL[l] + tid; k < SL[l + 1]; k += 32) {
+                            const int i = S[k];
+                            const int pp = par_s[i];
+                            const double r = pp == 0xffff ? r2_s[i] : fma(ga_s[i], r2_s[pp], r2_s[i]);
+                            r2_s[i] = r * d2_s[i];
                         }
-                        ra = r2_s[a] * rcp_fast(d2_s[a]);
-                    }
-                    r2_s[a] = ra;
-                    // root -> leaf; the previous node's value is carried
-                    double rprev = ra;
-                    for (int i = a + 1; i < b; ++i) {
-                        const int pp = par_s[i];
-                        const double rpar = (pp == i - 1) ? rprev : r2_s[pp];
-                        rprev = fma(ga_s[i], rpar, r2_s[i]) * d2_s[i];
-                        r2_s[i] = rprev;
+                        __syncwarp();
                     }
                 }
                 __syncthreads();

@@ -29,12 +29,12 @@ struct FusedArgs {
     double dt, cm;
     int32_t* err;
     // cable form (tiles hold whole cells): per-node parent (-1 at roots),
-    // axial conductances, and the cell boundaries
+    // axial conductances, and the tiles' level schedules of the tree solve
+    // (tile record fields 2 + 2 T and 3 + 2 T: offset and length in sched)
     const int32_t* parent;
     const double* ga;
     const double* gb;
-    const int64_t* cell_off;
-    int64_t n_cells;
+    const uint16_t* sched;
     int32_t cable;
 };
 

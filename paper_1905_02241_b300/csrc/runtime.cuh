@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 
 #include <memory>
+#include <cstdint>
 #include <vector>
 
 #include "kernels.cuh"
@@ -53,6 +54,7 @@ struct Plan {
     int32_t* d_tiles = nullptr;
     nmodl::MechD* d_md = nullptr;
     int32_t* d_counter = nullptr;   // persistent form's tile queue
+    uint16_t* d_sched = nullptr;    // cable form: level schedules of the tiles
     bool persistent = false;
     size_t budget = 0;
     int grid = 0;                   // blocks per launch
@@ -62,6 +64,7 @@ struct Plan {
         cudaFree(d_tiles);
         cudaFree(d_md);
         cudaFree(d_counter);
+        cudaFree(d_sched);
     }
 };
 
@@ -147,7 +150,8 @@ struct nmodl_cable {
     int32_t* d_parent = nullptr;
     double *d_ga = nullptr, *d_gb = nullptr;
     int64_t* d_cell_off = nullptr;
-    std::vector<int64_t> cell_off;             // host copy (cell boundaries)
+    std::vector<int64_t> cell_off;             // host copies: cell boundaries,
+    std::vector<int32_t> parent;               // parents (for the tile schedules)
     double *d_d2 = nullptr, *d_r2 = nullptr;  // eliminated system (scratch)
     std::vector<GraphEntry> graphs;
     std::vector<nmodl_mech*> graph_mechs;      // mechanism list the graphs hold

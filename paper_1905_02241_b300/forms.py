@@ -386,6 +386,62 @@ def surrogate_kernel_case(dev=0, n=4_000_000, steps=3, tol=1e-4):
     ctx.close()
 
 
+def kernel_cases(dev=0):
+    """Profiling case of the small-system, ion and cable kernels (seeded,
+    synthetic): two calcium-buffer and two 3-state updates on 4M instances,
+    one current update with ion write-back of each mechanism of the
+    ion-tagged cortical mix on 500k nodes, and one 40-step window of the
+    fused cable step on 4,000 cells (fixed 160 KB tiles of 512 threads, no
+    autotuning).  Prints instance-steps/s of each part."""
+    from .api import Cable
+    dv = f"cuda:{dev}"
+    out = {}
+    n = 4_000_000
+    ni = torch.arange(n, dtype=torch.int32, device=dv)
+    vk = torch.tensor(W.Stream(21, 1).uniform(n, -90.0, 40.0), device=dv)
+    ica = -torch.tensor(W.Stream(21, 2).loguniform(n, 1e-4, 1.0), device=dv)
+    ctx = Context(dev)
+    ctx.set_ions(ica=ica)
+    buf = Mechanism(ctx, W.TYPE_CACUM, ni, n, W.cacum_params())
+    k3 = Mechanism(ctx, W.TYPE_KIN3, ni, n, W.kin3_params(W.Stream(8, 802)))
+    for m, key in ((buf, "cacum"), (k3, "kin3")):
+        m.init(vk)
+        ms = _time(lambda: [m.state(DT, vk) for _ in range(2)], ctx, 1)
+        out[key + "_state"] = 2 * n / (ms * 1e-3)
+        m.close()
+    ctx.close()
+    wl = W.cortical_ions(500_000, seed=8)
+    nn = wl["n_nodes"]
+    ctx = Context(dev)
+    arrs = [torch.zeros(nn, dtype=torch.float64, device=dv) for _ in range(3)]
+    ctx.set_ions(*arrs)
+    mechs = [m for m in _ion_mechs(ctx, wl) if m.type != W.TYPE_CACUM]
+    v = torch.tensor(wl["v0"], device=dv)
+    rhs = torch.zeros_like(v)
+    d = torch.zeros_like(v)
+    for m in mechs:
+        m.init(v)
+    ms = _time(lambda: [m.cur(v, rhs, d) for m in mechs], ctx, 1)
+    out["cur_ions"] = sum(m.n for m in mechs) / (ms * 1e-3)
+    ctx.close()
+    cab = W.cable_cells(4000, seed=7)
+    wl = W.cortical_mix(cab["n_nodes"], seed=2)
+    ctx = Context(dev, autotune=0, tile_smem=160 * 1024, block=512)
+    mechs = _mechs(ctx, wl)
+    v = torch.tensor(wl["v0"], device=dv)
+    rhs = torch.zeros_like(v)
+    d = torch.zeros_like(v)
+    for m in mechs:
+        m.init(v)
+    cb = Cable(ctx, cab["parent"], cab["ga"], cab["gb"])
+    ms = _time(lambda: cb.step(mechs, DT, CM, v, rhs, d, 40), ctx, 1)
+    out["cable_fused"] = _ninst(wl) * 40 / (ms * 1e-3)
+    out["cable_plan"] = ctx.plan(mechs)
+    cb.close()
+    ctx.close()
+    print(out)
+
+
 if __name__ == "__main__":
     import sys
     surrogate_kernel_case(n=int(sys.argv[1]) if len(sys.argv) > 1 else 4_000_000,

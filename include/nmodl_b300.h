@@ -216,10 +216,13 @@ NMODL_API int nmodl_cur(nmodl_mech *m, const double *v, double *rhs, double *d);
  *   d += 1e-3 cm/dt; v += rhs/d (skipped with options.clamp_v);
  *   nrn_state of every mechanism at the new v.
  * On return rhs and d hold the last step's values.  When every mechanism is
- * NMODL_HH or NMODL_CNEXP the steps run in one fused kernel per window of
- * options.window steps, each node tile's states staged in shared memory for
- * the window (the compartments are not coupled); otherwise each step is a
- * sequence of per-mechanism launches.  nsteps = 0 is a no-op. */
+ * NMODL_HH, NMODL_CNEXP, NMODL_KIN3 or NMODL_CACUM (at most 16 of them) the
+ * steps run in one fused kernel per window of options.window steps, each
+ * node tile's states staged in shared memory for the window (the
+ * compartments are not coupled; ion arrays, when registered, are summed per
+ * node in the tile and the buffer reads the tile's ica); otherwise (e.g. a
+ * NMODL_KIN9 in the list) each step is a sequence of per-mechanism launches.
+ * nsteps = 0 is a no-op. */
 NMODL_API int nmodl_step(nmodl_ctx *ctx, nmodl_mech *const *mechs, int n_mechs,
                double dt, double cm, double *v, double *rhs, double *d,
                int nsteps);
@@ -256,11 +259,10 @@ NMODL_API int nmodl_cable_n_cells(const nmodl_cable *cable);
  * with off-diagonals -ga (row i) and -gb (row p) is solved per cell and
  * added to v; nrn_state at the new v.  rhs and d return the last step's
  * assembled values.  With options.clamp_v the system is assembled (rhs and
- * d reported) but not solved, and v is held.  When every mechanism is
- * NMODL_HH or NMODL_CNEXP and no ion arrays are registered, the steps run in
- * the fused tile kernel with tiles of whole cells, each cell's tree system
- * solved in shared memory between the current and state phases; otherwise
- * as per-step launch sequences.  Windows of options.window steps are
+ * d reported) but not solved, and v is held.  When the mechanisms fuse (as
+ * for nmodl_step), the steps run in the fused tile kernel with tiles of
+ * whole cells, each cell's tree system solved in shared memory between the
+ * current and state phases; otherwise as per-step launch sequences.  Windows of options.window steps are
  * replayed from CUDA graphs. */
 NMODL_API int nmodl_step_cable(nmodl_ctx *ctx, nmodl_cable *cable,
                                nmodl_mech *const *mechs, int n_mechs, double dt,
@@ -275,8 +277,8 @@ NMODL_API int nmodl_step_cable(nmodl_ctx *ctx, nmodl_cable *cable,
  * zero the registered arrays at the start of every step, and NMODL_CACUM
  * reads ica (required: NMODL_ERR_ARG from nmodl_state / nmodl_step when no
  * ica array is registered).  Calling again with all NULL unregisters.
- * Registered arrays make nmodl_step take the per-mechanism launch sequence
- * instead of the fused tile kernel. */
+ * The fused tile kernel of nmodl_step writes the arrays on the last step of
+ * each window (the values of the last step, as for rhs and d). */
 NMODL_API int nmodl_ctx_set_ions(nmodl_ctx *ctx, int64_t n_nodes, double *ina,
                                  double *ik, double *ica);
 /* Tag the whole current of a CNEXP, KIN9 or KIN3 mechanism as the current

@@ -114,6 +114,10 @@ static int build_desc(nmodl_mech* m) {
             if (k.af[e] < 0.0 || k.ab[e] < 0.0) return NMODL_ERR_ARG;
         }
         m->n_states = 3;
+        m->md = MechD{};
+        m->md.kind = NMODL_KIN3;
+        m->md.n_gates = 3;
+        m->md.k3 = k;
         return NMODL_OK;
     }
     if (m->type == NMODL_CACUM) {
@@ -129,6 +133,10 @@ static int build_desc(nmodl_mech* m) {
         c.kb = p[4];
         c.btot = p[5];
         m->n_states = 2;
+        m->md = MechD{};
+        m->md.kind = NMODL_CACUM;
+        m->md.n_gates = 2;
+        m->md.cd = c;
         return NMODL_OK;
     }
     if (m->type == NMODL_KIN9) {
@@ -481,7 +489,7 @@ int nmodl_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
 
 // Shared memory of one tile, matching the layout in k_fused_tiles.
 static size_t tile_smem_bytes(int prec, int T, const int* gates, int64_t NT, const int64_t* cnt,
-                              bool cable) {
+                              bool cable, bool ions) {
     size_t b = 8 * (size_t)NT;
     size_t inst = 0, items = 0;
     for (int t = 0; t < T; ++t) {
@@ -490,6 +498,7 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, int64_t NT, con
     }
     b += 8 * items + 2 * inst + 2 * (size_t)T * (NT + 1);
     if (prec == NMODL_MIXED) b = (b + 15) / 16 * 16 + 4 * (size_t)NT;
+    if (ions) b = (b + 15) / 16 * 16 + 8 * (size_t)NT;  // the step's ica per node
     // d, rhs, ga, gb, parent, and the level schedule (at most 6 NT + 5 uint16)
     if (cable) b = (b + 15) / 16 * 16 + 34 * (size_t)NT + 2 * (6 * (size_t)NT + 5);
     return (b + 15) / 16 * 16;
@@ -501,7 +510,7 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, int64_t NT, con
 // does not fit.
 static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, int T,
                        const int* gates, const std::vector<int64_t>& bounds, bool cable,
-                       size_t budget, std::vector<int32_t>& recs, size_t& max_smem) {
+                       bool ions, size_t budget, std::vector<int32_t>& recs, size_t& max_smem) {
     recs.clear();
     max_smem = 0;
     const int64_t K = (int64_t)off[0].size() - 1;  // fine blocks
@@ -516,7 +525,7 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
                 cnt[t] = off[t][b] - off[t][a];
                 if (cnt[t] > 65535) return false;
             }
-            return tile_smem_bytes(prec, T, gates, NT, cnt.data(), cable) <= budget;
+            return tile_smem_bytes(prec, T, gates, NT, cnt.data(), cable, ions) <= budget;
         };
         if (!fits(k0, k1)) return false;
         while (k1 < K && fits(k0, k1 + 1)) ++k1;
@@ -528,7 +537,8 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
             recs.push_back(off[t][k1]);
             cnt[t] = off[t][k1] - off[t][k0];
         }
-        max_smem = std::max(max_smem, tile_smem_bytes(prec, T, gates, n1 - n0, cnt.data(), cable));
+        max_smem = std::max(max_smem,
+                            tile_smem_bytes(prec, T, gates, n1 - n0, cnt.data(), cable, ions));
         k0 = k1;
     }
     return true;
@@ -643,10 +653,18 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     p->cable = cb;
     p->precision = c->opt.precision;
     p->n_nodes = mechs[0]->n_nodes;
-    // the fused tile kernel covers HH and CNEXP mechanisms without ion arrays
-    bool cnexp = n_mechs <= kMaxMechsFused && !c->has_ions();
+    // the fused tile kernel covers HH, CNEXP and the small systems (KIN3,
+    // CACUM), with or without ion arrays
+    bool cnexp = n_mechs <= kMaxMechsFused;
     for (int i = 0; i < n_mechs; ++i)
-        if (mechs[i]->type != NMODL_HH && mechs[i]->type != NMODL_CNEXP) cnexp = false;
+        if (mechs[i]->type != NMODL_HH && mechs[i]->type != NMODL_CNEXP &&
+            mechs[i]->type != NMODL_KIN3 && mechs[i]->type != NMODL_CACUM)
+            cnexp = false;
+    const bool ions = c->has_ions();
+    bool ext = ions;  // the kernel variant with the small systems and ion sums
+    for (int i = 0; i < n_mechs; ++i)
+        if (mechs[i]->type == NMODL_KIN3 || mechs[i]->type == NMODL_CACUM) ext = true;
+    p->variant = p->precision + (ext ? 2 : 0);
     p->fused = false;
     const bool dbg = std::getenv("NMODL_PLAN_DEBUG") != nullptr;
     if (!cnexp || p->n_nodes == 0) {
@@ -692,9 +710,9 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
 
     int dev_smem_optin = 0;
     cudaDeviceGetAttribute(&dev_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    const size_t stat = fused_static_smem(p->precision);
+    const size_t stat = fused_static_smem(p->variant);
     const size_t cap = dev_smem_optin > (int)stat ? dev_smem_optin - stat : 0;
-    e = fused_prepare(p->precision, cap);
+    e = fused_prepare(p->variant, cap);
     if (e != cudaSuccess) return cuda_status(e);
     p->tile_stride = 2 + 2 * T + (cb ? 2 : 0);
     const int stride = p->tile_stride;
@@ -721,8 +739,8 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
         auto sched_p = std::make_shared<std::vector<uint16_t>>();
         std::vector<uint16_t>& sched = *sched_p;
         size_t max_smem = 0;
-        if (b > cap || !make_tiles(p->precision, off, T, gates, bounds, cb != nullptr, b, recs,
-                                   max_smem)) {
+        if (b > cap || !make_tiles(p->precision, off, T, gates, bounds, cb != nullptr, ions, b,
+                                   recs, max_smem)) {
             if (dbg) std::fprintf(stderr, "[nmodl plan] budget %zu: no tiling\n", b);
             continue;
         }
@@ -827,6 +845,9 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
                 a.gb = cb->d_gb;
                 a.sched = d_sched_trial;
             }
+            a.ions = ions;  // sums and ica kept, no ion array written
+            a.newton_tol = c->opt.newton_tol;
+            a.newton_max_iter = c->opt.newton_max_iter;
             // descriptors
             if (!p->d_md) {
                 if (dalloc(&p->d_md, T) != cudaSuccess) { ok = false; break; }
@@ -842,9 +863,9 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
                 if (cd.persistent) cudaMemsetAsync(d_counter, 0, sizeof(int32_t), c->stream);
                 cudaEventRecord(e0, c->stream);
                 const int grid = cd.persistent
-                                     ? fused_resident_grid(p->precision, a.n_tiles, cd.block, cd.smem)
+                                     ? fused_resident_grid(p->variant, a.n_tiles, cd.block, cd.smem)
                                      : a.n_tiles;
-                ok = launch_fused(p->precision, a, grid, cd.block, cd.smem, c->stream) ==
+                ok = launch_fused(p->variant, a, grid, cd.block, cd.smem, c->stream) ==
                      cudaSuccess;
                 cudaEventRecord(e1, c->stream);
                 ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
@@ -878,7 +899,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     p->persistent = ch.persistent;
     p->smem = ch.smem;
     p->n_tiles = (int)(ch.recs.size() / p->tile_stride);
-    p->grid = ch.persistent ? fused_resident_grid(p->precision, p->n_tiles, ch.block, ch.smem)
+    p->grid = ch.persistent ? fused_resident_grid(p->variant, p->n_tiles, ch.block, ch.smem)
                             : p->n_tiles;
     if ((e = dalloc(&p->d_tiles, ch.recs.size())) != cudaSuccess) return cuda_status(e);
     cudaMemcpyAsync(p->d_tiles, ch.recs.data(), ch.recs.size() * sizeof(int32_t),
@@ -942,6 +963,10 @@ static FusedArgs fused_args(nmodl_ctx* c, Plan* p, double dt, double cm, double*
     a.dt = dt;
     a.cm = cm;
     a.err = c->d_err;
+    a.ions = c->has_ions();
+    for (int q = 1; q < 4; ++q) a.ion[q] = c->ion[q];
+    a.newton_tol = c->opt.newton_tol;
+    a.newton_max_iter = c->opt.newton_max_iter;
     if (nmodl_cable* cb = p->cable) {
         a.cable = 1;
         a.parent = cb->d_parent;
@@ -977,7 +1002,7 @@ cudaError_t nmodl_run_window(nmodl_ctx* c, Plan* p, nmodl_mech* const* mechs, in
                 cudaError_t me = cudaMemsetAsync(p->d_counter, 0, sizeof(int32_t), c->stream);
                 if (me != cudaSuccess) return me;
             }
-            return launch_fused(p->precision, a, p->grid, p->block, p->smem, c->stream);
+            return launch_fused(p->variant, a, p->grid, p->block, p->smem, c->stream);
         }
         return enqueue_generic_steps(c, mechs, n_mechs, dt, cm, v, rhs, d, w, p->n_nodes);
     };
@@ -1077,6 +1102,7 @@ int nmodl_mech_set_ion(nmodl_mech* m, int ion) {
     if (e != cudaSuccess) return cuda_status(e);
     nmodl_invalidate_plans(m->ctx, m);
     m->ion = ion;
+    m->md.ion = ion;
     return NMODL_OK;
 }
 

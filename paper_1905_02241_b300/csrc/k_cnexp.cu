@@ -14,6 +14,7 @@
 #include <climits>
 
 #include "kernels.cuh"
+#include "small_systems.cuh"
 
 namespace nmodl {
 
@@ -241,7 +242,7 @@ __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
 // parents precede children) scheduled by levels.  v += the solution.  On
 // the last step of the window the assembled system is written out first
 // (rhs and d report it).
-template <int PREC>
+template <int PREC, bool EXT>
 __global__ void __launch_bounds__(kFusedMaxBlock)
     k_fused_tiles(FusedArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -320,11 +321,13 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     // at the next 16-byte boundary
     float* vf_s = reinterpret_cast<float*>(
         (reinterpret_cast<uintptr_t>(seg_s + T * (NT + 1)) + 15) & ~(uintptr_t)15);
-    // cable: the tree system, at the next 16-byte boundary after the above
-    double* d2_s = reinterpret_cast<double*>(
-        (reinterpret_cast<uintptr_t>(PREC == NMODL_MIXED ? (void*)(vf_s + NT)
-                                                         : (void*)(seg_s + T * (NT + 1))) +
-         15) & ~(uintptr_t)15);
+    // ions: the step's ica per node; cable: the tree system -- each at the
+    // next 16-byte boundary after the above
+    uintptr_t end_p = reinterpret_cast<uintptr_t>(
+        PREC == NMODL_MIXED ? (void*)(vf_s + NT) : (void*)(seg_s + T * (NT + 1)));
+    double* ica_s = reinterpret_cast<double*>((end_p + 15) & ~(uintptr_t)15);
+    if (EXT && A.ions) end_p = reinterpret_cast<uintptr_t>(ica_s + NT);
+    double* d2_s = reinterpret_cast<double*>((end_p + 15) & ~(uintptr_t)15);
     double* r2_s = d2_s + NT;
     double* ga_s = r2_s + NT;
     double* gb_s = ga_s + NT;
@@ -389,15 +392,37 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         for (int n = tid; n < NT; n += blockDim.x) {
             const double vv = v_s[n];
             double r = 0.0, dd = 0.0;
+            double s_na = 0.0, s_k = 0.0, s_ca = 0.0;  // ion sums (ions)
             for (int t = 0; t < T; ++t) {
                 const MechD& M = md_s[t];
                 const uint16_t* seg = seg_s + t * (NT + 1);
                 const int j0 = seg[n], j1 = seg[n + 1];
                 const int cnt = cnt_s[t];
+                if (EXT && M.kind == NMODL_CACUM) continue;  // no membrane current
                 for (int j = j0; j < j1; ++j) {
                     double ci, gi;
-                    if (PREC == NMODL_FP64) {
-                        cur_cnexp_d(M, st_d + st_off[t], cnt, j, vv, ci, gi);
+                    if (EXT && M.kind == NMODL_KIN3) {
+                        const int o = M.k3.open * cnt + j;
+                        const double x = PREC == NMODL_FP64
+                                             ? st_d[st_off[t] + o]
+                                             : f2d_int(st_f[st_off[t] + o].x) + f2d_int(st_f[st_off[t] + o].y);
+                        gi = M.k3.gbar * x;
+                        ci = gi * (vv - M.k3.e);
+                    } else if (PREC == NMODL_FP64) {
+                        if (EXT && A.ions && M.kind == NMODL_HH) {
+                            const double* st = st_d + st_off[t];
+                            const double m = st[j], h = st[cnt + j], nn = st[2 * cnt + j];
+                            const double gna = M.hh_g[0] * m * m * m * h;
+                            const double gk = M.hh_g[1] * nn * nn * nn * nn;
+                            const double ina = gna * (vv - M.hh_e[0]);
+                            const double ik = gk * (vv - M.hh_e[1]);
+                            s_na += ina;
+                            s_k += ik;
+                            ci = ina + ik + M.hh_g[2] * (vv - M.hh_e[2]);
+                            gi = gna + gk + M.hh_g[2];
+                        } else {
+                            cur_cnexp_d(M, st_d + st_off[t], cnt, j, vv, ci, gi);
+                        }
                     } else {
                         const float2* st = st_f + st_off[t];
                         const float vf = vf_s[n];
@@ -407,8 +432,13 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                             const float gna = (float)M.hh_g[0] * m * m * m * h;
                             const float gk = (float)M.hh_g[1] * nn * nn * nn * nn;
                             const float gl = (float)M.hh_g[2];
-                            cf = gna * (vf - (float)M.hh_e[0]) + gk * (vf - (float)M.hh_e[1]) +
-                                 gl * (vf - (float)M.hh_e[2]);
+                            const float inaf = gna * (vf - (float)M.hh_e[0]);
+                            const float ikf = gk * (vf - (float)M.hh_e[1]);
+                            if (EXT && A.ions) {
+                                s_na += f2d_int(inaf);
+                                s_k += f2d_int(ikf);
+                            }
+                            cf = inaf + ikf + gl * (vf - (float)M.hh_e[2]);
                             gf = gna + gk + gl;
                         } else {
                             gf = (float)M.gbar;
@@ -421,8 +451,21 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                         ci = f2d_int(cf);
                         gi = f2d_int(gf);
                     }
+                    if (EXT && M.ion) {  // tagged whole current
+                        if (M.ion == NMODL_ION_NA) s_na += ci;
+                        else if (M.ion == NMODL_ION_K) s_k += ci;
+                        else s_ca += ci;
+                    }
                     r -= ci;
                     dd += gi;
+                }
+            }
+            if (EXT && A.ions) {
+                ica_s[n] = s_ca;
+                if (last) {
+                    if (A.ion[NMODL_ION_NA]) A.ion[NMODL_ION_NA][n0 + n] = s_na;
+                    if (A.ion[NMODL_ION_K]) A.ion[NMODL_ION_K][n0 + n] = s_k;
+                    if (A.ion[NMODL_ION_CA]) A.ion[NMODL_ION_CA][n0 + n] = s_ca;
                 }
             }
             dd += cmdt;
@@ -517,6 +560,35 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             while (k >= pair_start[q + 1]) ++q;
             const int t = pair_t[q], g = pair_g[q];
             const int j = k - pair_start[q];
+            const int kind = EXT ? md_s[t].kind : NMODL_CNEXP;
+            if (EXT && (kind == NMODL_KIN3 || kind == NMODL_CACUM)) {
+                // coupled states: the item of the first state updates all
+                if (g != 0) continue;
+                const int cnt = cnt_s[t], nd = nid_s[nid_off[t] + j];
+                double x[3];
+                const int ns = kind == NMODL_KIN3 ? 3 : 2;
+                for (int a = 0; a < ns; ++a) {
+                    const int o = st_off[t] + a * cnt + j;
+                    x[a] = PREC == NMODL_FP64 ? st_d[o] : f2d_int(st_f[o].x) + f2d_int(st_f[o].y);
+                }
+                if (kind == NMODL_KIN3) {
+                    kin3_step_d(md_s[t].k3, v_s[nd], A.dt, x);
+                } else {
+                    bool conv;
+                    cacum_newton_d(md_s[t].cd, ica_s[nd], A.dt, A.newton_tol, A.newton_max_iter,
+                                   x[0], x[1], conv);
+                }
+                for (int a = 0; a < ns; ++a) {
+                    const int o = st_off[t] + a * cnt + j;
+                    if (PREC == NMODL_FP64) {
+                        st_d[o] = x[a];
+                    } else {
+                        const float hi = d2f_int(x[a]);
+                        st_f[o] = make_float2(hi, d2f_int(x[a] - f2d_int(hi)));
+                    }
+                }
+                continue;
+            }
             if (PREC == NMODL_FP64) {
                 const double vv = v_s[nid_s[nid_off[t] + j]];
                 const GateD& G = md_s[t].gate[g];
@@ -614,42 +686,40 @@ void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
 
 // grid = blocks of this launch (one per tile, or the resident count in the
 // persistent form)
-cudaError_t launch_fused(int prec, const FusedArgs& a, int grid, int block, size_t smem,
+// variant = precision + 2 * ext: ext instantiates the kernel with the small
+// systems and ion sums (EXT); plain HH/CNEXP plans use the leaner variant
+using FusedKernel = void (*)(FusedArgs);
+static FusedKernel fused_kernel(int variant) {
+    switch (variant) {
+    case 0: return k_fused_tiles<NMODL_FP64, false>;
+    case 1: return k_fused_tiles<NMODL_MIXED, false>;
+    case 2: return k_fused_tiles<NMODL_FP64, true>;
+    default: return k_fused_tiles<NMODL_MIXED, true>;
+    }
+}
+
+cudaError_t launch_fused(int variant, const FusedArgs& a, int grid, int block, size_t smem,
                          cudaStream_t s) {
-    if (grid <= 0 || a.n_tiles == 0) return cudaSuccess;
-    if (prec == NMODL_FP64)
-        k_fused_tiles<NMODL_FP64><<<grid, block, smem, s>>>(a);
-    else
-        k_fused_tiles<NMODL_MIXED><<<grid, block, smem, s>>>(a);
+    fused_kernel(variant)<<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-// Blocks of the persistent form: as many as can be resident at once.
-int fused_resident_grid(int prec, int n_tiles, int block, size_t smem) {
+int fused_resident_grid(int variant, int n_tiles, int block, size_t smem) {
     int dev = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (prec == NMODL_FP64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tiles<NMODL_FP64>, block, smem);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tiles<NMODL_MIXED>, block, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel(variant), block, smem);
     return std::min(n_tiles, std::max(1, per_sm) * sms);
 }
 
-// Raise the kernel's dynamic shared-memory limit to max_smem (set once, at
-// planning time, outside any stream capture).
-cudaError_t fused_prepare(int prec, size_t max_smem) {
-    if (prec == NMODL_FP64)
-        return cudaFuncSetAttribute(k_fused_tiles<NMODL_FP64>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-    return cudaFuncSetAttribute(k_fused_tiles<NMODL_MIXED>,
+cudaError_t fused_prepare(int variant, size_t max_smem) {
+    return cudaFuncSetAttribute(fused_kernel(variant),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
 }
 
-size_t fused_static_smem(int prec) {
+size_t fused_static_smem(int variant) {
     cudaFuncAttributes fa{};
-    if (prec == NMODL_FP64) cudaFuncGetAttributes(&fa, k_fused_tiles<NMODL_FP64>);
-    else cudaFuncGetAttributes(&fa, k_fused_tiles<NMODL_MIXED>);
+    cudaFuncGetAttributes(&fa, fused_kernel(variant));
     return fa.sharedSizeBytes;
 }
 

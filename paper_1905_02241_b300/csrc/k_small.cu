@@ -17,61 +17,13 @@
 //               the current updates of the same step.
 //
 // One thread per instance; states are SoA rows of `stride` doubles.  The
-// calcium buffer has no transcendental function and is memory bound, so
-// both precisions run it in FP64.
+// calcium buffer has no transcendental function and little work per byte
+// even in FP64, so both precisions run it in FP64.  The per-instance math
+// lives in small_systems.cuh (shared with the fused tile kernel).
 #include "kernels.cuh"
+#include "small_systems.cuh"
 
 namespace nmodl {
-
-namespace {
-
-// rates of the three edges at v: kf[e] (lo -> hi) and kb[e] (hi -> lo)
-__device__ __forceinline__ void kin3_rates_d(const Kin3D& K, double v, double (&kf)[3],
-                                             double (&kb)[3]) {
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        kf[e] = K.af[e] * exp_tang(K.bf[e] * v);
-        kb[e] = K.ab[e] * exp_tang(-K.bb[e] * v);
-    }
-}
-
-// Row-major M = I - dt A from the edge rates: off-diagonals -dt k, the
-// diagonal 1 + dt (outflow of the state).
-template <typename R>
-__device__ __forceinline__ void kin3_matrix(const R (&kf)[3], const R (&kb)[3], R dt,
-                                            R (&M)[3][3]) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) M[a][b] = (a == b) ? R(1) : R(0);
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        const int lo = kin3_lo(e), hi = kin3_hi(e);
-        M[hi][lo] = -dt * kf[e];
-        M[lo][hi] = -dt * kb[e];
-        M[lo][lo] += dt * kf[e];
-        M[hi][hi] += dt * kb[e];
-    }
-}
-
-// Gaussian elimination of the 3x3 system, written out: M y = b.
-template <typename R>
-__device__ __forceinline__ void solve3(const R (&M)[3][3], R (&b)[3]) {
-    const R r0 = R(1) / M[0][0];
-    const R l10 = M[1][0] * r0, l20 = M[2][0] * r0;
-    const R u11 = M[1][1] - l10 * M[0][1], u12 = M[1][2] - l10 * M[0][2];
-    const R s21 = M[2][1] - l20 * M[0][1], s22 = M[2][2] - l20 * M[0][2];
-    const R r1 = R(1) / u11;
-    const R l21 = s21 * r1;
-    const R u22 = s22 - l21 * u12;
-    const R z1 = b[1] - l10 * b[0];
-    const R z2 = b[2] - l20 * b[0] - l21 * z1;
-    b[2] = z2 / u22;
-    b[1] = (z1 - u12 * b[2]) * r1;
-    b[0] = (b[0] - M[0][1] * b[1] - M[0][2] * b[2]) * r0;
-}
-
-}  // namespace
 
 // ------------------------------------------------------------- KIN3
 
@@ -194,11 +146,8 @@ __global__ void k_cacum_init(const CacumD* __restrict__ cd, int64_t n, double* s
     st[stride + i] = C.kf * C.cai0 * C.btot / (C.kf * C.cai0 + C.kb);
 }
 
-// Newton on F(y) = y - x - dt f(y) with J = I - dt df/dy:
-//   J = [[1 + dt (kf (btot - y1) + 1/tau), -dt (kf y0 + kb)],
-//        [-dt kf (btot - y1),               1 + dt (kf y0 + kb)]]
-// delta = J^-1 (-F) by the adjugate over the determinant; stop when both
-// |delta| <= tol or after max_iter updates.
+// Newton with the closed-form 2x2 inverse (cacum_newton_d), reading the
+// node's ica.
 __global__ void __launch_bounds__(256)
     k_cacum_state(const CacumD* __restrict__ cd, int64_t n, const int32_t* __restrict__ ni,
                   const double* __restrict__ ica, double* st, int64_t stride, double dt,
@@ -208,31 +157,9 @@ __global__ void __launch_bounds__(256)
     int it_max = 0;
     if (i < n) {
         const CacumD C = *cd;
-        const double x0 = st[i], x1 = st[stride + i];
-        const double src = C.rtau * C.cai0 - C.k * ica[ni[i]];  // constant part of f0
-        double y0 = x0, y1 = x1;
-        int it = 0;
+        double y0 = st[i], y1 = st[stride + i];
         bool conv = false;
-        while (it < max_iter) {
-            const double fr = C.btot - y1;
-            const double on = C.kf * fr, off = fma(C.kf, y0, C.kb);
-            const double bind = fma(on, y0, -C.kb * y1);
-            const double f0 = src - bind - C.rtau * y0;
-            const double r0 = fma(dt, f0, x0 - y0);
-            const double r1 = fma(dt, bind, x1 - y1);
-            const double a = fma(dt, on + C.rtau, 1.0), b = -dt * off;
-            const double c = -dt * on, d = fma(dt, off, 1.0);
-            const double rdet = 1.0 / fma(a, d, -b * c);
-            const double d0 = fma(d, r0, -b * r1) * rdet;
-            const double d1 = fma(a, r1, -c * r0) * rdet;
-            y0 += d0;
-            y1 += d1;
-            ++it;
-            if (fabs(d0) <= tol && fabs(d1) <= tol) {
-                conv = true;
-                break;
-            }
-        }
+        const int it = cacum_newton_d(C, ica[ni[i]], dt, tol, max_iter, y0, y1, conv);
         if (!isfinite(y0) || !isfinite(y1)) latch_error(err, NMODL_ERR_NONFINITE);
         st[i] = y0;
         st[stride + i] = y1;

@@ -36,6 +36,13 @@ struct FusedArgs {
     const double* gb;
     const uint16_t* sched;
     int32_t cable;
+    // ion currents (USEION): ion[1..3] = ina, ik, ica per node (null: not
+    // recorded); with ions set, the step's ica is kept per node for the
+    // state updates that read it (calcium buffer)
+    double* ion[4];
+    int32_t ions;
+    int32_t newton_max_iter;
+    double newton_tol;
 };
 
 void launch_init_gates(const MechD* md, int n_gates, int64_t n, const int32_t* ni,
@@ -52,11 +59,13 @@ void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
                     const int32_t* chunk, const int32_t* ni, const double* v,
                     const double* st, int64_t stride, double* rhs, double* d,
                     double* ion_a, double* ion_b, int32_t* err, cudaStream_t s);
-cudaError_t launch_fused(int prec, const FusedArgs& a, int grid, int block,
+// variant = precision + 2 * ext (ext: the kernel instantiated with the small
+// systems KIN3 / CACUM and the ion sums)
+cudaError_t launch_fused(int variant, const FusedArgs& a, int grid, int block,
                          size_t smem, cudaStream_t s);
-int fused_resident_grid(int prec, int n_tiles, int block, size_t smem);
-size_t fused_static_smem(int prec);
-cudaError_t fused_prepare(int prec, size_t max_smem);
+int fused_resident_grid(int variant, int n_tiles, int block, size_t smem);
+size_t fused_static_smem(int variant);
+cudaError_t fused_prepare(int variant, size_t max_smem);
 
 // kinetic scheme
 struct KinCounters {

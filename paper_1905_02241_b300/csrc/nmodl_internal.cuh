@@ -29,15 +29,33 @@ struct GateD {
     int32_t aform, bform, power, pad;
 };
 
-// Device descriptor of one HH / CNEXP mechanism (staged in shared memory).
+// 3-state scheme: edge e in {0: (0,1), 1: (1,2), 2: (0,2)}
+struct Kin3D {
+    double gbar, e;
+    int32_t open, pad;
+    double af[3], bf[3], ab[3], bb[3];
+};
+__host__ __device__ constexpr int kin3_lo(int e) { return e == 1 ? 1 : 0; }
+__host__ __device__ constexpr int kin3_hi(int e) { return e == 0 ? 1 : 2; }
+
+// calcium buffer: k, 1/tau, cai0, kf, kb, btot
+struct CacumD {
+    double k, rtau, cai0, kf, kb, btot;
+};
+
+// Device descriptor of one mechanism of the fused step (staged in shared
+// memory): HH, CNEXP, and the small systems KIN3 and CACUM.
 struct MechD {
-    int32_t kind;     // NMODL_HH or NMODL_CNEXP
-    int32_t n_gates;  // 3 for HH
+    int32_t kind;     // NMODL_HH, NMODL_CNEXP, NMODL_KIN3 or NMODL_CACUM
+    int32_t n_gates;  // states per instance (3 for HH)
     double phi;       // temperature factor
     double gbar, e;   // CNEXP single current
     double hh_g[3];   // HH gnabar, gkbar, gl
     double hh_e[3];   // HH ena, ek, el
     GateD gate[kMaxGates];
+    int32_t ion, pad; // USEION WRITE tag of the whole current
+    Kin3D k3;         // NMODL_KIN3
+    CacumD cd;        // NMODL_CACUM
 };
 
 // Edge e of the 3x3 kinetic lattice joins state lo(e) and hi(e): edges
@@ -53,20 +71,6 @@ struct Kin9D {
     double gbar, e;
     int32_t open, pad;
     double af[kKinEdges], bf[kKinEdges], ab[kKinEdges], bb[kKinEdges];
-};
-
-// 3-state scheme: edge e in {0: (0,1), 1: (1,2), 2: (0,2)}
-struct Kin3D {
-    double gbar, e;
-    int32_t open, pad;
-    double af[3], bf[3], ab[3], bb[3];
-};
-__host__ __device__ constexpr int kin3_lo(int e) { return e == 1 ? 1 : 0; }
-__host__ __device__ constexpr int kin3_hi(int e) { return e == 0 ? 1 : 2; }
-
-// calcium buffer: k, 1/tau, cai0, kf, kb, btot
-struct CacumD {
-    double k, rtau, cai0, kf, kb, btot;
 };
 
 // ------------------------------------------------------------ FP64 math

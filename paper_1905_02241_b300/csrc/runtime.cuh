@@ -46,6 +46,7 @@ struct Plan {
     std::vector<nmodl_mech*> mechs;
     nmodl_cable* cable = nullptr;   // cable form: tiles of whole cells
     int precision = 0;
+    int variant = 0;                // fused kernel: precision + 2 * (small systems / ions)
     int64_t n_nodes = 0;
     bool fused = false;
     // fused form

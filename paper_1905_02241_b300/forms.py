@@ -141,13 +141,14 @@ def cable(dev, n_cells=10000, nsteps=200):
     out["plan_cable"] = ctx.plan(mechs)
     ms = _time(lambda: cb.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["cable_fp64"] = ninst * nsteps / (ms * 1e-3)
-    # the per-step launch sequence (taken while ion arrays are registered)
-    ion = torch.zeros_like(v)
-    ctx.set_ions(ina=ion)
-    cb.step(mechs, DT, CM, v, rhs, d, 40)
-    ms = _time(lambda: cb.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
+    # the per-step launch sequence (taken when a 9-state mechanism is in the
+    # list: an empty one here)
+    k9 = Mechanism(ctx, W.TYPE_KIN9, np.zeros(0, np.int32), cab["n_nodes"],
+                   W.kin9_params(W.Stream(4, 401)))
+    cb.step(mechs + [k9], DT, CM, v, rhs, d, 40)
+    ms = _time(lambda: cb.step(mechs + [k9], DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["cable_per_step_launches_fp64"] = ninst * nsteps / (ms * 1e-3)
-    ctx.set_ions()
+    k9.close()
     ctx.step(mechs, DT, CM, v, rhs, d, 40)
     ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["isolated_fused_fp64"] = ninst * nsteps / (ms * 1e-3)
@@ -168,9 +169,11 @@ def _ion_mechs(ctx, wl):
 def ions(dev, n_nodes=2_000_000, nsteps=200):
     """USEION write-back and the small systems on the ion-tagged cortical mix
     (10 cnexp types writing ina/ik/ica, a 3-state potassium scheme on half
-    of the nodes, one calcium buffer per node reading ica):
+    of the nodes, one calcium buffer per node reading ica), all in the fused
+    tile kernel:
 
       network_fp64 / network_mixed   whole steps with ion arrays registered
+      network_per_mechanism_fp64     the same as per-mechanism launches
       no_buffer_ions_fp64            the same without the buffer
       no_buffer_no_ions_fp64         ... and without ion arrays: the cost of
                                      the ion write-back is the ratio
@@ -210,6 +213,24 @@ def ions(dev, n_nodes=2_000_000, nsteps=200):
         for m in mechs:
             m.close()
         ctx.close()
+    # the per-mechanism launch sequence (an empty 9-state mechanism in the list)
+    ctx = Context(dev)
+    arrs = [torch.zeros_like(v0) for _ in range(3)]
+    ctx.set_ions(*arrs)
+    mechs = _ion_mechs(ctx, wl) + [Mechanism(ctx, W.TYPE_KIN9, np.zeros(0, np.int32), n_nodes,
+                                             W.kin9_params(W.Stream(4, 401)))]
+    v = v0.clone()
+    rhs = torch.zeros_like(v)
+    d = torch.zeros_like(v)
+    for m in mechs:
+        m.init(v)
+    ctx.step(mechs, DT, CM, v, rhs, d, 40)
+    ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
+    out["network_per_mechanism_fp64"] = _ninst(wl) * nsteps / (ms * 1e-3)
+    for m in mechs:
+        m.close()
+    ctx.close()
+    out["fused_over_per_mechanism"] = out["network_fp64"] / out["network_per_mechanism_fp64"]
     out["ion_writeback_cost"] = out["no_buffer_no_ions_fp64"] / out["no_buffer_ions_fp64"]
     out["mixed_over_fp64"] = out["network_mixed"] / out["network_fp64"]
     # kernels alone, 8M instances, one per node

@@ -246,7 +246,57 @@ def test_network_one_step_parity(api, orc):
             assert err <= 1e-10, err
         else:
             assert state_err(got, s) <= 1e-11, (m.type, state_err(got, s))
-    assert ctx.plan(ms)["fused"] == 0
+    assert ctx.plan(ms)["fused"] == 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_network_fused_and_per_mechanism_paths_agree(api, orc, prec):
+    """The ion-tagged network with the 3-state scheme and the buffer in the
+    fused tile kernel (several tiles) against the per-mechanism launch
+    sequence (forced by an empty 9-state mechanism in the list): v, rhs, d,
+    the ion arrays and every state after 12 steps."""
+    net = W.cortical_ions(3000, seed=22)
+    n = net["n_nodes"]
+    P = api.NMODL_FP64 if prec == "fp64" else api.NMODL_MIXED
+    res = {}
+    for form in ("fused", "per_mechanism"):
+        ctx = api.Context(0, precision=P, tile_smem=24 * 1024, window=5)
+        ions = [torch.zeros(n, dtype=torch.float64, device="cuda:0") for _ in range(3)]
+        ctx.set_ions(*ions)
+        ms = [mech(api, ctx, m, n) for m in net["mechs"]]
+        if form == "per_mechanism":
+            ms.append(api.Mechanism(ctx, api.NMODL_KIN9, np.zeros(0, np.int32), n,
+                                    W.kin9_params(W.Stream(4, 401))))
+        v = to_dev(net["v0"])
+        for m in ms:
+            m.init(v)
+        rhs = torch.zeros(n, dtype=torch.float64, device="cuda:0")
+        d = torch.zeros_like(rhs)
+        ctx.step(ms, 0.025, 1.0, v, rhs, d, 12)
+        assert ctx.sync() == 0
+        plan = ctx.plan(ms)
+        assert plan["fused"] == (form == "fused")
+        if form == "fused":
+            assert plan["tiles"] > 1
+        res[form] = (v.cpu().numpy(), rhs.cpu().numpy(), d.cpu().numpy(),
+                     [x.cpu().numpy() for x in ions],
+                     [m.states().cpu().numpy() for m in ms[:len(net["mechs"])]])
+    (vf, rf, df, iof, sf), (vg, rg, dg, iog, sg) = res["fused"], res["per_mechanism"]
+    if prec == "fp64":
+        assert np.max(np.abs(vf - vg) / np.maximum(np.abs(vg), 1.0)) <= 1e-10
+        assert np.max(np.abs(df - dg) / dg) <= 1e-11
+        for a, b in zip(iof, iog):
+            assert np.max(np.abs(a - b)) <= 1e-10 * max(1.0, np.abs(b).max())
+        for a, b in zip(sf, sg):
+            if a.size:
+                assert np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-3)) <= 1e-9
+    else:
+        assert np.max(np.abs(vf - vg)) <= 1e-3
+        for a, b in zip(sf, sg):
+            if a.size:
+                assert np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-3)) <= 1e-4
+    cai = sf[-1][0]
+    assert np.all(np.isfinite(cai)) and cai.min() >= 0
 
 
 def test_network_trajectory_and_determinism(api, orc):
@@ -267,7 +317,9 @@ def test_network_trajectory_and_determinism(api, orc):
     assert np.all(np.isfinite(cai)) and cai.min() >= 0
 
 
-def test_unregistering_restores_the_fused_plan(api):
+def test_plan_forms(api):
+    """Ion arrays keep the fused plan; a 9-state mechanism in the list does
+    not fuse; unregistering the arrays keeps the fused plan."""
     net = W.cortical_mix(2000, seed=19)
     n = net["n_nodes"]
     ctx = api.Context(0)
@@ -278,7 +330,11 @@ def test_unregistering_restores_the_fused_plan(api):
     ina = torch.zeros_like(rhs)
     ctx.set_ions(ina=ina)
     ctx.step(ms, 0.025, 1.0, v, rhs, d, 3)
-    assert ctx.plan(ms)["fused"] == 0
+    assert ctx.plan(ms)["fused"] == 1
+    k9 = api.Mechanism(ctx, api.NMODL_KIN9, np.zeros(0, np.int32), n,
+                       W.kin9_params(W.Stream(4, 401)))
+    ctx.step(ms + [k9], 0.025, 1.0, v, rhs, d, 3)
+    assert ctx.plan(ms + [k9])["fused"] == 0
     ctx.set_ions()
     ctx.step(ms, 0.025, 1.0, v, rhs, d, 3)
     assert ctx.plan(ms)["fused"] == 1

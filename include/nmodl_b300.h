@@ -262,7 +262,8 @@ NMODL_API int nmodl_cable_n_cells(const nmodl_cable *cable);
  * d reported) but not solved, and v is held.  When the mechanisms fuse (as
  * for nmodl_step), the steps run in the fused tile kernel with tiles of
  * whole cells, each cell's tree system solved in shared memory between the
- * current and state phases; otherwise as per-step launch sequences.  Windows of options.window steps are
+ * current and state phases (by one warp, in levels of the tree); otherwise
+ * as per-step launch sequences.  Windows of options.window steps are
  * replayed from CUDA graphs. */
 NMODL_API int nmodl_step_cable(nmodl_ctx *ctx, nmodl_cable *cable,
                                nmodl_mech *const *mechs, int n_mechs, double dt,

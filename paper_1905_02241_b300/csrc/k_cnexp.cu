@@ -1,15 +1,20 @@
-// k_cnexp.cu -- cnexp-family kernels (HH and generic gates) for sm_103a.
+// k_cnexp.cu -- cnexp-family kernels (HH and generic gates) and the fused
+// step for sm_103a.
 //
 //  k_init_gates      INITIAL: gate := minf(v[node])
 //  k_state_gates     nrn_state, one thread per (instance, gate): the cnexp
 //                    exact exponential update (Section 5.2)
 //  k_cur_seg         nrn_cur with the analytic conductance (Section 5.2,
 //                    CONDUCTANCE) and a node_index-sorted segmented
-//                    warp-shuffle reduction into rhs/d (no atomics)
+//                    warp-shuffle reduction into rhs/d and the ion arrays
+//                    (no atomics); HH, CNEXP, KIN9 and KIN3 currents
 //  k_fused_tiles     nsteps whole network steps (cur -> v -> state) per node
 //                    tile, with the tile's states resident in shared memory
-//                    for the whole window (the compartments are isolated, so
-//                    tiles never exchange data)
+//                    for the whole window (isolated compartments: tiles never
+//                    exchange data; cable form: tiles of whole cells with the
+//                    tree solve inside); HH, CNEXP and, in the EXT
+//                    instantiation, the 3-state scheme, the calcium buffer
+//                    and ion sums
 #include <algorithm>
 #include <climits>
 

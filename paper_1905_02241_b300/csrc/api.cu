@@ -488,8 +488,8 @@ int nmodl_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
 // -------------------------------------------------------------- planning
 
 // Shared memory of one tile, matching the layout in k_fused_tiles.
-static size_t tile_smem_bytes(int prec, int T, const int* gates, int64_t NT, const int64_t* cnt,
-                              bool cable, bool ions) {
+static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* terms, int64_t NT,
+                              const int64_t* cnt, bool cable, bool ions) {
     size_t b = 8 * (size_t)NT;
     size_t inst = 0, items = 0;
     for (int t = 0; t < T; ++t) {
@@ -501,6 +501,11 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, int64_t NT, con
     if (ions) b = (b + 15) / 16 * 16 + 8 * (size_t)NT;  // the step's ica per node
     // d, rhs, ga, gb, parent, and the level schedule (at most 6 NT + 5 uint16)
     if (cable) b = (b + 15) / 16 * 16 + 34 * (size_t)NT + 2 * (6 * (size_t)NT + 5);
+    if (prec == NMODL_FP64) {  // conductance terms of the step
+        size_t g = 0;
+        for (int t = 0; t < T; ++t) g += (size_t)terms[t] * cnt[t];
+        b = (b + 15) / 16 * 16 + 8 * g;
+    }
     return (b + 15) / 16 * 16;
 }
 
@@ -509,7 +514,8 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, int64_t NT, con
 // tile's shared memory stays within budget; returns false if one fine block
 // does not fit.
 static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, int T,
-                       const int* gates, const std::vector<int64_t>& bounds, bool cable,
+                       const int* gates, const int* terms, const std::vector<int64_t>& bounds,
+                       bool cable,
                        bool ions, size_t budget, std::vector<int32_t>& recs, size_t& max_smem) {
     recs.clear();
     max_smem = 0;
@@ -525,7 +531,7 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
                 cnt[t] = off[t][b] - off[t][a];
                 if (cnt[t] > 65535) return false;
             }
-            return tile_smem_bytes(prec, T, gates, NT, cnt.data(), cable, ions) <= budget;
+            return tile_smem_bytes(prec, T, gates, terms, NT, cnt.data(), cable, ions) <= budget;
         };
         if (!fits(k0, k1)) return false;
         while (k1 < K && fits(k0, k1 + 1)) ++k1;
@@ -538,7 +544,7 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
             cnt[t] = off[t][k1] - off[t][k0];
         }
         max_smem = std::max(max_smem,
-                            tile_smem_bytes(prec, T, gates, n1 - n0, cnt.data(), cable, ions));
+                            tile_smem_bytes(prec, T, gates, terms, n1 - n0, cnt.data(), cable, ions));
         k0 = k1;
     }
     return true;
@@ -705,8 +711,12 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     std::vector<std::vector<int32_t>> off(T);
     for (int t = 0; t < T; ++t)
         off[t].assign(hoff.begin() + t * (K + 1), hoff.begin() + (t + 1) * (K + 1));
-    int gates[kMaxMechsFused];
-    for (int t = 0; t < T; ++t) gates[t] = mechs[t]->n_states;
+    int gates[kMaxMechsFused], terms[kMaxMechsFused];
+    for (int t = 0; t < T; ++t) {
+        gates[t] = mechs[t]->n_states;
+        // conductance terms per instance in the fused kernel's FP64 scratch
+        terms[t] = mechs[t]->type == NMODL_HH ? 2 : mechs[t]->type == NMODL_CACUM ? 0 : 1;
+    }
 
     int dev_smem_optin = 0;
     cudaDeviceGetAttribute(&dev_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
@@ -739,8 +749,8 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
         auto sched_p = std::make_shared<std::vector<uint16_t>>();
         std::vector<uint16_t>& sched = *sched_p;
         size_t max_smem = 0;
-        if (b > cap || !make_tiles(p->precision, off, T, gates, bounds, cb != nullptr, ions, b,
-                                   recs, max_smem)) {
+        if (b > cap || !make_tiles(p->precision, off, T, gates, terms, bounds, cb != nullptr, ions,
+                                   b, recs, max_smem)) {
             if (dbg) std::fprintf(stderr, "[nmodl plan] budget %zu: no tiling\n", b);
             continue;
         }

@@ -234,6 +234,8 @@ __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
 //   double  d2_s[NT], r2_s[NT], ga_s[NT], gb_s[NT]   (cable), 16-aligned
 //   uint16  par_s[NT]                     (cable) local parent, 0xffff at roots
 //   uint16  sched_s[...]                  (cable) level schedule of the solve
+//   double  g_s[sum_t terms_t * cnt_t]    (FP64) conductance terms of the step,
+//                                         16-aligned after the above
 // Tile record (int32): n0, n1, then a_t, b_t per type (instance ranges).
 // The host plan guarantees NT <= 65535, cnt_t <= 65535 and that the layout
 // fits the dynamic shared memory of the launch.
@@ -262,6 +264,8 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     __shared__ float phidt_f[kMaxMechsFused];
 
     __shared__ int tile_s;
+    __shared__ int inst_start[kMaxMechsFused + 1];  // instance offset of each type
+    __shared__ int gt_off[kMaxMechsFused];          // conductance terms of each type
 
     const int tid = threadIdx.x;
     const int T = A.n_types;
@@ -302,6 +306,14 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         }
         pair_start[q] = so;
         n_pairs = q;
+        int go = 0;
+        for (int t = 0; t < T; ++t) {
+            inst_start[t] = nid_off[t];
+            gt_off[t] = go;
+            const int kind = md_s[t].kind;
+            go += (kind == NMODL_HH ? 2 : kind == NMODL_CACUM ? 0 : 1) * cnt_s[t];
+        }
+        inst_start[T] = no;
     }
     __syncthreads();
     if (PREC == NMODL_MIXED) {
@@ -338,6 +350,13 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     double* gb_s = ga_s + NT;
     uint16_t* par_s = reinterpret_cast<uint16_t*>(gb_s + NT);
     uint16_t* sched_s = par_s + NT;
+    // FP64: conductance terms of the step (HH: gna, gk; others: g)
+    double* g_s;
+    {
+        uintptr_t e = reinterpret_cast<uintptr_t>(d2_s);
+        if (A.cable) e = reinterpret_cast<uintptr_t>(sched_s + 6 * NT + 5);
+        g_s = reinterpret_cast<double*>((e + 15) & ~(uintptr_t)15);
+    }
     if (A.cable) {
         const int32_t off = rec[2 + 2 * T], len = rec[3 + 2 * T];
         for (int k = tid; k < len; k += blockDim.x) sched_s[k] = A.sched[off + k];
@@ -392,6 +411,31 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     const double cmdt = 1e-3 * A.cm / A.dt;
     for (int step = 0; step < A.nsteps; ++step) {
         const bool last = (step == A.nsteps - 1);
+        if (PREC == NMODL_FP64) {
+            // ---- conductances, one thread per instance (lane-efficient;
+            // the owner loop below then spends two operations per instance)
+            int q = 0;
+            for (int k = tid; k < inst_start[T]; k += blockDim.x) {
+                while (k >= inst_start[q + 1]) ++q;
+                const int j = k - inst_start[q];
+                const MechD& M = md_s[q];
+                const int cnt = cnt_s[q];
+                const double* st = st_d + st_off[q];
+                double* gp = g_s + gt_off[q];
+                if (M.kind == NMODL_HH) {
+                    const double m = st[j], h = st[cnt + j], nn = st[2 * cnt + j];
+                    gp[j] = M.hh_g[0] * m * m * m * h;
+                    gp[cnt + j] = M.hh_g[1] * nn * nn * nn * nn;
+                } else if (EXT && M.kind == NMODL_KIN3) {
+                    gp[j] = M.k3.gbar * st[M.k3.open * cnt + j];
+                } else if (!EXT || M.kind != NMODL_CACUM) {
+                    double gg = M.gbar;
+                    for (int g = 0; g < M.n_gates; ++g) gg *= ipow_d(st[g * cnt + j], M.gate[g].power);
+                    gp[j] = gg;
+                }
+            }
+            __syncthreads();
+        }
         // ---- current update and v update, one owner thread per node; the
         // terms are summed in mechanism order, then ascending instance.
         for (int n = tid; n < NT; n += blockDim.x) {
@@ -404,30 +448,47 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 const int j0 = seg[n], j1 = seg[n + 1];
                 const int cnt = cnt_s[t];
                 if (EXT && M.kind == NMODL_CACUM) continue;  // no membrane current
+                if (PREC == NMODL_FP64) {
+                    const double* gp = g_s + gt_off[t];
+                    if (M.kind == NMODL_HH) {
+                        const double gl = M.hh_g[2];
+                        for (int j = j0; j < j1; ++j) {
+                            const double gna = gp[j], gk = gp[cnt + j];
+                            const double ina = gna * (vv - M.hh_e[0]);
+                            const double ik = gk * (vv - M.hh_e[1]);
+                            if (EXT && A.ions) {
+                                s_na += ina;
+                                s_k += ik;
+                            }
+                            r -= ina + ik + gl * (vv - M.hh_e[2]);
+                            dd += gna + gk + gl;
+                        }
+                    } else {
+                        const double ve = vv - ((EXT && M.kind == NMODL_KIN3) ? M.k3.e : M.e);
+                        for (int j = j0; j < j1; ++j) {
+                            const double g = gp[j];
+                            if (EXT && M.ion) {  // tagged whole current
+                                const double ci = g * ve;
+                                if (M.ion == NMODL_ION_NA) s_na += ci;
+                                else if (M.ion == NMODL_ION_K) s_k += ci;
+                                else s_ca += ci;
+                                r -= ci;
+                            } else {
+                                r = fma(-g, ve, r);
+                            }
+                            dd += g;
+                        }
+                    }
+                    continue;
+                }
+                // MIXED: FP32 currents from the hi parts of the states
                 for (int j = j0; j < j1; ++j) {
                     double ci, gi;
                     if (EXT && M.kind == NMODL_KIN3) {
                         const int o = M.k3.open * cnt + j;
-                        const double x = PREC == NMODL_FP64
-                                             ? st_d[st_off[t] + o]
-                                             : f2d_int(st_f[st_off[t] + o].x) + f2d_int(st_f[st_off[t] + o].y);
+                        const double x = f2d_int(st_f[st_off[t] + o].x) + f2d_int(st_f[st_off[t] + o].y);
                         gi = M.k3.gbar * x;
                         ci = gi * (vv - M.k3.e);
-                    } else if (PREC == NMODL_FP64) {
-                        if (EXT && A.ions && M.kind == NMODL_HH) {
-                            const double* st = st_d + st_off[t];
-                            const double m = st[j], h = st[cnt + j], nn = st[2 * cnt + j];
-                            const double gna = M.hh_g[0] * m * m * m * h;
-                            const double gk = M.hh_g[1] * nn * nn * nn * nn;
-                            const double ina = gna * (vv - M.hh_e[0]);
-                            const double ik = gk * (vv - M.hh_e[1]);
-                            s_na += ina;
-                            s_k += ik;
-                            ci = ina + ik + M.hh_g[2] * (vv - M.hh_e[2]);
-                            gi = gna + gk + M.hh_g[2];
-                        } else {
-                            cur_cnexp_d(M, st_d + st_off[t], cnt, j, vv, ci, gi);
-                        }
                     } else {
                         const float2* st = st_f + st_off[t];
                         const float vf = vf_s[n];

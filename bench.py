@@ -283,7 +283,7 @@ def main():
         roof["frac"] = roof["achieved"] / roof["peak"]
     # DRAM bytes per launch from profiles/k_fused_tiles_fp64_cortical_1M.md
     # (1M-node capture of the current kernel, scaled by instances to 2M)
-    roof["traffic"] = (312.5e6 * ninst / 11548985 if prec == NMODL_FP64 and window == 40
+    roof["traffic"] = (313.3e6 * ninst / 11548985 if prec == NMODL_FP64 and window == 40
                        else None)
     roof["traffic_unit"] = "bytes per launch"
     roof["kernel"] = "k_fused_tiles<FP64>" if prec == NMODL_FP64 else "k_fused_tiles<MIXED>"

@@ -262,6 +262,10 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     __shared__ int pair_start[kMaxMechsFused * kMaxGates + 1];
     __shared__ int n_pairs;
     __shared__ float phidt_f[kMaxMechsFused];
+    // MIXED: FP32 copies of the current parameters (gbar, e, HH g[3], e[3]),
+    // converted once rather than per instance (FP64 -> FP32 conversions run
+    // on the FP64 pipe)
+    __shared__ float curf_s[kMaxMechsFused][8];
 
     __shared__ int tile_s;
     __shared__ int inst_start[kMaxMechsFused + 1];  // instance offset of each type
@@ -317,7 +321,16 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     }
     __syncthreads();
     if (PREC == NMODL_MIXED) {
-        for (int k = tid; k < T; k += blockDim.x) phidt_f[k] = (float)(md_s[k].phi * A.dt);
+        for (int k = tid; k < T; k += blockDim.x) {
+            const MechD& M = md_s[k];
+            phidt_f[k] = (float)(M.phi * A.dt);
+            curf_s[k][0] = (float)M.gbar;
+            curf_s[k][1] = (float)M.e;
+            for (int q = 0; q < 3; ++q) {
+                curf_s[k][2 + q] = (float)M.hh_g[q];
+                curf_s[k][5 + q] = (float)M.hh_e[q];
+            }
+        }
         for (int k = tid; k < T * kMaxGates; k += blockDim.x) {
             const GateD& G = md_s[k / kMaxGates].gate[k % kMaxGates];
             gf_s[k / kMaxGates][k % kMaxGates] =
@@ -493,26 +506,27 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                         const float2* st = st_f + st_off[t];
                         const float vf = vf_s[n];
                         float gf, cf;
+                        const float* cf_p = curf_s[t];
                         if (M.kind == NMODL_HH) {
                             const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
-                            const float gna = (float)M.hh_g[0] * m * m * m * h;
-                            const float gk = (float)M.hh_g[1] * nn * nn * nn * nn;
-                            const float gl = (float)M.hh_g[2];
-                            const float inaf = gna * (vf - (float)M.hh_e[0]);
-                            const float ikf = gk * (vf - (float)M.hh_e[1]);
+                            const float gna = cf_p[2] * m * m * m * h;
+                            const float gk = cf_p[3] * nn * nn * nn * nn;
+                            const float gl = cf_p[4];
+                            const float inaf = gna * (vf - cf_p[5]);
+                            const float ikf = gk * (vf - cf_p[6]);
                             if (EXT && A.ions) {
                                 s_na += f2d_int(inaf);
                                 s_k += f2d_int(ikf);
                             }
-                            cf = inaf + ikf + gl * (vf - (float)M.hh_e[2]);
+                            cf = inaf + ikf + gl * (vf - cf_p[7]);
                             gf = gna + gk + gl;
                         } else {
-                            gf = (float)M.gbar;
+                            gf = cf_p[0];
                             for (int q = 0; q < M.n_gates; ++q) {
                                 const float x = st[q * cnt + j].x;
                                 for (int p = 0; p < M.gate[q].power; ++p) gf *= x;
                             }
-                            cf = gf * (vf - (float)M.e);
+                            cf = gf * (vf - cf_p[1]);
                         }
                         ci = f2d_int(cf);
                         gi = f2d_int(gf);

@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                     continue;
                 }
                 // MIXED: FP32 currents from the hi parts of the states
-                for (int j = j0; j < j1; ++j) {
+                for (int j = j0; PREC == NMODL_MIXED && j < j1; ++j) {
                     double ci, gi;
                     if (EXT && M.kind == NMODL_KIN3) {
                         const int o = M.k3.open * cnt + j;

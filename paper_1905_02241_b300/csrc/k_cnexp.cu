@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 const int j0 = seg[n], j1 = seg[n + 1];
                 const int cnt = cnt_s[t];
                 if (EXT && M.kind == NMODL_CACUM) continue;  // no membrane current
-                if (PREC == NMODL_FP64) {
+                if constexpr (PREC == NMODL_FP64) {
                     const double* gp = g_s + gt_off[t];
                     if (M.kind == NMODL_HH) {
                         const double gl = M.hh_g[2];
@@ -492,10 +492,9 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                             dd += g;
                         }
                     }
-                    continue;
-                }
+                } else {
                 // MIXED: FP32 currents from the hi parts of the states
-                for (int j = j0; PREC == NMODL_MIXED && j < j1; ++j) {
+                for (int j = j0; j < j1; ++j) {
                     double ci, gi;
                     if (EXT && M.kind == NMODL_KIN3) {
                         const int o = M.k3.open * cnt + j;
@@ -538,6 +537,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                     }
                     r -= ci;
                     dd += gi;
+                }
                 }
             }
             if (EXT && A.ions) {

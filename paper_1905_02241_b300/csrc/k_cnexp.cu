@@ -493,51 +493,51 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                         }
                     }
                 } else {
-                // MIXED: FP32 currents from the hi parts of the states
-                for (int j = j0; j < j1; ++j) {
-                    double ci, gi;
-                    if (EXT && M.kind == NMODL_KIN3) {
-                        const int o = M.k3.open * cnt + j;
-                        const double x = f2d_int(st_f[st_off[t] + o].x) + f2d_int(st_f[st_off[t] + o].y);
-                        gi = M.k3.gbar * x;
-                        ci = gi * (vv - M.k3.e);
-                    } else {
-                        const float2* st = st_f + st_off[t];
-                        const float vf = vf_s[n];
-                        float gf, cf;
-                        const float* cf_p = curf_s[t];
-                        if (M.kind == NMODL_HH) {
-                            const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
-                            const float gna = cf_p[2] * m * m * m * h;
-                            const float gk = cf_p[3] * nn * nn * nn * nn;
-                            const float gl = cf_p[4];
-                            const float inaf = gna * (vf - cf_p[5]);
-                            const float ikf = gk * (vf - cf_p[6]);
-                            if (EXT && A.ions) {
-                                s_na += f2d_int(inaf);
-                                s_k += f2d_int(ikf);
-                            }
-                            cf = inaf + ikf + gl * (vf - cf_p[7]);
-                            gf = gna + gk + gl;
+                    // MIXED: FP32 currents from the hi parts of the states
+                    for (int j = j0; j < j1; ++j) {
+                        double ci, gi;
+                        if (EXT && M.kind == NMODL_KIN3) {
+                            const int o = M.k3.open * cnt + j;
+                            const double x = f2d_int(st_f[st_off[t] + o].x) + f2d_int(st_f[st_off[t] + o].y);
+                            gi = M.k3.gbar * x;
+                            ci = gi * (vv - M.k3.e);
                         } else {
-                            gf = cf_p[0];
-                            for (int q = 0; q < M.n_gates; ++q) {
-                                const float x = st[q * cnt + j].x;
-                                for (int p = 0; p < M.gate[q].power; ++p) gf *= x;
+                            const float2* st = st_f + st_off[t];
+                            const float vf = vf_s[n];
+                            float gf, cf;
+                            const float* cf_p = curf_s[t];
+                            if (M.kind == NMODL_HH) {
+                                const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
+                                const float gna = cf_p[2] * m * m * m * h;
+                                const float gk = cf_p[3] * nn * nn * nn * nn;
+                                const float gl = cf_p[4];
+                                const float inaf = gna * (vf - cf_p[5]);
+                                const float ikf = gk * (vf - cf_p[6]);
+                                if (EXT && A.ions) {
+                                    s_na += f2d_int(inaf);
+                                    s_k += f2d_int(ikf);
+                                }
+                                cf = inaf + ikf + gl * (vf - cf_p[7]);
+                                gf = gna + gk + gl;
+                            } else {
+                                gf = cf_p[0];
+                                for (int q = 0; q < M.n_gates; ++q) {
+                                    const float x = st[q * cnt + j].x;
+                                    for (int p = 0; p < M.gate[q].power; ++p) gf *= x;
+                                }
+                                cf = gf * (vf - cf_p[1]);
                             }
-                            cf = gf * (vf - cf_p[1]);
+                            ci = f2d_int(cf);
+                            gi = f2d_int(gf);
                         }
-                        ci = f2d_int(cf);
-                        gi = f2d_int(gf);
+                        if (EXT && M.ion) {  // tagged whole current
+                            if (M.ion == NMODL_ION_NA) s_na += ci;
+                            else if (M.ion == NMODL_ION_K) s_k += ci;
+                            else s_ca += ci;
+                        }
+                        r -= ci;
+                        dd += gi;
                     }
-                    if (EXT && M.ion) {  // tagged whole current
-                        if (M.ion == NMODL_ION_NA) s_na += ci;
-                        else if (M.ion == NMODL_ION_K) s_k += ci;
-                        else s_ca += ci;
-                    }
-                    r -= ci;
-                    dd += gi;
-                }
                 }
             }
             if (EXT && A.ions) {

@@ -501,7 +501,7 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* term
     if (ions) b = (b + 15) / 16 * 16 + 8 * (size_t)NT;  // the step's ica per node
     // d, rhs, ga, gb, parent, and the level schedule (at most 6 NT + 5 uint16)
     if (cable) b = (b + 15) / 16 * 16 + 34 * (size_t)NT + 2 * (6 * (size_t)NT + 5);
-    if (prec == NMODL_FP64) {  // conductance terms of the step
+    {  // conductance terms of the step
         size_t g = 0;
         for (int t = 0; t < T; ++t) g += (size_t)terms[t] * cnt[t];
         b = (b + 15) / 16 * 16 + 8 * g;

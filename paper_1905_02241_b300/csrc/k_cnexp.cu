@@ -424,27 +424,48 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     const double cmdt = 1e-3 * A.cm / A.dt;
     for (int step = 0; step < A.nsteps; ++step) {
         const bool last = (step == A.nsteps - 1);
-        if (PREC == NMODL_FP64) {
+        {
             // ---- conductances, one thread per instance (lane-efficient;
-            // the owner loop below then spends two operations per instance)
+            // the owner loop below then spends two operations per instance).
+            // MIXED: from the FP32 hi parts of the states, converted once.
             int q = 0;
             for (int k = tid; k < inst_start[T]; k += blockDim.x) {
                 while (k >= inst_start[q + 1]) ++q;
                 const int j = k - inst_start[q];
                 const MechD& M = md_s[q];
                 const int cnt = cnt_s[q];
-                const double* st = st_d + st_off[q];
                 double* gp = g_s + gt_off[q];
-                if (M.kind == NMODL_HH) {
-                    const double m = st[j], h = st[cnt + j], nn = st[2 * cnt + j];
-                    gp[j] = M.hh_g[0] * m * m * m * h;
-                    gp[cnt + j] = M.hh_g[1] * nn * nn * nn * nn;
-                } else if (EXT && M.kind == NMODL_KIN3) {
-                    gp[j] = M.k3.gbar * st[M.k3.open * cnt + j];
-                } else if (!EXT || M.kind != NMODL_CACUM) {
-                    double gg = M.gbar;
-                    for (int g = 0; g < M.n_gates; ++g) gg *= ipow_d(st[g * cnt + j], M.gate[g].power);
-                    gp[j] = gg;
+                if constexpr (PREC == NMODL_FP64) {
+                    const double* st = st_d + st_off[q];
+                    if (M.kind == NMODL_HH) {
+                        const double m = st[j], h = st[cnt + j], nn = st[2 * cnt + j];
+                        gp[j] = M.hh_g[0] * m * m * m * h;
+                        gp[cnt + j] = M.hh_g[1] * nn * nn * nn * nn;
+                    } else if (EXT && M.kind == NMODL_KIN3) {
+                        gp[j] = M.k3.gbar * st[M.k3.open * cnt + j];
+                    } else if (!EXT || M.kind != NMODL_CACUM) {
+                        double gg = M.gbar;
+                        for (int g = 0; g < M.n_gates; ++g) gg *= ipow_d(st[g * cnt + j], M.gate[g].power);
+                        gp[j] = gg;
+                    }
+                } else {
+                    const float2* st = st_f + st_off[q];
+                    const float* cf_p = curf_s[q];
+                    if (M.kind == NMODL_HH) {
+                        const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
+                        gp[j] = f2d_int(cf_p[2] * m * m * m * h);
+                        gp[cnt + j] = f2d_int(cf_p[3] * nn * nn * nn * nn);
+                    } else if (EXT && M.kind == NMODL_KIN3) {
+                        const float2 x = st[M.k3.open * cnt + j];
+                        gp[j] = M.k3.gbar * (f2d_int(x.x) + f2d_int(x.y));
+                    } else if (!EXT || M.kind != NMODL_CACUM) {
+                        float gf = cf_p[0];
+                        for (int g = 0; g < M.n_gates; ++g) {
+                            const float x = st[g * cnt + j].x;
+                            for (int p = 0; p < M.gate[g].power; ++p) gf *= x;
+                        }
+                        gp[j] = f2d_int(gf);
+                    }
                 }
             }
             __syncthreads();
@@ -461,7 +482,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 const int j0 = seg[n], j1 = seg[n + 1];
                 const int cnt = cnt_s[t];
                 if (EXT && M.kind == NMODL_CACUM) continue;  // no membrane current
-                if constexpr (PREC == NMODL_FP64) {
+                {
                     const double* gp = g_s + gt_off[t];
                     if (M.kind == NMODL_HH) {
                         const double gl = M.hh_g[2];
@@ -491,52 +512,6 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                             }
                             dd += g;
                         }
-                    }
-                } else {
-                    // MIXED: FP32 currents from the hi parts of the states
-                    for (int j = j0; j < j1; ++j) {
-                        double ci, gi;
-                        if (EXT && M.kind == NMODL_KIN3) {
-                            const int o = M.k3.open * cnt + j;
-                            const double x = f2d_int(st_f[st_off[t] + o].x) + f2d_int(st_f[st_off[t] + o].y);
-                            gi = M.k3.gbar * x;
-                            ci = gi * (vv - M.k3.e);
-                        } else {
-                            const float2* st = st_f + st_off[t];
-                            const float vf = vf_s[n];
-                            float gf, cf;
-                            const float* cf_p = curf_s[t];
-                            if (M.kind == NMODL_HH) {
-                                const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
-                                const float gna = cf_p[2] * m * m * m * h;
-                                const float gk = cf_p[3] * nn * nn * nn * nn;
-                                const float gl = cf_p[4];
-                                const float inaf = gna * (vf - cf_p[5]);
-                                const float ikf = gk * (vf - cf_p[6]);
-                                if (EXT && A.ions) {
-                                    s_na += f2d_int(inaf);
-                                    s_k += f2d_int(ikf);
-                                }
-                                cf = inaf + ikf + gl * (vf - cf_p[7]);
-                                gf = gna + gk + gl;
-                            } else {
-                                gf = cf_p[0];
-                                for (int q = 0; q < M.n_gates; ++q) {
-                                    const float x = st[q * cnt + j].x;
-                                    for (int p = 0; p < M.gate[q].power; ++p) gf *= x;
-                                }
-                                cf = gf * (vf - cf_p[1]);
-                            }
-                            ci = f2d_int(cf);
-                            gi = f2d_int(gf);
-                        }
-                        if (EXT && M.ion) {  // tagged whole current
-                            if (M.ion == NMODL_ION_NA) s_na += ci;
-                            else if (M.ion == NMODL_ION_K) s_k += ci;
-                            else s_ca += ci;
-                        }
-                        r -= ci;
-                        dd += gi;
                     }
                 }
             }

@@ -125,23 +125,35 @@ __device__ __forceinline__ float sur_inputs(int scaled, float vf, float dtf,
     return s;
 }
 
-// Euclidean projection of w onto {x >= 0, sum x = 1}: theta = (S_j - 1)/c_j
-// for the largest set {i : w_i >= w_j} (c_j members, sum S_j) whose smallest
-// member stays above theta, i.e. w_j c_j - (S_j - 1) > 0; one division.
+// Euclidean projection of w onto {x >= 0, sum x = 1} by the sort-based
+// method (Held, Wolfe & Crowder 1974; as described by Duchi et al. 2008):
+// u = w sorted in descending order, S_k its prefix sums, rho the largest k
+// with u_k k - (S_k - 1) > 0, theta = (S_rho - 1)/rho, x = max(w - theta, 0).
+// The sort is Batcher's odd-even merge network for 16 inputs pruned to 9
+// (padding would hold -inf and never move): 28 comparators, checked on all
+// 2^9 zero-one inputs (the zero-one principle).
 __device__ __forceinline__ void project_simplex9(float (&w)[9]) {
-    float bestS = 0.f, bestC = 0.f;
+    constexpr int kNet[28][2] = {{0, 1}, {2, 3}, {0, 2}, {1, 3}, {1, 2}, {4, 5}, {6, 7},
+                                 {4, 6}, {5, 7}, {5, 6}, {0, 4}, {2, 6}, {2, 4}, {1, 5},
+                                 {3, 7}, {3, 5}, {1, 2}, {3, 4}, {5, 6}, {0, 8}, {4, 8},
+                                 {2, 4}, {6, 8}, {3, 5}, {1, 2}, {3, 4}, {5, 6}, {7, 8}};
+    float u[9];
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        float S = 0.f, c = 0.f;
+    for (int i = 0; i < 9; ++i) u[i] = w[i];
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-            if (w[i] >= w[j]) {
-                S += w[i];
-                c += 1.f;
-            }
-        if (fmaf(w[j], c, 1.0f - S) > 0.f && c > bestC) {
-            bestC = c;
+    for (int c = 0; c < 28; ++c) {
+        const float hi = fmaxf(u[kNet[c][0]], u[kNet[c][1]]);
+        const float lo = fminf(u[kNet[c][0]], u[kNet[c][1]]);
+        u[kNet[c][0]] = hi;
+        u[kNet[c][1]] = lo;
+    }
+    float S = 0.f, bestS = 0.f, bestC = 1.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        S += u[k];
+        if (fmaf(u[k], (float)(k + 1), 1.0f - S) > 0.f) {
             bestS = S;
+            bestC = (float)(k + 1);
         }
     }
     const float theta = (bestS - 1.0f) / bestC;

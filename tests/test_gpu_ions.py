@@ -339,3 +339,67 @@ def test_plan_forms(api):
     ctx.step(ms, 0.025, 1.0, v, rhs, d, 3)
     assert ctx.plan(ms)["fused"] == 1
     assert ctx.sync() == 0
+
+
+def test_fused_with_empty_small_systems(api, orc):
+    """Empty 3-state and buffer mechanisms in a fused list change nothing."""
+    net = W.cortical_mix(600, seed=24)
+    n = net["n_nodes"]
+    ctx = api.Context(0)
+    ions = [torch.zeros(n, dtype=torch.float64, device="cuda:0") for _ in range(3)]
+    ctx.set_ions(*ions)
+    ms = [mech(api, ctx, m, n) for m in net["mechs"]]
+    empty = [api.Mechanism(ctx, api.NMODL_KIN3, np.zeros(0, np.int32), n,
+                           W.kin3_params(W.Stream(1, 1))),
+             api.Mechanism(ctx, api.NMODL_CACUM, np.zeros(0, np.int32), n, W.cacum_params())]
+    v = to_dev(net["v0"])
+    for m in ms:
+        m.init(v)
+    rhs = torch.zeros(n, dtype=torch.float64, device="cuda:0")
+    d = torch.zeros_like(rhs)
+    ctx.step(ms + empty, 0.025, 1.0, v, rhs, d, 6)
+    assert ctx.sync() == 0 and ctx.plan(ms + empty)["fused"] == 1
+    st0 = [orc.mech_init(m["type"], m["params"], m["node_index"], net["v0"])
+           for m in net["mechs"]]
+    v_ref, _, d_ref, _ = orc.step(net["mechs"], st0, net["v0"], n, 0.025, nsteps=6)
+    assert np.max(np.abs(v.cpu().numpy() - v_ref) / np.maximum(np.abs(v_ref), 1.0)) <= 1e-10
+    np.testing.assert_allclose(d.cpu().numpy(), d_ref, rtol=1e-11)
+
+
+def test_cable_with_ions_fused_matches_per_step(api):
+    """Cells of compartments with ion arrays, the 3-state scheme and the
+    buffer: the fused cable form (tiles of whole cells, EXT kernel) against
+    the per-step launch sequence of the same step (itself checked against the
+    oracle by the cable and ion tests)."""
+    cab = W.cable_cells(60, seed=25, size_lo=5, size_hi=80)
+    n = cab["n_nodes"]
+    net = W.cortical_ions(n, seed=25, kin3_frac=0.5)
+    res = {}
+    for form in ("fused", "per_step"):
+        ctx = api.Context(0, tile_smem=48 * 1024, window=6)
+        ions = [torch.zeros(n, dtype=torch.float64, device="cuda:0") for _ in range(3)]
+        ctx.set_ions(*ions)
+        ms = [mech(api, ctx, m, n) for m in net["mechs"]]
+        if form == "per_step":
+            ms.append(api.Mechanism(ctx, api.NMODL_KIN9, np.zeros(0, np.int32), n,
+                                    W.kin9_params(W.Stream(4, 401))))
+        v = to_dev(net["v0"])
+        for m in ms:
+            m.init(v)
+        cable = api.Cable(ctx, cab["parent"], cab["ga"], cab["gb"])
+        rhs = torch.zeros(n, dtype=torch.float64, device="cuda:0")
+        d = torch.zeros_like(rhs)
+        cable.step(ms, 0.025, 1.0, v, rhs, d, 15)
+        assert ctx.sync() == 0
+        assert ctx.plan(ms)["fused"] == (form == "fused")
+        res[form] = (v.cpu().numpy(), d.cpu().numpy(), [x.cpu().numpy() for x in ions],
+                     [m.states().cpu().numpy() for m in ms[:len(net["mechs"])]])
+        cable.close()
+    (vf, df, iof, sf), (vg, dg, iog, sg) = res["fused"], res["per_step"]
+    assert np.max(np.abs(vf - vg) / np.maximum(np.abs(vg), 1.0)) <= 1e-10
+    assert np.max(np.abs(df - dg) / dg) <= 1e-11
+    for a, b in zip(iof, iog):
+        assert np.max(np.abs(a - b)) <= 1e-10 * max(1.0, np.abs(b).max())
+    for a, b in zip(sf, sg):
+        if a.size:
+            assert np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-3)) <= 1e-9

@@ -340,6 +340,17 @@ NMODL_API int nmodl_surrogate_loss_grad(nmodl_surrogate *s, int64_t n,
 NMODL_API int nmodl_surrogate_train_step(nmodl_surrogate *s, int64_t n,
                                          const float *X, const float *T,
                                          float lr, float *loss_dev);
+/* A whole training run: `epochs` passes over the n rows of X/T (device,
+ * layouts as for nmodl_surrogate_train_step) in minibatches of `batch` rows
+ * (a multiple of 16, at most max_batch) taken in row order (n rounded down
+ * to a multiple of batch); Adam with the learning rate on a cosine schedule
+ * from lr to lr_min over all steps.  loss_steps (device, epochs * (n /
+ * batch) floats) receives each step's loss.  One optimiser step is captured
+ * as a CUDA graph and replayed, its kernels reading the step index from
+ * device memory; synchronises the stream at the end. */
+NMODL_API int nmodl_surrogate_fit(nmodl_surrogate *s, int64_t n, const float *X,
+                                  const float *T, int64_t batch, int epochs, float lr,
+                                  float lr_min, float *loss_steps);
 /* Training pairs from Newton steps: inputs X [n][11] and targets
  * T [n][9] = (y - x)/s for samples (v[i], dt[i], x) -> y (device FP64; x
  * and y SoA with row stride), with the kinetic parameters of kin. */

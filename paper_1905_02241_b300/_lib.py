@@ -86,6 +86,8 @@ _SIGS = {
     "nmodl_surrogate_forward": (_i32, [_vp, _i64, _vp, _vp]),
     "nmodl_surrogate_loss_grad": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp]),
     "nmodl_surrogate_train_step": (_i32, [_vp, _i64, _vp, _vp, ctypes.c_float, _vp]),
+    "nmodl_surrogate_fit": (_i32, [_vp, _i64, _vp, _vp, _i64, _i32, ctypes.c_float,
+                                   ctypes.c_float, _vp]),
     "nmodl_surrogate_make_pairs": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "nmodl_kin9_solve": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _i64]),
     "nmodl_mech_attach_surrogate": (_i32, [_vp, _vp, _d]),
@@ -326,3 +328,9 @@ def nmodl_step_cable(ctx: int, cb: int, mechs, dt: float, cm: float, v_ptr: int,
     arr = (_vp * len(mechs))(*mechs)
     _check(lib.nmodl_step_cable(ctx, cb, ctypes.cast(arr, _vp), len(mechs), float(dt),
                                 float(cm), v_ptr, rhs_ptr, d_ptr, int(nsteps)), "nmodl_step_cable")
+
+
+def nmodl_surrogate_fit(sur: int, n: int, X_ptr: int, T_ptr: int, batch: int, epochs: int,
+                        lr: float, lr_min: float, loss_ptr: int) -> None:
+    _check(lib.nmodl_surrogate_fit(sur, int(n), X_ptr, T_ptr, int(batch), int(epochs),
+                                   float(lr), float(lr_min), loss_ptr), "nmodl_surrogate_fit")

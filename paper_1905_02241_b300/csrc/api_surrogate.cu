@@ -121,11 +121,12 @@ void back_delta(nmodl_surrogate* s, int64_t n, const __nv_bfloat16* delta, int n
 }
 
 // loss (device scalar s->loss) and all gradients into s->grad
-void loss_and_grad(nmodl_surrogate* s, int64_t n, const float* X, const float* T) {
+void loss_and_grad(nmodl_surrogate* s, int64_t n, const float* X, const float* T,
+                   FitSched fs = FitSched{}) {
     cudaStream_t st = s->ctx->stream;
-    launch_pack_input(X, n, s->H0, st);
+    launch_pack_input(X, n, s->H0, st, fs);
     forward(s, n);
-    const int blocks = launch_loss_delta(s->OUT, T, n, s->D4, s->loss_part, st);
+    const int blocks = launch_loss_delta(s->OUT, T, n, s->D4, s->loss_part, st, fs);
     launch_reduce_splits(s->loss_part, blocks, 1, s->loss, st);
     weight_grad(s, n, s->D4, kOut, s->H3, kHid, kOffW4, kOffB4);
     back_delta(s, n, s->D4, kOut, s->wbf + kBfW4, kHid, s->Z3, s->D3);
@@ -275,6 +276,56 @@ NMODL_API int nmodl_surrogate_train_step(nmodl_surrogate* s, int64_t n, const fl
     refresh_bf16(s);
     if (loss_dev) cudaMemcpyAsync(loss_dev, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
     return nmodl_cuda_status(cudaGetLastError());
+}
+
+// A whole training run: one optimiser step (loss and gradients, Adam with
+// the scheduled learning rate, bf16 refresh, loss record) is captured as a
+// CUDA graph whose kernels read the step index from device memory, then
+// replayed once per step.
+NMODL_API int nmodl_surrogate_fit(nmodl_surrogate* s, int64_t n, const float* X, const float* T,
+                                  int64_t batch, int epochs, float lr, float lr_min,
+                                  float* loss_steps) {
+    if (!s || batch < 16 || batch > s->max_batch || (batch % 16) || n < batch || epochs < 1 ||
+        !X || !T || !loss_steps || !(lr > 0.f) || !(lr_min >= 0.f) || !(lr_min <= lr))
+        return NMODL_ERR_ARG;
+    nmodl_ctx* c = s->ctx;
+    DeviceGuard dg(c->device);
+    cudaStream_t st = c->stream;
+    const int64_t spe = n / batch, total = spe * (int64_t)epochs;
+    int64_t* d_step = nullptr;
+    cudaError_t e = dalloc(&d_step, 1);
+    if (e != cudaSuccess) return nmodl_cuda_status(e);
+    e = cudaMemsetAsync(d_step, 0, sizeof(int64_t), st);
+    FitSched fs{d_step, spe, total, lr, lr_min, s->step, 1};
+    auto one_step = [&]() {
+        loss_and_grad(s, batch, X, T, fs);
+        launch_adam_sched(s->params, s->grad, s->m, s->v, kParamsPadded, 0.9f, 0.999f, 1e-8f,
+                          fs, st);
+        refresh_bf16(s);
+        launch_fit_end(loss_steps, s->loss, fs, st);
+    };
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && st != nullptr) {
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            one_step();
+            const cudaError_t le = cudaGetLastError();
+            e = cudaStreamEndCapture(st, &graph);
+            if (e == cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        for (int64_t k = 0; e == cudaSuccess && k < total; ++k) e = cudaGraphLaunch(exec, st);
+        if (exec) cudaGraphExecDestroy(exec);
+    } else if (e == cudaSuccess) {  // legacy stream: no capture, plain launches
+        for (int64_t k = 0; k < total; ++k) one_step();
+        e = cudaGetLastError();
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(d_step);
+    if (e == cudaSuccess) s->step += (int)total;
+    return nmodl_cuda_status(e);
 }
 
 NMODL_API int nmodl_surrogate_make_pairs(nmodl_surrogate* s, const nmodl_mech* kin, int64_t n,

@@ -163,9 +163,11 @@ __global__ void k_reduce_splits(const float* __restrict__ part, int splits, int6
     }
 }
 
-__global__ void k_pack_input(const float* __restrict__ X, int64_t n, __nv_bfloat16* H0) {
+__global__ void k_pack_input(const float* __restrict__ X, int64_t n, __nv_bfloat16* H0,
+                             FitSched fs) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (fs.active) X += (*fs.step % fs.steps_per_epoch) * n * kInRaw;
 #pragma unroll
     for (int f = 0; f < kIn; f += 2) {
         const float a = f < kInRaw ? X[i * kInRaw + f] : 0.f;
@@ -176,8 +178,10 @@ __global__ void k_pack_input(const float* __restrict__ X, int64_t n, __nv_bfloat
 
 // delta[b][c] = (out - t)/B for c < 9, 0 otherwise; per-block partial loss.
 __global__ void k_loss_delta(const float* __restrict__ out, const float* __restrict__ T,
-                             int64_t B, __nv_bfloat16* delta, float* block_loss) {
+                             int64_t B, __nv_bfloat16* delta, float* block_loss,
+                             FitSched fs) {
     __shared__ float red[256];
+    if (fs.active) T += (*fs.step % fs.steps_per_epoch) * B * kOutRaw;
     float l = 0.f;
     const float invB = 1.0f / (float)B;
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < B;
@@ -233,6 +237,31 @@ __global__ void k_adam(float* p, const float* __restrict__ grad, float* m, float
     }
 }
 
+// Adam with the learning rate and bias corrections of the run's current
+// step: lr = lr_min + (lr0 - lr_min)(1 + cos(pi k / total))/2, t = t0 + k + 1.
+__global__ void k_adam_sched(float* p, const float* __restrict__ grad, float* m, float* v,
+                             int64_t count, float b1, float b2, float eps, FitSched fs) {
+    const int64_t k = *fs.step;
+    const float lr = fs.lr_min + 0.5f * (fs.lr0 - fs.lr_min) *
+                                     (1.0f + cosf(3.14159265358979f * (float)k / (float)fs.total));
+    const float t = (float)(fs.t0 + k + 1);
+    const float bc1 = 1.f - powf(b1, t), bc2 = 1.f - powf(b2, t);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gr = grad[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gr;
+        const float vi = b2 * v[i] + (1.f - b2) * gr * gr;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+__global__ void k_fit_end(float* loss_steps, const float* loss, FitSched fs) {
+    loss_steps[*fs.step] = *loss;
+    *fs.step += 1;
+}
+
 __global__ void k_to_bf16(const float* __restrict__ src, int64_t count, __nv_bfloat16* dst) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -267,16 +296,26 @@ void launch_reduce_splits(const float* part, int splits, int64_t count, float* o
     k_reduce_splits<<<grid, 256, 0, s>>>(part, splits, count, out);
 }
 
-void launch_pack_input(const float* X, int64_t n, __nv_bfloat16* H0, cudaStream_t s) {
+void launch_pack_input(const float* X, int64_t n, __nv_bfloat16* H0, cudaStream_t s,
+                       FitSched fs) {
     if (n == 0) return;
-    k_pack_input<<<(int)((n + 255) / 256), 256, 0, s>>>(X, n, H0);
+    k_pack_input<<<(int)((n + 255) / 256), 256, 0, s>>>(X, n, H0, fs);
 }
 
 int launch_loss_delta(const float* out, const float* T, int64_t B, __nv_bfloat16* delta,
-                      float* block_loss, cudaStream_t s) {
+                      float* block_loss, cudaStream_t s, FitSched fs) {
     const int grid = (int)std::min<int64_t>((B + 255) / 256, 256);
-    k_loss_delta<<<grid, 256, 0, s>>>(out, T, B, delta, block_loss);
+    k_loss_delta<<<grid, 256, 0, s>>>(out, T, B, delta, block_loss, fs);
     return grid;
+}
+
+void launch_adam_sched(float* p, const float* grad, float* m, float* v, int64_t count,
+                       float b1, float b2, float eps, FitSched fs, cudaStream_t s) {
+    k_adam_sched<<<148, 256, 0, s>>>(p, grad, m, v, count, b1, b2, eps, fs);
+}
+
+void launch_fit_end(float* loss_steps, const float* loss, FitSched fs, cudaStream_t s) {
+    k_fit_end<<<1, 1, 0, s>>>(loss_steps, loss, fs);
 }
 
 void launch_colsum(const __nv_bfloat16* delta, int64_t B, int N, float* part, float* out,

@@ -56,9 +56,26 @@ struct GemmArgs {
 void launch_gemm(int ta, int tb, int epi, const GemmArgs& g, int splits, cudaStream_t s);
 void launch_reduce_splits(const float* part, int splits, int64_t count, float* out,
                           cudaStream_t s);
-void launch_pack_input(const float* X, int64_t n, __nv_bfloat16* H0, cudaStream_t s);
+// Schedule of a whole training run replayed from one captured step: the
+// kernels read the step index from device memory and derive the minibatch
+// (rows (k mod steps_per_epoch) * B of X and T), the cosine learning rate
+// and Adam's bias corrections from it.  active == 0: plain single step.
+struct FitSched {
+    int64_t* step;            // device: index of the current step in the run
+    int64_t steps_per_epoch;
+    int64_t total;
+    float lr0, lr_min;
+    int32_t t0;               // Adam steps taken before the run
+    int32_t active;
+};
+void launch_pack_input(const float* X, int64_t n, __nv_bfloat16* H0, cudaStream_t s,
+                       FitSched fs = FitSched{});
 int launch_loss_delta(const float* out, const float* T, int64_t B, __nv_bfloat16* delta,
-                      float* block_loss, cudaStream_t s);
+                      float* block_loss, cudaStream_t s, FitSched fs = FitSched{});
+void launch_adam_sched(float* p, const float* grad, float* m, float* v, int64_t count,
+                       float b1, float b2, float eps, FitSched fs, cudaStream_t s);
+// loss_steps[step] = *loss; ++step (the last kernel of a captured step)
+void launch_fit_end(float* loss_steps, const float* loss, FitSched fs, cudaStream_t s);
 void launch_colsum(const __nv_bfloat16* delta, int64_t B, int N, float* part, float* out,
                    cudaStream_t s);
 void launch_adam(float* p, const float* grad, float* m, float* v, int64_t count, float lr,

@@ -322,7 +322,7 @@ def kinetic(dev, n=1_000_000, nsteps=200, steps=1):
     return out
 
 
-def surrogate(dev, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=20):
+def surrogate(dev, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=60):
     from .surrogate import Surrogate, attach, make_training_pairs
     p = W.kin9_params(W.Stream(4, 401))
     out = {"instances": n, "steps_per_run": nsteps, "training_pairs": n_pairs,

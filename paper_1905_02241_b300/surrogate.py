@@ -82,21 +82,16 @@ class Surrogate:
     def fit(self, X: torch.Tensor, T: torch.Tensor, epochs: int = 20, batch: int = 8192,
             lr: float = 2e-3, lr_min: float = 1e-5, log_every: int = 0):
         """Adam over mini-batches in the (already random) order of the rows,
-        learning rate on a cosine schedule from lr to lr_min.  Returns the
-        mean loss of each epoch."""
+        learning rate on a cosine schedule from lr to lr_min (the library
+        replays one captured optimiser step per minibatch).  Returns the mean
+        loss of each epoch."""
         n = X.shape[0] // batch * batch
         steps_per_epoch = n // batch
         total = epochs * steps_per_epoch
         loss_dev = torch.zeros(total, dtype=torch.float32, device=X.device)
         self.ctx.enter()
-        k = 0
-        for ep in range(epochs):
-            for b in range(steps_per_epoch):
-                a = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * k / max(1, total)))
-                o = b * batch
-                _lib.nmodl_surrogate_train_step(self.handle, batch, X[o].data_ptr(),
-                                                T[o].data_ptr(), a, loss_dev[k].data_ptr())
-                k += 1
+        _lib.nmodl_surrogate_fit(self.handle, n, X.data_ptr(), T.data_ptr(), batch, epochs,
+                                 lr, lr_min, loss_dev.data_ptr())
         self.ctx.leave()
         losses = loss_dev.view(epochs, steps_per_epoch).mean(dim=1).cpu().numpy()
         return losses

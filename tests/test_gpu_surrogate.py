@@ -114,6 +114,38 @@ def test_training_reduces_loss(S, ctx):
     sur.close()
 
 
+def test_fit_replays_the_optimiser_step(S, ctx):
+    """The graph-replayed training run equals the loop of single optimiser
+    steps (same kernels; the learning rate and bias corrections computed on
+    the device instead of the host)."""
+    from paper_1905_02241_b300 import _lib
+    import math
+    p = W.kin9_params(W.Stream(4, 401))
+    Ws, bs = W.mlp_init(13)
+    a = S.Surrogate(ctx, max_batch=512, weights=S.Surrogate.pack(Ws, bs))
+    b = S.Surrogate(ctx, max_batch=512, weights=S.Surrogate.pack(Ws, bs))
+    X, T = S.make_training_pairs(ctx, a, p, 4096, seed=14)
+    epochs, batch, lr, lr_min = 3, 512, 2e-3, 1e-4
+    la = a.fit(X, T, epochs=epochs, batch=batch, lr=lr, lr_min=lr_min)
+    spe = X.shape[0] // batch
+    total = epochs * spe
+    loss = torch.zeros(total, dtype=torch.float32, device="cuda:0")
+    ctx.enter()
+    for k in range(total):
+        o = (k % spe) * batch
+        rate = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * k / total))
+        _lib.nmodl_surrogate_train_step(b.handle, batch, X[o].data_ptr(), T[o].data_ptr(),
+                                        rate, loss[k].data_ptr())
+    ctx.leave()
+    lb = loss.view(epochs, spe).mean(dim=1).cpu().numpy()
+    np.testing.assert_allclose(la, lb, rtol=1e-4)
+    wa, wb = a.get_weights(), b.get_weights()
+    assert np.max(np.abs(wa - wb)) <= 1e-4 * np.max(np.abs(wb))
+    assert ctx.sync() == 0
+    a.close()
+    b.close()
+
+
 def _kin_setup(ctx, n, seed=4):
     wl = W.kin9_clamped(n, seed=seed)
     (m,) = make_mechs(ctx, wl)

@@ -487,24 +487,28 @@ int nmodl_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
 
 // -------------------------------------------------------------- planning
 
-// Shared memory of one tile, matching the layout in k_fused_tiles.
+// Shared memory of one tile, matching the layout in k_fused_tiles (tables:
+// per-type segment tables and per-term conductances, used by the variant
+// with the small systems and ion sums and by the cable form; otherwise flat
+// node-major slots of 16 bytes per instance).
 static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* terms, int64_t NT,
-                              const int64_t* cnt, bool cable, bool ions) {
+                              const int64_t* cnt, bool cable, bool ions, bool tables) {
     size_t b = 8 * (size_t)NT;
     size_t inst = 0, items = 0;
     for (int t = 0; t < T; ++t) {
         inst += cnt[t];
         items += (size_t)gates[t] * cnt[t];
     }
-    b += 8 * items + 2 * inst + 2 * (size_t)T * (NT + 1);
+    b += 8 * items + 2 * inst;
+    b += tables ? 2 * (size_t)T * (NT + 1) : 2 * inst + 2 * (size_t)(NT + 1) + 2 * (size_t)NT;
     if (prec == NMODL_MIXED) b = (b + 15) / 16 * 16 + 4 * (size_t)NT;
     if (ions) b = (b + 15) / 16 * 16 + 8 * (size_t)NT;  // the step's ica per node
     // d, rhs, ga, gb, parent, and the level schedule (at most 6 NT + 5 uint16)
     if (cable) b = (b + 15) / 16 * 16 + 34 * (size_t)NT + 2 * (6 * (size_t)NT + 5);
-    {  // conductance terms of the step
+    {  // conductance terms (tables) or (x, g) slots (flat) of the step
         size_t g = 0;
         for (int t = 0; t < T; ++t) g += (size_t)terms[t] * cnt[t];
-        b = (b + 15) / 16 * 16 + 8 * g;
+        b = (b + 15) / 16 * 16 + (tables ? 8 * g : 16 * inst);
     }
     return (b + 15) / 16 * 16;
 }
@@ -515,8 +519,9 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* term
 // does not fit.
 static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, int T,
                        const int* gates, const int* terms, const std::vector<int64_t>& bounds,
-                       bool cable,
-                       bool ions, size_t budget, std::vector<int32_t>& recs, size_t& max_smem) {
+                       bool cable, bool ions, bool ext, size_t budget,
+                       std::vector<int32_t>& recs, size_t& max_smem) {
+    const bool tables = ext || cable;
     recs.clear();
     max_smem = 0;
     const int64_t K = (int64_t)off[0].size() - 1;  // fine blocks
@@ -527,11 +532,14 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
         auto fits = [&](int64_t a, int64_t b) -> bool {
             const int64_t NT = bounds[b] - bounds[a];
             if (NT > 65535) return false;
+            int64_t inst = 0;
             for (int t = 0; t < T; ++t) {
                 cnt[t] = off[t][b] - off[t][a];
+                inst += cnt[t];
                 if (cnt[t] > 65535) return false;
             }
-            return tile_smem_bytes(prec, T, gates, terms, NT, cnt.data(), cable, ions) <= budget;
+            if (!tables && inst > 65535) return false;  // uint16 node-major slots
+            return tile_smem_bytes(prec, T, gates, terms, NT, cnt.data(), cable, ions, tables) <= budget;
         };
         if (!fits(k0, k1)) return false;
         while (k1 < K && fits(k0, k1 + 1)) ++k1;
@@ -544,7 +552,8 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
             cnt[t] = off[t][k1] - off[t][k0];
         }
         max_smem = std::max(max_smem,
-                            tile_smem_bytes(prec, T, gates, terms, n1 - n0, cnt.data(), cable, ions));
+                            tile_smem_bytes(prec, T, gates, terms, n1 - n0, cnt.data(), cable, ions,
+                                            tables));
         k0 = k1;
     }
     return true;
@@ -750,7 +759,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
         std::vector<uint16_t>& sched = *sched_p;
         size_t max_smem = 0;
         if (b > cap || !make_tiles(p->precision, off, T, gates, terms, bounds, cb != nullptr, ions,
-                                   b, recs, max_smem)) {
+                                   ext, b, recs, max_smem)) {
             if (dbg) std::fprintf(stderr, "[nmodl plan] budget %zu: no tiling\n", b);
             continue;
         }

@@ -225,20 +225,79 @@ __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
 
 // ---------------------------------------------------- fused tile kernel
 
+// first j in [0, n) with a[j] >= key (a sorted non-decreasing)
+__device__ __forceinline__ int lower_bound_u16(const uint16_t* a, int n, int key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// In-place inclusive prefix sum of a[0, n) in shared memory (the total fits
+// uint16).  Each thread sums a contiguous chunk; the chunk sums are scanned
+// with warp shuffles and one warp over the per-warp totals (wsum: 32 ints
+// of shared memory).  Block size a multiple of 32; called by every thread.
+__device__ void block_inclusive_scan_u16(uint16_t* a, int n, int* wsum) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int per = (n + nt - 1) / nt;
+    const int b0 = min(n, tid * per), b1 = min(n, b0 + per);
+    int s = 0;
+    for (int k = b0; k < b1; ++k) s += a[k];
+    const int lane = tid & 31, w = tid >> 5;
+    int inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = nt >> 5;
+        int x = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane < nw) wsum[lane] = x;
+    }
+    __syncthreads();
+    int run = (w ? wsum[w - 1] : 0) + inc - s;
+    for (int k = b0; k < b1; ++k) {
+        run += a[k];
+        a[k] = (uint16_t)run;
+    }
+    __syncthreads();
+}
+
 // Shared-memory layout of one tile (built from the tile record):
 //   double  v_s[NT]
 //   state   st_s[sum_t gates_t * cnt_t]   (double, or float2 hi/lo in MIXED)
 //   uint16  nid_s[sum_t cnt_t]            local node id of each instance
-//   uint16  seg_s[T][NT + 1]              per-type segment offsets
+//   tables: uint16 seg_s[T][NT + 1]       per-type segment offsets
+//   flat:   uint16 pos_s[sum_t cnt_t]     node-major slot of each instance
+//           uint16 eoff_s[NT + 1]         slot range of each node
+//           uint16 perm_s[NT]             owner order (by slot count)
 //   float   vf_s[NT]                      (MIXED) float copy of v, 16-aligned
+//   double  ica_s[NT]                     (EXT with ions) the step's ica
 //   double  d2_s[NT], r2_s[NT], ga_s[NT], gb_s[NT]   (cable), 16-aligned
 //   uint16  par_s[NT]                     (cable) local parent, 0xffff at roots
 //   uint16  sched_s[...]                  (cable) level schedule of the solve
-//   double  g_s[sum_t terms_t * cnt_t]    (FP64) conductance terms of the step,
-//                                         16-aligned after the above
+//   tables: double  g_s[sum_t terms_t * cnt_t]  conductance terms of the step
+//   flat:   double2 xg_s[sum_t cnt_t]     (x, g) of each instance, node-major;
+//           16-aligned after the above
+// "flat" is the lean (HH/CNEXP) variant on isolated compartments: one sum
+// over contiguous slots per node, owners ordered by slot count.  EXT and the
+// cable form keep the per-type tables (in the cable form, where tiles hold
+// whole cells, the smaller footprint means fewer tiles, hence fewer tree
+// solves, which cost more than the flat sum saves).
 // Tile record (int32): n0, n1, then a_t, b_t per type (instance ranges).
-// The host plan guarantees NT <= 65535, cnt_t <= 65535 and that the layout
-// fits the dynamic shared memory of the launch.
+// The host plan guarantees NT <= 65535, cnt_t <= 65535 (flat: the sum of
+// cnt_t too) and that the layout fits the dynamic shared memory of the
+// launch.
 //
 // Cable form: tiles hold whole cells.  After the current phase each node
 // adds its own axial term (in parallel).  The tree system is then solved by
@@ -270,6 +329,8 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     __shared__ int tile_s;
     __shared__ int inst_start[kMaxMechsFused + 1];  // instance offset of each type
     __shared__ int gt_off[kMaxMechsFused];          // conductance terms of each type
+    __shared__ int scan_s[32];                      // per-warp sums of the block scan
+    __shared__ int hist_s[64];                      // owner-order counting sort
 
     const int tid = threadIdx.x;
     const int T = A.n_types;
@@ -346,15 +407,22 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     double* st_d = v_s + NT;                                   // FP64 states
     float2* st_f = reinterpret_cast<float2*>(v_s + NT);        // MIXED states
     uint16_t* nid_s = reinterpret_cast<uint16_t*>(st_d + total_items);
+    // Per-type tables (EXT, and the cable form): the segment offsets of each
+    // node.  Flat (lean, isolated compartments): the node-major slot of each
+    // instance, the slot range of each node, and the owner order.
+    const bool flat = !EXT && !A.cable;
     uint16_t* seg_s = nid_s + total_inst;
-    // MIXED: a float copy of v per node follows the per-type segment table,
-    // at the next 16-byte boundary
+    uint16_t* pos_s = nid_s + total_inst;
+    uint16_t* eoff_s = pos_s + total_inst;
+    uint16_t* perm_s = eoff_s + NT + 1;
+    uint16_t* idx_end = flat ? perm_s + NT : seg_s + T * (NT + 1);
+    // MIXED: a float copy of v per node follows at the next 16-byte boundary
     float* vf_s = reinterpret_cast<float*>(
-        (reinterpret_cast<uintptr_t>(seg_s + T * (NT + 1)) + 15) & ~(uintptr_t)15);
+        (reinterpret_cast<uintptr_t>(idx_end) + 15) & ~(uintptr_t)15);
     // ions: the step's ica per node; cable: the tree system -- each at the
     // next 16-byte boundary after the above
     uintptr_t end_p = reinterpret_cast<uintptr_t>(
-        PREC == NMODL_MIXED ? (void*)(vf_s + NT) : (void*)(seg_s + T * (NT + 1)));
+        PREC == NMODL_MIXED ? (void*)(vf_s + NT) : (void*)idx_end);
     double* ica_s = reinterpret_cast<double*>((end_p + 15) & ~(uintptr_t)15);
     if (EXT && A.ions) end_p = reinterpret_cast<uintptr_t>(ica_s + NT);
     double* d2_s = reinterpret_cast<double*>((end_p + 15) & ~(uintptr_t)15);
@@ -363,13 +431,15 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     double* gb_s = ga_s + NT;
     uint16_t* par_s = reinterpret_cast<uint16_t*>(gb_s + NT);
     uint16_t* sched_s = par_s + NT;
-    // FP64: conductance terms of the step (HH: gna, gk; others: g)
+    // Per-type tables: conductance terms of the step (HH: gna, gk; others:
+    // g).  Flat: (x, g) of each instance in node-major slots (xg_s).
     double* g_s;
     {
         uintptr_t e = reinterpret_cast<uintptr_t>(d2_s);
         if (A.cable) e = reinterpret_cast<uintptr_t>(sched_s + 6 * NT + 5);
         g_s = reinterpret_cast<double*>((e + 15) & ~(uintptr_t)15);
     }
+    double2* xg_s = reinterpret_cast<double2*>(g_s);
     if (A.cable) {
         const int32_t off = rec[2 + 2 * T], len = rec[3 + 2 * T];
         for (int k = tid; k < len; k += blockDim.x) sched_s[k] = A.sched[off + k];
@@ -406,20 +476,59 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         for (int j = tid; j < cnt_s[t]; j += blockDim.x)
             nid_s[nid_off[t] + j] = (uint16_t)(A.ni[t][a_s[t] + j] - n0);
     __syncthreads();
-    for (int t = 0; t < T; ++t) {
-        const uint16_t* nid = nid_s + nid_off[t];
-        uint16_t* seg = seg_s + t * (NT + 1);
-        const int cnt = cnt_s[t];
-        for (int n = tid; n <= NT; n += blockDim.x) {
-            int lo = 0, hi = cnt;  // first j with nid[j] >= n
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (nid[mid] < n) lo = mid + 1; else hi = mid;
-            }
-            seg[n] = (uint16_t)lo;
+    if (!flat) {
+        for (int t = 0; t < T; ++t) {
+            const uint16_t* nid = nid_s + nid_off[t];
+            uint16_t* seg = seg_s + t * (NT + 1);
+            const int cnt = cnt_s[t];
+            for (int n = tid; n <= NT; n += blockDim.x) seg[n] = (uint16_t)lower_bound_u16(nid, cnt, n);
         }
+        __syncthreads();
+    } else {
+        // Node-major slots: node n owns slots [eoff[n], eoff[n+1]), its
+        // instances in mechanism order, then ascending instance.
+        for (int n = tid; n < NT; n += blockDim.x) {
+            int c = 0;
+            for (int t = 0; t < T; ++t) {
+                const uint16_t* nid = nid_s + nid_off[t];
+                c += lower_bound_u16(nid, cnt_s[t], n + 1) - lower_bound_u16(nid, cnt_s[t], n);
+            }
+            eoff_s[n + 1] = (uint16_t)c;
+        }
+        if (tid == 0) eoff_s[0] = 0;
+        __syncthreads();
+        block_inclusive_scan_u16(eoff_s + 1, NT, scan_s);
+        for (int n = tid; n < NT; n += blockDim.x) {
+            int o = eoff_s[n];
+            for (int t = 0; t < T; ++t) {
+                const uint16_t* nid = nid_s + nid_off[t];
+                const int hi = lower_bound_u16(nid, cnt_s[t], n + 1);
+                for (int j = lower_bound_u16(nid, cnt_s[t], n); j < hi; ++j)
+                    pos_s[nid_off[t] + j] = (uint16_t)o++;
+            }
+        }
+        // Owner order: nodes by decreasing slot count (counting sort on
+        // min(count, 63)), so that the lanes of a warp run sums of similar
+        // length.  Which thread owns a node does not change its result, so
+        // the order within a count is free.
+        for (int k = tid; k < 64; k += blockDim.x) hist_s[k] = 0;
+        __syncthreads();
+        for (int n = tid; n < NT; n += blockDim.x)
+            atomicAdd(&hist_s[63 - min(eoff_s[n + 1] - eoff_s[n], 63)], 1);
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int k = 0; k < 64; ++k) {
+                const int h = hist_s[k];
+                hist_s[k] = acc;
+                acc += h;
+            }
+        }
+        __syncthreads();
+        for (int n = tid; n < NT; n += blockDim.x)
+            perm_s[atomicAdd(&hist_s[63 - min(eoff_s[n + 1] - eoff_s[n], 63)], 1)] = (uint16_t)n;
+        __syncthreads();
     }
-    __syncthreads();
 
     const double cmdt = 1e-3 * A.cm / A.dt;
     for (int step = 0; step < A.nsteps; ++step) {
@@ -434,37 +543,83 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 const int j = k - inst_start[q];
                 const MechD& M = md_s[q];
                 const int cnt = cnt_s[q];
-                double* gp = g_s + gt_off[q];
-                if constexpr (PREC == NMODL_FP64) {
-                    const double* st = st_d + st_off[q];
-                    if (M.kind == NMODL_HH) {
-                        const double m = st[j], h = st[cnt + j], nn = st[2 * cnt + j];
-                        gp[j] = M.hh_g[0] * m * m * m * h;
-                        gp[cnt + j] = M.hh_g[1] * nn * nn * nn * nn;
-                    } else if (EXT && M.kind == NMODL_KIN3) {
-                        gp[j] = M.k3.gbar * st[M.k3.open * cnt + j];
-                    } else if (!EXT || M.kind != NMODL_CACUM) {
-                        double gg = M.gbar;
-                        for (int g = 0; g < M.n_gates; ++g) gg *= ipow_d(st[g * cnt + j], M.gate[g].power);
-                        gp[j] = gg;
-                    }
-                } else {
-                    const float2* st = st_f + st_off[q];
-                    const float* cf_p = curf_s[q];
-                    if (M.kind == NMODL_HH) {
-                        const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
-                        gp[j] = f2d_int(cf_p[2] * m * m * m * h);
-                        gp[cnt + j] = f2d_int(cf_p[3] * nn * nn * nn * nn);
-                    } else if (EXT && M.kind == NMODL_KIN3) {
-                        const float2 x = st[M.k3.open * cnt + j];
-                        gp[j] = M.k3.gbar * (f2d_int(x.x) + f2d_int(x.y));
-                    } else if (!EXT || M.kind != NMODL_CACUM) {
-                        float gf = cf_p[0];
-                        for (int g = 0; g < M.n_gates; ++g) {
-                            const float x = st[g * cnt + j].x;
-                            for (int p = 0; p < M.gate[g].power; ++p) gf *= x;
+                if (flat) {
+                    // Flat: the instance's (x, g) into its node-major slot;
+                    // FP64 x = i = g (v - e), so that the node sum is that of
+                    // the currents; MIXED x = g e and the node forms
+                    // sum(g e) - v sum(g) (its g is FP32-accurate anyway).
+                    double x, g;
+                    if constexpr (PREC == NMODL_FP64) {
+                        const double* st = st_d + st_off[q];
+                        const double vv = v_s[nid_s[k]];
+                        if (M.kind == NMODL_HH) {
+                            const double m = st[j], h = st[cnt + j], nn = st[2 * cnt + j];
+                            const double gna = M.hh_g[0] * m * m * m * h;
+                            const double gk = M.hh_g[1] * nn * nn * nn * nn;
+                            const double gl = M.hh_g[2];
+                            x = gna * (vv - M.hh_e[0]) + gk * (vv - M.hh_e[1]) + gl * (vv - M.hh_e[2]);
+                            g = gna + gk + gl;
+                        } else {
+                            double gg = M.gbar;
+                            for (int gi = 0; gi < M.n_gates; ++gi)
+                                gg *= ipow_d(st[gi * cnt + j], M.gate[gi].power);
+                            x = gg * (vv - M.e);
+                            g = gg;
                         }
-                        gp[j] = f2d_int(gf);
+                    } else {
+                        const float2* st = st_f + st_off[q];
+                        const float* cf_p = curf_s[q];
+                        if (M.kind == NMODL_HH) {
+                            const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
+                            const double gna = f2d_int(cf_p[2] * m * m * m * h);
+                            const double gk = f2d_int(cf_p[3] * nn * nn * nn * nn);
+                            const double gl = M.hh_g[2];
+                            x = fma(gna, M.hh_e[0], fma(gk, M.hh_e[1], gl * M.hh_e[2]));
+                            g = gna + gk + gl;
+                        } else {
+                            float gf = cf_p[0];
+                            for (int gi = 0; gi < M.n_gates; ++gi) {
+                                const float xs = st[gi * cnt + j].x;
+                                for (int pw = 0; pw < M.gate[gi].power; ++pw) gf *= xs;
+                            }
+                            g = f2d_int(gf);
+                            x = g * M.e;
+                        }
+                    }
+                    xg_s[pos_s[k]] = make_double2(x, g);
+                } else {
+                    double* gp = g_s + gt_off[q];
+                    if constexpr (PREC == NMODL_FP64) {
+                        const double* st = st_d + st_off[q];
+                        if (M.kind == NMODL_HH) {
+                            const double m = st[j], h = st[cnt + j], nn = st[2 * cnt + j];
+                            gp[j] = M.hh_g[0] * m * m * m * h;
+                            gp[cnt + j] = M.hh_g[1] * nn * nn * nn * nn;
+                        } else if (EXT && M.kind == NMODL_KIN3) {
+                            gp[j] = M.k3.gbar * st[M.k3.open * cnt + j];
+                        } else if (!EXT || M.kind != NMODL_CACUM) {
+                            double gg = M.gbar;
+                            for (int g = 0; g < M.n_gates; ++g) gg *= ipow_d(st[g * cnt + j], M.gate[g].power);
+                            gp[j] = gg;
+                        }
+                    } else {
+                        const float2* st = st_f + st_off[q];
+                        const float* cf_p = curf_s[q];
+                        if (M.kind == NMODL_HH) {
+                            const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
+                            gp[j] = f2d_int(cf_p[2] * m * m * m * h);
+                            gp[cnt + j] = f2d_int(cf_p[3] * nn * nn * nn * nn);
+                        } else if (EXT && M.kind == NMODL_KIN3) {
+                            const float2 x = st[M.k3.open * cnt + j];
+                            gp[j] = M.k3.gbar * (f2d_int(x.x) + f2d_int(x.y));
+                        } else if (!EXT || M.kind != NMODL_CACUM) {
+                            float gf = cf_p[0];
+                            for (int g = 0; g < M.n_gates; ++g) {
+                                const float x = st[g * cnt + j].x;
+                                for (int p = 0; p < M.gate[g].power; ++p) gf *= x;
+                            }
+                            gp[j] = f2d_int(gf);
+                        }
                     }
                 }
             }
@@ -472,11 +627,22 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         }
         // ---- current update and v update, one owner thread per node; the
         // terms are summed in mechanism order, then ascending instance.
-        for (int n = tid; n < NT; n += blockDim.x) {
+        for (int p = tid; p < NT; p += blockDim.x) {
+            const int n = flat ? (int)perm_s[p] : p;
             const double vv = v_s[n];
             double r = 0.0, dd = 0.0;
             double s_na = 0.0, s_k = 0.0, s_ca = 0.0;  // ion sums (ions)
-            for (int t = 0; t < T; ++t) {
+            if (flat) {
+                double X = 0.0, G = 0.0;
+                for (int sl = eoff_s[n]; sl < eoff_s[n + 1]; ++sl) {
+                    const double2 xg = xg_s[sl];
+                    X += xg.x;
+                    G += xg.y;
+                }
+                r = PREC == NMODL_FP64 ? -X : fma(-vv, G, X);
+                dd = G;
+            }
+            for (int t = 0; !flat && t < T; ++t) {
                 const MechD& M = md_s[t];
                 const uint16_t* seg = seg_s + t * (NT + 1);
                 const int j0 = seg[n], j1 = seg[n + 1];

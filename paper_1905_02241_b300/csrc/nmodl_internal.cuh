@@ -252,16 +252,25 @@ __device__ __forceinline__ void gate_coef_f(const GateF& G, float phidt, float v
 
 // Conversions between float and double on the integer pipe (the FP64 pipe
 // of the B300 also executes the hardware conversions, at a low rate).
-// float -> double is exact; double -> float rounds to nearest even.  Zero,
-// subnormal, infinite and NaN operands take the hardware conversion.
+// float -> double is exact and handles every operand with integer
+// operations (a subnormal float is a normal double; NaNs come out quiet);
+// double -> float rounds to nearest even, and results that are zero,
+// subnormal, infinite or NaN take the hardware conversion.
 __device__ __forceinline__ double f2d_int(float x) {
     const unsigned f = __float_as_uint(x);
-    const unsigned e = (f >> 23) & 0xffu;
-    if (e - 1u < 254u) {
-        const unsigned hi = (f & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((f & 0x7fffffu) >> 3);
-        return __hiloint2double((int)hi, (int)((f & 7u) << 29));
-    }
-    return (double)x;
+    const unsigned e = (f >> 23) & 0xffu, m = f & 0x7fffffu, s = f & 0x80000000u;
+    if (e - 1u < 254u)
+        return __hiloint2double((int)(s | ((e + (1023u - 127u)) << 20) | (m >> 3)), (int)(m << 29));
+    if (e == 255u)  // infinity; NaN with the quiet bit set
+        return __hiloint2double((int)(s | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u)),
+                                (int)(m << 29));
+    if (m == 0u) return __hiloint2double((int)s, 0);
+    // subnormal m 2^-149: the leading one (bit p) becomes the implicit bit
+    const int p = 31 - __clz((int)m);
+    const unsigned long long b = ((unsigned long long)s << 32) |
+                                 ((unsigned long long)(p + 874) << 52) |
+                                 ((unsigned long long)(m ^ (1u << p)) << (52 - p));
+    return __longlong_as_double((long long)b);
 }
 __device__ __forceinline__ float d2f_int(double d) {
     const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);

@@ -85,7 +85,7 @@ def test_cable_fused_tiles_match_per_step_path(api, orc, prec):
            for m in wl["mechs"]]
     out = {}
     for form in ("fused", "per_step"):
-        ctx = api.Context(0, precision=P, tile_smem=24 * 1024, window=7)
+        ctx = api.Context(0, precision=P, tile_smem=32 * 1024, window=7)
         mechs = make_mechs(ctx, wl)
         if form == "per_step":
             mechs.append(api.Mechanism(ctx, api.NMODL_KIN9, np.zeros(0, np.int32), n,

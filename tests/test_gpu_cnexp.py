@@ -163,7 +163,7 @@ def test_empty_mechanism(api, orc):
 
 # ----------------------------------------------------------------- step
 
-def _step_case(api, orc, wl, nsteps, tol, **opts):
+def _step_case(api, orc, wl, nsteps, tol, fused=None, **opts):
     ctx = _ctx(api, **opts)
     mechs = make_mechs(ctx, wl)
     st0 = [orc.mech_init(m["type"], m["params"], m["node_index"], wl["v0"])
@@ -175,6 +175,9 @@ def _step_case(api, orc, wl, nsteps, tol, **opts):
     v, rhs, d = to_dev(wl["v0"]), to_dev(np.zeros(n)), to_dev(np.zeros(n))
     ctx.step(mechs, 0.025, 1.0, v, rhs, d, nsteps)
     assert ctx.sync() == 0
+    if fused is not None:  # the path the tile budget selects: fused tiles or generic
+        plan = ctx.plan(mechs)
+        assert plan["fused"] == fused and (not fused or plan["tiles"] > 1), plan
     v_ref, r_ref, d_ref, s_ref = orc.step(wl["mechs"], st0, wl["v0"], n, 0.025,
                                           nsteps=nsteps, clamp_v=opts.get("clamp_v", 0))
     ev = np.max(np.abs(v.cpu().numpy() - v_ref) / np.maximum(np.abs(v_ref), 1.0))
@@ -188,17 +191,17 @@ def _step_case(api, orc, wl, nsteps, tol, **opts):
     return ev, es
 
 
-@pytest.mark.parametrize("tile_smem", [0, 6144, 64])  # 64: no tile fits -> generic
+@pytest.mark.parametrize("tile_smem", [0, 16384, 64])  # 64: no tile fits -> generic
 def test_step_one_fp64(api, orc, tile_smem):
     wl = W.cortical_mix(5003, seed=8)
-    _step_case(api, orc, wl, 1, TOL_FP64, tile_smem=tile_smem)
+    _step_case(api, orc, wl, 1, TOL_FP64, fused=tile_smem != 64, tile_smem=tile_smem)
 
 
 @pytest.mark.parametrize("window,use_graph", [(40, 1), (7, 0), (3, 1)])
 def test_step_window_fp64(api, orc, window, use_graph):
     wl = W.cortical_mix(3001, seed=9)
-    _step_case(api, orc, wl, 20, 1e-10, window=window, use_graph=use_graph,
-               tile_smem=8192)
+    _step_case(api, orc, wl, 20, 1e-10, fused=True, window=window, use_graph=use_graph,
+               tile_smem=16384)
 
 
 def test_step_hh_trajectory(api, orc):
@@ -217,7 +220,7 @@ def test_step_with_hh_and_mix(api, orc):
     wl = W.cortical_mix(2500, seed=12)
     wl["mechs"].insert(3, dict(type=W.TYPE_HH, params=W.hh_params(),
                                node_index=np.arange(0, 2500, 3, dtype=np.int32)))
-    _step_case(api, orc, wl, 10, 1e-10, tile_smem=12288)
+    _step_case(api, orc, wl, 10, 1e-10, fused=True, tile_smem=16384)
 
 
 # ------------------------------------------------------------ precision
@@ -238,6 +241,8 @@ def test_mixed_precision_errors(api, orc):
         v, rhs, d = to_dev(wl["v0"]), to_dev(np.zeros(n)), to_dev(np.zeros(n))
         ctx.step(mechs, 0.025, 1.0, v, rhs, d, nsteps)
         assert ctx.sync() == 0
+        plan = ctx.plan(mechs)
+        assert plan["fused"] and plan["tiles"] > 1, plan
         v_ref, r_ref, d_ref, s_ref = orc.step(wl["mechs"], st0, wl["v0"], n, 0.025,
                                               nsteps=nsteps)
         es = max(float(np.max(np.abs(m.states().cpu().numpy() - s)))
@@ -353,7 +358,7 @@ def test_fast_reciprocal_within_one_ulp():
 def test_integer_pipe_conversions_round_like_hardware():
     """double -> float -> double through the integer-pipe conversions equals
     numpy's float32 rounding bit for bit (ties, carries into the exponent,
-    zeros, subnormal and huge values included)."""
+    zeros, subnormal, huge, infinite and NaN values included)."""
     from paper_1905_02241_b300 import _lib
     rng = np.random.default_rng(5)
     f = rng.uniform(-1, 1, 20000).astype(np.float32).astype(np.float64)
@@ -362,7 +367,7 @@ def test_integer_pipe_conversions_round_like_hardware():
         rng.uniform(-1, 1, 50000), rng.uniform(0, 1, 50000) * 10.0 ** rng.integers(-40, 40, 50000),
         f + 0.5 * ulp, f - 0.5 * ulp, f + 0.5 * ulp * (1 + 2e-16),   # ties and near-ties
         [0.0, -0.0, 1e-300, -1e-310, 3.4028234663852886e38, 3.5e38, 1.1754943508222875e-38,
-         1.0 - 2 ** -25, 2.0 - 2 ** -24]])
+         1.0 - 2 ** -25, 2.0 - 2 ** -24, np.inf, -np.inf, np.nan, 1.4e-45, -2.9e-39]])
     xd = to_dev(x)
     y = torch.empty_like(xd)
     _lib.nmodl_math_eval(2, x.size, xd.data_ptr(), y.data_ptr(), 0)

@@ -39,13 +39,27 @@ METRIC = "mechanism instance-steps/s (state+cur)"
 # table + degree-4 polynomial + reconstruction); reciprocal 3 (hardware seed
 # on the MUFU pipe, one third-order Newton step).  A gate: each rate as
 # numerator/denominator (u = (v - vh)/k: 2; EXP A e^u: exp + 1; SIGMOID
-# A/(1 + e^-u): exp + 1; LINOID A u/(1 - e^-u): exp + 2), then one
-# reciprocal for minf and alpha + beta (8 + 3 + 1), then cnexp (x, exp,
-# 1 - e, diff, fma: 13).
+# A/(1 + e^-u): exp + 1; LINOID A u/(1 - e^-u): exp + 2); then minf and
+# alpha + beta with one reciprocal (general 8 + 3; an EXP rate has the
+# denominator 1: beta EXP 6 + 3, alpha EXP 7 + 3, both 2 + 3); then cnexp
+# minf + (m - minf) exp(-phi dt s) (x, exp, diff, fma: 12).
 C_EXP, C_RCP = 9, 3
 RATE_COST = {0: 2 + C_EXP + 1, 1: 2 + C_EXP + 1, 2: 2 + C_EXP + 2}
-GATE_TAIL = 8 + C_RCP + 1 + C_EXP + 1 + 1 + 1
+CNEXP_COST = 1 + C_EXP + 1 + 1
 NODE_COST = 1 + C_RCP + 1                       # d += cm/dt, 1/d, v += rhs * (1/d)
+
+
+def gate_tail(aform: int, bform: int) -> int:
+    """minf and alpha + beta from the two rates, then the cnexp update."""
+    if aform == 0 and bform == 0:
+        comb = 2 + C_RCP
+    elif bform == 0:
+        comb = 6 + C_RCP
+    elif aform == 0:
+        comb = 7 + C_RCP
+    else:
+        comb = 8 + C_RCP
+    return comb + CNEXP_COST
 
 
 def fp64_ops_per_step(wl) -> float:
@@ -57,7 +71,7 @@ def fp64_ops_per_step(wl) -> float:
             # gates m, h, n: (alpha form, beta form) = (LINOID, EXP), (EXP,
             # SIGMOID), (LINOID, EXP); currents: gna (4 mul), gk (4 mul),
             # three g(v - e) (2 each), sums (4), accumulate (2)
-            per = sum(RATE_COST[a] + RATE_COST[b] + GATE_TAIL
+            per = sum(RATE_COST[a] + RATE_COST[b] + gate_tail(a, b)
                       for a, b in ((2, 0), (0, 1), (2, 0)))
             per += 4 + 4 + 3 * 2 + 4 + 2
         else:
@@ -66,7 +80,8 @@ def fp64_ops_per_step(wl) -> float:
             pw = 0
             for g in range(ng):
                 o = 6 + 9 * g
-                per += RATE_COST[int(p[o + 1])] + RATE_COST[int(p[o + 5])] + GATE_TAIL
+                af, bf = int(p[o + 1]), int(p[o + 5])
+                per += RATE_COST[af] + RATE_COST[bf] + gate_tail(af, bf)
                 pw += int(p[o])
             per += pw + 2 + 2
         ops += per * n

@@ -92,7 +92,7 @@ __device__ __forceinline__ void cur_cnexp_d(const MechD& M, const double* st,
     } else {
         double gg = M.gbar;
         for (int q = 0; q < M.n_gates; ++q)
-            gg *= ipow_d(st[q * stride + j], M.gate[q].power);
+            gg = mul_pow_d(gg, st[q * stride + j], M.gate[q].power);
         i = gg * (vv - M.e);
         g = gg;
     }
@@ -320,7 +320,14 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     __shared__ int pair_g[kMaxMechsFused * kMaxGates];
     __shared__ int pair_start[kMaxMechsFused * kMaxGates + 1];
     __shared__ int n_pairs;
+    // work order of the state phase (see below): pair of each work slot and
+    // its first work index
+    __shared__ int wq_s[kMaxMechsFused * kMaxGates];
+    __shared__ int wstart_s[kMaxMechsFused * kMaxGates + 1];
+    __shared__ int wkey[kMaxMechsFused * kMaxGates];
+    __shared__ int n_work;
     __shared__ float phidt_f[kMaxMechsFused];
+    __shared__ double phidt_d[kMaxMechsFused];  // phi dt of each type
     // MIXED: FP32 copies of the current parameters (gbar, e, HH g[3], e[3]),
     // converted once rather than per instance (FP64 -> FP32 conversions run
     // on the FP64 pipe)
@@ -371,6 +378,38 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         }
         pair_start[q] = so;
         n_pairs = q;
+        // Work order of the FP64 state phase: the gates grouped by their pair
+        // of rate forms (each pair of forms is one straight-line body), each
+        // group padded to whole warps so that no warp runs two bodies; the
+        // coupled small systems (one item per instance) last.  (MIXED, whose
+        // FP32 bodies are cheap and issue-bound, keeps the storage order.)
+        int nw = 0;
+        for (int p = 0; p < q; ++p) {
+            const int t = pair_t[p], g = pair_g[p], kind = md_s[t].kind;
+            int key;
+            if (EXT && (kind == NMODL_KIN3 || kind == NMODL_CACUM)) {
+                if (g != 0) continue;
+                key = kind == NMODL_KIN3 ? 9 : 10;
+            } else {
+                key = md_s[t].gate[g].aform * 3 + md_s[t].gate[g].bform;
+            }
+            int i = nw++;  // insertion, stable in storage order
+            while (i > 0 && wkey[i - 1] > key) {
+                wkey[i] = wkey[i - 1];
+                wq_s[i] = wq_s[i - 1];
+                --i;
+            }
+            wkey[i] = key;
+            wq_s[i] = p;
+        }
+        int w = 0;
+        for (int i = 0; i < nw; ++i) {
+            wstart_s[i] = w;
+            w += cnt_s[pair_t[wq_s[i]]];
+            if (i + 1 == nw || wkey[i + 1] != wkey[i]) w = (w + 31) & ~31;
+        }
+        wstart_s[nw] = w;
+        n_work = nw;
         int go = 0;
         for (int t = 0; t < T; ++t) {
             inst_start[t] = nid_off[t];
@@ -381,6 +420,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         inst_start[T] = no;
     }
     __syncthreads();
+    for (int k = tid; k < T; k += blockDim.x) phidt_d[k] = md_s[k].phi * A.dt;
     if (PREC == NMODL_MIXED) {
         for (int k = tid; k < T; k += blockDim.x) {
             const MechD& M = md_s[k];
@@ -562,7 +602,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                         } else {
                             double gg = M.gbar;
                             for (int gi = 0; gi < M.n_gates; ++gi)
-                                gg *= ipow_d(st[gi * cnt + j], M.gate[gi].power);
+                                gg = mul_pow_d(gg, st[gi * cnt + j], M.gate[gi].power);
                             x = gg * (vv - M.e);
                             g = gg;
                         }
@@ -599,7 +639,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                             gp[j] = M.k3.gbar * st[M.k3.open * cnt + j];
                         } else if (!EXT || M.kind != NMODL_CACUM) {
                             double gg = M.gbar;
-                            for (int g = 0; g < M.n_gates; ++g) gg *= ipow_d(st[g * cnt + j], M.gate[g].power);
+                            for (int g = 0; g < M.n_gates; ++g) gg = mul_pow_d(gg, st[g * cnt + j], M.gate[g].power);
                             gp[j] = gg;
                         }
                     } else {
@@ -775,16 +815,13 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             }
             __syncthreads();
         }
-        // ---- state update, one thread per (instance, gate) item
-        int q = 0;
-        for (int k = tid; k < total_items; k += blockDim.x) {
-            while (k >= pair_start[q + 1]) ++q;
-            const int t = pair_t[q], g = pair_g[q];
-            const int j = k - pair_start[q];
+        // ---- state update, one thread per (instance, gate) item k (storage
+        // index) of gate g of type t, instance j
+        auto item = [&](int k, int t, int g, int j) {
             const int kind = EXT ? md_s[t].kind : NMODL_CNEXP;
             if (EXT && (kind == NMODL_KIN3 || kind == NMODL_CACUM)) {
                 // coupled states: the item of the first state updates all
-                if (g != 0) continue;
+                if (g != 0) return;
                 const int cnt = cnt_s[t], nd = nid_s[nid_off[t] + j];
                 double x[3];
                 const int ns = kind == NMODL_KIN3 ? 3 : 2;
@@ -808,13 +845,13 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                         st_f[o] = make_float2(hi, d2f_int(x[a] - f2d_int(hi)));
                     }
                 }
-                continue;
+                return;
             }
             if (PREC == NMODL_FP64) {
                 const double vv = v_s[nid_s[nid_off[t] + j]];
                 const GateD& G = md_s[t].gate[g];
-                st_d[k] = A.pade ? gate_step_pade_d(G, md_s[t].phi * A.dt, vv, st_d[k])
-                                 : gate_step_fast_d(G, md_s[t].phi * A.dt, vv, st_d[k]);
+                st_d[k] = A.pade ? gate_step_pade_d(G, phidt_d[t], vv, st_d[k])
+                                 : gate_step_fast_d(G, phidt_d[t], vv, st_d[k]);
             } else {
                 float minf, f;
                 gate_coef_f(gf_s[t][g], phidt_f[t], vf_s[nid_s[nid_off[t] + j]], minf, f,
@@ -828,6 +865,23 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 m.y = lo - (hi2 - s);
                 m.x = hi2;
                 st_f[k] = m;
+            }
+        };
+        if constexpr (PREC == NMODL_FP64) {
+            // work order (slots past a pair's count are a group's padding)
+            int wi = 0;
+            for (int w = tid; w < wstart_s[n_work]; w += blockDim.x) {
+                while (w >= wstart_s[wi + 1]) ++wi;
+                const int q = wq_s[wi];
+                const int t = pair_t[q], j = w - wstart_s[wi];
+                if (j < cnt_s[t]) item(pair_start[q] + j, t, pair_g[q], j);
+            }
+        } else {
+            // storage order (one group: the bodies are cheap and issue-bound)
+            int q = 0;
+            for (int k = tid; k < total_items; k += blockDim.x) {
+                while (k >= pair_start[q + 1]) ++q;
+                item(k, pair_t[q], pair_g[q], k - pair_start[q]);
             }
         }
         __syncthreads();

@@ -141,20 +141,78 @@ __device__ __forceinline__ void rate_nd(int form, double A, double vh, double rk
 
 // cnexp gate step with one reciprocal: alpha = Pa/Da, beta = Pb/Db,
 // N = Pa Db + Pb Da, D = Da Db, R = 1/(N D): minf = Pa Db D R,
-// alpha + beta = N N R.
+// alpha + beta = N N R.  With the rate forms known at compile time an EXP
+// rate's denominator 1 removes multiplications:
+//   beta EXP:  N = Pa + Pb Da, R = 1/(N Da), minf = Pa Da R, s = N N R
+//   alpha EXP: N = Pb + Pa Db, R = 1/(N Db), minf = Pa Db Db R, s = N N R
+//   both EXP:  N = Pa + Pb,    R = 1/N,      minf = Pa R,       s = N.
+// The update m + (1 - e)(minf - m), e = exp(-phi dt s), is taken as
+// minf + (m - minf) e (the same value; one operation fewer).
+template <int AF, int BF>
+__device__ __forceinline__ double gate_step_forms_d(const GateD& G, double phidt, double v,
+                                                    double m) {
+    double na, da, nb, db;
+    rate_nd(AF, G.aA, G.avh, G.ark, v, na, da);
+    rate_nd(BF, G.bA, G.bvh, G.brk, v, nb, db);
+    double minf, s;
+    if constexpr (AF == kExp && BF == kExp) {
+        s = na + nb;
+        minf = na * rcp_fast(s);
+    } else if constexpr (BF == kExp) {
+        const double N = fma(nb, da, na);
+        const double R = rcp_fast(N * da);
+        minf = na * (da * R);
+        s = N * (N * R);
+    } else if constexpr (AF == kExp) {
+        const double P = na * db;
+        const double N = nb + P;
+        const double R = rcp_fast(N * db);
+        minf = P * (db * R);
+        s = N * (N * R);
+    } else {
+        const double P = na * db;
+        const double N = fma(nb, da, P);
+        const double D = da * db;
+        const double R = rcp_fast(N * D);
+        minf = P * (D * R);
+        s = N * (N * R);
+    }
+    return fma(m - minf, exp_tang(-phidt * s), minf);
+}
+
+// One form pair as a separate (not inlined) function: the call boundary
+// keeps the compiler from merging the nine bodies into one predicated
+// sequence, in which every lane would occupy the FP64 pipe for the
+// instructions of all the forms.  A call costs integer instructions only.
+template <int AF, int BF>
+__device__ __noinline__ double gate_step_call_d(double aA, double avh, double ark, double bA,
+                                                double bvh, double brk, double phidt, double v,
+                                                double m) {
+    GateD G;
+    G.aA = aA; G.avh = avh; G.ark = ark;
+    G.bA = bA; G.bvh = bvh; G.brk = brk;
+    return gate_step_forms_d<AF, BF>(G, phidt, v, m);
+}
+
+// The gate step for the gate's forms: a switch that is uniform over the
+// items of one gate, one straight-line body per form pair.
 __device__ __forceinline__ double gate_step_fast_d(const GateD& G, double phidt, double v,
                                                    double m) {
-    double na, da, nb, db;
-    rate_nd(G.aform, G.aA, G.avh, G.ark, v, na, da);
-    rate_nd(G.bform, G.bA, G.bvh, G.brk, v, nb, db);
-    const double P = na * db;
-    const double N = fma(nb, da, P);
-    const double D = da * db;
-    const double R = rcp_fast(N * D);
-    const double minf = P * (D * R);
-    const double s = N * (N * R);
-    const double f = 1.0 - exp_tang(-phidt * s);
-    return fma(f, minf - m, m);
+#define NMODL_GATE_CASE(C, A, B) \
+    case C: return gate_step_call_d<A, B>(G.aA, G.avh, G.ark, G.bA, G.bvh, G.brk, phidt, v, m)
+    switch (G.aform * 3 + G.bform) {
+        NMODL_GATE_CASE(0, kExp, kExp);
+        NMODL_GATE_CASE(1, kExp, kSigmoid);
+        NMODL_GATE_CASE(2, kExp, kLinoid);
+        NMODL_GATE_CASE(3, kSigmoid, kExp);
+        NMODL_GATE_CASE(4, kSigmoid, kSigmoid);
+        NMODL_GATE_CASE(5, kSigmoid, kLinoid);
+        NMODL_GATE_CASE(6, kLinoid, kExp);
+        NMODL_GATE_CASE(7, kLinoid, kSigmoid);
+    default: return gate_step_call_d<kLinoid, kLinoid>(G.aA, G.avh, G.ark, G.bA, G.bvh, G.brk,
+                                                       phidt, v, m);
+    }
+#undef NMODL_GATE_CASE
 }
 
 __device__ __forceinline__ double rate_d(int form, double A, double vh,
@@ -199,10 +257,10 @@ __device__ __forceinline__ double gate_inf_d(const GateD& G, double v) {
     return a / (a + b);
 }
 
-__device__ __forceinline__ double ipow_d(double x, int p) {
-    double r = 1.0;
-    for (int k = 0; k < p; ++k) r *= x;
-    return r;
+// g x^p multiplied out from the left: p multiplications
+__device__ __forceinline__ double mul_pow_d(double g, double x, int p) {
+    for (int k = 0; k < p; ++k) g *= x;
+    return g;
 }
 
 // ------------------------------------------------------------ FP32 math

@@ -1,12 +1,14 @@
 """Generate exp_tang_table.cuh: constants of the table-driven FP64 exp.
 
 Tang, "Table-driven implementation of the exponential function in IEEE
-floating-point arithmetic", ACM TOMS 15(2), 1989: x = (256 m + j) ln2/256 + r,
-exp(x) = 2^m 2^(j/256) exp(r).  The values are mathematical constants
-evaluated with mpmath at 60 digits and rounded to double:
-  T[j] = 2^(j/256), j = 0..255
-  L1 + L2 = ln2/256 with L1 keeping 34 significant bits (so n*L1 is exact for
-  |n| < 2^19, i.e. |x| < 1000), L2 the rounded remainder.
+floating-point arithmetic", ACM TOMS 15(2), 1989: with N = 2^BITS,
+x = (N m + j) ln2/N + r, exp(x) = 2^m 2^(j/N) exp(r).  The values are
+mathematical constants evaluated with mpmath at 60 digits and rounded to
+double:
+  T[j] = 2^(j/N), j = 0..N-1
+  L1 + L2 = ln2/N with L1 keeping L1_BITS significant bits (so n*L1 is exact
+  for |n| < 2^(53 - L1_BITS), here |n| < 2^22, i.e. |x| < 1000), L2 the
+  rounded remainder.
 Run:  python gen_exp_table.py > exp_tang_table.cuh
 """
 import mpmath
@@ -18,9 +20,9 @@ def hexd(x):
     return float(x).hex()
 
 
-BITS = 8           # table of 2^BITS entries
+BITS = 11          # table of 2^BITS entries
 N = 1 << BITS
-L1_BITS = 34
+L1_BITS = 31
 
 
 def main():

@@ -76,14 +76,15 @@ struct Kin9D {
 // ------------------------------------------------------------ FP64 math
 
 // exp(x) by Tang's table-driven method (ACM TOMS 15(2), 1989): with
-// n = round(256 x / ln2) = 256 m + j and r = x - n ln2/256 (two-constant
-// Cody-Waite reduction, |r| <= ln2/512), exp(x) = 2^m 2^(j/256) (1 + p(r)),
-// p(r) the degree-4 Taylor polynomial of exp(r) - 1 (truncation < 4e-17);
-// error within 1.5 ulp (checked against libm on the GPU tests).
-// 9 FP64 instructions; 2^m is applied to the exponent field with integer
-// operations.  x <= -708 returns 0 (the exact value is below 3.3e-308; this
-// is the common case of the cnexp factor of very fast gates); x >= 708 and
-// NaN go to the library exp.
+// N = 2048, n = round(N x / ln2) = N m + j and r = x - n ln2/N (two-constant
+// Cody-Waite reduction, |r| <= ln2/(2N) = 1.7e-4), exp(x) = 2^m 2^(j/N)
+// (1 + p(r)), p(r) = r + r^2/2 + r^3/6 the degree-3 Taylor polynomial of
+// exp(r) - 1 (truncation r^4/24 < 3.5e-17); error within 1.5 ulp (checked
+// against mpmath on the GPU tests).  8 FP64 instructions; 2^m is applied to
+// the exponent field with integer operations; the 16 KB table stays in L1.
+// x <= -708 returns 0 (the exact value is below 3.3e-308; this is the
+// common case of the cnexp factor of very fast gates); x >= 708 and NaN go
+// to the library exp.
 __device__ __forceinline__ double exp_tang(double x) {
     // |x| < 708 tested on the high word (integer pipe): 708 = 0x4086200000000000
     const int hx = __double2hiint(x);
@@ -94,8 +95,7 @@ __device__ __forceinline__ double exp_tang(double x) {
     const double n = t - kShift;
     double r = fma(n, -kExpL1, x);
     r = fma(n, -kExpL2, r);
-    double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
-    q = fma(q, r, 0.5);
+    double q = fma(r, 1.0 / 6.0, 0.5);
     q = fma(q, r, 1.0);
     const double pr = q * r;
     const double T = __ldg(&kExpTable[k & ((1 << kExpBits) - 1)]);

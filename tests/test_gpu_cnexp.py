@@ -307,8 +307,8 @@ def test_full_size_sampled_parity(api, orc):
 
 
 def test_table_exp_ulp_error():
-    """The FP64 exp of the state kernels (Tang's table-driven method, 256-entry
-    table, degree-4 polynomial) against mpmath at 40 digits and against
+    """The FP64 exp of the state kernels (Tang's table-driven method, 2048-entry
+    table, degree-3 polynomial) against mpmath at 40 digits and against
     CUDA's exp: within 1.5 ulp (table entries are rounded to double)."""
     import mpmath
     from paper_1905_02241_b300 import _lib

@@ -327,7 +327,6 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     __shared__ int wkey[kMaxMechsFused * kMaxGates];
     __shared__ int n_work;
     __shared__ float phidt_f[kMaxMechsFused];
-    __shared__ double phidt_d[kMaxMechsFused];  // phi dt of each type
     // MIXED: FP32 copies of the current parameters (gbar, e, HH g[3], e[3]),
     // converted once rather than per instance (FP64 -> FP32 conversions run
     // on the FP64 pipe)
@@ -343,6 +342,15 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     const int T = A.n_types;
     for (int k = tid; k < T * (int)(sizeof(MechD) / 4); k += blockDim.x)
         ((int32_t*)md_s)[k] = ((const int32_t*)A.md)[k];
+    if constexpr (PREC == NMODL_FP64) {
+        // gate parameters folded for this launch (u by one multiply-add,
+        // rates carrying phi dt); ordered by the first barrier of the loop
+        __syncthreads();
+        for (int k = tid; k < T * kMaxGates; k += blockDim.x) {
+            MechD& M = md_s[k / kMaxGates];
+            if (k % kMaxGates < M.n_gates) fold_gate(M.gate[k % kMaxGates], M.phi * A.dt);
+        }
+    }
 
     // Tiles come from the work list in order (largest first): either one
     // per block, or -- persistent form -- pulled from an atomic counter by
@@ -420,7 +428,6 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         inst_start[T] = no;
     }
     __syncthreads();
-    for (int k = tid; k < T; k += blockDim.x) phidt_d[k] = md_s[k].phi * A.dt;
     if (PREC == NMODL_MIXED) {
         for (int k = tid; k < T; k += blockDim.x) {
             const MechD& M = md_s[k];
@@ -850,8 +857,8 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             if (PREC == NMODL_FP64) {
                 const double vv = v_s[nid_s[nid_off[t] + j]];
                 const GateD& G = md_s[t].gate[g];
-                st_d[k] = A.pade ? gate_step_pade_d(G, phidt_d[t], vv, st_d[k])
-                                 : gate_step_fast_d(G, phidt_d[t], vv, st_d[k]);
+                st_d[k] = A.pade ? gate_step_pade_d<true>(G, 1.0, vv, st_d[k])
+                                 : gate_step_fast_d<true>(G, 1.0, vv, st_d[k]);
             } else {
                 float minf, f;
                 gate_coef_f(gf_s[t][g], phidt_f[t], vf_s[nid_s[nid_off[t] + j]], minf, f,

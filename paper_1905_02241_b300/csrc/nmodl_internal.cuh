@@ -120,9 +120,8 @@ __device__ __forceinline__ double rcp_fast(double x) {
 // EXP A e^u / 1; SIGMOID A / (1 + e^-u); LINOID A u / (1 - e^-u), with the
 // series A (1 + u/2 + u^2/12 - u^4/720) / 1 for |u| < 0.01 (next term
 // u^6/30240 < 4e-17).
-__device__ __forceinline__ void rate_nd(int form, double A, double vh, double rk, double v,
-                                        double& num, double& den) {
-    const double u = (v - vh) * rk;
+__device__ __forceinline__ void rate_nd_u(int form, double A, double u, double& num,
+                                          double& den) {
     if (form == kExp) {
         num = A * exp_tang(u);
         den = 1.0;
@@ -138,6 +137,22 @@ __device__ __forceinline__ void rate_nd(int form, double A, double vh, double rk
         den = 1.0 - exp_tang(-u);
     }
 }
+__device__ __forceinline__ void rate_nd(int form, double A, double vh, double rk, double v,
+                                        double& num, double& den) {
+    rate_nd_u(form, A, (v - vh) * rk, num, den);
+}
+
+// A gate's parameters folded for one launch: vh becomes c = -vh/k, so that
+// u = v (1/k) + c is one multiply-add (its rounding moves u by at most a
+// few units of |c| 2^-53: a few ulp in e^u, and in LINOID the same u enters
+// numerator and denominator), and each A is multiplied by phi dt, so that
+// alpha + beta comes out as phi dt (alpha + beta) and minf is unchanged.
+__device__ __forceinline__ void fold_gate(GateD& G, double phidt) {
+    G.avh = -G.avh * G.ark;
+    G.bvh = -G.bvh * G.brk;
+    G.aA *= phidt;
+    G.bA *= phidt;
+}
 
 // cnexp gate step with one reciprocal: alpha = Pa/Da, beta = Pb/Db,
 // N = Pa Db + Pb Da, D = Da Db, R = 1/(N D): minf = Pa Db D R,
@@ -148,12 +163,13 @@ __device__ __forceinline__ void rate_nd(int form, double A, double vh, double rk
 //   both EXP:  N = Pa + Pb,    R = 1/N,      minf = Pa R,       s = N.
 // The update m + (1 - e)(minf - m), e = exp(-phi dt s), is taken as
 // minf + (m - minf) e (the same value; one operation fewer).
-template <int AF, int BF>
+// FOLD: G folded by fold_gate (phidt unused).
+template <int AF, int BF, bool FOLD>
 __device__ __forceinline__ double gate_step_forms_d(const GateD& G, double phidt, double v,
                                                     double m) {
     double na, da, nb, db;
-    rate_nd(AF, G.aA, G.avh, G.ark, v, na, da);
-    rate_nd(BF, G.bA, G.bvh, G.brk, v, nb, db);
+    rate_nd_u(AF, G.aA, FOLD ? fma(v, G.ark, G.avh) : (v - G.avh) * G.ark, na, da);
+    rate_nd_u(BF, G.bA, FOLD ? fma(v, G.brk, G.bvh) : (v - G.bvh) * G.brk, nb, db);
     double minf, s;
     if constexpr (AF == kExp && BF == kExp) {
         s = na + nb;
@@ -177,29 +193,31 @@ __device__ __forceinline__ double gate_step_forms_d(const GateD& G, double phidt
         minf = P * (D * R);
         s = N * (N * R);
     }
-    return fma(m - minf, exp_tang(-phidt * s), minf);
+    return fma(m - minf, exp_tang(FOLD ? -s : -phidt * s), minf);
 }
 
 // One form pair as a separate (not inlined) function: the call boundary
 // keeps the compiler from merging the nine bodies into one predicated
 // sequence, in which every lane would occupy the FP64 pipe for the
 // instructions of all the forms.  A call costs integer instructions only.
-template <int AF, int BF>
+template <int AF, int BF, bool FOLD>
 __device__ __noinline__ double gate_step_call_d(double aA, double avh, double ark, double bA,
                                                 double bvh, double brk, double phidt, double v,
                                                 double m) {
     GateD G;
     G.aA = aA; G.avh = avh; G.ark = ark;
     G.bA = bA; G.bvh = bvh; G.brk = brk;
-    return gate_step_forms_d<AF, BF>(G, phidt, v, m);
+    return gate_step_forms_d<AF, BF, FOLD>(G, phidt, v, m);
 }
 
 // The gate step for the gate's forms: a switch that is uniform over the
-// items of one gate, one straight-line body per form pair.
+// items of one gate, one straight-line body per form pair.  FOLD: G folded
+// by fold_gate.
+template <bool FOLD = false>
 __device__ __forceinline__ double gate_step_fast_d(const GateD& G, double phidt, double v,
                                                    double m) {
 #define NMODL_GATE_CASE(C, A, B) \
-    case C: return gate_step_call_d<A, B>(G.aA, G.avh, G.ark, G.bA, G.bvh, G.brk, phidt, v, m)
+    case C: return gate_step_call_d<A, B, FOLD>(G.aA, G.avh, G.ark, G.bA, G.bvh, G.brk, phidt, v, m)
     switch (G.aform * 3 + G.bform) {
         NMODL_GATE_CASE(0, kExp, kExp);
         NMODL_GATE_CASE(1, kExp, kSigmoid);
@@ -209,8 +227,8 @@ __device__ __forceinline__ double gate_step_fast_d(const GateD& G, double phidt,
         NMODL_GATE_CASE(5, kSigmoid, kLinoid);
         NMODL_GATE_CASE(6, kLinoid, kExp);
         NMODL_GATE_CASE(7, kLinoid, kSigmoid);
-    default: return gate_step_call_d<kLinoid, kLinoid>(G.aA, G.avh, G.ark, G.bA, G.bvh, G.brk,
-                                                       phidt, v, m);
+    default: return gate_step_call_d<kLinoid, kLinoid, FOLD>(G.aA, G.avh, G.ark, G.bA, G.bvh,
+                                                             G.brk, phidt, v, m);
     }
 #undef NMODL_GATE_CASE
 }
@@ -238,14 +256,17 @@ __device__ __forceinline__ double gate_step_d(const GateD& G, double phidt,
 // The same step with exp(-x), x = phi dt (alpha + beta), replaced by its
 // (1,1) Pade approximant: the factor 2x/(2 + x) folds into the one division,
 // m += 2 c (Pa Db - m N) / (2 D + c N) with c = phi dt.
+// FOLD: G folded by fold_gate (the rates carry phi dt; phidt unused).
+template <bool FOLD = false>
 __device__ __forceinline__ double gate_step_pade_d(const GateD& G, double phidt, double v,
                                                    double m) {
     double na, da, nb, db;
-    rate_nd(G.aform, G.aA, G.avh, G.ark, v, na, da);
-    rate_nd(G.bform, G.bA, G.bvh, G.brk, v, nb, db);
+    rate_nd_u(G.aform, G.aA, FOLD ? fma(v, G.ark, G.avh) : (v - G.avh) * G.ark, na, da);
+    rate_nd_u(G.bform, G.bA, FOLD ? fma(v, G.brk, G.bvh) : (v - G.bvh) * G.brk, nb, db);
     const double P = na * db;
     const double N = fma(nb, da, P);
     const double D = da * db;
+    if (FOLD) return m + (2.0 * fma(-m, N, P)) * rcp_fast(N + (D + D));
     const double num = 2.0 * phidt * fma(-m, N, P);
     const double den = fma(phidt, N, D + D);
     return m + num * rcp_fast(den);

@@ -85,10 +85,15 @@ struct Kin9D {
 // x <= -708 returns 0 (the exact value is below 3.3e-308; this is the
 // common case of the cnexp factor of very fast gates); x >= 708 and NaN go
 // to the library exp.
+// The rare arguments of exp_tang, out of line: a call boundary keeps their
+// FP64 instructions out of the common path (not predicated into it).
+static __device__ __noinline__ double exp_tang_rare(double x) {
+    return (__double2hiint(x) < 0 && x == x) ? 0.0 : exp(x);
+}
 __device__ __forceinline__ double exp_tang(double x) {
     // |x| < 708 tested on the high word (integer pipe): 708 = 0x4086200000000000
     const int hx = __double2hiint(x);
-    if ((hx & 0x7fffffff) >= 0x40862000) return (hx < 0 && x == x) ? 0.0 : exp(x);
+    if ((hx & 0x7fffffff) >= 0x40862000) return exp_tang_rare(x);
     const double kShift = 0x1.8p52;
     const double t = fma(x, kExpInvL, kShift);
     const int k = __double2loint(t);
@@ -116,6 +121,13 @@ __device__ __forceinline__ double rcp_fast(double x) {
     return fma(y, fma(e, e, e), y);
 }
 
+// LINOID's series u/(1 - e^-u) = 1 + u/2 + u^2/12 - u^4/720 for |u| < 0.01,
+// out of line like exp_tang_rare
+static __device__ __noinline__ double linoid_series(double u) {
+    const double s = u * u;
+    return fma(u, 0.5, fma(s, fma(s, -1.0 / 720.0, 1.0 / 12.0), 1.0));
+}
+
 // A rate as numerator / denominator (so that a gate needs one reciprocal):
 // EXP A e^u / 1; SIGMOID A / (1 + e^-u); LINOID A u / (1 - e^-u), with the
 // series A (1 + u/2 + u^2/12 - u^4/720) / 1 for |u| < 0.01 (next term
@@ -129,8 +141,7 @@ __device__ __forceinline__ void rate_nd_u(int form, double A, double u, double& 
         num = A;
         den = 1.0 + exp_tang(-u);
     } else if ((__double2hiint(u) & 0x7fffffff) < 0x3f847ae1) {  // |u| < 0.01
-        const double s = u * u;
-        num = A * fma(u, 0.5, fma(s, fma(s, -1.0 / 720.0, 1.0 / 12.0), 1.0));
+        num = A * linoid_series(u);
         den = 1.0;
     } else {
         num = A * u;

@@ -413,7 +413,7 @@ void nmodl_enqueue_state(nmodl_mech* m, double dt, const double* v) {
     if (m->type == NMODL_KIN9 && m->sur) {
         nmodl::enqueue_surrogate_state(m, dt, v);
     } else if (m->type == NMODL_KIN9)
-        launch_kin9_state(o.precision, m->d_kd, m->n, m->d_ni, v, m->d_states, m->stride,
+        launch_kin9_state(o.precision, m->d_kd, m->kd, m->n, m->d_ni, v, m->d_states, m->stride,
                           dt, nullptr, o.newton_tol, o.newton_max_iter, o.ir_max, nullptr, 0,
                           nullptr, m->d_cnt, c->d_err, c->stream);
     else if (m->type == NMODL_KIN3)

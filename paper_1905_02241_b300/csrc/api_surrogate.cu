@@ -354,7 +354,7 @@ NMODL_API int nmodl_kin9_solve(nmodl_mech* kin, int64_t n, const double* v, cons
                                       c->stream);
     if (e != cudaSuccess) return nmodl_cuda_status(e);
     const nmodl_options& o = c->opt;
-    launch_kin9_state(o.precision, kin->d_kd, n, nullptr, v, y, stride, 0.0, dt, o.newton_tol,
+    launch_kin9_state(o.precision, kin->d_kd, kin->kd, n, nullptr, v, y, stride, 0.0, dt, o.newton_tol,
                       o.newton_max_iter, o.ir_max, nullptr, 0, nullptr, nullptr, c->d_err,
                       c->stream);
     return nmodl_cuda_status(cudaGetLastError());
@@ -410,7 +410,7 @@ cudaError_t enqueue_surrogate_state(nmodl_mech* m, double dt, const double* v) {
     e = launch_surrogate_step(a, c->stream);
     if (e != cudaSuccess) return e;
     const nmodl_options& o = c->opt;
-    launch_kin9_state(o.precision, m->d_kd, m->n, m->d_ni, v, m->d_states, m->stride, dt,
+    launch_kin9_state(o.precision, m->d_kd, m->kd, m->n, m->d_ni, v, m->d_states, m->stride, dt,
                       nullptr, o.newton_tol, o.newton_max_iter, o.ir_max, m->d_fb_list, m->n,
                       m->d_fb_count, m->d_cnt, c->d_err, c->stream);
     return cudaGetLastError();

@@ -17,6 +17,7 @@
 // summing exactly to one) and the update of y in FP64; the FP32 factors
 // refine y until max|delta| <= tol or ir_max refinements.
 #include <algorithm>
+#include <cmath>
 
 #include "kernels.cuh"
 
@@ -138,15 +139,28 @@ __global__ void k_kin9_init(const Kin9D* __restrict__ kd, int64_t n,
 
 // One thread per instance (or per entry of the first *n_list_dev of list).  ni == nullptr means instance i reads v[i]; dt_arr != nullptr gives
 // each instance its own step (used to generate training pairs).
+// Rate constants of one launch, folded on the host and passed by value.
+// With one dt for all instances dt k = exp(b v + ln(dt a)): one multiply-add
+// and the exp (FP64: lnc = ln(dt af), ln(dt ab); MIXED: kf = bf, bb, then
+// ln(dt af), ln(dt ab) in FP32).  With a dt per instance (training pairs)
+// MIXED keeps af, ab in kf and scales by dt.  FP32 copies are made on the
+// host because FP64 -> FP32 conversions run on the FP64 pipe.
+struct Kin9Launch {
+    double lnc[2 * kKinEdges];
+    float kf[4 * kKinEdges];
+};
+
 template <int PREC, bool LIST>
 __global__ void __launch_bounds__(128)
-    k_kin9_state(const Kin9D* __restrict__ kd, int64_t n,
+    k_kin9_state(const Kin9D* __restrict__ kd, const Kin9Launch KL, int64_t n,
                  const int32_t* __restrict__ ni, const double* __restrict__ v,
                  double* st, int64_t stride, double dt_scalar,
                  const double* __restrict__ dt_arr, double tol, int max_iter,
                  int ir_max, const int32_t* __restrict__ list,
                  const int32_t* __restrict__ n_list_dev, KinCounters* cnt,
                  int32_t* err) {
+    const double* lnc_s = KL.lnc;
+    const float* kf_s = KL.kf;
     const int64_t n_work = LIST ? (int64_t)*n_list_dev : n;
     unsigned long long it_sum = 0, nc_sum = 0;
     int it_max = 0;
@@ -166,10 +180,18 @@ __global__ void __launch_bounds__(128)
         }
         if (PREC == NMODL_FP64) {
             double dk_f[kKinEdges], dk_b[kKinEdges];
+            if (dt_arr) {
 #pragma unroll
-            for (int e = 0; e < kKinEdges; ++e) {
-                dk_f[e] = dt * (K.af[e] * exp_tang(K.bf[e] * vv));
-                dk_b[e] = dt * (K.ab[e] * exp_tang(-K.bb[e] * vv));
+                for (int e = 0; e < kKinEdges; ++e) {
+                    dk_f[e] = dt * (K.af[e] * exp_tang(K.bf[e] * vv));
+                    dk_b[e] = dt * (K.ab[e] * exp_tang(-K.bb[e] * vv));
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < kKinEdges; ++e) {
+                    dk_f[e] = exp_tang(fma(K.bf[e], vv, lnc_s[e]));
+                    dk_b[e] = exp_tang(fma(-K.bb[e], vv, lnc_s[kKinEdges + e]));
+                }
             }
             double diag[9];
 #pragma unroll
@@ -214,27 +236,42 @@ __global__ void __launch_bounds__(128)
             }
         } else {
             float dk_f[kKinEdges], dk_b[kKinEdges];
-            const float dtf = (float)dt, vf = (float)vv;
+            const float vf = d2f_int(vv);
+            if (dt_arr) {
+                const float dtf = d2f_int(dt);
+#pragma unroll
+                for (int e = 0; e < kKinEdges; ++e) {
+                    dk_f[e] = dtf * (kf_s[2 * kKinEdges + e] * __expf(kf_s[e] * vf));
+                    dk_b[e] = dtf * (kf_s[3 * kKinEdges + e] * __expf(-kf_s[kKinEdges + e] * vf));
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < kKinEdges; ++e) {
+                    dk_f[e] = __expf(fmaf(kf_s[e], vf, kf_s[2 * kKinEdges + e]));
+                    dk_b[e] = __expf(fmaf(-kf_s[kKinEdges + e], vf, kf_s[3 * kKinEdges + e]));
+                }
+            }
+            // FP64 copies of the FP32 rates (exact, integer pipe), and the
+            // FP64 diagonal from them: columns of J sum to 1
+            double dkd_f[kKinEdges], dkd_b[kKinEdges], diag[9];
 #pragma unroll
             for (int e = 0; e < kKinEdges; ++e) {
-                dk_f[e] = dtf * ((float)K.af[e] * __expf((float)K.bf[e] * vf));
-                dk_b[e] = dtf * ((float)K.ab[e] * __expf(-(float)K.bb[e] * vf));
+                dkd_f[e] = f2d_int(dk_f[e]);
+                dkd_b[e] = f2d_int(dk_b[e]);
             }
-            // FP64 diagonal from the FP32 off-diagonals: columns of J sum to 1
-            double diag[9];
 #pragma unroll
             for (int a = 0; a < 9; ++a) diag[a] = 1.0;
 #pragma unroll
             for (int e = 0; e < kKinEdges; ++e) {
-                diag[edge_lo(e)] += (double)dk_f[e];
-                diag[edge_hi(e)] += (double)dk_b[e];
+                diag[edge_lo(e)] += dkd_f[e];
+                diag[edge_hi(e)] += dkd_b[e];
             }
             float M[9][9];
 #pragma unroll
             for (int a = 0; a < 9; ++a)
 #pragma unroll
                 for (int b = 0; b < 9; ++b)
-                    if (in_band(a, b)) M[a][b] = (a == b) ? (float)diag[a] : 0.0f;
+                    if (in_band(a, b)) M[a][b] = (a == b) ? d2f_int(diag[a]) : 0.0f;
 #pragma unroll
             for (int e = 0; e < kKinEdges; ++e) {
                 M[edge_hi(e)][edge_lo(e)] = -dk_f[e];
@@ -248,21 +285,21 @@ __global__ void __launch_bounds__(128)
                 for (int a = 0; a < 9; ++a) r[a] = x[a] - diag[a] * y[a];
 #pragma unroll
                 for (int e = 0; e < kKinEdges; ++e) {
-                    r[edge_hi(e)] += (double)dk_f[e] * y[edge_lo(e)];
-                    r[edge_lo(e)] += (double)dk_b[e] * y[edge_hi(e)];
+                    r[edge_hi(e)] += dkd_f[e] * y[edge_lo(e)];
+                    r[edge_lo(e)] += dkd_b[e] * y[edge_hi(e)];
                 }
                 float rf[9];
 #pragma unroll
-                for (int a = 0; a < 9; ++a) rf[a] = (float)r[a];
+                for (int a = 0; a < 9; ++a) rf[a] = d2f_int(r[a]);
                 lu_band_solve(M, rf);
                 float dmax = 0.0f;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
-                    y[a] += (double)rf[a];
+                    y[a] += f2d_int(rf[a]);
                     dmax = fmaxf(dmax, fabsf(rf[a]));
                 }
                 ++iters;
-                if ((double)dmax <= tol) break;
+                if (f2d_int(dmax) <= tol) break;
                 if (iters == cap) nonconv = true;
             }
         }
@@ -286,7 +323,7 @@ void launch_kin9_init(const Kin9D* kd, int64_t n, const int32_t* ni,
     k_kin9_init<<<(int)((n + block - 1) / block), block, 0, s>>>(kd, n, ni, v, st, stride, err);
 }
 
-void launch_kin9_state(int prec, const Kin9D* kd, int64_t n, const int32_t* ni,
+void launch_kin9_state(int prec, const Kin9D* kd, const Kin9D& kh, int64_t n, const int32_t* ni,
                        const double* v, double* st, int64_t stride, double dt,
                        const double* dt_arr, double tol, int max_iter, int ir_max,
                        const int32_t* list, int64_t n_list_max,
@@ -296,16 +333,27 @@ void launch_kin9_state(int prec, const Kin9D* kd, int64_t n, const int32_t* ni,
     const int64_t work = list ? n_list_max : n;
     if (work == 0) return;
     const int grid = (int)((work + block - 1) / block);
+    Kin9Launch KL;
+    for (int e = 0; e < kKinEdges; ++e) {
+        const double cf = dt_arr ? 0.0 : std::log(dt * kh.af[e]);
+        const double cb = dt_arr ? 0.0 : std::log(dt * kh.ab[e]);
+        KL.lnc[e] = cf;
+        KL.lnc[kKinEdges + e] = cb;
+        KL.kf[e] = (float)kh.bf[e];
+        KL.kf[kKinEdges + e] = (float)kh.bb[e];
+        KL.kf[2 * kKinEdges + e] = (float)(dt_arr ? kh.af[e] : cf);
+        KL.kf[3 * kKinEdges + e] = (float)(dt_arr ? kh.ab[e] : cb);
+    }
     if (prec == NMODL_FP64) {
         if (list)
-            k_kin9_state<NMODL_FP64, true><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, dt_arr, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
+            k_kin9_state<NMODL_FP64, true><<<grid, block, 0, s>>>(kd, KL, n, ni, v, st, stride, dt, dt_arr, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
         else
-            k_kin9_state<NMODL_FP64, false><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, dt_arr, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
+            k_kin9_state<NMODL_FP64, false><<<grid, block, 0, s>>>(kd, KL, n, ni, v, st, stride, dt, dt_arr, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
     } else {
         if (list)
-            k_kin9_state<NMODL_MIXED, true><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, dt_arr, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
+            k_kin9_state<NMODL_MIXED, true><<<grid, block, 0, s>>>(kd, KL, n, ni, v, st, stride, dt, dt_arr, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
         else
-            k_kin9_state<NMODL_MIXED, false><<<grid, block, 0, s>>>(kd, n, ni, v, st, stride, dt, dt_arr, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
+            k_kin9_state<NMODL_MIXED, false><<<grid, block, 0, s>>>(kd, KL, n, ni, v, st, stride, dt, dt_arr, tol, max_iter, ir_max, list, n_list_dev, cnt, err);
     }
 }
 

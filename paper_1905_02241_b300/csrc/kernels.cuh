@@ -95,7 +95,9 @@ __device__ __forceinline__ void warp_count(KinCounters* cnt, unsigned long long 
 void launch_kin9_init(const Kin9D* kd, int64_t n, const int32_t* ni,
                       const double* v, double* st, int64_t stride, int32_t* err,
                       cudaStream_t s);
-void launch_kin9_state(int prec, const Kin9D* kd, int64_t n, const int32_t* ni,
+// kd: the device descriptor; kh: the same on the host (the launch folds
+// its rate constants with dt)
+void launch_kin9_state(int prec, const Kin9D* kd, const Kin9D& kh, int64_t n, const int32_t* ni,
                        const double* v, double* st, int64_t stride, double dt,
                        const double* dt_arr, double tol, int max_iter, int ir_max,
                        const int32_t* list, int64_t n_list_max,

@@ -490,14 +490,16 @@ int nmodl_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
 // Shared memory of one tile, matching the layout in k_fused_tiles (tables:
 // per-type segment tables and per-term conductances, used by the variant
 // with the small systems and ion sums and by the cable form; otherwise flat
-// node-major slots of 16 bytes per instance).
-static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* terms, int64_t NT,
-                              const int64_t* cnt, bool cable, bool ions, bool tables) {
+// node-major slots of 16 bytes, slots[t] per instance).
+static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* terms,
+                              const int* slots, int64_t NT, const int64_t* cnt, bool cable,
+                              bool ions, bool tables) {
     size_t b = 8 * (size_t)NT;
-    size_t inst = 0, items = 0;
+    size_t inst = 0, items = 0, nslot = 0;
     for (int t = 0; t < T; ++t) {
         inst += cnt[t];
         items += (size_t)gates[t] * cnt[t];
+        nslot += (size_t)slots[t] * cnt[t];
     }
     b += 8 * items + 2 * inst;
     b += tables ? 2 * (size_t)T * (NT + 1) : 2 * inst + 2 * (size_t)(NT + 1) + 2 * (size_t)NT;
@@ -508,7 +510,7 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* term
     {  // conductance terms (tables) or (x, g) slots (flat) of the step
         size_t g = 0;
         for (int t = 0; t < T; ++t) g += (size_t)terms[t] * cnt[t];
-        b = (b + 15) / 16 * 16 + (tables ? 8 * g : 16 * inst);
+        b = (b + 15) / 16 * 16 + (tables ? 8 * g : 16 * nslot);
     }
     return (b + 15) / 16 * 16;
 }
@@ -518,8 +520,9 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* term
 // tile's shared memory stays within budget; returns false if one fine block
 // does not fit.
 static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, int T,
-                       const int* gates, const int* terms, const std::vector<int64_t>& bounds,
-                       bool cable, bool ions, bool ext, size_t budget,
+                       const int* gates, const int* terms, const int* slots,
+                       const std::vector<int64_t>& bounds, bool cable, bool ions, bool ext,
+                       size_t budget,
                        std::vector<int32_t>& recs, size_t& max_smem) {
     const bool tables = ext || cable;
     recs.clear();
@@ -532,14 +535,15 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
         auto fits = [&](int64_t a, int64_t b) -> bool {
             const int64_t NT = bounds[b] - bounds[a];
             if (NT > 65535) return false;
-            int64_t inst = 0;
+            int64_t nslot = 0;
             for (int t = 0; t < T; ++t) {
                 cnt[t] = off[t][b] - off[t][a];
-                inst += cnt[t];
+                nslot += slots[t] * cnt[t];
                 if (cnt[t] > 65535) return false;
             }
-            if (!tables && inst > 65535) return false;  // uint16 node-major slots
-            return tile_smem_bytes(prec, T, gates, terms, NT, cnt.data(), cable, ions, tables) <= budget;
+            if (!tables && nslot > 65535) return false;  // uint16 node-major slots
+            return tile_smem_bytes(prec, T, gates, terms, slots, NT, cnt.data(), cable, ions,
+                                   tables) <= budget;
         };
         if (!fits(k0, k1)) return false;
         while (k1 < K && fits(k0, k1 + 1)) ++k1;
@@ -552,8 +556,8 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
             cnt[t] = off[t][k1] - off[t][k0];
         }
         max_smem = std::max(max_smem,
-                            tile_smem_bytes(prec, T, gates, terms, n1 - n0, cnt.data(), cable, ions,
-                                            tables));
+                            tile_smem_bytes(prec, T, gates, terms, slots, n1 - n0, cnt.data(), cable,
+                                            ions, tables));
         k0 = k1;
     }
     return true;
@@ -720,11 +724,12 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     std::vector<std::vector<int32_t>> off(T);
     for (int t = 0; t < T; ++t)
         off[t].assign(hoff.begin() + t * (K + 1), hoff.begin() + (t + 1) * (K + 1));
-    int gates[kMaxMechsFused], terms[kMaxMechsFused];
+    int gates[kMaxMechsFused], terms[kMaxMechsFused], slots[kMaxMechsFused];
     for (int t = 0; t < T; ++t) {
         gates[t] = mechs[t]->n_states;
         // conductance terms per instance in the fused kernel's FP64 scratch
         terms[t] = mechs[t]->type == NMODL_HH ? 2 : mechs[t]->type == NMODL_CACUM ? 0 : 1;
+        slots[t] = mixed_slots(mechs[t]->type, p->precision);
     }
 
     int dev_smem_optin = 0;
@@ -758,8 +763,8 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
         auto sched_p = std::make_shared<std::vector<uint16_t>>();
         std::vector<uint16_t>& sched = *sched_p;
         size_t max_smem = 0;
-        if (b > cap || !make_tiles(p->precision, off, T, gates, terms, bounds, cb != nullptr, ions,
-                                   ext, b, recs, max_smem)) {
+        if (b > cap || !make_tiles(p->precision, off, T, gates, terms, slots, bounds, cb != nullptr,
+                                   ions, ext, b, recs, max_smem)) {
             if (dbg) std::fprintf(stderr, "[nmodl plan] budget %zu: no tiling\n", b);
             continue;
         }

@@ -255,6 +255,36 @@ def test_mixed_precision_errors(api, orc):
     assert out[200][0] <= 1e-4 and out[200][1] <= 1e-2
 
 
+def test_mixed_step_with_hh_and_mix(api, orc):
+    """MIXED fused step with HH among the cnexp types (an HH instance takes
+    three node-major slots, one per current) against the FP64 oracle, per
+    quantity, 20 steps on many tiles."""
+    wl = W.cortical_mix(2500, seed=12)
+    wl["mechs"].insert(3, dict(type=W.TYPE_HH, params=W.hh_params(),
+                               node_index=np.arange(0, 2500, 3, dtype=np.int32)))
+    n = wl["n_nodes"]
+    st0 = [orc.mech_init(m["type"], m["params"], m["node_index"], wl["v0"])
+           for m in wl["mechs"]]
+    ctx = _ctx(api, precision=api.NMODL_MIXED, tile_smem=24576)
+    mechs = make_mechs(ctx, wl)
+    for m, s in zip(mechs, st0):
+        if m.n_states:
+            m.set_states(to_dev(s))
+    v, rhs, d = to_dev(wl["v0"]), to_dev(np.zeros(n)), to_dev(np.zeros(n))
+    ctx.step(mechs, 0.025, 1.0, v, rhs, d, 20)
+    assert ctx.sync() == 0
+    plan = ctx.plan(mechs)
+    assert plan["fused"] and plan["tiles"] > 1, plan
+    v_ref, r_ref, d_ref, s_ref = orc.step(wl["mechs"], st0, wl["v0"], n, 0.025, nsteps=20)
+    es = max(float(np.max(np.abs(m.states().cpu().numpy() - s)))
+             for m, s in zip(mechs, s_ref) if m.n_states)
+    ev = float(np.max(np.abs(v.cpu().numpy() - v_ref)))
+    ed = float(np.max(np.abs(d.cpu().numpy() - d_ref) / d_ref))
+    er = float(np.max(np.abs(rhs.cpu().numpy() - r_ref) / (200.0 * d_ref)))
+    print("MIXED with HH, 20 steps (states abs, v abs mV, d rel, rhs):", es, ev, ed, er)
+    assert es <= 2e-5 and ev <= 2e-3 and ed <= 1e-6 and er <= 1e-6
+
+
 def test_mixed_standalone_state(api, orc):
     wl = W.cortical_mix(2001, seed=14, v_lo=-100, v_hi=60)
     ctx = _ctx(api, precision=api.NMODL_MIXED)

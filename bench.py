@@ -47,7 +47,9 @@ METRIC = "mechanism instance-steps/s (state+cur)"
 C_EXP, C_RCP = 8, 3
 RATE_COST = {0: 1 + C_EXP + 1, 1: 1 + C_EXP + 1, 2: 1 + C_EXP + 2}
 CNEXP_COST = C_EXP + 1 + 1
-NODE_COST = 1 + C_RCP + 1                       # d += cm/dt, 1/d, v += rhs * (1/d)
+# per node: rhs = sum(g e) - v sum(g), d += cm/dt, 1/d, v += rhs * (1/d);
+# per current: its g e and g summed into the node (2)
+NODE_COST = 1 + 1 + C_RCP + 1
 
 
 def gate_tail(aform: int, bform: int) -> int:
@@ -70,11 +72,11 @@ def fp64_ops_per_step(wl) -> float:
         p, n = m["params"], m["node_index"].size
         if m["type"] == W.TYPE_HH:
             # gates m, h, n: (alpha form, beta form) = (LINOID, EXP), (EXP,
-            # SIGMOID), (LINOID, EXP); currents: gna (4 mul), gk (4 mul),
-            # three g(v - e) (2 each), sums (4), accumulate (2)
+            # SIGMOID), (LINOID, EXP); conductances gna (4 mul), gk (4 mul);
+            # three currents summed into the node (2 each)
             per = sum(RATE_COST[a] + RATE_COST[b] + gate_tail(a, b)
                       for a, b in ((2, 0), (0, 1), (2, 0)))
-            per += 4 + 4 + 3 * 2 + 4 + 2
+            per += 4 + 4 + 3 * 2
         else:
             ng = int(p[0])
             per = 0
@@ -84,7 +86,7 @@ def fp64_ops_per_step(wl) -> float:
                 af, bf = int(p[o + 1]), int(p[o + 5])
                 per += RATE_COST[af] + RATE_COST[bf] + gate_tail(af, bf)
                 pw += int(p[o])
-            per += pw + 2 + 2
+            per += pw + 2                    # gbar x^p, then summed into the node
         ops += per * n
     return float(ops)
 

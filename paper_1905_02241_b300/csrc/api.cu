@@ -729,7 +729,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
         gates[t] = mechs[t]->n_states;
         // conductance terms per instance in the fused kernel's FP64 scratch
         terms[t] = mechs[t]->type == NMODL_HH ? 2 : mechs[t]->type == NMODL_CACUM ? 0 : 1;
-        slots[t] = mixed_slots(mechs[t]->type, p->precision);
+        slots[t] = flat_slots(mechs[t]->type);
     }
 
     int dev_smem_optin = 0;

@@ -287,9 +287,8 @@ __device__ void block_inclusive_scan_u16(uint16_t* a, int n, int* wsum) {
 //   uint16  par_s[NT]                     (cable) local parent, 0xffff at roots
 //   uint16  sched_s[...]                  (cable) level schedule of the solve
 //   tables: double  g_s[sum_t terms_t * cnt_t]  conductance terms of the step
-//   flat:   double2 xg_s[slots]           node-major: FP64 (x, g) of each
-//           instance; MIXED (e, g) of each current (HH three per instance);
-//           16-aligned after the above
+//   flat:   double2 xg_s[slots]           node-major (e, g) of each current
+//           (HH three per instance); 16-aligned after the above
 // "flat" is the lean (HH/CNEXP) variant on isolated compartments: one sum
 // over contiguous slots per node, owners ordered by slot count.  EXT and the
 // cable form keep the per-type tables (in the cable form, where tiles hold
@@ -534,14 +533,13 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         __syncthreads();
     } else {
         // Node-major slots: node n owns slots [eoff[n], eoff[n+1]), its
-        // instances in mechanism order, then ascending instance.  FP64: one
-        // slot (x, g) per instance.  MIXED: one slot (e, g) per current
-        // (HH: three), e written here once per window.
+        // instances in mechanism order, then ascending instance; one slot
+        // (e, g) per current (HH: three), e written here once per window.
         for (int n = tid; n < NT; n += blockDim.x) {
             int c = 0;
             for (int t = 0; t < T; ++t) {
                 const uint16_t* nid = nid_s + nid_off[t];
-                c += mixed_slots(md_s[t].kind, PREC) *
+                c += flat_slots(md_s[t].kind) *
                      (lower_bound_u16(nid, cnt_s[t], n + 1) - lower_bound_u16(nid, cnt_s[t], n));
             }
             eoff_s[n + 1] = (uint16_t)c;
@@ -557,15 +555,11 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 const int hi = lower_bound_u16(nid, cnt_s[t], n + 1);
                 for (int j = lower_bound_u16(nid, cnt_s[t], n); j < hi; ++j) {
                     pos_s[nid_off[t] + j] = (uint16_t)o;
-                    if (PREC == NMODL_MIXED) {
-                        if (M.kind == NMODL_HH) {
-                            for (int q = 0; q < 3; ++q) xg_s[o + q].x = M.hh_e[q];
-                            o += 3;
-                        } else {
-                            xg_s[o++].x = M.e;
-                        }
+                    if (M.kind == NMODL_HH) {
+                        for (int q = 0; q < 3; ++q) xg_s[o + q].x = M.hh_e[q];
+                        o += 3;
                     } else {
-                        ++o;
+                        xg_s[o++].x = M.e;
                     }
                 }
             }
@@ -607,34 +601,25 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 const MechD& M = md_s[q];
                 const int cnt = cnt_s[q];
                 if (flat) {
-                    // Flat: FP64, the instance's (x, g) into its node-major
-                    // slot, x = i = g (v - e), so that the node sum is that of
-                    // the currents.  MIXED: each current's g next to its e
-                    // (the node forms sum(g e) - v sum(g); its g is
-                    // FP32-accurate anyway).
+                    // Flat: each current's g next to its e in the instance's
+                    // node-major slots (the node forms sum(g e) - v sum(g)).
+                    const int sl = pos_s[k];
                     if constexpr (PREC == NMODL_FP64) {
-                        double x, g;
                         const double* st = st_d + st_off[q];
-                        const double vv = v_s[nid_s[k]];
                         if (M.kind == NMODL_HH) {
                             const double m = st[j], h = st[cnt + j], nn = st[2 * cnt + j];
-                            const double gna = M.hh_g[0] * m * m * m * h;
-                            const double gk = M.hh_g[1] * nn * nn * nn * nn;
-                            const double gl = M.hh_g[2];
-                            x = gna * (vv - M.hh_e[0]) + gk * (vv - M.hh_e[1]) + gl * (vv - M.hh_e[2]);
-                            g = gna + gk + gl;
+                            xg_s[sl].y = M.hh_g[0] * m * m * m * h;
+                            xg_s[sl + 1].y = M.hh_g[1] * nn * nn * nn * nn;
+                            xg_s[sl + 2].y = M.hh_g[2];
                         } else {
                             double gg = M.gbar;
                             for (int gi = 0; gi < M.n_gates; ++gi)
                                 gg = mul_pow_d(gg, st[gi * cnt + j], M.gate[gi].power);
-                            x = gg * (vv - M.e);
-                            g = gg;
+                            xg_s[sl].y = gg;
                         }
-                        xg_s[pos_s[k]] = make_double2(x, g);
                     } else {
                         const float2* st = st_f + st_off[q];
                         const float* cf_p = curf_s[q];
-                        const int sl = pos_s[k];
                         if (M.kind == NMODL_HH) {
                             const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
                             xg_s[sl].y = f2d_int(cf_p[2] * m * m * m * h);
@@ -697,11 +682,11 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             if (flat) {
                 double X = 0.0, G = 0.0;
                 for (int sl = eoff_s[n]; sl < eoff_s[n + 1]; ++sl) {
-                    const double2 xg = xg_s[sl];
-                    X = PREC == NMODL_FP64 ? X + xg.x : fma(xg.y, xg.x, X);
-                    G += xg.y;
+                    const double2 eg = xg_s[sl];
+                    X = fma(eg.y, eg.x, X);
+                    G += eg.y;
                 }
-                r = PREC == NMODL_FP64 ? -X : fma(-vv, G, X);
+                r = fma(-vv, G, X);  // -sum g (v - e)
                 dd = G;
             }
             for (int t = 0; !flat && t < T; ++t) {

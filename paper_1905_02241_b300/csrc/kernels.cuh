@@ -9,11 +9,8 @@ namespace nmodl {
 constexpr int kFusedMaxBlock = 1024;
 
 // node-major slots per instance of the fused step's flat layout: one
-// (x, g) in FP64; one (e, g) per current in MIXED (HH: sodium, potassium,
-// leak)
-__host__ __device__ constexpr int mixed_slots(int kind, int prec) {
-    return (prec == NMODL_MIXED && kind == NMODL_HH) ? 3 : 1;
-}
+// (e, g) per current (HH: sodium, potassium, leak)
+__host__ __device__ constexpr int flat_slots(int kind) { return kind == NMODL_HH ? 3 : 1; }
 
 // Arguments of the fused multi-step tile kernel (passed by value).
 struct FusedArgs {

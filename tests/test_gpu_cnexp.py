@@ -220,7 +220,7 @@ def test_step_with_hh_and_mix(api, orc):
     wl = W.cortical_mix(2500, seed=12)
     wl["mechs"].insert(3, dict(type=W.TYPE_HH, params=W.hh_params(),
                                node_index=np.arange(0, 2500, 3, dtype=np.int32)))
-    _step_case(api, orc, wl, 10, 1e-10, fused=True, tile_smem=16384)
+    _step_case(api, orc, wl, 10, 1e-10, fused=True, tile_smem=24576)
 
 
 # ------------------------------------------------------------ precision

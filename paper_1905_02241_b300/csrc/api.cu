@@ -503,6 +503,7 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* term
     }
     b += 8 * items + 2 * inst;
     b += tables ? 2 * (size_t)T * (NT + 1) : 2 * inst + 2 * (size_t)(NT + 1) + 2 * (size_t)NT;
+    if (!tables && ions) b += nslot;  // the ion of each slot
     if (prec == NMODL_MIXED) b = (b + 15) / 16 * 16 + 4 * (size_t)NT;
     if (ions) b = (b + 15) / 16 * 16 + 8 * (size_t)NT;  // the step's ica per node
     // d, rhs, ga, gb, parent, and the level schedule (at most 6 NT + 5 uint16)
@@ -524,7 +525,7 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
                        const std::vector<int64_t>& bounds, bool cable, bool ions, bool ext,
                        size_t budget,
                        std::vector<int32_t>& recs, size_t& max_smem) {
-    const bool tables = ext || cable;
+    const bool tables = cable;
     recs.clear();
     max_smem = 0;
     const int64_t K = (int64_t)off[0].size() - 1;  // fine blocks

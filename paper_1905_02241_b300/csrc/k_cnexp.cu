@@ -336,6 +336,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     __shared__ int inst_start[kMaxMechsFused + 1];  // instance offset of each type
     __shared__ int gt_off[kMaxMechsFused];          // conductance terms of each type
     __shared__ int scan_s[32];                      // per-warp sums of the block scan
+    __shared__ int n_slots_s;                       // node-major slots of the tile (flat)
     __shared__ int hist_s[64];                      // owner-order counting sort
 
     const int tid = threadIdx.x;
@@ -426,6 +427,9 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             go += (kind == NMODL_HH ? 2 : kind == NMODL_CACUM ? 0 : 1) * cnt_s[t];
         }
         inst_start[T] = no;
+        int ns = 0;
+        for (int t = 0; t < T; ++t) ns += flat_slots(md_s[t].kind) * cnt_s[t];
+        n_slots_s = ns;
     }
     __syncthreads();
     if (PREC == NMODL_MIXED) {
@@ -454,22 +458,25 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     double* st_d = v_s + NT;                                   // FP64 states
     float2* st_f = reinterpret_cast<float2*>(v_s + NT);        // MIXED states
     uint16_t* nid_s = reinterpret_cast<uint16_t*>(st_d + total_items);
-    // Per-type tables (EXT, and the cable form): the segment offsets of each
-    // node.  Flat (lean, isolated compartments): the node-major slot of each
-    // instance, the slot range of each node, and the owner order.
-    const bool flat = !EXT && !A.cable;
+    // Per-type tables (the cable form): the segment offsets of each node.
+    // Flat (isolated compartments): the node-major slot of each instance, the
+    // slot range of each node, the owner order, and (with ion arrays) the ion
+    // of each slot.
+    const bool flat = !A.cable;
     uint16_t* seg_s = nid_s + total_inst;
     uint16_t* pos_s = nid_s + total_inst;
     uint16_t* eoff_s = pos_s + total_inst;
     uint16_t* perm_s = eoff_s + NT + 1;
-    uint16_t* idx_end = flat ? perm_s + NT : seg_s + T * (NT + 1);
+    uint8_t* tag_s = reinterpret_cast<uint8_t*>(perm_s + NT);
+    void* idx_end = flat ? ((EXT && A.ions) ? (void*)(tag_s + n_slots_s) : (void*)(perm_s + NT))
+                         : (void*)(seg_s + T * (NT + 1));
     // MIXED: a float copy of v per node follows at the next 16-byte boundary
     float* vf_s = reinterpret_cast<float*>(
         (reinterpret_cast<uintptr_t>(idx_end) + 15) & ~(uintptr_t)15);
     // ions: the step's ica per node; cable: the tree system -- each at the
     // next 16-byte boundary after the above
     uintptr_t end_p = reinterpret_cast<uintptr_t>(
-        PREC == NMODL_MIXED ? (void*)(vf_s + NT) : (void*)idx_end);
+        PREC == NMODL_MIXED ? (void*)(vf_s + NT) : idx_end);
     double* ica_s = reinterpret_cast<double*>((end_p + 15) & ~(uintptr_t)15);
     if (EXT && A.ions) end_p = reinterpret_cast<uintptr_t>(ica_s + NT);
     double* d2_s = reinterpret_cast<double*>((end_p + 15) & ~(uintptr_t)15);
@@ -556,10 +563,16 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 for (int j = lower_bound_u16(nid, cnt_s[t], n); j < hi; ++j) {
                     pos_s[nid_off[t] + j] = (uint16_t)o;
                     if (M.kind == NMODL_HH) {
-                        for (int q = 0; q < 3; ++q) xg_s[o + q].x = M.hh_e[q];
+                        for (int q = 0; q < 3; ++q) {
+                            xg_s[o + q].x = M.hh_e[q];
+                            if (EXT && A.ions)
+                                tag_s[o + q] = q == 0 ? NMODL_ION_NA : q == 1 ? NMODL_ION_K : NMODL_ION_NONE;
+                        }
                         o += 3;
-                    } else {
-                        xg_s[o++].x = M.e;
+                    } else if (!EXT || M.kind != NMODL_CACUM) {
+                        xg_s[o].x = (EXT && M.kind == NMODL_KIN3) ? M.k3.e : M.e;
+                        if (EXT && A.ions) tag_s[o] = (uint8_t)M.ion;
+                        ++o;
                     }
                 }
             }
@@ -604,6 +617,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                     // Flat: each current's g next to its e in the instance's
                     // node-major slots (the node forms sum(g e) - v sum(g)).
                     const int sl = pos_s[k];
+                    if (EXT && M.kind == NMODL_CACUM) continue;  // no membrane current
                     if constexpr (PREC == NMODL_FP64) {
                         const double* st = st_d + st_off[q];
                         if (M.kind == NMODL_HH) {
@@ -611,6 +625,8 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                             xg_s[sl].y = M.hh_g[0] * m * m * m * h;
                             xg_s[sl + 1].y = M.hh_g[1] * nn * nn * nn * nn;
                             xg_s[sl + 2].y = M.hh_g[2];
+                        } else if (EXT && M.kind == NMODL_KIN3) {
+                            xg_s[sl].y = M.k3.gbar * st[M.k3.open * cnt + j];
                         } else {
                             double gg = M.gbar;
                             for (int gi = 0; gi < M.n_gates; ++gi)
@@ -625,6 +641,9 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                             xg_s[sl].y = f2d_int(cf_p[2] * m * m * m * h);
                             xg_s[sl + 1].y = f2d_int(cf_p[3] * nn * nn * nn * nn);
                             xg_s[sl + 2].y = M.hh_g[2];
+                        } else if (EXT && M.kind == NMODL_KIN3) {
+                            const float2 x = st[M.k3.open * cnt + j];
+                            xg_s[sl].y = M.k3.gbar * (f2d_int(x.x) + f2d_int(x.y));
                         } else {
                             float gf = cf_p[0];
                             for (int gi = 0; gi < M.n_gates; ++gi) {
@@ -680,14 +699,33 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             double r = 0.0, dd = 0.0;
             double s_na = 0.0, s_k = 0.0, s_ca = 0.0;  // ion sums (ions)
             if (flat) {
-                double X = 0.0, G = 0.0;
-                for (int sl = eoff_s[n]; sl < eoff_s[n + 1]; ++sl) {
+                double X = 0.0, G = 0.0, Xca = 0.0, Gca = 0.0;
+                const int s0 = eoff_s[n], s1 = eoff_s[n + 1];
+                for (int sl = s0; sl < s1; ++sl) {
                     const double2 eg = xg_s[sl];
                     X = fma(eg.y, eg.x, X);
                     G += eg.y;
+                    if (EXT && A.ions) {
+                        // calcium every step (the buffer reads it), without a
+                        // branch: sum(g e) and sum(g) over the calcium slots
+                        const double gc = tag_s[sl] == NMODL_ION_CA ? eg.y : 0.0;
+                        Xca = fma(gc, eg.x, Xca);
+                        Gca += gc;
+                    }
                 }
                 r = fma(-vv, G, X);  // -sum g (v - e)
                 dd = G;
+                if (EXT && A.ions) {
+                    s_ca = fma(vv, Gca, -Xca);
+                    if (last) {  // sodium and potassium, once per window
+                        for (int sl = s0; sl < s1; ++sl) {
+                            const double2 eg = xg_s[sl];
+                            const int tg = tag_s[sl];
+                            if (tg == NMODL_ION_NA) s_na = fma(eg.y, vv - eg.x, s_na);
+                            else if (tg == NMODL_ION_K) s_k = fma(eg.y, vv - eg.x, s_k);
+                        }
+                    }
+                }
             }
             for (int t = 0; !flat && t < T; ++t) {
                 const MechD& M = md_s[t];

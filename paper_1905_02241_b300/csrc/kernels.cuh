@@ -9,8 +9,10 @@ namespace nmodl {
 constexpr int kFusedMaxBlock = 1024;
 
 // node-major slots per instance of the fused step's flat layout: one
-// (e, g) per current (HH: sodium, potassium, leak)
-__host__ __device__ constexpr int flat_slots(int kind) { return kind == NMODL_HH ? 3 : 1; }
+// (e, g) per current (HH: sodium, potassium, leak; the calcium buffer none)
+__host__ __device__ constexpr int flat_slots(int kind) {
+    return kind == NMODL_HH ? 3 : kind == NMODL_CACUM ? 0 : 1;
+}
 
 // Arguments of the fused multi-step tile kernel (passed by value).
 struct FusedArgs {

@@ -75,14 +75,21 @@ __device__ __forceinline__ void kin_rates_f(const Kin9D& K, float vf, float dtf,
         dkb[e] = dtf * ((float)K.ab[e] * __expf(-(float)K.bb[e] * vf));
     }
 }
-// the same rates from FP32 copies of the parameters (af, bf, ab, bb, 12
-// each), e.g. staged in shared memory: no FP64 conversions per instance
-__device__ __forceinline__ void kin_rates_f32(const float* kp, float vf, float dtf,
-                                              float (&dkf)[kKinEdges], float (&dkb)[kKinEdges]) {
+// The same rates with the launch's constants folded: dt k = 2^(b' v + c')
+// with b' = b log2(e) (negated for the backward rates) and c' = log2(dt a),
+// so that each rate is one multiply-add and the hardware exp2 (kp: b'f, c'f,
+// b'b, c'b, 12 each, staged once per CTA)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ void kin_rates_folded(const float* kp, float vf,
+                                                 float (&dkf)[kKinEdges], float (&dkb)[kKinEdges]) {
 #pragma unroll
     for (int e = 0; e < kKinEdges; ++e) {
-        dkf[e] = dtf * (kp[e] * __expf(kp[kKinEdges + e] * vf));
-        dkb[e] = dtf * (kp[2 * kKinEdges + e] * __expf(-kp[3 * kKinEdges + e] * vf));
+        dkf[e] = ex2_approx(fmaf(kp[e], vf, kp[kKinEdges + e]));
+        dkb[e] = ex2_approx(fmaf(kp[2 * kKinEdges + e], vf, kp[3 * kKinEdges + e]));
     }
 }
 __device__ __forceinline__ void dtAx_f(const float (&dkf)[kKinEdges],
@@ -215,10 +222,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_surrogate_step(SurArgs a) {
     if (tid < kOut) put_pair(kOffB4i, tid, 0, 16, a.params[kOffB4 + tid]);
     float* kps = reinterpret_cast<float*>(smem + kOffRate);
     if (tid < kKinEdges) {
-        kps[tid] = (float)a.kd->af[tid];
-        kps[kKinEdges + tid] = (float)a.kd->bf[tid];
-        kps[2 * kKinEdges + tid] = (float)a.kd->ab[tid];
-        kps[3 * kKinEdges + tid] = (float)a.kd->bb[tid];
+        const double kLog2e = 1.4426950408889634;  // log2(e)
+        kps[tid] = (float)(a.kd->bf[tid] * kLog2e);
+        kps[kKinEdges + tid] = (float)log2(a.dt * a.kd->af[tid]);
+        kps[2 * kKinEdges + tid] = (float)(-a.kd->bb[tid] * kLog2e);
+        kps[3 * kKinEdges + tid] = (float)log2(a.dt * a.kd->ab[tid]);
     }
     if (tid == 0) {
         for (int k = 0; k < kWG; ++k) mbar_init(&bars[k], 1);
@@ -317,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_surrogate_step(SurArgs a) {
 #pragma unroll
                 for (int k = 0; k < 9; ++k) xf[k] = d2f_int(a.st[k * a.stride + i]);
                 const float vf = d2f_int(a.v[a.ni[i]]);
-                kin_rates_f32(kps, vf, dtf, dkf, dkb);
+                kin_rates_folded(kps, vf, dkf, dkb);
                 dtAx_f(dkf, dkb, xf, z);
                 s = sur_inputs(a.scaled, vf, dtf, xf, z, f);
             }

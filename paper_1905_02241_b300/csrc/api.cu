@@ -417,12 +417,12 @@ void nmodl_enqueue_state(nmodl_mech* m, double dt, const double* v) {
                           dt, nullptr, o.newton_tol, o.newton_max_iter, o.ir_max, nullptr, 0,
                           nullptr, m->d_cnt, c->d_err, c->stream);
     else if (m->type == NMODL_KIN3)
-        launch_kin3_state(o.precision, m->d_k3, m->n, m->d_ni, v, m->d_states, m->stride, dt,
-                          o.newton_tol, o.ir_max, m->d_cnt, c->d_err, c->stream);
+        launch_kin3_state(o.precision, m->d_k3, m->k3, m->n, m->d_ni, v, m->d_states, m->stride,
+                          dt, o.newton_tol, o.ir_max, m->d_cnt, c->d_err, c->stream);
     else if (m->type == NMODL_CACUM)
-        launch_cacum_state(m->d_cd, m->n, m->d_ni, c->ion[NMODL_ION_CA], m->d_states,
-                           m->stride, dt, o.newton_tol, o.newton_max_iter, m->d_cnt, c->d_err,
-                           c->stream);
+        launch_cacum_state(o.precision, m->d_cd, m->cd, m->n, m->d_ni, c->ion[NMODL_ION_CA],
+                           m->d_states, m->stride, dt, o.newton_tol, o.newton_max_iter, o.ir_max,
+                           m->d_cnt, c->d_err, c->stream);
     else
         launch_state_gates(o.precision, m->d_md, m->n_states, m->n, m->d_ni, v,
                            m->d_states, m->stride, dt, o.cnexp_pade, c->d_err, c->stream);
@@ -873,6 +873,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
             a.ions = ions;  // sums and ica kept, no ion array written
             a.newton_tol = c->opt.newton_tol;
             a.newton_max_iter = c->opt.newton_max_iter;
+            a.ir_max = c->opt.ir_max;
             // descriptors
             if (!p->d_md) {
                 if (dalloc(&p->d_md, T) != cudaSuccess) { ok = false; break; }
@@ -992,6 +993,7 @@ static FusedArgs fused_args(nmodl_ctx* c, Plan* p, double dt, double cm, double*
     for (int q = 1; q < 4; ++q) a.ion[q] = c->ion[q];
     a.newton_tol = c->opt.newton_tol;
     a.newton_max_iter = c->opt.newton_max_iter;
+    a.ir_max = c->opt.ir_max;
     if (nmodl_cable* cb = p->cable) {
         a.cable = 1;
         a.parent = cb->d_parent;

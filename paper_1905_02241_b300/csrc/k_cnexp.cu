@@ -331,6 +331,9 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     // converted once rather than per instance (FP64 -> FP32 conversions run
     // on the FP64 pipe)
     __shared__ float curf_s[kMaxMechsFused][8];
+    // MIXED with the small systems: their parameters in FP32
+    __shared__ Kin3F k3f_s[EXT ? kMaxMechsFused : 1];
+    __shared__ CacumF cdf_s[EXT ? kMaxMechsFused : 1];
 
     __shared__ int tile_s;
     __shared__ int inst_start[kMaxMechsFused + 1];  // instance offset of each type
@@ -443,6 +446,22 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 curf_s[k][5 + q] = (float)M.hh_e[q];
             }
         }
+        if (EXT)
+            for (int k = tid; k < T; k += blockDim.x) {
+                const MechD& M = md_s[k];
+                if (M.kind == NMODL_KIN3) {
+                    for (int e = 0; e < 3; ++e) {
+                        k3f_s[k].af[e] = (float)M.k3.af[e];
+                        k3f_s[k].bf[e] = (float)M.k3.bf[e];
+                        k3f_s[k].ab[e] = (float)M.k3.ab[e];
+                        k3f_s[k].bb[e] = (float)M.k3.bb[e];
+                    }
+                } else if (M.kind == NMODL_CACUM) {
+                    const CacumD& C = M.cd;
+                    cdf_s[k] = CacumF{(float)C.k, (float)C.rtau, (float)C.cai0, (float)C.kf,
+                                      (float)C.kb, (float)C.btot};
+                }
+            }
         for (int k = tid; k < T * kMaxGates; k += blockDim.x) {
             const GateD& G = md_s[k / kMaxGates].gate[k % kMaxGates];
             gf_s[k / kMaxGates][k % kMaxGates] =
@@ -874,12 +893,19 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                     const int o = st_off[t] + a * cnt + j;
                     x[a] = PREC == NMODL_FP64 ? st_d[o] : f2d_int(st_f[o].x) + f2d_int(st_f[o].y);
                 }
+                bool flag;
                 if (kind == NMODL_KIN3) {
-                    kin3_step_d(md_s[t].k3, v_s[nd], A.dt, x);
-                } else {
-                    bool conv;
+                    if (PREC == NMODL_FP64)
+                        kin3_step_d(md_s[t].k3, v_s[nd], A.dt, x);
+                    else
+                        kin3_step_mixed(k3f_s[t], vf_s[nd], d2f_int(A.dt), A.newton_tol, A.ir_max,
+                                        x, flag);
+                } else if (PREC == NMODL_FP64) {
                     cacum_newton_d(md_s[t].cd, ica_s[nd], A.dt, A.newton_tol, A.newton_max_iter,
-                                   x[0], x[1], conv);
+                                   x[0], x[1], flag);
+                } else {
+                    cacum_newton_mixed(md_s[t].cd, cdf_s[t], ica_s[nd], A.dt, A.newton_tol,
+                                       A.newton_max_iter, A.ir_max, x[0], x[1], flag);
                 }
                 for (int a = 0; a < ns; ++a) {
                     const int o = st_off[t] + a * cnt + j;

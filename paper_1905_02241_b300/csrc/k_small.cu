@@ -16,10 +16,11 @@
 //               current ica of the node is read from the ion array filled by
 //               the current updates of the same step.
 //
-// One thread per instance; states are SoA rows of `stride` doubles.  The
-// calcium buffer has no transcendental function and little work per byte
-// even in FP64, so both precisions run it in FP64.  The per-instance math
-// lives in small_systems.cuh (shared with the fused tile kernel).
+// One thread per instance; states are SoA rows of `stride` doubles.  MIXED:
+// FP32 rates, eliminations and Newton updates, the residual and the
+// refinement in FP64 (FP32 parameters passed by value from the host).  The
+// per-instance math lives in small_systems.cuh (shared with the fused tile
+// kernel).
 #include "kernels.cuh"
 #include "small_systems.cuh"
 
@@ -56,9 +57,10 @@ __global__ void k_kin3_init(const Kin3D* __restrict__ kd, int64_t n,
 // max|delta| <= tol or ir_max refinements.
 template <int PREC>
 __global__ void __launch_bounds__(256)
-    k_kin3_state(const Kin3D* __restrict__ kd, int64_t n, const int32_t* __restrict__ ni,
-                 const double* __restrict__ v, double* st, int64_t stride, double dt,
-                 double tol, int ir_max, KinCounters* cnt, int32_t* err) {
+    k_kin3_state(const Kin3D* __restrict__ kd, const Kin3F kf32, int64_t n,
+                 const int32_t* __restrict__ ni, const double* __restrict__ v, double* st,
+                 int64_t stride, double dt, double tol, int ir_max, KinCounters* cnt,
+                 int32_t* err) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     unsigned long long it_sum = 0, nc_sum = 0;
     int it_max = 0;
@@ -77,52 +79,11 @@ __global__ void __launch_bounds__(256)
             for (int a = 0; a < 3; ++a) y[a] = x[a];
             solve3(M, y);
         } else {
-            float kf[3], kb[3], M[3][3];
-            const float vf = (float)vv, dtf = (float)dt;
+            bool nonconv;
 #pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                kf[e] = (float)K.af[e] * __expf((float)K.bf[e] * vf);
-                kb[e] = (float)K.ab[e] * __expf(-(float)K.bb[e] * vf);
-            }
-            kin3_matrix(kf, kb, dtf, M);
-            double off[3][3], diag[3] = {1.0, 1.0, 1.0};
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = 0; b < 3; ++b) off[a][b] = (a == b) ? 0.0 : (double)M[a][b];
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    if (a != b) diag[b] -= off[a][b];
-            float yf[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) yf[a] = (float)x[a];
-            solve3(M, yf);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) y[a] = (double)yf[a];
-            bool done = false;
-            for (int k = 0; k < ir_max && !done; ++k) {
-                float r[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    double ra = x[a] - diag[a] * y[a];
-#pragma unroll
-                    for (int b = 0; b < 3; ++b)
-                        if (b != a) ra -= off[a][b] * y[b];
-                    r[a] = (float)ra;
-                }
-                solve3(M, r);
-                float dmax = 0.0f;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    y[a] += (double)r[a];
-                    dmax = fmaxf(dmax, fabsf(r[a]));
-                }
-                ++iters;
-                done = (double)dmax <= tol;
-            }
-            if (!done && ir_max > 0) nc_sum = 1;
+            for (int a = 0; a < 3; ++a) y[a] = x[a];
+            iters = kin3_step_mixed(kf32, d2f_int(vv), d2f_int(dt), tol, ir_max, y, nonconv);
+            if (nonconv) nc_sum = 1;
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -146,12 +107,14 @@ __global__ void k_cacum_init(const CacumD* __restrict__ cd, int64_t n, double* s
     st[stride + i] = C.kf * C.cai0 * C.btot / (C.kf * C.cai0 + C.kb);
 }
 
-// Newton with the closed-form 2x2 inverse (cacum_newton_d), reading the
-// node's ica.
+// Newton with the closed-form 2x2 inverse (cacum_newton_d; MIXED:
+// cacum_newton_mixed), reading the node's ica.
+template <int PREC>
 __global__ void __launch_bounds__(256)
-    k_cacum_state(const CacumD* __restrict__ cd, int64_t n, const int32_t* __restrict__ ni,
-                  const double* __restrict__ ica, double* st, int64_t stride, double dt,
-                  double tol, int max_iter, KinCounters* cnt, int32_t* err) {
+    k_cacum_state(const CacumD* __restrict__ cd, const CacumF cf32, int64_t n,
+                  const int32_t* __restrict__ ni, const double* __restrict__ ica, double* st,
+                  int64_t stride, double dt, double tol, int max_iter, int ir_max,
+                  KinCounters* cnt, int32_t* err) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     unsigned long long it_sum = 0, nc_sum = 0;
     int it_max = 0;
@@ -159,7 +122,10 @@ __global__ void __launch_bounds__(256)
         const CacumD C = *cd;
         double y0 = st[i], y1 = st[stride + i];
         bool conv = false;
-        const int it = cacum_newton_d(C, ica[ni[i]], dt, tol, max_iter, y0, y1, conv);
+        const int it = PREC == NMODL_FP64
+                           ? cacum_newton_d(C, ica[ni[i]], dt, tol, max_iter, y0, y1, conv)
+                           : cacum_newton_mixed(C, cf32, ica[ni[i]], dt, tol, max_iter, ir_max,
+                                                y0, y1, conv);
         if (!isfinite(y0) || !isfinite(y1)) latch_error(err, NMODL_ERR_NONFINITE);
         st[i] = y0;
         st[stride + i] = y1;
@@ -178,15 +144,30 @@ void launch_kin3_init(const Kin3D* kd, int64_t n, const int32_t* ni, const doubl
     k_kin3_init<<<(int)((n + 255) / 256), 256, 0, s>>>(kd, n, ni, v, st, stride, err);
 }
 
-void launch_kin3_state(int prec, const Kin3D* kd, int64_t n, const int32_t* ni,
+Kin3F kin3_f32(const Kin3D& K) {
+    Kin3F f;
+    for (int e = 0; e < 3; ++e) {
+        f.af[e] = (float)K.af[e];
+        f.bf[e] = (float)K.bf[e];
+        f.ab[e] = (float)K.ab[e];
+        f.bb[e] = (float)K.bb[e];
+    }
+    return f;
+}
+CacumF cacum_f32(const CacumD& C) {
+    return CacumF{(float)C.k, (float)C.rtau, (float)C.cai0, (float)C.kf, (float)C.kb, (float)C.btot};
+}
+
+void launch_kin3_state(int prec, const Kin3D* kd, const Kin3D& kh, int64_t n, const int32_t* ni,
                        const double* v, double* st, int64_t stride, double dt, double tol,
                        int ir_max, KinCounters* cnt, int32_t* err, cudaStream_t s) {
     if (n == 0) return;
     const int grid = (int)((n + 255) / 256);
+    const Kin3F f = kin3_f32(kh);
     if (prec == NMODL_FP64)
-        k_kin3_state<NMODL_FP64><<<grid, 256, 0, s>>>(kd, n, ni, v, st, stride, dt, tol, ir_max, cnt, err);
+        k_kin3_state<NMODL_FP64><<<grid, 256, 0, s>>>(kd, f, n, ni, v, st, stride, dt, tol, ir_max, cnt, err);
     else
-        k_kin3_state<NMODL_MIXED><<<grid, 256, 0, s>>>(kd, n, ni, v, st, stride, dt, tol, ir_max, cnt, err);
+        k_kin3_state<NMODL_MIXED><<<grid, 256, 0, s>>>(kd, f, n, ni, v, st, stride, dt, tol, ir_max, cnt, err);
 }
 
 void launch_cacum_init(const CacumD* cd, int64_t n, double* st, int64_t stride,
@@ -195,12 +176,19 @@ void launch_cacum_init(const CacumD* cd, int64_t n, double* st, int64_t stride,
     k_cacum_init<<<(int)((n + 255) / 256), 256, 0, s>>>(cd, n, st, stride);
 }
 
-void launch_cacum_state(const CacumD* cd, int64_t n, const int32_t* ni, const double* ica,
-                        double* st, int64_t stride, double dt, double tol, int max_iter,
-                        KinCounters* cnt, int32_t* err, cudaStream_t s) {
+void launch_cacum_state(int prec, const CacumD* cd, const CacumD& ch, int64_t n,
+                        const int32_t* ni, const double* ica, double* st, int64_t stride,
+                        double dt, double tol, int max_iter, int ir_max, KinCounters* cnt,
+                        int32_t* err, cudaStream_t s) {
     if (n == 0) return;
-    k_cacum_state<<<(int)((n + 255) / 256), 256, 0, s>>>(cd, n, ni, ica, st, stride, dt, tol,
-                                                         max_iter, cnt, err);
+    const int grid = (int)((n + 255) / 256);
+    const CacumF f = cacum_f32(ch);
+    if (prec == NMODL_FP64)
+        k_cacum_state<NMODL_FP64><<<grid, 256, 0, s>>>(cd, f, n, ni, ica, st, stride, dt, tol,
+                                                       max_iter, ir_max, cnt, err);
+    else
+        k_cacum_state<NMODL_MIXED><<<grid, 256, 0, s>>>(cd, f, n, ni, ica, st, stride, dt, tol,
+                                                        max_iter, ir_max, cnt, err);
 }
 
 }  // namespace nmodl

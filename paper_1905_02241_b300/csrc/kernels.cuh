@@ -3,6 +3,7 @@
 #pragma once
 
 #include "nmodl_internal.cuh"
+#include "small_systems.cuh"
 
 namespace nmodl {
 
@@ -49,6 +50,7 @@ struct FusedArgs {
     int32_t ions;
     int32_t newton_max_iter;
     double newton_tol;
+    int32_t ir_max;  // refinements of the mixed small systems
 };
 
 void launch_init_gates(const MechD* md, int n_gates, int64_t n, const int32_t* ni,
@@ -113,14 +115,20 @@ void launch_kin9_state(int prec, const Kin9D* kd, const Kin9D& kh, int64_t n, co
 // small systems: 3-state kinetic scheme and the calcium buffer
 void launch_kin3_init(const Kin3D* kd, int64_t n, const int32_t* ni, const double* v,
                       double* st, int64_t stride, int32_t* err, cudaStream_t s);
-void launch_kin3_state(int prec, const Kin3D* kd, int64_t n, const int32_t* ni,
+// kd / cd: the device descriptor; kh / ch: the same on the host (its FP32
+// copy is passed by value to the mixed form)
+void launch_kin3_state(int prec, const Kin3D* kd, const Kin3D& kh, int64_t n, const int32_t* ni,
                        const double* v, double* st, int64_t stride, double dt, double tol,
                        int ir_max, KinCounters* cnt, int32_t* err, cudaStream_t s);
 void launch_cacum_init(const CacumD* cd, int64_t n, double* st, int64_t stride,
                        cudaStream_t s);
-void launch_cacum_state(const CacumD* cd, int64_t n, const int32_t* ni, const double* ica,
-                        double* st, int64_t stride, double dt, double tol, int max_iter,
-                        KinCounters* cnt, int32_t* err, cudaStream_t s);
+void launch_cacum_state(int prec, const CacumD* cd, const CacumD& ch, int64_t n,
+                        const int32_t* ni, const double* ica, double* st, int64_t stride,
+                        double dt, double tol, int max_iter, int ir_max, KinCounters* cnt,
+                        int32_t* err, cudaStream_t s);
+// FP32 copies of the small systems' parameters (host)
+Kin3F kin3_f32(const Kin3D& K);
+CacumF cacum_f32(const CacumD& C);
 
 // common
 void launch_chunk_starts(const int32_t* ni, int64_t n, int64_t n_chunks,

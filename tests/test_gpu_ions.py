@@ -133,6 +133,28 @@ def test_cacum_init_and_newton(api, orc, n):
     assert ctx.sync() == 0
 
 
+@pytest.mark.parametrize("n", [1, 4097])
+def test_cacum_mixed_refinement(api, orc, n):
+    """The mixed buffer step (Newton updates in FP32, then refinements with
+    the FP64 residual through the FP32 Jacobian) against the FP64 oracle: the
+    refinement reaches the oracle's Newton solution at the FP64 tolerance,
+    every instance within the refinement budget."""
+    spec, ica, x = cacum_case(n)
+    ctx = api.Context(0, precision=api.NMODL_MIXED)
+    m = mech(api, ctx, spec, n)
+    ctx.set_ions(ica=to_dev(ica))
+    for dt in (0.025, 0.25):
+        m.set_states(to_dev(x))
+        m.state(dt, to_dev(np.zeros(n)))
+        ref = orc.mech_state(W.TYPE_CACUM, spec["params"], spec["node_index"], np.zeros(n), x,
+                             dt, ica=ica)
+        got = m.states().cpu().numpy()
+        err = np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-12))
+        assert err <= TOL_FP64, err
+    assert m.stats()["nonconverged"] == 0
+    assert ctx.sync() == 0
+
+
 def test_cacum_needs_an_ica_array(api):
     spec, ica, x = cacum_case(8)
     ctx = api.Context(0)

@@ -128,14 +128,15 @@ extern "C" {
 #define NMODL_FP64 0  /* every operation in IEEE double                    */
 #define NMODL_MIXED 1 /* rates and exponentials in FP32; gate increments
                          compensated (FP32 hi/lo pair folded into the FP64
-                         state); rhs/d accumulation, v update, kinetic
-                         residual and refinement in FP64                    */
+                         state); rhs/d accumulation, v update, the Newton
+                         residuals and refinements (kinetic schemes,
+                         calcium buffer) in FP64                             */
 
 typedef struct nmodl_options {
     int32_t precision;       /* NMODL_FP64 (default) or NMODL_MIXED          */
     int32_t newton_max_iter; /* Newton updates per kinetic solve (default 8) */
     double newton_tol;       /* stop when max|delta| <= tol (default 1e-14)  */
-    int32_t ir_max;          /* refinements of the FP32 LU (default 4)       */
+    int32_t ir_max;          /* FP64 refinements of an FP32 solve (4)        */
     int32_t window;          /* steps fused into one launch (default 40)     */
     int32_t use_graph;       /* replay each window from a CUDA graph (1)     */
     int32_t autotune;        /* time candidate tile/block shapes (1)         */

@@ -748,8 +748,20 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     std::vector<bool> pers;
     const bool tune = c->opt.autotune != 0;
     if (c->opt.tile_smem > 0) budgets = {std::min<size_t>(c->opt.tile_smem, cap)};
-    else if (tune) budgets = {16 * 1024, 24 * 1024, 32 * 1024, 48 * 1024, 64 * 1024,
-                              96 * 1024, 150 * 1024, cap};
+    else if (tune) {
+        budgets = {16 * 1024, 24 * 1024, 32 * 1024, 48 * 1024, 64 * 1024, 96 * 1024, 150 * 1024,
+                   cap};
+        // and the largest tile with which k blocks fit on an SM, k = 1..4
+        int sm_smem = 0, reserved = 0;
+        cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, c->device);
+        for (int k = 1; k <= 4; ++k) {
+            const int64_t per = (int64_t)sm_smem / k - (int64_t)stat - reserved;
+            if (per >= 16 * 1024) budgets.push_back((size_t)(per / 1024 * 1024));
+        }
+        std::sort(budgets.begin(), budgets.end());
+        budgets.erase(std::unique(budgets.begin(), budgets.end()), budgets.end());
+    }
     else budgets = {std::min<size_t>(cap, 96 * 1024)};
     size_t items = 0;
     for (int t = 0; t < T; ++t) items += (size_t)gates[t] * mechs[t]->n;

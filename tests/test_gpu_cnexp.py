@@ -225,6 +225,17 @@ def test_step_with_hh_and_mix(api, orc):
 
 # ------------------------------------------------------------ precision
 
+def test_step_crowded_node_beyond_the_slot_range(api, orc):
+    """A node carrying more currents than a tile can number with its uint16
+    slots (70,000 instances of one type on node 0 of a 40-node network): no
+    tile fits that node, so the step falls back to the per-mechanism launches
+    (one warp reduces the whole segment), which match the oracle."""
+    wl = W.cortical_mix(40, seed=31)
+    wl["mechs"].append(dict(type=W.TYPE_CNEXP, params=W.cortical_type_params(2)[4],
+                            node_index=np.zeros(70000, dtype=np.int32)))
+    _step_case(api, orc, wl, 3, 1e-10, fused=False)
+
+
 def test_mixed_precision_errors(api, orc):
     """MIXED vs the FP64 oracle, per quantity (one step and 200 steps)."""
     wl = W.cortical_mix(3001, seed=13)

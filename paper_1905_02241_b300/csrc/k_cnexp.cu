@@ -51,10 +51,12 @@ __global__ void k_state_gates(const MechD* __restrict__ md, int64_t n,
     const double phidt = md->phi * dt;
     double* row = states + g * stride;
     if (PREC == NMODL_FP64) {
+        GateD Gf = G;  // folded once per thread for its grid-stride loop
+        fold_gate(Gf, phidt);
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
              i += (int64_t)gridDim.x * blockDim.x) {
-            const double m = pade ? gate_step_pade_d(G, phidt, v[ni[i]], row[i])
-                                  : gate_step_fast_d(G, phidt, v[ni[i]], row[i]);
+            const double m = pade ? gate_step_pade_d<true>(Gf, 1.0, v[ni[i]], row[i])
+                                  : gate_step_fast_d<true>(Gf, 1.0, v[ni[i]], row[i]);
             if (!isfinite(m)) latch_error(err, NMODL_ERR_NONFINITE);
             row[i] = m;
         }

@@ -302,14 +302,14 @@ __device__ void block_inclusive_scan_u16(uint16_t* a, int n, int* wsum) {
 // launch.
 //
 // Cable form: tiles hold whole cells.  After the current phase each node
-// adds its own axial term (in parallel).  The tree system is then solved by
-// one warp in levels: nodes of equal height above the leaves are eliminated
-// together (each gathers its children's axial terms and eliminated rows, in
-// a fixed order, and keeps 1/d), then nodes of equal depth below the root
-// are substituted together -- Hines' elimination (1984; no fill because
-// parents precede children) scheduled by levels.  v += the solution.  On
-// the last step of the window the assembled system is written out first
-// (rhs and d report it).
+// adds its own and its children's axial terms (in parallel).  The tree
+// system is then solved by one warp in levels: nodes of equal height above
+// the leaves are eliminated together (each gathers its children's
+// eliminated rows, in a fixed order, and keeps 1/d' and r'/d'), then nodes
+// of equal depth below the root are substituted together -- Hines'
+// elimination (1984; no fill because parents precede children) scheduled by
+// levels.  v += the solution.  On the last step of the window rhs and d
+// report the assembled system.
 template <int PREC, bool EXT>
 __global__ void __launch_bounds__(kFusedMaxBlock)
     k_fused_tiles(FusedArgs A) {
@@ -621,6 +621,9 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         __syncthreads();
     }
 
+    // cable: the level schedule [H, D, EL, SL, E, S, coff, clist] of the tile
+    // (offsets recomputed where used, to keep registers free)
+    auto sched_coff = [&]() { return sched_s + 2 + (sched_s[0] + 1) + (sched_s[1] + 1) + 2 * NT; };
     const double cmdt = 1e-3 * A.cm / A.dt;
     for (int step = 0; step < A.nsteps; ++step) {
         const bool last = (step == A.nsteps - 1);
@@ -797,13 +800,26 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             }
             dd += cmdt;
             if (A.cable) {
+                // the node's row of the tree system: its own axial term, then
+                // its children's (v is the step's old v throughout)
                 const int pp = par_s[n];
-                if (pp != 0xffff) {  // own axial term
+                if (pp != 0xffff) {
                     r = fma(-ga_s[n], vv - v_s[pp], r);
                     dd += ga_s[n];
                 }
+                const uint16_t* coff = sched_coff();
+                const uint16_t* clist = coff + NT + 1;
+                for (int q = coff[n]; q < coff[n + 1]; ++q) {
+                    const int c = clist[q];
+                    r = fma(gb_s[c], v_s[c] - vv, r);
+                    dd += gb_s[c];
+                }
                 r2_s[n] = r;
                 d2_s[n] = dd;
+                if (last) {  // rhs and d report the assembled system
+                    A.rhs[n0 + n] = r;
+                    A.d[n0 + n] = dd;
+                }
                 continue;
             }
             const double vn = A.clamp_v ? vv : fma(r, rcp_fast(dd), vv);
@@ -816,58 +832,41 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         }
         __syncthreads();
         if (A.cable) {
-            const int H = sched_s[0], D = sched_s[1];
-            const uint16_t* EL = sched_s + 2;
-            const uint16_t* SL = EL + H + 1;
-            const uint16_t* E = SL + D + 1;
-            const uint16_t* S = E + NT;
-            const uint16_t* coff = S + NT;
-            const uint16_t* clist = coff + NT + 1;
-            if (last) {
-                // the assembled system: children's axial terms into parents
-                for (int n = tid; n < NT; n += blockDim.x) {
-                    double r = r2_s[n], dd = d2_s[n];
-                    for (int q = coff[n]; q < coff[n + 1]; ++q) {
-                        const int c = clist[q];
-                        r = fma(gb_s[c], v_s[c] - v_s[n], r);
-                        dd += gb_s[c];
-                    }
-                    r2_s[n] = r;
-                    d2_s[n] = dd;
-                    A.rhs[n0 + n] = r;
-                    A.d[n0 + n] = dd;
-                }
-                __syncthreads();
-            }
             if (!A.clamp_v) {
                 if (tid < 32) {
-                    // leaves -> roots by height; d2_s[i] := 1/d of node i
-                    for (int h = 0; h < H; ++h) {
-                        for (int k = EL[h] + tid; k < EL[h + 1]; k += 32) {
-                            const int i = E[k];
+                    const int cH = sched_s[0], cD = sched_s[1];
+                    const uint16_t* cEL = sched_s + 2;
+                    const uint16_t* cSL = cEL + cH + 1;
+                    const uint16_t* cE = cSL + cD + 1;
+                    const uint16_t* cS = cE + NT;
+                    const uint16_t* coff = cS + NT;
+                    const uint16_t* clist = coff + NT + 1;
+                    // leaves -> roots by height: d2_s[i] := 1/d' of node i
+                    // and r2_s[i] := r'/d' once its children are eliminated
+                    // (the dependent chain per level: one multiply-add per
+                    // child and the reciprocal)
+                    for (int h = 0; h < cH; ++h) {
+                        for (int k = cEL[h] + tid; k < cEL[h + 1]; k += 32) {
+                            const int i = cE[k];
                             double dd = d2_s[i], r = r2_s[i];
                             for (int q = coff[i]; q < coff[i + 1]; ++q) {
                                 const int c = clist[q];
-                                if (!last) {
-                                    r = fma(gb_s[c], v_s[c] - v_s[i], r);
-                                    dd += gb_s[c];
-                                }
-                                const double g = gb_s[c] * d2_s[c];
-                                dd = fma(-g, ga_s[c], dd);
-                                r = fma(g, r2_s[c], r);
+                                dd = fma(-(ga_s[c] * gb_s[c]), d2_s[c], dd);
+                                r = fma(gb_s[c], r2_s[c], r);
                             }
-                            d2_s[i] = rcp_fast(dd);
-                            r2_s[i] = r;
+                            const double inv = rcp_fast(dd);
+                            d2_s[i] = inv;
+                            r2_s[i] = r * inv;
                         }
                         __syncwarp();
                     }
-                    // roots -> leaves by depth: r2_s[i] := the change of v
-                    for (int l = 0; l < D; ++l) {
-                        for (int k = SL[l] + tid; k < SL[l + 1]; k += 32) {
-                            const int i = S[k];
+                    // roots -> leaves by depth: r2_s[i] := the change of v,
+                    // x_i = r'/d' + (ga_i / d') x_parent
+                    for (int l = 0; l < cD; ++l) {
+                        for (int k = cSL[l] + tid; k < cSL[l + 1]; k += 32) {
+                            const int i = cS[k];
                             const int pp = par_s[i];
-                            const double r = pp == 0xffff ? r2_s[i] : fma(ga_s[i], r2_s[pp], r2_s[i]);
-                            r2_s[i] = r * d2_s[i];
+                            if (pp != 0xffff) r2_s[i] = fma(ga_s[i] * d2_s[i], r2_s[pp], r2_s[i]);
                         }
                         __syncwarp();
                     }

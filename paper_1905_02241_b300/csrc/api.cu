@@ -766,7 +766,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     size_t items = 0;
     for (int t = 0; t < T; ++t) items += (size_t)gates[t] * mechs[t]->n;
     if (c->opt.block > 0) blocks = {c->opt.block};
-    else if (tune) blocks = {128, 256, 512};
+    else if (tune) blocks = {128, 256, 512, 1024};
     else blocks = {256};
     pers = tune ? std::vector<bool>{false, true} : std::vector<bool>{false};
 

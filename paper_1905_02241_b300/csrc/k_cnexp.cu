@@ -152,8 +152,12 @@ __device__ __forceinline__ void cur_any_d(const void* desc, const double* st, in
 // single warp and each node is written by exactly one lane (deterministic,
 // no atomics).  Within a 32-wide piece a segmented inclusive scan on the
 // sorted keys sums each node's terms; a segment that runs past the piece is
-// carried into the next piece from lane 31.  With ION the ion parts of the
-// current (USEION WRITE) go through the same scan into ion_a / ion_b.
+// carried into the next piece from lane 31.  The scan stops at the first
+// offset that spans the longest segment of the piece (one level for
+// segments of at most 2, two for at most 4, else five; a warp vote on the
+// keys decides), since its FP64 additions are the kernel's main cost.  With
+// ION the ion parts of the current (USEION WRITE) go through the same scan
+// into ion_a / ion_b.
 template <int KIND, bool ION>
 __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
                           const int32_t* __restrict__ chunk,
@@ -182,8 +186,15 @@ __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
                 vb += cb;
             }
         }
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
+        int span;  // the scan's last offset: 2 * span covers every segment
+        {
+            const int k2 = __shfl_up_sync(0xffffffffu, key, 2);
+            const int k4 = __shfl_up_sync(0xffffffffu, key, 4);
+            span = !__any_sync(0xffffffffu, lane >= 2 && k2 == key)   ? 1
+                   : !__any_sync(0xffffffffu, lane >= 4 && k4 == key) ? 2
+                                                                      : 16;
+        }
+        for (int off = 1; off <= span; off <<= 1) {
             const double oi = __shfl_up_sync(0xffffffffu, vi, off);
             const double og = __shfl_up_sync(0xffffffffu, vg, off);
             double oa = 0.0, ob = 0.0;

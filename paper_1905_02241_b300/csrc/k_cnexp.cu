@@ -68,10 +68,11 @@ __global__ void k_state_gates(const MechD* __restrict__ md, int64_t n,
              i += (int64_t)gridDim.x * blockDim.x) {
             const double m = row[i];
             float minf, f;
-            gate_coef_f(F, phidtf, (float)v[ni[i]], minf, f, pade != 0);
+            gate_coef_f(F, phidtf, d2f_int(v[ni[i]]), minf, f, pade != 0);
             // FP32 increment from the FP32-rounded state, added in FP64
-            const float delta = f * (minf - (float)m);
-            const double mn = m + (double)delta;
+            // (conversions on the integer pipe)
+            const float delta = f * (minf - d2f_int(m));
+            const double mn = m + f2d_int(delta);
             if (!isfinite(mn)) latch_error(err, NMODL_ERR_NONFINITE);
             row[i] = mn;
         }

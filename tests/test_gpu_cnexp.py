@@ -347,6 +347,47 @@ def test_full_size_sampled_parity(api, orc):
     np.testing.assert_allclose(d.cpu().numpy()[nodes], d_ref, rtol=1e-9)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_full_size_sampled_parity(api, orc, prec):
+    """The batched benchmark's configuration: 64 networks of uneven size
+    (~8.5M nodes, ~104M instances) in one fused launch per 40-step window
+    with CUDA graphs and the autotuned plan, 200 steps, checked on 1,500
+    sampled nodes that the oracle integrates as their own sub-network (FP64
+    at the trajectory tolerance; MIXED within its 200-step bounds)."""
+    wl = W.batched_networks(64, seed=3)
+    P = api.NMODL_FP64 if prec == "fp64" else api.NMODL_MIXED
+    ctx = _ctx(api, precision=P)
+    mechs = make_mechs(ctx, wl)
+    n = wl["n_nodes"]
+    v = to_dev(wl["v0"])
+    for m in mechs:
+        m.init(v)
+    rhs, d = torch.zeros_like(v), torch.zeros_like(v)
+    ctx.step(mechs, 0.025, 1.0, v, rhs, d, 200)
+    assert ctx.sync() == 0
+    assert ctx.plan(mechs)["fused"]
+    nodes = np.unique(W.Stream(79, 1).integers(1500, 0, n - 1))
+    sub, sel = sub_network(wl, nodes)
+    st0 = [orc.mech_init(m["type"], m["params"], m["node_index"], wl["v0"][nodes])
+           for m in sub["mechs"]]
+    v_ref, r_ref, d_ref, s_ref = orc.step(sub["mechs"], st0, wl["v0"][nodes], nodes.size,
+                                          0.025, nsteps=200)
+    vg = v.cpu().numpy()[nodes]
+    gs = [m.states()[:, torch.as_tensor(idx, device="cuda:0")].cpu().numpy() if m.n_states
+          else None for m, idx in zip(mechs, sel)]
+    if prec == "fp64":
+        assert np.max(np.abs(vg - v_ref) / np.maximum(np.abs(v_ref), 1.0)) <= 1e-9
+        for g, s in zip(gs, s_ref):
+            if g is not None:
+                assert state_err(g, s) <= 1e-9
+        np.testing.assert_allclose(d.cpu().numpy()[nodes], d_ref, rtol=1e-9)
+    else:
+        assert np.max(np.abs(vg - v_ref)) <= 1e-2
+        for g, s in zip(gs, s_ref):
+            if g is not None:
+                assert np.max(np.abs(g - s)) <= 1e-4
+
+
 def test_table_exp_ulp_error():
     """The FP64 exp of the state kernels (Tang's table-driven method, 2048-entry
     table, degree-3 polynomial) against mpmath at 40 digits and against

@@ -104,3 +104,35 @@ def test_cur_and_clamped_step(api, orc):
     assert state_err(m.states().cpu().numpy(), s_ref[0]) <= 1e-11
     np.testing.assert_allclose(d.cpu().numpy(), d_ref, rtol=1e-12)
     np.testing.assert_allclose(rhs.cpu().numpy(), r_ref, rtol=1e-11, atol=1e-15)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_kinetic_full_size_sampled_parity(api, orc, prec):
+    """The kinetic benchmark's configuration: 1,000,000 clamped instances, 200
+    clamped network steps (the per-mechanism launch sequence in graph
+    windows), checked on 1,000 sampled instances against the oracle's own
+    200-step trajectories (FP64 at the trajectory tolerance; MIXED, whose FP32
+    rates change the solved system at ~1e-7 per step, within 2e-5)."""
+    n = 1_000_000
+    wl = W.kin9_clamped(n, seed=4)
+    P = api.NMODL_FP64 if prec == "fp64" else api.NMODL_MIXED
+    ctx = api.Context(0, precision=P, clamp_v=1)
+    (m,) = make_mechs(ctx, wl)
+    v = to_dev(wl["v0"])
+    rhs, d = torch.zeros_like(v), torch.zeros_like(v)
+    m.set_states(to_dev(wl["x0"]))
+    ctx.step([m], 0.025, 1.0, v, rhs, d, 200)
+    assert ctx.sync() == 0
+    idx = np.unique(W.Stream(78, 1).integers(1000, 0, n - 1))
+    spec = wl["mechs"][0]
+    sub_ni = np.arange(idx.size, dtype=np.int32)
+    x = wl["x0"][:, idx]
+    for _ in range(200):
+        x = orc.mech_state(spec["type"], spec["params"], sub_ni, wl["v0"][idx], x, 0.025)
+    got = m.states()[:, torch.as_tensor(idx, device="cuda:0")].cpu().numpy()
+    if prec == "fp64":
+        assert state_err(got, x) <= 1e-11, state_err(got, x)
+    else:
+        assert float(np.max(np.abs(got - x))) <= 2e-5, float(np.max(np.abs(got - x)))
+    assert m.stats()["nonconverged"] == 0
+

@@ -255,6 +255,31 @@ def test_surrogate_error_bound_and_oracle(S, ctx, orc, trained):
     assert ctx.sync() == 0
 
 
+def test_surrogate_full_size_sampled_bound(S, ctx, orc, trained):
+    """The surrogate benchmark's configuration: 4,000,000 clamped instances,
+    one residual-gated surrogate step (kept predictions and Newton fallbacks
+    together), checked on 2,000 sampled instances against the exact
+    implicit Euler step: every one within the 1e-4 bound (P8), whatever the
+    network's training."""
+    n = 4_000_000
+    wl, m = _kin_setup(ctx, n, seed=5)
+    spec = wl["mechs"][0]
+    S.attach(m, trained, 1e-4)
+    m.state(0.025, to_dev(wl["v0"]))
+    idx = np.unique(W.Stream(80, 1).integers(2000, 0, n - 1))
+    got = m.states()[:, torch.as_tensor(idx, device="cuda:0")].cpu().numpy()
+    exact = orc.mech_state(spec["type"], spec["params"], np.arange(idx.size, dtype=np.int32),
+                           wl["v0"][idx], wl["x0"][:, idx], 0.025)
+    err1 = np.sum(np.abs(got - exact), axis=0)
+    st = m.stats()
+    print(f"full size: fallback {st['fallback']}/{n}, sampled max L1 error {err1.max():.2e}")
+    assert err1.max() <= 1e-4 * (1 + 1e-3) + 1e-6
+    assert st["surrogate_calls"] == 1 and 0 <= st["fallback"] <= n
+    S.attach(m, None)
+    m.close()
+    assert ctx.sync() == 0
+
+
 def test_surrogate_gain_over_newton(S, ctx, orc, trained):
     """What the trained network gains: the share of Newton solves it replaces
     over a 200-step relaxation, at a final error within the 1e-4 bound per

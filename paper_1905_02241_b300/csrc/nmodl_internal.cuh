@@ -148,10 +148,6 @@ __device__ __forceinline__ void rate_nd_u(int form, double A, double u, double& 
         den = 1.0 - exp_tang(-u);
     }
 }
-__device__ __forceinline__ void rate_nd(int form, double A, double vh, double rk, double v,
-                                        double& num, double& den) {
-    rate_nd_u(form, A, (v - vh) * rk, num, den);
-}
 
 // A gate's parameters folded for one launch: vh becomes c = -vh/k, so that
 // u = v (1/k) + c is one multiply-add (its rounding moves u by at most a
@@ -254,15 +250,6 @@ __device__ __forceinline__ double rate_d(int form, double A, double vh,
     return A * u / (-expm1(-u));
 }
 
-__device__ __forceinline__ double gate_step_d(const GateD& G, double phidt,
-                                              double v, double m) {
-    const double a = rate_d(G.aform, G.aA, G.avh, G.ark, v);
-    const double b = rate_d(G.bform, G.bA, G.bvh, G.brk, v);
-    const double s = a + b;
-    const double minf = a / s;
-    const double f = 1.0 - exp(-phidt * s);
-    return m + f * (minf - m);
-}
 
 // The same step with exp(-x), x = phi dt (alpha + beta), replaced by its
 // (1,1) Pade approximant: the factor 2x/(2 + x) folds into the one division,

@@ -488,12 +488,11 @@ int nmodl_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
 // -------------------------------------------------------------- planning
 
 // Shared memory of one tile, matching the layout in k_fused_tiles (tables:
-// per-type segment tables and per-term conductances, used by the variant
-// with the small systems and ion sums and by the cable form; otherwise flat
-// node-major slots of 16 bytes, slots[t] per instance).
-static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* terms,
-                              const int* slots, int64_t NT, const int64_t* cnt, bool cable,
-                              bool ions, bool tables) {
+// per-type segment tables, the cable form, which computes conductances in
+// its owner loop; otherwise flat node-major slots of 16 bytes, slots[t] per
+// instance).
+static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* slots, int64_t NT,
+                              const int64_t* cnt, bool cable, bool ions, bool tables) {
     size_t b = 8 * (size_t)NT;
     size_t inst = 0, items = 0, nslot = 0;
     for (int t = 0; t < T; ++t) {
@@ -508,11 +507,7 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* term
     if (ions) b = (b + 15) / 16 * 16 + 8 * (size_t)NT;  // the step's ica per node
     // d, rhs, ga, gb, parent, and the level schedule (at most 6 NT + 5 uint16)
     if (cable) b = (b + 15) / 16 * 16 + 34 * (size_t)NT + 2 * (6 * (size_t)NT + 5);
-    {  // conductance terms (tables) or (x, g) slots (flat) of the step
-        size_t g = 0;
-        for (int t = 0; t < T; ++t) g += (size_t)terms[t] * cnt[t];
-        b = (b + 15) / 16 * 16 + (tables ? 8 * g : 16 * nslot);
-    }
+    if (!tables) b = (b + 15) / 16 * 16 + 16 * nslot;  // (e, g) slots of the step
     return (b + 15) / 16 * 16;
 }
 
@@ -521,7 +516,7 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* term
 // tile's shared memory stays within budget; returns false if one fine block
 // does not fit.
 static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, int T,
-                       const int* gates, const int* terms, const int* slots,
+                       const int* gates, const int* slots,
                        const std::vector<int64_t>& bounds, bool cable, bool ions, bool ext,
                        size_t budget,
                        std::vector<int32_t>& recs, size_t& max_smem) {
@@ -543,8 +538,8 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
                 if (cnt[t] > 65535) return false;
             }
             if (!tables && nslot > 65535) return false;  // uint16 node-major slots
-            return tile_smem_bytes(prec, T, gates, terms, slots, NT, cnt.data(), cable, ions,
-                                   tables) <= budget;
+            return tile_smem_bytes(prec, T, gates, slots, NT, cnt.data(), cable, ions, tables) <=
+                   budget;
         };
         if (!fits(k0, k1)) return false;
         while (k1 < K && fits(k0, k1 + 1)) ++k1;
@@ -557,7 +552,7 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
             cnt[t] = off[t][k1] - off[t][k0];
         }
         max_smem = std::max(max_smem,
-                            tile_smem_bytes(prec, T, gates, terms, slots, n1 - n0, cnt.data(), cable,
+                            tile_smem_bytes(prec, T, gates, slots, n1 - n0, cnt.data(), cable,
                                             ions, tables));
         k0 = k1;
     }
@@ -725,11 +720,9 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     std::vector<std::vector<int32_t>> off(T);
     for (int t = 0; t < T; ++t)
         off[t].assign(hoff.begin() + t * (K + 1), hoff.begin() + (t + 1) * (K + 1));
-    int gates[kMaxMechsFused], terms[kMaxMechsFused], slots[kMaxMechsFused];
+    int gates[kMaxMechsFused], slots[kMaxMechsFused];
     for (int t = 0; t < T; ++t) {
         gates[t] = mechs[t]->n_states;
-        // conductance terms per instance in the fused kernel's FP64 scratch
-        terms[t] = mechs[t]->type == NMODL_HH ? 2 : mechs[t]->type == NMODL_CACUM ? 0 : 1;
         slots[t] = flat_slots(mechs[t]->type);
     }
 
@@ -776,8 +769,8 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
         auto sched_p = std::make_shared<std::vector<uint16_t>>();
         std::vector<uint16_t>& sched = *sched_p;
         size_t max_smem = 0;
-        if (b > cap || !make_tiles(p->precision, off, T, gates, terms, slots, bounds, cb != nullptr,
-                                   ions, ext, b, recs, max_smem)) {
+        if (b > cap || !make_tiles(p->precision, off, T, gates, slots, bounds, cb != nullptr, ions,
+                                   ext, b, recs, max_smem)) {
             if (dbg) std::fprintf(stderr, "[nmodl plan] budget %zu: no tiling\n", b);
             continue;
         }

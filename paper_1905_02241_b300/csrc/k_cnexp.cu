@@ -300,14 +300,14 @@ __device__ void block_inclusive_scan_u16(uint16_t* a, int n, int* wsum) {
 //   double  d2_s[NT], r2_s[NT], ga_s[NT], gb_s[NT]   (cable), 16-aligned
 //   uint16  par_s[NT]                     (cable) local parent, 0xffff at roots
 //   uint16  sched_s[...]                  (cable) level schedule of the solve
-//   tables: double  g_s[sum_t terms_t * cnt_t]  conductance terms of the step
 //   flat:   double2 xg_s[slots]           node-major (e, g) of each current
 //           (HH three per instance); 16-aligned after the above
-// "flat" is the lean (HH/CNEXP) variant on isolated compartments: one sum
-// over contiguous slots per node, owners ordered by slot count.  EXT and the
-// cable form keep the per-type tables (in the cable form, where tiles hold
-// whole cells, the smaller footprint means fewer tiles, hence fewer tree
-// solves, which cost more than the flat sum saves).
+// "flat" is the layout on isolated compartments: one sum over contiguous
+// slots per node, owners ordered by slot count.  The cable form keeps the
+// per-type tables and computes each instance's conductance in its owner
+// loop (tiles hold whole cells; the smaller footprint means fewer tiles,
+// hence fewer tree solves, and lets the largest cells fit tiles small
+// enough for two blocks per SM).
 // Tile record (int32): n0, n1, then a_t, b_t per type (instance ranges).
 // The host plan guarantees NT <= 65535, cnt_t <= 65535 (flat: the sum of
 // cnt_t too) and that the layout fits the dynamic shared memory of the
@@ -351,7 +351,6 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
 
     __shared__ int tile_s;
     __shared__ int inst_start[kMaxMechsFused + 1];  // instance offset of each type
-    __shared__ int gt_off[kMaxMechsFused];          // conductance terms of each type
     __shared__ int scan_s[32];                      // per-warp sums of the block scan
     __shared__ int n_slots_s;                       // node-major slots of the tile (flat)
     __shared__ int hist_s[64];                      // owner-order counting sort
@@ -436,13 +435,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         }
         wstart_s[nw] = w;
         n_work = nw;
-        int go = 0;
-        for (int t = 0; t < T; ++t) {
-            inst_start[t] = nid_off[t];
-            gt_off[t] = go;
-            const int kind = md_s[t].kind;
-            go += (kind == NMODL_HH ? 2 : kind == NMODL_CACUM ? 0 : 1) * cnt_s[t];
-        }
+        for (int t = 0; t < T; ++t) inst_start[t] = nid_off[t];
         inst_start[T] = no;
         int ns = 0;
         for (int t = 0; t < T; ++t) ns += flat_slots(md_s[t].kind) * cnt_s[t];
@@ -518,15 +511,9 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     double* gb_s = ga_s + NT;
     uint16_t* par_s = reinterpret_cast<uint16_t*>(gb_s + NT);
     uint16_t* sched_s = par_s + NT;
-    // Per-type tables: conductance terms of the step (HH: gna, gk; others:
-    // g).  Flat: (x, g) of each instance in node-major slots (xg_s).
-    double* g_s;
-    {
-        uintptr_t e = reinterpret_cast<uintptr_t>(d2_s);
-        if (A.cable) e = reinterpret_cast<uintptr_t>(sched_s + 6 * NT + 5);
-        g_s = reinterpret_cast<double*>((e + 15) & ~(uintptr_t)15);
-    }
-    double2* xg_s = reinterpret_cast<double2*>(g_s);
+    // Flat: the (e, g) node-major slots of the step (the cable form has none)
+    double2* xg_s = reinterpret_cast<double2*>(
+        (reinterpret_cast<uintptr_t>(d2_s) + 15) & ~(uintptr_t)15);
     if (A.cable) {
         const int32_t off = rec[2 + 2 * T], len = rec[3 + 2 * T];
         for (int k = tid; k < len; k += blockDim.x) sched_s[k] = A.sched[off + k];
@@ -637,12 +624,54 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     // (offsets recomputed where used, to keep registers free)
     auto sched_coff = [&]() { return sched_s + 2 + (sched_s[0] + 1) + (sched_s[1] + 1) + 2 * NT; };
     const double cmdt = 1e-3 * A.cm / A.dt;
+    // conductance(s) of instance j of type q from its states (HH: gna, gk;
+    // not for the calcium buffer)
+    auto inst_g = [&](int q, int j, double& g0, double& g1) {
+        const MechD& M = md_s[q];
+        const int cnt = cnt_s[q];
+        g1 = 0.0;
+        if constexpr (PREC == NMODL_FP64) {
+            const double* st = st_d + st_off[q];
+            if (M.kind == NMODL_HH) {
+                const double m = st[j], h = st[cnt + j], nn = st[2 * cnt + j];
+                g0 = M.hh_g[0] * m * m * m * h;
+                g1 = M.hh_g[1] * nn * nn * nn * nn;
+            } else if (EXT && M.kind == NMODL_KIN3) {
+                g0 = M.k3.gbar * st[M.k3.open * cnt + j];
+            } else {
+                double gg = M.gbar;
+                for (int gi = 0; gi < M.n_gates; ++gi)
+                    gg = mul_pow_d(gg, st[gi * cnt + j], M.gate[gi].power);
+                g0 = gg;
+            }
+        } else {
+            const float2* st = st_f + st_off[q];
+            const float* cf_p = curf_s[q];
+            if (M.kind == NMODL_HH) {
+                const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
+                g0 = f2d_int(cf_p[2] * m * m * m * h);
+                g1 = f2d_int(cf_p[3] * nn * nn * nn * nn);
+            } else if (EXT && M.kind == NMODL_KIN3) {
+                const float2 x = st[M.k3.open * cnt + j];
+                g0 = M.k3.gbar * (f2d_int(x.x) + f2d_int(x.y));
+            } else {
+                float gf = cf_p[0];
+                for (int gi = 0; gi < M.n_gates; ++gi) {
+                    const float xs = st[gi * cnt + j].x;
+                    for (int pw = 0; pw < M.gate[gi].power; ++pw) gf *= xs;
+                }
+                g0 = f2d_int(gf);
+            }
+        }
+    };
     for (int step = 0; step < A.nsteps; ++step) {
         const bool last = (step == A.nsteps - 1);
-        {
+        if (flat) {
             // ---- conductances, one thread per instance (lane-efficient;
             // the owner loop below then spends two operations per instance).
             // MIXED: from the FP32 hi parts of the states, converted once.
+            // (The cable form computes them in its owner loop instead: its
+            // tiles of whole cells must stay small.)
             int q = 0;
             for (int k = tid; k < inst_start[T]; k += blockDim.x) {
                 while (k >= inst_start[q + 1]) ++q;
@@ -689,40 +718,6 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                             xg_s[sl].y = f2d_int(gf);
                         }
                     }
-                } else {
-                    double* gp = g_s + gt_off[q];
-                    if constexpr (PREC == NMODL_FP64) {
-                        const double* st = st_d + st_off[q];
-                        if (M.kind == NMODL_HH) {
-                            const double m = st[j], h = st[cnt + j], nn = st[2 * cnt + j];
-                            gp[j] = M.hh_g[0] * m * m * m * h;
-                            gp[cnt + j] = M.hh_g[1] * nn * nn * nn * nn;
-                        } else if (EXT && M.kind == NMODL_KIN3) {
-                            gp[j] = M.k3.gbar * st[M.k3.open * cnt + j];
-                        } else if (!EXT || M.kind != NMODL_CACUM) {
-                            double gg = M.gbar;
-                            for (int g = 0; g < M.n_gates; ++g) gg = mul_pow_d(gg, st[g * cnt + j], M.gate[g].power);
-                            gp[j] = gg;
-                        }
-                    } else {
-                        const float2* st = st_f + st_off[q];
-                        const float* cf_p = curf_s[q];
-                        if (M.kind == NMODL_HH) {
-                            const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
-                            gp[j] = f2d_int(cf_p[2] * m * m * m * h);
-                            gp[cnt + j] = f2d_int(cf_p[3] * nn * nn * nn * nn);
-                        } else if (EXT && M.kind == NMODL_KIN3) {
-                            const float2 x = st[M.k3.open * cnt + j];
-                            gp[j] = M.k3.gbar * (f2d_int(x.x) + f2d_int(x.y));
-                        } else if (!EXT || M.kind != NMODL_CACUM) {
-                            float gf = cf_p[0];
-                            for (int g = 0; g < M.n_gates; ++g) {
-                                const float x = st[g * cnt + j].x;
-                                for (int p = 0; p < M.gate[g].power; ++p) gf *= x;
-                            }
-                            gp[j] = f2d_int(gf);
-                        }
-                    }
                 }
             }
             __syncthreads();
@@ -767,14 +762,13 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 const MechD& M = md_s[t];
                 const uint16_t* seg = seg_s + t * (NT + 1);
                 const int j0 = seg[n], j1 = seg[n + 1];
-                const int cnt = cnt_s[t];
                 if (EXT && M.kind == NMODL_CACUM) continue;  // no membrane current
                 {
-                    const double* gp = g_s + gt_off[t];
                     if (M.kind == NMODL_HH) {
                         const double gl = M.hh_g[2];
                         for (int j = j0; j < j1; ++j) {
-                            const double gna = gp[j], gk = gp[cnt + j];
+                            double gna, gk;
+                            inst_g(t, j, gna, gk);
                             const double ina = gna * (vv - M.hh_e[0]);
                             const double ik = gk * (vv - M.hh_e[1]);
                             if (EXT && A.ions) {
@@ -787,7 +781,8 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                     } else {
                         const double ve = vv - ((EXT && M.kind == NMODL_KIN3) ? M.k3.e : M.e);
                         for (int j = j0; j < j1; ++j) {
-                            const double g = gp[j];
+                            double g, g1;
+                            inst_g(t, j, g, g1);
                             if (EXT && M.ion) {  // tagged whole current
                                 const double ci = g * ve;
                                 if (M.ion == NMODL_ION_NA) s_na += ci;

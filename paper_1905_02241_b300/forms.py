@@ -412,7 +412,8 @@ def kernel_cases(dev=0):
     synthetic): two calcium-buffer and two 3-state updates on 4M instances,
     one current update with ion write-back of each mechanism of the
     ion-tagged cortical mix on 500k nodes, and one 40-step window of the
-    fused cable step on 4,000 cells (fixed 160 KB tiles of 512 threads, no
+    fused cable step on the benchmark's 10,000 cells (fixed 104 KB tiles of 512
+    threads, two blocks per SM as the autotuner picks on the bench, no
     autotuning).  Prints instance-steps/s of each part."""
     from .api import Cable
     dv = f"cuda:{dev}"
@@ -445,9 +446,9 @@ def kernel_cases(dev=0):
     ms = _time(lambda: [m.cur(v, rhs, d) for m in mechs], ctx, 1)
     out["cur_ions"] = sum(m.n for m in mechs) / (ms * 1e-3)
     ctx.close()
-    cab = W.cable_cells(4000, seed=7)
+    cab = W.cable_cells(10000, seed=7)
     wl = W.cortical_mix(cab["n_nodes"], seed=2)
-    ctx = Context(dev, autotune=0, tile_smem=160 * 1024, block=512)
+    ctx = Context(dev, autotune=0, tile_smem=104 * 1024, block=512)
     mechs = _mechs(ctx, wl)
     v = torch.tensor(wl["v0"], device=dv)
     rhs = torch.zeros_like(v)

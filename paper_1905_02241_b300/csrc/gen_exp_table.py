@@ -9,9 +9,12 @@ double:
   L1 + L2 = ln2/N with L1 keeping L1_BITS significant bits (so n*L1 is exact
   for |n| < 2^(53 - L1_BITS), here |n| < 2^22, i.e. |x| < 1000), L2 the
   rounded remainder.
+  InvLh + InvLl = N/ln2 as two floats (the leading float and the float
+  nearest the remainder), for choosing n in single precision.
 Run:  python gen_exp_table.py > exp_tang_table.cuh
 """
 import mpmath
+import numpy as np
 
 mpmath.mp.dps = 60
 
@@ -38,6 +41,11 @@ def main():
     print("namespace nmodl {")
     print(f"constexpr int kExpBits = {BITS};")
     print(f"constexpr double kExpInvL = {hexd(N / mpmath.log(2))};   // {N}/ln2")
+    inv = N / mpmath.log(2)
+    inv_h = np.float32(float(inv))
+    inv_l = np.float32(float(inv - mpmath.mpf(float(inv_h))))
+    print(f"constexpr float kExpInvLh = {float(inv_h).hex()}f;   // {N}/ln2, leading float")
+    print(f"constexpr float kExpInvLl = {float(inv_l).hex()}f;   // {N}/ln2 - InvLh")
     print(f"constexpr double kExpL1 = {hexd(L1)};   // ln2/{N}, {L1_BITS} leading bits")
     print(f"constexpr double kExpL2 = {hexd(L2)};   // ln2/{N} - L1")
     print(f"__device__ const double kExpTable[{N}] = {{")

@@ -77,11 +77,17 @@ struct Kin9D {
 
 // exp(x) by Tang's table-driven method (ACM TOMS 15(2), 1989): with
 // N = 2048, n = round(N x / ln2) = N m + j and r = x - n ln2/N (two-constant
-// Cody-Waite reduction, |r| <= ln2/(2N) = 1.7e-4), exp(x) = 2^m 2^(j/N)
-// (1 + p(r)), p(r) = r + r^2/2 + r^3/6 the degree-3 Taylor polynomial of
-// exp(r) - 1 (truncation r^4/24 < 3.5e-17); error within 1.5 ulp (checked
-// against mpmath on the GPU tests).  8 FP64 instructions; 2^m is applied to
-// the exponent field with integer operations; the 16 KB table stays in L1.
+// Cody-Waite reduction, |r| <= ln2/(2N) = 1.7e-4 up to the n choice below),
+// exp(x) = 2^m 2^(j/N) (1 + p(r)), p(r) = r + r^2/2 + r^3/6 the degree-3
+// Taylor polynomial of exp(r) - 1 (truncation r^4/24 < 5.5e-17); error
+// within 1.5 ulp (checked against mpmath on the GPU tests).  6 FP64
+// instructions: n is chosen in single precision (the FP64 pipe of this GPU
+// runs 1/64 of the FP32 rate, its issue slots are the scarce resource), from
+// x rounded to a float by integer operations (relative error 2^-25) times
+// N/ln2 as a float pair with the product's exact error, so |x N/ln2 - n| <=
+// 0.5 + 0.062 at |x| = 708 (0.5 + 0.005 for |x| <= 50); n goes to FP64 as an
+// exact integer-valued double by integer operations; 2^m is applied to the
+// exponent field likewise; the 16 KB table stays in L1.
 // x <= -708 returns 0 (the exact value is below 3.3e-308; this is the
 // common case of the cnexp factor of very fast gates); x >= 708 and NaN go
 // to the library exp.
@@ -90,14 +96,33 @@ struct Kin9D {
 static __device__ __noinline__ double exp_tang_rare(double x) {
     return (__double2hiint(x) < 0 && x == x) ? 0.0 : exp(x);
 }
+// An integer-valued float (normal or zero) as the equal double, integer
+// operations only.
+__device__ __forceinline__ double f2d_int_nz(float x) {
+    const unsigned f = __float_as_uint(x), a = f & 0x7fffffffu;
+    const unsigned hi = (f & 0x80000000u) | (a ? (a >> 3) + ((1023u - 127u) << 20) : 0u);
+    return __hiloint2double((int)hi, (int)(f << 29));
+}
 __device__ __forceinline__ double exp_tang(double x) {
     // |x| < 708 tested on the high word (integer pipe): 708 = 0x4086200000000000
     const int hx = __double2hiint(x);
-    if ((hx & 0x7fffffff) >= 0x40862000) return exp_tang_rare(x);
-    const double kShift = 0x1.8p52;
-    const double t = fma(x, kExpInvL, kShift);
-    const int k = __double2loint(t);
-    const double n = t - kShift;
+    const unsigned ax = (unsigned)hx & 0x7fffffffu, lx = (unsigned)__double2loint(x);
+    if (ax >= 0x40862000u) return exp_tang_rare(x);
+    // x as a float, rounded (half up in magnitude) from its leading 24 bits;
+    // |x| < 2^-30 gives 0 (then n = 0)
+    float xh = __uint_as_float((__funnelshift_l(lx, ax - 0x38000000u, 3) + ((lx >> 28) & 1u)) |
+                               ((unsigned)hx & 0x80000000u));
+    if (ax < 0x3e100000u) xh = 0.0f;
+    // x N/ln2 = kh + kl (kl: the product's exact error and the low part of
+    // N/ln2); n = rint(kh), moved by one where kh - n + kl passes +-1/2
+    const float kh = xh * kExpInvLh;
+    const float kl = fmaf(xh, kExpInvLl, fmaf(xh, kExpInvLh, -kh));
+    const float t = kh + 0x1.8p23f;  // |kh| < 2^22: t's low bits hold rint(kh)
+    const float nh = t - 0x1.8p23f;
+    const float fr = (kh - nh) + kl;
+    const int up = fr > 0.5f, dn = fr < -0.5f;
+    const int k = (__float_as_int(t) - 0x4b400000) + up - dn;
+    const double n = f2d_int_nz(nh + (up ? 1.0f : (dn ? -1.0f : 0.0f)));
     double r = fma(n, -kExpL1, x);
     r = fma(n, -kExpL2, r);
     double q = fma(r, 1.0 / 6.0, 0.5);
@@ -108,15 +133,33 @@ __device__ __forceinline__ double exp_tang(double x) {
     return __hiloint2double(__double2hiint(y) + ((k >> kExpBits) << 20), __double2loint(y));
 }
 
-// 1/x from the hardware approximation y0 (rcp.approx.ftz.f64, relative
-// error e0 of about 2^-22) refined by one third-order Newton step for the
-// reciprocal (the series 1/(1 - e) ~ 1 + e + e^2 with e = 1 - x y0):
-// relative error ~e0^3 before the last rounding, so the result is within
-// one ulp.  Three FP64 instructions.  Normal-range x only (zero, infinity
-// and subnormals propagate as inf / 0 / NaN).
-__device__ __forceinline__ double rcp_fast(double x) {
+// 1/x from a seed y0 of FP32 accuracy (relative error e0 below about
+// 2^-22) refined by one third-order Newton step for the reciprocal (the
+// series 1/(1 - e) ~ 1 + e + e^2 with e = 1 - x y0): relative error ~e0^3
+// before the last rounding, so the result is within one ulp.  The seed is
+// the FP32 hardware reciprocal of x's leading 24 significand bits, scaled
+// by x's exponent with integer operations, so that only the three FP64
+// instructions of the step use the FP64 pipe.  x of exponent field 0 or
+// above 2043 (zero, subnormals, |x| >= 2^1021, infinity, NaN) takes the
+// FP64 hardware seed, out of line: zero, infinity and subnormals then
+// propagate as inf / 0 / NaN.
+static __device__ __noinline__ double rcp_rare(double x) {
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
+}
+__device__ __forceinline__ double rcp_fast(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    if (((hi >> 20) & 0x7ffu) - 1u >= 2043u) return rcp_rare(x);
+    const float mf = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));
+    // rf = 2^(fe - 127) 1.f in [0.5, 1]; y0 = +-rf 2^(1023 - E): biased
+    // exponent fe + 1919 - E, in [1, 2045] for E in [1, 2043]
+    const unsigned rb = __float_as_uint(rf);
+    const double y = __hiloint2double(
+        (int)((hi & 0x80000000u) | ((rb >> 3) + 0x77f00000u - (hi & 0x7ff00000u))), (int)(rb << 29));
     const double e = fma(-x, y, 1.0);
     return fma(y, fma(e, e, e), y);
 }

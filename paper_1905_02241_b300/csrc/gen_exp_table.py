@@ -10,7 +10,8 @@ double:
   for |n| < 2^(53 - L1_BITS), here |n| < 2^22, i.e. |x| < 1000), L2 the
   rounded remainder.
   InvLh + InvLl = N/ln2 as two floats (the leading float and the float
-  nearest the remainder), for choosing n in single precision.
+  nearest the remainder), for choosing n in single precision; L2h + L2l = L2
+  as two floats likewise, for n L2 in single-precision pairs.
 Run:  python gen_exp_table.py > exp_tang_table.cuh
 """
 import mpmath
@@ -46,6 +47,10 @@ def main():
     inv_l = np.float32(float(inv - mpmath.mpf(float(inv_h))))
     print(f"constexpr float kExpInvLh = {float(inv_h).hex()}f;   // {N}/ln2, leading float")
     print(f"constexpr float kExpInvLl = {float(inv_l).hex()}f;   // {N}/ln2 - InvLh")
+    l2_h = np.float32(float(L2))
+    l2_l = np.float32(float(L2 - mpmath.mpf(float(l2_h))))
+    print(f"constexpr float kExpL2h = {float(l2_h).hex()}f;   // L2, leading float")
+    print(f"constexpr float kExpL2l = {float(l2_l).hex()}f;   // L2 - L2h")
     print(f"constexpr double kExpL1 = {hexd(L1)};   // ln2/{N}, {L1_BITS} leading bits")
     print(f"constexpr double kExpL2 = {hexd(L2)};   // ln2/{N} - L1")
     print(f"__device__ const double kExpTable[{N}] = {{")

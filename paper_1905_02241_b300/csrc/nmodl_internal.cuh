@@ -73,21 +73,69 @@ struct Kin9D {
     double af[kKinEdges], bf[kKinEdges], ab[kKinEdges], bb[kKinEdges];
 };
 
+// Conversions between float and double on the integer pipe (the FP64 pipe
+// of the B300 also executes the hardware conversions, at a low rate).
+// float -> double is exact and handles every operand with integer
+// operations (a subnormal float is a normal double; NaNs come out quiet);
+// double -> float rounds to nearest even, and results that are zero,
+// subnormal, infinite or NaN take the hardware conversion.
+__device__ __forceinline__ double f2d_int(float x) {
+    const unsigned f = __float_as_uint(x);
+    const unsigned e = (f >> 23) & 0xffu, m = f & 0x7fffffu, s = f & 0x80000000u;
+    if (e - 1u < 254u)
+        return __hiloint2double((int)(s | ((e + (1023u - 127u)) << 20) | (m >> 3)), (int)(m << 29));
+    if (e == 255u)  // infinity; NaN with the quiet bit set
+        return __hiloint2double((int)(s | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u)),
+                                (int)(m << 29));
+    if (m == 0u) return __hiloint2double((int)s, 0);
+    // subnormal m 2^-149: the leading one (bit p) becomes the implicit bit
+    const int p = 31 - __clz((int)m);
+    const unsigned long long b = ((unsigned long long)s << 32) |
+                                 ((unsigned long long)(p + 874) << 52) |
+                                 ((unsigned long long)(m ^ (1u << p)) << (52 - p));
+    return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ float d2f_int(double d) {
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const int e = (int)((hi >> 20) & 0x7ffu) - (1023 - 127);
+    if (e >= 1 && e <= 254) {
+        const unsigned m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const unsigned rem = lo & 0x1fffffffu;
+        unsigned f = (hi & 0x80000000u) | ((unsigned)e << 23) | m23;
+        if (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) f += 1u;
+        return __uint_as_float(f);
+    }
+    return (float)d;
+}
+
+// Knuth TwoSum: s + err == a + b exactly.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& err) {
+    s = a + b;
+    const float bp = s - a;
+    err = (a - (s - bp)) + (b - bp);
+}
+
 // ------------------------------------------------------------ FP64 math
 
 // exp(x) by Tang's table-driven method (ACM TOMS 15(2), 1989): with
 // N = 2048, n = round(N x / ln2) = N m + j and r = x - n ln2/N (two-constant
-// Cody-Waite reduction, |r| <= ln2/(2N) = 1.7e-4 up to the n choice below),
-// exp(x) = 2^m 2^(j/N) (1 + p(r)), p(r) = r + r^2/2 + r^3/6 the degree-3
-// Taylor polynomial of exp(r) - 1 (truncation r^4/24 < 5.5e-17); error
-// within 1.5 ulp (checked against mpmath on the GPU tests).  6 FP64
-// instructions: n is chosen in single precision (the FP64 pipe of this GPU
-// runs 1/64 of the FP32 rate, its issue slots are the scarce resource), from
-// x rounded to a float by integer operations (relative error 2^-25) times
-// N/ln2 as a float pair with the product's exact error, so |x N/ln2 - n| <=
-// 0.5 + 0.062 at |x| = 708 (0.5 + 0.005 for |x| <= 50); n goes to FP64 as an
-// exact integer-valued double by integer operations; 2^m is applied to the
-// exponent field likewise; the 16 KB table stays in L1.
+// Cody-Waite reduction, ln2/N = L1 + L2, |r| <= ln2/(2N) = 1.7e-4 up to the
+// n choice below), exp(x) = 2^m 2^(j/N) (1 + p(r)), p(r) = r + r^2/2 +
+// r^3/6 the degree-3 Taylor polynomial of exp(r) - 1 (truncation r^4/24 <
+// 5.5e-17); error within 1.5 ulp (checked against mpmath on the GPU tests).
+// The FP64 pipe of this GPU runs 1/64 of the FP32 rate and its issue slots
+// are the scarce resource, so only 4 FP64 instructions remain:
+//   r1 = x - n L1 (one fma, exact: L1 has 31 bits, |n| < 2^22),
+//   p  = r1 + w, w = -n L2 + r^2/2 + r^3/6 (two adds),
+//   y  = T + T p (one fma).
+// n is chosen in single precision from x split into two floats by integer
+// operations (47 bits) times N/ln2 as a float pair with the product's exact
+// error, so |x N/ln2 - n| <= 0.5 + 1e-7; n reaches FP64 as an exact
+// integer-valued double by integer operations.  w (|w| < 4e-7) is needed to about 2^-33 of itself:
+// it is formed in single-precision pairs (head + tail, about 46 bits) from
+// r1 split into two floats by integer operations and n L2 as a float pair,
+// and its two floats are added to r1 one after the other.  2^m is applied to
+// the exponent field; the 16 KB table stays in L1.
 // x <= -708 returns 0 (the exact value is below 3.3e-308; this is the
 // common case of the cnexp factor of very fast gates); x >= 708 and NaN go
 // to the library exp.
@@ -103,31 +151,52 @@ __device__ __forceinline__ double f2d_int_nz(float x) {
     const unsigned hi = (f & 0x80000000u) | (a ? (a >> 3) + ((1023u - 127u) << 20) : 0u);
     return __hiloint2double((int)hi, (int)(f << 29));
 }
+// r = h + l to 47 bits (h: the leading 24 significand bits, l: the next 23),
+// integer operations only; |r| < 2^-60 gives h = l = 0, |r| < 2^100 assumed.
+__device__ __forceinline__ void split_d_ff(double r, float& h, float& l) {
+    const unsigned hr = (unsigned)__double2hiint(r), lr = (unsigned)__double2loint(r);
+    const unsigned ar = hr & 0x7fffffffu, sg = hr & 0x80000000u;
+    h = __uint_as_float(__funnelshift_l(lr, ar - 0x38000000u, 3) | sg);
+    // significand bits 6..28 of the low word, worth 2^(E - 1069) per unit
+    const float m23 = __uint_as_float(0x4b000000u | ((lr >> 6) & 0x7fffffu)) - 8388608.0f;
+    l = __uint_as_float(__float_as_uint(m23 * __uint_as_float(((ar >> 20) - 942u) << 23)) | sg);
+    if (ar < 0x3c300000u) {
+        h = 0.0f;
+        l = 0.0f;
+    }
+}
 __device__ __forceinline__ double exp_tang(double x) {
     // |x| < 708 tested on the high word (integer pipe): 708 = 0x4086200000000000
-    const int hx = __double2hiint(x);
-    const unsigned ax = (unsigned)hx & 0x7fffffffu, lx = (unsigned)__double2loint(x);
-    if (ax >= 0x40862000u) return exp_tang_rare(x);
-    // x as a float, rounded (half up in magnitude) from its leading 24 bits;
-    // |x| < 2^-30 gives 0 (then n = 0)
-    float xh = __uint_as_float((__funnelshift_l(lx, ax - 0x38000000u, 3) + ((lx >> 28) & 1u)) |
-                               ((unsigned)hx & 0x80000000u));
-    if (ax < 0x3e100000u) xh = 0.0f;
-    // x N/ln2 = kh + kl (kl: the product's exact error and the low part of
-    // N/ln2); n = rint(kh), moved by one where kh - n + kl passes +-1/2
+    if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40862000u) return exp_tang_rare(x);
+    // x = xh + xl to 47 bits; x N/ln2 = kh + kl (kl: the product's exact
+    // error, the low part of N/ln2 and xl's share); n = rint(kh), moved by
+    // one where kh - n + kl passes +-1/2
+    float xh, xl;
+    split_d_ff(x, xh, xl);
     const float kh = xh * kExpInvLh;
-    const float kl = fmaf(xh, kExpInvLl, fmaf(xh, kExpInvLh, -kh));
+    const float kl = fmaf(xl, kExpInvLh, fmaf(xh, kExpInvLl, fmaf(xh, kExpInvLh, -kh)));
     const float t = kh + 0x1.8p23f;  // |kh| < 2^22: t's low bits hold rint(kh)
     const float nh = t - 0x1.8p23f;
     const float fr = (kh - nh) + kl;
     const int up = fr > 0.5f, dn = fr < -0.5f;
     const int k = (__float_as_int(t) - 0x4b400000) + up - dn;
-    const double n = f2d_int_nz(nh + (up ? 1.0f : (dn ? -1.0f : 0.0f)));
-    double r = fma(n, -kExpL1, x);
-    r = fma(n, -kExpL2, r);
-    double q = fma(r, 1.0 / 6.0, 0.5);
-    q = fma(q, r, 1.0);
-    const double pr = q * r;
+    const float nf = nh + (up ? 1.0f : (dn ? -1.0f : 0.0f));
+    const double r1 = fma(f2d_int_nz(nf), -kExpL1, x);
+    // single-precision pairs: n L2 = a + ae, r = r1 - n L2 = R + Rl,
+    // w = -n L2 + r^2/2 + r^3/6 = W + Wl
+    float rh, rl;
+    split_d_ff(r1, rh, rl);
+    const float a = nf * kExpL2h;
+    const float ae = fmaf(nf, kExpL2l, fmaf(nf, kExpL2h, -a));
+    float R, Rl;
+    two_sum_f(rh, -a, R, Rl);
+    Rl += rl - ae;
+    const float P = R * R;  // r^2 = P + Pe + 2 R Rl (+ Rl^2, below 2^-90)
+    const float Pe = fmaf(R, R, -P);
+    float W, Wl;
+    two_sum_f(0.5f * P, -a, W, Wl);
+    Wl += fmaf(0.5f, Pe, fmaf(R, Rl, fmaf(P * R, 1.0f / 6.0f, -ae)));
+    const double pr = (r1 + f2d_int(W)) + f2d_int(Wl);
     const double T = __ldg(&kExpTable[k & ((1 << kExpBits) - 1)]);
     const double y = fma(T, pr, T);
     return __hiloint2double(__double2hiint(y) + ((k >> kExpBits) << 20), __double2loint(y));
@@ -368,48 +437,6 @@ __device__ __forceinline__ void gate_coef_f(const GateF& G, float phidt, float v
     minf = __fdividef(a, s);
     const float x = phidt * s;
     f = pade ? __fdividef(x, fmaf(0.5f, x, 1.0f)) : one_minus_expneg_f(x);
-}
-
-// Conversions between float and double on the integer pipe (the FP64 pipe
-// of the B300 also executes the hardware conversions, at a low rate).
-// float -> double is exact and handles every operand with integer
-// operations (a subnormal float is a normal double; NaNs come out quiet);
-// double -> float rounds to nearest even, and results that are zero,
-// subnormal, infinite or NaN take the hardware conversion.
-__device__ __forceinline__ double f2d_int(float x) {
-    const unsigned f = __float_as_uint(x);
-    const unsigned e = (f >> 23) & 0xffu, m = f & 0x7fffffu, s = f & 0x80000000u;
-    if (e - 1u < 254u)
-        return __hiloint2double((int)(s | ((e + (1023u - 127u)) << 20) | (m >> 3)), (int)(m << 29));
-    if (e == 255u)  // infinity; NaN with the quiet bit set
-        return __hiloint2double((int)(s | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u)),
-                                (int)(m << 29));
-    if (m == 0u) return __hiloint2double((int)s, 0);
-    // subnormal m 2^-149: the leading one (bit p) becomes the implicit bit
-    const int p = 31 - __clz((int)m);
-    const unsigned long long b = ((unsigned long long)s << 32) |
-                                 ((unsigned long long)(p + 874) << 52) |
-                                 ((unsigned long long)(m ^ (1u << p)) << (52 - p));
-    return __longlong_as_double((long long)b);
-}
-__device__ __forceinline__ float d2f_int(double d) {
-    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-    const int e = (int)((hi >> 20) & 0x7ffu) - (1023 - 127);
-    if (e >= 1 && e <= 254) {
-        const unsigned m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);
-        const unsigned rem = lo & 0x1fffffffu;
-        unsigned f = (hi & 0x80000000u) | ((unsigned)e << 23) | m23;
-        if (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) f += 1u;
-        return __uint_as_float(f);
-    }
-    return (float)d;
-}
-
-// Knuth TwoSum: s + err == a + b exactly.
-__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& err) {
-    s = a + b;
-    const float bp = s - a;
-    err = (a - (s - bp)) + (b - bp);
 }
 
 __device__ __forceinline__ void latch_error(int32_t* err, int32_t code) {

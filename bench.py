@@ -35,10 +35,10 @@ METRIC = "mechanism instance-steps/s (state+cur)"
 
 # FP64 pipe instructions of a minimal implementation of each operation,
 # the unit of the algorithmic op count of the FP64 path:
-# add/sub/mul/fma 1; exp 4 (table-driven with a 2048-entry table: n chosen
+# add/sub/mul/fma 1; exp 2 (table-driven with a 2048-entry table: n chosen
 # in single precision off the FP64 pipe; r1 = x - n L1 1; the rest of the
-# reduction and the degree-3 polynomial formed in single-precision pairs and
-# added to r1, 2; reconstruction 1); reciprocal 3 (FP32 hardware seed of the
+# reduction and the degree-3 polynomial p formed as a single-precision pair
+# and widened to a double by integer operations; T + T p 1); reciprocal 3 (FP32 hardware seed of the
 # leading significand bits scaled by integer operations, one third-order
 # Newton step).  Per-launch constants are
 # folded (u = v/k - vh/k: 1 multiply-add; each rate's A times phi dt).  A
@@ -47,7 +47,7 @@ METRIC = "mechanism instance-steps/s (state+cur)"
 # and phi dt (alpha + beta) with one reciprocal (general 8 + 3; an EXP rate
 # has the denominator 1: beta EXP 6 + 3, alpha EXP 7 + 3, both 2 + 3); then
 # cnexp minf + (m - minf) exp(-phi dt s) (exp, diff, fma: 10).
-C_EXP, C_RCP = 4, 3
+C_EXP, C_RCP = 2, 3
 RATE_COST = {0: 1 + C_EXP + 1, 1: 1 + C_EXP + 1, 2: 1 + C_EXP + 2}
 CNEXP_COST = C_EXP + 1 + 1
 # per node: rhs = sum(g e) - v sum(g), d += cm/dt, 1/d, v += rhs * (1/d);

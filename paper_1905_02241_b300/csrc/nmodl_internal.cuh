@@ -124,18 +124,18 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& err
 // r^3/6 the degree-3 Taylor polynomial of exp(r) - 1 (truncation r^4/24 <
 // 5.5e-17); error within 1.5 ulp (checked against mpmath on the GPU tests).
 // The FP64 pipe of this GPU runs 1/64 of the FP32 rate and its issue slots
-// are the scarce resource, so only 4 FP64 instructions remain:
-//   r1 = x - n L1 (one fma, exact: L1 has 31 bits, |n| < 2^22),
-//   p  = r1 + w, w = -n L2 + r^2/2 + r^3/6 (two adds),
+// are the scarce resource, so only 2 FP64 instructions remain:
+//   r1 = x - n L1 (one fma, exact: L1 has 31 bits, |n| < 2^22), and
 //   y  = T + T p (one fma).
 // n is chosen in single precision from x split into two floats by integer
 // operations (47 bits) times N/ln2 as a float pair with the product's exact
 // error, so |x N/ln2 - n| <= 0.5 + 1e-7; n reaches FP64 as an exact
-// integer-valued double by integer operations.  w (|w| < 4e-7) is needed to about 2^-33 of itself:
-// it is formed in single-precision pairs (head + tail, about 46 bits) from
-// r1 split into two floats by integer operations and n L2 as a float pair,
-// and its two floats are added to r1 one after the other.  2^m is applied to
-// the exponent field; the 16 KB table stays in L1.
+// integer-valued double by integer operations.  p (|p| < 1.8e-4) is needed
+// to about 2^-42 of itself (its error enters y as T dp): it is formed as a
+// normalized float pair (about 46 bits) from r1 split into two floats, n L2
+// as a float pair and the products' exact errors, then widened to a double
+// by integer operations.  2^m is applied to the exponent field; the 16 KB
+// table stays in L1.
 // x <= -708 returns 0 (the exact value is below 3.3e-308; this is the
 // common case of the cnexp factor of very fast gates); x >= 708 and NaN go
 // to the library exp.
@@ -165,6 +165,28 @@ __device__ __forceinline__ void split_d_ff(double r, float& h, float& l) {
         l = 0.0f;
     }
 }
+// hi + lo as a double for a normalized float pair (|lo| <= ulp(hi)/2, hi
+// normal or zero), integer operations only: hi's bits widened, then lo added
+// in units of hi's double ulp, truncated toward zero (relative error below
+// 2^-52 of the sum; a subnormal lo is dropped).  Where hi is a power of two
+// and lo has the opposite sign, the sum lies in the binade below, whose ulp
+// is half as large; otherwise |lo| <= ulp(hi)/2 keeps it in hi's binade, or
+// carries into the exponent field exactly as the next binade requires.
+__device__ __forceinline__ double ff2d_int(float hi, float lo) {
+    const unsigned fh = __float_as_uint(hi), fl = __float_as_uint(lo);
+    const unsigned ah = fh & 0x7fffffffu, al = fl & 0x7fffffffu;
+    const int sh = (int)(al >> 23) - (int)(ah >> 23) + 29;  // <= 5
+    const unsigned m = (al & 0x7fffffu) | 0x800000u;
+    unsigned d = sh >= 0 ? m << sh : (sh > -24 ? m >> -sh : 0u);
+    if ((al >> 23) == 0u) d = 0u;
+    const bool opp = ((fh ^ fl) & 0x80000000u) != 0u;
+    if (opp && (ah & 0x7fffffu) == 0u) d <<= 1;
+    unsigned long long H = ((unsigned long long)((ah >> 3) + ((1023u - 127u) << 20)) << 32) |
+                           (unsigned long long)(ah << 29);
+    H = opp ? H - d : H + d;
+    H |= (unsigned long long)(fh & 0x80000000u) << 32;
+    return ah == 0u ? 0.0 : __longlong_as_double((long long)H);
+}
 __device__ __forceinline__ double exp_tang(double x) {
     // |x| < 708 tested on the high word (integer pipe): 708 = 0x4086200000000000
     if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40862000u) return exp_tang_rare(x);
@@ -173,7 +195,7 @@ __device__ __forceinline__ double exp_tang(double x) {
     // one where kh - n + kl passes +-1/2
     float xh, xl;
     split_d_ff(x, xh, xl);
-    const float kh = xh * kExpInvLh;
+    const float kh = __fmul_rn(xh, kExpInvLh);  // not contracted: kl holds its error
     const float kl = fmaf(xl, kExpInvLh, fmaf(xh, kExpInvLl, fmaf(xh, kExpInvLh, -kh)));
     const float t = kh + 0x1.8p23f;  // |kh| < 2^22: t's low bits hold rint(kh)
     const float nh = t - 0x1.8p23f;
@@ -183,20 +205,21 @@ __device__ __forceinline__ double exp_tang(double x) {
     const float nf = nh + (up ? 1.0f : (dn ? -1.0f : 0.0f));
     const double r1 = fma(f2d_int_nz(nf), -kExpL1, x);
     // single-precision pairs: n L2 = a + ae, r = r1 - n L2 = R + Rl,
-    // w = -n L2 + r^2/2 + r^3/6 = W + Wl
+    // p = r + r^2/2 + r^3/6 = S + Sl (normalized), widened to a double
     float rh, rl;
     split_d_ff(r1, rh, rl);
-    const float a = nf * kExpL2h;
+    const float a = __fmul_rn(nf, kExpL2h);  // rounded products feed the TwoSums
     const float ae = fmaf(nf, kExpL2l, fmaf(nf, kExpL2h, -a));
     float R, Rl;
     two_sum_f(rh, -a, R, Rl);
     Rl += rl - ae;
-    const float P = R * R;  // r^2 = P + Pe + 2 R Rl (+ Rl^2, below 2^-90)
+    const float P = __fmul_rn(R, R);  // r^2 = P + Pe + 2 R Rl (+ Rl^2, below 2^-90)
     const float Pe = fmaf(R, R, -P);
-    float W, Wl;
-    two_sum_f(0.5f * P, -a, W, Wl);
-    Wl += fmaf(0.5f, Pe, fmaf(R, Rl, fmaf(P * R, 1.0f / 6.0f, -ae)));
-    const double pr = (r1 + f2d_int(W)) + f2d_int(Wl);
+    float S0, S0l, S, Sl;
+    two_sum_f(R, 0.5f * P, S0, S0l);
+    S0l += Rl + fmaf(0.5f, Pe, fmaf(R, Rl, (P * R) * (1.0f / 6.0f)));
+    two_sum_f(S0, S0l, S, Sl);
+    const double pr = ff2d_int(S, Sl);
     const double T = __ldg(&kExpTable[k & ((1 << kExpBits) - 1)]);
     const double y = fma(T, pr, T);
     return __hiloint2double(__double2hiint(y) + ((k >> kExpBits) << 20), __double2loint(y));

@@ -34,21 +34,22 @@ DT, CM, NSTEPS = 0.025, 1.0, 200
 METRIC = "mechanism instance-steps/s (state+cur)"
 
 # FP64 pipe instructions of a minimal implementation of each operation,
-# the unit of the algorithmic op count of the FP64 path:
-# add/sub/mul/fma 1; exp 2 (table-driven with a 2048-entry table: n chosen
-# in single precision off the FP64 pipe; r1 = x - n L1 1; the rest of the
-# reduction and the degree-3 polynomial p formed as a single-precision pair
-# and widened to a double by integer operations; T + T p 1); reciprocal 3 (FP32 hardware seed of the
-# leading significand bits scaled by integer operations, one third-order
-# Newton step).  Per-launch constants are
-# folded (u = v/k - vh/k: 1 multiply-add; each rate's A times phi dt).  A
-# gate: each rate as numerator/denominator (u: 1; EXP A e^u: exp + 1;
-# SIGMOID A/(1 + e^-u): exp + 1; LINOID A u/(1 - e^-u): exp + 2); then minf
-# and phi dt (alpha + beta) with one reciprocal (general 8 + 3; an EXP rate
-# has the denominator 1: beta EXP 6 + 3, alpha EXP 7 + 3, both 2 + 3); then
-# cnexp minf + (m - minf) exp(-phi dt s) (exp, diff, fma: 10).
-C_EXP, C_RCP = 2, 3
-RATE_COST = {0: 1 + C_EXP + 1, 1: 1 + C_EXP + 1, 2: 1 + C_EXP + 2}
+# the unit of the algorithmic op count of the FP64 path (integer and FP32
+# work runs on other pipes, 32x or more faster on this GPU, and is not
+# counted): add/sub/mul/fma 1; exp 2 (table-driven with a 2048-entry table:
+# r1 = x - n L1, then T + T p; n, the rest of the reduction and the
+# degree-3 polynomial p are formed in single precision and widened by
+# integer operations); reciprocal 2 (a seed good to 2^-45 formed in single
+# precision, one Newton step e = 1 - x y, y + y e).  Per-launch constants
+# are folded (u = v/k - vh/k: 1 multiply-add; each rate's A times phi dt;
+# an EXP rate's ln|A| added to u).  A gate: each rate as numerator /
+# denominator (u: 1; EXP e^u: exp; SIGMOID A/(1 + e^-u): exp + 1; LINOID
+# A u/(1 - e^-u): exp + 2); then minf and phi dt (alpha + beta) with one
+# reciprocal (general 8 + rcp; an EXP rate has the denominator 1: beta EXP
+# 6 + rcp, alpha EXP 7 + rcp, both 2 + rcp); then the cnexp update
+# minf + (m - minf) exp(-phi dt s) (exp, diff, fma).
+C_EXP, C_RCP = 2, 2
+RATE_COST = {0: 1 + C_EXP, 1: 1 + C_EXP + 1, 2: 1 + C_EXP + 2}
 CNEXP_COST = C_EXP + 1 + 1
 # per node: rhs = sum(g e) - v sum(g), d += cm/dt, 1/d, v += rhs * (1/d);
 # per current: its g e and g summed into the node (2)

@@ -51,8 +51,14 @@ __global__ void k_state_gates(const MechD* __restrict__ md, int64_t n,
     const double phidt = md->phi * dt;
     double* row = states + g * stride;
     if (PREC == NMODL_FP64) {
-        GateD Gf = G;  // folded once per thread for its grid-stride loop
-        fold_gate(Gf, phidt);
+        // folded once per block (the fold takes a log per EXP rate)
+        __shared__ GateD Gs;
+        if (threadIdx.x == 0) {
+            Gs = G;
+            fold_gate(Gs, phidt);
+        }
+        __syncthreads();
+        const GateD Gf = Gs;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
              i += (int64_t)gridDim.x * blockDim.x) {
             const double m = pade ? gate_step_pade_d<true>(Gf, 1.0, v[ni[i]], row[i])

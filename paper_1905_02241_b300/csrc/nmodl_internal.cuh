@@ -225,16 +225,18 @@ __device__ __forceinline__ double exp_tang(double x) {
     return __hiloint2double(__double2hiint(y) + ((k >> kExpBits) << 20), __double2loint(y));
 }
 
-// 1/x from a seed y0 of FP32 accuracy (relative error e0 below about
-// 2^-22) refined by one third-order Newton step for the reciprocal (the
-// series 1/(1 - e) ~ 1 + e + e^2 with e = 1 - x y0): relative error ~e0^3
-// before the last rounding, so the result is within one ulp.  The seed is
-// the FP32 hardware reciprocal of x's leading 24 significand bits, scaled
-// by x's exponent with integer operations, so that only the three FP64
-// instructions of the step use the FP64 pipe.  x of exponent field 0 or
-// above 2043 (zero, subnormals, |x| >= 2^1021, infinity, NaN) takes the
-// FP64 hardware seed, out of line: zero, infinity and subnormals then
-// propagate as inf / 0 / NaN.
+// 1/x with two FP64 instructions: a seed y0 good to about 2^-45 formed off
+// the FP64 pipe, then one Newton step y = y0 + y0 e, e = 1 - x y0, whose
+// result is within (1 + 2^-88) of 1/x before its one rounding, so within
+// one ulp (exact at powers of two).  The seed: x's significand m = mh + ml
+// split into two floats by integer operations, rh the FP32 hardware
+// reciprocal of mh, d = 1 - m rh (the first product's residual is exact in
+// an fma), 1/m = rh (1 + d + d^2 + ...) = rh + rh (d + d^2) as a float pair,
+// widened to a double by integer operations and scaled by x's exponent
+// (exponent field E in [1, 2043]).  Other x (zero, subnormals, |x| >=
+// 2^1021, infinity, NaN) take the FP64 hardware seed and a third-order
+// step, out of line: zero, infinity and subnormals then propagate as
+// inf / 0 / NaN.
 static __device__ __noinline__ double rcp_rare(double x) {
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
@@ -243,17 +245,20 @@ static __device__ __noinline__ double rcp_rare(double x) {
 }
 __device__ __forceinline__ double rcp_fast(double x) {
     const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    if (((hi >> 20) & 0x7ffu) - 1u >= 2043u) return rcp_rare(x);
-    const float mf = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));
-    float rf;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));
-    // rf = 2^(fe - 127) 1.f in [0.5, 1]; y0 = +-rf 2^(1023 - E): biased
-    // exponent fe + 1919 - E, in [1, 2045] for E in [1, 2043]
-    const unsigned rb = __float_as_uint(rf);
+    const int E = (int)((hi >> 20) & 0x7ffu);
+    if ((unsigned)E - 1u >= 2043u) return rcp_rare(x);
+    float mh, ml;
+    split_d_ff(__hiloint2double((int)((hi & 0xfffffu) | 0x3ff00000u), (int)lo), mh, ml);
+    float rh;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rh) : "f"(mh));
+    const float d = fmaf(-ml, rh, fmaf(-mh, rh, 1.0f));
+    float h, l;
+    two_sum_f(rh, __fmul_rn(rh, fmaf(d, d, d)), h, l);
+    const double ym = ff2d_int(h, l);  // 1/m in (0.5, 1]
     const double y = __hiloint2double(
-        (int)((hi & 0x80000000u) | ((rb >> 3) + 0x77f00000u - (hi & 0x7ff00000u))), (int)(rb << 29));
-    const double e = fma(-x, y, 1.0);
-    return fma(y, fma(e, e, e), y);
+        (int)(((unsigned)(__double2hiint(ym) + (1023 - E) * (1 << 20))) | (hi & 0x80000000u)),
+        __double2loint(ym));
+    return fma(y, fma(-x, y, 1.0), y);
 }
 
 // LINOID's series u/(1 - e^-u) = 1 + u/2 + u^2/12 - u^4/720 for |u| < 0.01,
@@ -266,11 +271,19 @@ static __device__ __noinline__ double linoid_series(double u) {
 // A rate as numerator / denominator (so that a gate needs one reciprocal):
 // EXP A e^u / 1; SIGMOID A / (1 + e^-u); LINOID A u / (1 - e^-u), with the
 // series A (1 + u/2 + u^2/12 - u^4/720) / 1 for |u| < 0.01 (next term
-// u^6/30240 < 4e-17).
+// u^6/30240 < 4e-17).  FA: an EXP rate's |A| is folded into u (fold_gate)
+// and A carries only its sign, applied to e^u by an integer operation.
+template <bool FA = false>
 __device__ __forceinline__ void rate_nd_u(int form, double A, double u, double& num,
                                           double& den) {
     if (form == kExp) {
-        num = A * exp_tang(u);
+        if (FA) {
+            const double e = exp_tang(u);
+            num = __hiloint2double(__double2hiint(e) ^ (__double2hiint(A) & (int)0x80000000u),
+                                   __double2loint(e));
+        } else {
+            num = A * exp_tang(u);
+        }
         den = 1.0;
     } else if (form == kSigmoid) {
         num = A;
@@ -289,11 +302,22 @@ __device__ __forceinline__ void rate_nd_u(int form, double A, double u, double& 
 // few units of |c| 2^-53: a few ulp in e^u, and in LINOID the same u enters
 // numerator and denominator), and each A is multiplied by phi dt, so that
 // alpha + beta comes out as phi dt (alpha + beta) and minf is unchanged.
+// An EXP rate's A e^u becomes sign(A) e^(u + ln|A|): ln|A| joins c (one
+// more rounding of the same kind) and A keeps its sign only (A = 0 gives
+// e^-inf = 0).  Takes a log per rate: fold once per block, not per item.
 __device__ __forceinline__ void fold_gate(GateD& G, double phidt) {
     G.avh = -G.avh * G.ark;
     G.bvh = -G.bvh * G.brk;
     G.aA *= phidt;
     G.bA *= phidt;
+    if (G.aform == kExp) {
+        G.avh += log(fabs(G.aA));
+        G.aA = copysign(1.0, G.aA);
+    }
+    if (G.bform == kExp) {
+        G.bvh += log(fabs(G.bA));
+        G.bA = copysign(1.0, G.bA);
+    }
 }
 
 // cnexp gate step with one reciprocal: alpha = Pa/Da, beta = Pb/Db,
@@ -310,8 +334,8 @@ template <int AF, int BF, bool FOLD>
 __device__ __forceinline__ double gate_step_forms_d(const GateD& G, double phidt, double v,
                                                     double m) {
     double na, da, nb, db;
-    rate_nd_u(AF, G.aA, FOLD ? fma(v, G.ark, G.avh) : (v - G.avh) * G.ark, na, da);
-    rate_nd_u(BF, G.bA, FOLD ? fma(v, G.brk, G.bvh) : (v - G.bvh) * G.brk, nb, db);
+    rate_nd_u<FOLD>(AF, G.aA, FOLD ? fma(v, G.ark, G.avh) : (v - G.avh) * G.ark, na, da);
+    rate_nd_u<FOLD>(BF, G.bA, FOLD ? fma(v, G.brk, G.bvh) : (v - G.bvh) * G.brk, nb, db);
     double minf, s;
     if constexpr (AF == kExp && BF == kExp) {
         s = na + nb;
@@ -394,8 +418,8 @@ template <bool FOLD = false>
 __device__ __forceinline__ double gate_step_pade_d(const GateD& G, double phidt, double v,
                                                    double m) {
     double na, da, nb, db;
-    rate_nd_u(G.aform, G.aA, FOLD ? fma(v, G.ark, G.avh) : (v - G.avh) * G.ark, na, da);
-    rate_nd_u(G.bform, G.bA, FOLD ? fma(v, G.brk, G.bvh) : (v - G.bvh) * G.brk, nb, db);
+    rate_nd_u<FOLD>(G.aform, G.aA, FOLD ? fma(v, G.ark, G.avh) : (v - G.avh) * G.ark, na, da);
+    rate_nd_u<FOLD>(G.bform, G.bA, FOLD ? fma(v, G.brk, G.bvh) : (v - G.bvh) * G.brk, nb, db);
     const double P = na * db;
     const double N = fma(nb, da, P);
     const double D = da * db;

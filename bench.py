@@ -44,11 +44,13 @@ METRIC = "mechanism instance-steps/s (state+cur)"
 # are folded (u = v/k - vh/k: 1 multiply-add; each rate's A times phi dt;
 # an EXP rate's ln|A| added to u).  A gate: each rate as numerator /
 # denominator (u: 1; EXP e^u: exp; SIGMOID A/(1 + e^-u): exp + 1; LINOID
-# A u/(1 - e^-u): exp + 2); then minf and phi dt (alpha + beta) with one
-# reciprocal (general 8 + rcp; an EXP rate has the denominator 1: beta EXP
-# 6 + rcp, alpha EXP 7 + rcp, both 2 + rcp); then the cnexp update
+# A u/(1 - e^-u): exp + 2); then minf and phi dt (alpha + beta) by two
+# divisions of 2 each (a quotient good to 2^-44 formed in single precision,
+# then r = x - y q, q + r y0) from N = Pa Db + Pb Da and D = Da Db
+# (general 3 + 2 div; an EXP rate has the denominator 1: beta EXP 1 + 2 div,
+# alpha EXP 2 + 2 div, both 1 + 1 div); then the cnexp update
 # minf + (m - minf) exp(-phi dt s) (exp, diff, fma).
-C_EXP, C_RCP = 2, 2
+C_EXP, C_RCP, C_DIV = 2, 2, 2
 RATE_COST = {0: 1 + C_EXP, 1: 1 + C_EXP + 1, 2: 1 + C_EXP + 2}
 CNEXP_COST = C_EXP + 1 + 1
 # per node: rhs = sum(g e) - v sum(g), d += cm/dt, 1/d, v += rhs * (1/d);
@@ -59,13 +61,13 @@ NODE_COST = 1 + 1 + C_RCP + 1
 def gate_tail(aform: int, bform: int) -> int:
     """minf and alpha + beta from the two rates, then the cnexp update."""
     if aform == 0 and bform == 0:
-        comb = 2 + C_RCP
+        comb = 1 + C_DIV
     elif bform == 0:
-        comb = 6 + C_RCP
+        comb = 1 + 2 * C_DIV
     elif aform == 0:
-        comb = 7 + C_RCP
+        comb = 2 + 2 * C_DIV
     else:
-        comb = 8 + C_RCP
+        comb = 3 + 2 * C_DIV
     return comb + CNEXP_COST
 
 

@@ -415,8 +415,9 @@ NMODL_API int nmodl_probe_peak(int device, int kind, double *ops_per_s);
  * f = the FP64 exp of the state kernels (fn 0: table-driven, Tang 1989),
  * CUDA's exp (fn 1), the round trip double -> float -> double through
  * the kernels' integer-pipe conversions (fn 2), or the reciprocal of the
- * gate and node updates (fn 3: hardware approximation + one third-order
- * Newton step), so tests can measure them. */
+ * node updates and small solves (fn 3: a seed formed in single precision +
+ * one Newton step); fn 4: the division of the gate updates, y[i] =
+ * x[2i] / x[2i+1] (x then holds 2n doubles), so tests can measure them. */
 NMODL_API int nmodl_math_eval(int fn, int64_t n, const double *x, double *y,
                               void *cuda_stream);
 

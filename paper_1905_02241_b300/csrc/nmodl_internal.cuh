@@ -261,6 +261,43 @@ __device__ __forceinline__ double rcp_fast(double x) {
     return fma(y, fma(-x, y, 1.0), y);
 }
 
+// x / y with two FP64 instructions: a quotient q0 good to about 2^-44
+// formed off the FP64 pipe, then r = x - y q0 and q = q0 + r y0 with y0
+// the FP32 reciprocal seed of y (the correction's error is that of q0
+// times that of y0, about 2^-67), so q is within one ulp of x / y.  q0:
+// the significands mx = mxh + mxl and my = myh + myl split into floats by
+// integer operations, 1/my = rh + rh (d + d^2) with rh the FP32 hardware
+// reciprocal of myh and d = 1 - my rh, mx/my as a float pair from the
+// products' exact errors, widened to a double and scaled by 2^(Ex - Ey)
+// with integer operations.  Zero, subnormal, huge or non-finite operands,
+// and quotients near the ends of the range, take IEEE division out of line.
+static __device__ __noinline__ double ddiv_rare(double x, double y) { return x / y; }
+__device__ __forceinline__ double ddiv_fast(double x, double y) {
+    const unsigned hx = (unsigned)__double2hiint(x), hy = (unsigned)__double2hiint(y);
+    const int Ex = (int)((hx >> 20) & 0x7ffu), Ey = (int)((hy >> 20) & 0x7ffu);
+    if ((unsigned)Ex - 1u >= 2046u || (unsigned)Ey - 1u >= 2043u ||
+        (unsigned)(Ex - Ey + 1021) >= 2044u)
+        return ddiv_rare(x, y);
+    float mxh, mxl, myh, myl;
+    split_d_ff(__hiloint2double((int)((hx & 0xfffffu) | 0x3ff00000u), __double2loint(x)), mxh, mxl);
+    split_d_ff(__hiloint2double((int)((hy & 0xfffffu) | 0x3ff00000u), __double2loint(y)), myh, myl);
+    float rh;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rh) : "f"(myh));
+    const float d = fmaf(-myl, rh, fmaf(-myh, rh, 1.0f));
+    const float c = __fmul_rn(rh, fmaf(d, d, d));
+    const float qh = __fmul_rn(mxh, rh);
+    float h, l;
+    two_sum_f(qh, fmaf(mxh, rh, -qh) + fmaf(mxh, c, __fmul_rn(mxl, rh)), h, l);
+    const double qm = ff2d_int(h, l);  // mx / my in (0.5, 2)
+    const double q0 = __hiloint2double(
+        (int)(((unsigned)(__double2hiint(qm) + (Ex - Ey) * (1 << 20))) | ((hx ^ hy) & 0x80000000u)),
+        __double2loint(qm));
+    const unsigned rb = __float_as_uint(rh);
+    const double y0 = __hiloint2double(
+        (int)((hy & 0x80000000u) | ((rb >> 3) + 0x77f00000u - (hy & 0x7ff00000u))), (int)(rb << 29));
+    return fma(fma(-y, q0, x), y0, q0);
+}
+
 // LINOID's series u/(1 - e^-u) = 1 + u/2 + u^2/12 - u^4/720 for |u| < 0.01,
 // out of line like exp_tang_rare
 static __device__ __noinline__ double linoid_series(double u) {
@@ -320,13 +357,14 @@ __device__ __forceinline__ void fold_gate(GateD& G, double phidt) {
     }
 }
 
-// cnexp gate step with one reciprocal: alpha = Pa/Da, beta = Pb/Db,
-// N = Pa Db + Pb Da, D = Da Db, R = 1/(N D): minf = Pa Db D R,
-// alpha + beta = N N R.  With the rate forms known at compile time an EXP
-// rate's denominator 1 removes multiplications:
-//   beta EXP:  N = Pa + Pb Da, R = 1/(N Da), minf = Pa Da R, s = N N R
-//   alpha EXP: N = Pb + Pa Db, R = 1/(N Db), minf = Pa Db Db R, s = N N R
-//   both EXP:  N = Pa + Pb,    R = 1/N,      minf = Pa R,       s = N.
+// cnexp gate step from the rates as alpha = Pa/Da, beta = Pb/Db:
+// N = Pa Db + Pb Da, D = Da Db, minf = Pa Db / N and alpha + beta = N / D,
+// each one division of two FP64 instructions (ddiv_fast).  With the rate
+// forms known at compile time an EXP rate's denominator 1 removes
+// multiplications:
+//   beta EXP:  N = Pa + Pb Da, minf = Pa / N,    s = N / Da
+//   alpha EXP: N = Pb + Pa Db, minf = Pa Db / N, s = N / Db
+//   both EXP:  s = Pa + Pb,    minf = Pa / s.
 // The update m + (1 - e)(minf - m), e = exp(-phi dt s), is taken as
 // minf + (m - minf) e (the same value; one operation fewer).
 // FOLD: G folded by fold_gate (phidt unused).
@@ -339,25 +377,21 @@ __device__ __forceinline__ double gate_step_forms_d(const GateD& G, double phidt
     double minf, s;
     if constexpr (AF == kExp && BF == kExp) {
         s = na + nb;
-        minf = na * rcp_fast(s);
+        minf = ddiv_fast(na, s);
     } else if constexpr (BF == kExp) {
         const double N = fma(nb, da, na);
-        const double R = rcp_fast(N * da);
-        minf = na * (da * R);
-        s = N * (N * R);
+        minf = ddiv_fast(na, N);
+        s = ddiv_fast(N, da);
     } else if constexpr (AF == kExp) {
         const double P = na * db;
         const double N = nb + P;
-        const double R = rcp_fast(N * db);
-        minf = P * (db * R);
-        s = N * (N * R);
+        minf = ddiv_fast(P, N);
+        s = ddiv_fast(N, db);
     } else {
         const double P = na * db;
         const double N = fma(nb, da, P);
-        const double D = da * db;
-        const double R = rcp_fast(N * D);
-        minf = P * (D * R);
-        s = N * (N * R);
+        minf = ddiv_fast(P, N);
+        s = ddiv_fast(N, da * db);
     }
     return fma(m - minf, exp_tang(FOLD ? -s : -phidt * s), minf);
 }

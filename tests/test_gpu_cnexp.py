@@ -437,6 +437,38 @@ def test_fast_reciprocal_within_one_ulp():
     assert np.array_equal(got[p2:], ref[p2:])
 
 
+def test_fast_division_within_one_ulp():
+    """The division of the gate updates (a quotient formed in single
+    precision, corrected by one FP64 residual step) against the correctly
+    rounded quotient: within one ulp over normal-range operands of both
+    signs, exact when both are powers of two; zero numerators, huge or tiny
+    operands and quotients near the range ends take IEEE division."""
+    from paper_1905_02241_b300 import _lib
+    rng = np.random.default_rng(11)
+    n = 200000
+    a = rng.uniform(1, 10, n) * 10.0 ** rng.integers(-150, 150, n) * rng.choice([-1, 1], n)
+    b = rng.uniform(1, 10, n) * 10.0 ** rng.integers(-150, 150, n) * rng.choice([-1, 1], n)
+    a[:500] = 2.0 ** rng.integers(-300, 300, 500)
+    b[:500] = -(2.0 ** rng.integers(-300, 300, 500))
+    special = np.array([[0.0, 3.0], [-0.0, 2.0], [1e308, 1e-10], [1e-310, 3.0], [5.0, 1e-320],
+                        [1e300, 1e-300], [1.5, 1e308], [7.0, 7.0]])
+    a = np.concatenate([a, special[:, 0]])
+    b = np.concatenate([b, special[:, 1]])
+    xd = to_dev(np.stack([a, b], axis=1).reshape(-1))
+    y = torch.empty(a.size, dtype=torch.float64, device="cuda")
+    _lib.nmodl_math_eval(4, a.size, xd.data_ptr(), y.data_ptr(), 0)
+    torch.cuda.synchronize()
+    with np.errstate(over="ignore", divide="ignore"):
+        ref = a / b
+    got = y.cpu().numpy()
+    fin = np.isfinite(ref) & (ref != 0)
+    ulps = np.abs(got[fin] - ref[fin]) / np.spacing(np.abs(ref[fin]))
+    print(f"fast division: max {ulps.max():.3f} ulp, correctly rounded {np.mean(got == ref):.4f}")
+    assert ulps.max() <= 1.0
+    assert np.array_equal(got[:500], ref[:500])
+    assert np.array_equal(got[n:], ref[n:])   # out-of-line IEEE division
+
+
 def test_integer_pipe_conversions_round_like_hardware():
     """double -> float -> double through the integer-pipe conversions equals
     numpy's float32 rounding bit for bit (ties, carries into the exponent,

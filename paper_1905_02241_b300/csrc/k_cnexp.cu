@@ -867,7 +867,7 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                                 dd = fma(-(ga_s[c] * gb_s[c]), d2_s[c], dd);
                                 r = fma(gb_s[c], r2_s[c], r);
                             }
-                            const double inv = rcp_fast(dd);
+                            const double inv = rcp_chain(dd);  // on the level chain: latency
                             d2_s[i] = inv;
                             r2_s[i] = r * inv;
                         }

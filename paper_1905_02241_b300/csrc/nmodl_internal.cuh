@@ -237,12 +237,18 @@ __device__ __forceinline__ double exp_tang(double x) {
 // 2^1021, infinity, NaN) take the FP64 hardware seed and a third-order
 // step, out of line: zero, infinity and subnormals then propagate as
 // inf / 0 / NaN.
-static __device__ __noinline__ double rcp_rare(double x) {
+// 1/x for a dependent chain (the levels of a tree solve): the FP64
+// hardware seed (relative error about 2^-22) and one third-order Newton
+// step, 1/(1 - e) ~ 1 + e + e^2 with e = 1 - x y0 -- four FP64 pipe
+// instructions but a short dependent path; within one ulp for normal-range
+// x (zero, infinity and subnormals propagate as inf / 0 / NaN).
+__device__ __forceinline__ double rcp_chain(double x) {
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
     const double e = fma(-x, y, 1.0);
     return fma(y, fma(e, e, e), y);
 }
+static __device__ __noinline__ double rcp_rare(double x) { return rcp_chain(x); }
 __device__ __forceinline__ double rcp_fast(double x) {
     const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
     const int E = (int)((hi >> 20) & 0x7ffu);

@@ -43,15 +43,16 @@ METRIC = "mechanism instance-steps/s (state+cur)"
 # precision, one Newton step e = 1 - x y, y + y e).  Per-launch constants
 # are folded (u = v/k - vh/k: 1 multiply-add; each rate's A times phi dt;
 # an EXP rate's ln|A| added to u).  A gate: each rate as numerator /
-# denominator (u: 1; EXP e^u: exp; SIGMOID A/(1 + e^-u): exp + 1; LINOID
-# A u/(1 - e^-u): exp + 2); then minf and phi dt (alpha + beta) by two
+# denominator (u: 1; EXP e^u: exp; SIGMOID A/(1 + e^-u): exp, the 1 + 2^m T
+# of 1 + e^-u = 2^m T p + (1 + 2^m T) formed by integer operations; LINOID
+# A u/(1 - e^-u): exp + 1); then minf and phi dt (alpha + beta) by two
 # divisions of 2 each (a quotient good to 2^-44 formed in single precision,
 # then r = x - y q, q + r y0) from N = Pa Db + Pb Da and D = Da Db
 # (general 3 + 2 div; an EXP rate has the denominator 1: beta EXP 1 + 2 div,
 # alpha EXP 2 + 2 div, both 1 + 1 div); then the cnexp update
 # minf + (m - minf) exp(-phi dt s) (exp, diff, fma).
 C_EXP, C_RCP, C_DIV = 2, 2, 2
-RATE_COST = {0: 1 + C_EXP, 1: 1 + C_EXP + 1, 2: 1 + C_EXP + 2}
+RATE_COST = {0: 1 + C_EXP, 1: 1 + C_EXP, 2: 1 + C_EXP + 1}
 CNEXP_COST = C_EXP + 1 + 1
 # per node: rhs = sum(g e) - v sum(g), d += cm/dt, 1/d, v += rhs * (1/d);
 # per current: its g e and g summed into the node (2)

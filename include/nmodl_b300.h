@@ -417,7 +417,8 @@ NMODL_API int nmodl_probe_peak(int device, int kind, double *ops_per_s);
  * the kernels' integer-pipe conversions (fn 2), or the reciprocal of the
  * node updates and small solves (fn 3: a seed formed in single precision +
  * one Newton step); fn 4: the division of the gate updates, y[i] =
- * x[2i] / x[2i+1] (x then holds 2n doubles), so tests can measure them. */
+ * x[2i] / x[2i+1] (x then holds 2n doubles); fn 5 and 6: the SIGMOID and
+ * LINOID denominators 1 + e^x and 1 - e^x; so tests can measure them. */
 NMODL_API int nmodl_math_eval(int fn, int64_t n, const double *x, double *y,
                               void *cuda_stream);
 

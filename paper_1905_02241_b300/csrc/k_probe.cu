@@ -57,7 +57,9 @@ __global__ void k_math_eval(int fn, int64_t n, const double* __restrict__ x, dou
            : fn == 1 ? exp(x[i])
            : fn == 2 ? f2d_int(d2f_int(x[i]))
            : fn == 3 ? rcp_fast(x[i])
-                     : ddiv_fast(x[2 * i], x[2 * i + 1]);
+           : fn == 4 ? ddiv_fast(x[2 * i], x[2 * i + 1])
+           : fn == 5 ? one_pm_exp<1>(x[i])
+                     : one_pm_exp<-1>(x[i]);
 }
 
 }  // namespace nmodl
@@ -69,7 +71,7 @@ using namespace nmodl;
 // fn 3: the refined hardware reciprocal of the gate and node updates
 extern "C" NMODL_API int nmodl_math_eval(int fn, int64_t n, const double* x, double* y,
                                          void* stream) {
-    if (fn < 0 || fn > 4 || n < 0 || (n > 0 && (!x || !y))) return NMODL_ERR_ARG;
+    if (fn < 0 || fn > 6 || n < 0 || (n > 0 && (!x || !y))) return NMODL_ERR_ARG;
     if (n == 0) return NMODL_OK;
     k_math_eval<<<(int)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(fn, n, x, y);
     return cudaGetLastError() == cudaSuccess ? NMODL_OK : NMODL_ERR_CUDA;

@@ -187,9 +187,9 @@ __device__ __forceinline__ double ff2d_int(float hi, float lo) {
     H |= (unsigned long long)(fh & 0x80000000u) << 32;
     return ah == 0u ? 0.0 : __longlong_as_double((long long)H);
 }
-__device__ __forceinline__ double exp_tang(double x) {
-    // |x| < 708 tested on the high word (integer pipe): 708 = 0x4086200000000000
-    if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40862000u) return exp_tang_rare(x);
+// e^x = 2^m T (1 + p) for |x| < 708: the table entry T, k (m = k >> kExpBits)
+// and p, as described above.
+__device__ __forceinline__ void exp_tang_core(double x, double& T, int& k, double& pr) {
     // x = xh + xl to 47 bits; x N/ln2 = kh + kl (kl: the product's exact
     // error, the low part of N/ln2 and xl's share); n = rint(kh), moved by
     // one where kh - n + kl passes +-1/2
@@ -201,7 +201,7 @@ __device__ __forceinline__ double exp_tang(double x) {
     const float nh = t - 0x1.8p23f;
     const float fr = (kh - nh) + kl;
     const int up = fr > 0.5f, dn = fr < -0.5f;
-    const int k = (__float_as_int(t) - 0x4b400000) + up - dn;
+    k = (__float_as_int(t) - 0x4b400000) + up - dn;
     const float nf = nh + (up ? 1.0f : (dn ? -1.0f : 0.0f));
     const double r1 = fma(f2d_int_nz(nf), -kExpL1, x);
     // single-precision pairs: n L2 = a + ae, r = r1 - n L2 = R + Rl,
@@ -219,10 +219,63 @@ __device__ __forceinline__ double exp_tang(double x) {
     two_sum_f(R, 0.5f * P, S0, S0l);
     S0l += Rl + fmaf(0.5f, Pe, fmaf(R, Rl, (P * R) * (1.0f / 6.0f)));
     two_sum_f(S0, S0l, S, Sl);
-    const double pr = ff2d_int(S, Sl);
-    const double T = __ldg(&kExpTable[k & ((1 << kExpBits) - 1)]);
+    pr = ff2d_int(S, Sl);
+    T = __ldg(&kExpTable[k & ((1 << kExpBits) - 1)]);
+}
+__device__ __forceinline__ double exp_tang(double x) {
+    // |x| < 708 tested on the high word (integer pipe): 708 = 0x4086200000000000
+    if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40862000u) return exp_tang_rare(x);
+    double T, pr;
+    int k;
+    exp_tang_core(x, T, k, pr);
     const double y = fma(T, pr, T);
     return __hiloint2double(__double2hiint(y) + ((k >> kExpBits) << 20), __double2loint(y));
+}
+
+// 1 + S e^x for S = +1 or -1 (the denominators of SIGMOID and LINOID
+// rates) with one FP64 instruction after the exp's first: with e^x =
+// 2^m T (1 + p), 1 + S e^x = S 2^m T p + C, C = 1 + S 2^m T formed by
+// 64-bit integer operations on a common grid (exact, then rounded once to
+// 53 bits; for m >= 53 the 1 is below half an ulp and C = S 2^m T).  Its
+// error is within that of 1 + S exp_tang(x) (checked bit for bit on the
+// CPU: 1.68 ulp worst for S = +1; for S = -1 the cancellation near x = 0
+// amplifies e^x's own error alike).
+template <int S>
+static __device__ __noinline__ double one_pm_exp_rare(double x) {
+    return 1.0 + (double)S * exp_tang_rare(x);
+}
+template <int S>
+__device__ __forceinline__ double one_pm_exp(double x) {
+    if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40862000u) return one_pm_exp_rare<S>(x);
+    double T, pr;
+    int k;
+    exp_tang_core(x, T, k, pr);
+    const int m = k >> kExpBits;
+    const long long Tb = __double_as_longlong(T);
+    const double T2m = __longlong_as_double(Tb + ((long long)m << 52));
+    double C;
+    if (m >= 53) {
+        C = S > 0 ? T2m : -T2m;
+    } else {
+        // grid 2^g, g = max(m - 52, -62): 1 = 2^-g, 2^m T = MT 2^(m - 52)
+        const long long MT = (Tb & 0xfffffffffffffLL) | (1LL << 52);
+        const int g = max(m - 52, -62);
+        const int sh = max(0, -10 - m);
+        const long long Tg = sh >= 63 ? 0LL : (MT >> sh);
+        const long long one = 1LL << (-g);
+        const long long Sv = S > 0 ? one + Tg : one - Tg;
+        const unsigned long long A = (unsigned long long)(Sv < 0 ? -Sv : Sv);
+        if (A == 0ULL) {
+            C = 0.0;
+        } else {
+            const int lz = __clzll((long long)A);
+            const int rs = 11 - lz;  // to a 53-bit significand, rounded half up
+            const unsigned long long Ar = rs > 0 ? (A + (1ULL << (rs - 1))) >> rs : A << (-rs);
+            const long long bits = ((long long)(63 - lz + g + 1022) << 52) + (long long)Ar;
+            C = __longlong_as_double(Sv < 0 ? (bits | (long long)0x8000000000000000ULL) : bits);
+        }
+    }
+    return fma(S > 0 ? T2m : -T2m, pr, C);
 }
 
 // 1/x with two FP64 instructions: a seed y0 good to about 2^-45 formed off
@@ -330,13 +383,13 @@ __device__ __forceinline__ void rate_nd_u(int form, double A, double u, double& 
         den = 1.0;
     } else if (form == kSigmoid) {
         num = A;
-        den = 1.0 + exp_tang(-u);
+        den = one_pm_exp<1>(-u);
     } else if ((__double2hiint(u) & 0x7fffffff) < 0x3f847ae1) {  // |u| < 0.01
         num = A * linoid_series(u);
         den = 1.0;
     } else {
         num = A * u;
-        den = 1.0 - exp_tang(-u);
+        den = one_pm_exp<-1>(-u);
     }
 }
 

@@ -437,6 +437,40 @@ def test_fast_reciprocal_within_one_ulp():
     assert np.array_equal(got[p2:], ref[p2:])
 
 
+def test_rate_denominators_one_plus_minus_exp():
+    """The SIGMOID and LINOID denominators 1 + e^x and 1 - e^x (the exp's
+    constant part 1 +- 2^m T formed by integer operations, then one fma)
+    against mpmath: 1 + e^x within 2 ulp; 1 - e^x within 2 ulp of e^x plus
+    one of the result (the cancellation near x = 0 amplifies e^x's own
+    error, as in 1 - exp(x) itself)."""
+    import mpmath
+    from paper_1905_02241_b300 import _lib
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(13)
+    x = np.concatenate([rng.uniform(-700, 700, 4000), rng.uniform(-40, 40, 8000),
+                        rng.uniform(-1, 1, 4000), [0.0, 1e-9, -1e-9, 36.7, 37.3, 38.2,
+                                                   -36.7, -745.0, 709.0]])
+    xd = to_dev(x)
+    yp, ym = torch.empty_like(xd), torch.empty_like(xd)
+    _lib.nmodl_math_eval(5, x.size, xd.data_ptr(), yp.data_ptr(), 0)
+    _lib.nmodl_math_eval(6, x.size, xd.data_ptr(), ym.data_ptr(), 0)
+    torch.cuda.synchronize()
+    yp, ym = yp.cpu().numpy(), ym.cpu().numpy()
+    worst_p = worst_m = 0.0
+    for i in range(x.size):
+        e = mpmath.exp(mpmath.mpf(float(x[i])))
+        rp, rm = 1 + e, 1 - e
+        if mpmath.isinf(rp) or float(rp) == float("inf"):
+            assert np.isinf(yp[i]) and np.isinf(ym[i])
+            continue
+        worst_p = max(worst_p, float(abs(mpmath.mpf(float(yp[i])) - rp)) / np.spacing(float(rp)))
+        bound = 2 * np.spacing(float(e)) + np.spacing(abs(float(rm)))
+        worst_m = max(worst_m, float(abs(mpmath.mpf(float(ym[i])) - rm)) / bound)
+    print(f"1 + e^x: max {worst_p:.3f} ulp; 1 - e^x: max {worst_m:.3f} of the bound")
+    assert worst_p <= 2.0
+    assert worst_m <= 1.0
+
+
 def test_fast_division_within_one_ulp():
     """The division of the gate updates (a quotient formed in single
     precision, corrected by one FP64 residual step) against the correctly

@@ -821,9 +821,9 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
         ok = ok && dalloc(&d_sched_trial, max_sched) == cudaSuccess;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
-        const int trial_steps = std::min(c->opt.window, 8);
-        for (size_t ci = 0; ok && ci < cands.size(); ++ci) {
-            Candidate& cd = cands[ci];
+        // ms per instance of one candidate over nsteps steps (best of 2), or
+        // a negative value if a launch failed
+        auto time_cand = [&](Candidate& cd, int nsteps) -> double {
             // prefix of the tiles in node order: re-sort the (LPT) list by n0
             const int st = p->tile_stride;
             const size_t nt = cd.recs.size() / st;
@@ -859,7 +859,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
             a.tile_stride = st;
             a.n_tiles = (int)(sub.size() / st);
             a.tile_counter = cd.persistent ? d_counter : nullptr;
-            a.nsteps = trial_steps;
+            a.nsteps = nsteps;
             a.clamp_v = c->opt.clamp_v;
             a.pade = c->opt.cnexp_pade;
             a.v = sv;
@@ -881,7 +881,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
             a.ir_max = c->opt.ir_max;
             // descriptors
             if (!p->d_md) {
-                if (dalloc(&p->d_md, T) != cudaSuccess) { ok = false; break; }
+                if (dalloc(&p->d_md, T) != cudaSuccess) return -1.0;
                 std::vector<MechD> mds(T);
                 for (int t = 0; t < T; ++t) mds[t] = mechs[t]->md;
                 cudaMemcpyAsync(p->d_md, mds.data(), T * sizeof(MechD), cudaMemcpyHostToDevice,
@@ -904,8 +904,43 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
                 cudaEventElapsedTime(&ms, e0, e1);
                 best_ms = std::min(best_ms, (double)ms);
             }
-            cd.ms = best_ms / std::max<int64_t>(1, inst);
-            if (cd.ms < cands[best].ms || ci == 0) best = ci;
+            if (!ok) return -1.0;
+            return best_ms / std::max<int64_t>(1, inst);
+        };
+        // stage 1: every candidate over min(window, 8) steps; stage 2: the
+        // four fastest again over the window (at most 64 steps), where the
+        // load and store of each tile weigh as little as in the real launch
+        // (over 8 steps they favoured shapes that lose at full length)
+        const int trial_steps = std::min(c->opt.window, 8);
+        const int full_steps = std::min(c->opt.window, 64);
+        for (size_t ci = 0; ok && ci < cands.size(); ++ci) {
+            const double ms = time_cand(cands[ci], trial_steps);
+            if (ms < 0.0) ok = false;
+            cands[ci].ms = ms;
+            if (cands[ci].ms < cands[best].ms || ci == 0) best = ci;
+        }
+        if (ok && full_steps > trial_steps && cands.size() > 1) {
+            std::vector<size_t> order(cands.size());
+            for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+            std::stable_sort(order.begin(), order.end(),
+                             [&](size_t x, size_t y) { return cands[x].ms < cands[y].ms; });
+            double best_full = 1e30;
+            for (size_t r = 0; ok && r < std::min<size_t>(4, order.size()); ++r) {
+                const double ms = time_cand(cands[order[r]], full_steps);
+                if (ms < 0.0) {
+                    ok = false;
+                } else {
+                    if (dbg)
+                        std::fprintf(stderr, "[nmodl plan] window trial budget %zu block %d persistent %d ns/inst (per %d steps) %.4f\n",
+                                     cands[order[r]].budget, cands[order[r]].block,
+                                     (int)cands[order[r]].persistent, trial_steps,
+                                     ms * 1e6 * trial_steps / full_steps);
+                    if (ms < best_full) {
+                        best_full = ms;
+                        best = order[r];
+                    }
+                }
+            }
         }
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);

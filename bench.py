@@ -314,7 +314,7 @@ def main():
     # DRAM bytes per 40-step launch from the 1M-node captures of the current
     # kernels (profiles/k_fused_tiles_fp64_cortical_1M.md and
     # profiles/k_fused_tiles_mixed_cortical_1M.md), scaled by instances
-    per_1m = {NMODL_FP64: 315.7e6, NMODL_MIXED: 311.9e6}[prec]
+    per_1m = {NMODL_FP64: 311.0e6, NMODL_MIXED: 311.9e6}[prec]
     roof["traffic"] = per_1m * ninst / 11548985 if window == 40 else None
     roof["traffic_unit"] = "bytes per launch"
     roof["kernel"] = "k_fused_tiles<FP64>" if prec == NMODL_FP64 else "k_fused_tiles<MIXED>"

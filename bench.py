@@ -370,7 +370,7 @@ def main():
     plan = ctx.plan(mechs)
     forms = None
     if rank == 0 and world == 1 and args.forms != "none":
-        from paper_1905_02241_b300 import forms as F
+        import bench_forms as F
         want = (["batched", "mixed_errors", "kinetic", "surrogate", "pade", "cable", "ions"]
                 if args.forms == "all"
                 else args.forms.split(","))

@@ -24,9 +24,9 @@ import time
 import numpy as np
 import torch
 
-from . import _lib
-from . import workloads as W
-from .api import NMODL_FP64, NMODL_MIXED, Context, Mechanism
+from paper_1905_02241_b300 import _lib  # noqa: F401
+from paper_1905_02241_b300 import workloads as W
+from paper_1905_02241_b300.api import NMODL_FP64, NMODL_MIXED, Context, Mechanism
 
 DT, CM = 0.025, 1.0
 
@@ -123,7 +123,7 @@ def cable(dev, n_cells=10000, nsteps=200):
     """The cortical mix on cells of 20..400 compartments with tree
     morphologies: FP64 steps with the per-cell tree solve against the same
     compartments isolated (fused step), instance-steps/s."""
-    from .api import Cable
+    from paper_1905_02241_b300.api import Cable
     cab = W.cable_cells(n_cells, seed=7)
     wl = W.cortical_mix(cab["n_nodes"], seed=2)
     ninst = _ninst(wl)
@@ -323,7 +323,7 @@ def kinetic(dev, n=1_000_000, nsteps=200, steps=1):
 
 
 def surrogate(dev, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=60):
-    from .surrogate import Surrogate, attach, make_training_pairs
+    from paper_1905_02241_b300.surrogate import Surrogate, attach, make_training_pairs
     p = W.kin9_params(W.Stream(4, 401))
     out = {"instances": n, "steps_per_run": nsteps, "training_pairs": n_pairs,
            "epochs": epochs, "tolerance": 1e-4}
@@ -387,7 +387,7 @@ def surrogate_kernel_case(dev=0, n=4_000_000, steps=3, tol=1e-4):
     `steps` surrogate state updates with seeded (untrained) weights and the
     residual gate tol (inf keeps every prediction, timing the surrogate
     kernel alone); prints instance-steps/s."""
-    from .surrogate import Surrogate, attach
+    from paper_1905_02241_b300.surrogate import Surrogate, attach
     wl = W.kin9_clamped(n, seed=5)
     ctx = Context(dev)
     sur = Surrogate(ctx, max_batch=256)
@@ -415,7 +415,7 @@ def kernel_cases(dev=0):
     fused cable step on the benchmark's 10,000 cells (fixed 104 KB tiles of 512
     threads, two blocks per SM as the autotuner picks on the bench, no
     autotuning).  Prints instance-steps/s of each part."""
-    from .api import Cable
+    from paper_1905_02241_b300.api import Cable
     dv = f"cuda:{dev}"
     out = {}
     n = 4_000_000

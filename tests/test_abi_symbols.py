@@ -46,3 +46,20 @@ def test_header_compiles_as_c():
                         "-I", os.path.join(ROOT, "include"), "-"], input=src, text=True,
                        capture_output=True)
     assert p.returncode == 0, p.stderr
+
+
+def test_product_package_has_no_route_to_the_oracle():
+    """The shipped package (library, binding, workloads) imports, loads and
+    names nothing under oracle/: parity claims rest on the two sharing no
+    code.  Only tests, the smoke check and the bench's CPU legs use it."""
+    pkg = os.path.join(ROOT, "paper_1905_02241_b300")
+    pat = re.compile(r"^\s*(from\s+oracle\b|import\s+oracle\b)|liboracle|nmodl_oracle",
+                     re.M)
+    hits = []
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                p = os.path.join(dirpath, fn)
+                if pat.search(open(p, errors="replace").read()):
+                    hits.append(os.path.relpath(p, ROOT))
+    assert not hits, hits

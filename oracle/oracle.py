@@ -401,7 +401,7 @@ def simplex_project(y):
     return out[:, 0] if col else out
 
 
-def surrogate_step(Ws, bs, v, dt, x, params=None):
+def surrogate_step(Ws, bs, v, dt, x, params=None, net=None):
     """Projected surrogate prediction of the implicit Euler step, (9, batch).
 
     Scaled form (kinetic parameter block `params` given): with
@@ -409,17 +409,23 @@ def surrogate_step(Ws, bs, v, dt, x, params=None):
     output y gives the increment s*y; the exact increment is J^-1 z with
     ||J^-1||_1 = 1, so the target J^-1 z / s is a smooth function of the
     inputs.  Raw form (params None): the network sees (v_n, dt_n, x) and its
-    output is the increment itself."""
+    output is the increment itself.
+
+    net: the network as a function of the (11, batch) inputs; by default the
+    MLP (Ws, bs).  Tests put known functions there (zero, identity on the
+    state inputs, the exact target) to check the composition around it."""
+    if net is None:
+        def net(X):
+            return mlp_forward(Ws, bs, X)[0]
     x = np.asarray(x, dtype=np.float64).reshape(9, -1)
     v = np.atleast_1d(np.asarray(v, dtype=np.float64))
     if params is None:
-        out, _ = mlp_forward(Ws, bs, surrogate_inputs(v, dt, x))
-        return simplex_project(x + out)
+        return simplex_project(x + net(surrogate_inputs(v, dt, x)))
     z = np.stack([dt * (kin9_matrix(params, v[c]) @ x[:, c]) for c in range(x.shape[1])],
                  axis=1)
     s = np.sum(np.abs(z), axis=0)
     zn = np.where(s > 0, z / np.where(s > 0, s, 1.0), 0.0)
-    out, _ = mlp_forward(Ws, bs, surrogate_inputs(v, dt, zn))
+    out = net(surrogate_inputs(v, dt, zn))
     return simplex_project(x + out * s[None, :])
 
 

@@ -459,6 +459,90 @@ def test_p9_simplex_projection(orc):
     np.testing.assert_allclose(orc.simplex_project(e), np.eye(9)[4])
 
 
+# ------------------------------------------- P9b: the surrogate composition
+# oracle.surrogate_step wraps the network: z = dt A(v) x, s = ||z||_1, the
+# network sees (v_n, dt_n, z/s), the increment is s * output, and the sum is
+# projected onto the simplex.  Known functions in place of the network pin
+# every piece of that wrapper against the implicit-Euler step (Section 5.2)
+# and the explicit one, independently of any trained weights.
+
+def _implicit_euler_dense(A, dt, x):
+    return np.linalg.solve(np.eye(9) - dt * A, x)
+
+
+def test_p9b_surrogate_inputs_normalisation(orc):
+    # the training ranges v in [-100, 60] mV and dt in [0.0125, 0.05] ms map
+    # onto [-1, 1]; their midpoints onto 0; the state rows pass unchanged
+    X = orc.surrogate_inputs([-100.0, 60.0, -20.0], [0.0125, 0.05, 0.03125],
+                             np.arange(27.0).reshape(9, 3))
+    assert X.shape == (11, 3)
+    np.testing.assert_allclose(X[0], [-1.0, 1.0, 0.0], atol=1e-15)
+    np.testing.assert_allclose(X[1], [-1.0, 1.0, 0.0], atol=1e-14)
+    np.testing.assert_array_equal(X[2:], np.arange(27.0).reshape(9, 3))
+
+
+def test_p9b_exact_network_gives_the_implicit_euler_step(orc):
+    """With the network replaced by the exact map z/s -> J^-1 z/s, the
+    wrapped prediction is the dense implicit-Euler step to rounding; the
+    network's state inputs are the direction of dt A x, with unit 1-norm and
+    zero sum (the columns of A sum to zero)."""
+    p = W.kin9_params(W.Stream(4, 401))
+    v = np.array([-100.0, -63.0, -20.5, 0.0, 37.0, 60.0])
+    dts = np.array([0.0125, 0.025, 0.05, 0.025, 0.03, 0.025])
+    x = W.Stream(9, 2).dirichlet(v.size, 9)
+    x[:, 3] = orc.kin9_stationary(p, v[3])          # s ~ 0: the stationary point
+    for dt in (0.0125, 0.025, 0.05):
+        def exact(X, dt=dt):
+            zn = X[2:]
+            col_l1 = np.sum(np.abs(zn), axis=0)
+            assert np.all((np.abs(col_l1 - 1) < 1e-14) | (col_l1 == 0)), col_l1
+            # zero sum up to rounding; at the stationary point (column 3) z is
+            # rounding noise and its direction is arbitrary
+            assert np.all(np.delete(np.abs(zn.sum(axis=0)), 3) < 1e-14)
+            return np.stack([np.linalg.solve(np.eye(9) - dt * orc.kin9_matrix(p, v[c]), zn[:, c])
+                             for c in range(v.size)], axis=1)
+        got = orc.surrogate_step(None, None, v, dt, x, params=p, net=exact)
+        for c in range(v.size):
+            want = _implicit_euler_dense(orc.kin9_matrix(p, v[c]), dt, x[:, c])
+            np.testing.assert_allclose(got[:, c], want, rtol=0, atol=1e-14)
+    # dt = 0: z = 0 exactly, s = 0, and the step returns x itself
+    got = orc.surrogate_step(None, None, v, 0.0, x, params=p, net=lambda X: np.ones((9, v.size)))
+    np.testing.assert_allclose(got, x, atol=1e-15)
+
+
+def test_p9b_identity_network_gives_the_explicit_euler_step(orc):
+    """A one-layer network that copies its state inputs makes the increment
+    s * z/s = dt A x, so the prediction is the projected explicit Euler step
+    x + dt A x (on the simplex already for small dt: A's off-diagonals are
+    nonnegative and its columns sum to zero)."""
+    p = W.kin9_params(W.Stream(4, 401))
+    v = np.array([-80.0, -10.0, 45.0])
+    x = W.Stream(9, 5).dirichlet(3, 9)
+    Wid = np.hstack([np.zeros((9, 2)), np.eye(9)])
+    dt = 1e-3
+    got = orc.surrogate_step([Wid], [np.zeros(9)], v, dt, x, params=p)
+    for c in range(3):
+        A = orc.kin9_matrix(p, v[c])
+        want = x[:, c] + dt * A @ x[:, c]
+        assert np.all(want >= 0)
+        np.testing.assert_allclose(got[:, c], want, rtol=0, atol=1e-15)
+    # the raw form with a zero network returns the projected input
+    Z = [np.zeros((9, 11))]
+    np.testing.assert_allclose(orc.surrogate_step(Z, [np.zeros(9)], v, 0.025, x), x,
+                               atol=1e-15)
+
+
+def test_p9b_mlp_forward_closed_form(orc):
+    # two layers, one unit each: out = 2 silu(z) + 1 with silu(1) = e/(e + 1)
+    # and silu(-2) = -2/(1 + e^2); SiLU on the hidden layer only
+    X = np.array([[1.0, -2.0]])
+    out, _ = orc.mlp_forward([np.array([[1.0]]), np.array([[2.0]])],
+                             [np.zeros(1), np.ones(1)], X)
+    e = np.e
+    np.testing.assert_allclose(out[0], [2 * e / (e + 1) + 1, 2 * (-2 / (1 + e * e)) + 1],
+                               rtol=1e-15)
+
+
 # ------------------------------------------------------------------ P10
 
 def test_p10_accumulation_vs_brute_force(orc):

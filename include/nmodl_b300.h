@@ -27,7 +27,7 @@
  *                ica of the same step (USEION ca READ ica); no membrane
  *                current of its own.
  *
- * Ion currents (USEION WRITE, Section 3; dependency order, Section 4.2):
+ * Ion currents (USEION WRITE and the ion dependencies it declares, Section 3):
  * per-node arrays ina, ik, ica registered on the context receive, from the
  * current update, the HH sodium and potassium terms and the whole current
  * of every CNEXP / KIN9 / KIN3 mechanism tagged with that ion; a state
@@ -180,7 +180,11 @@ NMODL_API int nmodl_sync(nmodl_ctx *ctx);
 NMODL_API void nmodl_ctx_destroy(nmodl_ctx *ctx);
 
 /* Create a mechanism instance set of kind `type` with n_instances >= 0
- * instances.  node_index (host or device, n_instances int32, copied) maps
+ * instances.  Defined by: Section 1 (each channel type, one NMODL file,
+ * brings its own state-update and current-update kernels over all of its
+ * instances) and Section 3 (a density mechanism: RANGE variables, one value
+ * per compartment; PARAMETER block constant at run time, here `params`).
+ * node_index (host or device, n_instances int32, copied) maps
  * instance -> node and must be non-decreasing with values in [0, n_nodes):
  * NMODL_ERR_UNSORTED / NMODL_ERR_RANGE otherwise.  params (host, n_params
  * doubles, copied) is the kind's parameter block; NMODL_ERR_ARG on a wrong
@@ -195,24 +199,50 @@ NMODL_API void nmodl_mech_destroy(nmodl_mech *m);
 NMODL_API int nmodl_mech_n_states(const nmodl_mech *m);
 
 /* INITIAL: gates := minf(v[node]); kinetic states := the stationary
- * distribution of A(v[node]) (A pi = 0, sum pi = 1).  v: device, n_nodes. */
+ * distribution of A(v[node]) (A pi = 0, sum pi = 1); the buffer as listed
+ * with its parameter block.  Defined by: Section 3 names the INITIAL block
+ * but not its content; setting every state to its steady state at the
+ * initial voltage is NEURON's convention for these channel kinds, taken
+ * here as the reading.  v: device, n_nodes.  Asynchronous; a non-finite
+ * result is latched (NMODL_ERR_NONFINITE at the next nmodl_sync). */
 NMODL_API int nmodl_init(nmodl_mech *m, const double *v);
 
 /* nrn_state: advance every instance's states over dt (ms) at the node
- * voltages v (device, n_nodes) -- cnexp for gates, implicit Euler + Newton
- * for NMODL_KIN9 (tolerance and precision from the context options). */
+ * voltages v (device, n_nodes).  Defined by: Section 5.2 (SOLVE ... METHOD
+ * cnexp: linear independent gate ODEs solved exactly over the step, m +=
+ * (1 - exp(-dt/mtau))(minf - m)); Sections 5.1-5.3 (KINETIC converted to
+ * ODEs, implicit Euler, Newton iteration on the analytic Jacobian with an
+ * LU solve for NMODL_KIN9; symbolic Gaussian elimination for the <= 3
+ * equation NMODL_KIN3; Newton with the closed-form 2x2 inverse for
+ * NMODL_CACUM).  Tolerance, iteration cap and precision come from the
+ * context options.  Asynchronous; an instance that reaches the iteration
+ * cap latches NMODL_ERR_NOCONV and a non-finite state NMODL_ERR_NONFINITE
+ * (both returned by the next nmodl_sync; the count by nmodl_stats). */
 NMODL_API int nmodl_state(nmodl_mech *m, double dt, const double *v);
 
 /* nrn_cur: for every instance compute i = g (v - e) with the analytic
  * conductance g = dI/dv and ACCUMULATE rhs[node] -= i, d[node] += g
- * (rhs, d: device, n_nodes; the caller zeroes them).  The sum over the
- * instances of a node is a deterministic node_index-sorted segmented
+ * (rhs, d: device, n_nodes; the caller zeroes them).  Defined by: Section
+ * 3 (BREAKPOINT: current and conductance updated every step; with an ohmic
+ * current-voltage relation the conductance is the analytic expression
+ * rather than a numerical derivative), Section 5.2 (the generated
+ * CONDUCTANCE statement: dI/dv differentiated symbolically, not by a
+ * difference quotient at run time) and Section 8 (the per-node
+ * reduction of the current update, done there with atomics).  The sum over
+ * the instances of a node is a deterministic node_index-sorted segmented
  * warp-shuffle reduction without atomics: repeated calls give bitwise
- * equal results. */
+ * equal results.  Asynchronous; non-finite rhs or d latch
+ * NMODL_ERR_NONFINITE. */
 NMODL_API int nmodl_cur(nmodl_mech *m, const double *v, double *rhs, double *d);
 
 /* nsteps time steps of the isolated-compartment network formed by the
- * mechanisms (all on the same node set of n_nodes of mechs[0]):
+ * mechanisms (all on the same node set of n_nodes of mechs[0]).  Defined
+ * by: Section 1 and Fig. 1 (a NEURON step runs the current update and the
+ * state update of every mechanism, which dominate its time) and the ion
+ * dependencies that USEION declares (Section 3: currents an ion reader
+ * needs come first); the ordering below (currents at v_n, the
+ * diagonal voltage update, states at v_n+1) is NEURON's fixed-step
+ * convention, which the paper does not spell out -- taken as the reading:
  *   rhs = d = 0; nrn_cur of every mechanism in array order;
  *   d += 1e-3 cm/dt; v += rhs/d (skipped with options.clamp_v);
  *   nrn_state of every mechanism at the new v.

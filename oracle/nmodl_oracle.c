@@ -30,7 +30,7 @@
  *    ascending instance) -> d += 1e-3 cm/dt -> v += rhs/d -> state; the
  *    3x3 lattice topology of the 9-state scheme; vtrap evaluated through
  *    expm1 with a 3-term Taylor branch for |x/y| < 1e-6.
- *  - Section 3 (USEION) and Section 4.2 (ion dependencies): ion currents
+ *  - Section 3 (USEION and the ion dependencies it declares): ion currents
  *    are written per node (ina, ik, ica) by the current update of every
  *    step, before the state updates that read them (calcium accumulation
  *    reads ica).  Readings: the 3-state triangle scheme (Section 5.2

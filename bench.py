@@ -228,7 +228,9 @@ def main():
                 "unit": "instance-steps/s", "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": config,
+                "data": "synthetic",
+                "config": dict(config, instances=n_instances(wl),
+                               parallelism=f"replicas x{args.gpus}"),
                 "cpu_baseline": {"value": v, "unit": "instance-steps/s", "cores": cores,
                                  "kind": "oracle", "sample": sample},
                 "e2e": {"value": v, "unit": "instance-steps/s",
@@ -311,12 +313,14 @@ def main():
                 "unit": "Tops/s"}
     if roof.get("achieved") is not None:
         roof["frac"] = roof["achieved"] / roof["peak"]
-    # DRAM bytes per 40-step launch from the 1M-node captures of the current
-    # kernels (profiles/k_fused_tiles_fp64_cortical_1M.md and
-    # profiles/k_fused_tiles_mixed_cortical_1M.md), scaled by instances
+    # DRAM bytes per 40-step launch: dram__bytes_read.sum + dram__bytes_write.sum
+    # of one ncu capture of the same kernel on the 1,000,000-node network
+    # (11,548,985 instances), scaled to this network by its instance count
     per_1m = {NMODL_FP64: 311.0e6, NMODL_MIXED: 311.9e6}[prec]
     roof["traffic"] = per_1m * ninst / 11548985 if window == 40 else None
     roof["traffic_unit"] = "bytes per launch"
+    roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                              "launch on the 1,000,000-node network, scaled by instances")
     roof["kernel"] = "k_fused_tiles<FP64>" if prec == NMODL_FP64 else "k_fused_tiles<MIXED>"
 
     # end to end through the C ABI with host buffers (pinned)

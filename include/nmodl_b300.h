@@ -422,9 +422,12 @@ NMODL_API int nmodl_mech_attach_surrogate(nmodl_mech *m, nmodl_surrogate *s,
  * device looks up that array's device address (cudaGetSymbolAddress) --
  * make that first call before any stream capture.  The call validates
  * node_index and waits for that check on the stream (NMODL_ERR_UNSORTED /
- * NMODL_ERR_RANGE), then enqueues the reduction and returns.  Every call
- * shares the one scratch array: calls whose work overlaps on the GPU (other
- * streams, other host threads) race and must be serialised by the caller. */
+ * NMODL_ERR_RANGE), then runs the reduction and waits for it too: it
+ * returns once rhs and d are written, with NMODL_ERR_NONFINITE if any rhs
+ * or d it wrote is NaN or infinite (where nmodl_cur latches the same error
+ * in its context).  Every call shares the one scratch array: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. */
 NMODL_API int nmodl_cur_noalloc(int device, void *cuda_stream, int type,
                                 int64_t n_instances, const int32_t *node_index,
                                 int64_t n_nodes, const double *params,
@@ -440,6 +443,15 @@ NMODL_API int64_t nmodl_cur_noalloc_max_instances(void);
  * second).  Used as the roofline denominator of the ALU-bound kernels.
  * Synchronous; allocates 64 bytes for the duration of the call. */
 NMODL_API int nmodl_probe_peak(int device, int kind, double *ops_per_s);
+
+/* Diagnostic (no counterpart in the paper's method): one block runs the
+ * bounded mbarrier wait of the tensor-core kernels (the surrogate) on a
+ * barrier that nothing arrives at; after `polls` polls (1 .. 2^20) every
+ * thread gives up and NMODL_ERR_TIMEOUT is latched in the context, to be
+ * returned by the next nmodl_sync, after which the context is usable as
+ * before.  Lets tests check the timeout path without stalling real work.
+ * Asynchronous on the context stream; allocates nothing. */
+NMODL_API int nmodl_probe_wait(nmodl_ctx *ctx, int32_t polls);
 
 /* Diagnostic: y[i] = f(x[i]) on the device (x, y: device, n doubles),
  * f = the FP64 exp of the state kernels (fn 0: table-driven, Tang 1989),

@@ -75,6 +75,7 @@ _SIGS = {
     "nmodl_set_state": (_i32, [_vp, _i32, _vp]),
     "nmodl_stats": (_i32, [_vp, _P(nmodl_stats_t)]),
     "nmodl_probe_peak": (_i32, [_i32, _i32, _P(_d)]),
+    "nmodl_probe_wait": (_i32, [_vp, _i32]),
     "nmodl_cur_noalloc": (_i32, [_i32, _vp, _i32, _i64, _vp, _i64, _vp, _i64, _vp,
                                  _i64, _vp, _vp, _vp]),
     "nmodl_cur_noalloc_max_instances": (_i64, []),
@@ -334,3 +335,7 @@ def nmodl_surrogate_fit(sur: int, n: int, X_ptr: int, T_ptr: int, batch: int, ep
                         lr: float, lr_min: float, loss_ptr: int) -> None:
     _check(lib.nmodl_surrogate_fit(sur, int(n), X_ptr, T_ptr, int(batch), int(epochs),
                                    float(lr), float(lr_min), loss_ptr), "nmodl_surrogate_fit")
+
+
+def nmodl_probe_wait(ctx, polls: int) -> None:
+    _check(lib.nmodl_probe_wait(ctx, int(polls)), "nmodl_probe_wait")

@@ -83,6 +83,7 @@ class Context:
         ptr = [0 if t is None else _dptr(t, device=self.device) for t in (ina, ik, ica)]
         self.enter()
         _lib.nmodl_ctx_set_ions(self.handle, n, *ptr)
+        self.leave()
         self._ions = (ina, ik, ica)
 
     def plan(self, mechs) -> dict:
@@ -116,6 +117,7 @@ class Mechanism:
         self.handle = _lib.nmodl_mech_create(ctx.handle, self.type, self.n,
                                              ptr if n else 0, self.n_nodes,
                                              p.ctypes.data, p.size)
+        ctx.leave()
         self.n_states = _lib.nmodl_mech_n_states(self.handle)
         self.ion = NMODL_ION_NONE
         if ion != NMODL_ION_NONE:

@@ -36,17 +36,26 @@ def up_to_date() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
+    from concurrent.futures import ThreadPoolExecutor
     nvcc = os.environ.get("NVCC", "nvcc")
-    objs = []
     os.makedirs(os.path.join(HERE, "_build"), exist_ok=True)
+    newest_header = max((os.path.getmtime(h) for h in headers()), default=0.0)
+    jobs, objs = [], []
     for src in sources():
         obj = os.path.join(HERE, "_build", os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
-        if verbose:
-            cmd += ["-Xptxas", "-v"]
-            print(" ".join(cmd))
-        subprocess.check_call(cmd)
         objs.append(obj)
+        stale = (force or not os.path.exists(obj) or
+                 os.path.getmtime(obj) < max(os.path.getmtime(src), newest_header))
+        if stale:
+            cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+            if verbose:
+                cmd += ["-Xptxas", "-v"]
+                print(" ".join(cmd))
+            jobs.append(cmd)
+    # the translation units are independent: compile them side by side
+    with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        for f in [ex.submit(subprocess.check_call, c) for c in jobs]:
+            f.result()
     tmp = LIB + ".tmp"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
     os.replace(tmp, LIB)

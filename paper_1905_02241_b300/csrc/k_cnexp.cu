@@ -907,20 +907,22 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                     const int o = st_off[t] + a * cnt + j;
                     x[a] = PREC == NMODL_FP64 ? st_d[o] : f2d_int(st_f[o].x) + f2d_int(st_f[o].y);
                 }
-                bool flag;
+                // failed: the refinement or Newton iteration reached its cap
+                bool failed = false, conv = true;
                 if (kind == NMODL_KIN3) {
                     if (PREC == NMODL_FP64)
                         kin3_step_d(md_s[t].k3, v_s[nd], A.dt, x);
                     else
                         kin3_step_mixed(k3f_s[t], vf_s[nd], d2f_int(A.dt), A.newton_tol, A.ir_max,
-                                        x, flag);
+                                        x, failed);
                 } else if (PREC == NMODL_FP64) {
                     cacum_newton_d(md_s[t].cd, ica_s[nd], A.dt, A.newton_tol, A.newton_max_iter,
-                                   x[0], x[1], flag);
+                                   x[0], x[1], conv);
                 } else {
                     cacum_newton_mixed(md_s[t].cd, cdf_s[t], ica_s[nd], A.dt, A.newton_tol,
-                                       A.newton_max_iter, A.ir_max, x[0], x[1], flag);
+                                       A.newton_max_iter, A.ir_max, x[0], x[1], conv);
                 }
+                if (failed || !conv) latch_error(A.err, NMODL_ERR_NOCONV);
                 for (int a = 0; a < ns; ++a) {
                     const int o = st_off[t] + a * cnt + j;
                     if (PREC == NMODL_FP64) {

@@ -308,6 +308,7 @@ __global__ void __launch_bounds__(128)
             if (!isfinite(y[a])) latch_error(err, NMODL_ERR_NONFINITE);
             st[a * stride + i] = y[a];
         }
+        if (nonconv) latch_error(err, NMODL_ERR_NOCONV);
         it_sum += iters;
         nc_sum += nonconv ? 1 : 0;
         it_max = max(it_max, iters);

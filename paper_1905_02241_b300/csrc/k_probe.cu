@@ -6,6 +6,8 @@
 #include <algorithm>
 
 #include "kernels.cuh"
+#include "runtime.cuh"
+#include "tcgen05.cuh"
 
 namespace nmodl {
 
@@ -62,9 +64,38 @@ __global__ void k_math_eval(int fn, int64_t n, const double* __restrict__ x, dou
                      : one_pm_exp<-1>(x[i]);
 }
 
+// The bounded mbarrier wait of the tensor-core kernels, on a barrier that
+// nothing arrives at: every thread polls it `polls` times, gives up, and the
+// block latches NMODL_ERR_TIMEOUT -- the path a stalled MMA completion would
+// take, exercised without stalling anything.  The barrier lives in this
+// block's shared memory and is invalidated before the block exits.
+__global__ void k_probe_wait(uint32_t polls, int32_t* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0, polls);
+    const bool any_timeout = __syncthreads_or(!ok);
+    if (threadIdx.x == 0) {
+        if (any_timeout) latch_error(err, NMODL_ERR_TIMEOUT);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&bar)) : "memory");
+    }
+}
+
 }  // namespace nmodl
 
 using namespace nmodl;
+
+// Run the bounded wait on the context's stream; the timeout is latched in the
+// context like any device error and returned by the next nmodl_sync.
+extern "C" NMODL_API int nmodl_probe_wait(nmodl_ctx* ctx, int32_t polls) {
+    if (!ctx || polls < 1 || polls > (1 << 20)) return NMODL_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    k_probe_wait<<<1, 128, 0, ctx->stream>>>((uint32_t)polls, ctx->d_err);
+    return cudaGetLastError() == cudaSuccess ? NMODL_OK : NMODL_ERR_CUDA;
+}
 
 // fn 0: the library's table-driven FP64 exp; fn 1: CUDA exp (for comparison);
 // fn 2: rounding to float and back through the integer-pipe conversions;

@@ -83,7 +83,10 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int a = 0; a < 3; ++a) y[a] = x[a];
             iters = kin3_step_mixed(kf32, d2f_int(vv), d2f_int(dt), tol, ir_max, y, nonconv);
-            if (nonconv) nc_sum = 1;
+            if (nonconv) {
+                nc_sum = 1;
+                latch_error(err, NMODL_ERR_NOCONV);
+            }
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -127,6 +130,7 @@ __global__ void __launch_bounds__(256)
                            : cacum_newton_mixed(C, cf32, ica[ni[i]], dt, tol, max_iter, ir_max,
                                                 y0, y1, conv);
         if (!isfinite(y0) || !isfinite(y1)) latch_error(err, NMODL_ERR_NONFINITE);
+        if (!conv) latch_error(err, NMODL_ERR_NOCONV);
         st[i] = y0;
         st[stride + i] = y1;
         it_sum = it;

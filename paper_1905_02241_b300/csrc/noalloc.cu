@@ -22,7 +22,7 @@ int build_desc_for(int type, const double* params, int64_t n_params, MechD* md,
 namespace {
 
 constexpr size_t kScratchBytes = 1u << 20;  // 1 MiB per device
-constexpr size_t kFlagsOff = 0;             // int32 validation flags
+constexpr size_t kFlagsOff = 0;             // int32 flags: [0] validation, [1] non-finite
 constexpr size_t kDescOff = 256;            // MechD or Kin9D
 constexpr size_t kChunkOff = 1280;          // int32 chunk table
 constexpr int64_t kMaxChunks = (int64_t)((kScratchBytes - kChunkOff) / 4) - 1;
@@ -90,7 +90,7 @@ extern "C" NMODL_API int nmodl_cur_noalloc(int device, void* cuda_stream, int ty
         void* desc = base + kDescOff;
         int32_t* chunk = (int32_t*)(base + kChunkOff);
         const int64_t n_chunks = (n_instances + 31) / 32;
-        cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int32_t), s);
+        cudaError_t e = cudaMemsetAsync(flags, 0, 2 * sizeof(int32_t), s);
         if (e == cudaSuccess)
             e = (type == NMODL_KIN9)
                     ? cudaMemcpyAsync(desc, &kd, sizeof(kd), cudaMemcpyHostToDevice, s)
@@ -112,11 +112,20 @@ extern "C" NMODL_API int nmodl_cur_noalloc(int device, void* cuda_stream, int ty
         } else if (hflags & 1) {
             rc = NMODL_ERR_UNSORTED;
         } else {
+            // A non-finite rhs or d of this call is latched in flags[1] and
+            // read back once the reduction has finished, so the call reports
+            // it as nmodl_cur's context would (there is no context here).
             launch_chunk_starts(node_index, n_instances, n_chunks, chunk, s);
             launch_cur_seg(type == NMODL_KIN9 ? NMODL_KIN9 : NMODL_CNEXP, desc, n_chunks,
                            chunk, node_index, v, states, stride, rhs, d, nullptr, nullptr,
-                           nullptr, s);
-            if (cudaGetLastError() != cudaSuccess) rc = NMODL_ERR_CUDA;
+                           flags + 1, s);
+            int32_t hbad = 0;
+            e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&hbad, flags + 1, sizeof(hbad), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = NMODL_ERR_CUDA;
+            else if (hbad) rc = NMODL_ERR_NONFINITE;
         }
     }
     if (prev >= 0 && prev != device) cudaSetDevice(prev);

@@ -56,11 +56,13 @@ class Surrogate:
         assert w.size == self.N_PARAMS
         self.ctx.enter()
         _lib.nmodl_surrogate_set_weights(self.handle, w.ctypes.data)
+        self.ctx.leave()
 
     def get_weights(self) -> np.ndarray:
         w = np.zeros(self.N_PARAMS, dtype=np.float32)
         self.ctx.enter()
         _lib.nmodl_surrogate_get_weights(self.handle, w.ctypes.data)
+        self.ctx.leave()
         return w
 
     def forward(self, X: torch.Tensor) -> torch.Tensor:
@@ -77,6 +79,7 @@ class Surrogate:
         self.ctx.enter()
         _lib.nmodl_surrogate_loss_grad(self.handle, X.shape[0], X.data_ptr(), T.data_ptr(),
                                        g.ctypes.data, loss.ctypes.data)
+        self.ctx.leave()
         return float(loss[0]), g
 
     def fit(self, X: torch.Tensor, T: torch.Tensor, epochs: int = 20, batch: int = 8192,

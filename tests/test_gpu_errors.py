@@ -65,3 +65,89 @@ def test_nonfinite_latched(api):
     m.state(0.025, v)
     assert ctx.sync() == -5
     assert ctx.sync() == 0  # cleared after being reported
+
+
+# -------------------------------------------- Newton non-convergence
+# Provoked from the host with an iteration cap that no solve can meet (one
+# update, then the convergence check never runs): every instance reports
+# non-convergence, the context latches NMODL_ERR_NOCONV, nmodl_sync returns
+# it once, and the same context then runs normally with the default cap.
+
+def test_kinetic_nonconvergence_latched_and_counted(api):
+    for prec in (api.NMODL_FP64, api.NMODL_MIXED):
+        wl = W.kin9_clamped(1000, seed=4)
+        ctx = api.Context(0, precision=prec, newton_max_iter=1, ir_max=0, clamp_v=1)
+        (spec,) = wl["mechs"]
+        m = api.Mechanism(ctx, spec["type"], spec["node_index"], wl["n_nodes"], spec["params"])
+        m.set_states(to_dev(wl["x0"]))
+        v = to_dev(wl["v0"])
+        m.state(0.025, v)
+        assert ctx.sync() == -6
+        assert ctx.sync() == 0
+        st = m.stats()
+        assert st["nonconverged"] == 1000 and st["newton_max"] == 1
+        ctx.set_options(newton_max_iter=8, ir_max=4)
+        m.state(0.025, v)
+        assert ctx.sync() == 0
+        assert m.stats()["nonconverged"] == 1000
+        m.close()
+        ctx.close()
+
+
+def test_buffer_nonconvergence_latched_standalone_and_fused(api):
+    n = 2000
+    ica = -to_dev(W.Stream(21, 2).loguniform(n, 1e-3, 1.0))
+    v = to_dev(np.full(n, -65.0))
+    for prec in (api.NMODL_FP64, api.NMODL_MIXED):
+        ctx = api.Context(0, precision=prec, newton_max_iter=1, ir_max=0)
+        ctx.set_ions(ica=ica)
+        buf = api.Mechanism(ctx, W.TYPE_CACUM, np.arange(n, dtype=np.int32), n,
+                            W.cacum_params())
+        buf.init(v)
+        buf.state(0.025, v)
+        assert ctx.sync() == -6
+        assert buf.stats()["nonconverged"] == n
+        buf.close()
+        ctx.close()
+    # the fused tile kernel (the ion network's buffer items)
+    wl = W.cortical_ions(3000, seed=8)
+    ctx = api.Context(0, newton_max_iter=1)
+    arrs = [to_dev(np.zeros(wl["n_nodes"])) for _ in range(3)]
+    ctx.set_ions(*arrs)
+    mechs = [api.Mechanism(ctx, m["type"], m["node_index"], wl["n_nodes"], m["params"],
+                           ion=m.get("ion", 0)) for m in wl["mechs"]]
+    vv = to_dev(wl["v0"])
+    rhs, d = to_dev(np.zeros(wl["n_nodes"])), to_dev(np.zeros(wl["n_nodes"]))
+    for m in mechs:
+        m.init(vv)
+    ctx.step(mechs, 0.025, 1.0, vv, rhs, d, 3)
+    assert ctx.plan(mechs)["fused"]
+    assert ctx.sync() == -6
+    ctx.set_options(newton_max_iter=8)
+    ctx.step(mechs, 0.025, 1.0, vv, rhs, d, 3)
+    assert ctx.sync() == 0
+    for m in mechs:
+        m.close()
+    ctx.close()
+
+
+# -------------------------------------------------- bounded waits
+# The tensor-core kernels wait on mbarriers with a poll limit.  The probe
+# runs that wait on a barrier nothing arrives at: the limit runs out, the
+# context latches NMODL_ERR_TIMEOUT, and the context stays usable.
+
+def test_bounded_wait_timeout_latched_and_context_usable(api):
+    from paper_1905_02241_b300 import _lib
+    ctx, m = _create(api, [0, 1, 1, 5])
+    v = to_dev(np.full(10, -65.0))
+    m.init(v)
+    assert ctx.sync() == 0
+    _lib.nmodl_probe_wait(ctx.handle, 2000)
+    assert ctx.sync() == -7
+    assert ctx.sync() == 0
+    m.state(0.025, v)
+    assert ctx.sync() == 0
+    with pytest.raises(api.NmodlError):
+        _lib.nmodl_probe_wait(ctx.handle, 0)
+    m.close()
+    ctx.close()

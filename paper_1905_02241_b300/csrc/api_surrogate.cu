@@ -13,8 +13,6 @@ using namespace nmodl;
 
 namespace {
 
-constexpr int kSplitRows = 256;  // split-K chunk of the weight-gradient GEMMs
-
 // public (unpadded) <-> padded FP32 parameter layouts
 void pub_to_pad(const float* in, float* out) {
     std::memset(out, 0, sizeof(float) * kParamsPadded);
@@ -54,87 +52,44 @@ void refresh_bf16(nmodl_surrogate* s) {
 }
 
 void free_sur(nmodl_surrogate* s) {
-    void* ptrs[] = {s->params, s->wbf, s->grad, s->m, s->v, s->H0, s->H1, s->H2, s->H3,
-                    s->D4, s->D3, s->D2, s->D1, s->Z1, s->Z2, s->Z3, s->OUT, s->part,
+    void* ptrs[] = {s->params, s->wbf, s->grad, s->m, s->v, s->ds1, s->ds2, s->ds3, s->part,
                     s->loss_part, s->loss};
     for (void* p : ptrs) cudaFree(p);
     delete s;
 }
 
-GemmArgs gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M,
-              int N, int K) {
-    GemmArgs g{};
-    g.A = A;
-    g.lda = lda;
-    g.B = B;
-    g.ldb = ldb;
-    g.M = M;
-    g.N = N;
-    g.K = K;
-    g.k_per_split = K;
-    return g;
+TrainArgs train_args(nmodl_surrogate* s, int64_t n, const float* X, int* grid) {
+    TrainArgs a{};
+    a.X = X;
+    a.n = n;
+    a.wbf = s->wbf;
+    a.params = s->params;
+    a.ds1 = s->ds1;
+    a.ds2 = s->ds2;
+    a.ds3 = s->ds3;
+    a.part = s->part;
+    a.loss_part = s->loss_part;
+    a.err = s->ctx->d_err;
+    *grid = train_grid(n, &a.tiles_per_cta);
+    return a;
 }
 
-// forward of n <= max_batch rows already packed in H0; OUT = [n][16]
-void forward(nmodl_surrogate* s, int64_t n) {
+// Loss and gradient partials of one batch (the fused tensor-core kernel),
+// then their sum into s->grad (adam = 0) or the Adam step on the master
+// parameters and their bf16 copies (adam = 1); s->loss receives the loss.
+cudaError_t loss_and_grad(nmodl_surrogate* s, int64_t n, const float* X, const float* T,
+                          int adam, float lr, FitSched fs = FitSched{}) {
     cudaStream_t st = s->ctx->stream;
-    const int B = (int)n;
-    GemmArgs g = gemm(s->H0, kIn, s->wbf + kBfW1, kIn, B, kHid, kIn);
-    g.bias = s->params + kOffB1; g.Cf = s->Z1; g.ldc = kHid; g.Ch = s->H1; g.ldch = kHid;
-    launch_gemm(0, 0, kEpiBiasSilu, g, 1, st);
-    g = gemm(s->H1, kHid, s->wbf + kBfW2, kHid, B, kHid, kHid);
-    g.bias = s->params + kOffB2; g.Cf = s->Z2; g.ldc = kHid; g.Ch = s->H2; g.ldch = kHid;
-    launch_gemm(0, 0, kEpiBiasSilu, g, 1, st);
-    g = gemm(s->H2, kHid, s->wbf + kBfW3, kHid, B, kHid, kHid);
-    g.bias = s->params + kOffB3; g.Cf = s->Z3; g.ldc = kHid; g.Ch = s->H3; g.ldch = kHid;
-    launch_gemm(0, 0, kEpiBiasSilu, g, 1, st);
-    g = gemm(s->H3, kHid, s->wbf + kBfW4, kHid, B, kOut, kHid);
-    g.bias = s->params + kOffB4; g.Cf = s->OUT; g.ldc = kOut;
-    launch_gemm(0, 0, kEpiBias, g, 1, st);
-}
-
-// weight gradient dW[out][in] = delta^T H (split-K over the batch), bias
-// gradient = column sums of delta; written into s->grad at the offsets.
-void weight_grad(nmodl_surrogate* s, int64_t n, const __nv_bfloat16* delta, int n_out,
-                 const __nv_bfloat16* H, int n_in, int offW, int offB) {
-    cudaStream_t st = s->ctx->stream;
-    const int B = (int)n;
-    const int splits = (B + kSplitRows - 1) / kSplitRows;
-    GemmArgs g = gemm(delta, n_out, H, n_in, n_out, n_in, B);
-    g.k_per_split = kSplitRows;
-    g.Cf = s->part;
-    g.ldc = n_in;
-    launch_gemm(1, 1, kEpiPartial, g, splits, st);
-    launch_reduce_splits(s->part, splits, (int64_t)n_out * n_in, s->grad + offW, st);
-    launch_colsum(delta, n, n_out, s->part, s->grad + offB, st);
-}
-
-// delta_prev = (delta W) * SiLU'(Z_prev)
-void back_delta(nmodl_surrogate* s, int64_t n, const __nv_bfloat16* delta, int n_out,
-                const __nv_bfloat16* W, int n_in, const float* Zprev, __nv_bfloat16* out) {
-    GemmArgs g = gemm(delta, n_out, W, n_in, (int)n, n_in, n_out);
-    g.Zin = Zprev;
-    g.ldz = n_in;
-    g.Ch = out;
-    g.ldch = n_in;
-    launch_gemm(0, 1, kEpiDsilu, g, 1, s->ctx->stream);
-}
-
-// loss (device scalar s->loss) and all gradients into s->grad
-void loss_and_grad(nmodl_surrogate* s, int64_t n, const float* X, const float* T,
-                   FitSched fs = FitSched{}) {
-    cudaStream_t st = s->ctx->stream;
-    launch_pack_input(X, n, s->H0, st, fs);
-    forward(s, n);
-    const int blocks = launch_loss_delta(s->OUT, T, n, s->D4, s->loss_part, st, fs);
-    launch_reduce_splits(s->loss_part, blocks, 1, s->loss, st);
-    weight_grad(s, n, s->D4, kOut, s->H3, kHid, kOffW4, kOffB4);
-    back_delta(s, n, s->D4, kOut, s->wbf + kBfW4, kHid, s->Z3, s->D3);
-    weight_grad(s, n, s->D3, kHid, s->H2, kHid, kOffW3, kOffB3);
-    back_delta(s, n, s->D3, kHid, s->wbf + kBfW3, kHid, s->Z2, s->D2);
-    weight_grad(s, n, s->D2, kHid, s->H1, kHid, kOffW2, kOffB2);
-    back_delta(s, n, s->D2, kHid, s->wbf + kBfW2, kHid, s->Z1, s->D1);
-    weight_grad(s, n, s->D1, kHid, s->H0, kIn, kOffW1, kOffB1);
+    int grid = 0;
+    TrainArgs a = train_args(s, n, X, &grid);
+    a.T = T;
+    a.mode = 1;
+    a.fs = fs;
+    cudaError_t e = launch_train_tiles(a, grid, st);
+    if (e != cudaSuccess) return e;
+    launch_grad_adam(s->part, grid, s->loss_part, s->loss, s->grad, adam, s->params, s->m, s->v,
+                     s->wbf, lr, 0.9f, 0.999f, 1e-8f, s->step, fs, st);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -155,8 +110,7 @@ NMODL_API int nmodl_surrogate_create(nmodl_ctx* c, int64_t max_batch, const floa
     s->scaled = scaled ? 1 : 0;
     s->max_batch = max_batch;
     const int64_t B = max_batch;
-    const int64_t splits = (B + kSplitRows - 1) / kSplitRows;
-    s->part_count = std::max<int64_t>(splits * kHid * kHid, (B / 256 + 1) * kHid);
+    s->n_part_max = train_max_grid(B);
     cudaError_t e = cudaSuccess;
     do {
         if ((e = dalloc(&s->params, kParamsPadded)) != cudaSuccess) break;
@@ -164,20 +118,11 @@ NMODL_API int nmodl_surrogate_create(nmodl_ctx* c, int64_t max_batch, const floa
         if ((e = dalloc(&s->grad, kParamsPadded)) != cudaSuccess) break;
         if ((e = dalloc(&s->m, kParamsPadded)) != cudaSuccess) break;
         if ((e = dalloc(&s->v, kParamsPadded)) != cudaSuccess) break;
-        if ((e = dalloc(&s->H0, B * kIn)) != cudaSuccess) break;
-        if ((e = dalloc(&s->H1, B * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->H2, B * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->H3, B * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->D4, B * kOut)) != cudaSuccess) break;
-        if ((e = dalloc(&s->D3, B * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->D2, B * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->D1, B * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->Z1, B * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->Z2, B * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->Z3, B * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->OUT, B * kOut)) != cudaSuccess) break;
-        if ((e = dalloc(&s->part, s->part_count)) != cudaSuccess) break;
-        if ((e = dalloc(&s->loss_part, 256)) != cudaSuccess) break;
+        if ((e = dalloc(&s->ds1, B * kHid)) != cudaSuccess) break;
+        if ((e = dalloc(&s->ds2, B * kHid)) != cudaSuccess) break;
+        if ((e = dalloc(&s->ds3, B * kHid)) != cudaSuccess) break;
+        if ((e = dalloc(&s->part, (int64_t)s->n_part_max * kParamsPadded)) != cudaSuccess) break;
+        if ((e = dalloc(&s->loss_part, s->n_part_max)) != cudaSuccess) break;
         if ((e = dalloc(&s->loss, 1)) != cudaSuccess) break;
         std::vector<float> pad(kParamsPadded, 0.f);
         if (weights) pub_to_pad(weights, pad.data());
@@ -189,6 +134,7 @@ NMODL_API int nmodl_surrogate_create(nmodl_ctx* c, int64_t max_batch, const floa
         refresh_bf16(s);
         e = cudaStreamSynchronize(c->stream);
         if (e == cudaSuccess) e = surrogate_prepare();
+        if (e == cudaSuccess) e = train_prepare();
     } while (false);
     if (e != cudaSuccess) {
         free_sur(s);
@@ -238,21 +184,19 @@ NMODL_API int nmodl_surrogate_forward(nmodl_surrogate* s, int64_t n, const float
     if (!s || n < 0 || n > s->max_batch || (n > 0 && (!X || !Y))) return NMODL_ERR_ARG;
     if (n == 0) return NMODL_OK;
     DeviceGuard dg(s->ctx->device);
-    launch_pack_input(X, n, s->H0, s->ctx->stream);
-    forward(s, n);
-    cudaError_t e = cudaMemcpy2DAsync(Y, kOutRaw * sizeof(float), s->OUT, kOut * sizeof(float),
-                                      kOutRaw * sizeof(float), n, cudaMemcpyDeviceToDevice,
-                                      s->ctx->stream);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    return nmodl_cuda_status(e);
+    int grid = 0;
+    TrainArgs a = train_args(s, n, X, &grid);
+    a.Y = Y;
+    a.mode = 0;
+    return nmodl_cuda_status(launch_train_tiles(a, grid, s->ctx->stream));
 }
 
 NMODL_API int nmodl_surrogate_loss_grad(nmodl_surrogate* s, int64_t n, const float* X,
                                         const float* T, float* grad_host, float* loss_host) {
     if (!s || n < 16 || n > s->max_batch || !X || !T) return NMODL_ERR_ARG;
     DeviceGuard dg(s->ctx->device);
-    loss_and_grad(s, n, X, T);
-    cudaError_t e = cudaStreamSynchronize(s->ctx->stream);
+    cudaError_t e = loss_and_grad(s, n, X, T, 0, 0.f);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->ctx->stream);
     if (e == cudaSuccess && loss_host)
         e = cudaMemcpy(loss_host, s->loss, sizeof(float), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && grad_host) {
@@ -269,13 +213,11 @@ NMODL_API int nmodl_surrogate_train_step(nmodl_surrogate* s, int64_t n, const fl
     if (!s || n < 16 || n > s->max_batch || !X || !T || !(lr > 0.f)) return NMODL_ERR_ARG;
     DeviceGuard dg(s->ctx->device);
     cudaStream_t st = s->ctx->stream;
-    loss_and_grad(s, n, X, T);
     s->step += 1;
-    launch_adam(s->params, s->grad, s->m, s->v, kParamsPadded, lr, 0.9f, 0.999f, 1e-8f, s->step,
-                st);
-    refresh_bf16(s);
-    if (loss_dev) cudaMemcpyAsync(loss_dev, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
-    return nmodl_cuda_status(cudaGetLastError());
+    cudaError_t e = loss_and_grad(s, n, X, T, 1, lr);
+    if (e == cudaSuccess && loss_dev)
+        e = cudaMemcpyAsync(loss_dev, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
+    return nmodl_cuda_status(e);
 }
 
 // A whole training run: one optimiser step (loss and gradients, Adam with
@@ -298,10 +240,7 @@ NMODL_API int nmodl_surrogate_fit(nmodl_surrogate* s, int64_t n, const float* X,
     e = cudaMemsetAsync(d_step, 0, sizeof(int64_t), st);
     FitSched fs{d_step, spe, total, lr, lr_min, s->step, 1};
     auto one_step = [&]() {
-        loss_and_grad(s, batch, X, T, fs);
-        launch_adam_sched(s->params, s->grad, s->m, s->v, kParamsPadded, 0.9f, 0.999f, 1e-8f,
-                          fs, st);
-        refresh_bf16(s);
+        loss_and_grad(s, batch, X, T, 1, lr, fs);
         launch_fit_end(loss_steps, s->loss, fs, st);
     };
     cudaGraphExec_t exec = nullptr;

@@ -1,0 +1,506 @@
+// k_train.cu -- training and batch forward of the kinetic surrogate MLP
+// (11 -> 128 -> 128 -> 128 -> 9, SiLU) on the fifth-generation tensor cores.
+//
+// k_train_tiles: one CTA per SM, two warpgroups; each CTA takes a run of
+// 128-row tiles of the minibatch.  Per tile, one thread issues every
+// tcgen05.mma (bf16 operands in shared memory, FP32 accumulators in tensor
+// memory) and the 256 threads run the epilogues (thread = row of the tile,
+// warpgroup = half of the columns), reading the accumulators with
+// tcgen05.ld:
+//   forward   Z1 = H0 W1^T, H1 = SiLU(Z1), ... OUT = H3 W4^T (+ biases, fed
+//             through the MMAs as bf16 hi/lo pairs against columns of ones)
+//   loss      e = OUT - T, loss += e^2, D4 = e / n                 (bf16)
+//   backward  D3 = (D4 W4) * SiLU'(Z3), D2 = (D3 W3) * SiLU'(Z2),
+//             D1 = (D2 W2) * SiLU'(Z1)                            (bf16)
+//   gradients dW4^T += H3^T D4, dW3 += D3^T H2, dW2 += D2^T H1,
+//             dW1 += D1^T H0, db2, db3 += D^T 1 (db1 comes with dW1 through
+//             H0's column of ones; db4 as column sums on the CUDA cores)
+// The same shared-memory image serves both orientations: an activation
+// tile stored K-major for the forward product (K = features) is read
+// MN-major by the gradient products, whose contraction runs over the 128
+// rows of the tile; a weight image stored K-major for the forward (K = in)
+// is read MN-major by the backward product (K = out).  The gradient
+// accumulators stay in tensor memory over all tiles of the CTA and are
+// written once per CTA; k_grad_adam sums the CTA partials in a fixed order
+// (deterministic), then either stores the gradient or takes the Adam step
+// (Kingma & Ba 2015) and refreshes the bf16 weight copies.
+// Every mbarrier wait is bounded; a timeout is latched as
+// NMODL_ERR_TIMEOUT and the CTA stops.
+#include "kernels.cuh"
+#include "mlp.cuh"
+#include "tcgen05.cuh"
+
+namespace nmodl {
+
+namespace {
+constexpr int kTrThreads = 256;  // two warpgroups
+constexpr int kTrRows = 128;     // rows per tile (MMA M)
+// shared-memory images (K-major core matrices, umma_offset), bytes
+constexpr int kImW1 = kHid * kIn * 2, kImWH = kHid * kHid * 2, kImW4 = kOut * kHid * 2;
+constexpr int kImH0 = kTrRows * kIn * 2, kImH = kTrRows * kHid * 2, kImD4 = kTrRows * kOut * 2;
+constexpr int kImOne = kTrRows * 16 * 2, kImBH = kHid * 16 * 2, kImB4 = kOut * 16 * 2;
+constexpr int sW1 = 0, sW2 = sW1 + kImW1, sW3 = sW2 + kImWH, sW4 = sW3 + kImWH;
+constexpr int sH0 = sW4 + kImW4, sH1 = sH0 + kImH0, sH2 = sH1 + kImH, sH3 = sH2 + kImH;
+constexpr int sD4 = sH3 + kImH, sOne = sD4 + kImD4, sB2 = sOne + kImOne, sB3 = sB2 + kImBH;
+constexpr int sB4 = sB3 + kImBH;
+constexpr int sRed = sB4 + kImB4;        // float [4 warps][16]: per-warp column sums
+constexpr int sAcc = sRed + 4 * 16 * 4;  // float [16]: db4 (0..8) and sum e^2 (9) of the CTA
+constexpr int sBar = sAcc + 16 * 4;
+constexpr int kTrSmem = sBar + 16;
+static_assert(sBar % 8 == 0, "mbarrier alignment");
+static_assert(kTrSmem <= 227 * 1024, "shared memory per block");
+// tensor-memory columns: the working accumulator, then the gradient
+// accumulators that live across the CTA's tiles
+constexpr uint32_t cAcc = 0, cDW2 = 128, cDW3 = 256, cDW1 = 384, cDW4T = 400, cDB2 = 416,
+                   cDB3 = 432;
+constexpr uint32_t kTrTmemCols = 512;
+constexpr uint32_t kTrPolls = 1u << 22;
+
+// kind::f16 instruction descriptor, M = 128; bit 15 / 16: A / B MN-major
+__host__ __device__ constexpr uint32_t tr_idesc(uint32_t N, bool a_mn, bool b_mn) {
+    return umma_idesc_bf16(128, N) | (a_mn ? 1u << 15 : 0u) | (b_mn ? 1u << 16 : 0u);
+}
+}  // namespace
+
+// Descriptor of an image stored K-major with row width F (elements):
+// read K-major (K = its columns; LBO 128 B between core matrices along K,
+// SBO 16 F B between 8-row groups) or MN-major (K = its rows: core matrices
+// 16 F B apart along K, 128 B apart along MN).
+__device__ __forceinline__ uint64_t desc_k(uint32_t a, int F) { return umma_desc(a, 128, 16 * F); }
+__device__ __forceinline__ uint64_t desc_mn(uint32_t a, int F) { return umma_desc(a, 16 * F, 128); }
+
+// D (+)= A B^T over K = 16 ksteps: A, B images at a0, b0 with row widths
+// aF, bF, each read K-major or MN-major; the start address moves 32 B x 8
+// (two core matrices) per step along K in the K-major view, two 8-row
+// groups (32 F B) in the MN-major view.
+__device__ __forceinline__ void mma_run(uint32_t d, uint32_t a0, int aF, bool a_mn, uint32_t b0,
+                                        int bF, bool b_mn, int ksteps, uint32_t id, bool acc) {
+    for (int j = 0; j < ksteps; ++j) {
+        const uint32_t aa = a0 + (uint32_t)j * (a_mn ? 32u * aF : 256u);
+        const uint32_t bb = b0 + (uint32_t)j * (b_mn ? 32u * bF : 256u);
+        umma_bf16(d, a_mn ? desc_mn(aa, aF) : desc_k(aa, aF), b_mn ? desc_mn(bb, bF) : desc_k(bb, bF),
+                  id, (acc || j > 0) ? 1u : 0u);
+    }
+}
+
+__global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint32_t sb = smem_u32(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sBar);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + sBar + 8);
+    float* red = reinterpret_cast<float*>(smem + sRed);
+    float* accs = reinterpret_cast<float*>(smem + sAcc);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int t = tid & 127;  // row of the tile (tensor-memory lane)
+    const int h = tid >> 7;   // warpgroup: columns [64 h, 64 h + 64) of the hidden layers
+    const int n = (int)a.n;
+    const float inv_n = 1.0f / (float)n;
+    const float* X = a.X;
+    const float* T = a.T;
+    if (a.fs.active) {
+        const int64_t o = (*a.fs.step % a.fs.steps_per_epoch) * a.n;
+        X += o * kInRaw;
+        T += o * kOutRaw;
+    }
+
+    // ---- stage the weights (bf16 copies, row-major) as K-major images
+    auto stage = [&](const __nv_bfloat16* src, int off, int rows, int K) {
+        const int ch = K / 8;
+        for (int c = tid; c < rows * ch; c += kTrThreads) {
+            const int r = c / ch, k = (c % ch) * 8;
+            *reinterpret_cast<uint4*>(smem + off + umma_offset(r, k, K)) =
+                *reinterpret_cast<const uint4*>(src + r * K + k);
+        }
+    };
+    stage(a.wbf + kBfW1, sW1, kHid, kIn);
+    stage(a.wbf + kBfW2, sW2, kHid, kHid);
+    stage(a.wbf + kBfW3, sW3, kHid, kHid);
+    stage(a.wbf + kBfW4, sW4, kOut, kHid);
+    auto put = [&](int off, int r, int k, int K, float x) {
+        *reinterpret_cast<__nv_bfloat16*>(smem + off + umma_offset(r, k, K)) = __float2bfloat16_rn(x);
+    };
+    // bias as a bf16 pair hi + lo in columns k, k + 1
+    auto put_pair = [&](int off, int r, int k, int K, float b) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+        put(off, r, k, K, b);
+        put(off, r, k + 1, K, b - __bfloat162float(hi));
+    };
+    for (int i = tid; i < kTrRows * 16; i += kTrThreads) put(sOne, i / 16, i % 16, 16, (i % 16) < 2 ? 1.f : 0.f);
+    for (int i = tid; i < kHid * 16; i += kTrThreads) {
+        put(sB2, i / 16, i % 16, 16, 0.f);
+        put(sB3, i / 16, i % 16, 16, 0.f);
+    }
+    for (int i = tid; i < kOut * 16; i += kTrThreads) put(sB4, i / 16, i % 16, 16, 0.f);
+    if (tid < 16) accs[tid] = 0.f;
+    __syncthreads();
+    for (int i = tid; i < kHid; i += kTrThreads) {
+        put_pair(sW1, i, kInRaw, kIn, a.params[kOffB1 + i]);  // W1 columns 11, 12
+        put_pair(sB2, i, 0, 16, a.params[kOffB2 + i]);
+        put_pair(sB3, i, 0, 16, a.params[kOffB3 + i]);
+    }
+    if (tid < kOutRaw) put_pair(sB4, tid, 0, 16, a.params[kOffB4 + tid]);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, kTrTmemCols);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
+    uint32_t phase = 0;
+    bool timed_out = false;
+
+    // operands in shared memory written, earlier tensor-memory reads done
+    auto publish = [&]() {
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+    };
+    auto commit_wait = [&]() -> bool {
+        if (tid == 0) umma_commit(bar);
+        const bool ok = mbar_wait(bar, phase, kTrPolls);
+        phase ^= 1u;
+        const bool bad = __syncthreads_or(!ok);
+        tc_fence_after();
+        return !bad;
+    };
+    auto row_of = [&](int tile) { return (int64_t)tile * kTrRows + t; };
+
+    const int tiles = (n + kTrRows - 1) / kTrRows;
+    const int tile0 = blockIdx.x * a.tiles_per_cta;
+    const int tile1 = min(tiles, tile0 + a.tiles_per_cta);
+    for (int tile = tile0; tile < tile1 && !timed_out; ++tile) {
+        const bool first = tile == tile0;
+        const int64_t row = row_of(tile);
+        const bool valid = row < n;
+        // ---- inputs: row t of H0 (features, then the bias pair's ones)
+        if (h == 0) {
+            float f[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) f[k] = 0.f;
+            if (valid) {
+#pragma unroll
+                for (int k = 0; k < kInRaw; ++k) f[k] = X[row * kInRaw + k];
+                f[kInRaw] = 1.f;
+                f[kInRaw + 1] = 1.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                *reinterpret_cast<uint4*>(smem + sH0 + umma_offset(t, 8 * q, kIn)) =
+                    make_uint4(pack_bf16(f[8 * q], f[8 * q + 1]), pack_bf16(f[8 * q + 2], f[8 * q + 3]),
+                               pack_bf16(f[8 * q + 4], f[8 * q + 5]), pack_bf16(f[8 * q + 6], f[8 * q + 7]));
+        }
+        publish();
+        // ---- forward: hidden layers
+        for (int l = 1; l <= 3 && !timed_out; ++l) {
+            const int hin = l == 1 ? sH0 : l == 2 ? sH1 : sH2;
+            const int hout = l == 1 ? sH1 : l == 2 ? sH2 : sH3;
+            if (tid == 0) {
+                tc_fence_after();
+                if (l == 1) {
+                    mma_run(tmem + cAcc, sb + sH0, kIn, false, sb + sW1, kIn, false, 1,
+                            tr_idesc(kHid, false, false), false);
+                } else {
+                    const int wi = l == 2 ? sW2 : sW3, bi = l == 2 ? sB2 : sB3;
+                    mma_run(tmem + cAcc, sb + sOne, 16, false, sb + bi, 16, false, 1,
+                            tr_idesc(kHid, false, false), false);
+                    mma_run(tmem + cAcc, sb + hin, kHid, false, sb + wi, kHid, false, kHid / 16,
+                            tr_idesc(kHid, false, false), true);
+                }
+            }
+            if (!commit_wait()) { timed_out = true; break; }
+            float* ds = l == 1 ? a.ds1 : l == 2 ? a.ds2 : a.ds3;
+#pragma unroll 1
+            for (int cb = 0; cb < 64; cb += 16) {
+                const int c = 64 * h + cb;
+                uint32_t r[16];
+                tmem_ld16(lane_base + cAcc + c, r);
+                tmem_ld_wait();
+                float sv[16], dv[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const float z = __uint_as_float(r[e]);
+                    const float s = fmaf(0.5f, tanh_hw(0.5f * z), 0.5f);
+                    sv[e] = z * s;
+                    dv[e] = s * fmaf(z, 1.0f - s, 1.0f);
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    *reinterpret_cast<uint4*>(smem + hout + umma_offset(t, c + 8 * q, kHid)) =
+                        make_uint4(pack_bf16(sv[8 * q], sv[8 * q + 1]), pack_bf16(sv[8 * q + 2], sv[8 * q + 3]),
+                                   pack_bf16(sv[8 * q + 4], sv[8 * q + 5]),
+                                   pack_bf16(sv[8 * q + 6], sv[8 * q + 7]));
+                if (a.mode == 1 && valid) {
+                    float4* o = reinterpret_cast<float4*>(ds + row * kHid + c);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        o[q] = make_float4(dv[4 * q], dv[4 * q + 1], dv[4 * q + 2], dv[4 * q + 3]);
+                }
+            }
+            publish();
+        }
+        if (timed_out) break;
+        // ---- output layer
+        if (tid == 0) {
+            tc_fence_after();
+            mma_run(tmem + cAcc, sb + sOne, 16, false, sb + sB4, 16, false, 1,
+                    tr_idesc(kOut, false, false), false);
+            mma_run(tmem + cAcc, sb + sH3, kHid, false, sb + sW4, kHid, false, kHid / 16,
+                    tr_idesc(kOut, false, false), true);
+        }
+        if (!commit_wait()) { timed_out = true; break; }
+        if (h == 0) {
+            uint32_t r[16];
+            tmem_ld16(lane_base + cAcc, r);
+            tmem_ld_wait();
+            if (a.mode == 0) {
+                if (valid)
+#pragma unroll
+                    for (int k = 0; k < kOutRaw; ++k) a.Y[row * kOutRaw + k] = __uint_as_float(r[k]);
+            } else {
+                // loss and D4 = (OUT - T)/n, rounded to bf16; the column sums
+                // of the rounded D4 (db4) and the sum of e^2 per warp
+                float dv[16], e2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) dv[k] = 0.f;
+                if (valid) {
+#pragma unroll
+                    for (int k = 0; k < kOutRaw; ++k) {
+                        const float e = __uint_as_float(r[k]) - T[row * kOutRaw + k];
+                        e2 = fmaf(e, e, e2);
+                        dv[k] = __bfloat162float(__float2bfloat16_rn(e * inv_n));
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    *reinterpret_cast<uint4*>(smem + sD4 + umma_offset(t, 8 * q, kOut)) =
+                        make_uint4(pack_bf16(dv[8 * q], dv[8 * q + 1]), pack_bf16(dv[8 * q + 2], dv[8 * q + 3]),
+                                   pack_bf16(dv[8 * q + 4], dv[8 * q + 5]),
+                                   pack_bf16(dv[8 * q + 6], dv[8 * q + 7]));
+                dv[kOutRaw] = e2;
+#pragma unroll
+                for (int k = 0; k <= kOutRaw; ++k) {
+                    float x = dv[k];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                    if (lane == 0) red[warp * 16 + k] = x;
+                }
+            }
+        }
+        if (a.mode == 0) {
+            publish();  // the next tile's H0 overwrites nothing the MMAs still read
+            continue;
+        }
+        publish();
+        if (tid <= kOutRaw) accs[tid] += ((red[tid] + red[16 + tid]) + red[32 + tid]) + red[48 + tid];
+        // ---- backward through the output layer: dW4^T += H3^T D4, G3 = D4 W4
+        if (tid == 0) {
+            tc_fence_after();
+            mma_run(tmem + cDW4T, sb + sH3, kHid, true, sb + sD4, kOut, true, kTrRows / 16,
+                    tr_idesc(kOut, true, true), !first);
+            mma_run(tmem + cAcc, sb + sD4, kOut, false, sb + sW4, kHid, true, 1,
+                    tr_idesc(kHid, false, true), false);
+        }
+        if (!commit_wait()) { timed_out = true; break; }
+        // ---- hidden layers, top down: D_l = G_l * SiLU'(Z_l) into H_l's image
+        for (int l = 3; l >= 1 && !timed_out; --l) {
+            const int dimg = l == 3 ? sH3 : l == 2 ? sH2 : sH1;
+            const float* ds = l == 1 ? a.ds1 : l == 2 ? a.ds2 : a.ds3;
+#pragma unroll 1
+            for (int cb = 0; cb < 64; cb += 16) {
+                const int c = 64 * h + cb;
+                uint32_t r[16];
+                tmem_ld16(lane_base + cAcc + c, r);
+                tmem_ld_wait();
+                float dv[16];
+                if (valid) {
+                    const float4* ip = reinterpret_cast<const float4*>(ds + row * kHid + c);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 w = ip[q];
+                        dv[4 * q] = __uint_as_float(r[4 * q]) * w.x;
+                        dv[4 * q + 1] = __uint_as_float(r[4 * q + 1]) * w.y;
+                        dv[4 * q + 2] = __uint_as_float(r[4 * q + 2]) * w.z;
+                        dv[4 * q + 3] = __uint_as_float(r[4 * q + 3]) * w.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) dv[e] = 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    *reinterpret_cast<uint4*>(smem + dimg + umma_offset(t, c + 8 * q, kHid)) =
+                        make_uint4(pack_bf16(dv[8 * q], dv[8 * q + 1]), pack_bf16(dv[8 * q + 2], dv[8 * q + 3]),
+                                   pack_bf16(dv[8 * q + 4], dv[8 * q + 5]),
+                                   pack_bf16(dv[8 * q + 6], dv[8 * q + 7]));
+            }
+            publish();
+            if (tid == 0) {
+                tc_fence_after();
+                if (l > 1) {
+                    const int hprev = l == 3 ? sH2 : sH1;
+                    const int wl = l == 3 ? sW3 : sW2;
+                    const uint32_t cdw = l == 3 ? cDW3 : cDW2, cdb = l == 3 ? cDB3 : cDB2;
+                    mma_run(tmem + cdw, sb + dimg, kHid, true, sb + hprev, kHid, true, kTrRows / 16,
+                            tr_idesc(kHid, true, true), !first);
+                    mma_run(tmem + cdb, sb + dimg, kHid, true, sb + sOne, 16, true, kTrRows / 16,
+                            tr_idesc(16, true, true), !first);
+                    mma_run(tmem + cAcc, sb + dimg, kHid, false, sb + wl, kHid, true, kHid / 16,
+                            tr_idesc(kHid, false, true), false);
+                } else {
+                    // dW1 (its column 11 is db1: H0 holds ones there)
+                    mma_run(tmem + cDW1, sb + dimg, kHid, true, sb + sH0, kIn, true, kTrRows / 16,
+                            tr_idesc(kIn, true, true), !first);
+                }
+            }
+            if (!commit_wait()) { timed_out = true; break; }
+        }
+    }
+
+    // ---- the CTA's gradient partials (every entry of the padded layout)
+    if (a.mode == 1 && !timed_out) {
+        float* P = a.part + (int64_t)blockIdx.x * kParamsPadded;
+        auto dump = [&](uint32_t col, float* dst) {  // 64 columns of this row
+#pragma unroll 1
+            for (int cb = 0; cb < 64; cb += 16) {
+                uint32_t r[16];
+                tmem_ld16(lane_base + col + cb, r);
+                tmem_ld_wait();
+                float4* o = reinterpret_cast<float4*>(dst + cb);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    o[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                       __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+            }
+        };
+        dump(cDW2 + 64 * h, P + kOffW2 + t * kHid + 64 * h);
+        dump(cDW3 + 64 * h, P + kOffW3 + t * kHid + 64 * h);
+        uint32_t r[16];
+        if (h == 0) {
+            tmem_ld16(lane_base + cDW1, r);
+            tmem_ld_wait();
+#pragma unroll
+            for (int k = 0; k < kIn; ++k) P[kOffW1 + t * kIn + k] = k < kInRaw ? __uint_as_float(r[k]) : 0.f;
+            P[kOffB1 + t] = __uint_as_float(r[kInRaw]);
+            tmem_ld16(lane_base + cDB2, r);
+            tmem_ld_wait();
+            P[kOffB2 + t] = __uint_as_float(r[0]);
+        } else {
+            tmem_ld16(lane_base + cDW4T, r);  // row t = input feature, columns = outputs
+            tmem_ld_wait();
+#pragma unroll
+            for (int k = 0; k < kOut; ++k) P[kOffW4 + k * kHid + t] = k < kOutRaw ? __uint_as_float(r[k]) : 0.f;
+            tmem_ld16(lane_base + cDB3, r);
+            tmem_ld_wait();
+            P[kOffB3 + t] = __uint_as_float(r[0]);
+        }
+        if (tid < kOut) P[kOffB4 + tid] = tid < kOutRaw ? accs[tid] : 0.f;
+        if (tid == 0) a.loss_part[blockIdx.x] = 0.5f * accs[kOutRaw] * inv_n;
+    }
+    if (timed_out && tid == 0) latch_error(a.err, NMODL_ERR_TIMEOUT);
+    // ---- release the tensor memory
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTrTmemCols);
+    }
+}
+
+// grad[i] = sum over the CTA partials in launch order.  adam: then the Adam
+// step on the FP32 master parameter (learning rate and bias corrections from
+// the arguments, or from the run's step index when fs.active) and the bf16
+// copy of the weight matrices.  Block 0 also sums the loss partials.
+__global__ void k_grad_adam(const float* __restrict__ part, int n_part,
+                            const float* __restrict__ loss_part, float* loss, float* grad,
+                            int adam, float* p, float* m, float* v, __nv_bfloat16* wbf,
+                            float lr, float b1, float b2, float eps, float bc1, float bc2,
+                            FitSched fs) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        float l = 0.f;
+        for (int c = 0; c < n_part; ++c) l += loss_part[c];
+        *loss = l;
+    }
+    if (adam && fs.active) {
+        const int64_t k = *fs.step;
+        lr = fs.lr_min + 0.5f * (fs.lr0 - fs.lr_min) *
+                             (1.0f + cosf(3.14159265358979f * (float)k / (float)fs.total));
+        const float tt = (float)(fs.t0 + k + 1);
+        bc1 = 1.f - powf(b1, tt);
+        bc2 = 1.f - powf(b2, tt);
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kParamsPadded;
+         i += gridDim.x * blockDim.x) {
+        float g = 0.f;
+        for (int c = 0; c < n_part; ++c) g += part[(int64_t)c * kParamsPadded + i];
+        if (!adam) {
+            grad[i] = g;
+            continue;
+        }
+        const float mi = b1 * m[i] + (1.f - b1) * g;
+        const float vi = b2 * v[i] + (1.f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        p[i] = pi;
+        int bi = -1;
+        if (i >= kOffW1 && i < kOffB1) bi = kBfW1 + (i - kOffW1);
+        else if (i >= kOffW2 && i < kOffB2) bi = kBfW2 + (i - kOffW2);
+        else if (i >= kOffW3 && i < kOffB3) bi = kBfW3 + (i - kOffW3);
+        else if (i >= kOffW4 && i < kOffB4) bi = kBfW4 + (i - kOffW4);
+        if (bi >= 0) wbf[bi] = __float2bfloat16_rn(pi);
+    }
+}
+
+// ------------------------------------------------------------ launchers
+
+cudaError_t train_prepare() {
+    return cudaFuncSetAttribute(k_train_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kTrSmem);
+}
+
+static int device_sms() {
+    int sms = 148, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+int train_grid(int64_t n, int* tiles_per_cta) {
+    const int sms = device_sms();
+    const int64_t tiles = (n + kTrRows - 1) / kTrRows;
+    const int64_t g0 = std::min<int64_t>(std::max(1, sms), std::max<int64_t>(1, tiles));
+    const int64_t tpc = (tiles + g0 - 1) / g0;
+    *tiles_per_cta = (int)std::max<int64_t>(1, tpc);
+    return (int)std::max<int64_t>(1, (tiles + *tiles_per_cta - 1) / *tiles_per_cta);
+}
+
+int train_max_grid(int64_t max_batch) {
+    const int64_t tiles = (max_batch + kTrRows - 1) / kTrRows;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, std::max(1, device_sms())));
+}
+
+cudaError_t launch_train_tiles(const TrainArgs& a, int grid, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_train_tiles<<<grid, kTrThreads, kTrSmem, s>>>(a);
+    return cudaGetLastError();
+}
+
+void launch_grad_adam(const float* part, int n_part, const float* loss_part, float* loss,
+                      float* grad, int adam, float* p, float* m, float* v, __nv_bfloat16* wbf,
+                      float lr, float b1, float b2, float eps, int step, FitSched fs,
+                      cudaStream_t s) {
+    const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
+    k_grad_adam<<<(kParamsPadded + 255) / 256, 256, 0, s>>>(part, n_part, loss_part, loss, grad,
+                                                            adam, p, m, v, wbf, lr, b1, b2, eps,
+                                                            bc1, bc2, fs);
+}
+
+}  // namespace nmodl

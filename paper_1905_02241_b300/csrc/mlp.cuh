@@ -4,7 +4,7 @@
 
 #include <cuda_bf16.h>
 
-#include "mma_bf16.cuh"
+#include "bf16_util.cuh"
 #include "nmodl_internal.cuh"
 
 namespace nmodl {
@@ -35,27 +35,6 @@ constexpr int kParamsPublic = kHid * kInRaw + kHid + 2 * (kHid * kHid + kHid) +
 // Input normalisation of (v, dt): v_n = (v + 20)/80, dt_n = (dt - 0.03125)/0.01875
 constexpr float kVShift = 20.f, kVScale = 80.f, kDtShift = 0.03125f, kDtScale = 0.01875f;
 
-enum Epi : int { kEpiPartial = 0, kEpiBiasSilu = 1, kEpiBias = 2, kEpiDsilu = 3 };
-
-struct GemmArgs {
-    const __nv_bfloat16* A;
-    int lda;
-    const __nv_bfloat16* B;
-    int ldb;
-    int M, N, K;
-    int k_per_split;
-    const float* bias;
-    float* Cf;
-    int ldc;
-    __nv_bfloat16* Ch;
-    int ldch;
-    const float* Zin;
-    int ldz;
-};
-
-void launch_gemm(int ta, int tb, int epi, const GemmArgs& g, int splits, cudaStream_t s);
-void launch_reduce_splits(const float* part, int splits, int64_t count, float* out,
-                          cudaStream_t s);
 // Schedule of a whole training run replayed from one captured step: the
 // kernels read the step index from device memory and derive the minibatch
 // (rows (k mod steps_per_epoch) * B of X and T), the cosine learning rate
@@ -68,18 +47,39 @@ struct FitSched {
     int32_t t0;               // Adam steps taken before the run
     int32_t active;
 };
-void launch_pack_input(const float* X, int64_t n, __nv_bfloat16* H0, cudaStream_t s,
-                       FitSched fs = FitSched{});
-int launch_loss_delta(const float* out, const float* T, int64_t B, __nv_bfloat16* delta,
-                      float* block_loss, cudaStream_t s, FitSched fs = FitSched{});
-void launch_adam_sched(float* p, const float* grad, float* m, float* v, int64_t count,
-                       float b1, float b2, float eps, FitSched fs, cudaStream_t s);
+
+// Fused training / batch-forward kernel of the surrogate MLP (k_train.cu)
+struct TrainArgs {
+    const float* X;            // [n][11] normalised inputs (FP32)
+    const float* T;            // [n][9] targets (mode 1)
+    float* Y;                  // [n][9] network outputs (mode 0)
+    int64_t n;                 // rows of the batch
+    int tiles_per_cta;         // 128-row tiles per CTA
+    int mode;                  // 0: forward outputs; 1: loss and gradient partials
+    const __nv_bfloat16* wbf;  // bf16 weight copies (kBfCount)
+    const float* params;       // FP32 master parameters (biases read here)
+    float *ds1, *ds2, *ds3;    // [n][128] SiLU'(Z) of the hidden layers (mode 1)
+    float* part;               // [grid][kParamsPadded] gradient partials (mode 1)
+    float* loss_part;          // [grid] loss partials (mode 1)
+    FitSched fs;
+    int32_t* err;
+};
+cudaError_t train_prepare();
+// CTAs for a batch of n rows (at most one per SM) and the tiles each takes
+int train_grid(int64_t n, int* tiles_per_cta);
+// the most CTAs train_grid returns for batches of up to max_batch rows
+int train_max_grid(int64_t max_batch);
+cudaError_t launch_train_tiles(const TrainArgs& a, int grid, cudaStream_t s);
+// gradient = fixed-order sum of the n_part CTA partials; adam: then the
+// Adam step (lr and the bias corrections of step `step`, or from fs when
+// active) on the master parameters and the bf16 copies; *loss = the sum of
+// the loss partials
+void launch_grad_adam(const float* part, int n_part, const float* loss_part, float* loss,
+                      float* grad, int adam, float* p, float* m, float* v, __nv_bfloat16* wbf,
+                      float lr, float b1, float b2, float eps, int step, FitSched fs,
+                      cudaStream_t s);
 // loss_steps[step] = *loss; ++step (the last kernel of a captured step)
 void launch_fit_end(float* loss_steps, const float* loss, FitSched fs, cudaStream_t s);
-void launch_colsum(const __nv_bfloat16* delta, int64_t B, int N, float* part, float* out,
-                   cudaStream_t s);
-void launch_adam(float* p, const float* grad, float* m, float* v, int64_t count, float lr,
-                 float b1, float b2, float eps, int step, cudaStream_t s);
 void launch_to_bf16(const float* src, int64_t count, __nv_bfloat16* dst, cudaStream_t s);
 
 // surrogate state update (fused MLP + projection + residual + fallback list)

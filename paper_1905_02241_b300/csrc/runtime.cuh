@@ -119,11 +119,9 @@ struct nmodl_surrogate {
     float* params = nullptr;          // FP32 master, padded layout
     __nv_bfloat16* wbf = nullptr;     // bf16 weight copies
     float *grad = nullptr, *m = nullptr, *v = nullptr;
-    __nv_bfloat16 *H0 = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr;
-    __nv_bfloat16 *D4 = nullptr, *D3 = nullptr, *D2 = nullptr, *D1 = nullptr;
-    float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *OUT = nullptr;
+    float *ds1 = nullptr, *ds2 = nullptr, *ds3 = nullptr;  // [max_batch][128] SiLU'(Z)
     float *part = nullptr, *loss_part = nullptr, *loss = nullptr;
-    int64_t part_count = 0;
+    int n_part_max = 0;                                     // CTAs of the training kernel
 };
 
 

@@ -11,7 +11,7 @@
 
 #include <stdint.h>
 
-#include "mma_bf16.cuh"
+#include "bf16_util.cuh"
 
 namespace nmodl {
 

@@ -338,11 +338,12 @@ int orc_lu_pp(int n, double *M, int *perm)
     return swaps;
 }
 
-/* Solve (P^T L U) x = b using the factors of orc_lu_pp. */
+/* Solve (P^T L U) x = b using the factors of orc_lu_pp (any n: the
+ * intermediate vector is allocated for the call). */
 void orc_lu_solve(int n, const double *LU, const int *perm, const double *b,
                   double *x)
 {
-    double y[64];
+    double *y = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     for (int i = 0; i < n; ++i) {
         double s = b[perm[i]];
         for (int c = 0; c < i; ++c)
@@ -355,6 +356,7 @@ void orc_lu_solve(int n, const double *LU, const int *perm, const double *b,
             s -= LU[i * n + c] * x[c];
         x[i] = s / LU[i * n + i];
     }
+    free(y);
 }
 
 /* One implicit Euler step of one instance by Newton iteration (Section 5.2
@@ -465,6 +467,8 @@ int orc_kin_newton_n(int ns, const double *A, double dt, const double *x, double
 {
     double J[64], r[8], delta[8];
     int perm[8];
+    if (ns < 1 || ns > 8)
+        return -1;
     for (int a = 0; a < ns; ++a)
         for (int b = 0; b < ns; ++b)
             J[a * ns + b] = (a == b ? 1.0 : 0.0) - dt * A[a * ns + b];
@@ -498,6 +502,8 @@ int orc_kin_stationary_n(int ns, const double *A, double *pi)
 {
     double M[64], b[8];
     int perm[8];
+    if (ns < 1 || ns > 8)
+        return -1;
     memcpy(M, A, ns * ns * sizeof(double));
     for (int c = 0; c < ns; ++c)
         M[(ns - 1) * ns + c] = 1.0;

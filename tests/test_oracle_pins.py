@@ -377,6 +377,18 @@ def test_p6_two_state_closed_form(orc):
     assert np.all(y[2:] == x[2:])
 
 
+def test_lu_solve_of_any_size_vs_numpy(orc):
+    """The dense LU with partial pivoting and its solve on systems larger
+    than any fixed buffer (the cable form's cells reach 400 nodes)."""
+    rng = np.random.default_rng(12)
+    for n in (1, 9, 65, 200, 401):
+        M = rng.normal(size=(n, n)) + n * np.eye(n)
+        b = rng.normal(size=n)
+        LU, perm, _ = orc.lu_pp(M)
+        x = orc.lu_solve(LU, perm, b)
+        np.testing.assert_allclose(x, np.linalg.solve(M, b), rtol=1e-10, atol=1e-12)
+
+
 def test_p6_lu_pp_vs_numpy(orc):
     rng = np.random.default_rng(5)
     for _ in range(20):
@@ -692,8 +704,8 @@ def test_pade_factor_and_second_order(orc):
     assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
 
 
-def _cable_case(seed=3, n_cells=6):
-    cab = W.cable_cells(n_cells, seed=seed, size_lo=4, size_hi=25)
+def _cable_case(seed=3, n_cells=6, size_lo=4, size_hi=25):
+    cab = W.cable_cells(n_cells, seed=seed, size_lo=size_lo, size_hi=size_hi)
     wl = W.cortical_mix(cab["n_nodes"], seed=seed + 10)
     return cab, wl
 
@@ -710,10 +722,12 @@ def test_cable_without_coupling_is_the_isolated_step(orc):
     np.testing.assert_array_equal(a[2], b[2])
 
 
-def test_cable_step_solves_the_assembled_tree_system(orc):
+@pytest.mark.parametrize("n_cells,size_lo,size_hi", [(6, 4, 25), (3, 150, 400)])
+def test_cable_step_solves_the_assembled_tree_system(orc, n_cells, size_lo, size_hi):
     """v_new - v = M^-1 rhs with M, rhs assembled here from the membrane
-    terms (rhs0, d0 of the uncoupled step) and the axial conductances."""
-    cab, wl = _cable_case(seed=4)
+    terms (rhs0, d0 of the uncoupled step) and the axial conductances; small
+    cells and cells of the benchmark's largest sizes (up to 400 nodes)."""
+    cab, wl = _cable_case(seed=4, n_cells=n_cells, size_lo=size_lo, size_hi=size_hi)
     n = cab["n_nodes"]
     st = [orc.mech_init(m["type"], m["params"], m["node_index"], wl["v0"])
           for m in wl["mechs"]]

@@ -33,69 +33,24 @@ from paper_1905_02241_b300 import workloads as W  # noqa: E402
 DT, CM, NSTEPS = 0.025, 1.0, 200
 METRIC = "mechanism instance-steps/s (state+cur)"
 
-# FP64 pipe instructions of a minimal implementation of each operation,
-# the unit of the algorithmic op count of the FP64 path (integer and FP32
-# work runs on other pipes, 32x or more faster on this GPU, and is not
-# counted): add/sub/mul/fma 1; exp 2 (table-driven with a 2048-entry table:
-# r1 = x - n L1, then T + T p; n, the rest of the reduction and the
-# degree-3 polynomial p are formed in single precision and widened by
-# integer operations); reciprocal 2 (a seed good to 2^-45 formed in single
-# precision, one Newton step e = 1 - x y, y + y e).  Per-launch constants
-# are folded (u = v/k - vh/k: 1 multiply-add; each rate's A times phi dt;
-# an EXP rate's ln|A| added to u).  A gate: each rate as numerator /
-# denominator (u: 1; EXP e^u: exp; SIGMOID A/(1 + e^-u): exp, the 1 + 2^m T
-# of 1 + e^-u = 2^m T p + (1 + 2^m T) formed by integer operations; LINOID
-# A u/(1 - e^-u): exp + 1); then minf and phi dt (alpha + beta) by two
-# divisions of 2 each (a quotient good to 2^-44 formed in single precision,
-# then r = x - y q, q + r y0) from N = Pa Db + Pb Da and D = Da Db
-# (general 3 + 2 div; an EXP rate has the denominator 1: beta EXP 1 + 2 div,
-# alpha EXP 2 + 2 div, both 1 + 1 div); then the cnexp update
-# minf + (m - minf) exp(-phi dt s) (exp, diff, fma).
-C_EXP, C_RCP, C_DIV = 2, 2, 2
-RATE_COST = {0: 1 + C_EXP, 1: 1 + C_EXP, 2: 1 + C_EXP + 1}
-CNEXP_COST = C_EXP + 1 + 1
-# per node: rhs = sum(g e) - v sum(g), d += cm/dt, 1/d, v += rhs * (1/d);
-# per current: its g e and g summed into the node (2)
-NODE_COST = 1 + 1 + C_RCP + 1
+import bench_costs as C  # noqa: E402
+
+# the algorithmic FP64 count of a step (FP64 pipe instructions of this
+# design's minimal implementation; see bench_costs)
+fp64_ops_per_step = C.fp64_ops_per_step
 
 
-def gate_tail(aform: int, bform: int) -> int:
-    """minf and alpha + beta from the two rates, then the cnexp update."""
-    if aform == 0 and bform == 0:
-        comb = 1 + C_DIV
-    elif bform == 0:
-        comb = 1 + 2 * C_DIV
-    elif aform == 0:
-        comb = 2 + 2 * C_DIV
-    else:
-        comb = 3 + 2 * C_DIV
-    return comb + CNEXP_COST
-
-
-def fp64_ops_per_step(wl) -> float:
-    """Algorithmic FP64 ops of one network time step (cur + v + state)."""
-    ops = NODE_COST * wl["n_nodes"]
-    for m in wl["mechs"]:
-        p, n = m["params"], m["node_index"].size
-        if m["type"] == W.TYPE_HH:
-            # gates m, h, n: (alpha form, beta form) = (LINOID, EXP), (EXP,
-            # SIGMOID), (LINOID, EXP); conductances gna (4 mul), gk (4 mul);
-            # three currents summed into the node (2 each)
-            per = sum(RATE_COST[a] + RATE_COST[b] + gate_tail(a, b)
-                      for a, b in ((2, 0), (0, 1), (2, 0)))
-            per += 4 + 4 + 3 * 2
-        else:
-            ng = int(p[0])
-            per = 0
-            pw = 0
-            for g in range(ng):
-                o = 6 + 9 * g
-                af, bf = int(p[o + 1]), int(p[o + 5])
-                per += RATE_COST[af] + RATE_COST[bf] + gate_tail(af, bf)
-                pw += int(p[o])
-            per += pw + 2                    # gbar x^p, then summed into the node
-        ops += per * n
-    return float(ops)
+def bf16_peaks():
+    """Measured dense bf16 tensor-core peaks (burst, sustained) in flop/s:
+    the generated MEASURED_PEAKS.json when present, else the fallback
+    figures of an earlier B300 measurement (1.8 and 1.4 PFLOP/s)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        mp = json.load(open(path))
+        return (mp["bf16_tflops"] * 1e12, mp["bf16_tflops_sustained"] * 1e12,
+                "measured (MEASURED_PEAKS.json)")
+    except (OSError, KeyError, ValueError):
+        return 1.8e15, 1.4e15, "fallback (no measured peaks file)"
 
 
 def n_instances(wl) -> int:
@@ -196,9 +151,8 @@ def main():
     ap.add_argument("--block", type=int, default=0, help="fix the fused block size")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--forms", default="all",
-                    help="comma list of batched,kinetic,surrogate,mixed_errors,pade,cable,"
-                         "ions; "
-                         "all; none")
+                    help="comma list of hh,batched,kinetic,surrogate,mixed_errors,pade,"
+                         "cable,ions; all; none")
     args = ap.parse_args()
 
     from paper_1905_02241_b300.sharding import aggregate, network_seed, rank_info
@@ -299,20 +253,29 @@ def main():
 
     # roofline of the dominant kernel (the fused tile kernel: the whole step)
     launch_ms = ms / gpu_launches
+    peak = _lib.nmodl_probe_peak(dev, 0)  # FP64 FMA lane-ops/s, measured here
+    count = fp64_ops_per_step(wl) if prec == NMODL_FP64 else C.mixed_fp64_ops_per_step(wl)
+    ops_launch = count * window
+    roof = {"bound": "alu", "pipe": "fp64",
+            "achieved": ops_launch / (launch_ms * 1e-3) / 1e12,
+            "peak": peak / 1e12, "unit": "Tops/s (FP64 pipe instructions)",
+            "peak_source": "measured DFMA probe (nmodl_probe_peak), this run",
+            "ops_per_launch": ops_launch,
+            "ops_per_instance_step": count / ninst,
+            "what": ("FP64-pipe use: this design's minimal FP64 instruction count of the "
+                     "step (exp, reciprocal and division at their 2-instruction cost here) "
+                     "over the measured launch time, against the measured FP64 peak; "
+                     "HBM is idle (traffic below) and the integer and FP32 pipes have "
+                     "headroom, so the FP64 pipe is the bound" if prec == NMODL_FP64 else
+                     "FP64 residue of the mixed step (node sums and updates) over the "
+                     "launch time, against the measured FP64 peak")}
+    roof["frac"] = roof["achieved"] / roof["peak"]
     if prec == NMODL_FP64:
-        ops_launch = fp64_ops_per_step(wl) * window
-        peak = _lib.nmodl_probe_peak(dev, 0)  # FP64 FMA lane-ops/s
-        roof = {"bound": "alu", "pipe": "fp64", "achieved": ops_launch / (launch_ms * 1e-3) / 1e12,
-                "peak": peak / 1e12, "unit": "Tops/s (FP64 pipe instructions)",
-                "peak_source": "measured DFMA probe (nmodl_probe_peak), this run",
-                "ops_per_launch": ops_launch}
-    else:
-        ops_launch = None
-        peak = _lib.nmodl_probe_peak(dev, 0)
-        roof = {"bound": "alu", "pipe": "fp64", "achieved": None, "peak": peak / 1e12,
-                "unit": "Tops/s"}
-    if roof.get("achieved") is not None:
-        roof["frac"] = roof["achieved"] / roof["peak"]
+        # the same speed against the FP64-pipe bound of routines written
+        # entirely in FP64 (a yardstick that does not move with the design)
+        full = C.fp64_ops_per_step(wl, C.ALL_FP64)
+        roof["ops_per_instance_step_all_fp64"] = full / ninst
+        roof["frac_vs_all_fp64_routines"] = (full * window / (launch_ms * 1e-3)) / peak
     # DRAM bytes per 40-step launch: dram__bytes_read.sum + dram__bytes_write.sum
     # of one ncu capture of the same kernel on the 1,000,000-node network
     # (11,548,985 instances), scaled to this network by its instance count
@@ -375,13 +338,18 @@ def main():
     forms = None
     if rank == 0 and world == 1 and args.forms != "none":
         import bench_forms as F
-        want = (["batched", "mixed_errors", "kinetic", "surrogate", "pade", "cable", "ions"]
+        want = (["hh", "batched", "mixed_errors", "kinetic", "surrogate", "pade", "cable",
+                 "ions"]
                 if args.forms == "all"
                 else args.forms.split(","))
         forms = {}
+        burst, sustained, src = bf16_peaks()
+        peaks = {"fp64": peak, "fp32": _lib.nmodl_probe_peak(dev, 1),
+                 "mufu_ex2": _lib.nmodl_probe_peak(dev, 2), "bf16_burst": burst,
+                 "bf16_sustained": sustained, "bf16_source": src}
         for name in want:
             t0 = time.perf_counter()
-            forms[name] = getattr(F, name)(dev)
+            forms[name] = getattr(F, name)(dev, peaks)
             forms[name]["seconds"] = round(time.perf_counter() - t0, 1)
 
     if rank == 0:

@@ -1,5 +1,7 @@
-"""Measurements of the three derived forms against the plain FP64 form on the
-same GPU (used by bench.py):
+"""Measurements of the derived forms against the plain FP64 form on the
+same GPU (used by bench.py), each with its roofline (bench_costs):
+
+  hh       Hodgkin-Huxley on 4,096 isolated compartments, 1,000 steps, FP64
 
   batched  the 10-type mix over 64 independent networks of log-uniform size
            (10k..500k compartments), all types in one fused launch per
@@ -13,9 +15,11 @@ same GPU (used by bench.py):
   ions     ion current write-back (ina, ik, ica) with a 3-state scheme and a
            calcium buffer reading ica, on the ion-tagged cortical mix
 
-Each entry reports instance-steps/s (state + cur) and its ratio to the FP64
-form.  Errors against the FP64 CPU oracle of the mixed forms are measured
-by the tests and by `mixed_errors` on a sub-network sample.
+Each entry reports instance-steps/s (state + cur), its ratio to the FP64
+form and a roofline block: the algorithmic count per instance-step on the
+unit that bounds it, achieved rate, measured peak and fraction.  Errors of
+the mixed and surrogate forms are reported here against the FP64 GPU path;
+the tests compare both with the FP64 CPU oracle.
 """
 from __future__ import annotations
 
@@ -24,6 +28,7 @@ import time
 import numpy as np
 import torch
 
+import bench_costs as C
 from paper_1905_02241_b300 import _lib  # noqa: F401
 from paper_1905_02241_b300 import workloads as W
 from paper_1905_02241_b300.api import NMODL_FP64, NMODL_MIXED, Context, Mechanism
@@ -55,7 +60,48 @@ def _ninst(wl):
     return int(sum(m["node_index"].size for m in wl["mechs"]))
 
 
-def batched(dev, steps=2, nsteps=200, scale=1.0):
+def _roof(count, rate, peak, pipe, unit="Tops/s", what=""):
+    """count: operations per instance-step on the bounding unit; rate:
+    instance-steps/s; peak: the unit's measured operations/s."""
+    ach = count * rate
+    return {"bound": "tensor" if pipe.startswith("bf16") else "alu", "pipe": pipe,
+            "ops_per_instance_step": count, "achieved": ach / 1e12, "peak": peak / 1e12,
+            "unit": unit, "frac": ach / peak, "what": what}
+
+
+def hh(dev, peaks, n=4096, nsteps=1000, reps=3):
+    """Hodgkin-Huxley, one instance on each of n isolated compartments,
+    v0 uniform in [-70, -60] mV, dt 0.025 ms, nsteps steps of nmodl_step
+    (fused, CUDA graphs per 40-step window), FP64.  The problem fills only
+    as many SMs as the plan has tiles, so the roofline is given against the
+    whole GPU and against the SMs the tiles can occupy."""
+    wl = W.hh_single(n, seed=1)
+    ctx = Context(dev)
+    mechs = _mechs(ctx, wl)
+    v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
+    rhs = torch.zeros_like(v)
+    d = torch.zeros_like(v)
+    for m in mechs:
+        m.init(v)
+    ctx.step(mechs, DT, CM, v, rhs, d, nsteps)           # plan, autotune, graphs
+    ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, reps)
+    rate = n * nsteps * reps / (ms * 1e-3)
+    plan = ctx.plan(mechs)
+    count = C.fp64_ops_per_step(wl) / n
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = {"instances": n, "steps_per_run": nsteps, "fp64": rate, "plan": plan,
+           "roofline": _roof(count, rate, peaks["fp64"], "fp64", what=(
+               "FP64 pipe instructions per instance-step (bench_costs), whole-GPU peak"))}
+    busy = min(plan["tiles"], sms) / sms
+    out["roofline"]["frac_of_occupied_sms"] = out["roofline"]["frac"] / busy
+    out["roofline"]["occupied_sms"] = min(plan["tiles"], sms)
+    for m in mechs:
+        m.close()
+    ctx.close()
+    return out
+
+
+def batched(dev, peaks, steps=2, nsteps=200, scale=1.0):
     wl = W.batched_networks(64, seed=3, scale=scale)
     n, ninst = wl["n_nodes"], _ninst(wl)
     out = {"networks": 64, "nodes": n, "instances": ninst, "steps_per_run": nsteps}
@@ -81,13 +127,19 @@ def batched(dev, steps=2, nsteps=200, scale=1.0):
     out["fp64"] = ninst * 40 / (ms * 1e-3)
     out["mixed_over_fp64"] = out["mixed"] / out["fp64"]
     out["launches_per_run"] = -(-nsteps // ctx.options.window)
+    out["roofline_mixed"] = _roof(C.mixed_fp64_ops_per_step(wl) / ninst, out["mixed"],
+                                  peaks["fp64"], "fp64", what=(
+                                      "FP64 residue of the mixed step (node sums, node update) "
+                                      "per instance-step, against the measured FP64 peak"))
+    out["roofline_fp64"] = _roof(C.fp64_ops_per_step(wl) / ninst, out["fp64"], peaks["fp64"],
+                                 "fp64", what="FP64 pipe instructions per instance-step")
     for m in mechs:
         m.close()
     ctx.close()
     return out
 
 
-def pade(dev, n_nodes=2_000_000, nsteps=200):
+def pade(dev, peaks, n_nodes=2_000_000, nsteps=200):
     """(1,1) Pade cnexp (Section 5.2 option) against exact cnexp, both FP64,
     on the cortical mix: throughput ratio and the state / voltage difference
     after nsteps from the same initial condition."""
@@ -119,7 +171,7 @@ def pade(dev, n_nodes=2_000_000, nsteps=200):
     return out
 
 
-def cable(dev, n_cells=10000, nsteps=200):
+def cable(dev, peaks, n_cells=10000, nsteps=200):
     """The cortical mix on cells of 20..400 compartments with tree
     morphologies: FP64 steps with the per-cell tree solve against the same
     compartments isolated (fused step), instance-steps/s."""
@@ -154,6 +206,10 @@ def cable(dev, n_cells=10000, nsteps=200):
     out["isolated_fused_fp64"] = ninst * nsteps / (ms * 1e-3)
     out["plan_isolated"] = ctx.plan(mechs)
     out["cable_over_isolated"] = out["cable_fp64"] / out["isolated_fused_fp64"]
+    out["roofline"] = _roof(C.cable_fp64_ops_per_step(wl, cab["parent"]) / ninst,
+                            out["cable_fp64"], peaks["fp64"], "fp64", what=(
+                                "FP64 pipe instructions per instance-step with the tree "
+                                "solve in place of the diagonal update"))
     cb.close()
     for m in mechs:
         m.close()
@@ -166,7 +222,7 @@ def _ion_mechs(ctx, wl):
                       ion=m.get("ion", 0)) for m in wl["mechs"]]
 
 
-def ions(dev, n_nodes=2_000_000, nsteps=200):
+def ions(dev, peaks, n_nodes=2_000_000, nsteps=200):
     """USEION write-back and the small systems on the ion-tagged cortical mix
     (10 cnexp types writing ina/ik/ica, a 3-state potassium scheme on half
     of the nodes, one calcium buffer per node reading ica), all in the fused
@@ -233,6 +289,10 @@ def ions(dev, n_nodes=2_000_000, nsteps=200):
     out["fused_over_per_mechanism"] = out["network_fp64"] / out["network_per_mechanism_fp64"]
     out["ion_writeback_cost"] = out["no_buffer_no_ions_fp64"] / out["no_buffer_ions_fp64"]
     out["mixed_over_fp64"] = out["network_mixed"] / out["network_fp64"]
+    out["roofline_fp64"] = _roof(C.fp64_ops_per_step(wl) / _ninst(wl), out["network_fp64"],
+                                 peaks["fp64"], "fp64", what=(
+                                     "FP64 pipe instructions per instance-step (cnexp types, "
+                                     "3-state solve, buffer Newton with 4 updates)"))
     # kernels alone, 8M instances, one per node
     n = 8_000_000
     ni = torch.arange(n, dtype=torch.int32, device=dv)
@@ -260,43 +320,65 @@ def ions(dev, n_nodes=2_000_000, nsteps=200):
     return out
 
 
-def mixed_errors(dev, n_nodes=1500, nsteps=200):
-    """Per-quantity error of the MIXED fused step against the FP64 oracle on
-    a sub-network of the cortical mix (max over nodes / instances)."""
-    from oracle import oracle as orc
+def mixed_errors(dev, peaks, n_nodes=2_000_000, nsteps=200):
+    """Per-quantity difference of the MIXED fused step from the FP64 fused
+    step on the whole cortical network after nsteps from the same initial
+    state (the FP64 step itself agrees with the FP64 CPU oracle, which the
+    tests check; they also compare the MIXED step with the oracle directly).
+    States: max |difference| per type and gate; v in mV; rhs and d of the
+    last step relative to the node's d (rhs against 200 mV x d); currents:
+    per type, the per-node current of that type evaluated from each run's
+    final states and v, max |difference| over nodes relative to the type's
+    largest per-node current."""
     wl = W.cortical_mix(n_nodes, seed=2)
-    st0 = [orc.mech_init(m["type"], m["params"], m["node_index"], wl["v0"])
-           for m in wl["mechs"]]
-    ctx = Context(dev, precision=NMODL_MIXED)
-    mechs = _mechs(ctx, wl)
-    for m, s in zip(mechs, st0):
-        if m.n_states:
-            m.set_states(torch.tensor(s, device=f"cuda:{dev}"))
-    v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
-    rhs = torch.zeros_like(v)
-    d = torch.zeros_like(v)
-    ctx.step(mechs, DT, CM, v, rhs, d, nsteps)
-    ctx.check()
-    v_ref, r_ref, d_ref, s_ref = orc.step(wl["mechs"], st0, wl["v0"], n_nodes, DT,
-                                          nsteps=nsteps)
-    res = {"steps": nsteps, "nodes": n_nodes,
-           "v_abs_mV": float(np.max(np.abs(v.cpu().numpy() - v_ref))),
-           "d_rel": float(np.max(np.abs(d.cpu().numpy() - d_ref) / d_ref)),
-           "rhs_rel_to_200mV_d": float(np.max(np.abs(rhs.cpu().numpy() - r_ref) /
-                                              (200 * d_ref)))}
-    per_state = {}
-    for m, s, spec in zip(mechs, s_ref, W.CORTICAL_TYPES):
-        if m.n_states:
-            err = np.max(np.abs(m.states().cpu().numpy() - s), axis=1)
-            per_state[spec[0]] = [float(x) for x in err]
-    res["state_abs"] = per_state
-    for m in mechs:
-        m.close()
-    ctx.close()
+    dv = f"cuda:{dev}"
+    res = {"steps": nsteps, "nodes": n_nodes, "instances": _ninst(wl)}
+    runs = {}
+    for name, prec in (("fp64", NMODL_FP64), ("mixed", NMODL_MIXED)):
+        ctx = Context(dev, precision=prec)
+        mechs = _mechs(ctx, wl)
+        v = torch.tensor(wl["v0"], device=dv)
+        rhs = torch.zeros_like(v)
+        d = torch.zeros_like(v)
+        for m in mechs:
+            m.init(v)
+        ctx.step(mechs, DT, CM, v, rhs, d, nsteps)
+        ctx.check()
+        runs[name] = (v, rhs, d, [m.states() for m in mechs], ctx, mechs)
+    v64, r64, d64, s64, ctx64, mechs64 = runs["fp64"]
+    vmx, rmx, dmx, smx, ctxmx, mechsmx = runs["mixed"]
+    dv_abs = (vmx - v64).abs()
+    res["v_abs_mV_max"] = float(dv_abs.max())
+    res["v_abs_mV_median"] = float(dv_abs.median())
+    res["d_rel_max"] = float(((dmx - d64).abs() / d64).max())
+    res["rhs_rel_to_200mV_d_max"] = float(((rmx - r64).abs() / (200 * d64)).max())
+    per_state, per_cur = {}, {}
+    zero = torch.zeros_like(v64)
+    for k, (spec, a64, amx) in enumerate(zip(W.CORTICAL_TYPES, s64, smx)):
+        if a64.shape[0]:
+            per_state[spec[0]] = [float(x) for x in (amx - a64).abs().max(dim=1).values]
+        # the type's current per node from each run's states and v (FP64 call)
+        m = mechs64[k]
+        cur = []
+        for st, vv in ((a64, v64), (amx, vmx)):
+            if st.shape[0]:
+                m.set_states(st)
+            r = zero.clone()
+            m.cur(vv, r, zero.clone())
+            cur.append(r)
+        ctx64.check()
+        scale = float(cur[0].abs().max())
+        per_cur[spec[0]] = float((cur[1] - cur[0]).abs().max()) / max(scale, 1e-300)
+    res["state_abs_max"] = per_state
+    res["current_rel_max"] = per_cur
+    for name in runs:
+        for m in runs[name][5]:
+            m.close()
+        runs[name][4].close()
     return res
 
 
-def kinetic(dev, n=1_000_000, nsteps=200, steps=1):
+def kinetic(dev, peaks, n=1_000_000, nsteps=200, steps=1):
     wl = W.kin9_clamped(n, seed=4)
     out = {"instances": n, "steps_per_run": nsteps}
     x0 = torch.tensor(wl["x0"], device=f"cuda:{dev}")
@@ -319,27 +401,51 @@ def kinetic(dev, n=1_000_000, nsteps=200, steps=1):
     diff = (out.pop("mixed_final") - out.pop("fp64_final")).abs().sum(dim=0)
     out["mixed_over_fp64"] = out["mixed"] / out["fp64"]
     out["mixed_max_l1_vs_fp64"] = float(diff.max())
+    out["roofline_fp64"] = _roof(C.kin9_fp64_ops(out["fp64_updates_per_solve"]), out["fp64"],
+                                 peaks["fp64"], "fp64", what=(
+                                     "FP64 pipe instructions per instance-step: rates, banded "
+                                     "LU, Newton updates, current"))
+    out["roofline_mixed"] = _roof(C.kin9_mixed_fp64_ops(out["mixed_updates_per_solve"]),
+                                  out["mixed"], peaks["fp64"], "fp64", what=(
+                                      "FP64 residue per instance-step: diagonal of J, FP64 "
+                                      "residuals and updates, current"))
     return out
 
 
-def surrogate(dev, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=60):
+def surrogate(dev, peaks, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=60):
+    """The kinetic surrogate: FP64 Newton pairs, training (tensor-core
+    kernels), then 200 gated steps on n clamped instances against the FP64
+    and FP32-LU Newton solves; the inference kernel alone (every prediction
+    kept); rooflines of inference (tensor and special-function units) and of
+    training (tensor)."""
     from paper_1905_02241_b300.surrogate import Surrogate, attach, make_training_pairs
     p = W.kin9_params(W.Stream(4, 401))
     out = {"instances": n, "steps_per_run": nsteps, "training_pairs": n_pairs,
            "epochs": epochs, "tolerance": 1e-4}
     ctx = Context(dev, clamp_v=1)
     t0 = time.perf_counter()
-    sur = Surrogate(ctx, max_batch=8192)
+    batch = 8192
+    sur = Surrogate(ctx, max_batch=batch)
     Ws, bs = W.mlp_init(7)
     sur.set_weights(Surrogate.pack(Ws, bs))
     X, T = make_training_pairs(ctx, sur, p, n_pairs, seed=6)
     torch.cuda.synchronize()
     out["pairs_seconds"] = round(time.perf_counter() - t0, 2)
     t0 = time.perf_counter()
-    losses = sur.fit(X, T, epochs=epochs, batch=8192, lr=2e-3)
+    losses = sur.fit(X, T, epochs=epochs, batch=batch, lr=2e-3)
     torch.cuda.synchronize()
-    out["train_seconds"] = round(time.perf_counter() - t0, 2)
+    train_s = time.perf_counter() - t0
+    out["train_seconds"] = round(train_s, 2)
     out["final_loss"] = float(losses[-1])
+    rows = (n_pairs // batch) * batch * epochs
+    out["train_epoch_seconds"] = train_s / epochs
+    out["train_optimiser_step_us"] = train_s / (rows / batch) * 1e6
+    out["roofline_training"] = _roof(
+        C.TRAIN_FLOPS_PER_ROW, rows / train_s, peaks["bf16_sustained"], "bf16_sustained",
+        unit="TFLOP/s", what=("BF16 MMA flops per training row (forward, backward and "
+                              "weight-gradient products, padded shapes) over the wall time of "
+                              "the run (graph-replayed optimiser steps of 8,192 rows), "
+                              "against the sustained bf16 peak (" + peaks["bf16_source"] + ")"))
     del X, T
     wl = W.kin9_clamped(n, seed=5)
     x0 = torch.tensor(wl["x0"], device=f"cuda:{dev}")
@@ -371,11 +477,26 @@ def surrogate(dev, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=60):
     ms = _time(lambda: ctx.step([m], DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["surrogate_mixed_fallback"] = n * nsteps / (ms * 1e-3)
     out["fallback_rate_mixed"] = (m.stats()["fallback"] - fb0) / (n * nsteps)
+    # the inference kernel alone: every prediction kept (no fallback work)
+    attach(m, sur, 1e30)
+    m.set_states(x0)
+    m.state(DT, v)
+    reps = 10
+    ms = _time(lambda: [m.state(DT, v) for _ in range(reps)], ctx, 1)
+    out["surrogate_kernel_alone"] = n * reps / (ms * 1e-3)
     attach(m, None)
     m.set_states(x0)
     ms = _time(lambda: ctx.step([m], DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["newton_mixed"] = n * nsteps / (ms * 1e-3)
     out["surrogate_over_newton_mixed"] = out["surrogate_mixed_fallback"] / out["newton_mixed"]
+    for key, rate in (("kernel_alone", out["surrogate_kernel_alone"]),
+                      ("end_to_end", out["surrogate_mixed_fallback"])):
+        out["roofline_" + key] = _roof(
+            C.MLP_FLOPS, rate, peaks["bf16_sustained"], "bf16_sustained", unit="TFLOP/s",
+            what=("BF16 MMA flops of the MLP per instance-step (K and N padded to 16), "
+                  "against the sustained bf16 peak (" + peaks["bf16_source"] + ")"))
+        out["roofline_" + key]["frac_of_burst"] = C.MLP_FLOPS * rate / peaks["bf16_burst"]
+        out["roofline_" + key]["mufu_frac"] = C.SUR_MUFU * rate / peaks["mufu_ex2"]
     m.close()
     sur.close()
     ctx.close()

@@ -752,6 +752,12 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
             const int64_t per = (int64_t)sm_smem / k - (int64_t)stat - reserved;
             if (per >= 16 * 1024) budgets.push_back((size_t)(per / 1024 * 1024));
         }
+        // networks too small to give every SM a 16 KB tile: smaller tiles
+        // spread them over more SMs (a 32-node group is the smallest tile)
+        if (p->n_nodes <= 148 * 256) {
+            budgets.push_back(4 * 1024);
+            budgets.push_back(8 * 1024);
+        }
         std::sort(budgets.begin(), budgets.end());
         budgets.erase(std::unique(budgets.begin(), budgets.end()), budgets.end());
     }

@@ -58,3 +58,13 @@ def sub_network(wl, nodes):
         mechs.append(dict(type=m["type"], params=m["params"],
                           node_index=remap[m["node_index"][keep]].astype(np.int32)))
     return dict(n_nodes=nodes.size, mechs=mechs), sel
+
+
+def oracle_cable_cells(sub, nsteps):
+    """Pool worker (CPU only): the oracle's INITIAL and nsteps cable steps of
+    a sub-network of whole cells (dict of nodes, mechs, parent, ga, gb, v0)."""
+    from oracle import oracle as orc
+    st0 = [orc.mech_init(m["type"], m["params"], m["node_index"], sub["v0"])
+           for m in sub["mechs"]]
+    return orc.step_cable(sub["mechs"], st0, sub["v0"], sub["n_nodes"], sub["parent"],
+                          sub["ga"], sub["gb"], 0.025, nsteps=nsteps)

@@ -60,4 +60,62 @@ def test_cost_model_of_hh():
 def test_cost_model_of_the_cortical_mix_is_in_range():
     wl = W.cortical_mix(20000, seed=2)
     per = bench.fp64_ops_per_step(wl) / bench.n_instances(wl)
-    assert 25.0 < per < 35.0   # 29.4 on the 1M-node mix; the kernel executes 33.0
+    assert 25.0 < per < 35.0
+
+
+# ------------------------------------------------------------------------
+# The other forms' counts (bench_costs), each against a hand count.
+
+import bench_costs as C  # noqa: E402
+
+
+def test_banded_lu_of_the_lattice_scheme():
+    # 9 states, band |i - j| <= 3: pivots k = 0..5 each eliminate 3 rows,
+    # each row a multiplier + 3 updates (12); k = 6: 2 rows of 1 + 2 (6);
+    # k = 7: 1 row of 1 + 1 (2); 9 reciprocals of 2.  A solve: one fma per
+    # off-diagonal band entry (2 (8 + 7 + 6) = 42) and a multiply per row (9).
+    assert C._band_lu_counts(9, 3, C.DESIGN) == (6 * 12 + 6 + 2 + 9 * 2, 42 + 9)
+
+
+def test_kinetic_counts():
+    # rates 24 (fma + exp 2); diagonal 24; LU 98; per update residual 9 + 24,
+    # solve 51, y += delta 9; current 5; node 1
+    assert C.kin9_fp64_ops(2.0) == 24 * 3 + 24 + 98 + 2 * (33 + 51 + 9) + 5 + 1
+    assert C.kin9_fp64_ops(2.0, C.ALL_FP64) == 24 * 9 + 24 + (80 + 9 * 3) + 2 * (33 + 51 + 9) + 6
+    # mixed: diagonal 24, per update residual 33 + update 9, current and node 6
+    assert C.kin9_mixed_fp64_ops(3.0) == 24 + 3 * 42 + 6
+
+
+def test_small_system_counts():
+    # 3-state: 6 rates (mul, exp, mul), 12 for M, 3 reciprocals + 8, solve 9, current 3
+    assert C.kin3_fp64_ops() == 6 * 4 + 12 + (3 * 2 + 8) + 9 + 3
+    # buffer: source 1 + 4 updates of residual 11, Jacobian 7, reciprocal 2, update 8
+    assert C.cacum_fp64_ops() == 1 + 4 * (11 + 7 + 2 + 8)
+
+
+def test_all_fp64_yardstick_prices_each_routine_in_fp64():
+    wl = _one_gate(SIG, LIN, 2)
+    # design: SIG 3, LIN 4, tail 3 + 2*2 + 4 = 11; all-FP64: SIG 1 + 8 + 1,
+    # LIN 1 + 8 + 1 + 1, tail 3 + 2*6 + 8 + 2
+    assert C.fp64_ops_per_step(wl) == (NODE + 3 + 4 + 11 + 2 + 2) * wl["n_nodes"]
+    all64 = (1 + 1 + 3 + 1) + 10 + 11 + (3 + 12 + 8 + 2) + 2 + 2
+    assert C.fp64_ops_per_step(wl, C.ALL_FP64) == all64 * wl["n_nodes"]
+
+
+def test_mixed_residue_and_cable_counts():
+    n = 50
+    hh = dict(n_nodes=n, mechs=[dict(type=W.TYPE_HH, params=W.hh_params(),
+                                     node_index=np.arange(n, dtype=np.int32))])
+    assert C.mixed_fp64_ops_per_step(hh) == (NODE + 3 * 2) * n
+    # a chain of n nodes (one root): the diagonal update's 1/d and product
+    # (3 per node) give way to the tree solve: per non-root node 4 + 2 + 2,
+    # per node the pivot reciprocal + 1 and v += dv
+    parent = np.arange(-1, n - 1)
+    assert C.cable_fp64_ops_per_step(hh, parent) == (
+        C.fp64_ops_per_step(hh) - 3 * n + (n - 1) * 8 + n * 4)
+
+
+def test_surrogate_flop_counts():
+    assert C.MLP_FLOPS == 2 * (16 * 128 + 128 * 128 + 128 * 128 + 128 * 16) == 73728
+    # backward: D4 W4 (K 16), D3 W3, D2 W2; weight gradients as the forward
+    assert C.TRAIN_FLOPS_PER_ROW == 73728 + 2 * (16 * 128 + 2 * 128 * 128) + 73728

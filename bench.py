@@ -151,8 +151,8 @@ def main():
     ap.add_argument("--block", type=int, default=0, help="fix the fused block size")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--forms", default="all",
-                    help="comma list of hh,batched,kinetic,surrogate,mixed_errors,pade,"
-                         "cable,ions; all; none")
+                    help="comma list of hh,batched,kinetic,kin9_network,surrogate,"
+                         "mixed_errors,pade,cable,ions; all; none")
     args = ap.parse_args()
 
     from paper_1905_02241_b300.sharding import aggregate, network_seed, rank_info
@@ -338,8 +338,8 @@ def main():
     forms = None
     if rank == 0 and world == 1 and args.forms != "none":
         import bench_forms as F
-        want = (["hh", "batched", "mixed_errors", "kinetic", "surrogate", "pade", "cable",
-                 "ions"]
+        want = (["hh", "batched", "mixed_errors", "kinetic", "kin9_network", "surrogate", "pade",
+                 "cable", "ions"]
                 if args.forms == "all"
                 else args.forms.split(","))
         forms = {}

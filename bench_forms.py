@@ -193,14 +193,12 @@ def cable(dev, peaks, n_cells=10000, nsteps=200):
     out["plan_cable"] = ctx.plan(mechs)
     ms = _time(lambda: cb.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["cable_fp64"] = ninst * nsteps / (ms * 1e-3)
-    # the per-step launch sequence (taken when a 9-state mechanism is in the
-    # list: an empty one here)
-    k9 = Mechanism(ctx, W.TYPE_KIN9, np.zeros(0, np.int32), cab["n_nodes"],
-                   W.kin9_params(W.Stream(4, 401)))
-    cb.step(mechs + [k9], DT, CM, v, rhs, d, 40)
-    ms = _time(lambda: cb.step(mechs + [k9], DT, CM, v, rhs, d, nsteps), ctx, 1)
+    # the per-step launch sequence (the no_fuse option)
+    ctx.set_options(no_fuse=1)
+    cb.step(mechs, DT, CM, v, rhs, d, 40)
+    ms = _time(lambda: cb.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["cable_per_step_launches_fp64"] = ninst * nsteps / (ms * 1e-3)
-    k9.close()
+    ctx.set_options(no_fuse=0)
     ctx.step(mechs, DT, CM, v, rhs, d, 40)
     ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["isolated_fused_fp64"] = ninst * nsteps / (ms * 1e-3)
@@ -214,6 +212,47 @@ def cable(dev, peaks, n_cells=10000, nsteps=200):
     for m in mechs:
         m.close()
     ctx.close()
+    return out
+
+
+def kin9_network(dev, peaks, n_nodes=1_000_000, frac=0.25, nsteps=200):
+    """The cortical mix on n_nodes compartments with the 9-state kinetic
+    scheme on a seeded 25 % of them (one instance each, v not clamped): all
+    mechanism types in the fused tile kernel (its KIN variant) against the
+    per-mechanism launch sequence (no_fuse), FP64 and MIXED."""
+    wl = W.cortical_mix(n_nodes, seed=2)
+    ni = np.nonzero(W.Stream(2, 901).uniform(n_nodes) < frac)[0].astype(np.int32)
+    wl["mechs"].append(dict(type=W.TYPE_KIN9, params=W.kin9_params(W.Stream(4, 401)),
+                            node_index=ni, name="kin9"))
+    ninst = _ninst(wl)
+    out = {"nodes": n_nodes, "instances": ninst, "kin9_instances": int(ni.size),
+           "steps_per_run": nsteps}
+    for name, prec, nf in (("fused_fp64", NMODL_FP64, 0), ("per_mechanism_fp64", NMODL_FP64, 1),
+                           ("fused_mixed", NMODL_MIXED, 0),
+                           ("per_mechanism_mixed", NMODL_MIXED, 1)):
+        ctx = Context(dev, precision=prec, no_fuse=nf)
+        mechs = _mechs(ctx, wl)
+        v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
+        rhs = torch.zeros_like(v)
+        d = torch.zeros_like(v)
+        for m in mechs:
+            m.init(v)
+        ctx.step(mechs, DT, CM, v, rhs, d, 40)
+        ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
+        out[name] = ninst * nsteps / (ms * 1e-3)
+        if name == "fused_fp64":
+            out["plan_fused"] = ctx.plan(mechs)
+        for m in mechs:
+            m.close()
+        ctx.close()
+    out["fused_over_per_mechanism_fp64"] = out["fused_fp64"] / out["per_mechanism_fp64"]
+    out["fused_over_per_mechanism_mixed"] = out["fused_mixed"] / out["per_mechanism_mixed"]
+    iso = wl["mechs"][:-1]
+    count = (C.fp64_ops_per_step(dict(n_nodes=n_nodes, mechs=iso))
+             + C.kin9_fp64_ops(2.0) * ni.size) / ninst
+    out["roofline_fused_fp64"] = _roof(count, out["fused_fp64"], peaks["fp64"], "fp64", what=(
+        "FP64 pipe instructions per instance-step (cnexp types and the 9-state Newton solve "
+        "with 2 updates)"))
     return out
 
 
@@ -269,12 +308,11 @@ def ions(dev, peaks, n_nodes=2_000_000, nsteps=200):
         for m in mechs:
             m.close()
         ctx.close()
-    # the per-mechanism launch sequence (an empty 9-state mechanism in the list)
-    ctx = Context(dev)
+    # the per-mechanism launch sequence (the no_fuse option)
+    ctx = Context(dev, no_fuse=1)
     arrs = [torch.zeros_like(v0) for _ in range(3)]
     ctx.set_ions(*arrs)
-    mechs = _ion_mechs(ctx, wl) + [Mechanism(ctx, W.TYPE_KIN9, np.zeros(0, np.int32), n_nodes,
-                                             W.kin9_params(W.Stream(4, 401)))]
+    mechs = _ion_mechs(ctx, wl)
     v = v0.clone()
     rhs = torch.zeros_like(v)
     d = torch.zeros_like(v)

@@ -148,7 +148,10 @@ typedef struct nmodl_options {
                                 Pade approximant (1 - x/2)/(1 + x/2), the
                                 cheaper form of Section 5.2; second order,
                                 A- but not L-stable (0)                     */
-    int32_t reserved[4];
+    int32_t no_fuse;         /* 1: nmodl_step and nmodl_step_cable run the
+                                per-mechanism launch sequence even where the
+                                fused tile kernel applies (comparisons) (0)  */
+    int32_t reserved[3];
 } nmodl_options;
 
 typedef struct nmodl_stats_t {
@@ -247,13 +250,15 @@ NMODL_API int nmodl_cur(nmodl_mech *m, const double *v, double *rhs, double *d);
  *   d += 1e-3 cm/dt; v += rhs/d (skipped with options.clamp_v);
  *   nrn_state of every mechanism at the new v.
  * On return rhs and d hold the last step's values.  When every mechanism is
- * NMODL_HH, NMODL_CNEXP, NMODL_KIN3 or NMODL_CACUM (at most 16 of them) the
- * steps run in one fused kernel per window of options.window steps, each
- * node tile's states staged in shared memory for the window (the
- * compartments are not coupled; ion arrays, when registered, are summed per
- * node in the tile and the buffer reads the tile's ica); otherwise (e.g. a
- * NMODL_KIN9 in the list) each step is a sequence of per-mechanism launches.
- * nsteps = 0 is a no-op. */
+ * NMODL_HH, NMODL_CNEXP, NMODL_KIN3, NMODL_CACUM or NMODL_KIN9 without an
+ * attached surrogate (at most 16 mechanisms and 48 state rows in all) and
+ * options.no_fuse is 0, the steps run in one fused kernel per window of
+ * options.window steps, each node tile's states staged in shared memory for
+ * the window (the compartments are not coupled; ion arrays, when
+ * registered, are summed per node in the tile and the buffer reads the
+ * tile's ica; a 9-state instance's Newton solve runs in one thread);
+ * otherwise (e.g. a NMODL_KIN9 with a surrogate) each step is a sequence of
+ * per-mechanism launches.  nsteps = 0 is a no-op. */
 NMODL_API int nmodl_step(nmodl_ctx *ctx, nmodl_mech *const *mechs, int n_mechs,
                double dt, double cm, double *v, double *rhs, double *d,
                int nsteps);

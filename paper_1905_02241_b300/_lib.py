@@ -38,7 +38,8 @@ class nmodl_options(ctypes.Structure):
                 ("window", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("clamp_v", ctypes.c_int32),
                 ("tile_smem", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("cnexp_pade", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("cnexp_pade", ctypes.c_int32), ("no_fuse", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class nmodl_stats_t(ctypes.Structure):

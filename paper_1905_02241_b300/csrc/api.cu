@@ -155,6 +155,14 @@ static int build_desc(nmodl_mech* m) {
             if (k.af[e] < 0.0 || k.ab[e] < 0.0) return NMODL_ERR_ARG;
         }
         m->n_states = kKinStates;
+        // the fused kernel's view: kind, state count and the current
+        m->md = MechD{};
+        m->md.kind = NMODL_KIN9;
+        m->md.n_gates = kKinStates;
+        m->md.gbar = k.gbar;
+        m->md.e = k.e;
+        m->md.open = k.open;
+        m->md.ion = m->ion;
         return NMODL_OK;
     }
     return NMODL_ERR_ARG;
@@ -225,6 +233,7 @@ static int check_options(const nmodl_options* o) {
     if (o->ir_max < 0 || o->ir_max > 64) return NMODL_ERR_ARG;
     if (o->window < 1) return NMODL_ERR_ARG;
     if (o->cnexp_pade != 0 && o->cnexp_pade != 1) return NMODL_ERR_ARG;
+    if (o->no_fuse != 0 && o->no_fuse != 1) return NMODL_ERR_ARG;
     if (o->tile_smem < 0 || o->block < 0 || o->block > kFusedMaxBlock || (o->block % 32))
         return NMODL_ERR_ARG;
     return NMODL_OK;
@@ -652,6 +661,28 @@ static void add_cable_sched(const nmodl_cable* cb, int T, std::vector<int32_t>& 
     recs.swap(r2);
 }
 
+// The plan's device descriptors (once): MechD of every mechanism, and the
+// Kin9D rate constants of the 9-state ones (zero for the others).
+static cudaError_t upload_descriptors(nmodl_ctx* c, Plan* p, nmodl_mech* const* mechs, int T) {
+    if (p->d_md) return cudaSuccess;
+    cudaError_t e = dalloc(&p->d_md, T);
+    if (e == cudaSuccess) e = dalloc(&p->d_k9, T);
+    if (e != cudaSuccess) return e;
+    std::vector<MechD> mds(T);
+    std::vector<Kin9D> k9s(T, Kin9D{});
+    for (int t = 0; t < T; ++t) {
+        mds[t] = mechs[t]->md;
+        if (mechs[t]->type == NMODL_KIN9) k9s[t] = mechs[t]->kd;
+    }
+    e = cudaMemcpyAsync(p->d_md, mds.data(), T * sizeof(MechD), cudaMemcpyHostToDevice,
+                        c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_k9, k9s.data(), T * sizeof(Kin9D), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e;
+}
+
 struct Candidate {
     size_t budget;
     int block;
@@ -668,18 +699,28 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     p->cable = cb;
     p->precision = c->opt.precision;
     p->n_nodes = mechs[0]->n_nodes;
-    // the fused tile kernel covers HH, CNEXP and the small systems (KIN3,
-    // CACUM), with or without ion arrays
-    bool cnexp = n_mechs <= kMaxMechsFused;
-    for (int i = 0; i < n_mechs; ++i)
-        if (mechs[i]->type != NMODL_HH && mechs[i]->type != NMODL_CNEXP &&
-            mechs[i]->type != NMODL_KIN3 && mechs[i]->type != NMODL_CACUM)
+    // the fused tile kernel covers HH, CNEXP, the small systems (KIN3,
+    // CACUM) and the 9-state scheme (without an attached surrogate, whose
+    // inference runs on the tensor cores), with or without ion arrays, as
+    // long as the tile's per-state bookkeeping fits
+    bool cnexp = n_mechs <= kMaxMechsFused && !c->opt.no_fuse;
+    int state_rows = 0;
+    for (int i = 0; i < n_mechs; ++i) {
+        const int ty = mechs[i]->type;
+        if (ty != NMODL_HH && ty != NMODL_CNEXP && ty != NMODL_KIN3 && ty != NMODL_CACUM &&
+            !(ty == NMODL_KIN9 && !mechs[i]->sur))
             cnexp = false;
+        state_rows += mechs[i]->n_states;
+    }
+    if (state_rows > kMaxMechsFused * kMaxGates) cnexp = false;
     const bool ions = c->has_ions();
     bool ext = ions;  // the kernel variant with the small systems and ion sums
-    for (int i = 0; i < n_mechs; ++i)
+    bool kin = false;  // ... and the 9-state scheme
+    for (int i = 0; i < n_mechs; ++i) {
         if (mechs[i]->type == NMODL_KIN3 || mechs[i]->type == NMODL_CACUM) ext = true;
-    p->variant = p->precision + (ext ? 2 : 0);
+        if (mechs[i]->type == NMODL_KIN9) ext = kin = true;
+    }
+    p->variant = p->precision + (ext ? 2 : 0) + (kin ? 2 : 0);
     p->fused = false;
     const bool dbg = std::getenv("NMODL_PLAN_DEBUG") != nullptr;
     if (!cnexp || p->n_nodes == 0) {
@@ -764,8 +805,9 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     else budgets = {std::min<size_t>(cap, 96 * 1024)};
     size_t items = 0;
     for (int t = 0; t < T; ++t) items += (size_t)gates[t] * mechs[t]->n;
-    if (c->opt.block > 0) blocks = {c->opt.block};
-    else if (tune) blocks = {128, 256, 512, 1024};
+    const int max_block = kin ? kFusedKinBlock : kFusedMaxBlock;
+    if (c->opt.block > 0) blocks = {std::min(c->opt.block, max_block)};
+    else if (tune) blocks = kin ? std::vector<int>{128, 256} : std::vector<int>{128, 256, 512, 1024};
     else blocks = {256};
     pers = tune ? std::vector<bool>{false, true} : std::vector<bool>{false};
 
@@ -886,15 +928,9 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
             a.newton_max_iter = c->opt.newton_max_iter;
             a.ir_max = c->opt.ir_max;
             // descriptors
-            if (!p->d_md) {
-                if (dalloc(&p->d_md, T) != cudaSuccess) return -1.0;
-                std::vector<MechD> mds(T);
-                for (int t = 0; t < T; ++t) mds[t] = mechs[t]->md;
-                cudaMemcpyAsync(p->d_md, mds.data(), T * sizeof(MechD), cudaMemcpyHostToDevice,
-                                c->stream);
-                cudaStreamSynchronize(c->stream);
-            }
+            if (upload_descriptors(c, p, mechs, T) != cudaSuccess) return -1.0;
             a.md = p->d_md;
+            a.k9d = p->d_k9;
             double best_ms = 1e30;
             for (int rep = 0; rep < 2 && ok; ++rep) {
                 if (cd.persistent) cudaMemsetAsync(d_counter, 0, sizeof(int32_t), c->stream);
@@ -981,12 +1017,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
         cudaMemcpyAsync(p->d_sched, ch.sched->data(), ch.sched->size() * sizeof(uint16_t),
                         cudaMemcpyHostToDevice, c->stream);
     }
-    if (!p->d_md) {
-        if ((e = dalloc(&p->d_md, T)) != cudaSuccess) return cuda_status(e);
-        std::vector<MechD> mds(T);
-        for (int t = 0; t < T; ++t) mds[t] = mechs[t]->md;
-        cudaMemcpyAsync(p->d_md, mds.data(), T * sizeof(MechD), cudaMemcpyHostToDevice, c->stream);
-    }
+    if ((e = upload_descriptors(c, p, mechs, T)) != cudaSuccess) return cuda_status(e);
     cudaStreamSynchronize(c->stream);  // host buffers above go out of scope
     p->fused = true;
     return NMODL_OK;
@@ -1014,6 +1045,7 @@ static FusedArgs fused_args(nmodl_ctx* c, Plan* p, double dt, double cm, double*
                             double* rhs, double* d, int nsteps) {
     FusedArgs a{};
     a.md = p->d_md;
+    a.k9d = p->d_k9;
     a.n_types = (int)p->mechs.size();
     for (int t = 0; t < a.n_types; ++t) {
         nmodl_mech* m = p->mechs[t];

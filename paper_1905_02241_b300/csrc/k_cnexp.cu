@@ -14,11 +14,14 @@
 //                    exchange data; cable form: tiles of whole cells with the
 //                    tree solve inside); HH, CNEXP and, in the EXT
 //                    instantiation, the 3-state scheme, the calcium buffer
-//                    and ion sums
+//                    and ion sums; in the KIN instantiation also the 9-state
+//                    scheme (one thread per instance runs its banded Newton
+//                    solve)
 #include <algorithm>
 #include <climits>
 
 #include "kernels.cuh"
+#include "kin9.cuh"
 #include "small_systems.cuh"
 
 namespace nmodl {
@@ -328,9 +331,10 @@ __device__ void block_inclusive_scan_u16(uint16_t* a, int n, int* wsum) {
 // elimination (1984; no fill because parents precede children) scheduled by
 // levels.  v += the solution.  On the last step of the window rhs and d
 // report the assembled system.
-template <int PREC, bool EXT>
-__global__ void __launch_bounds__(kFusedMaxBlock)
+template <int PREC, bool EXT, bool KIN>
+__global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock)
     k_fused_tiles(FusedArgs A) {
+    static_assert(!KIN || EXT, "the 9-state scheme comes with the extended variant");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ MechD md_s[kMaxMechsFused];
     __shared__ GateF gf_s[kMaxMechsFused][kMaxGates];
@@ -354,6 +358,11 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     // MIXED with the small systems: their parameters in FP32
     __shared__ Kin3F k3f_s[EXT ? kMaxMechsFused : 1];
     __shared__ CacumF cdf_s[EXT ? kMaxMechsFused : 1];
+    // the 9-state scheme's rate constants folded with this launch's dt:
+    // FP64 dt k = exp(b v + ln(dt a)) with ln(dt a) in place of a; MIXED the
+    // FP32 b_f, b_b, ln(dt a_f), ln(dt a_b)
+    __shared__ Kin9D k9_s[KIN ? kMaxMechsFused : 1];
+    __shared__ float k9f_s[(KIN && PREC == NMODL_MIXED) ? kMaxMechsFused : 1][4 * kKinEdges];
 
     __shared__ int tile_s;
     __shared__ int inst_start[kMaxMechsFused + 1];  // instance offset of each type
@@ -365,13 +374,35 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
     const int T = A.n_types;
     for (int k = tid; k < T * (int)(sizeof(MechD) / 4); k += blockDim.x)
         ((int32_t*)md_s)[k] = ((const int32_t*)A.md)[k];
+    if constexpr (KIN)
+        for (int k = tid; k < T * (int)(sizeof(Kin9D) / 4); k += blockDim.x)
+            ((int32_t*)k9_s)[k] = ((const int32_t*)A.k9d)[k];
     if constexpr (PREC == NMODL_FP64) {
         // gate parameters folded for this launch (u by one multiply-add,
         // rates carrying phi dt); ordered by the first barrier of the loop
         __syncthreads();
         for (int k = tid; k < T * kMaxGates; k += blockDim.x) {
             MechD& M = md_s[k / kMaxGates];
-            if (k % kMaxGates < M.n_gates) fold_gate(M.gate[k % kMaxGates], M.phi * A.dt);
+            if (M.kind != NMODL_KIN9 && k % kMaxGates < M.n_gates)
+                fold_gate(M.gate[k % kMaxGates], M.phi * A.dt);
+        }
+    }
+    if constexpr (KIN) {
+        __syncthreads();
+        for (int k = tid; k < T * kKinEdges; k += blockDim.x) {
+            const int t = k / kKinEdges, e = k % kKinEdges;
+            if (md_s[t].kind != NMODL_KIN9) continue;
+            Kin9D& K = k9_s[t];
+            const double lf = log(A.dt * K.af[e]), lb = log(A.dt * K.ab[e]);
+            if constexpr (PREC == NMODL_MIXED) {
+                k9f_s[t][e] = (float)K.bf[e];
+                k9f_s[t][kKinEdges + e] = (float)K.bb[e];
+                k9f_s[t][2 * kKinEdges + e] = (float)lf;
+                k9f_s[t][3 * kKinEdges + e] = (float)lb;
+            } else {
+                K.af[e] = lf;
+                K.ab[e] = lb;
+            }
         }
     }
 
@@ -418,9 +449,9 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         for (int p = 0; p < q; ++p) {
             const int t = pair_t[p], g = pair_g[p], kind = md_s[t].kind;
             int key;
-            if (EXT && (kind == NMODL_KIN3 || kind == NMODL_CACUM)) {
+            if (EXT && (kind == NMODL_KIN3 || kind == NMODL_CACUM || (KIN && kind == NMODL_KIN9))) {
                 if (g != 0) continue;
-                key = kind == NMODL_KIN3 ? 9 : 10;
+                key = kind == NMODL_KIN3 ? 9 : kind == NMODL_CACUM ? 10 : 11;
             } else {
                 key = md_s[t].gate[g].aform * 3 + md_s[t].gate[g].bform;
             }
@@ -644,6 +675,8 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 g1 = M.hh_g[1] * nn * nn * nn * nn;
             } else if (EXT && M.kind == NMODL_KIN3) {
                 g0 = M.k3.gbar * st[M.k3.open * cnt + j];
+            } else if (KIN && M.kind == NMODL_KIN9) {
+                g0 = M.gbar * st[M.open * cnt + j];
             } else {
                 double gg = M.gbar;
                 for (int gi = 0; gi < M.n_gates; ++gi)
@@ -660,6 +693,9 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
             } else if (EXT && M.kind == NMODL_KIN3) {
                 const float2 x = st[M.k3.open * cnt + j];
                 g0 = M.k3.gbar * (f2d_int(x.x) + f2d_int(x.y));
+            } else if (KIN && M.kind == NMODL_KIN9) {
+                const float2 x = st[M.open * cnt + j];
+                g0 = M.gbar * (f2d_int(x.x) + f2d_int(x.y));
             } else {
                 float gf = cf_p[0];
                 for (int gi = 0; gi < M.n_gates; ++gi) {
@@ -698,6 +734,8 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                             xg_s[sl + 2].y = M.hh_g[2];
                         } else if (EXT && M.kind == NMODL_KIN3) {
                             xg_s[sl].y = M.k3.gbar * st[M.k3.open * cnt + j];
+                        } else if (KIN && M.kind == NMODL_KIN9) {
+                            xg_s[sl].y = M.gbar * st[M.open * cnt + j];
                         } else {
                             double gg = M.gbar;
                             for (int gi = 0; gi < M.n_gates; ++gi)
@@ -715,6 +753,9 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                         } else if (EXT && M.kind == NMODL_KIN3) {
                             const float2 x = st[M.k3.open * cnt + j];
                             xg_s[sl].y = M.k3.gbar * (f2d_int(x.x) + f2d_int(x.y));
+                        } else if (KIN && M.kind == NMODL_KIN9) {
+                            const float2 x = st[M.open * cnt + j];
+                            xg_s[sl].y = M.gbar * (f2d_int(x.x) + f2d_int(x.y));
                         } else {
                             float gf = cf_p[0];
                             for (int gi = 0; gi < M.n_gates; ++gi) {
@@ -897,6 +938,51 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
         // index) of gate g of type t, instance j
         auto item = [&](int k, int t, int g, int j) {
             const int kind = EXT ? md_s[t].kind : NMODL_CNEXP;
+            if (KIN && kind == NMODL_KIN9) {
+                // the implicit-Euler Newton solve of one instance (kin9.cuh)
+                if (g != 0) return;
+                const int cnt = cnt_s[t], nd = nid_s[nid_off[t] + j];
+                double x[9], y[9];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const int o = st_off[t] + a * cnt + j;
+                    x[a] = PREC == NMODL_FP64 ? st_d[o] : f2d_int(st_f[o].x) + f2d_int(st_f[o].y);
+                }
+                bool nonconv;
+                if constexpr (PREC == NMODL_FP64) {
+                    const Kin9D& K = k9_s[t];
+                    const double vv = v_s[nd];
+                    double dk_f[kKinEdges], dk_b[kKinEdges];
+#pragma unroll
+                    for (int e = 0; e < kKinEdges; ++e) {
+                        dk_f[e] = exp_tang(fma(K.bf[e], vv, K.af[e]));
+                        dk_b[e] = exp_tang(fma(-K.bb[e], vv, K.ab[e]));
+                    }
+                    kin9_newton_d(dk_f, dk_b, x, y, A.newton_tol, A.newton_max_iter, nonconv);
+                } else {
+                    const float* kf = k9f_s[t];
+                    const float vf = vf_s[nd];
+                    float dk_f[kKinEdges], dk_b[kKinEdges];
+#pragma unroll
+                    for (int e = 0; e < kKinEdges; ++e) {
+                        dk_f[e] = __expf(fmaf(kf[e], vf, kf[2 * kKinEdges + e]));
+                        dk_b[e] = __expf(fmaf(-kf[kKinEdges + e], vf, kf[3 * kKinEdges + e]));
+                    }
+                    kin9_refine_mixed(dk_f, dk_b, x, y, A.newton_tol, 1 + A.ir_max, nonconv);
+                }
+                if (nonconv) latch_error(A.err, NMODL_ERR_NOCONV);
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const int o = st_off[t] + a * cnt + j;
+                    if (PREC == NMODL_FP64) {
+                        st_d[o] = y[a];
+                    } else {
+                        const float hi = d2f_int(y[a]);
+                        st_f[o] = make_float2(hi, d2f_int(y[a] - f2d_int(hi)));
+                    }
+                }
+                return;
+            }
             if (EXT && (kind == NMODL_KIN3 || kind == NMODL_CACUM)) {
                 // coupled states: the item of the first state updates all
                 if (g != 0) return;
@@ -954,8 +1040,10 @@ __global__ void __launch_bounds__(kFusedMaxBlock)
                 st_f[k] = m;
             }
         };
-        if constexpr (PREC == NMODL_FP64) {
-            // work order (slots past a pair's count are a group's padding)
+        if constexpr (PREC == NMODL_FP64 || KIN) {
+            // work order (slots past a pair's count are a group's padding;
+            // with the 9-state scheme MIXED takes it too, so that its one item
+            // per instance does not leave eight of nine lanes idle)
             int wi = 0;
             for (int w = tid; w < wstart_s[n_work]; w += blockDim.x) {
                 while (w >= wstart_s[wi + 1]) ++wi;
@@ -1048,15 +1136,18 @@ void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
 
 // grid = blocks of this launch (one per tile, or the resident count in the
 // persistent form)
-// variant = precision + 2 * ext: ext instantiates the kernel with the small
-// systems and ion sums (EXT); plain HH/CNEXP plans use the leaner variant
+// variant = precision + 2 * ext + 2 * kin: ext instantiates the kernel with
+// the small systems and ion sums (EXT); kin adds the 9-state scheme (KIN);
+// plain HH/CNEXP plans use the leanest variant
 using FusedKernel = void (*)(FusedArgs);
 static FusedKernel fused_kernel(int variant) {
     switch (variant) {
-    case 0: return k_fused_tiles<NMODL_FP64, false>;
-    case 1: return k_fused_tiles<NMODL_MIXED, false>;
-    case 2: return k_fused_tiles<NMODL_FP64, true>;
-    default: return k_fused_tiles<NMODL_MIXED, true>;
+    case 0: return k_fused_tiles<NMODL_FP64, false, false>;
+    case 1: return k_fused_tiles<NMODL_MIXED, false, false>;
+    case 2: return k_fused_tiles<NMODL_FP64, true, false>;
+    case 3: return k_fused_tiles<NMODL_MIXED, true, false>;
+    case 4: return k_fused_tiles<NMODL_FP64, true, true>;
+    default: return k_fused_tiles<NMODL_MIXED, true, true>;
     }
 }
 

@@ -3,76 +3,20 @@
 // The KINETIC scheme is the linear ODE x' = A(v) x (Section 5.1); one
 // implicit Euler step solves F(y) = y - x - dt A y = 0 by Newton iteration
 // with the exact Jacobian J = I - dt A (Section 5.2 derivimplicit, Section
-// 5.3 Newton + LU).  One thread owns one instance.  J is a nonsingular
-// M-matrix whose columns sum to one (columns of -dt A sum to 0), so LU with
-// partial pivoting makes no row interchanges and the no-pivot LU below
-// performs the same eliminations.  States are numbered 3a+b on a 3x3
-// lattice whose edges join indices differing by 1 (same row) or 3, so J and
-// its LU factors live inside the band |i - j| <= 3; every loop is unrolled
-// at compile time and only band entries are ever touched.
+// 5.3 Newton + LU).  One thread owns one instance; the banded no-pivot LU
+// and the Newton / refinement loops are in kin9.cuh (shared with the fused
+// tile kernel).
 //
 // FP64 form: rates, J, LU, residual and update in double.
-// MIXED form: rates and the LU factorisation in FP32; the residual
-// F(y) = J y - x (with J's diagonal rebuilt in FP64 so that its columns keep
-// summing exactly to one) and the update of y in FP64; the FP32 factors
-// refine y until max|delta| <= tol or ir_max refinements.
+// MIXED form: rates and the LU factorisation in FP32; the FP64 residual and
+// update refine y until max|delta| <= tol or ir_max refinements.
 #include <algorithm>
 #include <cmath>
 
 #include "kernels.cuh"
+#include "kin9.cuh"
 
 namespace nmodl {
-
-namespace {
-
-
-__host__ __device__ constexpr bool in_band(int i, int j) { return (i - j <= 3) && (j - i <= 3); }
-
-// In-place no-pivot LU of the banded 9x9 matrix M (only band entries used);
-// the diagonal is replaced by the reciprocals of the pivots, so that the
-// triangular solves multiply instead of divide.
-// pivot reciprocal: the refined hardware reciprocal in FP64, IEEE in FP32
-__device__ __forceinline__ double recip(double x) { return rcp_fast(x); }
-__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
-
-template <typename R>
-__device__ __forceinline__ void lu_band(R (&M)[9][9]) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const R rp = recip(M[k][k]);
-        M[k][k] = rp;
-#pragma unroll
-        for (int i = k + 1; i < 9; ++i) {
-            if (!in_band(i, k)) continue;
-            const R l = M[i][k] * rp;
-            M[i][k] = l;
-#pragma unroll
-            for (int j = k + 1; j < 9; ++j) {
-                if (!in_band(k, j) || !in_band(i, j)) continue;
-                M[i][j] -= l * M[k][j];
-            }
-        }
-    }
-}
-
-// Solve L U z = b in place (b -> z).
-template <typename R>
-__device__ __forceinline__ void lu_band_solve(const R (&M)[9][9], R (&b)[9]) {
-#pragma unroll
-    for (int i = 1; i < 9; ++i)
-#pragma unroll
-        for (int c = 0; c < i; ++c)
-            if (in_band(i, c)) b[i] -= M[i][c] * b[c];
-#pragma unroll
-    for (int i = 8; i >= 0; --i) {
-#pragma unroll
-        for (int c = i + 1; c < 9; ++c)
-            if (in_band(i, c)) b[i] -= M[i][c] * b[c];
-        b[i] = b[i] * M[i][i];
-    }
-}
-
-}  // namespace
 
 // ------------------------------------------------------------- INITIAL
 // Stationary distribution: A pi = 0 with sum(pi) = 1, solved as the square
@@ -174,10 +118,7 @@ __global__ void __launch_bounds__(128)
         const double dt = dt_arr ? dt_arr[i] : dt_scalar;
         double x[9], y[9];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            x[a] = st[a * stride + i];
-            y[a] = x[a];
-        }
+        for (int a = 0; a < 9; ++a) x[a] = st[a * stride + i];
         if (PREC == NMODL_FP64) {
             double dk_f[kKinEdges], dk_b[kKinEdges];
             if (dt_arr) {
@@ -193,47 +134,7 @@ __global__ void __launch_bounds__(128)
                     dk_b[e] = exp_tang(fma(-K.bb[e], vv, lnc_s[kKinEdges + e]));
                 }
             }
-            double diag[9];
-#pragma unroll
-            for (int a = 0; a < 9; ++a) diag[a] = 1.0;
-#pragma unroll
-            for (int e = 0; e < kKinEdges; ++e) {
-                diag[edge_lo(e)] += dk_f[e];
-                diag[edge_hi(e)] += dk_b[e];
-            }
-            double M[9][9];
-#pragma unroll
-            for (int a = 0; a < 9; ++a)
-#pragma unroll
-                for (int b = 0; b < 9; ++b)
-                    if (in_band(a, b)) M[a][b] = (a == b) ? diag[a] : 0.0;
-#pragma unroll
-            for (int e = 0; e < kKinEdges; ++e) {
-                M[edge_hi(e)][edge_lo(e)] = -dk_f[e];
-                M[edge_lo(e)][edge_hi(e)] = -dk_b[e];
-            }
-            lu_band(M);
-            while (iters < max_iter) {
-                // r = -(J y - x)
-                double r[9];
-#pragma unroll
-                for (int a = 0; a < 9; ++a) r[a] = x[a] - diag[a] * y[a];
-#pragma unroll
-                for (int e = 0; e < kKinEdges; ++e) {
-                    r[edge_hi(e)] += dk_f[e] * y[edge_lo(e)];
-                    r[edge_lo(e)] += dk_b[e] * y[edge_hi(e)];
-                }
-                lu_band_solve(M, r);
-                double dmax = 0.0;
-#pragma unroll
-                for (int a = 0; a < 9; ++a) {
-                    y[a] += r[a];
-                    dmax = fmax(dmax, fabs(r[a]));
-                }
-                ++iters;
-                if (dmax <= tol) break;
-                if (iters == max_iter) nonconv = true;
-            }
+            iters = kin9_newton_d(dk_f, dk_b, x, y, tol, max_iter, nonconv);
         } else {
             float dk_f[kKinEdges], dk_b[kKinEdges];
             const float vf = d2f_int(vv);
@@ -251,57 +152,7 @@ __global__ void __launch_bounds__(128)
                     dk_b[e] = __expf(fmaf(-kf_s[kKinEdges + e], vf, kf_s[3 * kKinEdges + e]));
                 }
             }
-            // FP64 copies of the FP32 rates (exact, integer pipe), and the
-            // FP64 diagonal from them: columns of J sum to 1
-            double dkd_f[kKinEdges], dkd_b[kKinEdges], diag[9];
-#pragma unroll
-            for (int e = 0; e < kKinEdges; ++e) {
-                dkd_f[e] = f2d_int(dk_f[e]);
-                dkd_b[e] = f2d_int(dk_b[e]);
-            }
-#pragma unroll
-            for (int a = 0; a < 9; ++a) diag[a] = 1.0;
-#pragma unroll
-            for (int e = 0; e < kKinEdges; ++e) {
-                diag[edge_lo(e)] += dkd_f[e];
-                diag[edge_hi(e)] += dkd_b[e];
-            }
-            float M[9][9];
-#pragma unroll
-            for (int a = 0; a < 9; ++a)
-#pragma unroll
-                for (int b = 0; b < 9; ++b)
-                    if (in_band(a, b)) M[a][b] = (a == b) ? d2f_int(diag[a]) : 0.0f;
-#pragma unroll
-            for (int e = 0; e < kKinEdges; ++e) {
-                M[edge_hi(e)][edge_lo(e)] = -dk_f[e];
-                M[edge_lo(e)][edge_hi(e)] = -dk_b[e];
-            }
-            lu_band(M);
-            const int cap = 1 + ir_max;
-            while (iters < cap) {
-                double r[9];
-#pragma unroll
-                for (int a = 0; a < 9; ++a) r[a] = x[a] - diag[a] * y[a];
-#pragma unroll
-                for (int e = 0; e < kKinEdges; ++e) {
-                    r[edge_hi(e)] += dkd_f[e] * y[edge_lo(e)];
-                    r[edge_lo(e)] += dkd_b[e] * y[edge_hi(e)];
-                }
-                float rf[9];
-#pragma unroll
-                for (int a = 0; a < 9; ++a) rf[a] = d2f_int(r[a]);
-                lu_band_solve(M, rf);
-                float dmax = 0.0f;
-#pragma unroll
-                for (int a = 0; a < 9; ++a) {
-                    y[a] += f2d_int(rf[a]);
-                    dmax = fmaxf(dmax, fabsf(rf[a]));
-                }
-                ++iters;
-                if (f2d_int(dmax) <= tol) break;
-                if (iters == cap) nonconv = true;
-            }
+            iters = kin9_refine_mixed(dk_f, dk_b, x, y, tol, 1 + ir_max, nonconv);
         }
 #pragma unroll
         for (int a = 0; a < 9; ++a) {

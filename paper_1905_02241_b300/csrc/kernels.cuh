@@ -8,6 +8,9 @@
 namespace nmodl {
 
 constexpr int kFusedMaxBlock = 1024;
+// block limit of the fused variant with the 9-state scheme (its banded
+// Newton solve holds ~200 registers per thread)
+constexpr int kFusedKinBlock = 256;
 
 // node-major slots per instance of the fused step's flat layout: one
 // (e, g) per current (HH: sodium, potassium, leak; the calcium buffer none)
@@ -18,6 +21,7 @@ __host__ __device__ constexpr int flat_slots(int kind) {
 // Arguments of the fused multi-step tile kernel (passed by value).
 struct FusedArgs {
     const MechD* md;                       // n_types descriptors
+    const Kin9D* k9d;                      // n_types (NMODL_KIN9 entries used)
     int32_t n_types;
     int32_t n_gates[kMaxMechsFused];
     double* states[kMaxMechsFused];        // SoA, row stride below
@@ -67,8 +71,9 @@ void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
                     const int32_t* chunk, const int32_t* ni, const double* v,
                     const double* st, int64_t stride, double* rhs, double* d,
                     double* ion_a, double* ion_b, int32_t* err, cudaStream_t s);
-// variant = precision + 2 * ext (ext: the kernel instantiated with the small
-// systems KIN3 / CACUM and the ion sums)
+// variant = precision + 2 * ext + 2 * kin (ext: the kernel instantiated with
+// the small systems KIN3 / CACUM and the ion sums; kin: ext and the 9-state
+// scheme, variants 4 and 5, blocks of at most kFusedKinBlock)
 cudaError_t launch_fused(int variant, const FusedArgs& a, int grid, int block,
                          size_t smem, cudaStream_t s);
 int fused_resident_grid(int variant, int n_tiles, int block, size_t smem);

@@ -44,16 +44,18 @@ struct CacumD {
 };
 
 // Device descriptor of one mechanism of the fused step (staged in shared
-// memory): HH, CNEXP, and the small systems KIN3 and CACUM.
+// memory): HH, CNEXP, the small systems KIN3 and CACUM, and the current of
+// NMODL_KIN9 (whose rate constants travel in a Kin9D).
 struct MechD {
-    int32_t kind;     // NMODL_HH, NMODL_CNEXP, NMODL_KIN3 or NMODL_CACUM
+    int32_t kind;     // NMODL_HH, NMODL_CNEXP, NMODL_KIN3, NMODL_CACUM or NMODL_KIN9
     int32_t n_gates;  // states per instance (3 for HH)
     double phi;       // temperature factor
     double gbar, e;   // CNEXP single current
     double hh_g[3];   // HH gnabar, gkbar, gl
     double hh_e[3];   // HH ena, ek, el
     GateD gate[kMaxGates];
-    int32_t ion, pad; // USEION WRITE tag of the whole current
+    int32_t ion;      // USEION WRITE tag of the whole current
+    int32_t open;     // NMODL_KIN9: open state (gbar, e above hold its current)
     Kin3D k3;         // NMODL_KIN3
     CacumD cd;        // NMODL_CACUM
 };

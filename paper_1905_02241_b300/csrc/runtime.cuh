@@ -54,6 +54,7 @@ struct Plan {
     size_t smem = 0;
     int32_t* d_tiles = nullptr;
     nmodl::MechD* d_md = nullptr;
+    nmodl::Kin9D* d_k9 = nullptr;   // rate constants of the 9-state mechanisms
     int32_t* d_counter = nullptr;   // persistent form's tile queue
     uint16_t* d_sched = nullptr;    // cable form: level schedules of the tiles
     bool persistent = false;
@@ -64,6 +65,7 @@ struct Plan {
         for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
         cudaFree(d_tiles);
         cudaFree(d_md);
+        cudaFree(d_k9);
         cudaFree(d_counter);
         cudaFree(d_sched);
     }

@@ -76,8 +76,7 @@ def test_cable_mixed_precision(api, orc):
 def test_cable_fused_tiles_match_per_step_path(api, orc, prec):
     """The fused form (tiles of whole cells, tree solve in shared memory) on
     many small tiles against the oracle and against the per-step launch
-    sequence (taken when a 9-state mechanism is in the list; an empty one
-    here): v, rhs, d, states."""
+    sequence (the no_fuse option): v, rhs, d, states."""
     cab, wl = _case(8, 120)
     n = cab["n_nodes"]
     P = api.NMODL_FP64 if prec == "fp64" else api.NMODL_MIXED
@@ -85,11 +84,9 @@ def test_cable_fused_tiles_match_per_step_path(api, orc, prec):
            for m in wl["mechs"]]
     out = {}
     for form in ("fused", "per_step"):
-        ctx = api.Context(0, precision=P, tile_smem=32 * 1024, window=7)
+        ctx = api.Context(0, precision=P, tile_smem=32 * 1024, window=7,
+                          no_fuse=int(form == "per_step"))
         mechs = make_mechs(ctx, wl)
-        if form == "per_step":
-            mechs.append(api.Mechanism(ctx, api.NMODL_KIN9, np.zeros(0, np.int32), n,
-                                       W.kin9_params(W.Stream(4, 401))))
         for m, s in zip(mechs, st0):
             if m.n_states:
                 m.set_states(to_dev(s))

@@ -275,20 +275,18 @@ def test_network_one_step_parity(api, orc):
 def test_network_fused_and_per_mechanism_paths_agree(api, orc, prec):
     """The ion-tagged network with the 3-state scheme and the buffer in the
     fused tile kernel (several tiles) against the per-mechanism launch
-    sequence (forced by an empty 9-state mechanism in the list): v, rhs, d,
+    sequence (forced by the no_fuse option): v, rhs, d,
     the ion arrays and every state after 12 steps."""
     net = W.cortical_ions(3000, seed=22)
     n = net["n_nodes"]
     P = api.NMODL_FP64 if prec == "fp64" else api.NMODL_MIXED
     res = {}
     for form in ("fused", "per_mechanism"):
-        ctx = api.Context(0, precision=P, tile_smem=24 * 1024, window=5)
+        ctx = api.Context(0, precision=P, tile_smem=24 * 1024, window=5,
+                          no_fuse=int(form == "per_mechanism"))
         ions = [torch.zeros(n, dtype=torch.float64, device="cuda:0") for _ in range(3)]
         ctx.set_ions(*ions)
         ms = [mech(api, ctx, m, n) for m in net["mechs"]]
-        if form == "per_mechanism":
-            ms.append(api.Mechanism(ctx, api.NMODL_KIN9, np.zeros(0, np.int32), n,
-                                    W.kin9_params(W.Stream(4, 401))))
         v = to_dev(net["v0"])
         for m in ms:
             m.init(v)
@@ -340,8 +338,9 @@ def test_network_trajectory_and_determinism(api, orc):
 
 
 def test_plan_forms(api):
-    """Ion arrays keep the fused plan; a 9-state mechanism in the list does
-    not fuse; unregistering the arrays keeps the fused plan."""
+    """Ion arrays keep the fused plan; the no_fuse option gives the
+    per-mechanism plan and switching it back the fused one; unregistering
+    the arrays keeps the fused plan."""
     net = W.cortical_mix(2000, seed=19)
     n = net["n_nodes"]
     ctx = api.Context(0)
@@ -353,10 +352,10 @@ def test_plan_forms(api):
     ctx.set_ions(ina=ina)
     ctx.step(ms, 0.025, 1.0, v, rhs, d, 3)
     assert ctx.plan(ms)["fused"] == 1
-    k9 = api.Mechanism(ctx, api.NMODL_KIN9, np.zeros(0, np.int32), n,
-                       W.kin9_params(W.Stream(4, 401)))
-    ctx.step(ms + [k9], 0.025, 1.0, v, rhs, d, 3)
-    assert ctx.plan(ms + [k9])["fused"] == 0
+    ctx.set_options(no_fuse=1)
+    ctx.step(ms, 0.025, 1.0, v, rhs, d, 3)
+    assert ctx.plan(ms)["fused"] == 0
+    ctx.set_options(no_fuse=0)
     ctx.set_ions()
     ctx.step(ms, 0.025, 1.0, v, rhs, d, 3)
     assert ctx.plan(ms)["fused"] == 1
@@ -398,13 +397,10 @@ def test_cable_with_ions_fused_matches_per_step(api):
     net = W.cortical_ions(n, seed=25, kin3_frac=0.5)
     res = {}
     for form in ("fused", "per_step"):
-        ctx = api.Context(0, tile_smem=48 * 1024, window=6)
+        ctx = api.Context(0, tile_smem=48 * 1024, window=6, no_fuse=int(form == "per_step"))
         ions = [torch.zeros(n, dtype=torch.float64, device="cuda:0") for _ in range(3)]
         ctx.set_ions(*ions)
         ms = [mech(api, ctx, m, n) for m in net["mechs"]]
-        if form == "per_step":
-            ms.append(api.Mechanism(ctx, api.NMODL_KIN9, np.zeros(0, np.int32), n,
-                                    W.kin9_params(W.Stream(4, 401))))
         v = to_dev(net["v0"])
         for m in ms:
             m.init(v)

@@ -491,18 +491,21 @@ def surrogate(dev, peaks, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=60
     rhs = torch.zeros_like(v)
     d = torch.zeros_like(v)
     (m,) = _mechs(ctx, wl)
+    ctx.step([m], DT, CM, v, rhs, d, 2)        # plan (autotuned) outside the timing
     m.set_states(x0)
     ms = _time(lambda: ctx.step([m], DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["newton_fp64"] = n * nsteps / (ms * 1e-3)
     ref = m.states()
     m.close()
     (m,) = _mechs(ctx, wl)
-    m.set_states(x0)
     attach(m, sur, 1e-4)
+    ctx.step([m], DT, CM, v, rhs, d, 2)
+    m.set_states(x0)
+    fb_warm = m.stats()["fallback"]
     ms = _time(lambda: ctx.step([m], DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["surrogate"] = n * nsteps / (ms * 1e-3)
     st = m.stats()
-    out["fallback_rate"] = st["fallback"] / (n * nsteps)
+    out["fallback_rate"] = (st["fallback"] - fb_warm) / (n * nsteps)
     err = (m.states() - ref).abs().sum(dim=0)
     out["final_max_l1_vs_newton"] = float(err.max())
     out["final_mean_l1_vs_newton"] = float(err.mean())
@@ -523,6 +526,7 @@ def surrogate(dev, peaks, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=60
     ms = _time(lambda: [m.state(DT, v) for _ in range(reps)], ctx, 1)
     out["surrogate_kernel_alone"] = n * reps / (ms * 1e-3)
     attach(m, None)
+    ctx.step([m], DT, CM, v, rhs, d, 2)        # plan (autotuned) outside the timing
     m.set_states(x0)
     ms = _time(lambda: ctx.step([m], DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["newton_mixed"] = n * nsteps / (ms * 1e-3)

@@ -713,6 +713,13 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
         state_rows += mechs[i]->n_states;
     }
     if (state_rows > kMaxMechsFused * kMaxGates) cnexp = false;
+    // A list of 9-state schemes alone gains nothing from the tile kernel in
+    // MIXED (measured on 1M instances: 0.9x the standalone Newton kernel,
+    // whose smaller FP32 factorisation keeps more blocks per SM; FP64 1.09x):
+    // it keeps the per-mechanism launches there.
+    bool only_kin9 = true;
+    for (int i = 0; i < n_mechs; ++i) only_kin9 = only_kin9 && mechs[i]->type == NMODL_KIN9;
+    if (only_kin9 && c->opt.precision == NMODL_MIXED) cnexp = false;
     const bool ions = c->has_ions();
     bool ext = ions;  // the kernel variant with the small systems and ion sums
     bool kin = false;  // ... and the 9-state scheme
@@ -1053,6 +1060,8 @@ static FusedArgs fused_args(nmodl_ctx* c, Plan* p, double dt, double cm, double*
         a.states[t] = m->d_states;
         a.stride[t] = m->stride;
         a.ni[t] = m->d_ni;
+        if (m->type == NMODL_KIN9 || m->type == NMODL_KIN3 || m->type == NMODL_CACUM)
+            a.cnt[t] = m->d_cnt;
     }
     a.tiles = p->d_tiles;
     a.tile_stride = p->tile_stride;

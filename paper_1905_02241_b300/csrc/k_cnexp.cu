@@ -362,6 +362,10 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock)
     // FP64 dt k = exp(b v + ln(dt a)) with ln(dt a) in place of a; MIXED the
     // FP32 b_f, b_b, ln(dt a_f), ln(dt a_b)
     __shared__ Kin9D k9_s[KIN ? kMaxMechsFused : 1];
+    // per-block Newton / refinement counts of the coupled systems, added to
+    // the mechanisms' counters once at the end
+    __shared__ unsigned long long kit_s[EXT ? kMaxMechsFused : 1], knc_s[EXT ? kMaxMechsFused : 1];
+    __shared__ int kmx_s[EXT ? kMaxMechsFused : 1];
     __shared__ float k9f_s[(KIN && PREC == NMODL_MIXED) ? kMaxMechsFused : 1][4 * kKinEdges];
 
     __shared__ int tile_s;
@@ -374,6 +378,28 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock)
     const int T = A.n_types;
     for (int k = tid; k < T * (int)(sizeof(MechD) / 4); k += blockDim.x)
         ((int32_t*)md_s)[k] = ((const int32_t*)A.md)[k];
+    if constexpr (EXT)
+        if (tid < T) {
+            kit_s[tid] = 0;
+            knc_s[tid] = 0;
+            kmx_s[tid] = 0;
+        }
+    // counts of one solve of type t: summed over the lanes of the warp that
+    // solve the same type, then one shared atomic per warp and type (flushed
+    // to the mechanisms' counters at the end)
+    auto count_solve = [&](int t, int iters, bool failed) {
+        if constexpr (EXT) {
+            const unsigned same = __match_any_sync(__activemask(), t);
+            const unsigned sum = __reduce_add_sync(same, (unsigned)iters);
+            const unsigned nf = __reduce_add_sync(same, failed ? 1u : 0u);
+            const unsigned mx = __reduce_max_sync(same, (unsigned)iters);
+            if ((int)(threadIdx.x & 31) == __ffs(same) - 1) {
+                atomicAdd(&kit_s[t], (unsigned long long)sum);
+                if (nf) atomicAdd(&knc_s[t], (unsigned long long)nf);
+                atomicMax(&kmx_s[t], (int)mx);
+            }
+        }
+    };
     if constexpr (KIN)
         for (int k = tid; k < T * (int)(sizeof(Kin9D) / 4); k += blockDim.x)
             ((int32_t*)k9_s)[k] = ((const int32_t*)A.k9d)[k];
@@ -949,6 +975,7 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock)
                     x[a] = PREC == NMODL_FP64 ? st_d[o] : f2d_int(st_f[o].x) + f2d_int(st_f[o].y);
                 }
                 bool nonconv;
+                int iters;
                 if constexpr (PREC == NMODL_FP64) {
                     const Kin9D& K = k9_s[t];
                     const double vv = v_s[nd];
@@ -958,7 +985,7 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock)
                         dk_f[e] = exp_tang(fma(K.bf[e], vv, K.af[e]));
                         dk_b[e] = exp_tang(fma(-K.bb[e], vv, K.ab[e]));
                     }
-                    kin9_newton_d(dk_f, dk_b, x, y, A.newton_tol, A.newton_max_iter, nonconv);
+                    iters = kin9_newton_d(dk_f, dk_b, x, y, A.newton_tol, A.newton_max_iter, nonconv);
                 } else {
                     const float* kf = k9f_s[t];
                     const float vf = vf_s[nd];
@@ -968,9 +995,10 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock)
                         dk_f[e] = __expf(fmaf(kf[e], vf, kf[2 * kKinEdges + e]));
                         dk_b[e] = __expf(fmaf(-kf[kKinEdges + e], vf, kf[3 * kKinEdges + e]));
                     }
-                    kin9_refine_mixed(dk_f, dk_b, x, y, A.newton_tol, 1 + A.ir_max, nonconv);
+                    iters = kin9_refine_mixed(dk_f, dk_b, x, y, A.newton_tol, 1 + A.ir_max, nonconv);
                 }
                 if (nonconv) latch_error(A.err, NMODL_ERR_NOCONV);
+                count_solve(t, iters, nonconv);
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
                     const int o = st_off[t] + a * cnt + j;
@@ -995,20 +1023,22 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock)
                 }
                 // failed: the refinement or Newton iteration reached its cap
                 bool failed = false, conv = true;
+                int iters = 1;
                 if (kind == NMODL_KIN3) {
                     if (PREC == NMODL_FP64)
                         kin3_step_d(md_s[t].k3, v_s[nd], A.dt, x);
                     else
-                        kin3_step_mixed(k3f_s[t], vf_s[nd], d2f_int(A.dt), A.newton_tol, A.ir_max,
-                                        x, failed);
+                        iters = kin3_step_mixed(k3f_s[t], vf_s[nd], d2f_int(A.dt), A.newton_tol,
+                                                A.ir_max, x, failed);
                 } else if (PREC == NMODL_FP64) {
-                    cacum_newton_d(md_s[t].cd, ica_s[nd], A.dt, A.newton_tol, A.newton_max_iter,
-                                   x[0], x[1], conv);
+                    iters = cacum_newton_d(md_s[t].cd, ica_s[nd], A.dt, A.newton_tol,
+                                           A.newton_max_iter, x[0], x[1], conv);
                 } else {
-                    cacum_newton_mixed(md_s[t].cd, cdf_s[t], ica_s[nd], A.dt, A.newton_tol,
-                                       A.newton_max_iter, A.ir_max, x[0], x[1], conv);
+                    iters = cacum_newton_mixed(md_s[t].cd, cdf_s[t], ica_s[nd], A.dt, A.newton_tol,
+                                               A.newton_max_iter, A.ir_max, x[0], x[1], conv);
                 }
                 if (failed || !conv) latch_error(A.err, NMODL_ERR_NOCONV);
+                count_solve(t, iters, failed || !conv);
                 for (int a = 0; a < ns; ++a) {
                     const int o = st_off[t] + a * cnt + j;
                     if (PREC == NMODL_FP64) {
@@ -1083,6 +1113,14 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock)
     }
     __syncthreads();  // shared memory is reused by the next tile
     }
+    // every thread has left the tile loop after the same barrier: the
+    // block's counts are complete
+    if constexpr (EXT)
+        if (tid < T && A.cnt[tid] && kit_s[tid]) {
+            atomicAdd(&A.cnt[tid]->iters, kit_s[tid]);
+            if (knc_s[tid]) atomicAdd(&A.cnt[tid]->nonconv, knc_s[tid]);
+            atomicMax(&A.cnt[tid]->max_iter_seen, kmx_s[tid]);
+        }
 }
 
 // ------------------------------------------------------------ launchers

@@ -55,6 +55,9 @@ struct FusedArgs {
     int32_t newton_max_iter;
     double newton_tol;
     int32_t ir_max;  // refinements of the mixed small systems
+    // Newton / refinement counters of the KIN9, KIN3 and CACUM mechanisms
+    // (null: not counted, e.g. autotuning trials)
+    struct KinCounters* cnt[kMaxMechsFused];
 };
 
 void launch_init_gates(const MechD* md, int n_gates, int64_t n, const int32_t* ni,

@@ -359,6 +359,13 @@ __device__ __forceinline__ double ddiv_fast(double x, double y) {
     return fma(fma(-y, q0, x), y0, q0);
 }
 
+// -x by flipping the sign bit on the integer pipe: a negated argument that
+// goes on to the integer steps of exp_tang / one_pm_exp has to exist in a
+// register, and an FP64 negation there would take an FP64 pipe slot.
+__device__ __forceinline__ double neg_int(double x) {
+    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000u, __double2loint(x));
+}
+
 // LINOID's series u/(1 - e^-u) = 1 + u/2 + u^2/12 - u^4/720 for |u| < 0.01,
 // out of line like exp_tang_rare
 static __device__ __noinline__ double linoid_series(double u) {
@@ -385,13 +392,13 @@ __device__ __forceinline__ void rate_nd_u(int form, double A, double u, double& 
         den = 1.0;
     } else if (form == kSigmoid) {
         num = A;
-        den = one_pm_exp<1>(-u);
+        den = one_pm_exp<1>(neg_int(u));
     } else if ((__double2hiint(u) & 0x7fffffff) < 0x3f847ae1) {  // |u| < 0.01
         num = A * linoid_series(u);
         den = 1.0;
     } else {
         num = A * u;
-        den = one_pm_exp<-1>(-u);
+        den = one_pm_exp<-1>(neg_int(u));
     }
 }
 
@@ -454,7 +461,7 @@ __device__ __forceinline__ double gate_step_forms_d(const GateD& G, double phidt
         minf = ddiv_fast(P, N);
         s = ddiv_fast(N, da * db);
     }
-    return fma(m - minf, exp_tang(FOLD ? -s : -phidt * s), minf);
+    return fma(m - minf, exp_tang(FOLD ? neg_int(s) : -phidt * s), minf);
 }
 
 // One form pair as a separate (not inlined) function: the call boundary

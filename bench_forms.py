@@ -570,6 +570,31 @@ def surrogate_kernel_case(dev=0, n=4_000_000, steps=3, tol=1e-4):
     ctx.close()
 
 
+def training_case(dev=0, n_pairs=1 << 20, epochs=2, batch=8192):
+    """Profiling case of the fused tensor-core training kernel: n_pairs
+    FP64 Newton pairs of the 9-state scheme, `epochs` passes in minibatches
+    of `batch` rows (one k_train_tiles + one k_grad_adam launch per
+    optimiser step, replayed from a CUDA graph).  Prints optimiser steps/s
+    and the BF16 MMA rate."""
+    from paper_1905_02241_b300.surrogate import Surrogate, make_training_pairs
+    p = W.kin9_params(W.Stream(4, 401))
+    ctx = Context(dev)
+    sur = Surrogate(ctx, max_batch=batch)
+    Ws, bs = W.mlp_init(7)
+    sur.set_weights(Surrogate.pack(Ws, bs))
+    X, T = make_training_pairs(ctx, sur, p, n_pairs, seed=6)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sur.fit(X, T, epochs=epochs, batch=batch, lr=2e-3)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    steps = epochs * (n_pairs // batch)
+    print({"optimiser_steps_per_s": steps / el,
+           "bf16_tflops": steps * batch * C.TRAIN_FLOPS_PER_ROW / el / 1e12})
+    sur.close()
+    ctx.close()
+
+
 def kernel_cases(dev=0):
     """Profiling case of the small-system, ion and cable kernels (seeded,
     synthetic): two calcium-buffer and two 3-state updates on 4M instances,

@@ -452,10 +452,11 @@ def kinetic(dev, peaks, n=1_000_000, nsteps=200, steps=1):
 
 def surrogate(dev, peaks, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=60):
     """The kinetic surrogate: FP64 Newton pairs, training (tensor-core
-    kernels), then 200 gated steps on n clamped instances against the FP64
-    and FP32-LU Newton solves; the inference kernel alone (every prediction
-    kept); rooflines of inference (tensor and special-function units) and of
-    training (tensor)."""
+    kernels), then 200 gated steps on n clamped instances (instances above
+    the 1e-4 residual fall back to the FP32-LU Newton with FP64 refinement)
+    against the FP64 and FP32-LU Newton solves alone; the inference kernel
+    alone (every prediction kept); rooflines of inference (tensor and
+    special-function units) and of training (tensor)."""
     from paper_1905_02241_b300.surrogate import Surrogate, attach, make_training_pairs
     p = W.kin9_params(W.Stream(4, 401))
     out = {"instances": n, "steps_per_run": nsteps, "training_pairs": n_pairs,
@@ -510,14 +511,9 @@ def surrogate(dev, peaks, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=60
     out["final_max_l1_vs_newton"] = float(err.max())
     out["final_mean_l1_vs_newton"] = float(err.mean())
     out["surrogate_over_newton_fp64"] = out["surrogate"] / out["newton_fp64"]
-    # the same comparison with the FP32-LU + FP64-refinement Newton, which
-    # is also what the surrogate falls back to in this precision
+    # (the fallback at this tolerance is the FP32-LU Newton with FP64
+    # refinement; the comparison below is with that Newton alone)
     ctx.set_options(precision=NMODL_MIXED)
-    m.set_states(x0)
-    fb0 = m.stats()["fallback"]
-    ms = _time(lambda: ctx.step([m], DT, CM, v, rhs, d, nsteps), ctx, 1)
-    out["surrogate_mixed_fallback"] = n * nsteps / (ms * 1e-3)
-    out["fallback_rate_mixed"] = (m.stats()["fallback"] - fb0) / (n * nsteps)
     # the inference kernel alone: every prediction kept (no fallback work)
     attach(m, sur, 1e30)
     m.set_states(x0)
@@ -530,9 +526,9 @@ def surrogate(dev, peaks, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=60
     m.set_states(x0)
     ms = _time(lambda: ctx.step([m], DT, CM, v, rhs, d, nsteps), ctx, 1)
     out["newton_mixed"] = n * nsteps / (ms * 1e-3)
-    out["surrogate_over_newton_mixed"] = out["surrogate_mixed_fallback"] / out["newton_mixed"]
+    out["surrogate_over_newton_mixed"] = out["surrogate"] / out["newton_mixed"]
     for key, rate in (("kernel_alone", out["surrogate_kernel_alone"]),
-                      ("end_to_end", out["surrogate_mixed_fallback"])):
+                      ("end_to_end", out["surrogate"])):
         out["roofline_" + key] = _roof(
             C.MLP_FLOPS, rate, peaks["bf16_sustained"], "bf16_sustained", unit="TFLOP/s",
             what=("BF16 MMA flops of the MLP per instance-step (K and N padded to 16), "

@@ -403,7 +403,11 @@ NMODL_API int nmodl_kin9_solve(nmodl_mech *kin, int64_t n, const double *v,
                                int64_t stride);
 /* Let nmodl_state (and nmodl_step) of a NMODL_KIN9 mechanism use the
  * surrogate with residual tolerance tol (1-norm); s = NULL or tol <= 0
- * detaches.  The fallback count is reported by nmodl_stats. */
+ * detaches.  Instances above the tolerance fall back to the Newton solve:
+ * for tol >= 1e-5 (or a MIXED context) the FP32-LU Newton with FP64
+ * residual refinement (FP32 rates: within about 1e-7 of the FP64 step, far
+ * inside the tolerance), below that the FP64 Newton.  The fallback count is
+ * reported by nmodl_stats. */
 NMODL_API int nmodl_mech_attach_surrogate(nmodl_mech *m, nmodl_surrogate *s,
                                           double tol);
 

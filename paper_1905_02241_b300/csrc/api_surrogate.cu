@@ -348,8 +348,14 @@ cudaError_t enqueue_surrogate_state(nmodl_mech* m, double dt, const double* v) {
     a.err = c->d_err;
     e = launch_surrogate_step(a, c->stream);
     if (e != cudaSuccess) return e;
+    // The fallback solve: the FP32-LU Newton with FP64 residual refinement
+    // (its result differs from the FP64 step by about 1e-7, from the FP32
+    // rates) wherever the gate's tolerance is 1e-5 or more, so that the
+    // fallback's own error stays far inside it; the FP64 Newton below that.
     const nmodl_options& o = c->opt;
-    launch_kin9_state(o.precision, m->d_kd, m->kd, m->n, m->d_ni, v, m->d_states, m->stride, dt,
+    const int fb_prec = (o.precision == NMODL_MIXED || m->sur_tol >= 1e-5) ? NMODL_MIXED
+                                                                            : NMODL_FP64;
+    launch_kin9_state(fb_prec, m->d_kd, m->kd, m->n, m->d_ni, v, m->d_states, m->stride, dt,
                       nullptr, o.newton_tol, o.newton_max_iter, o.ir_max, m->d_fb_list, m->n,
                       m->d_fb_count, m->d_cnt, c->d_err, c->stream);
     return cudaGetLastError();

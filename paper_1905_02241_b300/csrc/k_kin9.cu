@@ -108,8 +108,10 @@ __global__ void __launch_bounds__(128)
     const int64_t n_work = LIST ? (int64_t)*n_list_dev : n;
     unsigned long long it_sum = 0, nc_sum = 0;
     int it_max = 0;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t < n_work) {
+    // grid-stride: a fallback list of unknown length runs on a grid sized
+    // for the device, not for the whole mechanism
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_work;
+         t += (int64_t)gridDim.x * blockDim.x) {
         int iters = 0;
         bool nonconv = false;
         const int64_t i = LIST ? (int64_t)list[t] : t;
@@ -184,7 +186,15 @@ void launch_kin9_state(int prec, const Kin9D* kd, const Kin9D& kh, int64_t n, co
     const int block = 128;
     const int64_t work = list ? n_list_max : n;
     if (work == 0) return;
-    const int grid = (int)((work + block - 1) / block);
+    int grid = (int)((work + block - 1) / block);
+    if (list) {
+        // the list's length is known on the device only: a resident grid
+        // (the kernel's ~200 registers allow a few 128-thread blocks per SM)
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = (int)std::min<int64_t>(grid, (int64_t)sms * 4);
+    }
     Kin9Launch KL;
     for (int e = 0; e < kKinEdges; ++e) {
         const double cf = dt_arr ? 0.0 : std::log(dt * kh.af[e]);

@@ -72,9 +72,12 @@ def _roof(count, rate, peak, pipe, unit="Tops/s", what=""):
 def hh(dev, peaks, n=4096, nsteps=1000, reps=3):
     """Hodgkin-Huxley, one instance on each of n isolated compartments,
     v0 uniform in [-70, -60] mV, dt 0.025 ms, nsteps steps of nmodl_step
-    (fused, CUDA graphs per 40-step window), FP64.  The problem fills only
-    as many SMs as the plan has tiles, so the roofline is given against the
-    whole GPU and against the SMs the tiles can occupy."""
+    (the single-HH gate-warp kernel, CUDA graphs per 40-step window), FP64.
+    The problem fills only part of the GPU (one block of three warps, one
+    per gate, on each of at most 148 SMs: three of the four sub-partitions
+    of an SM, each with its own FP64 unit), so the roofline is given
+    against the whole GPU and against the sub-partitions the blocks
+    occupy."""
     wl = W.hh_single(n, seed=1)
     ctx = Context(dev)
     mechs = _mechs(ctx, wl)
@@ -92,9 +95,15 @@ def hh(dev, peaks, n=4096, nsteps=1000, reps=3):
     out = {"instances": n, "steps_per_run": nsteps, "fp64": rate, "plan": plan,
            "roofline": _roof(count, rate, peaks["fp64"], "fp64", what=(
                "FP64 pipe instructions per instance-step (bench_costs), whole-GPU peak"))}
-    busy = min(plan["tiles"], sms) / sms
-    out["roofline"]["frac_of_occupied_sms"] = out["roofline"]["frac"] / busy
-    out["roofline"]["occupied_sms"] = min(plan["tiles"], sms)
+    if plan["form"] == "hh_gate_warps":  # blocks of 3 warps on 3 of 4 sub-partitions
+        busy = min(plan["tiles"], sms) * 3 / (4 * sms)
+        out["roofline"]["occupied_sub_partitions"] = min(plan["tiles"], sms) * 3
+        out["roofline"]["frac_of_occupied_sub_partitions"] = out["roofline"]["frac"] / busy
+        out["ns_per_step"] = 1e9 * n / rate
+    else:
+        busy = min(plan["tiles"], sms) / sms
+        out["roofline"]["frac_of_occupied_sms"] = out["roofline"]["frac"] / busy
+        out["roofline"]["occupied_sms"] = min(plan["tiles"], sms)
     for m in mechs:
         m.close()
     ctx.close()
@@ -563,6 +572,25 @@ def surrogate_kernel_case(dev=0, n=4_000_000, steps=3, tol=1e-4):
     attach(m, None)
     m.close()
     sur.close()
+    ctx.close()
+
+
+def hh_case(dev=0, n=4096, nsteps=200):
+    """Profiling case of the single-HH gate-warp kernel: the HH workload
+    (n isolated compartments, one instance each, FP64), nsteps steps in
+    windows of 40 (one launch each).  Prints instance-steps/s."""
+    wl = W.hh_single(n, seed=1)
+    ctx = Context(dev)
+    mechs = _mechs(ctx, wl)
+    v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
+    rhs, d = torch.zeros_like(v), torch.zeros_like(v)
+    for m in mechs:
+        m.init(v)
+    ctx.step(mechs, DT, CM, v, rhs, d, nsteps)
+    ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
+    print({"form": ctx.plan(mechs)["form"], "instance_steps_per_s": n * nsteps / (ms * 1e-3)})
+    for m in mechs:
+        m.close()
     ctx.close()
 
 

@@ -258,17 +258,24 @@ NMODL_API int nmodl_cur(nmodl_mech *m, const double *v, double *rhs, double *d);
  * registered, are summed per node in the tile and the buffer reads the
  * tile's ica; a 9-state instance's Newton solve runs in one thread);
  * otherwise (e.g. a NMODL_KIN9 with a surrogate) each step is a sequence of
- * per-mechanism launches.  nsteps = 0 is a no-op. */
+ * per-mechanism launches.  One NMODL_HH mechanism with one instance on each
+ * node (node_index 0, 1, ..., n_nodes - 1) on at most 32 nodes per SM, in
+ * FP64 without ion arrays or options.cnexp_pade (and options.no_fuse 0),
+ * runs in a kernel of its own instead: one launch per window, three warps
+ * per block, one per gate, a network too small to fill the GPU being bound
+ * by the length of each step's dependent chain.  nsteps = 0 is a no-op. */
 NMODL_API int nmodl_step(nmodl_ctx *ctx, nmodl_mech *const *mechs, int n_mechs,
                double dt, double cm, double *v, double *rhs, double *d,
                int nsteps);
 
 /* Shape nmodl_step chose for this mechanism list (after a first call):
- * out[0] fused (1) or per-mechanism launches (0), out[1] tiles, out[2]
- * block size, out[3] dynamic shared memory per block (bytes), out[4]
- * persistent tile queue (1) or one block per tile (0), out[5] tile
- * shared-memory budget.  The autotuner (options.autotune) picks these by
- * timing candidates on a scratch copy of the first <= 16M instances. */
+ * out[0] fused tiles (1), per-mechanism launches (0) or the single-HH
+ * gate-warp kernel (2), out[1] tiles (form 2: blocks), out[2] block size,
+ * out[3] dynamic shared memory per block (bytes), out[4] persistent tile
+ * queue (1) or one block per tile (0), out[5] tile shared-memory budget
+ * (form 2: nodes per block).  The autotuner (options.autotune) picks the
+ * tile shape by timing candidates on a scratch copy of the first <= 16M
+ * instances. */
 NMODL_API int nmodl_plan_describe(nmodl_ctx *ctx, nmodl_mech *const *mechs,
                                   int n_mechs, int64_t *out);
 

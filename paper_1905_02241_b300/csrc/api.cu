@@ -693,6 +693,32 @@ struct Candidate {
     std::shared_ptr<std::vector<uint16_t>> sched;  // cable level schedules
 };
 
+// The gate-warp form of k_hh.cu: one HH mechanism with one instance on
+// each node (node_index = 0, 1, ..., n - 1), FP64, isolated compartments,
+// no ion arrays, the exponential cnexp factor, and at most 32 nodes per SM
+// (a network too small for the tile kernel to fill the GPU).  Returns the
+// nodes per block, 0 where the form does not apply.
+static int hh_warps_shape(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs,
+                          nmodl_cable* cb) {
+    if (n_mechs != 1 || cb || c->opt.no_fuse || c->opt.precision != NMODL_FP64 ||
+        c->opt.cnexp_pade || c->has_ions())
+        return 0;
+    const nmodl_mech* m = mechs[0];
+    if (m->type != NMODL_HH || m->n != m->n_nodes || m->n == 0) return 0;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        sms <= 0 || m->n > 32 * (int64_t)sms)
+        return 0;
+    std::vector<int32_t> ni((size_t)m->n);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+        cudaMemcpy(ni.data(), m->d_ni, ni.size() * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return 0;
+    for (int64_t i = 0; i < m->n; ++i)
+        if (ni[(size_t)i] != i) return 0;
+    return hh_warps_per_block(m->n, sms);
+}
+
 static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan* p,
                       const double* v_user, nmodl_cable* cb) {
     p->mechs.assign(mechs, mechs + n_mechs);
@@ -730,6 +756,12 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     p->variant = p->precision + (ext ? 2 : 0) + (kin ? 2 : 0);
     p->fused = false;
     const bool dbg = std::getenv("NMODL_PLAN_DEBUG") != nullptr;
+    if ((p->hh_per_block = hh_warps_shape(c, mechs, n_mechs, cb)) > 0) {
+        p->fused = true;
+        if (dbg) std::fprintf(stderr, "[nmodl plan] HH gate warps, %d nodes per block\n",
+                              p->hh_per_block);
+        return NMODL_OK;
+    }
     if (!cnexp || p->n_nodes == 0) {
         if (dbg) std::fprintf(stderr, "[nmodl plan] not fusable\n");
         return NMODL_OK;
@@ -1110,6 +1142,29 @@ cudaError_t nmodl_run_window(nmodl_ctx* c, Plan* p, nmodl_mech* const* mechs, in
                               double dt, double cm, double* v, double* rhs, double* d,
                               int w) {
     auto direct = [&]() -> cudaError_t {
+        if (p->hh_per_block > 0) {
+            nmodl_mech* m = mechs[0];
+            HhArgs a{};
+            for (int q = 0; q < 3; ++q) {
+                a.gate[q] = m->md.gate[q];
+                fold_gate(a.gate[q], m->md.phi * dt);
+                a.g[q] = m->md.hh_g[q];
+                a.e[q] = m->md.hh_e[q];
+            }
+            a.n = p->n_nodes;
+            a.per_block = p->hh_per_block;
+            a.nsteps = w;
+            a.clamp_v = c->opt.clamp_v;
+            a.dt = dt;
+            a.cm = cm;
+            a.v = v;
+            a.states = m->d_states;
+            a.stride = m->stride;
+            a.rhs = rhs;
+            a.d = d;
+            a.err = c->d_err;
+            return launch_hh_gate_warps(a, c->stream);
+        }
         if (p->fused) {
             FusedArgs a = fused_args(c, p, dt, cm, v, rhs, d, w);
             if (p->persistent) {
@@ -1180,6 +1235,15 @@ int nmodl_plan_describe(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, int
         auto& p = *it;
         if ((int)p->mechs.size() == n_mechs && p->precision == c->opt.precision &&
             std::equal(p->mechs.begin(), p->mechs.end(), mechs)) {
+            if (p->hh_per_block > 0) {
+                out[0] = 2;
+                out[1] = (p->n_nodes + p->hh_per_block - 1) / p->hh_per_block;
+                out[2] = 96;
+                out[3] = 0;
+                out[4] = 0;
+                out[5] = p->hh_per_block;
+                return NMODL_OK;
+            }
             out[0] = p->fused ? 1 : 0;
             out[1] = p->n_tiles;
             out[2] = p->block;

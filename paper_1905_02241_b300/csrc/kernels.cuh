@@ -138,6 +138,28 @@ void launch_cacum_state(int prec, const CacumD* cd, const CacumD& ch, int64_t n,
 Kin3F kin3_f32(const Kin3D& K);
 CacumF cacum_f32(const CacumD& C);
 
+// Arguments of the single-HH gate-warp step (k_hh.cu): n nodes, instance i
+// on node i, per_block nodes per block of three warps.
+struct HhArgs {
+    GateD gate[3];         // m, h, n folded for this launch's dt (fold_gate)
+    double g[3], e[3];     // gnabar, gkbar, gl; ena, ek, el
+    int64_t n;
+    int32_t per_block;     // 1..32
+    int32_t nsteps;
+    int32_t clamp_v;
+    double dt, cm;
+    double* v;
+    double* states;        // m, h, n rows of the given stride
+    int64_t stride;
+    double* rhs;
+    double* d;
+    int32_t* err;
+};
+// nodes per block: the network spread over the SMs, at most 32
+int hh_warps_per_block(int64_t n, int sms);
+cudaError_t launch_hh_gate_warps(const HhArgs& a, cudaStream_t s);
+
+
 // common
 void launch_chunk_starts(const int32_t* ni, int64_t n, int64_t n_chunks,
                          int32_t* chunk, cudaStream_t s);

@@ -410,7 +410,7 @@ __device__ __forceinline__ void rate_nd_u(int form, double A, double u, double& 
 // An EXP rate's A e^u becomes sign(A) e^(u + ln|A|): ln|A| joins c (one
 // more rounding of the same kind) and A keeps its sign only (A = 0 gives
 // e^-inf = 0).  Takes a log per rate: fold once per block, not per item.
-__device__ __forceinline__ void fold_gate(GateD& G, double phidt) {
+__host__ __device__ __forceinline__ void fold_gate(GateD& G, double phidt) {
     G.avh = -G.avh * G.ark;
     G.bvh = -G.bvh * G.brk;
     G.aA *= phidt;

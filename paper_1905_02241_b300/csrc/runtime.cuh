@@ -49,6 +49,8 @@ struct Plan {
     int variant = 0;                // fused kernel: precision + 2 * (small systems / ions)
     int64_t n_nodes = 0;
     bool fused = false;
+    // single-HH gate-warp form (k_hh.cu): nodes per block, 0 = not used
+    int hh_per_block = 0;
     // fused form
     int n_tiles = 0, block = 256, tile_stride = 0;
     size_t smem = 0;

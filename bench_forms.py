@@ -227,8 +227,11 @@ def cable(dev, peaks, n_cells=10000, nsteps=200):
 def kin9_network(dev, peaks, n_nodes=1_000_000, frac=0.25, nsteps=200):
     """The cortical mix on n_nodes compartments with the 9-state kinetic
     scheme on a seeded 25 % of them (one instance each, v not clamped): all
-    mechanism types in the fused tile kernel (its KIN variant) against the
-    per-mechanism launch sequence (no_fuse), FP64 and MIXED."""
+    mechanism types in the fused tile kernel (its KIN variant; in FP64 with
+    the largest tiles, the shape the autotuner picks among the fused ones)
+    against the per-mechanism launch sequence (no_fuse), FP64 and MIXED; and
+    the FP64 form the autotuner picks when it may also choose the
+    per-mechanism launches."""
     wl = W.cortical_mix(n_nodes, seed=2)
     ni = np.nonzero(W.Stream(2, 901).uniform(n_nodes) < frac)[0].astype(np.int32)
     wl["mechs"].append(dict(type=W.TYPE_KIN9, params=W.kin9_params(W.Stream(4, 401)),
@@ -236,10 +239,12 @@ def kin9_network(dev, peaks, n_nodes=1_000_000, frac=0.25, nsteps=200):
     ninst = _ninst(wl)
     out = {"nodes": n_nodes, "instances": ninst, "kin9_instances": int(ni.size),
            "steps_per_run": nsteps}
-    for name, prec, nf in (("fused_fp64", NMODL_FP64, 0), ("per_mechanism_fp64", NMODL_FP64, 1),
-                           ("fused_mixed", NMODL_MIXED, 0),
-                           ("per_mechanism_mixed", NMODL_MIXED, 1)):
-        ctx = Context(dev, precision=prec, no_fuse=nf)
+    for name, prec, opt in (("fused_fp64", NMODL_FP64, dict(tile_smem=1 << 30)),
+                            ("per_mechanism_fp64", NMODL_FP64, dict(no_fuse=1)),
+                            ("autotuned_fp64", NMODL_FP64, {}),
+                            ("fused_mixed", NMODL_MIXED, {}),
+                            ("per_mechanism_mixed", NMODL_MIXED, dict(no_fuse=1))):
+        ctx = Context(dev, precision=prec, **opt)
         mechs = _mechs(ctx, wl)
         v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
         rhs = torch.zeros_like(v)
@@ -249,8 +254,8 @@ def kin9_network(dev, peaks, n_nodes=1_000_000, frac=0.25, nsteps=200):
         ctx.step(mechs, DT, CM, v, rhs, d, 40)
         ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, nsteps), ctx, 1)
         out[name] = ninst * nsteps / (ms * 1e-3)
-        if name == "fused_fp64":
-            out["plan_fused"] = ctx.plan(mechs)
+        if name in ("fused_fp64", "autotuned_fp64", "fused_mixed"):
+            out["plan_" + name] = ctx.plan(mechs)
         for m in mechs:
             m.close()
         ctx.close()

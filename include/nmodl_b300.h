@@ -139,7 +139,8 @@ typedef struct nmodl_options {
     int32_t ir_max;          /* FP64 refinements of an FP32 solve (4)        */
     int32_t window;          /* steps fused into one launch (default 40)     */
     int32_t use_graph;       /* replay each window from a CUDA graph (1)     */
-    int32_t autotune;        /* time candidate tile/block shapes (1)         */
+    int32_t autotune;        /* time candidate tile/block shapes (1); see
+                                nmodl_step for the FP64 9-state lists       */
     int32_t clamp_v;         /* nmodl_step leaves v unchanged (0)            */
     int32_t tile_smem;       /* fused tile shared-memory budget, bytes (0 =
                                 chosen by the autotuner / default)          */
@@ -258,7 +259,11 @@ NMODL_API int nmodl_cur(nmodl_mech *m, const double *v, double *rhs, double *d);
  * registered, are summed per node in the tile and the buffer reads the
  * tile's ica; a 9-state instance's Newton solve runs in one thread);
  * otherwise (e.g. a NMODL_KIN9 with a surrogate) each step is a sequence of
- * per-mechanism launches.  One NMODL_HH mechanism with one instance on each
+ * per-mechanism launches.  For an FP64 list with NMODL_KIN9 on isolated
+ * compartments, the autotuner (options.autotune, with options.tile_smem and
+ * options.block 0) also times the per-mechanism sequence on scratch copies
+ * and keeps it where it is faster (the fused variant holds one block per
+ * SM there).  One NMODL_HH mechanism with one instance on each
  * node (node_index 0, 1, ..., n_nodes - 1) on at most 32 nodes per SM, in
  * FP64 without ion arrays or options.cnexp_pade (and options.no_fuse 0),
  * runs in a kernel of its own instead: one launch per window, three warps

@@ -683,6 +683,10 @@ static cudaError_t upload_descriptors(nmodl_ctx* c, Plan* p, nmodl_mech* const* 
     return e;
 }
 
+static cudaError_t enqueue_generic_steps(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs,
+                                         double dt, double cm, double* v, double* rhs,
+                                         double* d, int nsteps, int64_t n_nodes);
+
 struct Candidate {
     size_t budget;
     int block;
@@ -877,6 +881,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     p->d_counter = d_counter;
 
     size_t best = 0;
+    bool generic_wins = false;
     if (cands.size() > 1) {
         // time each candidate on a scratch copy: a prefix of the network of
         // up to 16M instances (several waves of even the largest tiles),
@@ -1000,6 +1005,8 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
             cands[ci].ms = ms;
             if (cands[ci].ms < cands[best].ms || ci == 0) best = ci;
         }
+        double best_ms = ok ? cands[best].ms : 0.0;  // of the chosen shape, per instance
+        int best_steps = trial_steps;                // ... over this many steps
         if (ok && full_steps > trial_steps && cands.size() > 1) {
             std::vector<size_t> order(cands.size());
             for (size_t k = 0; k < order.size(); ++k) order[k] = k;
@@ -1019,9 +1026,54 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
                     if (ms < best_full) {
                         best_full = ms;
                         best = order[r];
+                        best_ms = ms;
+                        best_steps = full_steps;
                     }
                 }
             }
+        }
+        // FP64 lists with the 9-state scheme: the fused variant runs one
+        // block per SM (the FP64 solve holds ~245 registers per thread), so
+        // its cnexp items run at 8 warps per SM and the per-mechanism
+        // launches can be faster.  Time them too, over the whole network on
+        // the same scratch copies (each mechanism's state array swapped for
+        // its copy during the trial, its Newton counters restored after),
+        // and keep the faster form.  Not with a fixed tile budget or block.
+        if (ok && kin && p->precision == NMODL_FP64 && !cb && c->opt.tile_smem == 0 &&
+            c->opt.block == 0) {
+            std::vector<KinCounters> saved(T);
+            ok = cudaStreamSynchronize(c->stream) == cudaSuccess;
+            for (int t = 0; t < T && ok; ++t)
+                if (mechs[t]->d_cnt)
+                    ok = cudaMemcpy(&saved[t], mechs[t]->d_cnt, sizeof(KinCounters),
+                                    cudaMemcpyDeviceToHost) == cudaSuccess;
+            int64_t total = 0;
+            for (int t = 0; t < T; ++t) total += mechs[t]->n;
+            double gbest = 1e30;
+            if (ok) {
+                for (int t = 0; t < T; ++t) std::swap(mechs[t]->d_states, sst[t]);
+                for (int rep = 0; rep < 2 && ok; ++rep) {
+                    cudaEventRecord(e0, c->stream);
+                    ok = enqueue_generic_steps(c, mechs, n_mechs, 0.025, 1.0, sv, srhs, sd,
+                                               best_steps, p->n_nodes) == cudaSuccess;
+                    cudaEventRecord(e1, c->stream);
+                    ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    gbest = std::min(gbest, (double)ms);
+                }
+                cudaStreamSynchronize(c->stream);
+                for (int t = 0; t < T; ++t) std::swap(mechs[t]->d_states, sst[t]);
+                for (int t = 0; t < T; ++t)
+                    if (mechs[t]->d_cnt)
+                        cudaMemcpy(mechs[t]->d_cnt, &saved[t], sizeof(KinCounters),
+                                   cudaMemcpyHostToDevice);
+            }
+            const double gms = gbest / std::max<int64_t>(1, total);
+            if (dbg)
+                std::fprintf(stderr, "[nmodl plan] per-mechanism launches ns/inst (per %d steps) %.4f vs fused %.4f\n",
+                             best_steps, gms * 1e6, best_ms * 1e6);
+            generic_wins = ok && gms < best_ms;
         }
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
@@ -1040,6 +1092,10 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
                          cands[ci].budget, cands[ci].block, (int)cands[ci].persistent,
                          cands[ci].recs.size() / p->tile_stride, cands[ci].smem, cands[ci].ms * 1e6,
                          ci == best ? "  <- chosen" : "");
+    if (generic_wins) {
+        if (dbg) std::fprintf(stderr, "[nmodl plan] per-mechanism launches chosen\n");
+        return NMODL_OK;  // p->fused stays false
+    }
     Candidate& ch = cands[best];
     p->budget = ch.budget;
     p->block = ch.block;

@@ -51,7 +51,7 @@ __global__ void k_cable_solve(int64_t n_cells, const int64_t* __restrict__ cell_
     for (int64_t i = a + 1; i < b; ++i) r2[i] = (r2[i] + ga[i] * r2[parent[i]]) / d2[i];
     for (int64_t i = a; i < b; ++i) {
         const double vn = v[i] + r2[i];
-        if (!isfinite(vn)) latch_error(err, NMODL_ERR_NONFINITE);
+        if (!finite_int(vn)) latch_error(err, NMODL_ERR_NONFINITE);
         v[i] = vn;
     }
 }

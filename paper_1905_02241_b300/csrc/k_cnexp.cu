@@ -37,7 +37,7 @@ __global__ void k_init_gates(const MechD* __restrict__ md, int64_t n,
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double m = gate_inf_d(G, v[ni[i]]);
-        if (!isfinite(m)) latch_error(err, NMODL_ERR_NONFINITE);
+        if (!finite_int(m)) latch_error(err, NMODL_ERR_NONFINITE);
         states[g * stride + i] = m;
     }
 }
@@ -66,7 +66,7 @@ __global__ void k_state_gates(const MechD* __restrict__ md, int64_t n,
              i += (int64_t)gridDim.x * blockDim.x) {
             const double m = pade ? gate_step_pade_d<true>(Gf, 1.0, v[ni[i]], row[i])
                                   : gate_step_fast_d<true>(Gf, 1.0, v[ni[i]], row[i]);
-            if (!isfinite(m)) latch_error(err, NMODL_ERR_NONFINITE);
+            if (!finite_int(m)) latch_error(err, NMODL_ERR_NONFINITE);
             row[i] = m;
         }
     } else {
@@ -82,7 +82,7 @@ __global__ void k_state_gates(const MechD* __restrict__ md, int64_t n,
             // (conversions on the integer pipe)
             const float delta = f * (minf - d2f_int(m));
             const double mn = m + f2d_int(delta);
-            if (!isfinite(mn)) latch_error(err, NMODL_ERR_NONFINITE);
+            if (!finite_int(mn)) latch_error(err, NMODL_ERR_NONFINITE);
             row[i] = mn;
         }
     }
@@ -188,7 +188,9 @@ __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
         const int key = valid ? ni[j] : -1 - lane;  // invalid lanes never match
         double vi = 0.0, vg = 0.0, va = 0.0, vb = 0.0;
         if (valid) cur_any_d<KIND, ION>(desc, st, stride, j, v[key], vi, vg, va, vb);
-        if (lane == 0 && key == ckey) {
+        // the carry into lane 0 behind a warp-uniform branch: a predicated
+        // FP64 add would still take an FP64 issue slot of the whole warp
+        if (__shfl_sync(0xffffffffu, key, 0) == ckey && lane == 0) {
             vi += ci;
             vg += cg;
             if (ION) {
@@ -197,10 +199,12 @@ __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
             }
         }
         int span;  // the scan's last offset: 2 * span covers every segment
-        {
+        {          // (0: every node of the piece has one instance, no scan)
+            const int k1 = __shfl_up_sync(0xffffffffu, key, 1);
             const int k2 = __shfl_up_sync(0xffffffffu, key, 2);
             const int k4 = __shfl_up_sync(0xffffffffu, key, 4);
-            span = !__any_sync(0xffffffffu, lane >= 2 && k2 == key)   ? 1
+            span = !__any_sync(0xffffffffu, lane >= 1 && k1 == key)   ? 0
+                   : !__any_sync(0xffffffffu, lane >= 2 && k2 == key) ? 1
                    : !__any_sync(0xffffffffu, lane >= 4 && k4 == key) ? 2
                                                                       : 16;
         }
@@ -228,7 +232,7 @@ __global__ void k_cur_seg(const void* __restrict__ desc, int64_t n_chunks,
         if (tail && !cont) {
             const double r = rhs[key] - vi;
             const double dd = d[key] + vg;
-            if (!isfinite(r) || !isfinite(dd)) latch_error(err, NMODL_ERR_NONFINITE);
+            if (!finite_int(r) || !finite_int(dd)) latch_error(err, NMODL_ERR_NONFINITE);
             rhs[key] = r;
             d[key] = dd;
             if (ION) {
@@ -331,8 +335,15 @@ __device__ void block_inclusive_scan_u16(uint16_t* a, int n, int* wsum) {
 // elimination (1984; no fill because parents precede children) scheduled by
 // levels.  v += the solution.  On the last step of the window rhs and d
 // report the assembled system.
+// The KIN variant in MIXED is compiled for two 256-thread blocks per SM
+// (128 registers; the FP32 solve spills a few hundred bytes): its cnexp
+// items then run at 16 warps per SM instead of 8 (measured 1.13x on the
+// cortical mix with the 9-state scheme on a quarter of 1M nodes).  The FP64
+// variant keeps one block (~245 registers): its spilled FP64 solve lost
+// more (0.90x) than the occupancy gained.
 template <int PREC, bool EXT, bool KIN>
-__global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock)
+__global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
+                                  (KIN && PREC == NMODL_MIXED) ? 2 : 1)
     k_fused_tiles(FusedArgs A) {
     static_assert(!KIN || EXT, "the 9-state scheme comes with the extended variant");
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1095,7 +1106,7 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock)
     // ---- write the tile back
     for (int k = tid; k < NT; k += blockDim.x) {
         const double vn = v_s[k];
-        if (!isfinite(vn)) latch_error(A.err, NMODL_ERR_NONFINITE);
+        if (!finite_int(vn)) latch_error(A.err, NMODL_ERR_NONFINITE);
         A.v[n0 + k] = vn;
     }
     {
@@ -1107,7 +1118,7 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock)
             double m;
             if (PREC == NMODL_FP64) m = st_d[k];
             else m = f2d_int(st_f[k].x) + f2d_int(st_f[k].y);
-            if (!isfinite(m)) latch_error(A.err, NMODL_ERR_NONFINITE);
+            if (!finite_int(m)) latch_error(A.err, NMODL_ERR_NONFINITE);
             A.states[t][g * A.stride[t] + a_s[t] + j] = m;
         }
     }

@@ -61,7 +61,8 @@ __global__ void k_tile_bounds(const int32_t* __restrict__ ni, int64_t n,
     out[k] = (int32_t)lower_bound_i32(ni, 0, n, nodes[k]);
 }
 
-// d += 1e-3 cm/dt; v += rhs/d (unless clamped)
+// d += 1e-3 cm/dt; v += rhs/d (unless clamped; the quotient within one ulp
+// by the two-FP64-instruction division of the gate updates)
 __global__ void k_vupdate(int64_t n_nodes, double* v, const double* __restrict__ rhs,
                           double* d, double cmdt, int clamp, int32_t* err) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_nodes;
@@ -69,8 +70,8 @@ __global__ void k_vupdate(int64_t n_nodes, double* v, const double* __restrict__
         const double dd = d[k] + cmdt;
         d[k] = dd;
         if (!clamp) {
-            const double vn = v[k] + rhs[k] / dd;
-            if (!isfinite(vn)) latch_error(err, NMODL_ERR_NONFINITE);
+            const double vn = v[k] + ddiv_fast(rhs[k], dd);
+            if (!finite_int(vn)) latch_error(err, NMODL_ERR_NONFINITE);
             v[k] = vn;
         }
     }

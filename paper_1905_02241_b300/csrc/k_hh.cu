@@ -77,10 +77,10 @@ __global__ void __launch_bounds__(96) k_hh_gate_warps(HhArgs A) {
         asm volatile("bar.sync 1, 96;" ::: "memory");
     }
     if (act) {
-        if (!isfinite(s)) latch_error(A.err, NMODL_ERR_NONFINITE);
+        if (!finite_int(s)) latch_error(A.err, NMODL_ERR_NONFINITE);
         A.states[w * A.stride + i] = s;
         if (w == 0) {
-            if (!isfinite(vv)) latch_error(A.err, NMODL_ERR_NONFINITE);
+            if (!finite_int(vv)) latch_error(A.err, NMODL_ERR_NONFINITE);
             A.v[i] = vv;
         }
     }

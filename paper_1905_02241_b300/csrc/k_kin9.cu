@@ -74,7 +74,7 @@ __global__ void k_kin9_init(const Kin9D* __restrict__ kd, int64_t n,
     }
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        if (!isfinite(x[a])) latch_error(err, NMODL_ERR_NONFINITE);
+        if (!finite_int(x[a])) latch_error(err, NMODL_ERR_NONFINITE);
         st[a * stride + i] = x[a];
     }
 }
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(128)
         }
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            if (!isfinite(y[a])) latch_error(err, NMODL_ERR_NONFINITE);
+            if (!finite_int(y[a])) latch_error(err, NMODL_ERR_NONFINITE);
             st[a * stride + i] = y[a];
         }
         if (nonconv) latch_error(err, NMODL_ERR_NOCONV);

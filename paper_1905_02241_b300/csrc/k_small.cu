@@ -46,7 +46,7 @@ __global__ void k_kin3_init(const Kin3D* __restrict__ kd, int64_t n,
     const double p[3] = {w0 * r, w1 * r, w2 * r};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (!isfinite(p[a])) latch_error(err, NMODL_ERR_NONFINITE);
+        if (!finite_int(p[a])) latch_error(err, NMODL_ERR_NONFINITE);
         st[a * stride + i] = p[a];
     }
 }
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256)
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            if (!isfinite(y[a])) latch_error(err, NMODL_ERR_NONFINITE);
+            if (!finite_int(y[a])) latch_error(err, NMODL_ERR_NONFINITE);
             st[a * stride + i] = y[a];
         }
         it_sum = iters;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256)
                            ? cacum_newton_d(C, ica[ni[i]], dt, tol, max_iter, y0, y1, conv)
                            : cacum_newton_mixed(C, cf32, ica[ni[i]], dt, tol, max_iter, ir_max,
                                                 y0, y1, conv);
-        if (!isfinite(y0) || !isfinite(y1)) latch_error(err, NMODL_ERR_NONFINITE);
+        if (!finite_int(y0) || !finite_int(y1)) latch_error(err, NMODL_ERR_NONFINITE);
         if (!conv) latch_error(err, NMODL_ERR_NOCONV);
         st[i] = y0;
         st[stride + i] = y1;

@@ -359,6 +359,12 @@ __device__ __forceinline__ double ddiv_fast(double x, double y) {
     return fma(fma(-y, q0, x), y0, q0);
 }
 
+// x neither infinite nor NaN, from its exponent field on the integer pipe
+// (an FP64 comparison would take an FP64 pipe slot)
+__device__ __forceinline__ bool finite_int(double x) {
+    return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
 // -x by flipping the sign bit on the integer pipe: a negated argument that
 // goes on to the integer steps of exp_tang / one_pm_exp has to exist in a
 // register, and an FP64 negation there would take an FP64 pipe slot.

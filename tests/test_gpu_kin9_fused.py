@@ -80,7 +80,7 @@ def test_fused_one_step_and_trajectory_fp64(api, orc):
 
 def test_fused_matches_the_per_mechanism_sequence(api, orc):
     wl = _network(3000, seed=42, frac=0.6)
-    a = _run(api, orc, wl, 10, window=4)
+    a = _run(api, orc, wl, 10, window=4, tile_smem=24 * 1024)  # fused (fixed tiles)
     b = _run(api, orc, wl, 10, window=4, no_fuse=1)
     assert a["plan"]["fused"] and not b["plan"]["fused"]
     assert np.max(np.abs(a["v"] - b["v"]) / np.maximum(np.abs(b["v"]), 1.0)) <= 1e-12

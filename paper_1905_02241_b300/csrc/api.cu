@@ -501,7 +501,7 @@ int nmodl_cur(nmodl_mech* m, const double* v, double* rhs, double* d) {
 // its owner loop; otherwise flat node-major slots of 16 bytes, slots[t] per
 // instance).
 static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* slots, int64_t NT,
-                              const int64_t* cnt, bool cable, bool ions, bool tables) {
+                              const int64_t* cnt, bool cable, bool ions, bool tables, bool ext) {
     size_t b = 8 * (size_t)NT;
     size_t inst = 0, items = 0, nslot = 0;
     for (int t = 0; t < T; ++t) {
@@ -516,7 +516,9 @@ static size_t tile_smem_bytes(int prec, int T, const int* gates, const int* slot
     if (ions) b = (b + 15) / 16 * 16 + 8 * (size_t)NT;  // the step's ica per node
     // d, rhs, ga, gb, parent, and the level schedule (at most 6 NT + 5 uint16)
     if (cable) b = (b + 15) / 16 * 16 + 34 * (size_t)NT + 2 * (6 * (size_t)NT + 5);
-    if (!tables) b = (b + 15) / 16 * 16 + 16 * nslot;  // (e, g) slots of the step
+    // the node-major slots of the step: (e, g) doubles; MIXED without the
+    // small systems: three FP32 conductance factors and the current's id
+    if (!tables) b = (b + 15) / 16 * 16 + 16 * nslot;
     return (b + 15) / 16 * 16;
 }
 
@@ -547,7 +549,7 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
                 if (cnt[t] > 65535) return false;
             }
             if (!tables && nslot > 65535) return false;  // uint16 node-major slots
-            return tile_smem_bytes(prec, T, gates, slots, NT, cnt.data(), cable, ions, tables) <=
+            return tile_smem_bytes(prec, T, gates, slots, NT, cnt.data(), cable, ions, tables, ext) <=
                    budget;
         };
         if (!fits(k0, k1)) return false;
@@ -562,7 +564,7 @@ static bool make_tiles(int prec, const std::vector<std::vector<int32_t>>& off, i
         }
         max_smem = std::max(max_smem,
                             tile_smem_bytes(prec, T, gates, slots, n1 - n0, cnt.data(), cable,
-                                            ions, tables));
+                                            ions, tables, ext));
         k0 = k1;
     }
     return true;

@@ -346,6 +346,18 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
                                   (KIN && PREC == NMODL_MIXED) ? 2 : 1)
     k_fused_tiles(FusedArgs A) {
     static_assert(!KIN || EXT, "the 9-state scheme comes with the extended variant");
+    // MIXED without the small systems, on isolated compartments: each gate
+    // update writes its instance's conductance factor into the instance's
+    // node-major slot (gbar m^p for a type's first gate, h^q for the next
+    // ones; HH: gnabar m^3 and h into the sodium slot, gkbar n^4 into the
+    // potassium slot), the slot's fourth float holds the id of its current
+    // (its reversal potential in efac_s), and the owner pass multiplies the
+    // factors: no separate conductance pass, two barriers per step, not three
+    constexpr bool FAC_V = PREC == NMODL_MIXED && !EXT;
+    __shared__ double efac_s[FAC_V ? 3 * kMaxMechsFused : 1];   // e of current 3 t + q
+    __shared__ float fmul_s[FAC_V ? kMaxMechsFused * kMaxGates : 1];
+    __shared__ int fidx_s[FAC_V ? kMaxMechsFused * kMaxGates : 1];  // 4 slot + component
+    __shared__ int fpow_s[FAC_V ? kMaxMechsFused * kMaxGates : 1];
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ MechD md_s[kMaxMechsFused];
     __shared__ GateF gf_s[kMaxMechsFused][kMaxGates];
@@ -477,6 +489,20 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
         }
         pair_start[q] = so;
         n_pairs = q;
+        if (FAC_V) {  // the factor of each gate pair; the e of each current
+            for (int p = 0; p < q; ++p) {
+                const MechD& M = md_s[pair_t[p]];
+                const int g = pair_g[p];
+                const bool hh = M.kind == NMODL_HH;
+                fmul_s[p] = g == 0 ? (float)(hh ? M.hh_g[0] : M.gbar)
+                                   : (hh && g == 2) ? (float)M.hh_g[1] : 1.f;
+                fpow_s[p] = M.gate[g].power;
+                fidx_s[p] = hh ? (g == 2 ? 4 : g) : g;
+            }
+            for (int t = 0; t < T; ++t)
+                for (int c = 0; c < 3; ++c)
+                    efac_s[3 * t + c] = md_s[t].kind == NMODL_HH ? md_s[t].hh_e[c] : md_s[t].e;
+        }
         // Work order of the FP64 state phase: the gates grouped by their pair
         // of rate forms (each pair of forms is one straight-line body), each
         // group padded to whole warps so that no warp runs two bodies; the
@@ -563,6 +589,7 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
     // slot range of each node, the owner order, and (with ion arrays) the ion
     // of each slot.
     const bool flat = !A.cable;
+    const bool FAC = FAC_V && flat;
     uint16_t* seg_s = nid_s + total_inst;
     uint16_t* pos_s = nid_s + total_inst;
     uint16_t* eoff_s = pos_s + total_inst;
@@ -585,13 +612,27 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
     double* gb_s = ga_s + NT;
     uint16_t* par_s = reinterpret_cast<uint16_t*>(gb_s + NT);
     uint16_t* sched_s = par_s + NT;
-    // Flat: the (e, g) node-major slots of the step (the cable form has none)
+    // Flat: the (e, g) node-major slots of the step (the cable form has none).
+    // FAC (MIXED without the small systems): the factors and current id f_s
+    // instead, at the same place
     double2* xg_s = reinterpret_cast<double2*>(
         (reinterpret_cast<uintptr_t>(d2_s) + 15) & ~(uintptr_t)15);
+    float4* f_s = reinterpret_cast<float4*>(xg_s);
     if (A.cable) {
         const int32_t off = rec[2 + 2 * T], len = rec[3 + 2 * T];
         for (int k = tid; k < len; k += blockDim.x) sched_s[k] = A.sched[off + k];
     }
+    // FAC: the conductance factor of gate pair q, instance j, from the gate's
+    // FP32 state hi, into its component of the instance's slot
+    auto put_factor = [&](int q, int j, float hi) {
+        float f = fmul_s[q];
+        const int pw = fpow_s[q];
+        if (pw >= 1) f *= hi;
+        if (pw >= 2) f *= hi;
+        if (pw >= 3) f *= hi;
+        for (int k = 3; k < pw; ++k) f *= hi;
+        reinterpret_cast<float*>(f_s)[4 * pos_s[nid_off[pair_t[q]] + j] + fidx_s[q]] = f;
+    };
 
     // ---- load the tile
     for (int k = tid; k < NT; k += blockDim.x) {
@@ -656,7 +697,21 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
                 const int hi = lower_bound_u16(nid, cnt_s[t], n + 1);
                 for (int j = lower_bound_u16(nid, cnt_s[t], n); j < hi; ++j) {
                     pos_s[nid_off[t] + j] = (uint16_t)o;
-                    if (M.kind == NMODL_HH) {
+                    if (FAC) {
+                        // factors 1 except the constant conductances (the
+                        // HH leak; a cnexp type without gates); the gate
+                        // items fill in the rest
+                        if (M.kind == NMODL_HH) {
+                            for (int q = 0; q < 3; ++q)
+                                f_s[o + q] = make_float4(q == 2 ? curf_s[t][4] : 1.f, 1.f, 1.f,
+                                                         __int_as_float(3 * t + q));
+                            o += 3;
+                        } else {
+                            f_s[o] = make_float4(M.n_gates == 0 ? curf_s[t][0] : 1.f, 1.f, 1.f,
+                                                 __int_as_float(3 * t));
+                            ++o;
+                        }
+                    } else if (M.kind == NMODL_HH) {
                         for (int q = 0; q < 3; ++q) {
                             xg_s[o + q].x = M.hh_e[q];
                             if (EXT && A.ions)
@@ -691,6 +746,15 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
         __syncthreads();
         for (int n = tid; n < NT; n += blockDim.x)
             perm_s[atomicAdd(&hist_s[63 - min(eoff_s[n + 1] - eoff_s[n], 63)], 1)] = (uint16_t)n;
+        __syncthreads();
+    }
+
+    if (FAC) {  // the factors of the loaded states
+        int q = 0;
+        for (int k = tid; k < total_items; k += blockDim.x) {
+            while (k >= pair_start[q + 1]) ++q;
+            put_factor(q, k - pair_start[q], st_f[k].x);
+        }
         __syncthreads();
     }
 
@@ -745,7 +809,7 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
     };
     for (int step = 0; step < A.nsteps; ++step) {
         const bool last = (step == A.nsteps - 1);
-        if (flat) {
+        if (flat && !FAC) {
             // ---- conductances, one thread per instance (lane-efficient;
             // the owner loop below then spends two operations per instance).
             // MIXED: from the FP32 hi parts of the states, converted once.
@@ -816,7 +880,13 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
             if (flat) {
                 double X = 0.0, G = 0.0, Xca = 0.0, Gca = 0.0;
                 const int s0 = eoff_s[n], s1 = eoff_s[n + 1];
-                for (int sl = s0; sl < s1; ++sl) {
+                for (int sl = s0; FAC && sl < s1; ++sl) {
+                    const float4 f = f_s[sl];
+                    const double g = f2d_int((f.x * f.y) * f.z);
+                    X = fma(g, efac_s[__float_as_int(f.w)], X);
+                    G += g;
+                }
+                for (int sl = s0; !FAC && sl < s1; ++sl) {
                     const double2 eg = xg_s[sl];
                     X = fma(eg.y, eg.x, X);
                     G += eg.y;
@@ -1098,6 +1168,7 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
             for (int k = tid; k < total_items; k += blockDim.x) {
                 while (k >= pair_start[q + 1]) ++q;
                 item(k, pair_t[q], pair_g[q], k - pair_start[q]);
+                if (FAC) put_factor(q, k - pair_start[q], st_f[k].x);
             }
         }
         __syncthreads();

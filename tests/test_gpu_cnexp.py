@@ -244,7 +244,7 @@ def test_mixed_precision_errors(api, orc):
            for m in wl["mechs"]]
     out = {}
     for nsteps in (1, 200):
-        ctx = _ctx(api, precision=api.NMODL_MIXED, tile_smem=16384)
+        ctx = _ctx(api, precision=api.NMODL_MIXED, tile_smem=24576)
         mechs = make_mechs(ctx, wl)
         for m, s in zip(mechs, st0):
             if m.n_states:

@@ -346,14 +346,18 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
                                   (KIN && PREC == NMODL_MIXED) ? 2 : 1)
     k_fused_tiles(FusedArgs A) {
     static_assert(!KIN || EXT, "the 9-state scheme comes with the extended variant");
-    // MIXED without the small systems, on isolated compartments: each gate
-    // update writes its instance's conductance factor into the instance's
-    // node-major slot (gbar m^p for a type's first gate, h^q for the next
-    // ones; HH: gnabar m^3 and h into the sodium slot, gkbar n^4 into the
-    // potassium slot), the slot's fourth float holds the id of its current
-    // (its reversal potential in efac_s), and the owner pass multiplies the
-    // factors: no separate conductance pass, two barriers per step, not three
-    constexpr bool FAC_V = PREC == NMODL_MIXED && !EXT;
+    // MIXED on isolated compartments: each gate update writes its
+    // instance's conductance factor into the instance's node-major slot
+    // (gbar m^p for a type's first gate, h^q for the next ones; HH: gnabar
+    // m^3 and h into the sodium slot, gkbar n^4 into the potassium slot; a
+    // 3-state instance gbar x_open after its solve), the slot's fourth float
+    // holds the id of its current (its reversal potential in efac_s), and
+    // the owner pass multiplies the factors: no separate conductance pass,
+    // two barriers per step, not three.  Not in the variant with the 9-state
+    // scheme, whose 128-register bound the extra code pushed into more
+    // spills (measured 0.92x there; 1.16x on the cnexp networks, 1.06x with
+    // ion arrays and the small systems).
+    constexpr bool FAC_V = PREC == NMODL_MIXED && !KIN;
     __shared__ double efac_s[FAC_V ? 3 * kMaxMechsFused : 1];   // e of current 3 t + q
     __shared__ float fmul_s[FAC_V ? kMaxMechsFused * kMaxGates : 1];
     __shared__ int fidx_s[FAC_V ? kMaxMechsFused * kMaxGates : 1];  // 4 slot + component
@@ -494,6 +498,17 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
                 const MechD& M = md_s[pair_t[p]];
                 const int g = pair_g[p];
                 const bool hh = M.kind == NMODL_HH;
+                if (M.kind != NMODL_HH && M.kind != NMODL_CNEXP) {
+                    // a coupled system: its open state's factor gbar x_open
+                    // is written by the system's own update (power -1 here);
+                    // gbar and the open row serve the window's first factors
+                    const bool k3 = EXT && M.kind == NMODL_KIN3;
+                    const int open = k3 ? M.k3.open : M.open;
+                    fmul_s[p] = (float)(k3 ? M.k3.gbar : M.gbar);
+                    fpow_s[p] = (M.kind == NMODL_CACUM || g != open) ? -2 : -1;
+                    fidx_s[p] = 0;
+                    continue;
+                }
                 fmul_s[p] = g == 0 ? (float)(hh ? M.hh_g[0] : M.gbar)
                                    : (hh && g == 2) ? (float)M.hh_g[1] : 1.f;
                 fpow_s[p] = M.gate[g].power;
@@ -501,7 +516,9 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
             }
             for (int t = 0; t < T; ++t)
                 for (int c = 0; c < 3; ++c)
-                    efac_s[3 * t + c] = md_s[t].kind == NMODL_HH ? md_s[t].hh_e[c] : md_s[t].e;
+                    efac_s[3 * t + c] = md_s[t].kind == NMODL_HH     ? md_s[t].hh_e[c]
+                                        : (EXT && md_s[t].kind == NMODL_KIN3) ? md_s[t].k3.e
+                                                                        : md_s[t].e;
         }
         // Work order of the FP64 state phase: the gates grouped by their pair
         // of rate forms (each pair of forms is one straight-line body), each
@@ -546,7 +563,7 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
         for (int k = tid; k < T; k += blockDim.x) {
             const MechD& M = md_s[k];
             phidt_f[k] = (float)(M.phi * A.dt);
-            curf_s[k][0] = (float)M.gbar;
+            curf_s[k][0] = (float)((EXT && M.kind == NMODL_KIN3) ? M.k3.gbar : M.gbar);
             curf_s[k][1] = (float)M.e;
             for (int q = 0; q < 3; ++q) {
                 curf_s[k][2 + q] = (float)M.hh_g[q];
@@ -627,6 +644,7 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
     auto put_factor = [&](int q, int j, float hi) {
         float f = fmul_s[q];
         const int pw = fpow_s[q];
+        if (pw < 0) return;  // a coupled system's row
         if (pw >= 1) f *= hi;
         if (pw >= 2) f *= hi;
         if (pw >= 3) f *= hi;
@@ -700,15 +718,20 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
                     if (FAC) {
                         // factors 1 except the constant conductances (the
                         // HH leak; a cnexp type without gates); the gate
-                        // items fill in the rest
+                        // items and the systems' updates fill in the rest
                         if (M.kind == NMODL_HH) {
-                            for (int q = 0; q < 3; ++q)
+                            for (int q = 0; q < 3; ++q) {
                                 f_s[o + q] = make_float4(q == 2 ? curf_s[t][4] : 1.f, 1.f, 1.f,
                                                          __int_as_float(3 * t + q));
+                                if (EXT && A.ions)
+                                    tag_s[o + q] = q == 0 ? NMODL_ION_NA : q == 1 ? NMODL_ION_K : NMODL_ION_NONE;
+                            }
                             o += 3;
-                        } else {
-                            f_s[o] = make_float4(M.n_gates == 0 ? curf_s[t][0] : 1.f, 1.f, 1.f,
+                        } else if (!EXT || M.kind != NMODL_CACUM) {
+                            const bool konst = M.kind == NMODL_CNEXP && M.n_gates == 0;
+                            f_s[o] = make_float4(konst ? curf_s[t][0] : 1.f, 1.f, 1.f,
                                                  __int_as_float(3 * t));
+                            if (EXT && A.ions) tag_s[o] = (uint8_t)M.ion;
                             ++o;
                         }
                     } else if (M.kind == NMODL_HH) {
@@ -749,11 +772,17 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
         __syncthreads();
     }
 
+    // FAC: a coupled system's factor gbar x_open into its slot
+    auto put_open_factor = [&](int t, int j, float fmul, float x_open) {
+        reinterpret_cast<float*>(f_s)[4 * pos_s[nid_off[t] + j]] = fmul * x_open;
+    };
     if (FAC) {  // the factors of the loaded states
         int q = 0;
         for (int k = tid; k < total_items; k += blockDim.x) {
             while (k >= pair_start[q + 1]) ++q;
-            put_factor(q, k - pair_start[q], st_f[k].x);
+            const int j = k - pair_start[q];
+            if (fpow_s[q] == -1) put_open_factor(pair_t[q], j, fmul_s[q], st_f[k].x);
+            else put_factor(q, j, st_f[k].x);
         }
         __syncthreads();
     }
@@ -880,21 +909,29 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
             if (flat) {
                 double X = 0.0, G = 0.0, Xca = 0.0, Gca = 0.0;
                 const int s0 = eoff_s[n], s1 = eoff_s[n + 1];
-                for (int sl = s0; FAC && sl < s1; ++sl) {
-                    const float4 f = f_s[sl];
-                    const double g = f2d_int((f.x * f.y) * f.z);
-                    X = fma(g, efac_s[__float_as_int(f.w)], X);
+                // a slot's conductance and reversal potential: (e, g), or
+                // (FAC) the product of its FP32 factors and its current's e
+                auto slot_ge = [&](int sl, double& g, double& e) {
+                    if (FAC) {
+                        const float4 f = f_s[sl];
+                        g = f2d_int((f.x * f.y) * f.z);
+                        e = efac_s[__float_as_int(f.w)];
+                    } else {
+                        const double2 eg = xg_s[sl];
+                        g = eg.y;
+                        e = eg.x;
+                    }
+                };
+                for (int sl = s0; sl < s1; ++sl) {
+                    double g, e;
+                    slot_ge(sl, g, e);
+                    X = fma(g, e, X);
                     G += g;
-                }
-                for (int sl = s0; !FAC && sl < s1; ++sl) {
-                    const double2 eg = xg_s[sl];
-                    X = fma(eg.y, eg.x, X);
-                    G += eg.y;
                     if (EXT && A.ions) {
                         // calcium every step (the buffer reads it), without a
                         // branch: sum(g e) and sum(g) over the calcium slots
-                        const double gc = tag_s[sl] == NMODL_ION_CA ? eg.y : 0.0;
-                        Xca = fma(gc, eg.x, Xca);
+                        const double gc = tag_s[sl] == NMODL_ION_CA ? g : 0.0;
+                        Xca = fma(gc, e, Xca);
                         Gca += gc;
                     }
                 }
@@ -904,10 +941,11 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
                     s_ca = fma(vv, Gca, -Xca);
                     if (last) {  // sodium and potassium, once per window
                         for (int sl = s0; sl < s1; ++sl) {
-                            const double2 eg = xg_s[sl];
+                            double g, e;
+                            slot_ge(sl, g, e);
                             const int tg = tag_s[sl];
-                            if (tg == NMODL_ION_NA) s_na = fma(eg.y, vv - eg.x, s_na);
-                            else if (tg == NMODL_ION_K) s_k = fma(eg.y, vv - eg.x, s_k);
+                            if (tg == NMODL_ION_NA) s_na = fma(g, vv - e, s_na);
+                            else if (tg == NMODL_ION_K) s_k = fma(g, vv - e, s_k);
                         }
                     }
                 }
@@ -1090,6 +1128,13 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
                         st_f[o] = make_float2(hi, d2f_int(y[a] - f2d_int(hi)));
                     }
                 }
+                if (FAC) {
+                    double yo = y[0];
+#pragma unroll
+                    for (int a = 1; a < 9; ++a)
+                        if (a == md_s[t].open) yo = y[a];
+                    put_open_factor(t, j, curf_s[t][0], d2f_int(yo));
+                }
                 return;
             }
             if (EXT && (kind == NMODL_KIN3 || kind == NMODL_CACUM)) {
@@ -1129,6 +1174,11 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
                         st_f[o] = make_float2(hi, d2f_int(x[a] - f2d_int(hi)));
                     }
                 }
+                if (FAC && kind == NMODL_KIN3) {
+                    const int open = md_s[t].k3.open;
+                    put_open_factor(t, j, curf_s[t][0],
+                                    d2f_int(open == 0 ? x[0] : open == 1 ? x[1] : x[2]));
+                }
                 return;
             }
             if (PREC == NMODL_FP64) {
@@ -1160,7 +1210,10 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
                 while (w >= wstart_s[wi + 1]) ++wi;
                 const int q = wq_s[wi];
                 const int t = pair_t[q], j = w - wstart_s[wi];
-                if (j < cnt_s[t]) item(pair_start[q] + j, t, pair_g[q], j);
+                if (j < cnt_s[t]) {
+                    item(pair_start[q] + j, t, pair_g[q], j);
+                    if (FAC) put_factor(q, j, st_f[pair_start[q] + j].x);
+                }
             }
         } else {
             // storage order (one group: the bodies are cheap and issue-bound)

@@ -52,7 +52,7 @@ def _run(api, orc, wl, steps, ions=False, **opt):
     plan = ctx.plan(mechs)
     out = dict(v=v.cpu().numpy(), rhs=rhs.cpu().numpy(), d=d.cpu().numpy(),
                states=[m.states().cpu().numpy() if m.n_states else None for m in mechs],
-               plan=plan, st0=st0,
+               plan=plan, st0=st0, kin9_stats=mechs[-1].stats(),
                ions=[a.cpu().numpy() for a in arrs] if arrs else None)
     for m in mechs:
         m.close()
@@ -153,3 +153,24 @@ def test_fused_cable_form(api, orc):
     for m in mechs:
         m.close()
     ctx.close()
+
+
+def test_autotuned_form_parity_and_counters(api, orc):
+    """Default options (the autotuner may run an FP64 list with the 9-state
+    scheme as per-mechanism launches where they time faster than the fused
+    variant): whichever form it keeps, the trajectory matches the oracle, and
+    the Newton counters equal those of an explicit per-mechanism run (the
+    trial launches on scratch copies leave them untouched)."""
+    wl = _network(20000, seed=46, frac=0.3)
+    n = wl["n_nodes"]
+    steps = 45
+    got = _run(api, orc, wl, steps, window=9)
+    ref_run = _run(api, orc, wl, steps, window=9, no_fuse=1)
+    assert got["plan"]["form"] in ("tiles", "launches")
+    v_ref, _, _, s_ref = orc.step(wl["mechs"], got["st0"], wl["v0"], n, 0.025, nsteps=steps)
+    assert np.max(np.abs(got["v"] - v_ref) / np.maximum(np.abs(v_ref), 1.0)) <= 1e-9
+    for g, s in zip(got["states"], s_ref):
+        if g is not None:
+            assert state_err(g, s) <= 1e-9
+    assert got["kin9_stats"]["newton_iters"] == ref_run["kin9_stats"]["newton_iters"]
+    assert got["kin9_stats"]["newton_iters"] >= 2 * steps * wl["mechs"][-1]["node_index"].size

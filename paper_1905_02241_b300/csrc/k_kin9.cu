@@ -94,8 +94,12 @@ struct Kin9Launch {
     float kf[4 * kKinEdges];
 };
 
+// MIXED is compiled for three 128-thread blocks per SM (168 registers, a few
+// dozen bytes of spills): its FP64 residue then runs at 12 warps per SM
+// instead of 8 (measured 1.14x on 1M instances); the FP64 form keeps its
+// ~240 registers (two blocks), being bound by the FP64 pipe already.
 template <int PREC, bool LIST>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, PREC == NMODL_MIXED ? 3 : 1)
     k_kin9_state(const Kin9D* __restrict__ kd, const Kin9Launch KL, int64_t n,
                  const int32_t* __restrict__ ni, const double* __restrict__ v,
                  double* st, int64_t stride, double dt_scalar,

@@ -268,14 +268,20 @@ NMODL_API int nmodl_cur(nmodl_mech *m, const double *v, double *rhs, double *d);
  * FP64 without ion arrays or options.cnexp_pade (and options.no_fuse 0),
  * runs in a kernel of its own instead: one launch per window, three warps
  * per block, one per gate, a network too small to fill the GPU being bound
- * by the length of each step's dependent chain.  nsteps = 0 is a no-op. */
+ * by the length of each step's dependent chain.  One NMODL_KIN9 mechanism
+ * with an attached surrogate and one instance on each node (node_index 0,
+ * 1, ..., n_nodes - 1; no ion arrays, options.no_fuse 0) runs each step as
+ * the surrogate kernel, which forms every node's current, rhs, d and v
+ * update before the instance's state update, and the fallback solve: the
+ * same values as the per-mechanism sequence.  nsteps = 0 is a no-op. */
 NMODL_API int nmodl_step(nmodl_ctx *ctx, nmodl_mech *const *mechs, int n_mechs,
                double dt, double cm, double *v, double *rhs, double *d,
                int nsteps);
 
 /* Shape nmodl_step chose for this mechanism list (after a first call):
- * out[0] fused tiles (1), per-mechanism launches (0) or the single-HH
- * gate-warp kernel (2), out[1] tiles (form 2: blocks), out[2] block size,
+ * out[0] fused tiles (1), per-mechanism launches (0), the single-HH
+ * gate-warp kernel (2) or the surrogate network step (3), out[1] tiles
+ * (form 2: blocks), out[2] block size,
  * out[3] dynamic shared memory per block (bytes), out[4] persistent tile
  * queue (1) or one block per tile (0), out[5] tile shared-memory budget
  * (form 2: nodes per block).  The autotuner (options.autotune) picks the

@@ -302,7 +302,7 @@ def nmodl_plan_describe(ctx: int, mechs) -> dict:
     out = (ctypes.c_int64 * 6)()
     _check(lib.nmodl_plan_describe(ctx, ctypes.cast(arr, _vp), len(mechs),
                                    ctypes.cast(out, _vp)), "nmodl_plan_describe")
-    form = {0: "launches", 1: "tiles", 2: "hh_gate_warps"}[int(out[0])]
+    form = {0: "launches", 1: "tiles", 2: "hh_gate_warps", 3: "surrogate_step"}[int(out[0])]
     return dict(fused=bool(out[0]), form=form, tiles=int(out[1]), block=int(out[2]),
                 smem=int(out[3]), persistent=bool(out[4]), tile_budget=int(out[5]))
 

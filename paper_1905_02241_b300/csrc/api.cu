@@ -16,6 +16,8 @@ using namespace nmodl;
 namespace nmodl {
 // api_surrogate.cu: surrogate state update of a NMODL_KIN9 mechanism
 cudaError_t enqueue_surrogate_state(nmodl_mech* m, double dt, const double* v);
+cudaError_t enqueue_surrogate_network_step(nmodl_mech* m, double dt, double cm, double* v,
+                                           double* rhs, double* d, int clamp);
 }  // namespace nmodl
 
 // Drop the cached step plans (and their graphs) that involve mechanism m
@@ -704,25 +706,44 @@ struct Candidate {
 // no ion arrays, the exponential cnexp factor, and at most 32 nodes per SM
 // (a network too small for the tile kernel to fill the GPU).  Returns the
 // nodes per block, 0 where the form does not apply.
+// Instance i of m sits on node i for every i (node_index = 0, 1, ...,
+// n_nodes - 1).  Reads node_index back once, at plan time.
+static bool identity_nodes(nmodl_ctx* c, const nmodl_mech* m) {
+    if (m->n != m->n_nodes || m->n == 0) return false;
+    std::vector<int32_t> ni((size_t)m->n);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+        cudaMemcpy(ni.data(), m->d_ni, ni.size() * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return false;
+    for (int64_t i = 0; i < m->n; ++i)
+        if (ni[(size_t)i] != i) return false;
+    return true;
+}
+
 static int hh_warps_shape(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs,
                           nmodl_cable* cb) {
     if (n_mechs != 1 || cb || c->opt.no_fuse || c->opt.precision != NMODL_FP64 ||
         c->opt.cnexp_pade || c->has_ions())
         return 0;
     const nmodl_mech* m = mechs[0];
-    if (m->type != NMODL_HH || m->n != m->n_nodes || m->n == 0) return 0;
+    if (m->type != NMODL_HH) return 0;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-        sms <= 0 || m->n > 32 * (int64_t)sms)
+        sms <= 0 || m->n > 32 * (int64_t)sms || !identity_nodes(c, m))
         return 0;
-    std::vector<int32_t> ni((size_t)m->n);
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
-        cudaMemcpy(ni.data(), m->d_ni, ni.size() * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
-            cudaSuccess)
-        return 0;
-    for (int64_t i = 0; i < m->n; ++i)
-        if (ni[(size_t)i] != i) return 0;
     return hh_warps_per_block(m->n, sms);
+}
+
+// One NMODL_KIN9 mechanism with an attached surrogate, instance i on node i,
+// isolated compartments, no ion arrays: the surrogate kernel forms each
+// node's current, rhs and d and its v update itself before the state update
+// (one kernel and the fallback per step instead of the zeroing, current and
+// v-update launches in front of them).
+static bool sur_step_fits(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs,
+                          nmodl_cable* cb) {
+    if (n_mechs != 1 || cb || c->opt.no_fuse || c->has_ions()) return false;
+    const nmodl_mech* m = mechs[0];
+    return m->type == NMODL_KIN9 && m->sur && identity_nodes(c, m);
 }
 
 static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan* p,
@@ -762,6 +783,11 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     p->variant = p->precision + (ext ? 2 : 0) + (kin ? 2 : 0);
     p->fused = false;
     const bool dbg = std::getenv("NMODL_PLAN_DEBUG") != nullptr;
+    if ((p->sur_step = sur_step_fits(c, mechs, n_mechs, cb))) {
+        p->fused = true;
+        if (dbg) std::fprintf(stderr, "[nmodl plan] surrogate network step\n");
+        return NMODL_OK;
+    }
     if ((p->hh_per_block = hh_warps_shape(c, mechs, n_mechs, cb)) > 0) {
         p->fused = true;
         if (dbg) std::fprintf(stderr, "[nmodl plan] HH gate warps, %d nodes per block\n",
@@ -1200,6 +1226,14 @@ cudaError_t nmodl_run_window(nmodl_ctx* c, Plan* p, nmodl_mech* const* mechs, in
                               double dt, double cm, double* v, double* rhs, double* d,
                               int w) {
     auto direct = [&]() -> cudaError_t {
+        if (p->sur_step) {
+            for (int s = 0; s < w; ++s) {
+                const cudaError_t se = enqueue_surrogate_network_step(
+                    mechs[0], dt, cm, v, rhs, d, c->opt.clamp_v);
+                if (se != cudaSuccess) return se;
+            }
+            return cudaSuccess;
+        }
         if (p->hh_per_block > 0) {
             nmodl_mech* m = mechs[0];
             HhArgs a{};
@@ -1293,6 +1327,12 @@ int nmodl_plan_describe(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, int
         auto& p = *it;
         if ((int)p->mechs.size() == n_mechs && p->precision == c->opt.precision &&
             std::equal(p->mechs.begin(), p->mechs.end(), mechs)) {
+            if (p->sur_step) {
+                out[0] = 3;
+                out[1] = out[3] = out[4] = out[5] = 0;
+                out[2] = 512;
+                return NMODL_OK;
+            }
             if (p->hh_per_block > 0) {
                 out[0] = 2;
                 out[1] = (p->n_nodes + p->hh_per_block - 1) / p->hh_per_block;

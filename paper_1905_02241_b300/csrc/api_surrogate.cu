@@ -324,7 +324,18 @@ NMODL_API int nmodl_mech_attach_surrogate(nmodl_mech* m, nmodl_surrogate* s, dou
 namespace nmodl {
 // surrogate state update of a KIN9 mechanism with an attached surrogate:
 // fused MLP + projection + residual test, then Newton on the fallback list
-cudaError_t enqueue_surrogate_state(nmodl_mech* m, double dt, const double* v) {
+// step: null for the state update alone; else the whole network step of a
+// list of this one mechanism with instance i on node i (SurArgs::step)
+struct SurStep {
+    double cm;
+    double* v;
+    double* rhs;
+    double* d;
+    int clamp;
+};
+
+static cudaError_t enqueue_surrogate(nmodl_mech* m, double dt, const double* v,
+                                     const SurStep* step) {
     nmodl_ctx* c = m->ctx;
     nmodl_surrogate* s = m->sur;
     if (m->n == 0) return cudaSuccess;
@@ -346,6 +357,17 @@ cudaError_t enqueue_surrogate_state(nmodl_mech* m, double dt, const double* v) {
     a.fb_count = m->d_fb_count;
     a.fb_total = &m->d_cnt->fallback;
     a.err = c->d_err;
+    if (step) {
+        a.step = 1;
+        a.clamp = step->clamp;
+        a.open = m->kd.open;
+        a.gbar = m->kd.gbar;
+        a.e = m->kd.e;
+        a.cmdt = 1e-3 * step->cm / dt;
+        a.v_step = step->v;
+        a.rhs = step->rhs;
+        a.d = step->d;
+    }
     e = launch_surrogate_step(a, c->stream);
     if (e != cudaSuccess) return e;
     // The fallback solve: the FP32-LU Newton with FP64 residual refinement
@@ -359,5 +381,15 @@ cudaError_t enqueue_surrogate_state(nmodl_mech* m, double dt, const double* v) {
                       nullptr, o.newton_tol, o.newton_max_iter, o.ir_max, m->d_fb_list, m->n,
                       m->d_fb_count, m->d_cnt, c->d_err, c->stream);
     return cudaGetLastError();
+}
+
+cudaError_t enqueue_surrogate_state(nmodl_mech* m, double dt, const double* v) {
+    return enqueue_surrogate(m, dt, v, nullptr);
+}
+
+cudaError_t enqueue_surrogate_network_step(nmodl_mech* m, double dt, double cm, double* v,
+                                           double* rhs, double* d, int clamp) {
+    const SurStep st{cm, v, rhs, d, clamp};
+    return enqueue_surrogate(m, dt, v, &st);
 }
 }  // namespace nmodl

@@ -322,9 +322,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_surrogate_step(SurArgs a) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) f[k] = 0.f;
             if (valid) {
+                double vd = a.v[a.ni[i]];
+                if (a.step) {
+                    // the node's current, rhs and d, and its diagonal update
+                    // (node i holds this one instance), as the current
+                    // update, the v update and this state update in turn
+                    const double g = a.gbar * a.st[a.open * a.stride + i];
+                    const double r = 0.0 - g * (vd - a.e);
+                    const double dd = g + a.cmdt;
+                    if (!finite_int(r) || !finite_int(dd)) latch_error(a.err, NMODL_ERR_NONFINITE);
+                    a.rhs[i] = r;
+                    a.d[i] = dd;
+                    if (!a.clamp) {
+                        vd = vd + ddiv_fast(r, dd);
+                        if (!finite_int(vd)) latch_error(a.err, NMODL_ERR_NONFINITE);
+                        a.v_step[i] = vd;
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < 9; ++k) xf[k] = d2f_int(a.st[k * a.stride + i]);
-                const float vf = d2f_int(a.v[a.ni[i]]);
+                const float vf = d2f_int(vd);
                 kin_rates_folded(kps, vf, dkf, dkb);
                 dtAx_f(dkf, dkb, xf, z);
                 s = sur_inputs(a.scaled, vf, dtf, xf, z, f);

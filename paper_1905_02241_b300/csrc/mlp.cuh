@@ -99,6 +99,16 @@ struct SurArgs {
     int32_t* fb_count;
     unsigned long long* fb_total;
     int32_t* err;
+    // step != 0: the whole network step of a list of this one mechanism with
+    // instance i on node i: before its state update each instance forms its
+    // current at v_n (g = gbar x_open, i = g (v - e)), writes rhs = -i and
+    // d = g + cmdt, and (unless clamp) v = v_n + rhs/d, at which its state
+    // update then runs
+    int32_t step, clamp, open;
+    double gbar, e, cmdt;
+    double* v_step;            // v, written (the same array as v)
+    double* rhs;
+    double* d;
 };
 cudaError_t launch_surrogate_step(const SurArgs& a, cudaStream_t s);
 cudaError_t surrogate_prepare();

@@ -51,6 +51,9 @@ struct Plan {
     bool fused = false;
     // single-HH gate-warp form (k_hh.cu): nodes per block, 0 = not used
     int hh_per_block = 0;
+    // one NMODL_KIN9 mechanism with a surrogate, instance i on node i: the
+    // surrogate kernel runs the whole step (current, rhs/d, v, state)
+    bool sur_step = false;
     // fused form
     int n_tiles = 0, block = 256, tile_stride = 0;
     size_t smem = 0;

@@ -351,3 +351,73 @@ def test_ablation_raw_state_inputs(S, ctx, trained):
     print(f"fallback rate: raw-state network {r_raw:.3f}, scaled network {r_scaled:.3f}")
     assert r_scaled < r_raw
     raw.close()
+
+
+@pytest.mark.parametrize("clamp", [1, 0])
+def test_network_step_form_matches_per_mechanism_launches(S, orc, clamp):
+    """One 9-state mechanism with a surrogate and instance i on node i: the
+    surrogate kernel runs the whole step (current at v_n, rhs, d, v_n+1,
+    the gated state update and its fallback).  Against the per-mechanism
+    launch sequence (no_fuse) of the same list and weights, over 12 steps in
+    windows of 5, bit for bit: states, v, rhs, d and the fallback count; a
+    list whose instance i is not on node i keeps the launches."""
+    from paper_1905_02241_b300.api import Context, Mechanism
+    n = 10007
+    wl = W.kin9_clamped(n, seed=31)
+    spec = wl["mechs"][0]
+    Ws, bs = W.mlp_init(7)
+    w = S.Surrogate.pack(Ws, bs)
+    res = {}
+    for form, nf in (("fused", 0), ("launches", 1)):
+        ctx = Context(0, clamp_v=clamp, no_fuse=nf, window=5)
+        sur = S.Surrogate(ctx, max_batch=256)
+        sur.set_weights(w)
+        m = Mechanism(ctx, spec["type"], spec["node_index"], n, spec["params"])
+        m.set_states(to_dev(wl["x0"]))
+        S.attach(m, sur, 1e-4)
+        v, rhs, d = to_dev(wl["v0"]), to_dev(np.zeros(n)), to_dev(np.zeros(n))
+        ctx.step([m], 0.025, 1.0, v, rhs, d, 12)
+        assert ctx.sync() == 0
+        res[form] = dict(plan=ctx.plan([m])["form"], v=v.cpu().numpy(), rhs=rhs.cpu().numpy(),
+                         d=d.cpu().numpy(), x=m.states().cpu().numpy(), fb=m.stats()["fallback"])
+        S.attach(m, None)
+        m.close()
+        sur.close()
+        ctx.close()
+    a, b = res["fused"], res["launches"]
+    assert a["plan"] == "surrogate_step" and b["plan"] == "launches"
+    assert a["fb"] == b["fb"] > 0
+    for k in ("v", "rhs", "d", "x"):
+        assert np.array_equal(a[k], b[k]), k
+    if clamp:
+        assert np.array_equal(a["v"], wl["v0"])
+    else:
+        assert not np.array_equal(a["v"], wl["v0"])
+    # the one-step current against the oracle's (instance i on node i)
+    ctx = Context(0, clamp_v=clamp)
+    sur = S.Surrogate(ctx, max_batch=256)
+    sur.set_weights(w)
+    m = Mechanism(ctx, spec["type"], spec["node_index"], n, spec["params"])
+    m.set_states(to_dev(wl["x0"]))
+    S.attach(m, sur, 1e-4)
+    v, rhs, d = to_dev(wl["v0"]), to_dev(np.zeros(n)), to_dev(np.zeros(n))
+    ctx.step([m], 0.025, 1.0, v, rhs, d, 1)
+    assert ctx.sync() == 0
+    r_ref, d_ref = orc.mech_cur(spec["type"], spec["params"], spec["node_index"], wl["v0"],
+                                wl["x0"], np.zeros(n), np.zeros(n))
+    np.testing.assert_allclose(rhs.cpu().numpy(), r_ref, rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(d.cpu().numpy(), d_ref + 1e-3 / 0.025, rtol=1e-12)
+    S.attach(m, None)
+    m.close()
+    # not instance i on node i: the launches
+    ni = np.arange(n, dtype=np.int32)
+    ni[5] = 4
+    m = Mechanism(ctx, spec["type"], ni, n, spec["params"])
+    m.set_states(to_dev(wl["x0"]))
+    S.attach(m, sur, 1e-4)
+    ctx.step([m], 0.025, 1.0, v, rhs, d, 1)
+    assert ctx.sync() == 0 and ctx.plan([m])["form"] == "launches"
+    S.attach(m, None)
+    m.close()
+    sur.close()
+    ctx.close()

@@ -105,12 +105,24 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
     }
 
     // ---- stage the weights (bf16 copies, row-major) as K-major images
+    // (six 16-byte loads in flight per thread before their stores: the copy
+    // is otherwise one global-memory latency per chunk)
     auto stage = [&](const __nv_bfloat16* src, int off, int rows, int K) {
-        const int ch = K / 8;
-        for (int c = tid; c < rows * ch; c += kTrThreads) {
-            const int r = c / ch, k = (c % ch) * 8;
-            *reinterpret_cast<uint4*>(smem + off + umma_offset(r, k, K)) =
-                *reinterpret_cast<const uint4*>(src + r * K + k);
+        constexpr int kB = 6;
+        const int ch = K / 8, total = rows * ch;
+        for (int c0 = tid; c0 < total; c0 += kB * kTrThreads) {
+            uint4 w[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int c = c0 + u * kTrThreads;
+                if (c < total) w[u] = *reinterpret_cast<const uint4*>(src + (c / ch) * K + (c % ch) * 8);
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int c = c0 + u * kTrThreads;
+                if (c < total)
+                    *reinterpret_cast<uint4*>(smem + off + umma_offset(c / ch, (c % ch) * 8, K)) = w[u];
+            }
         }
     };
     stage(a.wbf + kBfW1, sW1, kHid, kIn);
@@ -300,6 +312,16 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
         }
         publish();
         if (tid <= kOutRaw) accs[tid] += ((red[tid] + red[16 + tid]) + red[32 + tid]) + red[48 + tid];
+        // this thread's 64 columns of SiLU'(Z_l) (stored by the forward pass),
+        // loaded as one batch before the tensor-core wait that precedes
+        // layer l's backward step, so that their latency hides under it
+        float4 dsv[16];
+        auto load_ds = [&](int l) {
+            const float* ds = l == 1 ? a.ds1 : l == 2 ? a.ds2 : a.ds3;
+            const float4* ip = reinterpret_cast<const float4*>(ds + row * kHid + 64 * h);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) dsv[q] = valid ? ip[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
         // ---- backward through the output layer: dW4^T += H3^T D4, G3 = D4 W4
         if (tid == 0) {
             tc_fence_after();
@@ -308,12 +330,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
             mma_run(tmem + cAcc, sb + sD4, kOut, false, sb + sW4, kHid, true, 1,
                     tr_idesc(kHid, false, true), false);
         }
+        load_ds(3);
         if (!commit_wait()) { timed_out = true; break; }
         // ---- hidden layers, top down: D_l = G_l * SiLU'(Z_l) into H_l's image
         for (int l = 3; l >= 1 && !timed_out; --l) {
             const int dimg = l == 3 ? sH3 : l == 2 ? sH2 : sH1;
-            const float* ds = l == 1 ? a.ds1 : l == 2 ? a.ds2 : a.ds3;
-#pragma unroll 1
+#pragma unroll
             for (int cb = 0; cb < 64; cb += 16) {
                 const int c = 64 * h + cb;
                 uint32_t r[16];
@@ -321,10 +343,9 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
                 tmem_ld_wait();
                 float dv[16];
                 if (valid) {
-                    const float4* ip = reinterpret_cast<const float4*>(ds + row * kHid + c);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 w = ip[q];
+                        const float4 w = dsv[cb / 4 + q];
                         dv[4 * q] = __uint_as_float(r[4 * q]) * w.x;
                         dv[4 * q + 1] = __uint_as_float(r[4 * q + 1]) * w.y;
                         dv[4 * q + 2] = __uint_as_float(r[4 * q + 2]) * w.z;
@@ -360,6 +381,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
                             tr_idesc(kIn, true, true), !first);
                 }
             }
+            if (l > 1) load_ds(l - 1);
             if (!commit_wait()) { timed_out = true; break; }
         }
     }

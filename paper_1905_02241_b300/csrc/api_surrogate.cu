@@ -118,9 +118,12 @@ NMODL_API int nmodl_surrogate_create(nmodl_ctx* c, int64_t max_batch, const floa
         if ((e = dalloc(&s->grad, kParamsPadded)) != cudaSuccess) break;
         if ((e = dalloc(&s->m, kParamsPadded)) != cudaSuccess) break;
         if ((e = dalloc(&s->v, kParamsPadded)) != cudaSuccess) break;
-        if ((e = dalloc(&s->ds1, B * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->ds2, B * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->ds3, B * kHid)) != cudaSuccess) break;
+        // whole 128-row tiles: the training kernel stores each tile's block
+        // column-major, a partial last tile included
+        const int64_t Bt = (B + 127) / 128 * 128;
+        if ((e = dalloc(&s->ds1, Bt * kHid)) != cudaSuccess) break;
+        if ((e = dalloc(&s->ds2, Bt * kHid)) != cudaSuccess) break;
+        if ((e = dalloc(&s->ds3, Bt * kHid)) != cudaSuccess) break;
         if ((e = dalloc(&s->part, (int64_t)s->n_part_max * kParamsPadded)) != cudaSuccess) break;
         if ((e = dalloc(&s->loss_part, s->n_part_max)) != cudaSuccess) break;
         if ((e = dalloc(&s->loss, 1)) != cudaSuccess) break;
@@ -222,8 +225,8 @@ NMODL_API int nmodl_surrogate_train_step(nmodl_surrogate* s, int64_t n, const fl
 
 // A whole training run: one optimiser step (loss and gradients, Adam with
 // the scheduled learning rate, bf16 refresh, loss record) is captured as a
-// CUDA graph whose kernels read the step index from device memory, then
-// replayed once per step.
+// CUDA graph of 16 steps whose kernels read the step index from device
+// memory, replayed once per 16 steps.
 NMODL_API int nmodl_surrogate_fit(nmodl_surrogate* s, int64_t n, const float* X, const float* T,
                                   int64_t batch, int epochs, float lr, float lr_min,
                                   float* loss_steps) {
@@ -243,20 +246,32 @@ NMODL_API int nmodl_surrogate_fit(nmodl_surrogate* s, int64_t n, const float* X,
         loss_and_grad(s, batch, X, T, 1, lr, fs);
         launch_fit_end(loss_steps, s->loss, fs, st);
     };
-    cudaGraphExec_t exec = nullptr;
-    if (e == cudaSuccess && st != nullptr) {
+    // graphs of kSteps optimiser steps (the step index lives on the device,
+    // so one graph serves every group), then one of the remaining steps: a
+    // graph launch per 16 steps instead of one per step
+    constexpr int64_t kSteps = 16;
+    auto make_exec = [&](int64_t steps, cudaGraphExec_t* ex) -> cudaError_t {
         cudaGraph_t graph = nullptr;
-        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            one_step();
+        cudaError_t ge = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (ge == cudaSuccess) {
+            for (int64_t k = 0; k < steps; ++k) one_step();
             const cudaError_t le = cudaGetLastError();
-            e = cudaStreamEndCapture(st, &graph);
-            if (e == cudaSuccess) e = le;
+            ge = cudaStreamEndCapture(st, &graph);
+            if (ge == cudaSuccess) ge = le;
         }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (ge == cudaSuccess) ge = cudaGraphInstantiate(ex, graph, 0);
         if (graph) cudaGraphDestroy(graph);
-        for (int64_t k = 0; e == cudaSuccess && k < total; ++k) e = cudaGraphLaunch(exec, st);
+        return ge;
+    };
+    if (e == cudaSuccess && st != nullptr) {
+        const int64_t groups = total / kSteps, rest = total % kSteps;
+        cudaGraphExec_t exec = nullptr, exec_rest = nullptr;
+        if (groups > 0) e = make_exec(kSteps, &exec);
+        for (int64_t k = 0; e == cudaSuccess && k < groups; ++k) e = cudaGraphLaunch(exec, st);
+        if (e == cudaSuccess && rest > 0) e = make_exec(rest, &exec_rest);
+        if (e == cudaSuccess && rest > 0) e = cudaGraphLaunch(exec_rest, st);
         if (exec) cudaGraphExecDestroy(exec);
+        if (exec_rest) cudaGraphExecDestroy(exec_rest);
     } else if (e == cudaSuccess) {  // legacy stream: no capture, plain launches
         for (int64_t k = 0; k < total; ++k) one_step();
         e = cudaGetLastError();

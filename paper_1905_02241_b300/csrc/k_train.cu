@@ -105,30 +105,22 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
     }
 
     // ---- stage the weights (bf16 copies, row-major) as K-major images
-    // (six 16-byte loads in flight per thread before their stores: the copy
-    // is otherwise one global-memory latency per chunk)
+    // (cp.async: every 16-byte piece in flight at once, no registers held;
+    // the copies overlap the zero fill below and are waited for before the
+    // bias pairs are written)
     auto stage = [&](const __nv_bfloat16* src, int off, int rows, int K) {
-        constexpr int kB = 6;
         const int ch = K / 8, total = rows * ch;
-        for (int c0 = tid; c0 < total; c0 += kB * kTrThreads) {
-            uint4 w[kB];
-#pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                const int c = c0 + u * kTrThreads;
-                if (c < total) w[u] = *reinterpret_cast<const uint4*>(src + (c / ch) * K + (c % ch) * 8);
-            }
-#pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                const int c = c0 + u * kTrThreads;
-                if (c < total)
-                    *reinterpret_cast<uint4*>(smem + off + umma_offset(c / ch, (c % ch) * 8, K)) = w[u];
-            }
+        for (int c = tid; c < total; c += kTrThreads) {
+            const uint32_t dst = sb + off + umma_offset(c / ch, (c % ch) * 8, K);
+            const __nv_bfloat16* g = src + (c / ch) * K + (c % ch) * 8;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(g) : "memory");
         }
     };
     stage(a.wbf + kBfW1, sW1, kHid, kIn);
     stage(a.wbf + kBfW2, sW2, kHid, kHid);
     stage(a.wbf + kBfW3, sW3, kHid, kHid);
     stage(a.wbf + kBfW4, sW4, kOut, kHid);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
     auto put = [&](int off, int r, int k, int K, float x) {
         *reinterpret_cast<__nv_bfloat16*>(smem + off + umma_offset(r, k, K)) = __float2bfloat16_rn(x);
     };
@@ -138,14 +130,17 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
         put(off, r, k, K, b);
         put(off, r, k + 1, K, b - __bfloat162float(hi));
     };
-    for (int i = tid; i < kTrRows * 16; i += kTrThreads) put(sOne, i / 16, i % 16, 16, (i % 16) < 2 ? 1.f : 0.f);
-    for (int i = tid; i < kHid * 16; i += kTrThreads) {
-        put(sB2, i / 16, i % 16, 16, 0.f);
-        put(sB3, i / 16, i % 16, 16, 0.f);
-    }
-    for (int i = tid; i < kOut * 16; i += kTrThreads) put(sB4, i / 16, i % 16, 16, 0.f);
+    // ONE and the bias images (contiguous from sOne): zeros by 16-byte
+    // stores, then the ones of ONE's columns 0, 1
+    static_assert(sB2 == sOne + kImOne && sB3 == sB2 + kImBH && sB4 == sB3 + kImBH &&
+                  (sB4 + kImB4 - sOne) % 16 == 0 && sOne % 16 == 0, "contiguous bias images");
+    for (int i = tid; i < (sB4 + kImB4 - sOne) / 16; i += kTrThreads)
+        *reinterpret_cast<uint4*>(smem + sOne + 16 * i) = make_uint4(0u, 0u, 0u, 0u);
     if (tid < 16) accs[tid] = 0.f;
+    // every weight piece landed (W1's bias columns below share its pieces)
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
+    for (int i = tid; i < kTrRows * 2; i += kTrThreads) put(sOne, i / 2, i % 2, 16, 1.f);
     for (int i = tid; i < kHid; i += kTrThreads) {
         put_pair(sW1, i, kInRaw, kIn, a.params[kOffB1 + i]);  // W1 columns 11, 12
         put_pair(sB2, i, 0, 16, a.params[kOffB2 + i]);
@@ -229,12 +224,16 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
             }
             if (!commit_wait()) { timed_out = true; break; }
             float* ds = l == 1 ? a.ds1 : l == 2 ? a.ds2 : a.ds3;
-#pragma unroll 1
+            // the 64 columns in four chunks, each chunk's tensor-memory read
+            // issued before the previous chunk's arithmetic
+            uint32_t rb[2][16];
+            tmem_ld16(lane_base + cAcc + 64 * h, rb[0]);
+#pragma unroll
             for (int cb = 0; cb < 64; cb += 16) {
                 const int c = 64 * h + cb;
-                uint32_t r[16];
-                tmem_ld16(lane_base + cAcc + c, r);
-                tmem_ld_wait();
+                tmem_ld_wait(rb[(cb >> 4) & 1]);
+                if (cb + 16 < 64) tmem_ld16(lane_base + cAcc + c + 16, rb[((cb >> 4) + 1) & 1]);
+                const uint32_t* r = rb[(cb >> 4) & 1];
                 float sv[16], dv[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
@@ -250,10 +249,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
                                    pack_bf16(sv[8 * q + 4], sv[8 * q + 5]),
                                    pack_bf16(sv[8 * q + 6], sv[8 * q + 7]));
                 if (a.mode == 1 && valid) {
-                    float4* o = reinterpret_cast<float4*>(ds + row * kHid + c);
+                    // the tile's SiLU' block column-major (column c of the
+                    // tile's 128 rows contiguous): a warp's store of one
+                    // column is 128 contiguous bytes
+                    float* o = ds + (row - t) * kHid + t;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        o[q] = make_float4(dv[4 * q], dv[4 * q + 1], dv[4 * q + 2], dv[4 * q + 3]);
+                    for (int e = 0; e < 16; ++e) o[(c + e) * kTrRows] = dv[e];
                 }
             }
             publish();
@@ -318,9 +319,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
         float4 dsv[16];
         auto load_ds = [&](int l) {
             const float* ds = l == 1 ? a.ds1 : l == 2 ? a.ds2 : a.ds3;
-            const float4* ip = reinterpret_cast<const float4*>(ds + row * kHid + 64 * h);
+            const float* ip = ds + (row - t) * kHid + t + (int64_t)(64 * h) * kTrRows;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) dsv[q] = valid ? ip[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = 0; q < 16; ++q)
+                dsv[q] = valid ? make_float4(ip[(4 * q) * kTrRows], ip[(4 * q + 1) * kTrRows],
+                                             ip[(4 * q + 2) * kTrRows], ip[(4 * q + 3) * kTrRows])
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
         };
         // ---- backward through the output layer: dW4^T += H3^T D4, G3 = D4 W4
         if (tid == 0) {
@@ -335,12 +339,14 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
         // ---- hidden layers, top down: D_l = G_l * SiLU'(Z_l) into H_l's image
         for (int l = 3; l >= 1 && !timed_out; --l) {
             const int dimg = l == 3 ? sH3 : l == 2 ? sH2 : sH1;
+            uint32_t rb[2][16];
+            tmem_ld16(lane_base + cAcc + 64 * h, rb[0]);
 #pragma unroll
             for (int cb = 0; cb < 64; cb += 16) {
                 const int c = 64 * h + cb;
-                uint32_t r[16];
-                tmem_ld16(lane_base + cAcc + c, r);
-                tmem_ld_wait();
+                tmem_ld_wait(rb[(cb >> 4) & 1]);
+                if (cb + 16 < 64) tmem_ld16(lane_base + cAcc + c + 16, rb[((cb >> 4) + 1) & 1]);
+                const uint32_t* r = rb[(cb >> 4) & 1];
                 float dv[16];
                 if (valid) {
 #pragma unroll
@@ -389,21 +395,37 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
     // ---- the CTA's gradient partials (every entry of the padded layout)
     if (a.mode == 1 && !timed_out) {
         float* P = a.part + (int64_t)blockIdx.x * kParamsPadded;
-        auto dump = [&](uint32_t col, float* dst) {  // 64 columns of this row
-#pragma unroll 1
+        // dW2, dW3: each warp's 32 rows x 64 columns through shared memory
+        // (the H images are free now; rows padded to 68 floats), then out by
+        // rows, two 256-byte rows per store instruction, instead of one
+        // 16-byte piece of 32 rows 512 bytes apart per instruction
+        float* tb = reinterpret_cast<float*>(smem + sH1) + warp * (32 * 68);
+        auto dump = [&](uint32_t col, float* dst) {  // dst: this half's column 0 of the matrix
+            uint32_t rb[2][16];
+            tmem_ld16(lane_base + col, rb[0]);
+#pragma unroll
             for (int cb = 0; cb < 64; cb += 16) {
-                uint32_t r[16];
-                tmem_ld16(lane_base + col + cb, r);
-                tmem_ld_wait();
-                float4* o = reinterpret_cast<float4*>(dst + cb);
+                tmem_ld_wait(rb[(cb >> 4) & 1]);
+                if (cb + 16 < 64) tmem_ld16(lane_base + col + cb + 16, rb[((cb >> 4) + 1) & 1]);
+                const uint32_t* r = rb[(cb >> 4) & 1];
+                float4* o = reinterpret_cast<float4*>(tb + lane * 68 + cb);
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     o[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
                                        __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
             }
+            __syncwarp();
+            const int rbase = 32 * (warp & 3);
+#pragma unroll 4
+            for (int k = 0; k < 16; ++k) {
+                const int rr = 2 * k + (lane >> 4), q = lane & 15;
+                *reinterpret_cast<float4*>(dst + (int64_t)(rbase + rr) * kHid + 4 * q) =
+                    *reinterpret_cast<const float4*>(tb + rr * 68 + 4 * q);
+            }
+            __syncwarp();
         };
-        dump(cDW2 + 64 * h, P + kOffW2 + t * kHid + 64 * h);
-        dump(cDW3 + 64 * h, P + kOffW3 + t * kHid + 64 * h);
+        dump(cDW2 + 64 * h, P + kOffW2 + 64 * h);
+        dump(cDW3 + 64 * h, P + kOffW3 + 64 * h);
         uint32_t r[16];
         if (h == 0) {
             tmem_ld16(lane_base + cDW1, r);
@@ -436,20 +458,34 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
     }
 }
 
-// grad[i] = sum over the CTA partials in launch order.  adam: then the Adam
+// grad[i] = sum over the CTA partials in a fixed order (below).  adam: then the Adam
 // step on the FP32 master parameter (learning rate and bias corrections from
 // the arguments, or from the run's step index when fs.active) and the bf16
 // copy of the weight matrices.  Block 0 also sums the loss partials.
-__global__ void k_grad_adam(const float* __restrict__ part, int n_part,
+__global__ void __launch_bounds__(128) k_grad_adam(const float* __restrict__ part, int n_part,
                             const float* __restrict__ loss_part, float* loss, float* grad,
                             int adam, float* p, float* m, float* v, __nv_bfloat16* wbf,
                             float lr, float b1, float b2, float eps, float bc1, float bc2,
                             FitSched fs) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        float l = 0.f;
-        for (int c = 0; c < n_part; ++c) l += loss_part[c];
-        *loss = l;
-    }
+    // Sums over the CTA partials in launch order within each quarter of the
+    // partials, loads in batches of 16 ahead of their additions; the four
+    // warps of a block take the four quarters of the same 32 parameters
+    // (coalesced rows), and the quarter sums are added in a fixed order
+    // (deterministic)
+    __shared__ float qs[4][32];
+    auto sum_parts = [](const float* base, int64_t stride, int c, int c1) {
+        float acc = 0.f;
+        for (; c + 16 <= c1; c += 16) {
+            float x[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) x[u] = base[(int64_t)(c + u) * stride];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc += x[u];
+        }
+        for (; c < c1; ++c) acc += base[(int64_t)c * stride];
+        return acc;
+    };
+    if (blockIdx.x == 0 && threadIdx.x == 0) *loss = sum_parts(loss_part, 1, 0, n_part);
     if (adam && fs.active) {
         const int64_t k = *fs.step;
         lr = fs.lr_min + 0.5f * (fs.lr0 - fs.lr_min) *
@@ -458,27 +494,30 @@ __global__ void k_grad_adam(const float* __restrict__ part, int n_part,
         bc1 = 1.f - powf(b1, tt);
         bc2 = 1.f - powf(b2, tt);
     }
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kParamsPadded;
-         i += gridDim.x * blockDim.x) {
-        float g = 0.f;
-        for (int c = 0; c < n_part; ++c) g += part[(int64_t)c * kParamsPadded + i];
-        if (!adam) {
-            grad[i] = g;
-            continue;
-        }
-        const float mi = b1 * m[i] + (1.f - b1) * g;
-        const float vi = b2 * v[i] + (1.f - b2) * g * g;
-        m[i] = mi;
-        v[i] = vi;
-        const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-        p[i] = pi;
-        int bi = -1;
-        if (i >= kOffW1 && i < kOffB1) bi = kBfW1 + (i - kOffW1);
-        else if (i >= kOffW2 && i < kOffB2) bi = kBfW2 + (i - kOffW2);
-        else if (i >= kOffW3 && i < kOffB3) bi = kBfW3 + (i - kOffW3);
-        else if (i >= kOffW4 && i < kOffB4) bi = kBfW4 + (i - kOffW4);
-        if (bi >= 0) wbf[bi] = __float2bfloat16_rn(pi);
+    const int lane = threadIdx.x & 31, q4 = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    const int per = (n_part + 3) / 4;
+    const int c0 = min(n_part, q4 * per), c1 = min(n_part, c0 + per);
+    qs[q4][lane] = i < kParamsPadded ? sum_parts(part + i, kParamsPadded, c0, c1) : 0.f;
+    __syncthreads();
+    if (q4 != 0 || i >= kParamsPadded) return;
+    const float g = ((qs[0][lane] + qs[1][lane]) + qs[2][lane]) + qs[3][lane];
+    if (!adam) {
+        grad[i] = g;
+        return;
     }
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    p[i] = pi;
+    int bi = -1;
+    if (i >= kOffW1 && i < kOffB1) bi = kBfW1 + (i - kOffW1);
+    else if (i >= kOffW2 && i < kOffB2) bi = kBfW2 + (i - kOffW2);
+    else if (i >= kOffW3 && i < kOffB3) bi = kBfW3 + (i - kOffW3);
+    else if (i >= kOffW4 && i < kOffB4) bi = kBfW4 + (i - kOffW4);
+    if (bi >= 0) wbf[bi] = __float2bfloat16_rn(pi);
 }
 
 // ------------------------------------------------------------ launchers
@@ -520,7 +559,7 @@ void launch_grad_adam(const float* part, int n_part, const float* loss_part, flo
                       float lr, float b1, float b2, float eps, int step, FitSched fs,
                       cudaStream_t s) {
     const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
-    k_grad_adam<<<(kParamsPadded + 255) / 256, 256, 0, s>>>(part, n_part, loss_part, loss, grad,
+    k_grad_adam<<<(kParamsPadded + 31) / 32, 128, 0, s>>>(part, n_part, loss_part, loss, grad,
                                                             adam, p, m, v, wbf, lr, b1, b2, eps,
                                                             bc1, bc2, fs);
 }

@@ -58,7 +58,8 @@ struct TrainArgs {
     int mode;                  // 0: forward outputs; 1: loss and gradient partials
     const __nv_bfloat16* wbf;  // bf16 weight copies (kBfCount)
     const float* params;       // FP32 master parameters (biases read here)
-    float *ds1, *ds2, *ds3;    // [n][128] SiLU'(Z) of the hidden layers (mode 1)
+    float *ds1, *ds2, *ds3;    // SiLU'(Z) of the hidden layers (mode 1): per 128-row
+                               // tile a 128 x 128 block, column-major
     float* part;               // [grid][kParamsPadded] gradient partials (mode 1)
     float* loss_part;          // [grid] loss partials (mode 1)
     FitSched fs;

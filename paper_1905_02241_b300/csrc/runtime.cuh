@@ -126,7 +126,7 @@ struct nmodl_surrogate {
     float* params = nullptr;          // FP32 master, padded layout
     __nv_bfloat16* wbf = nullptr;     // bf16 weight copies
     float *grad = nullptr, *m = nullptr, *v = nullptr;
-    float *ds1 = nullptr, *ds2 = nullptr, *ds3 = nullptr;  // [max_batch][128] SiLU'(Z)
+    float *ds1 = nullptr, *ds2 = nullptr, *ds3 = nullptr;  // SiLU'(Z), whole 128-row tiles
     float *part = nullptr, *loss_part = nullptr, *loss = nullptr;
     int n_part_max = 0;                                     // CTAs of the training kernel
 };

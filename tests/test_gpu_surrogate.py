@@ -74,10 +74,10 @@ def test_forward_matches_oracle_and_bf16_emulation(S, ctx, orc):
     sur.close()
 
 
-def test_gradients_vs_oracle(S, ctx, orc):
+@pytest.mark.parametrize("n,max_batch", [(512, 1024), (400, 400)])  # whole / partial last tile
+def test_gradients_vs_oracle(S, ctx, orc, n, max_batch):
     Ws, bs = W.mlp_init(5, out_scale=1.0)
-    sur = S.Surrogate(ctx, max_batch=1024, weights=S.Surrogate.pack(Ws, bs))
-    n = 512
+    sur = S.Surrogate(ctx, max_batch=max_batch, weights=S.Surrogate.pack(Ws, bs))
     X = _inputs(orc, n, 4)
     T = np.sin(np.arange(9 * n)).reshape(n, 9).astype(np.float32) * 0.3
     loss, g = sur.loss_grad(to_dev(X), to_dev(T))

@@ -315,6 +315,10 @@ def test_network_fused_and_per_mechanism_paths_agree(api, orc, prec):
         for a, b in zip(sf, sg):
             if a.size:
                 assert np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-3)) <= 1e-4
+        # the ion currents (the fused MIXED form sums FP32 conductance
+        # factors, the launches FP64 conductances of the same states)
+        for a, b in zip(iof, iog):
+            assert np.max(np.abs(a - b)) <= 1e-4 * max(1.0, np.abs(b).max())
     cai = sf[-1][0]
     assert np.all(np.isfinite(cai)) and cai.min() >= 0
 

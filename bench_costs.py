@@ -205,3 +205,12 @@ MLP_FLOPS = 2 * (16 * 128 + 2 * 128 * 128 + 128 * 16)          # forward, padded
 # 128) and the four weight-gradient products D^T H
 TRAIN_FLOPS_PER_ROW = MLP_FLOPS + 2 * (16 * 128 + 2 * 128 * 128) + MLP_FLOPS
 SUR_MUFU = 3 * 128 + 2 * KIN9_EDGES      # SiLU tanh per hidden unit, exp2 per rate
+
+
+# FP64 warp instructions per step of one warp of the single-HH gate-warp
+# kernel (ncu on the 4,096-node HH workload: FP64 pipe 33 % active on the
+# SMs, three of whose four sub-partitions hold a gate warp, 2.24 us per
+# step at 2.03 GHz and one warp instruction per 68.6 clocks -> about 30;
+# the FP64 operations written in the kernel's source give 22-27 per gate
+# warp; the measured count is used)
+HH_WARP_FP64_PER_STEP = 30

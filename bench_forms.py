@@ -100,6 +100,18 @@ def hh(dev, peaks, n=4096, nsteps=1000, reps=3):
         out["roofline"]["occupied_sub_partitions"] = min(plan["tiles"], sms) * 3
         out["roofline"]["frac_of_occupied_sub_partitions"] = out["roofline"]["frac"] / busy
         out["ns_per_step"] = 1e9 * n / rate
+        # the floor of a latency-bound step: one warp's FP64 instructions
+        # per step, each holding its sub-partition's FP64 unit for one issue
+        # interval (32 lanes / the unit's lane rate, from the measured peak)
+        interval_ns = 1e9 * 32 * 4 * sms / peaks["fp64"]
+        floor_ns = C.HH_WARP_FP64_PER_STEP * interval_ns
+        out["latency_roofline"] = {
+            "bound": "fp64_issue_chain", "fp64_warp_instructions_per_step": C.HH_WARP_FP64_PER_STEP,
+            "fp64_issue_interval_ns": interval_ns, "floor_ns_per_step": floor_ns,
+            "ns_per_step": out["ns_per_step"], "frac": floor_ns / out["ns_per_step"],
+            "what": ("a step's floor: one gate warp's FP64 instructions per step (ncu) times "
+                     "the FP64 issue interval of a sub-partition (from the measured FP64 peak); "
+                     "the integer and FP32 parts of the chain come on top")}
     else:
         busy = min(plan["tiles"], sms) / sms
         out["roofline"]["frac_of_occupied_sms"] = out["roofline"]["frac"] / busy

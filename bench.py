@@ -42,8 +42,9 @@ fp64_ops_per_step = C.fp64_ops_per_step
 
 def bf16_peaks():
     """Measured dense bf16 tensor-core peaks (burst, sustained) in flop/s:
-    the generated MEASURED_PEAKS.json when present, else the fallback
-    figures of an earlier B300 measurement (1.8 and 1.4 PFLOP/s)."""
+    the cuBLAS bf16 GEMM peaks measured on this GPU type and stored in
+    MEASURED_PEAKS.json at the repository root when present, else the
+    fallback figures of an earlier B300 measurement (1.8 and 1.4 PFLOP/s)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         mp = json.load(open(path))

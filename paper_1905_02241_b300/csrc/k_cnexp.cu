@@ -1040,21 +1040,24 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
                     const uint16_t* cS = cE + NT;
                     const uint16_t* coff = cS + NT;
                     const uint16_t* clist = coff + NT + 1;
-                    // leaves -> roots by height: d2_s[i] := 1/d' of node i
-                    // and r2_s[i] := r'/d' once its children are eliminated
-                    // (the dependent chain per level: one multiply-add per
-                    // child and the reciprocal)
+                    // leaves -> roots by height: d2_s[i] := ga_i / d' of node
+                    // i (0 at roots) and r2_s[i] := r'/d' once its children
+                    // are eliminated; 1/d' is only ever needed times ga_i
+                    // (by the parent, d'_p -= gb_c (ga_c / d'_c), and by the
+                    // substitution), so each level's chain -- one warp, each
+                    // FP64 instruction a full issue slot -- has one
+                    // multiply-add per child, the reciprocal and two products
                     for (int h = 0; h < cH; ++h) {
                         for (int k = cEL[h] + tid; k < cEL[h + 1]; k += 32) {
                             const int i = cE[k];
                             double dd = d2_s[i], r = r2_s[i];
                             for (int q = coff[i]; q < coff[i + 1]; ++q) {
                                 const int c = clist[q];
-                                dd = fma(-(ga_s[c] * gb_s[c]), d2_s[c], dd);
+                                dd = fma(-gb_s[c], d2_s[c], dd);
                                 r = fma(gb_s[c], r2_s[c], r);
                             }
                             const double inv = rcp_chain(dd);  // on the level chain: latency
-                            d2_s[i] = inv;
+                            d2_s[i] = (par_s[i] != 0xffff ? ga_s[i] : 0.0) * inv;
                             r2_s[i] = r * inv;
                         }
                         __syncwarp();
@@ -1065,7 +1068,7 @@ __global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
                         for (int k = cSL[l] + tid; k < cSL[l + 1]; k += 32) {
                             const int i = cS[k];
                             const int pp = par_s[i];
-                            if (pp != 0xffff) r2_s[i] = fma(ga_s[i] * d2_s[i], r2_s[pp], r2_s[i]);
+                            if (pp != 0xffff) r2_s[i] = fma(d2_s[i], r2_s[pp], r2_s[i]);
                         }
                         __syncwarp();
                     }

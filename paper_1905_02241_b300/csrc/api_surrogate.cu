@@ -49,10 +49,11 @@ void refresh_bf16(nmodl_surrogate* s) {
     launch_to_bf16(s->params + kOffW2, kHid * kHid, s->wbf + kBfW2, st);
     launch_to_bf16(s->params + kOffW3, kHid * kHid, s->wbf + kBfW3, st);
     launch_to_bf16(s->params + kOffW4, kOut * kHid, s->wbf + kBfW4, st);
+    launch_train_image(s->params, s->img, st);
 }
 
 void free_sur(nmodl_surrogate* s) {
-    void* ptrs[] = {s->params, s->wbf, s->grad, s->m, s->v, s->ds1, s->ds2, s->ds3, s->part,
+    void* ptrs[] = {s->params, s->wbf, s->img, s->grad, s->m, s->v, s->ds1, s->ds2, s->ds3, s->part,
                     s->loss_part, s->loss};
     for (void* p : ptrs) cudaFree(p);
     delete s;
@@ -62,8 +63,7 @@ TrainArgs train_args(nmodl_surrogate* s, int64_t n, const float* X, int* grid) {
     TrainArgs a{};
     a.X = X;
     a.n = n;
-    a.wbf = s->wbf;
-    a.params = s->params;
+    a.img = s->img;
     a.ds1 = s->ds1;
     a.ds2 = s->ds2;
     a.ds3 = s->ds3;
@@ -76,9 +76,12 @@ TrainArgs train_args(nmodl_surrogate* s, int64_t n, const float* X, int* grid) {
 
 // Loss and gradient partials of one batch (the fused tensor-core kernel),
 // then their sum into s->grad (adam = 0) or the Adam step on the master
-// parameters and their bf16 copies (adam = 1); s->loss receives the loss.
+// parameters, their bf16 copies and the weight image (adam = 1); s->loss
+// receives the loss (in a replayed run also loss_steps[step], and the step
+// index advances: done is the zeroed arrival counter of that).
 cudaError_t loss_and_grad(nmodl_surrogate* s, int64_t n, const float* X, const float* T,
-                          int adam, float lr, FitSched fs = FitSched{}) {
+                          int adam, float lr, FitSched fs = FitSched{},
+                          float* loss_steps = nullptr, unsigned int* done = nullptr) {
     cudaStream_t st = s->ctx->stream;
     int grid = 0;
     TrainArgs a = train_args(s, n, X, &grid);
@@ -88,7 +91,7 @@ cudaError_t loss_and_grad(nmodl_surrogate* s, int64_t n, const float* X, const f
     cudaError_t e = launch_train_tiles(a, grid, st);
     if (e != cudaSuccess) return e;
     launch_grad_adam(s->part, grid, s->loss_part, s->loss, s->grad, adam, s->params, s->m, s->v,
-                     s->wbf, lr, 0.9f, 0.999f, 1e-8f, s->step, fs, st);
+                     s->wbf, s->img, lr, 0.9f, 0.999f, 1e-8f, s->step, fs, loss_steps, done, st);
     return cudaGetLastError();
 }
 
@@ -115,6 +118,7 @@ NMODL_API int nmodl_surrogate_create(nmodl_ctx* c, int64_t max_batch, const floa
     do {
         if ((e = dalloc(&s->params, kParamsPadded)) != cudaSuccess) break;
         if ((e = dalloc(&s->wbf, kBfCount)) != cudaSuccess) break;
+        if ((e = dalloc(&s->img, kTrImgBytes)) != cudaSuccess) break;
         if ((e = dalloc(&s->grad, kParamsPadded)) != cudaSuccess) break;
         if ((e = dalloc(&s->m, kParamsPadded)) != cudaSuccess) break;
         if ((e = dalloc(&s->v, kParamsPadded)) != cudaSuccess) break;
@@ -237,15 +241,15 @@ NMODL_API int nmodl_surrogate_fit(nmodl_surrogate* s, int64_t n, const float* X,
     DeviceGuard dg(c->device);
     cudaStream_t st = c->stream;
     const int64_t spe = n / batch, total = spe * (int64_t)epochs;
+    // the run's step index, then the arrival counter of the kernel that
+    // advances it
     int64_t* d_step = nullptr;
-    cudaError_t e = dalloc(&d_step, 1);
+    cudaError_t e = dalloc(&d_step, 2);
     if (e != cudaSuccess) return nmodl_cuda_status(e);
-    e = cudaMemsetAsync(d_step, 0, sizeof(int64_t), st);
+    e = cudaMemsetAsync(d_step, 0, 2 * sizeof(int64_t), st);
+    unsigned int* d_done = reinterpret_cast<unsigned int*>(d_step + 1);
     FitSched fs{d_step, spe, total, lr, lr_min, s->step, 1};
-    auto one_step = [&]() {
-        loss_and_grad(s, batch, X, T, 1, lr, fs);
-        launch_fit_end(loss_steps, s->loss, fs, st);
-    };
+    auto one_step = [&]() { loss_and_grad(s, batch, X, T, 1, lr, fs, loss_steps, d_done); };
     // graphs of kSteps optimiser steps (the step index lives on the device,
     // so one graph serves every group), then one of the remaining steps: a
     // graph launch per 16 steps instead of one per step

@@ -12,10 +12,13 @@
 //   loss      e = OUT - T, loss += e^2, D4 = e / n                 (bf16)
 //   backward  D3 = (D4 W4) * SiLU'(Z3), D2 = (D3 W3) * SiLU'(Z2),
 //             D1 = (D2 W2) * SiLU'(Z1)                            (bf16)
-//   gradients dW4^T += H3^T D4, dW3 += D3^T H2, dW2 += D2^T H1,
+//   gradients dW4^T += H3^T D4, dW3^T += H2^T D3, dW2^T += H1^T D2,
 //             dW1 += D1^T H0, db2, db3 += D^T 1 (db1 comes with dW1 through
 //             H0's column of ones; db4 as column sums on the CUDA cores)
-// The same shared-memory image serves both orientations: an activation
+// The weights, the bias pairs and the column of ones arrive as one image
+// (kept in global memory in the shared-memory layout by the optimiser step)
+// in four bulk copies on the copy engine, waited for only before the first
+// MMA.  The same shared-memory image serves both orientations: an activation
 // tile stored K-major for the forward product (K = features) is read
 // MN-major by the gradient products, whose contraction runs over the 128
 // rows of the tile; a weight image stored K-major for the forward (K = in)
@@ -23,7 +26,7 @@
 // accumulators stay in tensor memory over all tiles of the CTA and are
 // written once per CTA; k_grad_adam sums the CTA partials in a fixed order
 // (deterministic), then either stores the gradient or takes the Adam step
-// (Kingma & Ba 2015) and refreshes the bf16 weight copies.
+// (Kingma & Ba 2015) and refreshes the bf16 weight copies and the image.
 // Every mbarrier wait is bounded; a timeout is latched as
 // NMODL_ERR_TIMEOUT and the CTA stops.
 #include "kernels.cuh"
@@ -33,24 +36,34 @@
 namespace nmodl {
 
 namespace {
-constexpr int kTrThreads = 256;  // two warpgroups
-constexpr int kTrRows = 128;     // rows per tile (MMA M)
+constexpr int kTrGroups = 2;                  // warpgroups
+constexpr int kTrThreads = 128 * kTrGroups;
+constexpr int kTrRows = 128;                  // rows per tile (MMA M)
+constexpr int kTrCols = 128 / kTrGroups;      // hidden columns per warpgroup
+static_assert(kTrCols % 16 == 0, "epilogue chunks of 16 columns");
 // shared-memory images (K-major core matrices, umma_offset), bytes
 constexpr int kImW1 = kHid * kIn * 2, kImWH = kHid * kHid * 2, kImW4 = kOut * kHid * 2;
 constexpr int kImH0 = kTrRows * kIn * 2, kImH = kTrRows * kHid * 2, kImD4 = kTrRows * kOut * 2;
 constexpr int kImOne = kTrRows * 16 * 2, kImBH = kHid * 16 * 2, kImB4 = kOut * 16 * 2;
+// the weight image (the first kImg bytes, as kept in global memory), then
+// the activation images; every MMA operand starts on a 1024-byte boundary
 constexpr int sW1 = 0, sW2 = sW1 + kImW1, sW3 = sW2 + kImWH, sW4 = sW3 + kImWH;
-constexpr int sH0 = sW4 + kImW4, sH1 = sH0 + kImH0, sH2 = sH1 + kImH, sH3 = sH2 + kImH;
-constexpr int sD4 = sH3 + kImH, sOne = sD4 + kImD4, sB2 = sOne + kImOne, sB3 = sB2 + kImBH;
-constexpr int sB4 = sB3 + kImBH;
-constexpr int sRed = sB4 + kImB4;        // float [4 warps][16]: per-warp column sums
+constexpr int sOne = sW4 + kImW4, sB2 = sOne + kImOne, sB3 = sB2 + kImBH, sB4 = sB3 + kImBH;
+constexpr int kImg = sB4 + kImB4;
+constexpr int kImgChunk = kImg / 4;  // four bulk copies
+static_assert(kImg == kTrImgBytes && kImgChunk % 16 == 0, "weight image");
+constexpr int sH0 = (kImg + 1023) / 1024 * 1024, sH1 = sH0 + kImH0, sH2 = sH1 + kImH;
+constexpr int sH3 = sH2 + kImH, sD4 = sH3 + kImH;
+static_assert(sB4 % 1024 == 0 && sH1 % 1024 == 0 && sD4 % 1024 == 0, "operand alignment");
+constexpr int sRed = sD4 + kImD4;        // float [4 warps][16]: per-warp column sums
 constexpr int sAcc = sRed + 4 * 16 * 4;  // float [16]: db4 (0..8) and sum e^2 (9) of the CTA
-constexpr int sBar = sAcc + 16 * 4;
-constexpr int kTrSmem = sBar + 16;
+constexpr int sBar = sAcc + 16 * 4;      // two mbarriers, the tensor-memory address
+constexpr int kTrSmem = sBar + 32;
 static_assert(sBar % 8 == 0, "mbarrier alignment");
 static_assert(kTrSmem <= 227 * 1024, "shared memory per block");
 // tensor-memory columns: the working accumulator, then the gradient
-// accumulators that live across the CTA's tiles
+// accumulators that live across the CTA's tiles (dW2, dW3 transposed: lane
+// = input unit, column = output unit)
 constexpr uint32_t cAcc = 0, cDW2 = 128, cDW3 = 256, cDW1 = 384, cDW4T = 400, cDB2 = 416,
                    cDB3 = 432;
 constexpr uint32_t kTrTmemCols = 512;
@@ -66,6 +79,55 @@ __host__ __device__ constexpr uint32_t tr_idesc(uint32_t N, bool a_mn, bool b_mn
 // read K-major (K = its columns; LBO 128 B between core matrices along K,
 // SBO 16 F B between 8-row groups) or MN-major (K = its rows: core matrices
 // 16 F B apart along K, 128 B apart along MN).
+// The weight image entries of master parameter i (value x): a weight's bf16
+// value at its place in its K-major image (W1's padding columns 11..15 are
+// skipped: 11, 12 hold b1); a bias as the bf16 pair hi + lo, hi = bf16(x),
+// lo = bf16(x - hi), in the two columns that meet the ones (W1's columns
+// 11, 12 for b1; columns 0, 1 of the B2, B3, B4 images).
+__device__ __forceinline__ void img_put(unsigned char* img, int i, float x) {
+    auto put = [&](int off, int r, int k, int K, float y) {
+        *reinterpret_cast<__nv_bfloat16*>(img + off + umma_offset(r, k, K)) = __float2bfloat16_rn(y);
+    };
+    auto pair = [&](int off, int r, int k, int K) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        put(off, r, k, K, x);
+        put(off, r, k + 1, K, x - __bfloat162float(hi));
+    };
+    if (i < kOffB1) {
+        const int o = (i - kOffW1) / kIn, k = (i - kOffW1) % kIn;
+        if (k < kInRaw) put(sW1, o, k, kIn, x);
+    } else if (i < kOffW2) {
+        pair(sW1, i - kOffB1, kInRaw, kIn);
+    } else if (i < kOffB2) {
+        put(sW2, (i - kOffW2) / kHid, (i - kOffW2) % kHid, kHid, x);
+    } else if (i < kOffW3) {
+        pair(sB2, i - kOffB2, 0, 16);
+    } else if (i < kOffB3) {
+        put(sW3, (i - kOffW3) / kHid, (i - kOffW3) % kHid, kHid, x);
+    } else if (i < kOffW4) {
+        pair(sB3, i - kOffB3, 0, 16);
+    } else if (i < kOffB4) {
+        put(sW4, (i - kOffW4) / kHid, (i - kOffW4) % kHid, kHid, x);
+    } else if (i < kParamsPadded) {
+        pair(sB4, i - kOffB4, 0, 16);
+    }
+}
+
+// The whole image from the master parameters (img zeroed beforehand): every
+// parameter's entries, and the ones of the ONE image's columns 0, 1.
+__global__ void k_train_image(const float* __restrict__ p, unsigned char* img) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kParamsPadded + 2 * kTrRows;
+         i += gridDim.x * blockDim.x) {
+        if (i < kParamsPadded) {
+            img_put(img, i, p[i]);
+        } else {
+            const int j = i - kParamsPadded;
+            *reinterpret_cast<__nv_bfloat16*>(img + sOne + umma_offset(j / 2, j % 2, 16)) =
+                __float2bfloat16_rn(1.f);
+        }
+    }
+}
+
 __device__ __forceinline__ uint64_t desc_k(uint32_t a, int F) { return umma_desc(a, 128, 16 * F); }
 __device__ __forceinline__ uint64_t desc_mn(uint32_t a, int F) { return umma_desc(a, 16 * F, 128); }
 
@@ -87,15 +149,26 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const uint32_t sb = smem_u32(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sBar);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + sBar + 8);
+    uint64_t* bar_w = bar + 1;  // the weight image's bulk copies
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + sBar + 16);
     float* red = reinterpret_cast<float*>(smem + sRed);
     float* accs = reinterpret_cast<float*>(smem + sAcc);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int t = tid & 127;  // row of the tile (tensor-memory lane)
-    const int h = tid >> 7;   // warpgroup: columns [64 h, 64 h + 64) of the hidden layers
+    const int h = tid >> 7;   // warpgroup: hidden columns [kTrCols h, kTrCols (h + 1))
     const int n = (int)a.n;
     const float inv_n = 1.0f / (float)n;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar_w, 1);
+        mbar_init_fence();
+    }
+    if (tid < 16) accs[tid] = 0.f;
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, kTrTmemCols);
+        tmem_relinquish();
+    }
     const float* X = a.X;
     const float* T = a.T;
     if (a.fs.active) {
@@ -103,57 +176,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
         X += o * kInRaw;
         T += o * kOutRaw;
     }
-
-    // ---- stage the weights (bf16 copies, row-major) as K-major images
-    // (cp.async: every 16-byte piece in flight at once, no registers held;
-    // the copies overlap the zero fill below and are waited for before the
-    // bias pairs are written)
-    auto stage = [&](const __nv_bfloat16* src, int off, int rows, int K) {
-        const int ch = K / 8, total = rows * ch;
-        for (int c = tid; c < total; c += kTrThreads) {
-            const uint32_t dst = sb + off + umma_offset(c / ch, (c % ch) * 8, K);
-            const __nv_bfloat16* g = src + (c / ch) * K + (c % ch) * 8;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(g) : "memory");
-        }
-    };
-    stage(a.wbf + kBfW1, sW1, kHid, kIn);
-    stage(a.wbf + kBfW2, sW2, kHid, kHid);
-    stage(a.wbf + kBfW3, sW3, kHid, kHid);
-    stage(a.wbf + kBfW4, sW4, kOut, kHid);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    auto put = [&](int off, int r, int k, int K, float x) {
-        *reinterpret_cast<__nv_bfloat16*>(smem + off + umma_offset(r, k, K)) = __float2bfloat16_rn(x);
-    };
-    // bias as a bf16 pair hi + lo in columns k, k + 1
-    auto put_pair = [&](int off, int r, int k, int K, float b) {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(b);
-        put(off, r, k, K, b);
-        put(off, r, k + 1, K, b - __bfloat162float(hi));
-    };
-    // ONE and the bias images (contiguous from sOne): zeros by 16-byte
-    // stores, then the ones of ONE's columns 0, 1
-    static_assert(sB2 == sOne + kImOne && sB3 == sB2 + kImBH && sB4 == sB3 + kImBH &&
-                  (sB4 + kImB4 - sOne) % 16 == 0 && sOne % 16 == 0, "contiguous bias images");
-    for (int i = tid; i < (sB4 + kImB4 - sOne) / 16; i += kTrThreads)
-        *reinterpret_cast<uint4*>(smem + sOne + 16 * i) = make_uint4(0u, 0u, 0u, 0u);
-    if (tid < 16) accs[tid] = 0.f;
-    // every weight piece landed (W1's bias columns below share its pieces)
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
-    for (int i = tid; i < kTrRows * 2; i += kTrThreads) put(sOne, i / 2, i % 2, 16, 1.f);
-    for (int i = tid; i < kHid; i += kTrThreads) {
-        put_pair(sW1, i, kInRaw, kIn, a.params[kOffB1 + i]);  // W1 columns 11, 12
-        put_pair(sB2, i, 0, 16, a.params[kOffB2 + i]);
-        put_pair(sB3, i, 0, 16, a.params[kOffB3 + i]);
-    }
-    if (tid < kOutRaw) put_pair(sB4, tid, 0, 16, a.params[kOffB4 + tid]);
+    // ---- the weight image: four bulk copies, in flight during the setup
+    // and the first tile's input stage
     if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_init_fence();
-    }
-    if (warp == 0) {
-        tmem_alloc(tmem_slot, kTrTmemCols);
-        tmem_relinquish();
+        mbar_expect_tx(bar_w, kImg);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bulk_g2s(sb + c * kImgChunk, a.img + c * kImgChunk, kImgChunk, bar_w);
     }
     fence_proxy_async_smem();
     tc_fence_before();
@@ -162,7 +190,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
     const uint32_t tmem = *tmem_slot;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
     uint32_t phase = 0;
-    bool timed_out = false;
+    bool timed_out = false, w_ready = false;
 
     // operands in shared memory written, earlier tensor-memory reads done
     auto publish = [&]() {
@@ -205,6 +233,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
                                pack_bf16(f[8 * q + 4], f[8 * q + 5]), pack_bf16(f[8 * q + 6], f[8 * q + 7]));
         }
         publish();
+        if (!w_ready) {  // the weight image landed (the MMA issuer waits)
+            const bool bad = tid == 0 && !mbar_wait(bar_w, 0, kTrPolls);
+            w_ready = true;
+            if (__syncthreads_or(bad)) { timed_out = true; break; }
+        }
         // ---- forward: hidden layers
         for (int l = 1; l <= 3 && !timed_out; ++l) {
             const int hin = l == 1 ? sH0 : l == 2 ? sH1 : sH2;
@@ -224,15 +257,15 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
             }
             if (!commit_wait()) { timed_out = true; break; }
             float* ds = l == 1 ? a.ds1 : l == 2 ? a.ds2 : a.ds3;
-            // the 64 columns in four chunks, each chunk's tensor-memory read
-            // issued before the previous chunk's arithmetic
+            // this warpgroup's columns in chunks of 16, each chunk's
+            // tensor-memory read issued before the previous chunk's arithmetic
             uint32_t rb[2][16];
-            tmem_ld16(lane_base + cAcc + 64 * h, rb[0]);
+            tmem_ld16(lane_base + cAcc + kTrCols * h, rb[0]);
 #pragma unroll
-            for (int cb = 0; cb < 64; cb += 16) {
-                const int c = 64 * h + cb;
+            for (int cb = 0; cb < kTrCols; cb += 16) {
+                const int c = kTrCols * h + cb;
                 tmem_ld_wait(rb[(cb >> 4) & 1]);
-                if (cb + 16 < 64) tmem_ld16(lane_base + cAcc + c + 16, rb[((cb >> 4) + 1) & 1]);
+                if (cb + 16 < kTrCols) tmem_ld16(lane_base + cAcc + c + 16, rb[((cb >> 4) + 1) & 1]);
                 const uint32_t* r = rb[(cb >> 4) & 1];
                 float sv[16], dv[16];
 #pragma unroll
@@ -313,15 +346,15 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
         }
         publish();
         if (tid <= kOutRaw) accs[tid] += ((red[tid] + red[16 + tid]) + red[32 + tid]) + red[48 + tid];
-        // this thread's 64 columns of SiLU'(Z_l) (stored by the forward pass),
+        // this thread's columns of SiLU'(Z_l) (stored by the forward pass),
         // loaded as one batch before the tensor-core wait that precedes
         // layer l's backward step, so that their latency hides under it
-        float4 dsv[16];
+        float4 dsv[kTrCols / 4];
         auto load_ds = [&](int l) {
             const float* ds = l == 1 ? a.ds1 : l == 2 ? a.ds2 : a.ds3;
-            const float* ip = ds + (row - t) * kHid + t + (int64_t)(64 * h) * kTrRows;
+            const float* ip = ds + (row - t) * kHid + t + (int64_t)(kTrCols * h) * kTrRows;
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+            for (int q = 0; q < kTrCols / 4; ++q)
                 dsv[q] = valid ? make_float4(ip[(4 * q) * kTrRows], ip[(4 * q + 1) * kTrRows],
                                              ip[(4 * q + 2) * kTrRows], ip[(4 * q + 3) * kTrRows])
                                : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -340,12 +373,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
         for (int l = 3; l >= 1 && !timed_out; --l) {
             const int dimg = l == 3 ? sH3 : l == 2 ? sH2 : sH1;
             uint32_t rb[2][16];
-            tmem_ld16(lane_base + cAcc + 64 * h, rb[0]);
+            tmem_ld16(lane_base + cAcc + kTrCols * h, rb[0]);
 #pragma unroll
-            for (int cb = 0; cb < 64; cb += 16) {
-                const int c = 64 * h + cb;
+            for (int cb = 0; cb < kTrCols; cb += 16) {
+                const int c = kTrCols * h + cb;
                 tmem_ld_wait(rb[(cb >> 4) & 1]);
-                if (cb + 16 < 64) tmem_ld16(lane_base + cAcc + c + 16, rb[((cb >> 4) + 1) & 1]);
+                if (cb + 16 < kTrCols) tmem_ld16(lane_base + cAcc + c + 16, rb[((cb >> 4) + 1) & 1]);
                 const uint32_t* r = rb[(cb >> 4) & 1];
                 float dv[16];
                 if (valid) {
@@ -375,7 +408,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
                     const int hprev = l == 3 ? sH2 : sH1;
                     const int wl = l == 3 ? sW3 : sW2;
                     const uint32_t cdw = l == 3 ? cDW3 : cDW2, cdb = l == 3 ? cDB3 : cDB2;
-                    mma_run(tmem + cdw, sb + dimg, kHid, true, sb + hprev, kHid, true, kTrRows / 16,
+                    mma_run(tmem + cdw, sb + hprev, kHid, true, sb + dimg, kHid, true, kTrRows / 16,
                             tr_idesc(kHid, true, true), !first);
                     mma_run(tmem + cdb, sb + dimg, kHid, true, sb + sOne, 16, true, kTrRows / 16,
                             tr_idesc(16, true, true), !first);
@@ -395,37 +428,24 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
     // ---- the CTA's gradient partials (every entry of the padded layout)
     if (a.mode == 1 && !timed_out) {
         float* P = a.part + (int64_t)blockIdx.x * kParamsPadded;
-        // dW2, dW3: each warp's 32 rows x 64 columns through shared memory
-        // (the H images are free now; rows padded to 68 floats), then out by
-        // rows, two 256-byte rows per store instruction, instead of one
-        // 16-byte piece of 32 rows 512 bytes apart per instruction
-        float* tb = reinterpret_cast<float*>(smem + sH1) + warp * (32 * 68);
-        auto dump = [&](uint32_t col, float* dst) {  // dst: this half's column 0 of the matrix
+        // dW2, dW3 from their transposed accumulators: thread t holds input
+        // unit t's gradients for this warpgroup's output units o, stored at
+        // o * kHid + t -- for each o a warp's store is 128 contiguous bytes
+        auto dump = [&](uint32_t col, float* dst) {  // dst: the matrix's entry (0, 0)
             uint32_t rb[2][16];
-            tmem_ld16(lane_base + col, rb[0]);
+            tmem_ld16(lane_base + col + kTrCols * h, rb[0]);
 #pragma unroll
-            for (int cb = 0; cb < 64; cb += 16) {
+            for (int cb = 0; cb < kTrCols; cb += 16) {
+                const int o = kTrCols * h + cb;
                 tmem_ld_wait(rb[(cb >> 4) & 1]);
-                if (cb + 16 < 64) tmem_ld16(lane_base + col + cb + 16, rb[((cb >> 4) + 1) & 1]);
+                if (cb + 16 < kTrCols) tmem_ld16(lane_base + col + o + 16, rb[((cb >> 4) + 1) & 1]);
                 const uint32_t* r = rb[(cb >> 4) & 1];
-                float4* o = reinterpret_cast<float4*>(tb + lane * 68 + cb);
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    o[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                       __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                for (int e = 0; e < 16; ++e) dst[(int64_t)(o + e) * kHid + t] = __uint_as_float(r[e]);
             }
-            __syncwarp();
-            const int rbase = 32 * (warp & 3);
-#pragma unroll 4
-            for (int k = 0; k < 16; ++k) {
-                const int rr = 2 * k + (lane >> 4), q = lane & 15;
-                *reinterpret_cast<float4*>(dst + (int64_t)(rbase + rr) * kHid + 4 * q) =
-                    *reinterpret_cast<const float4*>(tb + rr * 68 + 4 * q);
-            }
-            __syncwarp();
         };
-        dump(cDW2 + 64 * h, P + kOffW2 + 64 * h);
-        dump(cDW3 + 64 * h, P + kOffW3 + 64 * h);
+        dump(cDW2, P + kOffW2);
+        dump(cDW3, P + kOffW3);
         uint32_t r[16];
         if (h == 0) {
             tmem_ld16(lane_base + cDW1, r);
@@ -436,7 +456,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
             tmem_ld16(lane_base + cDB2, r);
             tmem_ld_wait();
             P[kOffB2 + t] = __uint_as_float(r[0]);
-        } else {
+        } else if (h == 1) {
             tmem_ld16(lane_base + cDW4T, r);  // row t = input feature, columns = outputs
             tmem_ld_wait();
 #pragma unroll
@@ -449,6 +469,9 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
         if (tid == 0) a.loss_part[blockIdx.x] = 0.5f * accs[kOutRaw] * inv_n;
     }
     if (timed_out && tid == 0) latch_error(a.err, NMODL_ERR_TIMEOUT);
+    // no bulk copy may still be writing this CTA's shared memory at exit
+    // (a CTA without tiles, or one whose wait gave up): wait again, bounded
+    if (tid == 0 && (!w_ready || timed_out)) mbar_wait(bar_w, 0, kTrPolls);
     // ---- release the tensor memory
     tc_fence_before();
     __syncthreads();
@@ -458,15 +481,19 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
     }
 }
 
-// grad[i] = sum over the CTA partials in a fixed order (below).  adam: then the Adam
-// step on the FP32 master parameter (learning rate and bias corrections from
-// the arguments, or from the run's step index when fs.active) and the bf16
-// copy of the weight matrices.  Block 0 also sums the loss partials.
+// grad[i] = sum over the CTA partials in a fixed order (below).  adam: then the
+// Adam step on the FP32 master parameter (learning rate and bias corrections
+// from the arguments, or from the run's step index when fs.active), the bf16
+// copy of the weight matrices and the weight image.  The first warp of block
+// 0 also sums the loss partials (each lane a fixed strided subset, then a
+// fixed butterfly) and, in a replayed run, records the loss; the last block
+// to finish advances the run's step index.
 __global__ void __launch_bounds__(128) k_grad_adam(const float* __restrict__ part, int n_part,
                             const float* __restrict__ loss_part, float* loss, float* grad,
                             int adam, float* p, float* m, float* v, __nv_bfloat16* wbf,
-                            float lr, float b1, float b2, float eps, float bc1, float bc2,
-                            FitSched fs) {
+                            unsigned char* img, float lr, float b1, float b2, float eps,
+                            float bc1, float bc2, FitSched fs, float* loss_steps,
+                            unsigned int* done) {
     // Sums over the CTA partials in launch order within each quarter of the
     // partials, loads in batches of 16 ahead of their additions; the four
     // warps of a block take the four quarters of the same 32 parameters
@@ -485,39 +512,68 @@ __global__ void __launch_bounds__(128) k_grad_adam(const float* __restrict__ par
         for (; c < c1; ++c) acc += base[(int64_t)c * stride];
         return acc;
     };
-    if (blockIdx.x == 0 && threadIdx.x == 0) *loss = sum_parts(loss_part, 1, 0, n_part);
+    const int lane = threadIdx.x & 31, q4 = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    const bool owner = q4 == 0 && i < kParamsPadded;
+    // the step index and this parameter's optimiser state first, so that
+    // their loads overlap the partial sums
+    const int64_t k_run = fs.active ? *fs.step : 0;
+    float p0 = 0.f, m0 = 0.f, v0 = 0.f;
+    if (adam && owner) {
+        p0 = p[i];
+        m0 = m[i];
+        v0 = v[i];
+    }
+    if (blockIdx.x == 0 && q4 == 0) {
+        float x = 0.f;
+        for (int c = lane; c < n_part; c += 32) x += loss_part[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) {
+            *loss = x;
+            if (fs.active && loss_steps) loss_steps[k_run] = x;
+        }
+    }
     if (adam && fs.active) {
-        const int64_t k = *fs.step;
         lr = fs.lr_min + 0.5f * (fs.lr0 - fs.lr_min) *
-                             (1.0f + cosf(3.14159265358979f * (float)k / (float)fs.total));
-        const float tt = (float)(fs.t0 + k + 1);
+                             (1.0f + cosf(3.14159265358979f * (float)k_run / (float)fs.total));
+        const float tt = (float)(fs.t0 + k_run + 1);
         bc1 = 1.f - powf(b1, tt);
         bc2 = 1.f - powf(b2, tt);
     }
-    const int lane = threadIdx.x & 31, q4 = threadIdx.x >> 5;
-    const int i = blockIdx.x * 32 + lane;
     const int per = (n_part + 3) / 4;
     const int c0 = min(n_part, q4 * per), c1 = min(n_part, c0 + per);
     qs[q4][lane] = i < kParamsPadded ? sum_parts(part + i, kParamsPadded, c0, c1) : 0.f;
     __syncthreads();
-    if (q4 != 0 || i >= kParamsPadded) return;
-    const float g = ((qs[0][lane] + qs[1][lane]) + qs[2][lane]) + qs[3][lane];
-    if (!adam) {
-        grad[i] = g;
-        return;
+    if (owner) {
+        const float g = ((qs[0][lane] + qs[1][lane]) + qs[2][lane]) + qs[3][lane];
+        if (!adam) {
+            grad[i] = g;
+        } else {
+            const float mi = b1 * m0 + (1.f - b1) * g;
+            const float vi = b2 * v0 + (1.f - b2) * g * g;
+            m[i] = mi;
+            v[i] = vi;
+            const float pi = p0 - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+            p[i] = pi;
+            int bi = -1;
+            if (i >= kOffW1 && i < kOffB1) bi = kBfW1 + (i - kOffW1);
+            else if (i >= kOffW2 && i < kOffB2) bi = kBfW2 + (i - kOffW2);
+            else if (i >= kOffW3 && i < kOffB3) bi = kBfW3 + (i - kOffW3);
+            else if (i >= kOffW4 && i < kOffB4) bi = kBfW4 + (i - kOffW4);
+            if (bi >= 0) wbf[bi] = __float2bfloat16_rn(pi);
+            img_put(img, i, pi);
+        }
     }
-    const float mi = b1 * m[i] + (1.f - b1) * g;
-    const float vi = b2 * v[i] + (1.f - b2) * g * g;
-    m[i] = mi;
-    v[i] = vi;
-    const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-    p[i] = pi;
-    int bi = -1;
-    if (i >= kOffW1 && i < kOffB1) bi = kBfW1 + (i - kOffW1);
-    else if (i >= kOffW2 && i < kOffB2) bi = kBfW2 + (i - kOffW2);
-    else if (i >= kOffW3 && i < kOffB3) bi = kBfW3 + (i - kOffW3);
-    else if (i >= kOffW4 && i < kOffB4) bi = kBfW4 + (i - kOffW4);
-    if (bi >= 0) wbf[bi] = __float2bfloat16_rn(pi);
+    // every thread of the block read the step index before the barrier
+    // above; the last block to arrive advances it for the next step
+    if (fs.active && done && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1u) == gridDim.x - 1) {
+            *done = 0u;
+            *fs.step = k_run + 1;
+        }
+    }
 }
 
 // ------------------------------------------------------------ launchers
@@ -556,12 +612,17 @@ cudaError_t launch_train_tiles(const TrainArgs& a, int grid, cudaStream_t s) {
 
 void launch_grad_adam(const float* part, int n_part, const float* loss_part, float* loss,
                       float* grad, int adam, float* p, float* m, float* v, __nv_bfloat16* wbf,
-                      float lr, float b1, float b2, float eps, int step, FitSched fs,
-                      cudaStream_t s) {
+                      unsigned char* img, float lr, float b1, float b2, float eps, int step,
+                      FitSched fs, float* loss_steps, unsigned int* done, cudaStream_t s) {
     const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
     k_grad_adam<<<(kParamsPadded + 31) / 32, 128, 0, s>>>(part, n_part, loss_part, loss, grad,
-                                                            adam, p, m, v, wbf, lr, b1, b2, eps,
-                                                            bc1, bc2, fs);
+                                                            adam, p, m, v, wbf, img, lr, b1, b2,
+                                                            eps, bc1, bc2, fs, loss_steps, done);
+}
+
+void launch_train_image(const float* params, unsigned char* img, cudaStream_t s) {
+    cudaMemsetAsync(img, 0, kImg, s);
+    k_train_image<<<(kParamsPadded + 2 * kTrRows + 255) / 256, 256, 0, s>>>(params, img);
 }
 
 }  // namespace nmodl

@@ -28,6 +28,13 @@ constexpr int kParamsPadded = kOffB4 + kOut;
 // bf16 copies of the weight matrices only: W1 | W2 | W3 | W4
 constexpr int kBfW1 = 0, kBfW2 = kBfW1 + kHid * kIn, kBfW3 = kBfW2 + kHid * kHid,
               kBfW4 = kBfW3 + kHid * kHid, kBfCount = kBfW4 + kOut * kHid;
+// The training kernel's weight image: the bf16 weights in the K-major
+// core-matrix layout of its shared memory (W1 with the bias pair of b1 in
+// columns 11, 12 | W2 | W3 | W4), then the column-of-ones image and the bias
+// pair images of b2, b3, b4; copied whole into shared memory at the start
+// of each training launch and kept current by the optimiser step.
+constexpr int kTrImgBytes = 2 * (kHid * kIn + 2 * kHid * kHid + kOut * kHid) +
+                            2 * (128 * 16 + 2 * kHid * 16 + kOut * 16);  // 86528
 // unpadded public layout (row-major [out][in] weights, then biases)
 constexpr int kParamsPublic = kHid * kInRaw + kHid + 2 * (kHid * kHid + kHid) +
                               kOutRaw * kHid + kOutRaw;  // 35721
@@ -56,8 +63,7 @@ struct TrainArgs {
     int64_t n;                 // rows of the batch
     int tiles_per_cta;         // 128-row tiles per CTA
     int mode;                  // 0: forward outputs; 1: loss and gradient partials
-    const __nv_bfloat16* wbf;  // bf16 weight copies (kBfCount)
-    const float* params;       // FP32 master parameters (biases read here)
+    const unsigned char* img;  // the weight image (kTrImgBytes, 16-byte aligned)
     float *ds1, *ds2, *ds3;    // SiLU'(Z) of the hidden layers (mode 1): per 128-row
                                // tile a 128 x 128 block, column-major
     float* part;               // [grid][kParamsPadded] gradient partials (mode 1)
@@ -73,14 +79,16 @@ int train_max_grid(int64_t max_batch);
 cudaError_t launch_train_tiles(const TrainArgs& a, int grid, cudaStream_t s);
 // gradient = fixed-order sum of the n_part CTA partials; adam: then the
 // Adam step (lr and the bias corrections of step `step`, or from fs when
-// active) on the master parameters and the bf16 copies; *loss = the sum of
-// the loss partials
+// active) on the master parameters, the bf16 copies and the weight image;
+// *loss = the sum of the loss partials.  With fs active and loss_steps
+// given, the loss is also recorded at loss_steps[*fs.step] and the last
+// block to finish advances *fs.step (done: a zeroed arrival counter).
 void launch_grad_adam(const float* part, int n_part, const float* loss_part, float* loss,
                       float* grad, int adam, float* p, float* m, float* v, __nv_bfloat16* wbf,
-                      float lr, float b1, float b2, float eps, int step, FitSched fs,
-                      cudaStream_t s);
-// loss_steps[step] = *loss; ++step (the last kernel of a captured step)
-void launch_fit_end(float* loss_steps, const float* loss, FitSched fs, cudaStream_t s);
+                      unsigned char* img, float lr, float b1, float b2, float eps, int step,
+                      FitSched fs, float* loss_steps, unsigned int* done, cudaStream_t s);
+// the whole weight image from the FP32 master parameters
+void launch_train_image(const float* params, unsigned char* img, cudaStream_t s);
 void launch_to_bf16(const float* src, int64_t count, __nv_bfloat16* dst, cudaStream_t s);
 
 // surrogate state update (fused MLP + projection + residual + fallback list)

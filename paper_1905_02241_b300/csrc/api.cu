@@ -876,9 +876,11 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     else budgets = {std::min<size_t>(cap, 96 * 1024)};
     size_t items = 0;
     for (int t = 0; t < T; ++t) items += (size_t)gates[t] * mechs[t]->n;
-    const int max_block = kin ? kFusedKinBlock : kFusedMaxBlock;
+    // (the 9-state variant: blocks up to 256 run its register-rich build,
+    // larger ones its 768-thread build)
+    const int max_block = kin ? kFusedKinWideBlock : kFusedMaxBlock;
     if (c->opt.block > 0) blocks = {std::min(c->opt.block, max_block)};
-    else if (tune) blocks = kin ? std::vector<int>{128, 256} : std::vector<int>{128, 256, 512, 1024};
+    else if (tune) blocks = kin ? std::vector<int>{128, 256, 512, 768} : std::vector<int>{128, 256, 512, 1024};
     else blocks = {256};
     pers = tune ? std::vector<bool>{false, true} : std::vector<bool>{false};
 

@@ -335,15 +335,25 @@ __device__ void block_inclusive_scan_u16(uint16_t* a, int n, int* wsum) {
 // elimination (1984; no fill because parents precede children) scheduled by
 // levels.  v += the solution.  On the last step of the window rhs and d
 // report the assembled system.
-// The KIN variant in MIXED is compiled for two 256-thread blocks per SM
-// (128 registers; the FP32 solve spills a few hundred bytes): its cnexp
-// items then run at 16 warps per SM instead of 8 (measured 1.13x on the
-// cortical mix with the 9-state scheme on a quarter of 1M nodes).  The FP64
-// variant keeps one block (~245 registers): its spilled FP64 solve lost
-// more (0.90x) than the occupancy gained.
-template <int PREC, bool EXT, bool KIN>
-__global__ void __launch_bounds__(KIN ? kFusedKinBlock : kFusedMaxBlock,
-                                  (KIN && PREC == NMODL_MIXED) ? 2 : 1)
+// The KIN variant (the 9-state scheme) has two builds.  KIN == 1: blocks of
+// at most 256 threads, the banded solve in registers (~245 in FP64, one
+// block per SM; MIXED two blocks per SM at 128 registers, the FP32 solve
+// spilling a few hundred bytes) -- best for lists of the 9-state scheme
+// alone.  KIN == 2: one 768-thread block per SM at 80 registers, the solve
+// keeping part of its state in local memory (about 1 KB per thread, served
+// by L1), so that cnexp items of the same tile run at 24 warps per SM
+// instead of 8 or 16.  Measured on the cortical mix with the 9-state scheme
+// on a quarter of 1M nodes, FP64 instance-steps/s by block (registers): 256
+// (244) 7.07e9, 384 (168) 7.66e9, 512 (128) 8.13e9, 768 (80) 8.53e9, 1024
+// (64) 8.49e9; MIXED: 2 x 256 (128) 1.91e10, 512 2.03e10, 768 2.05e10,
+// 1024 1.92e10.  On the 9-state scheme alone (1M clamped instances, FP64)
+// the 768-thread build loses (it and the per-mechanism launches 1.07e9 vs
+// 1.15e9).  The autotuner times block sizes of both builds.
+template <int PREC, bool EXT, int KIN>
+__global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
+                                  : KIN == 1 ? kFusedKinBlock
+                                             : kFusedKinWideBlock,
+                                  (KIN == 1 && PREC == NMODL_MIXED) ? 2 : 1)
     k_fused_tiles(FusedArgs A) {
     static_assert(!KIN || EXT, "the 9-state scheme comes with the extended variant");
     // MIXED on isolated compartments: each gate update writes its
@@ -1313,23 +1323,25 @@ void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
 // grid = blocks of this launch (one per tile, or the resident count in the
 // persistent form)
 // variant = precision + 2 * ext + 2 * kin: ext instantiates the kernel with
-// the small systems and ion sums (EXT); kin adds the 9-state scheme (KIN);
-// plain HH/CNEXP plans use the leanest variant
+// the small systems and ion sums (EXT); kin adds the 9-state scheme (KIN),
+// whose build follows the block size; plain HH/CNEXP plans use the leanest
+// variant
 using FusedKernel = void (*)(FusedArgs);
-static FusedKernel fused_kernel(int variant) {
+static FusedKernel fused_kernel(int variant, int block) {
+    const bool wide = block > kFusedKinBlock;
     switch (variant) {
-    case 0: return k_fused_tiles<NMODL_FP64, false, false>;
-    case 1: return k_fused_tiles<NMODL_MIXED, false, false>;
-    case 2: return k_fused_tiles<NMODL_FP64, true, false>;
-    case 3: return k_fused_tiles<NMODL_MIXED, true, false>;
-    case 4: return k_fused_tiles<NMODL_FP64, true, true>;
-    default: return k_fused_tiles<NMODL_MIXED, true, true>;
+    case 0: return k_fused_tiles<NMODL_FP64, false, 0>;
+    case 1: return k_fused_tiles<NMODL_MIXED, false, 0>;
+    case 2: return k_fused_tiles<NMODL_FP64, true, 0>;
+    case 3: return k_fused_tiles<NMODL_MIXED, true, 0>;
+    case 4: return wide ? k_fused_tiles<NMODL_FP64, true, 2> : k_fused_tiles<NMODL_FP64, true, 1>;
+    default: return wide ? k_fused_tiles<NMODL_MIXED, true, 2> : k_fused_tiles<NMODL_MIXED, true, 1>;
     }
 }
 
 cudaError_t launch_fused(int variant, const FusedArgs& a, int grid, int block, size_t smem,
                          cudaStream_t s) {
-    fused_kernel(variant)<<<grid, block, smem, s>>>(a);
+    fused_kernel(variant, block)<<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1337,19 +1349,29 @@ int fused_resident_grid(int variant, int n_tiles, int block, size_t smem) {
     int dev = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel(variant), block, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel(variant, block), block,
+                                                  smem);
     return std::min(n_tiles, std::max(1, per_sm) * sms);
 }
 
+// both builds of a 9-state variant (block sizes below and above kFusedKinBlock)
 cudaError_t fused_prepare(int variant, size_t max_smem) {
-    return cudaFuncSetAttribute(fused_kernel(variant),
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    cudaError_t e = cudaSuccess;
+    for (int block : {kFusedKinBlock, kFusedKinWideBlock})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fused_kernel(variant, block),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    return e;
 }
 
 size_t fused_static_smem(int variant) {
-    cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, fused_kernel(variant));
-    return fa.sharedSizeBytes;
+    size_t s = 0;
+    for (int block : {kFusedKinBlock, kFusedKinWideBlock}) {
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, fused_kernel(variant, block));
+        s = std::max(s, fa.sharedSizeBytes);
+    }
+    return s;
 }
 
 }  // namespace nmodl

@@ -8,9 +8,13 @@
 namespace nmodl {
 
 constexpr int kFusedMaxBlock = 1024;
-// block limit of the fused variant with the 9-state scheme (its banded
-// Newton solve holds ~200 registers per thread)
+// the fused variant with the 9-state scheme comes in two builds, picked by
+// the block size of the launch: blocks of at most kFusedKinBlock threads
+// run the register-rich build (the banded Newton solve in ~245 registers;
+// MIXED two blocks per SM), larger blocks (up to kFusedKinWideBlock) the
+// one compiled for a single 768-thread block per SM (80 registers)
 constexpr int kFusedKinBlock = 256;
+constexpr int kFusedKinWideBlock = 768;
 
 // node-major slots per instance of the fused step's flat layout: one
 // (e, g) per current (HH: sodium, potassium, leak; the calcium buffer none)
@@ -76,7 +80,8 @@ void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
                     double* ion_a, double* ion_b, int32_t* err, cudaStream_t s);
 // variant = precision + 2 * ext + 2 * kin (ext: the kernel instantiated with
 // the small systems KIN3 / CACUM and the ion sums; kin: ext and the 9-state
-// scheme, variants 4 and 5, blocks of at most kFusedKinBlock)
+// scheme, variants 4 and 5, blocks of at most kFusedKinWideBlock, the build
+// chosen by the block size)
 cudaError_t launch_fused(int variant, const FusedArgs& a, int grid, int block,
                          size_t smem, cudaStream_t s);
 int fused_resident_grid(int variant, int n_tiles, int block, size_t smem);

@@ -4,7 +4,9 @@ launch per window (the KIN variant of the tile kernel, one thread per
 9-state instance running its banded Newton solve).  Checked against the
 FP64 oracle (one step at 1e-12, a 45-step trajectory across several windows
 at 1e-9), against the per-mechanism launch sequence of the same list, in
-mixed precision, with ion arrays, and in the cable form."""
+mixed precision, with ion arrays, and in the cable form; both builds of the
+variant (blocks of at most 256 threads: the solve in registers; larger
+blocks: the 768-thread build with part of the solve in local memory)."""
 import numpy as np
 import pytest
 
@@ -60,12 +62,14 @@ def _run(api, orc, wl, steps, ions=False, **opt):
     return out
 
 
-def test_fused_one_step_and_trajectory_fp64(api, orc):
+@pytest.mark.parametrize("block", [256, 768])
+def test_fused_one_step_and_trajectory_fp64(api, orc, block):
     wl = _network(6000, seed=41)
     n = wl["n_nodes"]
     for steps, tol in ((1, TOL_FP64), (45, 1e-9)):
-        got = _run(api, orc, wl, steps, tile_smem=24 * 1024, window=7)
+        got = _run(api, orc, wl, steps, tile_smem=24 * 1024, window=7, block=block)
         assert got["plan"]["fused"] and got["plan"]["tiles"] > 20
+        assert got["plan"]["block"] == block
         v_ref, r_ref, d_ref, s_ref = orc.step(wl["mechs"], got["st0"], wl["v0"], n, 0.025,
                                               nsteps=steps)
         assert np.max(np.abs(got["v"] - v_ref) / np.maximum(np.abs(v_ref), 1.0)) <= tol
@@ -78,9 +82,10 @@ def test_fused_one_step_and_trajectory_fp64(api, orc):
                 assert state_err(g, s) <= tol, steps
 
 
-def test_fused_matches_the_per_mechanism_sequence(api, orc):
+@pytest.mark.parametrize("block", [128, 512])
+def test_fused_matches_the_per_mechanism_sequence(api, orc, block):
     wl = _network(3000, seed=42, frac=0.6)
-    a = _run(api, orc, wl, 10, window=4, tile_smem=24 * 1024)  # fused (fixed tiles)
+    a = _run(api, orc, wl, 10, window=4, tile_smem=24 * 1024, block=block)  # fused (fixed tiles)
     b = _run(api, orc, wl, 10, window=4, no_fuse=1)
     assert a["plan"]["fused"] and not b["plan"]["fused"]
     assert np.max(np.abs(a["v"] - b["v"]) / np.maximum(np.abs(b["v"]), 1.0)) <= 1e-12
@@ -90,11 +95,12 @@ def test_fused_matches_the_per_mechanism_sequence(api, orc):
             assert state_err(x, y) <= 1e-12
 
 
-def test_fused_mixed_precision(api, orc):
+@pytest.mark.parametrize("block", [256, 768])
+def test_fused_mixed_precision(api, orc, block):
     wl = _network(4000, seed=43)
     n = wl["n_nodes"]
-    got = _run(api, orc, wl, 20, precision=api.NMODL_MIXED, tile_smem=32 * 1024)
-    assert got["plan"]["fused"]
+    got = _run(api, orc, wl, 20, precision=api.NMODL_MIXED, tile_smem=32 * 1024, block=block)
+    assert got["plan"]["fused"] and got["plan"]["block"] == block
     v_ref, _, _, s_ref = orc.step(wl["mechs"], got["st0"], wl["v0"], n, 0.025, nsteps=20)
     assert np.max(np.abs(got["v"] - v_ref)) <= 1e-3
     for g, s in zip(got["states"], s_ref):

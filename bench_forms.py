@@ -611,6 +611,30 @@ def hh_case(dev=0, n=4096, nsteps=200):
     ctx.close()
 
 
+def ions_case(dev=0, n_nodes=1_000_000, windows=3):
+    """Profiling case of the fused tile kernel's extended variant: the
+    ion-tagged cortical mix (10 cnexp types writing ina/ik/ica, the 3-state
+    scheme on half of the nodes, a calcium buffer per node) with ion arrays,
+    FP64, autotuned on the first window, then `windows` timed windows of 40
+    steps (one launch each).  Prints the plan and instance-steps/s."""
+    wl = W.cortical_ions(n_nodes, seed=8)
+    ctx = Context(dev)
+    dv = f"cuda:{dev}"
+    v = torch.tensor(wl["v0"], device=dv)
+    arrs = [torch.zeros_like(v) for _ in range(3)]
+    ctx.set_ions(*arrs)
+    mechs = _ion_mechs(ctx, wl)
+    rhs, d = torch.zeros_like(v), torch.zeros_like(v)
+    for m in mechs:
+        m.init(v)
+    ctx.step(mechs, DT, CM, v, rhs, d, 40)
+    ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, 40 * windows), ctx, 1)
+    print({"plan": ctx.plan(mechs), "instance_steps_per_s": _ninst(wl) * 40 * windows / (ms * 1e-3)})
+    for m in mechs:
+        m.close()
+    ctx.close()
+
+
 def training_case(dev=0, n_pairs=1 << 20, epochs=2, batch=8192):
     """Profiling case of the fused tensor-core training kernel: n_pairs
     FP64 Newton pairs of the 9-state scheme, `epochs` passes in minibatches

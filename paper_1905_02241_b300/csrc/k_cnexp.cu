@@ -703,8 +703,10 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
         __syncthreads();
     } else {
         // Node-major slots: node n owns slots [eoff[n], eoff[n+1]), its
-        // instances in mechanism order, then ascending instance; one slot
-        // (e, g) per current (HH: three), e written here once per window.
+        // instances in mechanism order, then ascending instance -- with ion
+        // arrays the calcium-tagged currents after all others, so that the
+        // owner sums them in a loop of their own; one slot (e, g) per
+        // current (HH: three), e written here once per window.
         for (int n = tid; n < NT; n += blockDim.x) {
             int c = 0;
             for (int t = 0; t < T; ++t) {
@@ -719,8 +721,13 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
         block_inclusive_scan_u16(eoff_s + 1, NT, scan_s);
         for (int n = tid; n < NT; n += blockDim.x) {
             int o = eoff_s[n];
+            const int passes = (EXT && A.ions) ? 2 : 1;
+            for (int pass = 0; pass < passes; ++pass)
             for (int t = 0; t < T; ++t) {
                 const MechD& M = md_s[t];
+                if (EXT && A.ions &&
+                    (pass == 1) != (M.kind != NMODL_HH && M.ion == NMODL_ION_CA))
+                    continue;
                 const uint16_t* nid = nid_s + nid_off[t];
                 const int hi = lower_bound_u16(nid, cnt_s[t], n + 1);
                 for (int j = lower_bound_u16(nid, cnt_s[t], n); j < hi; ++j) {
@@ -910,7 +917,8 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
             __syncthreads();
         }
         // ---- current update and v update, one owner thread per node; the
-        // terms are summed in mechanism order, then ascending instance.
+        // terms are summed in mechanism order, then ascending instance (with
+        // ion arrays the calcium-tagged currents apart, added last).
         for (int p = tid; p < NT; p += blockDim.x) {
             const int n = flat ? (int)perm_s[p] : p;
             const double vv = v_s[n];
@@ -932,18 +940,27 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                         e = eg.x;
                     }
                 };
-                for (int sl = s0; sl < s1; ++sl) {
+                // with ion arrays the calcium slots sit last: calcium every
+                // step (the buffer reads it), in a loop of its own, then
+                // added to the node's sums
+                int sc = s1;
+                if (EXT && A.ions)
+                    while (sc > s0 && tag_s[sc - 1] == NMODL_ION_CA) --sc;
+                for (int sl = s0; sl < sc; ++sl) {
                     double g, e;
                     slot_ge(sl, g, e);
                     X = fma(g, e, X);
                     G += g;
-                    if (EXT && A.ions) {
-                        // calcium every step (the buffer reads it), without a
-                        // branch: sum(g e) and sum(g) over the calcium slots
-                        const double gc = tag_s[sl] == NMODL_ION_CA ? g : 0.0;
-                        Xca = fma(gc, e, Xca);
-                        Gca += gc;
+                }
+                if (EXT && A.ions) {
+                    for (int sl = sc; sl < s1; ++sl) {
+                        double g, e;
+                        slot_ge(sl, g, e);
+                        Xca = fma(g, e, Xca);
+                        Gca += g;
                     }
+                    X += Xca;
+                    G += Gca;
                 }
                 r = fma(-vv, G, X);  // -sum g (v - e)
                 dd = G;

@@ -115,14 +115,15 @@ __device__ __forceinline__ int kin9_newton_d(const double (&dk_f)[kKinEdges],
             r[edge_lo(e)] += dk_b[e] * y[edge_hi(e)];
         }
         kin9_lu_band_solve(M, r);
-        double dmax = 0.0;
+        // max|delta| and its test on the integer pipe
+        unsigned long long dmax = 0;
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
             y[a] += r[a];
-            dmax = fmax(dmax, fabs(r[a]));
+            dmax = absmax_bits(dmax, r[a]);
         }
         ++iters;
-        if (dmax <= tol) break;
+        if (bits_le(dmax, tol)) break;
         if (iters == max_iter) nonconv = true;
     }
     return iters;
@@ -185,7 +186,7 @@ __device__ __forceinline__ int kin9_refine_mixed(const float (&dk_f)[kKinEdges],
             dmax = fmaxf(dmax, fabsf(rf[a]));
         }
         ++iters;
-        if (f2d_int(dmax) <= tol) break;
+        if (abs_le_int(f2d_int(dmax), tol)) break;
         if (iters == cap) nonconv = true;
     }
     return iters;

@@ -365,6 +365,26 @@ __device__ __forceinline__ bool finite_int(double x) {
     return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
 }
 
+// |x| <= t on the integer pipe (an FP64 comparison or max would take an
+// FP64 pipe slot): for non-negative doubles the order of the values is the
+// order of their bit patterns as unsigned integers.  A NaN |x| lies above
+// every finite pattern and infinity, so it compares false, as the FP64
+// comparison does; a negative t admits nothing.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+}
+__device__ __forceinline__ bool bits_le(unsigned long long a, double t) {
+    const unsigned long long tb = (unsigned long long)__double_as_longlong(t);
+    return (tb >> 63) == 0 && a <= tb;
+}
+__device__ __forceinline__ bool abs_le_int(double x, double t) { return bits_le(abs_bits(x), t); }
+// running maximum of magnitudes kept as a bit pattern; a NaN x leaves it
+// unchanged, as fmax does
+__device__ __forceinline__ unsigned long long absmax_bits(unsigned long long m, double x) {
+    const unsigned long long b = abs_bits(x);
+    return (b > m && b <= 0x7ff0000000000000ULL) ? b : m;
+}
+
 // -x by flipping the sign bit on the integer pipe: a negated argument that
 // goes on to the integer steps of exp_tang / one_pm_exp has to exist in a
 // register, and an FP64 negation there would take an FP64 pipe slot.

@@ -98,7 +98,7 @@ __device__ __forceinline__ int cacum_newton_d(const CacumD& C, double ica, doubl
         y0 += d0;
         y1 += d1;
         ++it;
-        if (fabs(d0) <= tol && fabs(d1) <= tol) {
+        if (abs_le_int(d0, tol) && abs_le_int(d1, tol)) {  // integer pipe
             conv = true;
             break;
         }
@@ -169,7 +169,7 @@ __device__ __forceinline__ int kin3_step_mixed(const Kin3F& K, float vf, float d
             dmax = fmaxf(dmax, fabsf(r[a]));
         }
         ++iters;
-        done = f2d_int(dmax) <= tol;
+        done = abs_le_int(f2d_int(dmax), tol);
     }
     nonconv = !done && ir_max > 0;
 #pragma unroll
@@ -233,7 +233,7 @@ __device__ __forceinline__ int cacum_newton_mixed(const CacumD& C, const CacumF&
         y0 += f2d_int(d0);
         y1 += f2d_int(d1);
         ++it;
-        if (f2d_int(fabsf(d0)) <= tol && f2d_int(fabsf(d1)) <= tol) {
+        if (abs_le_int(f2d_int(d0), tol) && abs_le_int(f2d_int(d1), tol)) {
             conv = true;
             break;
         }

@@ -123,11 +123,11 @@ NMODL_API int nmodl_surrogate_create(nmodl_ctx* c, int64_t max_batch, const floa
         if ((e = dalloc(&s->m, kParamsPadded)) != cudaSuccess) break;
         if ((e = dalloc(&s->v, kParamsPadded)) != cudaSuccess) break;
         // whole 128-row tiles: the training kernel stores each tile's block
-        // column-major, a partial last tile included
+        // (FP16 column pairs), a partial last tile included
         const int64_t Bt = (B + 127) / 128 * 128;
-        if ((e = dalloc(&s->ds1, Bt * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->ds2, Bt * kHid)) != cudaSuccess) break;
-        if ((e = dalloc(&s->ds3, Bt * kHid)) != cudaSuccess) break;
+        if ((e = dalloc(&s->ds1, Bt * kHid / 2)) != cudaSuccess) break;
+        if ((e = dalloc(&s->ds2, Bt * kHid / 2)) != cudaSuccess) break;
+        if ((e = dalloc(&s->ds3, Bt * kHid / 2)) != cudaSuccess) break;
         if ((e = dalloc(&s->part, (int64_t)s->n_part_max * kParamsPadded)) != cudaSuccess) break;
         if ((e = dalloc(&s->loss_part, s->n_part_max)) != cudaSuccess) break;
         if ((e = dalloc(&s->loss, 1)) != cudaSuccess) break;

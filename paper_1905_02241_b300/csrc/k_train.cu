@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
                 }
             }
             if (!commit_wait()) { timed_out = true; break; }
-            float* ds = l == 1 ? a.ds1 : l == 2 ? a.ds2 : a.ds3;
+            __half2* ds = l == 1 ? a.ds1 : l == 2 ? a.ds2 : a.ds3;
             // this warpgroup's columns in chunks of 16, each chunk's
             // tensor-memory read issued before the previous chunk's arithmetic
             uint32_t rb[2][16];
@@ -282,12 +282,15 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
                                    pack_bf16(sv[8 * q + 4], sv[8 * q + 5]),
                                    pack_bf16(sv[8 * q + 6], sv[8 * q + 7]));
                 if (a.mode == 1 && valid) {
-                    // the tile's SiLU' block column-major (column c of the
-                    // tile's 128 rows contiguous): a warp's store of one
-                    // column is 128 contiguous bytes
-                    float* o = ds + (row - t) * kHid + t;
+                    // the tile's SiLU' block as FP16 column pairs (pair (c,
+                    // c + 1) of the tile's 128 rows contiguous): a warp's
+                    // store of one pair is 128 contiguous bytes.  FP16 keeps
+                    // SiLU' to 2^-11 relative, finer than the bf16 rounding
+                    // of the delta it scales.
+                    __half2* o = ds + (row - t) * (kHid / 2) + t;
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) o[(c + e) * kTrRows] = dv[e];
+                    for (int e = 0; e < 16; e += 2)
+                        o[((c + e) / 2) * kTrRows] = __floats2half2_rn(dv[e], dv[e + 1]);
                 }
             }
             publish();
@@ -349,15 +352,13 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
         // this thread's columns of SiLU'(Z_l) (stored by the forward pass),
         // loaded as one batch before the tensor-core wait that precedes
         // layer l's backward step, so that their latency hides under it
-        float4 dsv[kTrCols / 4];
+        __half2 dsv[kTrCols / 2];
         auto load_ds = [&](int l) {
-            const float* ds = l == 1 ? a.ds1 : l == 2 ? a.ds2 : a.ds3;
-            const float* ip = ds + (row - t) * kHid + t + (int64_t)(kTrCols * h) * kTrRows;
+            const __half2* ds = l == 1 ? a.ds1 : l == 2 ? a.ds2 : a.ds3;
+            const __half2* ip = ds + (row - t) * (kHid / 2) + t + (int64_t)(kTrCols * h / 2) * kTrRows;
 #pragma unroll
-            for (int q = 0; q < kTrCols / 4; ++q)
-                dsv[q] = valid ? make_float4(ip[(4 * q) * kTrRows], ip[(4 * q + 1) * kTrRows],
-                                             ip[(4 * q + 2) * kTrRows], ip[(4 * q + 3) * kTrRows])
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = 0; q < kTrCols / 2; ++q)
+                dsv[q] = valid ? ip[q * kTrRows] : __floats2half2_rn(0.f, 0.f);
         };
         // ---- backward through the output layer: dW4^T += H3^T D4, G3 = D4 W4
         if (tid == 0) {
@@ -383,12 +384,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
                 float dv[16];
                 if (valid) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 w = dsv[cb / 4 + q];
-                        dv[4 * q] = __uint_as_float(r[4 * q]) * w.x;
-                        dv[4 * q + 1] = __uint_as_float(r[4 * q + 1]) * w.y;
-                        dv[4 * q + 2] = __uint_as_float(r[4 * q + 2]) * w.z;
-                        dv[4 * q + 3] = __uint_as_float(r[4 * q + 3]) * w.w;
+                    for (int q = 0; q < 8; ++q) {
+                        const float2 w = __half22float2(dsv[cb / 2 + q]);
+                        dv[2 * q] = __uint_as_float(r[2 * q]) * w.x;
+                        dv[2 * q + 1] = __uint_as_float(r[2 * q + 1]) * w.y;
                     }
                 } else {
 #pragma unroll

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "bf16_util.cuh"
 #include "nmodl_internal.cuh"
@@ -64,8 +65,9 @@ struct TrainArgs {
     int tiles_per_cta;         // 128-row tiles per CTA
     int mode;                  // 0: forward outputs; 1: loss and gradient partials
     const unsigned char* img;  // the weight image (kTrImgBytes, 16-byte aligned)
-    float *ds1, *ds2, *ds3;    // SiLU'(Z) of the hidden layers (mode 1): per 128-row
-                               // tile a 128 x 128 block, column-major
+    __half2 *ds1, *ds2, *ds3;  // SiLU'(Z) of the hidden layers (mode 1) in FP16, per 128-row
+                               // tile a block of 64 column pairs x 128 rows (pair
+                               // (c, c + 1) of row t at 128 (c / 2) + t)
     float* part;               // [grid][kParamsPadded] gradient partials (mode 1)
     float* loss_part;          // [grid] loss partials (mode 1)
     FitSched fs;

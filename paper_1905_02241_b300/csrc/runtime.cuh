@@ -127,7 +127,7 @@ struct nmodl_surrogate {
     __nv_bfloat16* wbf = nullptr;     // bf16 weight copies
     unsigned char* img = nullptr;     // the training kernel's weight image (kTrImgBytes)
     float *grad = nullptr, *m = nullptr, *v = nullptr;
-    float *ds1 = nullptr, *ds2 = nullptr, *ds3 = nullptr;  // SiLU'(Z), whole 128-row tiles
+    __half2 *ds1 = nullptr, *ds2 = nullptr, *ds3 = nullptr;  // SiLU'(Z), whole 128-row tiles
     float *part = nullptr, *loss_part = nullptr, *loss = nullptr;
     int n_part_max = 0;                                     // CTAs of the training kernel
 };

@@ -446,8 +446,8 @@ NMODL_API int nmodl_mech_attach_surrogate(nmodl_mech *m, nmodl_surrogate *s,
  * 1 MiB device array that every GPU which loads the library holds until the
  * process exits; n_instances above nmodl_cur_noalloc_max_instances()
  * (8,000,000) is rejected with NMODL_ERR_TOO_LARGE.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) --
- * make that first call before any stream capture.  The call validates
+ * device looks up that array's device address (cudaGetSymbolAddress).
+ * The call validates
  * node_index and waits for that check on the stream (NMODL_ERR_UNSORTED /
  * NMODL_ERR_RANGE), then runs the reduction and waits for it too: it
  * returns once rhs and d are written, with NMODL_ERR_NONFINITE if any rhs

@@ -11,7 +11,9 @@
 //             through the MMAs as bf16 hi/lo pairs against columns of ones)
 //   loss      e = OUT - T, loss += e^2, D4 = e / n                 (bf16)
 //   backward  D3 = (D4 W4) * SiLU'(Z3), D2 = (D3 W3) * SiLU'(Z2),
-//             D1 = (D2 W2) * SiLU'(Z1)                            (bf16)
+//             D1 = (D2 W2) * SiLU'(Z1)                            (bf16;
+//             SiLU'(Z) kept by the forward pass in a global scratch in
+//             FP16, 2^-11 relative, below the bf16 rounding of D)
 //   gradients dW4^T += H3^T D4, dW3^T += H2^T D3, dW2^T += H1^T D2,
 //             dW1 += D1^T H0, db2, db3 += D^T 1 (db1 comes with dW1 through
 //             H0's column of ones; db4 as column sums on the CUDA cores)

@@ -387,6 +387,7 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
     __shared__ int wstart_s[kMaxMechsFused * kMaxGates + 1];
     __shared__ int wkey[kMaxMechsFused * kMaxGates];
     __shared__ int n_work;
+    __shared__ int wctr_s;  // KIN: the next work slot of the state phase
     __shared__ float phidt_f[kMaxMechsFused];
     // MIXED: FP32 copies of the current parameters (gbar, e, HH g[3], e[3]),
     // converted once rather than per instance (FP64 -> FP32 conversions run
@@ -533,15 +534,19 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
         // Work order of the FP64 state phase: the gates grouped by their pair
         // of rate forms (each pair of forms is one straight-line body), each
         // group padded to whole warps so that no warp runs two bodies; the
-        // coupled small systems (one item per instance) last.  (MIXED, whose
-        // FP32 bodies are cheap and issue-bound, keeps the storage order.)
+        // coupled systems one item per instance: the 9-state solve (about 13
+        // gate updates' worth) first, since with it the warps take the work
+        // in chunks as they come free, the 3-state solve and the buffer's
+        // Newton last.  (MIXED, whose FP32 bodies are cheap and
+        // issue-bound, keeps the storage order unless the 9-state scheme
+        // is in the list.)
         int nw = 0;
         for (int p = 0; p < q; ++p) {
             const int t = pair_t[p], g = pair_g[p], kind = md_s[t].kind;
             int key;
             if (EXT && (kind == NMODL_KIN3 || kind == NMODL_CACUM || (KIN && kind == NMODL_KIN9))) {
                 if (g != 0) continue;
-                key = kind == NMODL_KIN3 ? 9 : kind == NMODL_CACUM ? 10 : 11;
+                key = kind == NMODL_KIN3 ? 9 : kind == NMODL_CACUM ? 10 : -1;
             } else {
                 key = md_s[t].gate[g].aform * 3 + md_s[t].gate[g].bform;
             }
@@ -1056,6 +1061,7 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
             v_s[n] = vn;
             if (PREC == NMODL_MIXED) vf_s[n] = d2f_int(vn);
         }
+        if (KIN && tid == 0) wctr_s = 0;  // the state phase's work counter
         __syncthreads();
         if (A.cable) {
             if (!A.clamp_v) {
@@ -1235,8 +1241,7 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
             // work order (slots past a pair's count are a group's padding;
             // with the 9-state scheme MIXED takes it too, so that its one item
             // per instance does not leave eight of nine lanes idle)
-            int wi = 0;
-            for (int w = tid; w < wstart_s[n_work]; w += blockDim.x) {
+            auto work = [&](int w, int& wi) {
                 while (w >= wstart_s[wi + 1]) ++wi;
                 const int q = wq_s[wi];
                 const int t = pair_t[q], j = w - wstart_s[wi];
@@ -1244,6 +1249,28 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                     item(pair_start[q] + j, t, pair_g[q], j);
                     if (FAC) put_factor(q, j, st_f[pair_start[q] + j].x);
                 }
+            };
+            int wi = 0;
+            if constexpr (KIN != 0) {
+                // warps take whole-warp chunks of work slots (groups are
+                // padded to whole warps) from a counter as they come free:
+                // the 9-state solves, first in the order, run beside the
+                // gate updates instead of as a tail that leaves the rest of
+                // the block idle (measured on the cortical mix with the
+                // 9-state scheme on a quarter of 1M nodes: FP64 8.54e9 ->
+                // 9.0e9, MIXED 2.05e10 -> 2.41e10; on the ion network with
+                // the lighter 3-state and buffer solves the fixed order was
+                // 3 % faster, so only this variant takes it)
+                const int lane = tid & 31;
+                for (;;) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&wctr_s, 32);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (base >= wstart_s[n_work]) break;
+                    work(base + lane, wi);
+                }
+            } else {
+                for (int w = tid; w < wstart_s[n_work]; w += blockDim.x) work(w, wi);
             }
         } else {
             // storage order (one group: the bodies are cheap and issue-bound)

@@ -635,6 +635,31 @@ def ions_case(dev=0, n_nodes=1_000_000, windows=3):
     ctx.close()
 
 
+def kin9_network_case(dev=0, n_nodes=1_000_000, windows=3, mixed=False, **opt):
+    """Profiling case of the fused tile kernel's 9-state variant: the
+    cortical mix on n_nodes with the 9-state scheme on a seeded 25 % of the
+    nodes (the kin9_network form's workload), a first window (autotuned
+    unless `opt` fixes the shape, e.g. autotune=0, tile_smem=216528,
+    block=768), then `windows` timed windows of 40 steps.  Prints the plan
+    and instance-steps/s."""
+    wl = W.cortical_mix(n_nodes, seed=2)
+    ni = np.nonzero(W.Stream(2, 901).uniform(n_nodes) < 0.25)[0].astype(np.int32)
+    wl["mechs"].append(dict(type=W.TYPE_KIN9, params=W.kin9_params(W.Stream(4, 401)),
+                            node_index=ni, name="kin9"))
+    ctx = Context(dev, precision=NMODL_MIXED if mixed else NMODL_FP64, **opt)
+    mechs = _mechs(ctx, wl)
+    v = torch.tensor(wl["v0"], device=f"cuda:{dev}")
+    rhs, d = torch.zeros_like(v), torch.zeros_like(v)
+    for m in mechs:
+        m.init(v)
+    ctx.step(mechs, DT, CM, v, rhs, d, 40)
+    ms = _time(lambda: ctx.step(mechs, DT, CM, v, rhs, d, 40 * windows), ctx, 1)
+    print({"plan": ctx.plan(mechs), "instance_steps_per_s": _ninst(wl) * 40 * windows / (ms * 1e-3)})
+    for m in mechs:
+        m.close()
+    ctx.close()
+
+
 def training_case(dev=0, n_pairs=1 << 20, epochs=2, batch=8192):
     """Profiling case of the fused tensor-core training kernel: n_pairs
     FP64 Newton pairs of the 9-state scheme, `epochs` passes in minibatches

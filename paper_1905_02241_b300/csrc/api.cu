@@ -878,9 +878,10 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     for (int t = 0; t < T; ++t) items += (size_t)gates[t] * mechs[t]->n;
     // (the 9-state variant: blocks up to 256 run its register-rich build,
     // larger ones its 768-thread build)
-    const int max_block = kin ? kFusedKinWideBlock : kFusedMaxBlock;
+    const int max_block = kin ? fused_kin_wide_block(p->precision) : kFusedMaxBlock;
     if (c->opt.block > 0) blocks = {std::min(c->opt.block, max_block)};
-    else if (tune) blocks = kin ? std::vector<int>{128, 256, 512, 768} : std::vector<int>{128, 256, 512, 1024};
+    else if (tune && kin) blocks = {128, 256, max_block == 768 ? 512 : 384, max_block};
+    else if (tune) blocks = {128, 256, 512, 1024};
     else blocks = {256};
     pers = tune ? std::vector<bool>{false, true} : std::vector<bool>{false};
 

@@ -352,7 +352,7 @@ __device__ void block_inclusive_scan_u16(uint16_t* a, int n, int* wsum) {
 template <int PREC, bool EXT, int KIN>
 __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                                   : KIN == 1 ? kFusedKinBlock
-                                             : kFusedKinWideBlock,
+                                             : fused_kin_wide_block(PREC),
                                   (KIN == 1 && PREC == NMODL_MIXED) ? 2 : 1)
     k_fused_tiles(FusedArgs A) {
     static_assert(!KIN || EXT, "the 9-state scheme comes with the extended variant");
@@ -1398,10 +1398,11 @@ int fused_resident_grid(int variant, int n_tiles, int block, size_t smem) {
     return std::min(n_tiles, std::max(1, per_sm) * sms);
 }
 
-// both builds of a 9-state variant (block sizes below and above kFusedKinBlock)
+// both builds of a 9-state variant (kFusedKinBlock and kFusedKinBlock + 32
+// stand for the block sizes of the register-rich and the wide build)
 cudaError_t fused_prepare(int variant, size_t max_smem) {
     cudaError_t e = cudaSuccess;
-    for (int block : {kFusedKinBlock, kFusedKinWideBlock})
+    for (int block : {kFusedKinBlock, kFusedKinBlock + 32})
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(fused_kernel(variant, block),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
@@ -1410,7 +1411,7 @@ cudaError_t fused_prepare(int variant, size_t max_smem) {
 
 size_t fused_static_smem(int variant) {
     size_t s = 0;
-    for (int block : {kFusedKinBlock, kFusedKinWideBlock}) {
+    for (int block : {kFusedKinBlock, kFusedKinBlock + 32}) {
         cudaFuncAttributes fa{};
         cudaFuncGetAttributes(&fa, fused_kernel(variant, block));
         s = std::max(s, fa.sharedSizeBytes);

@@ -11,10 +11,13 @@ constexpr int kFusedMaxBlock = 1024;
 // the fused variant with the 9-state scheme comes in two builds, picked by
 // the block size of the launch: blocks of at most kFusedKinBlock threads
 // run the register-rich build (the banded Newton solve in ~245 registers;
-// MIXED two blocks per SM), larger blocks (up to kFusedKinWideBlock) the
-// one compiled for a single 768-thread block per SM (80 registers)
+// MIXED two blocks per SM), larger blocks (up to fused_kin_wide_block) the
+// one compiled for a single such block per SM (FP64 768 threads at 80
+// registers, MIXED 512 at 128)
 constexpr int kFusedKinBlock = 256;
-constexpr int kFusedKinWideBlock = 768;
+__host__ __device__ constexpr int fused_kin_wide_block(int prec) {
+    return prec == NMODL_MIXED ? 512 : 768;
+}
 
 // node-major slots per instance of the fused step's flat layout: one
 // (e, g) per current (HH: sodium, potassium, leak; the calcium buffer none)
@@ -80,8 +83,8 @@ void launch_cur_seg(int kind, const void* desc, int64_t n_chunks,
                     double* ion_a, double* ion_b, int32_t* err, cudaStream_t s);
 // variant = precision + 2 * ext + 2 * kin (ext: the kernel instantiated with
 // the small systems KIN3 / CACUM and the ion sums; kin: ext and the 9-state
-// scheme, variants 4 and 5, blocks of at most kFusedKinWideBlock, the build
-// chosen by the block size)
+// scheme, variants 4 and 5, blocks of at most fused_kin_wide_block, the
+// build chosen by the block size)
 cudaError_t launch_fused(int variant, const FusedArgs& a, int grid, int block,
                          size_t smem, cudaStream_t s);
 int fused_resident_grid(int variant, int n_tiles, int block, size_t smem);

@@ -6,7 +6,8 @@ FP64 oracle (one step at 1e-12, a 45-step trajectory across several windows
 at 1e-9), against the per-mechanism launch sequence of the same list, in
 mixed precision, with ion arrays, and in the cable form; both builds of the
 variant (blocks of at most 256 threads: the solve in registers; larger
-blocks: the 768-thread build with part of the solve in local memory)."""
+blocks: the wide build, FP64 768 threads, MIXED 512, with part of the solve
+in local memory)."""
 import numpy as np
 import pytest
 
@@ -95,7 +96,7 @@ def test_fused_matches_the_per_mechanism_sequence(api, orc, block):
             assert state_err(x, y) <= 1e-12
 
 
-@pytest.mark.parametrize("block", [256, 768])
+@pytest.mark.parametrize("block", [256, 512])
 def test_fused_mixed_precision(api, orc, block):
     wl = _network(4000, seed=43)
     n = wl["n_nodes"]

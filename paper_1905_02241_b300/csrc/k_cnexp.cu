@@ -1115,6 +1115,19 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
             }
             __syncthreads();
         }
+        // MIXED gate update of item k: the increment f (minf - m) added to
+        // the hi/lo pair compensated
+        auto gate_update_f = [&](int k, float minf, float f) {
+            float2 m = st_f[k];
+            const float delta = f * ((minf - m.x) - m.y);
+            float s, e;
+            two_sum_f(m.x, delta, s, e);
+            const float lo = m.y + e;
+            const float hi2 = s + lo;
+            m.y = lo - (hi2 - s);
+            m.x = hi2;
+            st_f[k] = m;
+        };
         // ---- state update, one thread per (instance, gate) item k (storage
         // index) of gate g of type t, instance j
         auto item = [&](int k, int t, int g, int j) {
@@ -1226,15 +1239,7 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                 float minf, f;
                 gate_coef_f(gf_s[t][g], phidt_f[t], vf_s[nid_s[nid_off[t] + j]], minf, f,
                             A.pade != 0);
-                float2 m = st_f[k];
-                const float delta = f * ((minf - m.x) - m.y);
-                float s, e;
-                two_sum_f(m.x, delta, s, e);
-                const float lo = m.y + e;
-                const float hi2 = s + lo;
-                m.y = lo - (hi2 - s);
-                m.x = hi2;
-                st_f[k] = m;
+                gate_update_f(k, minf, f);
             }
         };
         if constexpr (PREC == NMODL_FP64 || KIN) {
@@ -1274,11 +1279,54 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
             }
         } else {
             // storage order (one group: the bodies are cheap and issue-bound)
-            int q = 0;
-            for (int k = tid; k < total_items; k += blockDim.x) {
-                while (k >= pair_start[q + 1]) ++q;
-                item(k, pair_t[q], pair_g[q], k - pair_start[q]);
-                if (FAC) put_factor(q, k - pair_start[q], st_f[k].x);
+            if constexpr (!EXT) {
+                // gates only: the constants of a thread's current gate pair
+                // (its FP32 rate parameters, phi dt, node-id and slot bases,
+                // factor multiplier, power and component) kept in registers
+                // and reloaded when its next item starts another pair, since
+                // a thread's items stay in one pair for several rounds
+                int q = -1, end = 0, base = 0, nb = 0, pw = 0, fx = 0;
+                float pdt = 0.f, fm = 1.f;
+                GateF G{};
+                const bool pade = A.pade != 0;
+                for (int k = tid; k < total_items; k += blockDim.x) {
+                    if (k >= end) {
+                        do {
+                            ++q;
+                        } while (k >= pair_start[q + 1]);
+                        base = pair_start[q];
+                        end = pair_start[q + 1];
+                        const int t = pair_t[q];
+                        G = gf_s[t][pair_g[q]];
+                        pdt = phidt_f[t];
+                        nb = nid_off[t];
+                        if (FAC) {
+                            fm = fmul_s[q];
+                            pw = fpow_s[q];
+                            fx = fidx_s[q];
+                        }
+                    }
+                    const int j = k - base;
+                    float minf, f;
+                    gate_coef_f(G, pdt, vf_s[nid_s[nb + j]], minf, f, pade);
+                    gate_update_f(k, minf, f);
+                    if (FAC) {  // the gate's conductance factor (put_factor)
+                        const float hi = st_f[k].x;
+                        float fv = fm;
+                        if (pw >= 1) fv *= hi;
+                        if (pw >= 2) fv *= hi;
+                        if (pw >= 3) fv *= hi;
+                        for (int e = 3; e < pw; ++e) fv *= hi;
+                        reinterpret_cast<float*>(f_s)[4 * pos_s[nb + j] + fx] = fv;
+                    }
+                }
+            } else {
+                int q = 0;
+                for (int k = tid; k < total_items; k += blockDim.x) {
+                    while (k >= pair_start[q + 1]) ++q;
+                    item(k, pair_t[q], pair_g[q], k - pair_start[q]);
+                    if (FAC) put_factor(q, k - pair_start[q], st_f[k].x);
+                }
             }
         }
         __syncthreads();

@@ -181,3 +181,38 @@ def test_autotuned_form_parity_and_counters(api, orc):
             assert state_err(g, s) <= 1e-9
     assert got["kin9_stats"]["newton_iters"] == ref_run["kin9_stats"]["newton_iters"]
     assert got["kin9_stats"]["newton_iters"] >= 2 * steps * wl["mechs"][-1]["node_index"].size
+
+
+@pytest.mark.parametrize("prec,block", [("fp64", 256), ("fp64", 768), ("mixed", 256), ("mixed", 512)])
+def test_two_kinetic_mechanisms_share_the_first_work_group(api, orc, prec, block):
+    """Two 9-state mechanisms (different rates, ragged counts: 0 to 2
+    instances per node, 731 and 1,266 instances) beside the cnexp mix: their
+    items form the one padded group at the head of the state phase's work
+    order that the warps take in chunks.  One step against the FP64 oracle
+    (FP64 at 1e-12; MIXED within the mixed form's state bound) and a 15-step
+    window against the per-mechanism launches."""
+    wl = _network(5003, seed=47, frac=0.15)
+    s2 = W.Stream(48, 902)
+    ni2 = np.sort(np.concatenate([np.nonzero(s2.uniform(5003) < 0.2)[0],
+                                  np.nonzero(s2.uniform(5003) < 0.06)[0]])).astype(np.int32)
+    wl["mechs"].append(dict(type=W.TYPE_KIN9, params=W.kin9_params(W.Stream(49, 401)),
+                            node_index=ni2, name="kin9b"))
+    n = wl["n_nodes"]
+    opt = dict(tile_smem=24 * 1024, block=block)
+    if prec == "mixed":
+        opt["precision"] = api.NMODL_MIXED
+    got = _run(api, orc, wl, 1, **opt)
+    assert got["plan"]["fused"] and got["plan"]["block"] == block and got["plan"]["tiles"] > 10
+    v_ref, _, _, s_ref = orc.step(wl["mechs"], got["st0"], wl["v0"], n, 0.025, nsteps=1)
+    v_tol, s_tol = (TOL_FP64, TOL_FP64) if prec == "fp64" else (1e-4, 1e-5)
+    assert np.max(np.abs(got["v"] - v_ref) / np.maximum(np.abs(v_ref), 1.0)) <= v_tol
+    for g, s in zip(got["states"], s_ref):
+        if g is not None:  # FP64 relative (state_err), MIXED absolute
+            err = state_err(g, s) if prec == "fp64" else np.max(np.abs(g - s))
+            assert err <= s_tol
+    a = _run(api, orc, wl, 15, window=5, **opt)
+    b_opt = {"precision": api.NMODL_MIXED} if prec == "mixed" else {}
+    b = _run(api, orc, wl, 15, window=5, no_fuse=1, **b_opt)
+    assert a["plan"]["fused"] and not b["plan"]["fused"]
+    rt = 1e-12 if prec == "fp64" else 1e-4
+    assert np.max(np.abs(a["v"] - b["v"]) / np.maximum(np.abs(b["v"]), 1.0)) <= rt

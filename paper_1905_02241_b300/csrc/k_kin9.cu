@@ -192,12 +192,19 @@ void launch_kin9_state(int prec, const Kin9D* kd, const Kin9D& kh, int64_t n, co
     if (work == 0) return;
     int grid = (int)((work + block - 1) / block);
     if (list) {
-        // the list's length is known on the device only: a resident grid
-        // (the kernel's ~200 registers allow a few 128-thread blocks per SM)
-        int dev = 0, sms = 148;
+        // the list's length is known on the device only: exactly the
+        // resident grid (one wave; its ~200 registers allow two or three
+        // 128-thread blocks per SM), each thread striding over the list
+        int dev = 0, sms = 148, per_sm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid = (int)std::min<int64_t>(grid, (int64_t)sms * 4);
+        if (prec == NMODL_FP64)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kin9_state<NMODL_FP64, true>,
+                                                          block, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kin9_state<NMODL_MIXED, true>,
+                                                          block, 0);
+        grid = (int)std::min<int64_t>(grid, (int64_t)sms * std::max(1, per_sm));
     }
     Kin9Launch KL;
     for (int e = 0; e < kKinEdges; ++e) {

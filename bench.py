@@ -54,6 +54,23 @@ def bf16_peaks():
         return 1.8e15, 1.4e15, "fallback (no measured peaks file)"
 
 
+def issue_peak(dev: int) -> float:
+    """Warp instructions per second the GPU can issue: one per cycle on each
+    of an SM's four sub-partitions, at the maximum SM clock nvidia-smi
+    reports (2,032 MHz on this GPU type if it cannot be read)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = 2032.0
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(dev), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True,
+                             text=True, timeout=20).stdout.strip()
+        mhz = float(out.splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        pass
+    return 4.0 * sms * mhz * 1e6
+
+
 def n_instances(wl) -> int:
     return int(sum(m["node_index"].size for m in wl["mechs"]))
 
@@ -347,7 +364,8 @@ def main():
         burst, sustained, src = bf16_peaks()
         peaks = {"fp64": peak, "fp32": _lib.nmodl_probe_peak(dev, 1),
                  "mufu_ex2": _lib.nmodl_probe_peak(dev, 2), "bf16_burst": burst,
-                 "bf16_sustained": sustained, "bf16_source": src}
+                 "bf16_sustained": sustained, "bf16_source": src,
+                 "issue": issue_peak(dev)}
         for name in want:
             t0 = time.perf_counter()
             forms[name] = getattr(F, name)(dev, peaks)

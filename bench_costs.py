@@ -214,3 +214,12 @@ SUR_MUFU = 3 * 128 + 2 * KIN9_EDGES      # SiLU tanh per hidden unit, exp2 per r
 # the FP64 operations written in the kernel's source give 22-27 per gate
 # warp; the measured count is used)
 HH_WARP_FP64_PER_STEP = 30
+
+# Warp instructions the mixed-precision fused step issues per instance-step
+# (measured, not modelled: ncu smsp__inst_executed.sum of one 40-step launch
+# on the 1,000,000-node cortical mix, 5,046,778,632 instructions over
+# 11,548,985 instances x 40 steps), for its issue-rate roofline: an SM
+# issues at most one warp instruction per cycle on each of its four
+# sub-partitions.
+MIXED_WARP_INSTR_PER_STEP = 5046778632 / (11548985 * 40)
+ISSUE_PER_SM_PER_CYCLE = 4

@@ -64,7 +64,8 @@ def _roof(count, rate, peak, pipe, unit="Tops/s", what=""):
     """count: operations per instance-step on the bounding unit; rate:
     instance-steps/s; peak: the unit's measured operations/s."""
     ach = count * rate
-    return {"bound": "tensor" if pipe.startswith("bf16") else "alu", "pipe": pipe,
+    bound = "tensor" if pipe.startswith("bf16") else "issue" if pipe == "issue" else "alu"
+    return {"bound": bound, "pipe": pipe,
             "ops_per_instance_step": count, "achieved": ach / 1e12, "peak": peak / 1e12,
             "unit": unit, "frac": ach / peak, "what": what}
 
@@ -154,6 +155,13 @@ def batched(dev, peaks, steps=2, nsteps=200, scale=1.0):
                                       "per instance-step, against the measured FP64 peak"))
     out["roofline_fp64"] = _roof(C.fp64_ops_per_step(wl) / ninst, out["fp64"], peaks["fp64"],
                                  "fp64", what="FP64 pipe instructions per instance-step")
+    if peaks.get("issue"):
+        out["roofline_mixed_issue"] = _roof(
+            C.MIXED_WARP_INSTR_PER_STEP, out["mixed"], peaks["issue"], "issue",
+            unit="T warp-instructions/s", what=(
+                "warp instructions issued per instance-step (measured by ncu on the 1M-node "
+                "mix), against the SM issue peak: 4 per cycle per SM at the maximum SM clock; "
+                "the mixed step has no pipe near its peak and is bound by issue and barriers"))
     for m in mechs:
         m.close()
     ctx.close()

@@ -213,6 +213,25 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
     const int tiles = (n + kTrRows - 1) / kTrRows;
     const int tile0 = blockIdx.x * a.tiles_per_cta;
     const int tile1 = min(tiles, tile0 + a.tiles_per_cta);
+    // the CTA's gradient partials (mode 1), every entry of the padded layout
+    float* P = a.part + (int64_t)blockIdx.x * kParamsPadded;
+    // dW2, dW3 from their transposed accumulators: thread t holds input
+    // unit t's gradients for this warpgroup's output units o, stored at
+    // o * kHid + t -- for each o a warp's store is 128 contiguous bytes
+    auto dump = [&](uint32_t col, float* dst) {  // dst: the matrix's entry (0, 0)
+        uint32_t rb[2][16];
+        tmem_ld16(lane_base + col + kTrCols * h, rb[0]);
+#pragma unroll
+        for (int cb = 0; cb < kTrCols; cb += 16) {
+            const int o = kTrCols * h + cb;
+            tmem_ld_wait(rb[(cb >> 4) & 1]);
+            if (cb + 16 < kTrCols) tmem_ld16(lane_base + col + o + 16, rb[((cb >> 4) + 1) & 1]);
+            const uint32_t* r = rb[(cb >> 4) & 1];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) dst[(int64_t)(o + e) * kHid + t] = __uint_as_float(r[e]);
+        }
+    };
+    bool dumped23 = false;
     for (int tile = tile0; tile < tile1 && !timed_out; ++tile) {
         const bool first = tile == tile0;
         const int64_t row = row_of(tile);
@@ -422,31 +441,27 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tiles(TrainArgs a) {
                 }
             }
             if (l > 1) load_ds(l - 1);
+            // the CTA's last tile: an accumulator that an earlier wait
+            // completed goes out while this step's MMAs run (dW3 at l = 2,
+            // dW2 at l = 1; their columns are not written here)
+            if (a.mode == 1 && tile + 1 == tile1 && l < 3) {
+                if (l == 2) {
+                    dump(cDW3, P + kOffW3);
+                } else {
+                    dump(cDW2, P + kOffW2);
+                    dumped23 = true;
+                }
+            }
             if (!commit_wait()) { timed_out = true; break; }
         }
     }
 
-    // ---- the CTA's gradient partials (every entry of the padded layout)
+    // ---- the rest of the CTA's gradient partials
     if (a.mode == 1 && !timed_out) {
-        float* P = a.part + (int64_t)blockIdx.x * kParamsPadded;
-        // dW2, dW3 from their transposed accumulators: thread t holds input
-        // unit t's gradients for this warpgroup's output units o, stored at
-        // o * kHid + t -- for each o a warp's store is 128 contiguous bytes
-        auto dump = [&](uint32_t col, float* dst) {  // dst: the matrix's entry (0, 0)
-            uint32_t rb[2][16];
-            tmem_ld16(lane_base + col + kTrCols * h, rb[0]);
-#pragma unroll
-            for (int cb = 0; cb < kTrCols; cb += 16) {
-                const int o = kTrCols * h + cb;
-                tmem_ld_wait(rb[(cb >> 4) & 1]);
-                if (cb + 16 < kTrCols) tmem_ld16(lane_base + col + o + 16, rb[((cb >> 4) + 1) & 1]);
-                const uint32_t* r = rb[(cb >> 4) & 1];
-#pragma unroll
-                for (int e = 0; e < 16; ++e) dst[(int64_t)(o + e) * kHid + t] = __uint_as_float(r[e]);
-            }
-        };
-        dump(cDW2, P + kOffW2);
-        dump(cDW3, P + kOffW3);
+        if (!dumped23) {  // (a CTA without a tile)
+            dump(cDW2, P + kOffW2);
+            dump(cDW3, P + kOffW3);
+        }
         uint32_t r[16];
         if (h == 0) {
             tmem_ld16(lane_base + cDW1, r);

@@ -1263,9 +1263,10 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                 // gate updates instead of as a tail that leaves the rest of
                 // the block idle (measured on the cortical mix with the
                 // 9-state scheme on a quarter of 1M nodes: FP64 8.54e9 ->
-                // 9.0e9, MIXED 2.05e10 -> 2.41e10; on the ion network with
-                // the lighter 3-state and buffer solves the fixed order was
-                // 3 % faster, so only this variant takes it)
+                // 9.0e9, MIXED 2.05e10 -> 2.41e10; on the ion network, whose
+                // 3-state and buffer solves are lighter, chunks from the
+                // counter were 3-5 % slower -- one shared atomic per 32
+                // cheap items -- so only this variant takes them)
                 const int lane = tid & 31;
                 for (;;) {
                     int base = 0;

@@ -144,7 +144,9 @@ typedef struct nmodl_options {
     int32_t clamp_v;         /* nmodl_step leaves v unchanged (0)            */
     int32_t tile_smem;       /* fused tile shared-memory budget, bytes (0 =
                                 chosen by the autotuner / default)          */
-    int32_t block;           /* fused kernel block size (0 = auto)           */
+    int32_t block;           /* fused kernel block size (0 = auto; at most
+                                1024, with NMODL_KIN9 in the list 768 in
+                                FP64 and 512 in MIXED, see nmodl_step)      */
     int32_t cnexp_pade;      /* 1: cnexp with exp(-x) replaced by its (1,1)
                                 Pade approximant (1 - x/2)/(1 + x/2), the
                                 cheaper form of Section 5.2; second order,
@@ -262,8 +264,12 @@ NMODL_API int nmodl_cur(nmodl_mech *m, const double *v, double *rhs, double *d);
  * per-mechanism launches.  For an FP64 list with NMODL_KIN9 on isolated
  * compartments, the autotuner (options.autotune, with options.tile_smem and
  * options.block 0) also times the per-mechanism sequence on scratch copies
- * and keeps it where it is faster (the fused variant holds one block per
- * SM there).  One NMODL_HH mechanism with one instance on each
+ * and keeps it where it is faster.  The fused variant for lists with
+ * NMODL_KIN9 comes in two builds chosen by the block size: at most 256
+ * threads, the solve in registers (lists of the 9-state scheme alone);
+ * more (FP64 up to 768, MIXED up to 512), one block per SM with part of the
+ * solve in local memory, so that the other items run at more warps per SM;
+ * options.block above those limits is lowered to them.  One NMODL_HH mechanism with one instance on each
  * node (node_index 0, 1, ..., n_nodes - 1) on at most 32 nodes per SM, in
  * FP64 without ion arrays or options.cnexp_pade (and options.no_fuse 0),
  * runs in a kernel of its own instead: one launch per window, three warps

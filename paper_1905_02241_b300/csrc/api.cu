@@ -877,7 +877,7 @@ static int build_plan(nmodl_ctx* c, nmodl_mech* const* mechs, int n_mechs, Plan*
     size_t items = 0;
     for (int t = 0; t < T; ++t) items += (size_t)gates[t] * mechs[t]->n;
     // (the 9-state variant: blocks up to 256 run its register-rich build,
-    // larger ones its 768-thread build)
+    // larger ones its wide build: FP64 up to 768 threads, MIXED up to 512)
     const int max_block = kin ? fused_kin_wide_block(p->precision) : kFusedMaxBlock;
     if (c->opt.block > 0) blocks = {std::min(c->opt.block, max_block)};
     else if (tune && kin) blocks = {128, 256, max_block == 768 ? 512 : 384, max_block};

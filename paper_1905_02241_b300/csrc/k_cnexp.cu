@@ -339,16 +339,19 @@ __device__ void block_inclusive_scan_u16(uint16_t* a, int n, int* wsum) {
 // at most 256 threads, the banded solve in registers (~245 in FP64, one
 // block per SM; MIXED two blocks per SM at 128 registers, the FP32 solve
 // spilling a few hundred bytes) -- best for lists of the 9-state scheme
-// alone.  KIN == 2: one 768-thread block per SM at 80 registers, the solve
-// keeping part of its state in local memory (about 1 KB per thread, served
-// by L1), so that cnexp items of the same tile run at 24 warps per SM
-// instead of 8 or 16.  Measured on the cortical mix with the 9-state scheme
-// on a quarter of 1M nodes, FP64 instance-steps/s by block (registers): 256
-// (244) 7.07e9, 384 (168) 7.66e9, 512 (128) 8.13e9, 768 (80) 8.53e9, 1024
-// (64) 8.49e9; MIXED: 2 x 256 (128) 1.91e10, 512 2.03e10, 768 2.05e10,
-// 1024 1.92e10.  On the 9-state scheme alone (1M clamped instances, FP64)
-// the 768-thread build loses (it and the per-mechanism launches 1.07e9 vs
-// 1.15e9).  The autotuner times block sizes of both builds.
+// alone.  KIN == 2, the wide build: one block per SM, FP64 768 threads at
+// 80 registers, MIXED 512 at 128, the solve keeping part of its state in
+// local memory (about 1 KB per thread), so that cnexp items of the same
+// tile run at more warps per SM (24 or 16 instead of 8).  Measured on the
+// cortical mix with the 9-state scheme on a quarter of 1M nodes (in the
+// fixed work order), FP64 instance-steps/s by block (registers): 256 (244)
+// 7.07e9, 384 (168) 7.66e9, 512 (128) 8.13e9, 768 (80) 8.53e9, 1024 (64)
+// 8.49e9; MIXED: 2 x 256 (128) 1.91e10, 512 (80) 2.03e10, 768 (80)
+// 2.05e10, 1024 (64) 1.92e10; with the work chunks below, MIXED 512 at 128
+// registers 2.59e10 against 2.41e10 for the register-rich build.  On the
+// 9-state scheme alone (1M clamped instances, FP64) the wide build loses
+// (it and the per-mechanism launches 1.07e9 vs 1.15e9).  The autotuner
+// times block sizes of both builds.
 template <int PREC, bool EXT, int KIN>
 __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                                   : KIN == 1 ? kFusedKinBlock

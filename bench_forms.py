@@ -681,6 +681,9 @@ def training_case(dev=0, n_pairs=1 << 20, epochs=2, batch=8192):
     Ws, bs = W.mlp_init(7)
     sur.set_weights(Surrogate.pack(Ws, bs))
     X, T = make_training_pairs(ctx, sur, p, n_pairs, seed=6)
+    # torch loads its reduction kernels on first use (about a second), and
+    # fit averages the loss record with one: not part of the training
+    torch.zeros(2, device=X.device).mean().item()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sur.fit(X, T, epochs=epochs, batch=batch, lr=2e-3)

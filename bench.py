@@ -135,6 +135,28 @@ def _subnet(wl, nodes):
     return dict(n_nodes=int(nodes.size), mechs=mechs, v0=wl["v0"][nodes])
 
 
+# the one recipe of both the reference arm and the cpu_baseline leg: the
+# FP64 oracle on the host's cores, one process per core (at most 128), each
+# stepping its own shard of whole nodes of the same workload
+ORACLE_SHARD_NODES = 20000
+ORACLE_SHARD_SECONDS = 4.0
+
+
+def oracle_on_cores(wl, nodes: int):
+    """(instance-steps/s, processes, seconds, sample) of the oracle on the
+    host's cores: all shards' instance-steps over the longest shard's wall
+    time."""
+    from oracle import timing as otiming
+    shard = min(ORACLE_SHARD_NODES, nodes)
+    cores = max(1, min(otiming.host_cores(), nodes // shard, 128))
+    subs = [_subnet(wl, np.arange(k * shard, (k + 1) * shard)) for k in range(cores)]
+    rate, el = otiming.time_parallel(subs, DT, ORACLE_SHARD_SECONDS, NSTEPS)
+    sample = (f"{cores} processes (one per host core), each the oracle on its own "
+              f"{shard}-node shard of the same network (whole nodes), up to {NSTEPS} steps "
+              f"in about {ORACLE_SHARD_SECONDS:g} s")
+    return rate, cores, el, sample
+
+
 def time_oracle(wl, n_nodes_sample: int, target_s: float):
     from oracle import oracle as orc
     nodes = np.arange(min(n_nodes_sample, wl["n_nodes"]))
@@ -184,18 +206,14 @@ def main():
         if rank != 0:
             return
         wl = W.cortical_mix(args.nodes, seed=2)
-        from oracle import timing as otiming
-        cores = max(1, min(otiming.host_cores(), args.nodes // 4000, 128))
-        subs = [_subnet(wl, np.arange(k * 4000, (k + 1) * 4000)) for k in range(cores)]
         rates = []
         for s in range(args.warmup + args.steps):
-            r, _ = otiming.time_parallel(subs, DT, 2.0, NSTEPS)
+            r, cores, _, sample = oracle_on_cores(wl, args.nodes)
             if s >= args.warmup:
                 rates.append(r)
         v = float(np.median(rates))
-        sample = (f"{cores} processes (one per host core), each the oracle on its own "
-                  f"4000-node shard of the same network (whole nodes) for about 2 s per "
-                  f"step; median of {args.steps} steps")
+        sample += f" per step; median of {args.steps} steps"
+
         line = {"impl": "reference", "metric": METRIC, "value": v,
                 "unit": "instance-steps/s", "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
@@ -338,18 +356,12 @@ def main():
         r1, sample1, el1 = time_oracle(wl, 60000, 6.0)
         cpu = {"value": r1, "unit": "instance-steps/s", "cores": 1, "kind": "oracle",
                "sample": sample1, "seconds": round(el1, 2)}
-        # the same oracle on the host's cores: one process per core,
-        # each on its own 20,000-node shard of the network
-        from oracle import timing as otiming
-        cores = min(otiming.host_cores(), args.nodes // 20000, 128)
+        # the same oracle on the host's cores, by the reference arm's recipe
+        rp, cores, elp, sample = oracle_on_cores(wl, args.nodes)
         if cores > 1:
-            subs = [_subnet(wl, np.arange(k * 20000, (k + 1) * 20000)) for k in range(cores)]
-            rp, elp = otiming.time_parallel(subs, DT, 8.0, NSTEPS)
             cpu.update({"value": rp, "cores": cores, "seconds": round(elp, 2),
-                        "sample": f"{cores} processes, each the oracle on its own 20000-node "
-                                  f"shard of the same network (whole nodes), up to {NSTEPS} "
-                                  f"steps in about 8 s; single thread: {r1:.4g} on "
-                                  + sample1,
+                        "sample": f"{sample} (the reference arm's recipe); single thread: "
+                                  f"{r1:.4g} on " + sample1,
                         "single_thread": r1})
 
     plan = ctx.plan(mechs)

@@ -1289,11 +1289,18 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                 // factor multiplier, power and component) kept in registers
                 // and reloaded when its next item starts another pair, since
                 // a thread's items stay in one pair for several rounds
+                // Each warp takes a contiguous chunk of whole rounds of the
+                // items, its lanes striding by 32 inside it, so that a
+                // thread's next item is usually in the same pair (pairs are
+                // a few hundred items; a block-wide stride would leave it
+                // for another pair at almost every item)
                 int q = -1, end = 0, base = 0, nb = 0, pw = 0, fx = 0;
                 float pdt = 0.f, fm = 1.f;
                 GateF G{};
                 const bool pade = A.pade != 0;
-                for (int k = tid; k < total_items; k += blockDim.x) {
+                const int chunk = 32 * ((total_items + blockDim.x - 1) / blockDim.x);
+                const int k_end = min(total_items, (tid >> 5) * chunk + chunk);
+                for (int k = (tid >> 5) * chunk + (tid & 31); k < k_end; k += 32) {
                     if (k >= end) {
                         do {
                             ++q;

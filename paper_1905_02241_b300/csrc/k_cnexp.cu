@@ -372,6 +372,7 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
     // ion arrays and the small systems).
     constexpr bool FAC_V = PREC == NMODL_MIXED && !KIN;
     __shared__ double efac_s[FAC_V ? 3 * kMaxMechsFused : 1];   // e of current 3 t + q
+    __shared__ float2 efac2_s[FAC_V ? 3 * kMaxMechsFused : 1];  // the same as float pairs
     __shared__ float fmul_s[FAC_V ? kMaxMechsFused * kMaxGates : 1];
     __shared__ int fidx_s[FAC_V ? kMaxMechsFused * kMaxGates : 1];  // 4 slot + component
     __shared__ int fpow_s[FAC_V ? kMaxMechsFused * kMaxGates : 1];
@@ -533,6 +534,10 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                     efac_s[3 * t + c] = md_s[t].kind == NMODL_HH     ? md_s[t].hh_e[c]
                                         : (EXT && md_s[t].kind == NMODL_KIN3) ? md_s[t].k3.e
                                                                         : md_s[t].e;
+            for (int k = 0; k < 3 * T; ++k) {
+                const float h = d2f_int(efac_s[k]);
+                efac2_s[k] = make_float2(h, d2f_int(efac_s[k] - f2d_int(h)));
+            }
         }
         // Work order of the FP64 state phase: the gates grouped by their pair
         // of rate forms (each pair of forms is one straight-line body), each
@@ -954,11 +959,40 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                 int sc = s1;
                 if (EXT && A.ions)
                     while (sc > s0 && tag_s[sc - 1] == NMODL_ION_CA) --sc;
-                for (int sl = s0; sl < sc; ++sl) {
-                    double g, e;
-                    slot_ge(sl, g, e);
-                    X = fma(g, e, X);
-                    G += g;
+                if constexpr (FAC_V && !EXT) {
+                    // here flat, so FAC: sum(g) and sum(g e) as float pairs
+                    // on the FP32 pipe (TwoSum and the products' exact
+                    // errors, about 48 bits; each g is an FP32 product, e a
+                    // float pair), widened to doubles once per node -- the
+                    // FP64 pipe, 1/64 of the FP32 rate, had carried two
+                    // instructions per slot here on a few warps per block
+                    float gh = 0.f, gl = 0.f, xh = 0.f, xl = 0.f;
+                    for (int sl = s0; sl < s1; ++sl) {
+                        const float4 f = f_s[sl];
+                        const float g = (f.x * f.y) * f.z;
+                        const float2 e = efac2_s[__float_as_int(f.w)];
+                        float sm, er;
+                        two_sum_f(gh, g, sm, er);
+                        gh = sm;
+                        gl += er;
+                        const float ph = __fmul_rn(g, e.x);
+                        const float pl = fmaf(g, e.y, fmaf(g, e.x, -ph));
+                        two_sum_f(xh, ph, sm, er);
+                        xh = sm;
+                        xl += er + pl;
+                    }
+                    float sm, er;
+                    two_sum_f(gh, gl, sm, er);
+                    G = ff2d_int(sm, er);
+                    two_sum_f(xh, xl, sm, er);
+                    X = ff2d_int(sm, er);
+                } else {
+                    for (int sl = s0; sl < sc; ++sl) {
+                        double g, e;
+                        slot_ge(sl, g, e);
+                        X = fma(g, e, X);
+                        G += g;
+                    }
                 }
                 if (EXT && A.ions) {
                     for (int sl = sc; sl < s1; ++sl) {

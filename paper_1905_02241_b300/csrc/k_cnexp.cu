@@ -959,15 +959,15 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                 int sc = s1;
                 if (EXT && A.ions)
                     while (sc > s0 && tag_s[sc - 1] == NMODL_ION_CA) --sc;
-                if constexpr (FAC_V && !EXT) {
-                    // here flat, so FAC: sum(g) and sum(g e) as float pairs
-                    // on the FP32 pipe (TwoSum and the products' exact
-                    // errors, about 48 bits; each g is an FP32 product, e a
-                    // float pair), widened to doubles once per node -- the
-                    // FP64 pipe, 1/64 of the FP32 rate, had carried two
-                    // instructions per slot here on a few warps per block
+                // FAC (here flat, so FAC_V): sum(g) and sum(g e) over slots
+                // [a, b) as float pairs on the FP32 pipe (TwoSum and the
+                // products' exact errors, about 48 bits; each g is an FP32
+                // product, e a float pair), widened to doubles once per node
+                // -- the FP64 pipe, 1/64 of the FP32 rate, had carried two
+                // instructions per slot here on a few warps per block
+                auto ff_sums = [&](int a, int b, double& Gs, double& Xs) {
                     float gh = 0.f, gl = 0.f, xh = 0.f, xl = 0.f;
-                    for (int sl = s0; sl < s1; ++sl) {
+                    for (int sl = a; sl < b; ++sl) {
                         const float4 f = f_s[sl];
                         const float g = (f.x * f.y) * f.z;
                         const float2 e = efac2_s[__float_as_int(f.w)];
@@ -983,9 +983,12 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                     }
                     float sm, er;
                     two_sum_f(gh, gl, sm, er);
-                    G = ff2d_int(sm, er);
+                    Gs = ff2d_int(sm, er);
                     two_sum_f(xh, xl, sm, er);
-                    X = ff2d_int(sm, er);
+                    Xs = ff2d_int(sm, er);
+                };
+                if constexpr (FAC_V) {
+                    ff_sums(s0, sc, G, X);
                 } else {
                     for (int sl = s0; sl < sc; ++sl) {
                         double g, e;
@@ -995,11 +998,15 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                     }
                 }
                 if (EXT && A.ions) {
-                    for (int sl = sc; sl < s1; ++sl) {
-                        double g, e;
-                        slot_ge(sl, g, e);
-                        Xca = fma(g, e, Xca);
-                        Gca += g;
+                    if constexpr (FAC_V) {
+                        ff_sums(sc, s1, Gca, Xca);
+                    } else {
+                        for (int sl = sc; sl < s1; ++sl) {
+                            double g, e;
+                            slot_ge(sl, g, e);
+                            Xca = fma(g, e, Xca);
+                            Gca += g;
+                        }
                     }
                     X += Xca;
                     G += Gca;

@@ -306,6 +306,24 @@ def main():
                      "FP64 residue of the mixed step (node sums and updates) over the "
                      "launch time, against the measured FP64 peak")}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    if prec == NMODL_MIXED:
+        # the mixed step keeps little FP64 work (the node update) and no pipe
+        # near its peak: its bound is the SMs' instruction issue, at the
+        # warp instructions per instance-step ncu counts on the 1M-node mix
+        fp64_frac = roof["frac"]
+        ins = C.MIXED_WARP_INSTR_PER_STEP * ninst * window
+        roof = {"bound": "issue", "pipe": "issue",
+                "achieved": ins / (launch_ms * 1e-3) / 1e12,
+                "peak": issue_peak(dev) / 1e12, "unit": "T warp-instructions/s",
+                "peak_source": "4 warp instructions per cycle per SM at the maximum SM clock",
+                "ops_per_launch": ins,
+                "ops_per_instance_step": C.MIXED_WARP_INSTR_PER_STEP,
+                "what": ("issue use: the warp instructions the mixed step issues (ncu count on "
+                         "the 1,000,000-node mix, per instance-step) over the launch time, "
+                         "against one instruction per cycle per SM sub-partition"),
+                "fp64_residue_frac": fp64_frac,
+                "fp64_residue_ops_per_instance_step": count / ninst}
+        roof["frac"] = roof["achieved"] / roof["peak"]
     if prec == NMODL_FP64:
         # the same speed against the FP64-pipe bound of routines written
         # entirely in FP64 (a yardstick that does not move with the design)
@@ -315,7 +333,7 @@ def main():
     # DRAM bytes per 40-step launch: dram__bytes_read.sum + dram__bytes_write.sum
     # of one ncu capture of the same kernel on the 1,000,000-node network
     # (11,548,985 instances), scaled to this network by its instance count
-    per_1m = {NMODL_FP64: 311.8e6, NMODL_MIXED: 313.1e6}[prec]
+    per_1m = {NMODL_FP64: 311.8e6, NMODL_MIXED: 312.0e6}[prec]
     roof["traffic"] = per_1m * ninst / 11548985 if window == 40 else None
     roof["traffic_unit"] = "bytes per launch"
     roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "

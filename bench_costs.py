@@ -169,18 +169,10 @@ def cacum_fp64_ops(c=DESIGN, updates: float = 4.0) -> float:
 # --------------------------------------------------------------- mixed cnexp
 
 def mixed_fp64_ops_per_step(wl) -> float:
-    """FP64 residue of the mixed fused step: per current its g e and g into
-    the node sums (2; HH three currents), per node the update (5)."""
-    ops = _node(DESIGN) * wl["n_nodes"]
-    for m in wl["mechs"]:
-        n = m["node_index"].size
-        if m["type"] == W.TYPE_HH:
-            ops += 3 * 2 * n
-        elif m["type"] == W.TYPE_CACUM:
-            continue
-        else:
-            ops += 2 * n
-    return float(ops)
+    """FP64 residue of the mixed fused step without ion arrays: per node
+    v += dv (1).  The node sums of g e and g and the update's r = X - v G,
+    d = G + cm/dt and r/d run as float pairs on the FP32 pipe."""
+    return float(wl["n_nodes"])
 
 
 # ----------------------------------------------------------------- cable
@@ -217,9 +209,9 @@ HH_WARP_FP64_PER_STEP = 30
 
 # Warp instructions the mixed-precision fused step issues per instance-step
 # (measured, not modelled: ncu smsp__inst_executed.sum of one 40-step launch
-# on the 1,000,000-node cortical mix, 5,046,778,632 instructions over
+# on the 1,000,000-node cortical mix, 4,427,978,575 instructions over
 # 11,548,985 instances x 40 steps), for its issue-rate roofline: an SM
 # issues at most one warp instruction per cycle on each of its four
 # sub-partitions.
-MIXED_WARP_INSTR_PER_STEP = 5046778632 / (11548985 * 40)
+MIXED_WARP_INSTR_PER_STEP = 4427978575 / (11548985 * 40)
 ISSUE_PER_SM_PER_CYCLE = 4

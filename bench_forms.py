@@ -151,8 +151,9 @@ def batched(dev, peaks, steps=2, nsteps=200, scale=1.0):
     out["launches_per_run"] = -(-nsteps // ctx.options.window)
     out["roofline_mixed"] = _roof(C.mixed_fp64_ops_per_step(wl) / ninst, out["mixed"],
                                   peaks["fp64"], "fp64", what=(
-                                      "FP64 residue of the mixed step (node sums, node update) "
-                                      "per instance-step, against the measured FP64 peak"))
+                                      "FP64 residue of the mixed step (v += dv per node; the node "
+                                      "sums and the update run as float pairs on the FP32 "
+                                      "pipe) per instance-step, against the measured FP64 peak"))
     out["roofline_fp64"] = _roof(C.fp64_ops_per_step(wl) / ninst, out["fp64"], peaks["fp64"],
                                  "fp64", what="FP64 pipe instructions per instance-step")
     if peaks.get("issue"):

@@ -821,6 +821,8 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
     // (offsets recomputed where used, to keep registers free)
     auto sched_coff = [&]() { return sched_s + 2 + (sched_s[0] + 1) + (sched_s[1] + 1) + 2 * NT; };
     const double cmdt = 1e-3 * A.cm / A.dt;
+    // the same as a float pair (the mixed node update below)
+    const float cmdt_h = d2f_int(cmdt), cmdt_l = d2f_int(cmdt - f2d_int(cmdt_h));
     // conductance(s) of instance j of type q from its states (HH: gna, gk;
     // not for the calcium buffer)
     auto inst_g = [&](int q, int j, double& g0, double& g1) {
@@ -965,7 +967,7 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                 // product, e a float pair), widened to doubles once per node
                 // -- the FP64 pipe, 1/64 of the FP32 rate, had carried two
                 // instructions per slot here on a few warps per block
-                auto ff_sums = [&](int a, int b, double& Gs, double& Xs) {
+                auto ff_sums_f = [&](int a, int b, float& Gh, float& Gl, float& Xh, float& Xl) {
                     float gh = 0.f, gl = 0.f, xh = 0.f, xl = 0.f;
                     for (int sl = a; sl < b; ++sl) {
                         const float4 f = f_s[sl];
@@ -981,13 +983,48 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                         xh = sm;
                         xl += er + pl;
                     }
-                    float sm, er;
-                    two_sum_f(gh, gl, sm, er);
-                    Gs = ff2d_int(sm, er);
-                    two_sum_f(xh, xl, sm, er);
-                    Xs = ff2d_int(sm, er);
+                    two_sum_f(gh, gl, Gh, Gl);
+                    two_sum_f(xh, xl, Xh, Xl);
                 };
-                if constexpr (FAC_V) {
+                auto ff_sums = [&](int a, int b, double& Gs, double& Xs) {
+                    float Gh, Gl, Xh, Xl;
+                    ff_sums_f(a, b, Gh, Gl, Xh, Xl);
+                    Gs = ff2d_int_nf(Gh, Gl);
+                    Xs = ff2d_int_nf(Xh, Xl);
+                };
+                if constexpr (FAC_V && !EXT) {
+                    // without ion arrays the node update stays in float
+                    // pairs too: r = X - v G, d = G + cm/dt and the change
+                    // r/d (a quotient from the FP32 reciprocal and one
+                    // remainder correction, about 46 bits), one FP64
+                    // addition for v += dv (v split exactly to 47 bits for
+                    // the product; the addition takes all of v)
+                    float Gh, Gl, Xh, Xl;
+                    ff_sums_f(s0, s1, Gh, Gl, Xh, Xl);
+                    float vh, vl, sm, er, rh, rl, dh, dl;
+                    split_d_ff(vv, vh, vl);
+                    const float ph = __fmul_rn(vh, Gh);
+                    const float pl = fmaf(vh, Gl, fmaf(vl, Gh, fmaf(vh, Gh, -ph)));
+                    two_sum_f(Xh, -ph, sm, er);
+                    two_sum_f(sm, er + (Xl - pl), rh, rl);
+                    two_sum_f(Gh, cmdt_h, sm, er);
+                    two_sum_f(sm, er + (Gl + cmdt_l), dh, dl);
+                    if (last) {
+                        A.rhs[n0 + n] = ff2d_int_nf(rh, rl);
+                        A.d[n0 + n] = ff2d_int_nf(dh, dl);
+                    }
+                    double vn = vv;
+                    if (!A.clamp_v) {
+                        const float inv = __frcp_rn(dh);
+                        const float q1 = __fmul_rn(rh, inv);
+                        const float q2 = ((fmaf(-q1, dh, rh) + rl) - q1 * dl) * inv;
+                        two_sum_f(q1, q2, sm, er);
+                        vn = vv + ff2d_int_nf(sm, er);
+                    }
+                    v_s[n] = vn;
+                    vf_s[n] = d2f_int(vn);
+                    continue;
+                } else if constexpr (FAC_V) {
                     ff_sums(s0, sc, G, X);
                 } else {
                     for (int sl = s0; sl < sc; ++sl) {

@@ -189,6 +189,12 @@ __device__ __forceinline__ double ff2d_int(float hi, float lo) {
     H |= (unsigned long long)(fh & 0x80000000u) << 32;
     return ah == 0u ? 0.0 : __longlong_as_double((long long)H);
 }
+// ff2d_int, with a non-finite hi passed on as the equal double (an infinity,
+// a quiet NaN) rather than widened as if finite, for sums whose non-finite
+// values must reach the non-finite checks
+__device__ __forceinline__ double ff2d_int_nf(float hi, float lo) {
+    return (__float_as_uint(hi) & 0x7f800000u) == 0x7f800000u ? f2d_int(hi) : ff2d_int(hi, lo);
+}
 // e^x = 2^m T (1 + p) for |x| < 708: the table entry T, k (m = k >> kExpBits)
 // and p, as described above.
 __device__ __forceinline__ void exp_tang_core(double x, double& T, int& k, double& pr) {

@@ -106,7 +106,8 @@ def test_mixed_residue_and_cable_counts():
     n = 50
     hh = dict(n_nodes=n, mechs=[dict(type=W.TYPE_HH, params=W.hh_params(),
                                      node_index=np.arange(n, dtype=np.int32))])
-    assert C.mixed_fp64_ops_per_step(hh) == (NODE + 3 * 2) * n
+    # v += dv only: the node sums and the update run as float pairs
+    assert C.mixed_fp64_ops_per_step(hh) == n
     # a chain of n nodes (one root): the diagonal update's 1/d and product
     # (3 per node) give way to the tree solve: per non-root node 4 + 2 + 2,
     # per node the pivot reciprocal + 1 and v += dv

@@ -67,6 +67,34 @@ def test_nonfinite_latched(api):
     assert ctx.sync() == 0  # cleared after being reported
 
 
+def test_nonfinite_node_sums_of_the_mixed_step_latched(api):
+    # mixed precision forms a cnexp current's gbar m^p h^q in FP32: a gbar
+    # beyond the FP32 range makes the node's conductance sums non-finite
+    # while every state stays finite; the fused step must still report it
+    n = 600
+    ni = np.arange(n, dtype=np.int32)
+    for ions in (False, True):
+        ctx = api.Context(0, precision=api.NMODL_MIXED)
+        if ions:
+            ctx.set_ions(*[to_dev(np.zeros(n)) for _ in range(3)])
+        big = W.cortical_type_params(3)[1].copy()
+        big[1] = 1e300
+        ms = [api.Mechanism(ctx, W.TYPE_CNEXP, ni, n, W.cortical_type_params(3)[0]),
+              api.Mechanism(ctx, W.TYPE_CNEXP, ni[::7].copy(), n, big)]
+        v = to_dev(np.full(n, -65.0))
+        rhs, d = to_dev(np.zeros(n)), to_dev(np.zeros(n))
+        for m in ms:
+            m.init(v)
+        ctx.step(ms, 0.025, 1.0, v, rhs, d, 3)
+        assert ctx.plan(ms)["fused"]
+        assert ctx.sync() == -5, ions
+        got = v.cpu().numpy()
+        assert not np.all(np.isfinite(got[::7])) and np.all(np.isfinite(np.delete(got, np.s_[::7])))
+        for m in ms:
+            m.close()
+        ctx.close()
+
+
 # -------------------------------------------- Newton non-convergence
 # Provoked from the host with an iteration cap that no solve can meet (one
 # update, then the convergence check never runs): every instance reports

@@ -70,8 +70,7 @@ __global__ void k_state_gates(const MechD* __restrict__ md, int64_t n,
             row[i] = m;
         }
     } else {
-        const GateF F{(float)G.aA, (float)G.avh, (float)G.ark,
-                      (float)G.bA, (float)G.bvh, (float)G.brk, G.aform, G.bform};
+        const GateF F = gate_f(G);
         const float phidtf = (float)phidt;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
              i += (int64_t)gridDim.x * blockDim.x) {
@@ -611,9 +610,7 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
             }
         for (int k = tid; k < T * kMaxGates; k += blockDim.x) {
             const GateD& G = md_s[k / kMaxGates].gate[k % kMaxGates];
-            gf_s[k / kMaxGates][k % kMaxGates] =
-                GateF{(float)G.aA, (float)G.avh, (float)G.ark, (float)G.bA,
-                      (float)G.bvh, (float)G.brk, G.aform, G.bform};
+            gf_s[k / kMaxGates][k % kMaxGates] = gate_f(G);
         }
     }
     const int total_items = pair_start[n_pairs];

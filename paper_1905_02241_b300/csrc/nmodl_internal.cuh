@@ -577,21 +577,29 @@ __device__ __forceinline__ double mul_pow_d(double g, double x, int p) {
 
 // ------------------------------------------------------------ FP32 math
 // Rates and the cnexp factor in single precision.  exp uses the hardware
-// exp2 unit through __expf; the two cancelling differences (1 - exp(-u) in
-// LINOID and 1 - exp(-x) in cnexp) switch to their Taylor series where the
-// series is more accurate than the subtraction.
+// exp2 unit; the two cancelling differences (1 - exp(-u) in LINOID and
+// 1 - exp(-x) in cnexp) switch to their Taylor series where the series is
+// more accurate than the subtraction.
 
-__device__ __forceinline__ float rate_f(int form, float A, float vh, float rk,
-                                        float v) {
-    const float u = (v - vh) * rk;
-    if (form == kExp) return A * __expf(u);
-    if (form == kSigmoid) return __fdividef(A, 1.0f + __expf(-u));
-    // u/(1-e^-u) = 1 + u/2 + u^2/12 - u^4/720 + ...
-    if (fabsf(u) < 0.1f) {
-        const float u2 = u * u;
-        return A * (1.0f + 0.5f * u + u2 * (1.0f / 12.0f - u2 * (1.0f / 720.0f)));
+__device__ __forceinline__ float ex2_hw(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// A rate with its parameters folded for the exp2 unit: w = u log2(e) =
+// v k2 + c2 (k2 = rk log2(e), c2 = -vh rk log2(e): one multiply-add), and
+// LINOID's prefactor as A ln2 (A u = (A ln2) w).
+__device__ __forceinline__ float rate_f(int form, float A, float k2, float c2, float v) {
+    const float w = fmaf(v, k2, c2);
+    if (form == kExp) return A * ex2_hw(w);
+    if (form == kSigmoid) return __fdividef(A, 1.0f + ex2_hw(-w));
+    // u/(1-e^-u) = 1 + u/2 + u^2/12 - u^4/720 + ..., u = w ln2 and A = (A ln2) log2(e)
+    if (fabsf(w) < 0.1f * 1.44269504f) {
+        const float u = w * 0.693147181f, u2 = u * u;
+        return (A * 1.44269504f) * (1.0f + 0.5f * u + u2 * (1.0f / 12.0f - u2 * (1.0f / 720.0f)));
     }
-    return __fdividef(A * u, 1.0f - __expf(-u));
+    return __fdividef(A * w, 1.0f - ex2_hw(-w));
 }
 
 // 1 - exp(-x) for x >= 0
@@ -603,17 +611,25 @@ __device__ __forceinline__ float one_minus_expneg_f(float x) {
     return 1.0f - __expf(-x);
 }
 
+// a gate's two rates in FP32, folded as rate_f takes them
 struct GateF {
-    float aA, avh, ark, bA, bvh, brk;
+    float aA, ak2, ac2, bA, bk2, bc2;
     int32_t aform, bform;
 };
+__device__ __forceinline__ GateF gate_f(const GateD& G) {
+    constexpr double kLog2e = 1.4426950408889634, kLn2 = 0.6931471805599453;
+    return GateF{(float)(G.aform == kLinoid ? G.aA * kLn2 : G.aA), (float)(G.ark * kLog2e),
+                 (float)(-G.avh * G.ark * kLog2e),
+                 (float)(G.bform == kLinoid ? G.bA * kLn2 : G.bA), (float)(G.brk * kLog2e),
+                 (float)(-G.bvh * G.brk * kLog2e), G.aform, G.bform};
+}
 
 // (minf, 1 - exp(-dt/mtau)) of a gate in FP32; with pade the factor is the
 // (1,1) Pade form x/(1 + x/2)
 __device__ __forceinline__ void gate_coef_f(const GateF& G, float phidt, float v,
                                             float& minf, float& f, bool pade = false) {
-    const float a = rate_f(G.aform, G.aA, G.avh, G.ark, v);
-    const float b = rate_f(G.bform, G.bA, G.bvh, G.brk, v);
+    const float a = rate_f(G.aform, G.aA, G.ak2, G.ac2, v);
+    const float b = rate_f(G.bform, G.bA, G.bk2, G.bc2, v);
     const float s = a + b;
     minf = __fdividef(a, s);
     const float x = phidt * s;

@@ -209,9 +209,9 @@ HH_WARP_FP64_PER_STEP = 30
 
 # Warp instructions the mixed-precision fused step issues per instance-step
 # (measured, not modelled: ncu smsp__inst_executed.sum of one 40-step launch
-# on the 1,000,000-node cortical mix, 4,427,978,575 instructions over
+# on the 1,000,000-node cortical mix, 4,074,252,771 instructions over
 # 11,548,985 instances x 40 steps), for its issue-rate roofline: an SM
 # issues at most one warp instruction per cycle on each of its four
 # sub-partitions.
-MIXED_WARP_INSTR_PER_STEP = 4427978575 / (11548985 * 40)
+MIXED_WARP_INSTR_PER_STEP = 4074252771 / (11548985 * 40)
 ISSUE_PER_SM_PER_CYCLE = 4

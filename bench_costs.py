@@ -180,14 +180,14 @@ def mixed_fp64_ops_per_step(wl) -> float:
 def cable_fp64_ops_per_step(wl, parent) -> float:
     """The isolated step's count with the diagonal update (1/d, v += r/d: 3
     per node) replaced by the tree system: per non-root node its axial terms
-    in its own and its parent's row (4), its elimination into the parent
-    (2 fma) and its substitution (ga/d' times the parent's change: 2); per
-    node its pivot reciprocal and r'/d' (rcp + 1) and v += dv (1)."""
+    in its own and its parent's row (4); per node v += dv (1).  The
+    elimination, the pivots' reciprocals and the substitution run in float
+    pairs on the FP32 pipe (no FP64 instructions)."""
     import numpy as np
     n = wl["n_nodes"]
     nonroot = int(np.count_nonzero(np.asarray(parent) >= 0))
     iso = fp64_ops_per_step(wl)
-    return iso - (DESIGN["rcp"] + 1) * n + nonroot * (4 + 2 + 2) + n * (DESIGN["rcp"] + 1 + 1)
+    return iso - (DESIGN["rcp"] + 1) * n + nonroot * 4 + n
 
 
 # ------------------------------------------------------------- surrogate

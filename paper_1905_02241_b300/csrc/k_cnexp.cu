@@ -1123,8 +1123,11 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                     r = fma(gb_s[c], v_s[c] - vv, r);
                     dd += gb_s[c];
                 }
-                r2_s[n] = r;
-                d2_s[n] = dd;
+                // the row for the tree solve, as float pairs in the same
+                // 8 bytes
+                const ff2 rp = ff_of(r), dp = ff_of(dd);
+                reinterpret_cast<float2*>(r2_s)[n] = make_float2(rp.h, rp.l);
+                reinterpret_cast<float2*>(d2_s)[n] = make_float2(dp.h, dp.l);
                 if (last) {  // rhs and d report the assembled system
                     A.rhs[n0 + n] = r;
                     A.d[n0 + n] = dd;
@@ -1151,42 +1154,54 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                     const uint16_t* cS = cE + NT;
                     const uint16_t* coff = cS + NT;
                     const uint16_t* clist = coff + NT + 1;
-                    // leaves -> roots by height: d2_s[i] := ga_i / d' of node
-                    // i (0 at roots) and r2_s[i] := r'/d' once its children
-                    // are eliminated; 1/d' is only ever needed times ga_i
-                    // (by the parent, d'_p -= gb_c (ga_c / d'_c), and by the
-                    // substitution), so each level's chain -- one warp, each
-                    // FP64 instruction a full issue slot -- has one
-                    // multiply-add per child, the reciprocal and two products
+                    // The tree system in float pairs (rows r2/d2 as float2
+                    // in the same storage): each level's chain of dependent
+                    // FP32 operations has 4-cycle latencies where an FP64
+                    // instruction takes about 64 cycles, and the FP64 pipe is
+                    // left to the other warps' gate updates; the pairs carry
+                    // about 46 bits, far inside the solve's error budget.
+                    float2* d2f = reinterpret_cast<float2*>(d2_s);
+                    float2* r2f = reinterpret_cast<float2*>(r2_s);
+                    auto ld = [](const float2* a, int i) { const float2 x = a[i]; return ff2{x.x, x.y}; };
+                    auto st = [](float2* a, int i, ff2 x) { a[i] = make_float2(x.h, x.l); };
+                    // leaves -> roots by height: d2[i] := ga_i / d' of node i
+                    // (0 at roots) and r2[i] := r'/d' once its children are
+                    // eliminated; 1/d' is only ever needed times ga_i (by the
+                    // parent, d'_p -= gb_c (ga_c / d'_c), and by the
+                    // substitution), so each level's chain has one product
+                    // and difference per child, the reciprocal and two
+                    // products
                     for (int h = 0; h < cH; ++h) {
                         for (int k = cEL[h] + tid; k < cEL[h + 1]; k += 32) {
                             const int i = cE[k];
-                            double dd = d2_s[i], r = r2_s[i];
+                            ff2 dd = ld(d2f, i), r = ld(r2f, i);
                             for (int q = coff[i]; q < coff[i + 1]; ++q) {
                                 const int c = clist[q];
-                                dd = fma(-gb_s[c], d2_s[c], dd);
-                                r = fma(gb_s[c], r2_s[c], r);
+                                const ff2 gb = ff_of(gb_s[c]);
+                                dd = ff_sub(dd, ff_mul(gb, ld(d2f, c)));
+                                r = ff_add(r, ff_mul(gb, ld(r2f, c)));
                             }
-                            const double inv = rcp_chain(dd);  // on the level chain: latency
-                            d2_s[i] = (par_s[i] != 0xffff ? ga_s[i] : 0.0) * inv;
-                            r2_s[i] = r * inv;
+                            const ff2 inv = ff_rcp(dd);
+                            st(d2f, i, par_s[i] != 0xffff ? ff_mul(ff_of(ga_s[i]), inv) : ff2{0.f, 0.f});
+                            st(r2f, i, ff_mul(r, inv));
                         }
                         __syncwarp();
                     }
-                    // roots -> leaves by depth: r2_s[i] := the change of v,
+                    // roots -> leaves by depth: r2[i] := the change of v,
                     // x_i = r'/d' + (ga_i / d') x_parent
                     for (int l = 0; l < cD; ++l) {
                         for (int k = cSL[l] + tid; k < cSL[l + 1]; k += 32) {
                             const int i = cS[k];
                             const int pp = par_s[i];
-                            if (pp != 0xffff) r2_s[i] = fma(d2_s[i], r2_s[pp], r2_s[i]);
+                            if (pp != 0xffff) st(r2f, i, ff_add(ff_mul(ld(d2f, i), ld(r2f, pp)), ld(r2f, i)));
                         }
                         __syncwarp();
                     }
                 }
                 __syncthreads();
                 for (int n = tid; n < NT; n += blockDim.x) {
-                    const double vn = v_s[n] + r2_s[n];
+                    const float2 dv = reinterpret_cast<const float2*>(r2_s)[n];
+                    const double vn = v_s[n] + ff2d_int_nf(dv.x, dv.y);
                     v_s[n] = vn;
                     if (PREC == NMODL_MIXED) vf_s[n] = d2f_int(vn);
                 }

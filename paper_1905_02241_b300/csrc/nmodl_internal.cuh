@@ -189,6 +189,41 @@ __device__ __forceinline__ double ff2d_int(float hi, float lo) {
     H |= (unsigned long long)(fh & 0x80000000u) << 32;
     return ah == 0u ? 0.0 : __longlong_as_double((long long)H);
 }
+// Float-pair arithmetic for dependent chains (the tree solve's levels): a
+// value is h + l with |l| <= ulp(h)/2, about 46-48 significand bits in the
+// FP32 exponent range, each operation a few FP32 instructions of 4-cycle
+// latency where one FP64 instruction takes about 64 cycles on this GPU.
+// Products keep the exact error of h h' from an fma; sums are TwoSum; each
+// result is renormalised by a fast two-sum (|e| small against s, or s == 0).
+struct ff2 {
+    float h, l;
+};
+__device__ __forceinline__ ff2 ff_renorm(float s, float e) {
+    const float h = s + e;
+    return ff2{h, e - (h - s)};
+}
+__device__ __forceinline__ ff2 ff_of(double x) {  // to 47 bits (split_d_ff)
+    ff2 r;
+    split_d_ff(x, r.h, r.l);
+    return r;
+}
+__device__ __forceinline__ ff2 ff_mul(ff2 a, ff2 b) {
+    const float p = __fmul_rn(a.h, b.h);
+    return ff_renorm(p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p))));
+}
+__device__ __forceinline__ ff2 ff_add(ff2 a, ff2 b) {
+    float s, e;
+    two_sum_f(a.h, b.h, s, e);
+    return ff_renorm(s, e + (a.l + b.l));
+}
+__device__ __forceinline__ ff2 ff_sub(ff2 a, ff2 b) { return ff_add(a, ff2{-b.h, -b.l}); }
+// 1/a: the correctly rounded FP32 reciprocal y of a.h and one Newton step
+// y + y (1 - a y) (relative error about 2^-46)
+__device__ __forceinline__ ff2 ff_rcp(ff2 a) {
+    const float y = __frcp_rn(a.h);
+    return ff_renorm(y, y * fmaf(-a.l, y, fmaf(-a.h, y, 1.0f)));
+}
+
 // ff2d_int, with a non-finite hi passed on as the equal double (an infinity,
 // a quiet NaN) rather than widened as if finite, for sums whose non-finite
 // values must reach the non-finite checks

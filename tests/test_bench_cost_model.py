@@ -109,11 +109,12 @@ def test_mixed_residue_and_cable_counts():
     # v += dv only: the node sums and the update run as float pairs
     assert C.mixed_fp64_ops_per_step(hh) == n
     # a chain of n nodes (one root): the diagonal update's 1/d and product
-    # (3 per node) give way to the tree solve: per non-root node 4 + 2 + 2,
-    # per node the pivot reciprocal + 1 and v += dv
+    # (3 per node) give way to the tree system's FP64 part: per non-root
+    # node its axial terms (4), per node v += dv (the solve runs in float
+    # pairs)
     parent = np.arange(-1, n - 1)
     assert C.cable_fp64_ops_per_step(hh, parent) == (
-        C.fp64_ops_per_step(hh) - 3 * n + (n - 1) * 8 + n * 4)
+        C.fp64_ops_per_step(hh) - 3 * n + (n - 1) * 4 + n)
 
 
 def test_surrogate_flop_counts():

@@ -462,10 +462,11 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
             Kin9D& K = k9_s[t];
             const double lf = log(A.dt * K.af[e]), lb = log(A.dt * K.ab[e]);
             if constexpr (PREC == NMODL_MIXED) {
-                k9f_s[t][e] = (float)K.bf[e];
-                k9f_s[t][kKinEdges + e] = (float)K.bb[e];
-                k9f_s[t][2 * kKinEdges + e] = (float)lf;
-                k9f_s[t][3 * kKinEdges + e] = (float)lb;
+                // scaled by log2(e) for the exp2 unit
+                k9f_s[t][e] = (float)(K.bf[e] * 1.4426950408889634);
+                k9f_s[t][kKinEdges + e] = (float)(K.bb[e] * 1.4426950408889634);
+                k9f_s[t][2 * kKinEdges + e] = (float)(lf * 1.4426950408889634);
+                k9f_s[t][3 * kKinEdges + e] = (float)(lb * 1.4426950408889634);
             } else {
                 K.af[e] = lf;
                 K.ab[e] = lb;
@@ -598,9 +599,9 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                 if (M.kind == NMODL_KIN3) {
                     for (int e = 0; e < 3; ++e) {
                         k3f_s[k].af[e] = (float)M.k3.af[e];
-                        k3f_s[k].bf[e] = (float)M.k3.bf[e];
+                        k3f_s[k].bf[e] = (float)(M.k3.bf[e] * 1.4426950408889634);  // log2(e)
                         k3f_s[k].ab[e] = (float)M.k3.ab[e];
-                        k3f_s[k].bb[e] = (float)M.k3.bb[e];
+                        k3f_s[k].bb[e] = (float)(M.k3.bb[e] * 1.4426950408889634);
                     }
                 } else if (M.kind == NMODL_CACUM) {
                     const CacumD& C = M.cd;
@@ -1253,8 +1254,8 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                     float dk_f[kKinEdges], dk_b[kKinEdges];
 #pragma unroll
                     for (int e = 0; e < kKinEdges; ++e) {
-                        dk_f[e] = __expf(fmaf(kf[e], vf, kf[2 * kKinEdges + e]));
-                        dk_b[e] = __expf(fmaf(-kf[kKinEdges + e], vf, kf[3 * kKinEdges + e]));
+                        dk_f[e] = ex2_hw(fmaf(kf[e], vf, kf[2 * kKinEdges + e]));
+                        dk_b[e] = ex2_hw(fmaf(-kf[kKinEdges + e], vf, kf[3 * kKinEdges + e]));
                     }
                     iters = kin9_refine_mixed(dk_f, dk_b, x, y, A.newton_tol, 1 + A.ir_max, nonconv);
                 }

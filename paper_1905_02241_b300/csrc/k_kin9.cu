@@ -86,8 +86,9 @@ __global__ void k_kin9_init(const Kin9D* __restrict__ kd, int64_t n,
 // Rate constants of one launch, folded on the host and passed by value.
 // With one dt for all instances dt k = exp(b v + ln(dt a)): one multiply-add
 // and the exp (FP64: lnc = ln(dt af), ln(dt ab); MIXED: kf = bf, bb, then
-// ln(dt af), ln(dt ab) in FP32).  With a dt per instance (training pairs)
-// MIXED keeps af, ab in kf and scales by dt.  FP32 copies are made on the
+// ln(dt af), ln(dt ab) in FP32, all scaled by log2(e) for the exp2 unit).
+// With a dt per instance (training pairs) MIXED keeps af, ab in kf and
+// scales by dt.  FP32 copies are made on the
 // host because FP64 -> FP32 conversions run on the FP64 pipe.
 struct Kin9Launch {
     double lnc[2 * kKinEdges];
@@ -148,14 +149,14 @@ __global__ void __launch_bounds__(128, PREC == NMODL_MIXED ? 3 : 1)
                 const float dtf = d2f_int(dt);
 #pragma unroll
                 for (int e = 0; e < kKinEdges; ++e) {
-                    dk_f[e] = dtf * (kf_s[2 * kKinEdges + e] * __expf(kf_s[e] * vf));
-                    dk_b[e] = dtf * (kf_s[3 * kKinEdges + e] * __expf(-kf_s[kKinEdges + e] * vf));
+                    dk_f[e] = dtf * (kf_s[2 * kKinEdges + e] * ex2_hw(kf_s[e] * vf));
+                    dk_b[e] = dtf * (kf_s[3 * kKinEdges + e] * ex2_hw(-kf_s[kKinEdges + e] * vf));
                 }
             } else {
 #pragma unroll
                 for (int e = 0; e < kKinEdges; ++e) {
-                    dk_f[e] = __expf(fmaf(kf_s[e], vf, kf_s[2 * kKinEdges + e]));
-                    dk_b[e] = __expf(fmaf(-kf_s[kKinEdges + e], vf, kf_s[3 * kKinEdges + e]));
+                    dk_f[e] = ex2_hw(fmaf(kf_s[e], vf, kf_s[2 * kKinEdges + e]));
+                    dk_b[e] = ex2_hw(fmaf(-kf_s[kKinEdges + e], vf, kf_s[3 * kKinEdges + e]));
                 }
             }
             iters = kin9_refine_mixed(dk_f, dk_b, x, y, tol, 1 + ir_max, nonconv);
@@ -212,10 +213,11 @@ void launch_kin9_state(int prec, const Kin9D* kd, const Kin9D& kh, int64_t n, co
         const double cb = dt_arr ? 0.0 : std::log(dt * kh.ab[e]);
         KL.lnc[e] = cf;
         KL.lnc[kKinEdges + e] = cb;
-        KL.kf[e] = (float)kh.bf[e];
-        KL.kf[kKinEdges + e] = (float)kh.bb[e];
-        KL.kf[2 * kKinEdges + e] = (float)(dt_arr ? kh.af[e] : cf);
-        KL.kf[3 * kKinEdges + e] = (float)(dt_arr ? kh.ab[e] : cb);
+        constexpr double kLog2e = 1.4426950408889634;
+        KL.kf[e] = (float)(kh.bf[e] * kLog2e);
+        KL.kf[kKinEdges + e] = (float)(kh.bb[e] * kLog2e);
+        KL.kf[2 * kKinEdges + e] = (float)(dt_arr ? kh.af[e] : cf * kLog2e);
+        KL.kf[3 * kKinEdges + e] = (float)(dt_arr ? kh.ab[e] : cb * kLog2e);
     }
     if (prec == NMODL_FP64) {
         if (list)

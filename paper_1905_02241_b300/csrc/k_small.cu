@@ -152,9 +152,9 @@ Kin3F kin3_f32(const Kin3D& K) {
     Kin3F f;
     for (int e = 0; e < 3; ++e) {
         f.af[e] = (float)K.af[e];
-        f.bf[e] = (float)K.bf[e];
+        f.bf[e] = (float)(K.bf[e] * 1.4426950408889634);  // log2(e): the exp2 unit
         f.ab[e] = (float)K.ab[e];
-        f.bb[e] = (float)K.bb[e];
+        f.bb[e] = (float)(K.bb[e] * 1.4426950408889634);
     }
     return f;
 }

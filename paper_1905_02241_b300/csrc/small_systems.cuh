@@ -110,7 +110,8 @@ __device__ __forceinline__ int cacum_newton_d(const CacumD& C, double ica, doubl
 // Rates, matrices and eliminations in FP32; the residual and the
 // refinement of the result in FP64 (conversions on the integer pipe).
 
-// FP32 copies of the parameters, made once per launch or tile
+// FP32 copies of the parameters, made once per launch or tile (Kin3F: the
+// exponents' b scaled by log2(e) for the exp2 unit)
 struct Kin3F {
     float af[3], bf[3], ab[3], bb[3];
 };
@@ -128,8 +129,8 @@ __device__ __forceinline__ int kin3_step_mixed(const Kin3F& K, float vf, float d
     float kf[3], kb[3], M[3][3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        kf[e] = K.af[e] * __expf(K.bf[e] * vf);
-        kb[e] = K.ab[e] * __expf(-K.bb[e] * vf);
+        kf[e] = K.af[e] * ex2_hw(K.bf[e] * vf);
+        kb[e] = K.ab[e] * ex2_hw(-K.bb[e] * vf);
     }
     kin3_matrix(kf, kb, dtf, M);
     double off[3][3], diag[3] = {1.0, 1.0, 1.0};

@@ -333,7 +333,7 @@ def main():
     # DRAM bytes per 40-step launch: dram__bytes_read.sum + dram__bytes_write.sum
     # of one ncu capture of the same kernel on the 1,000,000-node network
     # (11,548,985 instances), scaled to this network by its instance count
-    per_1m = {NMODL_FP64: 311.8e6, NMODL_MIXED: 312.6e6}[prec]
+    per_1m = {NMODL_FP64: 310.7e6, NMODL_MIXED: 312.6e6}[prec]
     roof["traffic"] = per_1m * ninst / 11548985 if window == 40 else None
     roof["traffic_unit"] = "bytes per launch"
     roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "

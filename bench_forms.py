@@ -505,6 +505,10 @@ def surrogate(dev, peaks, n=4_000_000, nsteps=200, n_pairs=10_000_000, epochs=60
     X, T = make_training_pairs(ctx, sur, p, n_pairs, seed=6)
     torch.cuda.synchronize()
     out["pairs_seconds"] = round(time.perf_counter() - t0, 2)
+    # torch loads its reduction kernels on first use (about a second), and
+    # fit averages the loss record with one: not part of the training
+    torch.zeros(2, device=X.device).mean().item()
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     losses = sur.fit(X, T, epochs=epochs, batch=batch, lr=2e-3)
     torch.cuda.synchronize()

@@ -370,6 +370,10 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
     // spills (measured 0.92x there; 1.16x on the cnexp networks, 1.06x with
     // ion arrays and the small systems).
     constexpr bool FAC_V = PREC == NMODL_MIXED && !KIN;
+    // MIXED with the 9-state scheme: the (e, g) slots hold both as float
+    // pairs (e in the first 8 bytes, g in the second), summed as float
+    // pairs by the owner
+    constexpr bool XGF = PREC == NMODL_MIXED && KIN;
     __shared__ double efac_s[FAC_V ? 3 * kMaxMechsFused : 1];   // e of current 3 t + q
     __shared__ float2 efac2_s[FAC_V ? 3 * kMaxMechsFused : 1];  // the same as float pairs
     __shared__ float fmul_s[FAC_V ? kMaxMechsFused * kMaxGates : 1];
@@ -764,13 +768,24 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                         }
                     } else if (M.kind == NMODL_HH) {
                         for (int q = 0; q < 3; ++q) {
-                            xg_s[o + q].x = M.hh_e[q];
+                            if (XGF) {
+                                const ff2 ep = ff_of(M.hh_e[q]);
+                                reinterpret_cast<float2*>(xg_s)[2 * (o + q)] = make_float2(ep.h, ep.l);
+                            } else {
+                                xg_s[o + q].x = M.hh_e[q];
+                            }
                             if (EXT && A.ions)
                                 tag_s[o + q] = q == 0 ? NMODL_ION_NA : q == 1 ? NMODL_ION_K : NMODL_ION_NONE;
                         }
                         o += 3;
                     } else if (!EXT || M.kind != NMODL_CACUM) {
-                        xg_s[o].x = (EXT && M.kind == NMODL_KIN3) ? M.k3.e : M.e;
+                        const double e = (EXT && M.kind == NMODL_KIN3) ? M.k3.e : M.e;
+                        if (XGF) {
+                            const ff2 ep = ff_of(e);
+                            reinterpret_cast<float2*>(xg_s)[2 * o] = make_float2(ep.h, ep.l);
+                        } else {
+                            xg_s[o].x = e;
+                        }
                         if (EXT && A.ions) tag_s[o] = (uint8_t)M.ion;
                         ++o;
                     }
@@ -902,6 +917,30 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                                 gg = mul_pow_d(gg, st[gi * cnt + j], M.gate[gi].power);
                             xg_s[sl].y = gg;
                         }
+                    } else if constexpr (XGF) {
+                        // g as a float pair beside e's (no FP64 instructions)
+                        const float2* st = st_f + st_off[q];
+                        const float* cf_p = curf_s[q];
+                        float2* gp = reinterpret_cast<float2*>(xg_s) + 1;
+                        if (M.kind == NMODL_HH) {
+                            const float m = st[j].x, h = st[cnt + j].x, nn = st[2 * cnt + j].x;
+                            const ff2 gl = ff_of(M.hh_g[2]);
+                            gp[2 * sl] = make_float2(cf_p[2] * m * m * m * h, 0.f);
+                            gp[2 * (sl + 1)] = make_float2(cf_p[3] * nn * nn * nn * nn, 0.f);
+                            gp[2 * (sl + 2)] = make_float2(gl.h, gl.l);
+                        } else if (M.kind == NMODL_KIN3 || M.kind == NMODL_KIN9) {
+                            const bool k3 = M.kind == NMODL_KIN3;
+                            const float2 x = st[(k3 ? M.k3.open : M.open) * cnt + j];
+                            const ff2 g = ff_mul(ff_of(k3 ? M.k3.gbar : M.gbar), ff2{x.x, x.y});
+                            gp[2 * sl] = make_float2(g.h, g.l);
+                        } else {
+                            float gf = cf_p[0];
+                            for (int gi = 0; gi < M.n_gates; ++gi) {
+                                const float xs = st[gi * cnt + j].x;
+                                for (int pw = 0; pw < M.gate[gi].power; ++pw) gf *= xs;
+                            }
+                            gp[2 * sl] = make_float2(gf, 0.f);
+                        }
                     } else {
                         const float2* st = st_f + st_off[q];
                         const float* cf_p = curf_s[q];
@@ -947,11 +986,27 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                         const float4 f = f_s[sl];
                         g = f2d_int((f.x * f.y) * f.z);
                         e = efac_s[__float_as_int(f.w)];
+                    } else if (XGF) {
+                        const float4 q = reinterpret_cast<const float4*>(xg_s)[sl];
+                        g = ff2d_int_nf(q.z, q.w);
+                        e = ff2d_int_nf(q.x, q.y);
                     } else {
                         const double2 eg = xg_s[sl];
                         g = eg.y;
                         e = eg.x;
                     }
+                };
+                // XGF: the same sums over the float-pair (e, g) slots
+                auto ff_sums_xg = [&](int a, int b, double& Gs, double& Xs) {
+                    ff2 G2{0.f, 0.f}, X2{0.f, 0.f};
+                    for (int sl = a; sl < b; ++sl) {
+                        const float4 q = reinterpret_cast<const float4*>(xg_s)[sl];
+                        const ff2 g{q.z, q.w};
+                        G2 = ff_add(G2, g);
+                        X2 = ff_add(X2, ff_mul(g, ff2{q.x, q.y}));
+                    }
+                    Gs = ff2d_int_nf(G2.h, G2.l);
+                    Xs = ff2d_int_nf(X2.h, X2.l);
                 };
                 // with ion arrays the calcium slots sit last: calcium every
                 // step (the buffer reads it), in a loop of its own, then
@@ -1024,6 +1079,8 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                     continue;
                 } else if constexpr (FAC_V) {
                     ff_sums(s0, sc, G, X);
+                } else if constexpr (XGF) {
+                    ff_sums_xg(s0, sc, G, X);
                 } else {
                     for (int sl = s0; sl < sc; ++sl) {
                         double g, e;
@@ -1035,6 +1092,8 @@ __global__ void __launch_bounds__(KIN == 0 ? kFusedMaxBlock
                 if (EXT && A.ions) {
                     if constexpr (FAC_V) {
                         ff_sums(sc, s1, Gca, Xca);
+                    } else if constexpr (XGF) {
+                        ff_sums_xg(sc, s1, Gca, Xca);
                     } else {
                         for (int sl = sc; sl < s1; ++sl) {
                             double g, e;

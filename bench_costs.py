@@ -137,10 +137,11 @@ def kin9_fp64_ops(updates: float = 2.0, c=DESIGN) -> float:
 
 
 def kin9_mixed_fp64_ops(updates: float) -> float:
-    """FP64 residue of the mixed 9-state step (FP32 rates and LU): the FP64
-    diagonal of J (24 adds), per update the FP64 residual (9 + 24 fma) and
-    y += delta (9), the current and the node."""
-    return 2 * KIN9_EDGES + updates * (9 + 2 * KIN9_EDGES + 9) + 5 + 1
+    """FP64 residue of the mixed 9-state step (FP32 rates and LU; the
+    residual's rate products and sums and J's diagonal as float pairs on the
+    FP32 pipe): per update x - y (9) and y += delta (9), the current and the
+    node."""
+    return updates * (9 + 9) + 5 + 1
 
 
 def kin3_fp64_ops(c=DESIGN) -> int:

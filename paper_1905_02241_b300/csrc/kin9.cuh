@@ -129,8 +129,16 @@ __device__ __forceinline__ int kin9_newton_d(const double (&dk_f)[kKinEdges],
     return iters;
 }
 
-// MIXED: FP32 rates and LU, FP64 residual and update; at most cap updates
-// (the first solve and cap - 1 refinements).
+// MIXED: FP32 rates and LU, the residual to about 48 bits and the update in
+// FP64; at most cap updates (the first solve and cap - 1 refinements).
+// The residual x - J y = (x - y) - out .* y + (inflows), out_a the column's
+// outflow rates (J's diagonal minus 1): x - y in FP64 (one subtraction per
+// state, exact enough for the small increment), the rate products and sums
+// as float pairs on the FP32 pipe from y split to 47 bits -- the same split
+// y_a in column a's outflow and in the inflows it feeds, so that the sum of
+// the residual stays the sum of x - y and the scheme keeps conserving to
+// FP64 rounding.  (All in FP64 the residual took 57 FP64 instructions per
+// refinement and the diagonal 48 per solve, the whole step's FP64 bound.)
 __device__ __forceinline__ int kin9_refine_mixed(const float (&dk_f)[kKinEdges],
                                                  const float (&dk_b)[kKinEdges],
                                                  const double (&x)[9], double (&y)[9], double tol,
@@ -138,46 +146,48 @@ __device__ __forceinline__ int kin9_refine_mixed(const float (&dk_f)[kKinEdges],
     nonconv = false;
 #pragma unroll
     for (int a = 0; a < 9; ++a) y[a] = x[a];
-    // FP64 copies of the FP32 rates (exact, integer pipe), and the FP64
-    // diagonal from them: columns of J sum to 1
-    double dkd_f[kKinEdges], dkd_b[kKinEdges], diag[9];
+    // each column's outflow as a float pair (TwoSum of the FP32 rates)
+    ff2 out[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) out[a] = ff2{0.0f, 0.0f};
 #pragma unroll
     for (int e = 0; e < kKinEdges; ++e) {
-        dkd_f[e] = f2d_int(dk_f[e]);
-        dkd_b[e] = f2d_int(dk_b[e]);
-    }
-#pragma unroll
-    for (int a = 0; a < 9; ++a) diag[a] = 1.0;
-#pragma unroll
-    for (int e = 0; e < kKinEdges; ++e) {
-        diag[edge_lo(e)] += dkd_f[e];
-        diag[edge_hi(e)] += dkd_b[e];
+        out[edge_lo(e)] = ff_add(out[edge_lo(e)], ff2{dk_f[e], 0.0f});
+        out[edge_hi(e)] = ff_add(out[edge_hi(e)], ff2{dk_b[e], 0.0f});
     }
     float M[9][9];
 #pragma unroll
     for (int a = 0; a < 9; ++a)
 #pragma unroll
         for (int b = 0; b < 9; ++b)
-            if (kin9_in_band(a, b)) M[a][b] = (a == b) ? d2f_int(diag[a]) : 0.0f;
+            if (kin9_in_band(a, b)) M[a][b] = (a == b) ? (1.0f + out[a].h) + out[a].l : 0.0f;
 #pragma unroll
     for (int e = 0; e < kKinEdges; ++e) {
         M[edge_hi(e)][edge_lo(e)] = -dk_f[e];
         M[edge_lo(e)][edge_hi(e)] = -dk_b[e];
     }
     kin9_lu_band(M);
+    // a float times a pair, renormalised
+    auto mul_fp = [](float s, ff2 b) {
+        const float p = __fmul_rn(s, b.h);
+        return ff_renorm(p, fmaf(s, b.l, fmaf(s, b.h, -p)));
+    };
     int iters = 0;
     while (iters < cap) {
-        double r[9];
+        ff2 yp[9], r[9];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) r[a] = x[a] - diag[a] * y[a];
+        for (int a = 0; a < 9; ++a) {
+            yp[a] = ff_of(y[a]);
+            r[a] = ff_sub(ff_of(x[a] - y[a]), ff_mul(out[a], yp[a]));
+        }
 #pragma unroll
         for (int e = 0; e < kKinEdges; ++e) {
-            r[edge_hi(e)] += dkd_f[e] * y[edge_lo(e)];
-            r[edge_lo(e)] += dkd_b[e] * y[edge_hi(e)];
+            r[edge_hi(e)] = ff_add(r[edge_hi(e)], mul_fp(dk_f[e], yp[edge_lo(e)]));
+            r[edge_lo(e)] = ff_add(r[edge_lo(e)], mul_fp(dk_b[e], yp[edge_hi(e)]));
         }
         float rf[9];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) rf[a] = d2f_int(r[a]);
+        for (int a = 0; a < 9; ++a) rf[a] = r[a].h + r[a].l;
         kin9_lu_band_solve(M, rf);
         float dmax = 0.0f;
 #pragma unroll

@@ -83,7 +83,7 @@ def test_kinetic_counts():
     assert C.kin9_fp64_ops(2.0) == 24 * 3 + 24 + 98 + 2 * (33 + 51 + 9) + 5 + 1
     assert C.kin9_fp64_ops(2.0, C.ALL_FP64) == 24 * 9 + 24 + (80 + 9 * 3) + 2 * (33 + 51 + 9) + 6
     # mixed: diagonal 24, per update residual 33 + update 9, current and node 6
-    assert C.kin9_mixed_fp64_ops(3.0) == 24 + 3 * 42 + 6
+    assert C.kin9_mixed_fp64_ops(3.0) == 3 * 18 + 6
 
 
 def test_small_system_counts():

@@ -133,16 +133,18 @@ __device__ __forceinline__ int kin3_step_mixed(const Kin3F& K, float vf, float d
         kb[e] = K.ab[e] * ex2_hw(-K.bb[e] * vf);
     }
     kin3_matrix(kf, kb, dtf, M);
-    double off[3][3], diag[3] = {1.0, 1.0, 1.0};
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) off[a][b] = (a == b) ? 0.0 : f2d_int(M[a][b]);
+    // The refinement's residual x - J y = (x - y) - out .* y - off y (off:
+    // J's off-diagonals, out_b = -sum_a off[a][b] the column's outflow, J's
+    // diagonal minus 1): x - y in FP64, the rest as float pairs on the FP32
+    // pipe from y split to 47 bits (the same split y_b in column b's outflow
+    // and in its off-diagonal terms, so the residual's sum stays that of
+    // x - y and the scheme conserves to FP64 rounding)
+    ff2 out[3] = {ff2{0.f, 0.f}, ff2{0.f, 0.f}, ff2{0.f, 0.f}};
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            if (a != b) diag[b] -= off[a][b];
+            if (a != b) out[b] = ff_sub(out[b], ff2{M[a][b], 0.f});
     float yf[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) yf[a] = d2f_int(x[a]);
@@ -153,14 +155,20 @@ __device__ __forceinline__ int kin3_step_mixed(const Kin3F& K, float vf, float d
     int iters = 1;
     bool done = false;
     for (int k = 0; k < ir_max && !done; ++k) {
+        ff2 yp[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) yp[a] = ff_of(y[a]);
         float r[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double ra = x[a] - diag[a] * y[a];
+            ff2 ra = ff_sub(ff_of(x[a] - y[a]), ff_mul(out[a], yp[a]));
 #pragma unroll
             for (int b = 0; b < 3; ++b)
-                if (b != a) ra -= off[a][b] * y[b];
-            r[a] = d2f_int(ra);
+                if (b != a) {
+                    const float p = __fmul_rn(M[a][b], yp[b].h);
+                    ra = ff_sub(ra, ff_renorm(p, fmaf(M[a][b], yp[b].l, fmaf(M[a][b], yp[b].h, -p))));
+                }
+            r[a] = ra.h + ra.l;
         }
         solve3(M, r);
         float dmax = 0.0f;

@@ -125,12 +125,18 @@ extern "C" {
 #define NMODL_ION_CA 3
 
 /* ------------------------------------------------------------- precision */
-#define NMODL_FP64 0  /* every operation in IEEE double                    */
+#define NMODL_FP64 0  /* IEEE double arithmetic, except inside the exp,
+                         reciprocal and division routines (parts in float
+                         pairs; results within 1.5, 1 and 1 ulp) and the
+                         cable form's tree solve (float pairs, about 46
+                         significand bits)                                   */
 #define NMODL_MIXED 1 /* rates and exponentials in FP32; gate increments
                          compensated (FP32 hi/lo pair folded into the FP64
-                         state); rhs/d accumulation, v update, the Newton
-                         residuals and refinements (kinetic schemes,
-                         calcium buffer) in FP64                             */
+                         state); node sums, the node update and the kinetic
+                         schemes' refinement residuals as float pairs (about
+                         48 bits) beside FP64 differences, the calcium
+                         buffer's refinement in FP64; v, rhs, d and the
+                         states stored in FP64                               */
 
 typedef struct nmodl_options {
     int32_t precision;       /* NMODL_FP64 (default) or NMODL_MIXED          */
@@ -428,9 +434,10 @@ NMODL_API int nmodl_kin9_solve(nmodl_mech *kin, int64_t n, const double *v,
 /* Let nmodl_state (and nmodl_step) of a NMODL_KIN9 mechanism use the
  * surrogate with residual tolerance tol (1-norm); s = NULL or tol <= 0
  * detaches.  Instances above the tolerance fall back to the Newton solve:
- * for tol >= 1e-5 (or a MIXED context) the FP32-LU Newton with FP64
- * residual refinement (FP32 rates: within about 1e-7 of the FP64 step, far
- * inside the tolerance), below that the FP64 Newton.  The fallback count is
+ * for tol >= 1e-5 (or a MIXED context) the FP32-LU Newton with refinement
+ * on an FP64 x - y and float-pair rate terms (FP32 rates: within about
+ * 1e-7 of the FP64 step, far inside the tolerance), below that the FP64
+ * Newton.  The fallback count is
  * reported by nmodl_stats. */
 NMODL_API int nmodl_mech_attach_surrogate(nmodl_mech *m, nmodl_surrogate *s,
                                           double tol);

@@ -480,8 +480,9 @@ def kinetic(dev, peaks, n=1_000_000, nsteps=200, steps=1):
                                      "LU, Newton updates, current"))
     out["roofline_mixed"] = _roof(C.kin9_mixed_fp64_ops(out["mixed_updates_per_solve"]),
                                   out["mixed"], peaks["fp64"], "fp64", what=(
-                                      "FP64 residue per instance-step: diagonal of J, FP64 "
-                                      "residuals and updates, current"))
+                                      "FP64 residue per instance-step: x - y and y += delta per "
+                                      "update (the residual's rate terms and J's diagonal run as "
+                                      "float pairs on the FP32 pipe), current"))
     return out
 
 

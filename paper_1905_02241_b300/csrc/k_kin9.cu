@@ -95,12 +95,14 @@ struct Kin9Launch {
     float kf[4 * kKinEdges];
 };
 
-// MIXED is compiled for three 128-thread blocks per SM (168 registers, a few
-// dozen bytes of spills): its FP64 residue then runs at 12 warps per SM
-// instead of 8 (measured 1.14x on 1M instances); the FP64 form keeps its
-// ~240 registers (two blocks), being bound by the FP64 pipe already.
+// MIXED is compiled for four 128-thread blocks per SM (128 registers, about
+// 190 bytes of spills): with the refinement's residual in float pairs the
+// step is bound by issue latency more than by the FP64 pipe, and 16 warps
+// per SM beat 12 at 168 registers without spills (measured 1.04x on 1M
+// instances; before that change three blocks were best, 1.14x over two);
+// the FP64 form keeps its ~240 registers, bound by the FP64 pipe already.
 template <int PREC, bool LIST>
-__global__ void __launch_bounds__(128, PREC == NMODL_MIXED ? 3 : 1)
+__global__ void __launch_bounds__(128, PREC == NMODL_MIXED ? 4 : 1)
     k_kin9_state(const Kin9D* __restrict__ kd, const Kin9Launch KL, int64_t n,
                  const int32_t* __restrict__ ni, const double* __restrict__ v,
                  double* st, int64_t stride, double dt_scalar,
